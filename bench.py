@@ -1,0 +1,321 @@
+"""Benchmark: Gauss-Newton Hessian-vector products per second on one GB300.
+
+Workload (the paper-scale configuration): 384 x 1152 interior grid at 8 m plus
+a 40-cell sponge (464 x 1232 padded), seeded layered/faulted velocity model
+1500-5500 m/s smoothed to the Gauss-Newton point, 32 Ricker shots at 10 Hz,
+384 receivers every 24 m, 3000 steps at dt = 0.727 ms, binomial checkpointing
+with 30 snapshots per shot.  One step = one H v (forward, Born and adjoint
+sweeps over all 32 shots, recomputation from snapshots, imaging reduction).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints ONE JSON line.  Under torchrun every rank runs its own independent
+H v (weak scaling, no collective on the data path); the time is the maximum
+over ranks.  --impl reference times the FP64 CPU oracle on a bounded sample
+of the same workload on the host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = None
+try:
+    METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
+except Exception:  # pragma: no cover
+    METRIC = "H·v/s and Gpt-updates/s (% HBM peak) at ≤2e-4 rel err vs FP64; serve p50/p99"
+
+CKPT = 30
+UNIT = "H·v/s"
+
+
+def workload_config(w):
+    return {
+        "workload": f"GN Hessian apply, {w.nz}x{w.nx} grid at {w.h:g} m + {w.nb}-cell sponge "
+                    f"({w.nz + 2 * w.nb}x{w.nx + 2 * w.nb} padded), {w.ns} shots x {w.nr} receivers, "
+                    f"{w.nt} steps, {w.k} vector, {CKPT} snapshots/shot (binomial checkpointing)",
+        "grid": [w.nz, w.nx], "sponge": w.nb, "h_m": w.h, "shots": w.ns, "receivers": w.nr, "steps": w.nt,
+        "dt_s": w.dt, "f0_hz": w.f0, "vectors": w.k, "snapshots_per_shot": CKPT,
+        "l2": "inputs larger than L2 (per-step working set of fields and snapshots >> 129 MB)",
+    }
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+def csrc_hash() -> str:
+    d = os.path.join(ROOT, "paper_2507_10804_gb300", "csrc")
+    h = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", self.gpu], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_sample(w, threads: int, nt_s: int):
+    """Time the FP64 oracle's H v on `threads` shots of the workload for nt_s steps;
+    returns (Gpt-updates/s, seconds, description)."""
+    from oracle import oracle as O
+    from paper_2507_10804_gb300 import synth
+    ns_s = threads
+    idx = np.linspace(0, w.ns - 1, ns_s).round().astype(int)
+    P = O.Problem(nz=w.nz, nx=w.nx, nb=w.nb, h=w.h, nt=nt_s, dt=w.dt, f0=w.f0, t0=w.t0, vmax=w.vmax,
+                  src_iz=w.acq.src_iz[idx], src_ix=w.acq.src_ix[idx], rec_iz=w.acq.rec_iz[idx],
+                  rec_ix=w.acq.rec_ix[idx], R=w.R, sigma=w.sigma)
+    m = w.m.astype(np.float32).astype(np.float64)
+    v = w.v.astype(np.float32).astype(np.float64)
+    t = time.perf_counter()
+    O.hessian_apply(P, m, v, nthreads=threads)
+    sec = time.perf_counter() - t
+    upd = 3.0 * P.NZ * P.NX * nt_s * ns_s
+    desc = (f"oracle H v on {ns_s} of {w.ns} shots x first {nt_s} of {w.nt} steps (full grid), "
+            f"{threads} threads; scaled by Gpt-updates to one full H v")
+    return upd / sec / 1e9, sec, desc
+
+
+def updates_per_hv(w) -> float:
+    return 3.0 * (w.nz + 2 * w.nb) * (w.nx + 2 * w.nb) * w.nt * w.ns * (1 + 2.0 * (w.k - 1) / 3.0)
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    threads = min(os.cpu_count() or 1, 8)
+    nt_s = 120
+    upds = []
+    for _ in range(args.warmup):
+        oracle_sample(w, threads, nt_s)
+    tot = 0.0
+    desc = ""
+    for _ in range(args.steps):
+        g, sec, desc = oracle_sample(w, threads, nt_s)
+        upds.append(g)
+        tot += sec
+    gups = float(np.mean(upds))
+    val = gups * 1e9 / updates_per_hv(w)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded layered/faulted velocity model; stands in for the paper's Marmousi)",
+        "config": workload_config(w), "gpt_updates_per_s": gups * 1e9,
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": desc},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def run_ours(args, w):
+    import torch
+    import torch.distributed as dist
+
+    from paper_2507_10804_gb300.hv import Problem, kernel_launches
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    P = Problem.from_workload(w, device=dev)
+    m = torch.tensor(w.m, dtype=torch.float32, device=dev)
+    v = torch.tensor(w.v, dtype=torch.float32, device=dev)
+    st = torch.cuda.current_stream(dev)
+
+    for _ in range(args.warmup):
+        P.hessian_apply(m, v, ckpt=CKPT)
+    torch.cuda.synchronize(dev)
+
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    gpu_index = vis.split(",")[local] if vis else str(local)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    P.profile(True)
+    P.profile_read()
+    with ClockSampler(gpu_index) as clk:
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+        n0 = kernel_launches()
+        e0.record(st)
+        for _ in range(args.steps):
+            P.hessian_apply(m, v, ckpt=CKPT)
+        e1.record(st)
+        torch.cuda.synchronize(dev)
+        n1 = kernel_launches()
+        if world > 1:
+            dist.barrier()
+    prof = P.profile_read()
+    P.profile(False)
+    ms = e0.elapsed_time(e1)
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = args.steps * world / (ms_max / 1e3)
+
+    # end to end through the public API with host buffers (pinned), copies inside the timed region
+    mh = torch.tensor(w.m, dtype=torch.float32).pin_memory()
+    vh = torch.tensor(w.v, dtype=torch.float32).pin_memory()
+    out_h = torch.empty(v.shape, dtype=torch.float32).pin_memory()
+    md, vd = torch.empty_like(m), torch.empty_like(v)
+    ke = max(1, min(args.steps, 3))
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        md.copy_(mh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        Hv = P.hessian_apply(md, vd, ckpt=CKPT)
+        out_h.copy_(Hv, non_blocking=True)
+        torch.cuda.synchronize(dev)
+    e2e_s = (time.perf_counter() - t0) / ke
+    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_val = world / float(t.item())
+
+    if rank == 0:
+        pk, pk_kind = peaks()
+        NZ, NX = w.nz + 2 * w.nb, w.nx + 2 * w.nb
+        pts = NZ * NX * w.ns
+        alg = {"fwd": pts * (16 + 16 * w.k), "advance": pts * 16, "adj": pts * w.k * 20}
+        kernels = {}
+        for kind, (n, tms) in prof.items():
+            if n:
+                kernels[kind] = {"launches_per_step": n / args.steps, "ms_per_step": tms / args.steps,
+                                 "avg_launch_us": tms / n * 1e3}
+                if kind in alg:
+                    kernels[kind]["algorithmic_GBps"] = alg[kind] * n / (tms / 1e3) / 1e9
+        dom = max(alg, key=lambda k: prof[k][1])
+        n_dom, t_dom = prof[dom]
+        achieved = alg[dom] * n_dom / (t_dom / 1e3) / 1e9
+        traffic = None
+        try:
+            tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+            ent = tr.get(dom)
+            if ent and ent.get("csrc") == csrc_hash():
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            pass
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                "algorithmic_bytes_per_launch": alg[dom], "peak_source": pk_kind}
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            threads = min(os.cpu_count() or 1, 8)
+            g, sec, desc = oracle_sample(w, threads, 120)
+            cpu = {"value": g * 1e9 / updates_per_hv(w), "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": desc, "seconds": sec, "gpt_updates_per_s": g * 1e9}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded layered/faulted velocity model; stands in for the paper's Marmousi)",
+            "config": workload_config(w),
+            "gpt_updates_per_s": value * updates_per_hv(w),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": int(mh.numel() * 4 + vh.numel() * 4),
+                    "d2h_bytes_per_step": int(out_h.numel() * 4)},
+            "gpu_launches": int(n1 - n0),
+            "clocks": clk.summary(),
+            "kernels": kernels,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=int(os.environ.get("WORLD_SIZE", "1")))
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--nt", type=int, default=None, help="override the step count (smaller runs)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    from paper_2507_10804_gb300 import synth
+    w = synth.workload(2, nt=args.nt)
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,194 @@
+/*
+ * hv.h -- C ABI of libhv, a single-GPU (sm_103a) library for the matrix-free
+ * Gauss-Newton Hessian-vector product of 2D acoustic seismic inversion, and
+ * the forward map, Born map, migration and misfit gradient built from the same
+ * wave solves.
+ *
+ * Paper: M. Hu, N. Alger, R. Nammour, O. Ghattas, "Accelerating seismic
+ * inversion and uncertainty quantification with efficient high-rank Hessian
+ * approximations" (arXiv 2507.10804).
+ *
+ *  - forward map f(m), data d = f(m) + noise ........... section 2, eq. (pde), eq. (data)
+ *  - Born operator F = grad f, migration F* ............ section 2.1, eq. (grad)
+ *  - misfit Phi = 1/2 |f(m) - d|^2_{Gamma^-1}, grad .... section 2.1, eq. (grad) (no prior term)
+ *  - H_d v = F* Gamma^-1 F v, two wave solves per source
+ *    (plus the forward field) .......................... section 3, opening of the section
+ *
+ * Discretisation (the paper fixes only the continuous equation
+ * (1/m^2) u_tt - lap u = s(t) delta(x - x_s) with m the wave speed):
+ *  - padded grid NZ = nz + 2 nb rows by NX = nx + 2 nb columns, spacing h,
+ *    zero (Dirichlet) values outside it;
+ *  - 8th-order central Laplacian, 2nd-order leapfrog in time;
+ *  - absorbing sponge of nb cells on all four sides: (1/m^2)(u_tt + q u_t) - lap u = f,
+ *    q = q_max (d/(nb h))^2 with d the distance into the sponge,
+ *    q_max = 3 vmax ln(1/R) / (2 nb h), q = max over the two axes in corners;
+ *  - Ricker source s(t) = (1 - 2 pi^2 f0^2 (t-t0)^2) exp(-pi^2 f0^2 (t-t0)^2)
+ *    injected as s(n dt)/h^2 at one node per shot;
+ *  - receivers sample u^{n+1} at their node after step n (d[n][r], n < nt);
+ *  - the model on the sponge is the interior model replicated from the
+ *    nearest edge cell (operator E); gradients and Hessian outputs are folded
+ *    back onto the interior by E^T;
+ *  - Gamma_noise = sigma^2 I.
+ *
+ * Conventions for every call below:
+ *  - Return value: HV_OK (0) or an HV_E* code; hv_last_error() returns a
+ *    thread-local message for the last failure of the calling thread.
+ *  - All array arguments of the compute calls are DEVICE pointers owned by the
+ *    caller, on the device that was current at hv_create; the library keeps
+ *    no reference to them after the call is enqueued.
+ *  - Models, vectors, gradients and Hessian outputs are interior fields
+ *    [nz][nx] (x fastest), float32 unless stated.  Data are [ns][nt][nr]
+ *    float32 (Born data: [k][ns][nt][nr]).
+ *  - Every compute call is asynchronous on `stream` (a cudaStream_t passed as
+ *    void*; NULL is the legacy default stream).  Outputs are valid once the
+ *    stream reaches the point of the call.
+ *  - Scratch memory: the caller passes `ws`, a device buffer of at least the
+ *    size hv_workspace_size() reports for the same operation, k and budget,
+ *    aligned to 256 bytes.  Calls enqueued on different streams must use
+ *    different workspaces.  The library never allocates device memory inside
+ *    a compute call.
+ *  - Checkpoint budget `ckpt`: number of wavefield snapshots (each a pair of
+ *    time levels) kept per shot for the adjoint sweep; HV_CKPT_ALL keeps every
+ *    time level instead (no recomputation).  With 1 <= ckpt < nt - 1 the
+ *    forward field is recomputed from snapshots by an optimal binomial
+ *    schedule; results are bitwise identical to HV_CKPT_ALL.
+ */
+#ifndef HV_H
+#define HV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define HV_OK 0
+#define HV_EINVAL 1     /* an argument failed validation (message says which)      */
+#define HV_ENOMEM 2     /* a workspace or host allocation was too small / failed   */
+#define HV_ECUDA 3      /* a CUDA runtime call failed (message carries its string) */
+#define HV_ETIMEOUT 4   /* a bounded device or host wait ran out                   */
+#define HV_EBUSY 5      /* the resource is in use (server queue full, ...)         */
+#define HV_ENOTSUP 6    /* the operation is declared but not provided              */
+
+#define HV_CKPT_ALL (-1)
+
+/* Operations for hv_workspace_size. */
+#define HV_OP_FWD 0         /* hv_fwd_model                      */
+#define HV_OP_BORN 1        /* hv_born                           */
+#define HV_OP_MIGRATE 2     /* hv_migrate                        */
+#define HV_OP_GRAD 3        /* hv_misfit_grad                    */
+#define HV_OP_HV 4          /* hv_hessian_apply(_f64out)         */
+#define HV_OP_WAVEFIELD 5   /* hv_wavefield                      */
+
+/* Interior grid and sponge.  h in metres. */
+typedef struct hv_grid {
+    int nz, nx;     /* interior rows (depth) and columns, >= 1            */
+    int nb;         /* sponge width in cells on every side, >= 0          */
+    double h;       /* grid spacing [m], > 0                              */
+} hv_grid;
+
+/* Acquisition and time axis.  Node indices are interior (iz, ix), int32,
+ * host pointers read only during hv_create. */
+typedef struct hv_acq {
+    int ns;                 /* shots, >= 1                                      */
+    const int *src_iz;      /* [ns] source node row, 0 <= iz < nz               */
+    const int *src_ix;      /* [ns] source node column, 0 <= ix < nx            */
+    int nr;                 /* receivers per shot, >= 1                         */
+    const int *rec_iz;      /* [ns*nr] receiver rows (distinct nodes per shot)  */
+    const int *rec_ix;      /* [ns*nr] receiver columns                         */
+    int nt;                 /* time steps, >= 1                                 */
+    double dt;              /* time step [s]; stable for vmax dt / h < 0.5547   */
+    double f0;              /* Ricker peak frequency [Hz]                       */
+    double t0;              /* Ricker delay [s]                                 */
+    double vmax;            /* velocity that sizes the sponge rate [m/s], > 0   */
+    double R;               /* sponge target reflection coefficient, (0, 1)     */
+    double sigma;           /* noise standard deviation, > 0                    */
+} hv_acq;
+
+typedef struct hv_handle hv_handle;
+
+/* Thread-local description of the calling thread's last failure ("" if none). */
+const char *hv_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int hv_version(void);
+
+/* Validate the problem and create a handle on the current device.  Copies
+ * the acquisition arrays; precomputes the source wavelet, the sponge profiles
+ * and the receiver tables on the device (small allocations owned by the
+ * handle).  Rejects: non-positive sizes, out-of-range or duplicate receiver
+ * nodes, out-of-range source nodes, non-positive h/dt/vmax/sigma, R outside
+ * (0, 1).  Blocks until the set-up kernels finish. */
+int hv_create(const hv_grid *grid, const hv_acq *acq, hv_handle **out);
+
+/* Release the handle and its device memory (synchronises the device). */
+int hv_destroy(hv_handle *h);
+
+/* Bytes of workspace needed by operation `op` (HV_OP_*) with k vectors and
+ * checkpoint budget ckpt (ignored by HV_OP_FWD/BORN/WAVEFIELD). */
+int hv_workspace_size(const hv_handle *h, int op, int k, int ckpt, size_t *bytes);
+
+/* Forward map f(m): d[ns][nt][nr] = receiver samples of u.  m: [nz][nx] wave
+ * speed [m/s], every value > 0. */
+int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, size_t ws_bytes, void *stream);
+
+/* Forward wavefields at n_out selected steps: out[i][s][NZ][NX] = u^{steps[i]+1}
+ * of shot s on the padded grid (steps: HOST array, ascending, each in [0, nt)). */
+int hv_wavefield(hv_handle *h, const float *m, int n_out, const int *steps, float *out,
+                 void *ws, size_t ws_bytes, void *stream);
+
+/* Born map F dm for k perturbations: dd[k][ns][nt][nr]; dm: [k][nz][nx]. */
+int hv_born(hv_handle *h, const float *m, const float *dm, int k, float *dd,
+            void *ws, size_t ws_bytes, void *stream);
+
+/* Migration F^T r for data r[ns][nt][nr]: g[nz][nx]. */
+int hv_migrate(hv_handle *h, const float *m, const float *r, float *g, int ckpt,
+               void *ws, size_t ws_bytes, void *stream);
+
+/* Misfit and gradient: phi (DEVICE double scalar) = (1/(2 sigma^2)) sum (f(m) - d_obs)^2,
+ * grad[nz][nx] = F^T (f(m) - d_obs) / sigma^2.  Reductions in FP64, fixed order. */
+int hv_misfit_grad(hv_handle *h, const float *m, const float *d_obs, double *phi, float *grad,
+                   int ckpt, void *ws, size_t ws_bytes, void *stream);
+
+/* Gauss-Newton Hessian apply: Hv[j] = F^T F v[j] / sigma^2 for j < k; v and Hv
+ * are [k][nz][nx].  Images accumulate in FP64 and are summed over shots in a
+ * fixed order, so results do not depend on batching. */
+int hv_hessian_apply(hv_handle *h, const float *m, const float *v, int k, float *Hv, int ckpt,
+                     void *ws, size_t ws_bytes, void *stream);
+
+/* As hv_hessian_apply with a double output Hv[k][nz][nx]. */
+int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k, double *Hv, int ckpt,
+                            void *ws, size_t ws_bytes, void *stream);
+
+/* Profiling.  While enabled on a handle, each kernel launch the handle makes
+ * is bracketed by CUDA events on the launching stream.  hv_profile_read waits
+ * for those events and returns, per kernel kind (HV_K_*), the number of
+ * launches and their summed device time [ms], then clears the record.  Not
+ * thread-safe: profile one call stream at a time per handle. */
+#define HV_K_FWD 0       /* forward step of the first sweep (with Born fields)  */
+#define HV_K_ADVANCE 1   /* forward recomputation step during the reversal      */
+#define HV_K_ADJ 2       /* adjoint step with zero-lag imaging                  */
+#define HV_K_OTHER 3     /* model preparation, residual, reductions, fold, copies */
+#define HV_K_COUNT 4
+int hv_profile(hv_handle *h, int enable);
+int hv_profile_read(hv_handle *h, long long *launches, double *ms);
+
+/* Number of kernels the library has launched in this process (all handles). */
+long long hv_kernel_launches(void);
+
+/* Host-only: the checkpoint schedule the library runs for nt steps and `slots`
+ * snapshots.  Writes up to max_actions triples (op, arg0, arg1) into actions
+ * (HOST int array of 3*max_actions) and the counts; ops: 0 = forward step n
+ * (first sweep), 1 = save current state to slot, 2 = restore slot (-1: zero
+ * state), 3 = recompute one forward step, 4 = adjoint step n.  n_advances is
+ * the number of recomputed forward steps.  No GPU needed. */
+int hv_checkpoint_schedule(int nt, int slots, int *actions, int max_actions, int *n_actions,
+                           long long *n_advances);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HV_H */

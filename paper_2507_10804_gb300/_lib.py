@@ -1,0 +1,87 @@
+"""ctypes binding of libhv (argument marshalling only; every step runs in the library).
+
+The library must have been built (``__graft_entry__.build()`` or
+``python -m paper_2507_10804_gb300.build``); loading fails loudly otherwise.
+There is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+from . import build as _build
+
+c_int, c_double, c_size_t, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_size_t, ctypes.c_void_p
+ip = ctypes.POINTER(c_int)
+fp = ctypes.c_void_p        # device float* / double* passed as integers
+HEADER = os.path.join(_build.INCLUDE, "hv.h")
+
+HV_OK, HV_EINVAL, HV_ENOMEM, HV_ECUDA, HV_ETIMEOUT, HV_EBUSY, HV_ENOTSUP = range(7)
+HV_CKPT_ALL = -1
+HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD = range(6)
+HV_K_FWD, HV_K_ADVANCE, HV_K_ADJ, HV_K_OTHER = range(4)
+HV_K_COUNT = 4
+
+
+class HvGrid(ctypes.Structure):
+    _fields_ = [("nz", c_int), ("nx", c_int), ("nb", c_int), ("h", c_double)]
+
+
+class HvAcq(ctypes.Structure):
+    _fields_ = [("ns", c_int), ("src_iz", ip), ("src_ix", ip), ("nr", c_int), ("rec_iz", ip), ("rec_ix", ip),
+                ("nt", c_int), ("dt", c_double), ("f0", c_double), ("t0", c_double), ("vmax", c_double),
+                ("R", c_double), ("sigma", c_double)]
+
+
+_SIGS = {
+    "hv_last_error": ([], ctypes.c_char_p),
+    "hv_version": ([], c_int),
+    "hv_create": ([ctypes.POINTER(HvGrid), ctypes.POINTER(HvAcq), ctypes.POINTER(c_void_p)], c_int),
+    "hv_destroy": ([c_void_p], c_int),
+    "hv_workspace_size": ([c_void_p, c_int, c_int, c_int, ctypes.POINTER(c_size_t)], c_int),
+    "hv_fwd_model": ([c_void_p, fp, fp, fp, c_size_t, c_void_p], c_int),
+    "hv_wavefield": ([c_void_p, fp, c_int, ip, fp, fp, c_size_t, c_void_p], c_int),
+    "hv_born": ([c_void_p, fp, fp, c_int, fp, fp, c_size_t, c_void_p], c_int),
+    "hv_migrate": ([c_void_p, fp, fp, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_misfit_grad": ([c_void_p, fp, fp, fp, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_hessian_apply": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_hessian_apply_f64out": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_profile": ([c_void_p, c_int], c_int),
+    "hv_profile_read": ([c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_double)], c_int),
+    "hv_kernel_launches": ([], ctypes.c_longlong),
+    "hv_checkpoint_schedule": ([c_int, c_int, ip, c_int, ip, ctypes.POINTER(ctypes.c_longlong)], c_int),
+}
+
+_lib = None
+
+
+def header_symbols() -> list[str]:
+    """Every function the public header declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(hv_\w+)\s*\(", text, flags=re.M)))
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libhv.so is not built ({_build.LIB}); run __graft_entry__.build() first")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (args, res) in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = lib
+    return _lib
+
+
+class HvError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libhv error {code}: {msg}")
+        self.code = code
+
+
+def check(rc: int) -> None:
+    if rc != HV_OK:
+        raise HvError(rc, load().hv_last_error().decode())

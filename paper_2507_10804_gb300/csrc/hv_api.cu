@@ -1,0 +1,625 @@
+// hv_api.cu -- the C ABI of libhv: validation, workspace layout and the
+// executor that drives the forward sweep, the checkpointed adjoint sweep and
+// the final reductions (paper section 3: H_d v by two wave solves per source
+// plus the forward field; section 2.1, eq. (grad): misfit gradient).
+#include "hv_internal.h"
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <set>
+#include <utility>
+
+namespace hvi {
+
+static thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+}  // namespace hvi
+
+#define HV_CK(call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
+    } while (0)
+#define HV_RT(call)                                                                                   \
+    do {                                                                                              \
+        int r_ = (call);                                                                              \
+        if (r_ != HV_OK) return r_;                                                                   \
+    } while (0)
+
+extern "C" const char *hv_last_error(void) { return hvi::g_err.c_str(); }
+extern "C" int hv_version(void) { return 100; }
+
+namespace {
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+int build_rectiles(hv_handle *h, const hvi::Tiling &t)
+{
+    long long key = (long long)t.TX * 65536 + t.TZ;
+    if (h->rectiles.count(key)) return HV_OK;
+    std::vector<int> off((size_t)h->ns * (t.ntiles + 1)), rec((size_t)h->ns * h->nr), pos((size_t)h->ns * h->nr);
+    for (int s = 0; s < h->ns; ++s) {
+        std::vector<std::pair<int, int>> tr;   // (tile, receiver)
+        for (int r = 0; r < h->nr; ++r) {
+            int z = h->h_rec_zx[2 * ((size_t)s * h->nr + r)], x = h->h_rec_zx[2 * ((size_t)s * h->nr + r) + 1];
+            tr.push_back({(z / t.TZ) * t.ntx + (x / t.TX), r});
+        }
+        std::stable_sort(tr.begin(), tr.end(), [](auto &a, auto &b) { return a.first < b.first; });
+        int *o = off.data() + (size_t)s * (t.ntiles + 1);
+        size_t i = 0;
+        for (int tile = 0; tile <= t.ntiles; ++tile) {
+            while (i < tr.size() && tr[i].first < tile) ++i;
+            o[tile] = (int)i;
+        }
+        for (size_t q = 0; q < tr.size(); ++q) {
+            int r = tr[q].second;
+            int z = h->h_rec_zx[2 * ((size_t)s * h->nr + r)], x = h->h_rec_zx[2 * ((size_t)s * h->nr + r) + 1];
+            rec[(size_t)s * h->nr + q] = r;
+            pos[(size_t)s * h->nr + q] = (z + hvi::GH) * h->P + (x + hvi::GH);
+        }
+    }
+    hvi::RecTiles rt;
+    rt.TX = t.TX;
+    rt.TZ = t.TZ;
+    rt.ntiles = t.ntiles;
+    HV_CK(cudaMalloc(&rt.off, off.size() * sizeof(int)));
+    HV_CK(cudaMalloc(&rt.rec, rec.size() * sizeof(int)));
+    HV_CK(cudaMalloc(&rt.pos, pos.size() * sizeof(int)));
+    HV_CK(cudaMemcpy(rt.off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HV_CK(cudaMemcpy(rt.rec, rec.data(), rec.size() * sizeof(int), cudaMemcpyHostToDevice));
+    HV_CK(cudaMemcpy(rt.pos, pos.data(), pos.size() * sizeof(int), cudaMemcpyHostToDevice));
+    h->rectiles[key] = rt;
+    return HV_OK;
+}
+
+const hvi::RecTiles &rectiles_for(const hv_handle *h, const hvi::Tiling &t)
+{
+    return h->rectiles.at((long long)t.TX * 65536 + t.TZ);
+}
+
+// ---------------------------------------------------------------- workspace layout
+struct Layout {
+    bool history = false;     // keep every time level instead of snapshots
+    int slots = 0;            // snapshot pairs per shot (binomial mode)
+    int G = 1;                // adjoint shot groups (partial images)
+    size_t fb = 0;            // bytes of one field batch (all shots)
+    size_t C = 0, b = 0, zero = 0, work = 0, store = 0, D = 0, dd = 0, img = 0, part = 0, total = 0;
+};
+
+constexpr int kResidualBlocks = 1024;
+
+int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
+{
+    if (op < HV_OP_FWD || op > HV_OP_WAVEFIELD) return hvi::fail(HV_EINVAL, "unknown operation %d", op);
+    const bool adjoint = (op == HV_OP_MIGRATE || op == HV_OP_GRAD || op == HV_OP_HV);
+    const bool born = (op == HV_OP_BORN || op == HV_OP_HV);
+    if (born && (k < 1 || k > 65535)) return hvi::fail(HV_EINVAL, "k = %d vectors; need 1 <= k <= 65535", k);
+    if (!born) k = 1;
+    if (adjoint) {
+        if (ckpt != HV_CKPT_ALL && ckpt < 1)
+            return hvi::fail(HV_EINVAL, "checkpoint budget %d; use HV_CKPT_ALL or a value >= 1", ckpt);
+        L.history = (ckpt == HV_CKPT_ALL) || (ckpt >= h->nt - 1);
+        L.slots = L.history ? 0 : ckpt;
+        L.G = hvk::adj_groups(h);
+    }
+    L.fb = align256((size_t)h->ns * h->fsize * sizeof(float));
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    const size_t fbytes = h->fsize * sizeof(float);
+    L.C = take(fbytes);
+    if (born) L.b = take((size_t)k * fbytes);
+    L.zero = take(L.fb);
+    if (!adjoint || !L.history) L.work = take(3 * L.fb);
+    if (adjoint) L.store = take(L.history ? (size_t)h->nt * L.fb : (size_t)2 * L.slots * L.fb);
+    if (born || adjoint) L.D = take((size_t)2 * k * L.fb);
+    const size_t ndata = (size_t)h->ns * h->nt * h->nr;
+    if (op == HV_OP_HV) L.dd = take((size_t)k * ndata * sizeof(float));
+    if (op == HV_OP_GRAD) L.dd = take(ndata * sizeof(float));
+    if (adjoint) L.img = take((size_t)L.G * k * h->fsize * sizeof(double));
+    if (op == HV_OP_GRAD) L.part = take(kResidualBlocks * sizeof(double));
+    L.total = o;
+    return HV_OK;
+}
+
+// ---------------------------------------------------------------- profiling
+cudaEvent_t take_event(hv_handle *h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Brackets the launches of its scope with events when profiling is on.
+struct ProfScope {
+    hv_handle *h;
+    cudaStream_t st;
+    int kind;
+    cudaEvent_t a = nullptr;
+    ProfScope(hv_handle *hh, cudaStream_t s, int k) : h(hh), st(s), kind(k)
+    {
+        if (h->prof_on) {
+            a = take_event(h);
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(h);
+            cudaEventRecord(b, st);
+            h->prof_rec.push_back({kind, {a, b}});
+        }
+    }
+};
+
+// ---------------------------------------------------------------- executor
+struct Exec {
+    hv_handle *h;
+    cudaStream_t st;
+    Layout L;
+    char *ws;
+    int k;
+    float *C, *b, *zero;
+    float *work[3];
+    float *D;            // 2 k field batches: Born fields (first sweep), adjoint fields (reversal)
+    double *img;
+    const float *cur, *prev;
+    int j;               // current state index: cur = u^j, prev = u^{j-1}
+
+    float *batch(char *base, size_t i) const { return reinterpret_cast<float *>(base + i * L.fb); }
+    float *Dbuf(int parity) const { return reinterpret_cast<float *>(reinterpret_cast<char *>(D) + (size_t)parity * k * L.fb); }
+    float *hist(int n) const { return n == 0 ? zero : batch(ws + L.store, (size_t)(n - 1)); }
+    float *slotA(int s) const { return batch(ws + L.store, (size_t)2 * s); }
+    float *slotB(int s) const { return batch(ws + L.store, (size_t)2 * s + 1); }
+
+    float *pick_work() const
+    {
+        for (int i = 0; i < 3; ++i)
+            if (work[i] != cur && work[i] != prev) return work[i];
+        return nullptr;
+    }
+
+    void init(hv_handle *hh, cudaStream_t s, const Layout &l, void *w, int kk)
+    {
+        h = hh; st = s; L = l; ws = (char *)w; k = kk;
+        C = reinterpret_cast<float *>(ws + L.C);
+        b = L.b ? reinterpret_cast<float *>(ws + L.b) : nullptr;
+        zero = reinterpret_cast<float *>(ws + L.zero);
+        for (int i = 0; i < 3; ++i) work[i] = L.work ? batch(ws + L.work, i) : nullptr;
+        D = reinterpret_cast<float *>(ws + L.D);
+        img = reinterpret_cast<double *>(ws + L.img);
+        cur = prev = zero;
+        j = 0;
+    }
+
+    // One forward step from the current state.  born: advance the Born fields
+    // too (first sweep of H v / Born map).
+    int forward(int n, bool born, float *d_u, float *d_du, float *target, int kind = HV_K_FWD)
+    {
+        ProfScope ps(h, st, kind);
+        if (n != j) return hvi::fail(HV_EINVAL, "internal: forward step %d from state %d", n, j);
+        float *next = target ? target : pick_work();
+        if (!next) return hvi::fail(HV_EINVAL, "internal: no free working buffer");
+        hvk::FwdLaunch a{};
+        a.u_cur = cur; a.u_prev = prev; a.u_next = next; a.C = C;
+        a.n = n;
+        if (born) {
+            a.b = b; a.k = k;
+            a.du_cur = Dbuf(n & 1);
+            a.du_io = Dbuf((n + 1) & 1);
+            a.d_du = d_du;
+        }
+        a.d_u = d_u;
+        HV_RT(hvk::launch_fwd(h, rectiles_for(h, hvk::tiling_fwd(h)), a, st));
+        prev = cur;
+        cur = next;
+        j = n + 1;
+        return HV_OK;
+    }
+
+    int save(int slot)
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        float *A = slotA(slot), *B = slotB(slot);
+        if (cur == A && prev == B) return HV_OK;
+        if (cur == B || prev == A) return hvi::fail(HV_EINVAL, "internal: snapshot slot %d aliases the state", slot);
+        if (prev != B) HV_CK(cudaMemcpyAsync(B, prev, L.fb, cudaMemcpyDeviceToDevice, st));
+        if (cur != A) HV_CK(cudaMemcpyAsync(A, cur, L.fb, cudaMemcpyDeviceToDevice, st));
+        cur = A;
+        prev = B;
+        return HV_OK;
+    }
+
+    void restore(int slot, int state)
+    {
+        if (slot < 0) {
+            cur = prev = zero;
+            j = 0;
+        } else {
+            cur = slotA(slot);
+            prev = slotB(slot);
+            j = state;
+        }
+    }
+
+    int adjoint(int n, const float *u, const float *r, int r_per_vector, float rscale, int kk)
+    {
+        ProfScope ps(h, st, HV_K_ADJ);
+        hvk::AdjLaunch a{};
+        a.u = u;
+        a.lam1 = Dbuf((n + 1) & 1);
+        a.lam_io = Dbuf(n & 1);
+        a.C = C;
+        a.r = r;
+        a.r_per_vector = r_per_vector;
+        a.rscale = rscale;
+        a.img = img;
+        a.n = n;
+        a.k = kk;
+        a.G = L.G;
+        return hvk::launch_adj(h, rectiles_for(h, hvk::tiling_adj(h)), a, st);
+    }
+
+    const float *u_for(int n)
+    {
+        if (j == n) return cur;
+        if (j == n + 1) return prev;
+        return nullptr;
+    }
+};
+
+int check_common(hv_handle *h, const void *ws, size_t ws_bytes, int op, int k, int ckpt, Layout &L)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != h->device) return hvi::fail(HV_EINVAL, "current device %d is not the handle's device %d", dev, h->device);
+    HV_RT(make_layout(h, op, k, ckpt, L));
+    if (!ws) return hvi::fail(HV_EINVAL, "null workspace");
+    if (((uintptr_t)ws & 255u) != 0) return hvi::fail(HV_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < L.total)
+        return hvi::fail(HV_ENOMEM, "workspace of %zu bytes; this call needs %zu", ws_bytes, L.total);
+    return HV_OK;
+}
+
+const std::vector<hvi::Action> *schedule_for(hv_handle *h, int slots)
+{
+    std::lock_guard<std::mutex> g(h->mu);
+    auto it = h->schedules.find(slots);
+    if (it != h->schedules.end()) return &it->second;
+    std::vector<hvi::Action> acts;
+    long long adv = 0;
+    hvi::build_schedule(h->nt, slots, acts, &adv);
+    auto r = h->schedules.emplace(slots, std::move(acts));
+    return &r.first->second;
+}
+
+// The shared driver of migrate / misfit_grad / hessian_apply.
+//   kind 0: migrate   r = user data,                         scale h^2
+//   kind 1: gradient  r = f(m) - d_obs (computed),           scale h^2 / sigma^2
+//   kind 2: H v       r = F v (Born data, computed),         scale h^2 / sigma^2
+int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, float *out32, double *out64,
+                double *phi, int ckpt, void *ws, size_t ws_bytes, cudaStream_t st)
+{
+    const int op = kind == 0 ? HV_OP_MIGRATE : (kind == 1 ? HV_OP_GRAD : HV_OP_HV);
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, op, kind == 2 ? k : 1, ckpt, L));
+    const int kk = (kind == 2) ? k : 1;
+    Exec E;
+    E.init(h, st, L, ws, kk);
+    const bool born = (kind == 2);
+    HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * kk * L.fb, st));
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_prep(h, m, born ? in : nullptr, born ? kk : 0, E.C, born ? E.b : nullptr, st));
+    }
+    float *dd = (kind != 0) ? reinterpret_cast<float *>((char *)ws + L.dd) : nullptr;
+
+    const std::vector<hvi::Action> *sched = L.history ? nullptr : schedule_for(h, L.slots);
+    size_t ai = 0;
+    // ---- first sweep
+    for (int n = 0; n < h->nt; ++n) {
+        float *target = L.history ? E.hist(n + 1) : nullptr;
+        if (sched) {
+            const hvi::Action &a = (*sched)[ai++];
+            if (a.op != hvi::ACT_FORWARD || a.a0 != n) return hvi::fail(HV_EINVAL, "internal: schedule order");
+        }
+        HV_RT(E.forward(n, born, kind == 1 ? dd : nullptr, kind == 2 ? dd : nullptr, target));
+        if (sched && ai < sched->size() && (*sched)[ai].op == hvi::ACT_SAVE) HV_RT(E.save((*sched)[ai++].a0));
+    }
+    // ---- adjoint sources
+    const float *r = in;
+    int r_per_vector = 0;
+    float rscale = (float)(h->h * h->h);
+    if (kind == 1) {
+        ProfScope ps(h, st, HV_K_OTHER);
+        double *part = reinterpret_cast<double *>((char *)ws + L.part);
+        HV_RT(hvk::launch_residual(h, dd, in, dd, part, kResidualBlocks, st));
+        HV_RT(hvk::launch_reduce_phi(part, kResidualBlocks, 0.5 / (h->sigma * h->sigma), phi, st));
+        r = dd;
+        rscale = (float)(h->h * h->h / (h->sigma * h->sigma));
+    } else if (kind == 2) {
+        r = dd;
+        r_per_vector = 1;
+        rscale = (float)(h->h * h->h / (h->sigma * h->sigma));
+    }
+    // ---- reversal
+    HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * kk * L.fb, st));
+    HV_CK(cudaMemsetAsync((char *)ws + L.img, 0, (size_t)L.G * kk * h->fsize * sizeof(double), st));
+    if (L.history) {
+        for (int n = h->nt - 1; n >= 0; --n) HV_RT(E.adjoint(n, E.hist(n), r, r_per_vector, rscale, kk));
+    } else {
+        for (; ai < sched->size(); ++ai) {
+            const hvi::Action &a = (*sched)[ai];
+            switch (a.op) {
+            case hvi::ACT_SAVE: HV_RT(E.save(a.a0)); break;
+            case hvi::ACT_RESTORE: E.restore(a.a0, a.a1); break;
+            case hvi::ACT_ADVANCE: HV_RT(E.forward(E.j, false, nullptr, nullptr, nullptr, HV_K_ADVANCE)); break;
+            case hvi::ACT_ADJOINT: {
+                const float *u = E.u_for(a.a0);
+                if (!u) return hvi::fail(HV_EINVAL, "internal: adjoint step %d from state %d", a.a0, E.j);
+                HV_RT(E.adjoint(a.a0, u, r, r_per_vector, rscale, kk));
+                break;
+            }
+            default: return hvi::fail(HV_EINVAL, "internal: forward step inside the reversal");
+            }
+        }
+    }
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_finalize(h, m, E.img, L.G, kk, out32, out64, st));
+    }
+    return HV_OK;
+}
+
+int validate_create(const hv_grid *g, const hv_acq *a)
+{
+    if (!g || !a) return hvi::fail(HV_EINVAL, "null grid or acquisition");
+    if (g->nz < 1 || g->nx < 1) return hvi::fail(HV_EINVAL, "grid %d x %d; need nz, nx >= 1", g->nz, g->nx);
+    if (g->nb < 0) return hvi::fail(HV_EINVAL, "sponge width %d < 0", g->nb);
+    if (!(g->h > 0)) return hvi::fail(HV_EINVAL, "grid spacing must be > 0");
+    long long NZ = g->nz + 2LL * g->nb, NX = g->nx + 2LL * g->nb;
+    if (NZ > 65535 || NX > (1 << 20)) return hvi::fail(HV_EINVAL, "padded grid %lld x %lld too large", NZ, NX);
+    if (a->ns < 1 || a->nr < 1 || a->nt < 1)
+        return hvi::fail(HV_EINVAL, "ns = %d, nr = %d, nt = %d; all must be >= 1", a->ns, a->nr, a->nt);
+    if (a->ns > 65535) return hvi::fail(HV_EINVAL, "ns = %d > 65535", a->ns);
+    if (!a->src_iz || !a->src_ix || !a->rec_iz || !a->rec_ix) return hvi::fail(HV_EINVAL, "null acquisition array");
+    if (!(a->dt > 0) || !(a->vmax > 0) || !(a->sigma > 0) || !(a->f0 > 0))
+        return hvi::fail(HV_EINVAL, "dt, f0, vmax and sigma must be > 0");
+    if (!(a->R > 0 && a->R < 1)) return hvi::fail(HV_EINVAL, "sponge reflection coefficient must lie in (0, 1)");
+    for (int s = 0; s < a->ns; ++s) {
+        if (a->src_iz[s] < 0 || a->src_iz[s] >= g->nz || a->src_ix[s] < 0 || a->src_ix[s] >= g->nx)
+            return hvi::fail(HV_EINVAL, "shot %d source node (%d, %d) outside the %d x %d interior", s, a->src_iz[s],
+                             a->src_ix[s], g->nz, g->nx);
+        std::set<long long> seen;
+        for (int r = 0; r < a->nr; ++r) {
+            size_t i = (size_t)s * a->nr + r;
+            if (a->rec_iz[i] < 0 || a->rec_iz[i] >= g->nz || a->rec_ix[i] < 0 || a->rec_ix[i] >= g->nx)
+                return hvi::fail(HV_EINVAL, "shot %d receiver %d node (%d, %d) outside the interior", s, r,
+                                 a->rec_iz[i], a->rec_ix[i]);
+            if (!seen.insert((long long)a->rec_iz[i] * g->nx + a->rec_ix[i]).second)
+                return hvi::fail(HV_EINVAL, "shot %d receiver %d duplicates another receiver's node", s, r);
+        }
+    }
+    return HV_OK;
+}
+
+}  // namespace
+
+extern "C" int hv_create(const hv_grid *g, const hv_acq *a, hv_handle **out)
+{
+    if (!out) return hvi::fail(HV_EINVAL, "null output handle pointer");
+    *out = nullptr;
+    HV_RT(validate_create(g, a));
+    hv_handle *h = new hv_handle();
+    h->nz = g->nz; h->nx = g->nx; h->nb = g->nb; h->h = g->h;
+    h->NZ = g->nz + 2 * g->nb;
+    h->NX = g->nx + 2 * g->nb;
+    h->P = ((h->NX + 2 * hvi::GH) + 31) / 32 * 32;
+    h->rows = h->NZ + 2 * hvi::GH;
+    h->fsize = ((size_t)h->rows * h->P + 63) / 64 * 64;
+    h->ns = a->ns; h->nr = a->nr; h->nt = a->nt;
+    h->dt = a->dt; h->f0 = a->f0; h->t0 = a->t0; h->vmax = a->vmax; h->R = a->R; h->sigma = a->sigma;
+    h->h_src_zx.resize(2 * (size_t)h->ns);
+    h->h_rec_zx.resize(2 * (size_t)h->ns * h->nr);
+    for (int s = 0; s < h->ns; ++s) {
+        h->h_src_zx[2 * s] = a->src_iz[s] + h->nb;
+        h->h_src_zx[2 * s + 1] = a->src_ix[s] + h->nb;
+    }
+    for (size_t i = 0; i < (size_t)h->ns * h->nr; ++i) {
+        h->h_rec_zx[2 * i] = a->rec_iz[i] + h->nb;
+        h->h_rec_zx[2 * i + 1] = a->rec_ix[i] + h->nb;
+    }
+    auto cleanup_fail = [&](int rc) {
+        hv_destroy(h);
+        return rc;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return cleanup_fail(hvi::fail(HV_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e)));
+    if ((e = cudaMalloc(&h->wavelet, sizeof(float) * h->nt)) != cudaSuccess ||
+        (e = cudaMalloc(&h->az, sizeof(float) * h->NZ)) != cudaSuccess ||
+        (e = cudaMalloc(&h->ax, sizeof(float) * h->NX)) != cudaSuccess ||
+        (e = cudaMalloc(&h->src_zx, sizeof(int) * h->h_src_zx.size())) != cudaSuccess ||
+        (e = cudaMalloc(&h->rec_zx, sizeof(int) * h->h_rec_zx.size())) != cudaSuccess)
+        return cleanup_fail(hvi::fail(HV_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e)));
+    if ((e = cudaMemcpy(h->src_zx, h->h_src_zx.data(), sizeof(int) * h->h_src_zx.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess ||
+        (e = cudaMemcpy(h->rec_zx, h->h_rec_zx.data(), sizeof(int) * h->h_rec_zx.size(), cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+        return cleanup_fail(hvi::fail(HV_ECUDA, "cudaMemcpy: %s", cudaGetErrorString(e)));
+    int rc = hvk::launch_setup(h, 0);
+    if (rc != HV_OK) return cleanup_fail(rc);
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess)
+        return cleanup_fail(hvi::fail(HV_ECUDA, "set-up kernels: %s", cudaGetErrorString(e)));
+    if ((rc = build_rectiles(h, hvk::tiling_fwd(h))) != HV_OK) return cleanup_fail(rc);
+    if ((rc = build_rectiles(h, hvk::tiling_adj(h))) != HV_OK) return cleanup_fail(rc);
+    *out = h;
+    return HV_OK;
+}
+
+extern "C" int hv_destroy(hv_handle *h)
+{
+    if (!h) return HV_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->wavelet);
+    cudaFree(h->az);
+    cudaFree(h->ax);
+    cudaFree(h->src_zx);
+    cudaFree(h->rec_zx);
+    for (auto &r : h->prof_rec) {
+        cudaEventDestroy(r.second.first);
+        cudaEventDestroy(r.second.second);
+    }
+    for (cudaEvent_t e : h->ev_pool) cudaEventDestroy(e);
+    for (auto &kv : h->rectiles) {
+        cudaFree(kv.second.off);
+        cudaFree(kv.second.rec);
+        cudaFree(kv.second.pos);
+    }
+    delete h;
+    return HV_OK;
+}
+
+extern "C" int hv_workspace_size(const hv_handle *h, int op, int k, int ckpt, size_t *bytes)
+{
+    if (!h || !bytes) return hvi::fail(HV_EINVAL, "null handle or output");
+    Layout L;
+    if (op == HV_OP_FWD || op == HV_OP_BORN || op == HV_OP_WAVEFIELD) ckpt = HV_CKPT_ALL;
+    HV_RT(make_layout(h, op, k, ckpt, L));
+    *bytes = L.total;
+    return HV_OK;
+}
+
+extern "C" int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, size_t ws_bytes, void *stream)
+{
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_FWD, 1, HV_CKPT_ALL, L));
+    if (!m || !d) return hvi::fail(HV_EINVAL, "null model or data pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    Exec E;
+    E.init(h, st, L, ws, 0);
+    HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
+    for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, false, d, nullptr, nullptr));
+    return HV_OK;
+}
+
+extern "C" int hv_wavefield(hv_handle *h, const float *m, int n_out, const int *steps, float *out, void *ws,
+                            size_t ws_bytes, void *stream)
+{
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_WAVEFIELD, 1, HV_CKPT_ALL, L));
+    if (!m || !out || !steps || n_out < 1) return hvi::fail(HV_EINVAL, "null pointer or n_out < 1");
+    for (int i = 0; i < n_out; ++i)
+        if (steps[i] < 0 || steps[i] >= h->nt || (i > 0 && steps[i] <= steps[i - 1]))
+            return hvi::fail(HV_EINVAL, "steps must be ascending and in [0, nt)");
+    cudaStream_t st = (cudaStream_t)stream;
+    Exec E;
+    E.init(h, st, L, ws, 0);
+    HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
+    int i = 0;
+    for (int n = 0; n <= steps[n_out - 1]; ++n) {
+        HV_RT(E.forward(n, false, nullptr, nullptr, nullptr));
+        if (n == steps[i]) {
+            HV_RT(hvk::launch_copy_wavefield(h, E.cur, out + (size_t)i * h->ns * h->NZ * h->NX, st));
+            ++i;
+        }
+    }
+    return HV_OK;
+}
+
+extern "C" int hv_born(hv_handle *h, const float *m, const float *dm, int k, float *dd, void *ws, size_t ws_bytes,
+                       void *stream)
+{
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_BORN, k, HV_CKPT_ALL, L));
+    if (!m || !dm || !dd) return hvi::fail(HV_EINVAL, "null model, perturbation or output");
+    cudaStream_t st = (cudaStream_t)stream;
+    Exec E;
+    E.init(h, st, L, ws, k);
+    HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * k * L.fb, st));
+    HV_RT(hvk::launch_prep(h, m, dm, k, E.C, E.b, st));
+    for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, true, nullptr, dd, nullptr));
+    return HV_OK;
+}
+
+extern "C" int hv_migrate(hv_handle *h, const float *m, const float *r, float *g, int ckpt, void *ws, size_t ws_bytes,
+                          void *stream)
+{
+    if (!m || !r || !g) return hvi::fail(HV_EINVAL, "null model, data or output");
+    return run_adjoint(h, 0, m, r, 1, g, nullptr, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int hv_misfit_grad(hv_handle *h, const float *m, const float *d_obs, double *phi, float *grad, int ckpt,
+                              void *ws, size_t ws_bytes, void *stream)
+{
+    if (!m || !d_obs || !phi || !grad) return hvi::fail(HV_EINVAL, "null model, data, phi or gradient");
+    return run_adjoint(h, 1, m, d_obs, 1, grad, nullptr, phi, ckpt, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int hv_hessian_apply(hv_handle *h, const float *m, const float *v, int k, float *Hv, int ckpt, void *ws,
+                                size_t ws_bytes, void *stream)
+{
+    if (!m || !v || !Hv) return hvi::fail(HV_EINVAL, "null model, vector or output");
+    return run_adjoint(h, 2, m, v, k, Hv, nullptr, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k, double *Hv, int ckpt,
+                                       void *ws, size_t ws_bytes, void *stream)
+{
+    if (!m || !v || !Hv) return hvi::fail(HV_EINVAL, "null model, vector or output");
+    return run_adjoint(h, 2, m, v, k, nullptr, Hv, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
+}
+
+extern "C" int hv_profile(hv_handle *h, int enable)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    h->prof_on = enable != 0;
+    return HV_OK;
+}
+
+extern "C" int hv_profile_read(hv_handle *h, long long *launches, double *ms)
+{
+    if (!h || !launches || !ms) return hvi::fail(HV_EINVAL, "null handle or output");
+    for (int k = 0; k < HV_K_COUNT; ++k) {
+        launches[k] = 0;
+        ms[k] = 0.0;
+    }
+    for (auto &r : h->prof_rec) {
+        HV_CK(cudaEventSynchronize(r.second.second));
+        float t = 0.f;
+        HV_CK(cudaEventElapsedTime(&t, r.second.first, r.second.second));
+        launches[r.first] += 1;
+        ms[r.first] += t;
+        h->ev_pool.push_back(r.second.first);
+        h->ev_pool.push_back(r.second.second);
+    }
+    h->prof_rec.clear();
+    return HV_OK;
+}
+
+extern "C" long long hv_kernel_launches(void) { return hvk::launches_so_far(); }

@@ -1,0 +1,123 @@
+// hv_internal.h -- private declarations shared by the libhv translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "hv.h"
+
+namespace hvi {
+
+// ---------------------------------------------------------------- status
+int fail(int code, const char *fmt, ...);
+inline int ok() { return HV_OK; }
+
+// ---------------------------------------------------------------- schedule
+enum { ACT_FORWARD = 0, ACT_SAVE = 1, ACT_RESTORE = 2, ACT_ADVANCE = 3, ACT_ADJOINT = 4 };
+struct Action {
+    int op, a0, a1;
+};
+long long seg_cost(long long L, int f);
+int build_schedule(int nt, int slots, std::vector<Action> &out, long long *n_advances);
+
+// ---------------------------------------------------------------- geometry
+// Fields live on the padded grid (NZ x NX) inside a ghost band of GH = 4 zero
+// cells on every side: padded node (z, x) sits at offset (z + 4) * P + (x + 4)
+// of a field of `rows` = NZ + 8 rows and pitch P (a multiple of 4 floats, so
+// every row and every 4-aligned column starts on a 16-byte boundary).  The
+// ghost band is never written, which gives the Dirichlet zeros of the
+// stencil without bounds checks.
+constexpr int GH = 4;
+
+// Tiling of one kernel configuration: TX x TZ interior points per CTA.
+struct Tiling {
+    int TX, TZ, ntx, ntz, ntiles;
+};
+
+// Receivers of every shot grouped by tile (for fused sampling/injection).
+struct RecTiles {
+    int TX = 0, TZ = 0, ntiles = 0;
+    int *off = nullptr;   // [ns][ntiles+1] start of each tile's receivers
+    int *rec = nullptr;   // [ns][nr] receiver index, tile-sorted
+    int *pos = nullptr;   // [ns][nr] field offset of that receiver
+};
+
+}  // namespace hvi
+
+struct hv_handle {
+    int device = 0;
+    int nz = 0, nx = 0, nb = 0, NZ = 0, NX = 0;
+    int P = 0, rows = 0;
+    size_t fsize = 0;            // floats per field (rows * P rounded up to 64)
+    double h = 0, dt = 0, f0 = 0, t0 = 0, vmax = 0, R = 0, sigma = 1;
+    int ns = 0, nr = 0, nt = 0;
+    // device arrays owned by the handle
+    float *wavelet = nullptr;    // [nt]   s(n dt)
+    float *az = nullptr;         // [NZ]   sponge a = q dt / 2 along z
+    float *ax = nullptr;         // [NX]   sponge a = q dt / 2 along x
+    int *src_zx = nullptr;       // [ns][2] padded (z, x) of each source
+    int *rec_zx = nullptr;       // [ns*nr][2] padded (z, x) of each receiver
+    std::vector<int> h_src_zx, h_rec_zx;
+    std::mutex mu;
+    std::map<long long, hvi::RecTiles> rectiles;                 // keyed by TX * 65536 + TZ
+    std::map<int, std::vector<hvi::Action>> schedules;           // keyed by slots
+    // profiling (hv_profile)
+    bool prof_on = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> prof_rec;
+};
+
+namespace hvk {
+
+// Kernel configurations (see hv_kernels.cu).
+hvi::Tiling tiling_fwd(const hv_handle *h);
+hvi::Tiling tiling_adj(const hv_handle *h);
+
+struct FwdLaunch {
+    const float *u_cur, *u_prev;   // field batches [ns][fsize]
+    float *u_next;                 // may be nullptr (Born-only groups never write u)
+    const float *C;                // [fsize] m^2 dt^2 / h^2
+    const float *b;                // [k][fsize] 2 dm / m (Born) or nullptr
+    const float *du_cur;           // [k][ns][fsize] Born field at n
+    float *du_io;                  // [k][ns][fsize] Born field at n-1 in, n+1 out
+    float *d_u;                    // [ns][nt][nr] samples of u^{n+1} or nullptr
+    float *d_du;                   // [k][ns][nt][nr] samples of du^{n+1} or nullptr
+    int n, k;
+};
+int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const FwdLaunch &a, cudaStream_t st);
+
+struct AdjLaunch {
+    const float *u;                // u^n field batch [ns][fsize]
+    const float *lam1;             // [k][ns][fsize] lam^{n+1}
+    float *lam_io;                 // [k][ns][fsize] lam^{n+2} in, lam^n out
+    const float *C;
+    const float *r;                // adjoint source data, [k or 1][ns][nt][nr]
+    int r_per_vector;              // 1 if r has a vector dimension
+    float rscale;                  // multiplies r (h^2 / sigma^2 or h^2)
+    double *img;                   // [G][k][fsize] partial images
+    int n, k, G;
+};
+int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const AdjLaunch &a, cudaStream_t st);
+int adj_groups(const hv_handle *h);
+
+int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float *C, float *b, cudaStream_t st);
+int launch_finalize(const hv_handle *h, const float *m, const double *img, int G, int k, float *out32,
+                    double *out64, cudaStream_t st);
+int launch_residual(const hv_handle *h, const float *d, const float *dobs, float *r, double *partials,
+                    int nblocks, cudaStream_t st);
+int launch_reduce_phi(const double *partials, int nblocks, double scale, double *phi, cudaStream_t st);
+int launch_copy_wavefield(const hv_handle *h, const float *u, float *out, cudaStream_t st);
+int launch_setup(hv_handle *h, cudaStream_t st);
+
+// Process-wide kernel launch counter (hv_kernel_launches).
+void count_launch();
+long long launches_so_far();
+
+}  // namespace hvk

@@ -1,0 +1,184 @@
+"""Python face of libhv: one ``Problem`` per grid + acquisition, calls that take
+and return CUDA tensors.  Marshalling only -- every step of the path runs in
+the library's kernels on the caller's current CUDA stream.
+
+Names follow the C ABI (include/hv.h): fwd_model, wavefield, born, migrate,
+misfit_grad, hessian_apply.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import HV_CKPT_ALL, HV_OP_BORN, HV_OP_FWD, HV_OP_GRAD, HV_OP_HV, HV_OP_MIGRATE, HV_OP_WAVEFIELD, check
+
+__all__ = ["Problem", "HV_CKPT_ALL", "checkpoint_schedule"]
+
+
+def _i32(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32).reshape(-1))
+
+
+def _dev(t: torch.Tensor, dtype, shape, name: str, device) -> int:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+    if t.device != device:
+        raise ValueError(f"{name} is on {t.device}, the problem on {device}")
+    return t.data_ptr()
+
+
+class Problem:
+    """A discretised acquisition (grid, sponge, time axis, sources, receivers) on one GPU."""
+
+    def __init__(self, nz, nx, nb, h, nt, dt, f0, t0, vmax, src_iz, src_ix, rec_iz, rec_ix,
+                 R=1e-3, sigma=1.0, device=None):
+        self.lib = _lib.load()
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.nz, self.nx, self.nb, self.h = int(nz), int(nx), int(nb), float(h)
+        self.nt, self.dt = int(nt), float(dt)
+        self.src_iz, self.src_ix = _i32(src_iz), _i32(src_ix)
+        self.rec_iz, self.rec_ix = _i32(rec_iz), _i32(rec_ix)
+        self.ns = self.src_iz.size
+        self.nr = self.rec_iz.size // max(self.ns, 1)
+        self.sigma = float(sigma)
+        g = _lib.HvGrid(self.nz, self.nx, self.nb, self.h)
+        a = _lib.HvAcq(self.ns, self.src_iz.ctypes.data_as(_lib.ip), self.src_ix.ctypes.data_as(_lib.ip),
+                       self.nr, self.rec_iz.ctypes.data_as(_lib.ip), self.rec_ix.ctypes.data_as(_lib.ip),
+                       self.nt, self.dt, float(f0), float(t0), float(vmax), float(R), self.sigma)
+        handle = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hv_create(ctypes.byref(g), ctypes.byref(a), ctypes.byref(handle)))
+        self._h = handle
+        self._ws = {}
+        self.NZ, self.NX = self.nz + 2 * self.nb, self.nx + 2 * self.nb
+
+    @classmethod
+    def from_workload(cls, w, device=None) -> "Problem":
+        return cls(w.nz, w.nx, w.nb, w.h, w.nt, w.dt, w.f0, w.t0, w.vmax, w.acq.src_iz, w.acq.src_ix,
+                   w.acq.rec_iz, w.acq.rec_ix, R=w.R, sigma=w.sigma, device=device)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.hv_destroy(self._h)
+            self._h = None
+            self._ws.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- profiling
+    def profile(self, enable: bool = True) -> None:
+        """Bracket every kernel launch of this problem with CUDA events (hv_profile)."""
+        check(self.lib.hv_profile(self._h, int(bool(enable))))
+
+    def profile_read(self) -> dict:
+        """{kind: (launches, total_ms)} for kinds fwd, advance, adj, other; clears the record."""
+        n = (ctypes.c_longlong * _lib.HV_K_COUNT)()
+        t = (ctypes.c_double * _lib.HV_K_COUNT)()
+        check(self.lib.hv_profile_read(self._h, n, t))
+        names = ("fwd", "advance", "adj", "other")
+        return {names[i]: (int(n[i]), float(t[i])) for i in range(_lib.HV_K_COUNT)}
+
+    # ---------------------------------------------------------------- workspace
+    def workspace_size(self, op: int, k: int = 1, ckpt: int = HV_CKPT_ALL) -> int:
+        n = ctypes.c_size_t()
+        check(self.lib.hv_workspace_size(self._h, op, int(k), int(ckpt), ctypes.byref(n)))
+        return n.value
+
+    def _workspace(self, op, k, ckpt):
+        need = self.workspace_size(op, k, ckpt)
+        buf = self._ws.get("ws")
+        if buf is None or buf.numel() < need:
+            self._ws.pop("ws", None)
+            buf = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self._ws["ws"] = buf
+        return buf.data_ptr(), buf.numel()
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _m(self, m):
+        return _dev(m, torch.float32, (self.nz, self.nx), "m", self.device)
+
+    # ---------------------------------------------------------------- operations
+    def fwd_model(self, m: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """d[ns, nt, nr] = f(m) (paper eq. (data) without noise)."""
+        d = out if out is not None else torch.empty((self.ns, self.nt, self.nr), dtype=torch.float32, device=self.device)
+        pm, pd = self._m(m), _dev(d, torch.float32, (self.ns, self.nt, self.nr), "d", self.device)
+        ws, nb = self._workspace(HV_OP_FWD, 1, HV_CKPT_ALL)
+        check(self.lib.hv_fwd_model(self._h, pm, pd, ws, nb, self._stream()))
+        return d
+
+    def wavefield(self, m: torch.Tensor, steps) -> torch.Tensor:
+        """u^{n+1} of every shot on the padded grid at the given steps n: [len(steps), ns, NZ, NX]."""
+        steps = _i32(steps)
+        out = torch.empty((steps.size, self.ns, self.NZ, self.NX), dtype=torch.float32, device=self.device)
+        ws, nb = self._workspace(HV_OP_WAVEFIELD, 1, HV_CKPT_ALL)
+        check(self.lib.hv_wavefield(self._h, self._m(m), int(steps.size), steps.ctypes.data_as(_lib.ip),
+                                    out.data_ptr(), ws, nb, self._stream()))
+        return out
+
+    def born(self, m: torch.Tensor, dm: torch.Tensor) -> torch.Tensor:
+        """F dm for dm[k, nz, nx] -> [k, ns, nt, nr]."""
+        k = dm.shape[0]
+        pdm = _dev(dm, torch.float32, (k, self.nz, self.nx), "dm", self.device)
+        dd = torch.empty((k, self.ns, self.nt, self.nr), dtype=torch.float32, device=self.device)
+        ws, nb = self._workspace(HV_OP_BORN, k, HV_CKPT_ALL)
+        check(self.lib.hv_born(self._h, self._m(m), pdm, k, dd.data_ptr(), ws, nb, self._stream()))
+        return dd
+
+    def migrate(self, m: torch.Tensor, r: torch.Tensor, ckpt: int = HV_CKPT_ALL) -> torch.Tensor:
+        """F^T r for data r[ns, nt, nr] -> [nz, nx]."""
+        pr = _dev(r, torch.float32, (self.ns, self.nt, self.nr), "r", self.device)
+        g = torch.empty((self.nz, self.nx), dtype=torch.float32, device=self.device)
+        ws, nb = self._workspace(HV_OP_MIGRATE, 1, ckpt)
+        check(self.lib.hv_migrate(self._h, self._m(m), pr, g.data_ptr(), int(ckpt), ws, nb, self._stream()))
+        return g
+
+    def misfit_grad(self, m: torch.Tensor, d_obs: torch.Tensor, ckpt: int = HV_CKPT_ALL):
+        """(phi, grad): phi a 0-d float64 CUDA tensor, grad [nz, nx]."""
+        pd = _dev(d_obs, torch.float32, (self.ns, self.nt, self.nr), "d_obs", self.device)
+        phi = torch.empty((), dtype=torch.float64, device=self.device)
+        g = torch.empty((self.nz, self.nx), dtype=torch.float32, device=self.device)
+        ws, nb = self._workspace(HV_OP_GRAD, 1, ckpt)
+        check(self.lib.hv_misfit_grad(self._h, self._m(m), pd, phi.data_ptr(), g.data_ptr(), int(ckpt), ws, nb,
+                                      self._stream()))
+        return phi, g
+
+    def hessian_apply(self, m: torch.Tensor, v: torch.Tensor, ckpt: int = HV_CKPT_ALL,
+                      out_dtype=torch.float32) -> torch.Tensor:
+        """H_d v for v[k, nz, nx] -> [k, nz, nx] (float32 or float64 output)."""
+        k = v.shape[0]
+        pv = _dev(v, torch.float32, (k, self.nz, self.nx), "v", self.device)
+        out = torch.empty((k, self.nz, self.nx), dtype=out_dtype, device=self.device)
+        ws, nb = self._workspace(HV_OP_HV, k, ckpt)
+        fn = self.lib.hv_hessian_apply if out_dtype == torch.float32 else self.lib.hv_hessian_apply_f64out
+        if out_dtype not in (torch.float32, torch.float64):
+            raise ValueError("out_dtype must be float32 or float64")
+        check(fn(self._h, self._m(m), pv, k, out.data_ptr(), int(ckpt), ws, nb, self._stream()))
+        return out
+
+
+def checkpoint_schedule(nt: int, slots: int):
+    """The library's checkpoint schedule: (actions[n, 3] int32, recomputed forward steps)."""
+    lib = _lib.load()
+    n = ctypes.c_int()
+    adv = ctypes.c_longlong()
+    check(lib.hv_checkpoint_schedule(int(nt), int(slots), None, 0, ctypes.byref(n), ctypes.byref(adv)))
+    acts = np.zeros((n.value, 3), dtype=np.int32)
+    check(lib.hv_checkpoint_schedule(int(nt), int(slots), acts.ctypes.data_as(_lib.ip), n.value, ctypes.byref(n),
+                                     ctypes.byref(adv)))
+    return acts, adv.value
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libhv in this process so far."""
+    return int(_lib.load().hv_kernel_launches())

@@ -1,0 +1,116 @@
+"""Host-side checks of libhv that need no GPU: exported symbols, the checkpoint
+schedule (valid and optimal), and argument validation in hv_create."""
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import revolve_dp as R
+from paper_2507_10804_gb300 import _lib
+from paper_2507_10804_gb300.hv import checkpoint_schedule
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2507_10804_gb300 import build
+    build.build()
+    return _lib.load()
+
+
+def test_library_exports_every_header_symbol(lib):
+    names = _lib.header_symbols()
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.hv_version() >= 100
+
+
+def simulate(actions, nt, slots):
+    """Replay a schedule: every adjoint step exactly once in reverse order, each
+    with u^n available; snapshot slots within budget and never clobbered while in use."""
+    j = 0
+    where = ("zero", "zero")          # buffers holding (cur, prev)
+    slot_state = {}
+    adj = []
+    adv = 0
+    seen_forward = 0
+    for op, a0, a1 in actions:
+        if op == 0:
+            assert a0 == j == seen_forward
+            seen_forward += 1
+            j += 1
+            where = ("work", where[0])
+        elif op == 1:
+            assert 0 <= a0 < slots and a1 == j
+            if where != (("slotA", a0), ("slotB", a0)):
+                assert where[0] != ("slotB", a0) and where[1] != ("slotA", a0)
+            slot_state[a0] = j
+            where = (("slotA", a0), ("slotB", a0))
+        elif op == 2:
+            if a0 < 0:
+                j, where = 0, ("zero", "zero")
+            else:
+                assert slot_state.get(a0) == a1
+                j, where = a1, (("slotA", a0), ("slotB", a0))
+        elif op == 3:
+            assert a0 == j
+            j += 1
+            adv += 1
+            where = ("work", where[0])
+        elif op == 4:
+            assert j in (a0, a0 + 1), (a0, j)
+            adj.append(a0)
+        else:
+            raise AssertionError(op)
+    assert seen_forward == nt
+    assert adj == list(range(nt - 1, -1, -1))
+    return adv
+
+
+@pytest.mark.parametrize("nt,slots", [(1, 1), (2, 1), (7, 1), (12, 2), (40, 3), (97, 4), (150, 5), (64, 63)])
+def test_schedule_valid_and_optimal(lib, nt, slots):
+    acts, adv = checkpoint_schedule(nt, slots)
+    assert simulate(acts.tolist(), nt, slots) == adv
+    assert adv == R.min_advances_dp(nt, slots)
+
+
+def test_schedule_matches_exhaustive_search_on_tiny_chains(lib):
+    for s in (1, 2):
+        for nt in range(1, 9):
+            assert checkpoint_schedule(nt, s)[1] == R.min_advances_bruteforce(nt, s)
+
+
+def test_schedule_cost_at_paper_scale(lib):
+    # 3000 steps with 30 snapshots per shot (the 384 x 1152 workload)
+    acts, adv = checkpoint_schedule(3000, 30)
+    assert simulate(acts.tolist(), 3000, 30) == adv
+    assert adv < 2 * 3000
+
+
+def _create(lib, nz=8, nx=8, nb=2, ns=1, nr=2, src=((0, 3),), recs=((0, 1), (0, 5)), nt=10, dt=1e-3,
+            vmax=2000.0, R=1e-3, sigma=1.0):
+    g = _lib.HvGrid(nz, nx, nb, 10.0)
+    si = np.array([s[0] for s in src], np.int32)
+    sx = np.array([s[1] for s in src], np.int32)
+    ri = np.array([r[0] for r in recs], np.int32)
+    rx = np.array([r[1] for r in recs], np.int32)
+    a = _lib.HvAcq(ns, si.ctypes.data_as(_lib.ip), sx.ctypes.data_as(_lib.ip), nr, ri.ctypes.data_as(_lib.ip),
+                   rx.ctypes.data_as(_lib.ip), nt, dt, 15.0, 0.1, vmax, R, sigma)
+    h = ctypes.c_void_p()
+    rc = lib.hv_create(ctypes.byref(g), ctypes.byref(a), ctypes.byref(h))
+    return rc, lib.hv_last_error().decode()
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(src=((0, 8),)), "source node"),
+    (dict(recs=((0, 1), (9, 5))), "receiver 1"),
+    (dict(recs=((0, 1), (0, 1))), "duplicates"),
+    (dict(dt=0.0), "must be > 0"),
+    (dict(R=1.5), "reflection"),
+    (dict(nz=0), "grid"),
+    (dict(nt=0), "nt = 0"),
+])
+def test_create_rejects_bad_arguments_before_touching_the_gpu(lib, kw, needle):
+    rc, msg = _create(lib, **kw)
+    assert rc == _lib.HV_EINVAL
+    assert needle in msg
