@@ -301,16 +301,20 @@ def run_ours(args, w):
 
 
 def main():
+    global CKPT
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=int(os.environ.get("WORLD_SIZE", "1")))
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--nt", type=int, default=None, help="override the step count (smaller runs)")
+    ap.add_argument("--nt", type=int, default=None, help="override the step count (profiling runs)")
+    ap.add_argument("--shots", type=int, default=None, help="override the shot count (profiling runs)")
+    ap.add_argument("--ckpt", type=int, default=CKPT, help="snapshots per shot (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     from paper_2507_10804_gb300 import synth
-    w = synth.workload(2, nt=args.nt)
+    CKPT = args.ckpt
+    w = synth.workload(2, nt=args.nt, ns=args.shots)
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -281,6 +281,19 @@ struct Exec {
         return hvk::launch_adj(h, rectiles_for(h, hvk::tiling_adj(h)), a, st);
     }
 
+    // Zero the ghost bands of every field batch this call's kernels write:
+    // the zero state, the working levels, the stored levels, the Born/adjoint
+    // fields.  (Snapshot slots are filled by copies of these, ghosts included.)
+    int zero_ghosts(bool with_store)
+    {
+        const long long per_batch = (long long)h->ns;
+        HV_RT(hvk::launch_zero_ghosts(h, zero, per_batch, st));
+        if (L.work) HV_RT(hvk::launch_zero_ghosts(h, work[0], 3 * per_batch, st));
+        if (with_store && L.history) HV_RT(hvk::launch_zero_ghosts(h, hist(1), (long long)h->nt * per_batch, st));
+        if (L.D) HV_RT(hvk::launch_zero_ghosts(h, D, 2LL * k * per_batch, st));
+        return HV_OK;
+    }
+
     const float *u_for(int n)
     {
         if (j == n) return cur;
@@ -330,6 +343,7 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     E.init(h, st, L, ws, kk);
     const bool born = (kind == 2);
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(E.zero_ghosts(true));
     HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * kk * L.fb, st));
     {
         ProfScope ps(h, st, HV_K_OTHER);
@@ -521,6 +535,7 @@ extern "C" int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, si
     Exec E;
     E.init(h, st, L, ws, 0);
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(E.zero_ghosts(false));
     HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
     for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, false, d, nullptr, nullptr));
     return HV_OK;
@@ -539,6 +554,7 @@ extern "C" int hv_wavefield(hv_handle *h, const float *m, int n_out, const int *
     Exec E;
     E.init(h, st, L, ws, 0);
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(E.zero_ghosts(false));
     HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
     int i = 0;
     for (int n = 0; n <= steps[n_out - 1]; ++n) {
@@ -561,6 +577,7 @@ extern "C" int hv_born(hv_handle *h, const float *m, const float *dm, int k, flo
     Exec E;
     E.init(h, st, L, ws, k);
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(E.zero_ghosts(false));
     HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * k * L.fb, st));
     HV_RT(hvk::launch_prep(h, m, dm, k, E.C, E.b, st));
     for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, true, nullptr, dd, nullptr));

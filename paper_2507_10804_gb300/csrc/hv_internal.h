@@ -114,6 +114,7 @@ int launch_residual(const hv_handle *h, const float *d, const float *dobs, float
                     int nblocks, cudaStream_t st);
 int launch_reduce_phi(const double *partials, int nblocks, double scale, double *phi, cudaStream_t st);
 int launch_copy_wavefield(const hv_handle *h, const float *u, float *out, cudaStream_t st);
+int launch_zero_ghosts(const hv_handle *h, float *f, long long nfields, cudaStream_t st);
 int launch_setup(hv_handle *h, cudaStream_t st);
 
 // Process-wide kernel launch counter (hv_kernel_launches).

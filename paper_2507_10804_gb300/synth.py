@@ -66,7 +66,8 @@ def grf(seed: int, nz: int, nx: int, h: float, std: float, corr_len: float) -> n
     w = normal(seed, nz * nx).reshape(nz, nx)
     f = gaussian_smooth(w, corr_len / h / np.sqrt(2.0))
     f -= f.mean()
-    return f * (std / f.std())
+    sd = f.std()
+    return f * (std / sd) if sd > 0 else f
 
 
 @dataclass

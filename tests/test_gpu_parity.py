@@ -203,3 +203,23 @@ def test_full_size_hessian_symmetry_with_30_snapshots():
     assert np.all(np.isfinite(H))
     assert abs(np.vdot(u, H[1]) - np.vdot(H[0], v)) < 1e-3 * np.sqrt(np.vdot(u, H[0]) * np.vdot(v, H[1]))
     assert np.vdot(u, H[0]) > 0 and np.vdot(v, H[1]) > 0
+
+
+def test_results_do_not_depend_on_workspace_contents(ragged):
+    """Workspace memory arrives uninitialised: poisoning it with NaN bytes must not change anything."""
+    w, P, _ = ragged
+    m, v = gpu(w.m), gpu(w.v)
+    dobs = gpu(synth.normal(5, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr))
+    runs = {
+        "hv": lambda: P.hessian_apply(m, v, ckpt=3),
+        "hv_all": lambda: P.hessian_apply(m, v),
+        "fwd": lambda: P.fwd_model(m),
+        "born": lambda: P.born(m, v),
+        "grad": lambda: P.misfit_grad(m, dobs, ckpt=2)[1],
+    }
+    for name, fn in runs.items():
+        ref = host(fn())
+        P._ws["ws"].fill_(255)                       # every float32 in the workspace becomes NaN
+        again = host(fn())
+        assert np.array_equal(ref, again), name
+        assert np.all(np.isfinite(again)), name
