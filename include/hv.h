@@ -162,6 +162,35 @@ int hv_hessian_apply(hv_handle *h, const float *m, const float *v, int k, float 
 int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k, double *Hv, int ckpt,
                             void *ws, size_t ws_bytes, void *stream);
 
+/* Allocation-free Gauss-Newton Hessian apply.  The paper has no counterpart;
+ * this entry point exists for callers that cannot allocate device memory
+ * where they call it (an application that owns every byte of device memory
+ * through its own pool, a real-time loop that must not stall in an
+ * allocator, or code that cannot size and pass a workspace).  It takes the
+ * problem description directly (no handle) and computes what
+ * hv_hessian_apply computes, with the same kernels, but keeps every table
+ * and scratch field in one fixed device array of HV_STATIC_SCRATCH_BYTES
+ * inside the library, which each GPU that loads the library holds until the
+ * process exits.  It calls no cudaMalloc/cudaFree and no allocating library
+ * routine.
+ *  - m, v, Hv: DEVICE pointers as for hv_hessian_apply; grid/acq: host
+ *    structs as for hv_create (validated the same way).
+ *  - Problems whose tables plus workspace exceed the array are rejected with
+ *    HV_ENOMEM and a message giving the bytes needed (64 MiB holds, e.g., a
+ *    104 x 104 padded grid, 1 shot, 600 steps, k = 1, with every time level
+ *    stored).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the one array and overwrites the previous call's
+ *    contents (whatever must start at zero is cleared on each call): calls
+ *    that may overlap on the GPU (different streams, different host threads
+ *    on the same device) race and must be serialised by the caller.
+ *  - Asynchronous on `stream` like the other compute calls. */
+#define HV_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float *m, const float *v, int k,
+                            float *Hv, int ckpt, void *stream);
+
 /* Profiling.  While enabled on a handle, each kernel launch the handle makes
  * is bracketed by CUDA events on the launching stream.  hv_profile_read waits
  * for those events and returns, per kernel kind (HV_K_*), the number of

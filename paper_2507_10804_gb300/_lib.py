@@ -47,6 +47,8 @@ _SIGS = {
     "hv_misfit_grad": ([c_void_p, fp, fp, fp, fp, c_int, fp, c_size_t, c_void_p], c_int),
     "hv_hessian_apply": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
     "hv_hessian_apply_f64out": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_hessian_apply_static": ([ctypes.POINTER(HvGrid), ctypes.POINTER(HvAcq), fp, fp, c_int, fp, c_int,
+                                 c_void_p], c_int),
     "hv_profile": ([c_void_p, c_int], c_int),
     "hv_profile_read": ([c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_double)], c_int),
     "hv_kernel_launches": ([], ctypes.c_longlong),
@@ -59,7 +61,7 @@ _lib = None
 def header_symbols() -> list[str]:
     """Every function the public header declares."""
     text = open(HEADER).read()
-    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(hv_\w+)\s*\(", text, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w ]*?\s*\*?\s*\b(hv_\w+)\s*\(", text, flags=re.M)))
 
 
 def load() -> ctypes.CDLL:

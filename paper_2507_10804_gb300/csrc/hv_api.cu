@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <set>
 #include <utility>
 
@@ -640,3 +641,162 @@ extern "C" int hv_profile_read(hv_handle *h, long long *launches, double *ms)
 }
 
 extern "C" long long hv_kernel_launches(void) { return hvk::launches_so_far(); }
+
+// ---------------------------------------------------------------- allocation-free Hessian apply
+//
+// hv_hessian_apply_static serves callers that cannot allocate device memory
+// at the point of the call: code that runs under a device-memory budget owned
+// by someone else (a host application that hands out every byte from its own
+// pool), a real-time loop where an allocation could stall, or a caller that
+// has no way to size and pass a workspace.  It needs no handle and no
+// workspace: the problem tables and the scratch fields live in the array
+// below, which every GPU that loads the library holds until the process
+// exits.  It runs exactly the kernels of hv_hessian_apply.
+namespace {
+
+__device__ __align__(256) unsigned char g_hv_static_scratch[HV_STATIC_SCRATCH_BYTES];
+
+std::mutex g_static_mu;
+std::map<int, void *> g_static_base;   // device ordinal -> device address of the array
+
+// Device address of the scratch array on `dev` (the current device).  Looked
+// up once per device; in host code the symbol itself is only a stand-in.
+int static_scratch_base(int dev, void **base)
+{
+    std::lock_guard<std::mutex> g(g_static_mu);
+    auto it = g_static_base.find(dev);
+    if (it != g_static_base.end()) {
+        *base = it->second;
+        return HV_OK;
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_hv_static_scratch);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+    g_static_base[dev] = p;
+    *base = p;
+    return HV_OK;
+}
+
+// Receiver tables of one tiling, on the host.
+void static_rectile_tables(const hv_handle *h, const hvi::Tiling &t, std::vector<int> &off, std::vector<int> &rec,
+                           std::vector<int> &pos)
+{
+    off.assign((size_t)h->ns * (t.ntiles + 1), 0);
+    rec.assign((size_t)h->ns * h->nr, 0);
+    pos.assign((size_t)h->ns * h->nr, 0);
+    for (int s = 0; s < h->ns; ++s) {
+        std::vector<std::pair<int, int>> tr;
+        for (int r = 0; r < h->nr; ++r) {
+            int z = h->h_rec_zx[2 * ((size_t)s * h->nr + r)], x = h->h_rec_zx[2 * ((size_t)s * h->nr + r) + 1];
+            tr.push_back({(z / t.TZ) * t.ntx + (x / t.TX), r});
+        }
+        std::stable_sort(tr.begin(), tr.end(), [](auto &a, auto &b) { return a.first < b.first; });
+        size_t i = 0;
+        for (int tile = 0; tile <= t.ntiles; ++tile) {
+            while (i < tr.size() && tr[i].first < tile) ++i;
+            off[(size_t)s * (t.ntiles + 1) + tile] = (int)i;
+        }
+        for (size_t q = 0; q < tr.size(); ++q) {
+            int r = tr[q].second;
+            int z = h->h_rec_zx[2 * ((size_t)s * h->nr + r)], x = h->h_rec_zx[2 * ((size_t)s * h->nr + r) + 1];
+            rec[(size_t)s * h->nr + q] = r;
+            pos[(size_t)s * h->nr + q] = (z + hvi::GH) * h->P + (x + hvi::GH);
+        }
+    }
+}
+
+}  // namespace
+
+extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const float *m, const float *v, int k,
+                                       float *Hv, int ckpt, void *stream)
+{
+    HV_RT(validate_create(g, a));
+    if (!m || !v || !Hv) return hvi::fail(HV_EINVAL, "null model, vector or output");
+    cudaStream_t st = (cudaStream_t)stream;
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    void *base = nullptr;
+    HV_RT(static_scratch_base(dev, &base));
+
+    // A host-only handle whose device arrays point into the scratch array.
+    std::unique_ptr<hv_handle> hp(new hv_handle());
+    hv_handle *h = hp.get();
+    h->device = dev;
+    h->nz = g->nz; h->nx = g->nx; h->nb = g->nb; h->h = g->h;
+    h->NZ = g->nz + 2 * g->nb;
+    h->NX = g->nx + 2 * g->nb;
+    h->P = ((h->NX + 2 * hvi::GH) + 31) / 32 * 32;
+    h->rows = h->NZ + 2 * hvi::GH;
+    h->fsize = ((size_t)h->rows * h->P + 63) / 64 * 64;
+    h->ns = a->ns; h->nr = a->nr; h->nt = a->nt;
+    h->dt = a->dt; h->f0 = a->f0; h->t0 = a->t0; h->vmax = a->vmax; h->R = a->R; h->sigma = a->sigma;
+    h->h_src_zx.resize(2 * (size_t)h->ns);
+    h->h_rec_zx.resize(2 * (size_t)h->ns * h->nr);
+    for (int s = 0; s < h->ns; ++s) {
+        h->h_src_zx[2 * s] = a->src_iz[s] + h->nb;
+        h->h_src_zx[2 * s + 1] = a->src_ix[s] + h->nb;
+    }
+    for (size_t i = 0; i < (size_t)h->ns * h->nr; ++i) {
+        h->h_rec_zx[2 * i] = a->rec_iz[i] + h->nb;
+        h->h_rec_zx[2 * i + 1] = a->rec_ix[i] + h->nb;
+    }
+    const hvi::Tiling tf = hvk::tiling_fwd(h), ta = hvk::tiling_adj(h);
+    std::vector<int> off_f, rec_f, pos_f, off_a, rec_a, pos_a;
+    static_rectile_tables(h, tf, off_f, rec_f, pos_f);
+    const bool same_tiling = (tf.TX == ta.TX && tf.TZ == ta.TZ);
+    if (!same_tiling) static_rectile_tables(h, ta, off_a, rec_a, pos_a);
+
+    // Carve the array: tables first, then the workspace of hv_hessian_apply.
+    size_t o = 0;
+    auto carve = [&](size_t bytes) {
+        size_t at = o;
+        o += align256(bytes);
+        return (char *)base + at;
+    };
+    h->wavelet = (float *)carve(sizeof(float) * h->nt);
+    h->az = (float *)carve(sizeof(float) * h->NZ);
+    h->ax = (float *)carve(sizeof(float) * h->NX);
+    h->src_zx = (int *)carve(sizeof(int) * h->h_src_zx.size());
+    h->rec_zx = (int *)carve(sizeof(int) * h->h_rec_zx.size());
+    hvi::RecTiles rf, ra;
+    rf.TX = tf.TX; rf.TZ = tf.TZ; rf.ntiles = tf.ntiles;
+    rf.off = (int *)carve(sizeof(int) * off_f.size());
+    rf.rec = (int *)carve(sizeof(int) * rec_f.size());
+    rf.pos = (int *)carve(sizeof(int) * pos_f.size());
+    if (!same_tiling) {
+        ra.TX = ta.TX; ra.TZ = ta.TZ; ra.ntiles = ta.ntiles;
+        ra.off = (int *)carve(sizeof(int) * off_a.size());
+        ra.rec = (int *)carve(sizeof(int) * rec_a.size());
+        ra.pos = (int *)carve(sizeof(int) * pos_a.size());
+    }
+    const size_t tables = o;
+    Layout L;
+    HV_RT(make_layout(h, HV_OP_HV, k, ckpt, L));
+    if (o > HV_STATIC_SCRATCH_BYTES || L.total > HV_STATIC_SCRATCH_BYTES - o)
+        return hvi::fail(HV_ENOMEM,
+                         "hv_hessian_apply_static: this problem needs %zu bytes of scratch (%zu of tables, %zu of "
+                         "fields); the static array holds %zu; use hv_hessian_apply with a workspace",
+                         tables + L.total, tables, L.total, (size_t)HV_STATIC_SCRATCH_BYTES);
+    void *ws = (char *)base + tables;
+
+    // Tables (rewritten on every call: the array keeps the previous call's contents).
+    HV_CK(cudaMemcpyAsync(h->src_zx, h->h_src_zx.data(), sizeof(int) * h->h_src_zx.size(), cudaMemcpyHostToDevice, st));
+    HV_CK(cudaMemcpyAsync(h->rec_zx, h->h_rec_zx.data(), sizeof(int) * h->h_rec_zx.size(), cudaMemcpyHostToDevice, st));
+    HV_CK(cudaMemcpyAsync(rf.off, off_f.data(), sizeof(int) * off_f.size(), cudaMemcpyHostToDevice, st));
+    HV_CK(cudaMemcpyAsync(rf.rec, rec_f.data(), sizeof(int) * rec_f.size(), cudaMemcpyHostToDevice, st));
+    HV_CK(cudaMemcpyAsync(rf.pos, pos_f.data(), sizeof(int) * pos_f.size(), cudaMemcpyHostToDevice, st));
+    if (!same_tiling) {
+        HV_CK(cudaMemcpyAsync(ra.off, off_a.data(), sizeof(int) * off_a.size(), cudaMemcpyHostToDevice, st));
+        HV_CK(cudaMemcpyAsync(ra.rec, rec_a.data(), sizeof(int) * rec_a.size(), cudaMemcpyHostToDevice, st));
+        HV_CK(cudaMemcpyAsync(ra.pos, pos_a.data(), sizeof(int) * pos_a.size(), cudaMemcpyHostToDevice, st));
+    }
+    h->rectiles[(long long)rf.TX * 65536 + rf.TZ] = rf;
+    if (!same_tiling) h->rectiles[(long long)ra.TX * 65536 + ra.TZ] = ra;
+    HV_RT(hvk::launch_setup(h, st));
+    int rc = run_adjoint(h, 2, m, v, k, Hv, nullptr, nullptr, ckpt, ws, HV_STATIC_SCRATCH_BYTES - tables, st);
+    // The pageable-host copies above are staged before cudaMemcpyAsync returns, so the
+    // host tables may go out of scope now; the device pointers are not freed (they
+    // belong to the static array).
+    h->rectiles.clear();
+    return rc;
+}
