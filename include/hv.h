@@ -191,6 +191,12 @@ int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k,
 int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float *m, const float *v, int k,
                             float *Hv, int ckpt, void *stream);
 
+/* Device status of the handle's kernels since the last call of hv_status:
+ * HV_OK, or HV_ETIMEOUT if a bounded on-device wait (for a bulk tile copy)
+ * ran out and the kernel returned early (its outputs are then invalid).
+ * Synchronises the device, then clears the status. */
+int hv_status(hv_handle *h, int *device_status);
+
 /* Profiling.  While enabled on a handle, each kernel launch the handle makes
  * is bracketed by CUDA events on the launching stream.  hv_profile_read waits
  * for those events and returns, per kernel kind (HV_K_*), the number of

@@ -49,6 +49,7 @@ _SIGS = {
     "hv_hessian_apply_f64out": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
     "hv_hessian_apply_static": ([ctypes.POINTER(HvGrid), ctypes.POINTER(HvAcq), fp, fp, c_int, fp, c_int,
                                  c_void_p], c_int),
+    "hv_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
     "hv_profile": ([c_void_p, c_int], c_int),
     "hv_profile_read": ([c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_double)], c_int),
     "hv_kernel_launches": ([], ctypes.c_longlong),

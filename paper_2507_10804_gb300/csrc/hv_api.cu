@@ -97,6 +97,7 @@ struct Layout {
     int G = 1;                // adjoint shot groups (partial images)
     size_t fb = 0;            // bytes of one field batch (all shots)
     size_t C = 0, b = 0, zero = 0, work = 0, store = 0, D = 0, dd = 0, img = 0, part = 0, total = 0;
+    size_t fields_end = 0;    // the field regions (all first) end here: the tensor maps cover [0, fields_end)
 };
 
 constexpr int kResidualBlocks = 1024;
@@ -129,6 +130,7 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
     if (!adjoint || !L.history) L.work = take(3 * L.fb);
     if (adjoint) L.store = take(L.history ? (size_t)h->nt * L.fb : (size_t)2 * L.slots * L.fb);
     if (born || adjoint) L.D = take((size_t)2 * k * L.fb);
+    L.fields_end = o;         // every region above is a whole number of fields (fsize is 64-float aligned)
     const size_t ndata = (size_t)h->ns * h->nt * h->nr;
     if (op == HV_OP_HV) L.dd = take((size_t)k * ndata * sizeof(float));
     if (op == HV_OP_GRAD) L.dd = take(ndata * sizeof(float));
@@ -182,46 +184,66 @@ struct Exec {
     char *ws;
     int k;
     float *C, *b, *zero;
-    float *work[3];
     float *D;            // 2 k field batches: Born fields (first sweep), adjoint fields (reversal)
     double *img;
+    hvk::TmaMaps maps;   // tensor maps of this call's workspace
+    // Forward levels live in a pool of field batches (3 working + 2 per snapshot
+    // slot, contiguous).  A snapshot pins the two batches of the current state
+    // (reference counts) instead of copying them; a forward step writes into
+    // any batch that is neither pinned nor part of the current state.
+    std::vector<float *> pool;
+    std::vector<int> refs;
+    std::vector<std::pair<int, int>> slot_b;   // slot -> (batch of u^j, batch of u^{j-1}), -1 = zero
+    int cur_i = -1, prev_i = -1;               // pool indices of the current state (-1: zero batch)
     const float *cur, *prev;
     int j;               // current state index: cur = u^j, prev = u^{j-1}
 
     float *batch(char *base, size_t i) const { return reinterpret_cast<float *>(base + i * L.fb); }
     float *Dbuf(int parity) const { return reinterpret_cast<float *>(reinterpret_cast<char *>(D) + (size_t)parity * k * L.fb); }
     float *hist(int n) const { return n == 0 ? zero : batch(ws + L.store, (size_t)(n - 1)); }
-    float *slotA(int s) const { return batch(ws + L.store, (size_t)2 * s); }
-    float *slotB(int s) const { return batch(ws + L.store, (size_t)2 * s + 1); }
+    const float *ptr(int i) const { return i < 0 ? zero : pool[i]; }
 
-    float *pick_work() const
+    int pick_free() const
     {
-        for (int i = 0; i < 3; ++i)
-            if (work[i] != cur && work[i] != prev) return work[i];
-        return nullptr;
+        for (size_t i = 0; i < pool.size(); ++i)
+            if (refs[i] == 0 && (int)i != cur_i && (int)i != prev_i) return (int)i;
+        return -1;
     }
 
-    void init(hv_handle *hh, cudaStream_t s, const Layout &l, void *w, int kk)
+    int init(hv_handle *hh, cudaStream_t s, const Layout &l, void *w, int kk)
     {
         h = hh; st = s; L = l; ws = (char *)w; k = kk;
         C = reinterpret_cast<float *>(ws + L.C);
         b = L.b ? reinterpret_cast<float *>(ws + L.b) : nullptr;
         zero = reinterpret_cast<float *>(ws + L.zero);
-        for (int i = 0; i < 3; ++i) work[i] = L.work ? batch(ws + L.work, i) : nullptr;
         D = reinterpret_cast<float *>(ws + L.D);
         img = reinterpret_cast<double *>(ws + L.img);
+        if (L.work) {
+            const int n = 3 + (L.history ? 0 : 2 * L.slots);   // work and snapshot batches are contiguous
+            for (int i = 0; i < n; ++i) pool.push_back(batch(ws + L.work, i));
+            refs.assign(n, 0);
+            slot_b.assign(L.slots, {-1, -1});
+        }
         cur = prev = zero;
+        cur_i = prev_i = -1;
         j = 0;
+        return hvk::make_maps(h, ws, (long long)(L.fields_end / (h->fsize * sizeof(float))), &maps);
     }
 
     // One forward step from the current state.  born: advance the Born fields
-    // too (first sweep of H v / Born map).
+    // too (first sweep of H v / Born map).  target: write u^{n+1} there
+    // (stored-history mode) instead of into a pool batch.
     int forward(int n, bool born, float *d_u, float *d_du, float *target, int kind = HV_K_FWD)
     {
         ProfScope ps(h, st, kind);
         if (n != j) return hvi::fail(HV_EINVAL, "internal: forward step %d from state %d", n, j);
-        float *next = target ? target : pick_work();
-        if (!next) return hvi::fail(HV_EINVAL, "internal: no free working buffer");
+        int ni = -1;
+        float *next = target;
+        if (!next) {
+            ni = pick_free();
+            if (ni < 0) return hvi::fail(HV_EINVAL, "internal: no free forward buffer");
+            next = pool[ni];
+        }
         hvk::FwdLaunch a{};
         a.u_cur = cur; a.u_prev = prev; a.u_next = next; a.C = C;
         a.n = n;
@@ -232,36 +254,40 @@ struct Exec {
             a.d_du = d_du;
         }
         a.d_u = d_u;
-        HV_RT(hvk::launch_fwd(h, rectiles_for(h, hvk::tiling_fwd(h)), a, st));
+        HV_RT(hvk::launch_fwd(h, rectiles_for(h, hvk::tiling_fwd(h)), maps, a, st));
         prev = cur;
+        prev_i = cur_i;
         cur = next;
+        cur_i = ni;
         j = n + 1;
         return HV_OK;
     }
 
+    // Pin the current state in `slot` (no copy).
     int save(int slot)
     {
-        ProfScope ps(h, st, HV_K_OTHER);
-        float *A = slotA(slot), *B = slotB(slot);
-        if (cur == A && prev == B) return HV_OK;
-        if (cur == B || prev == A) return hvi::fail(HV_EINVAL, "internal: snapshot slot %d aliases the state", slot);
-        if (prev != B) HV_CK(cudaMemcpyAsync(B, prev, L.fb, cudaMemcpyDeviceToDevice, st));
-        if (cur != A) HV_CK(cudaMemcpyAsync(A, cur, L.fb, cudaMemcpyDeviceToDevice, st));
-        cur = A;
-        prev = B;
+        if (slot < 0 || slot >= (int)slot_b.size()) return hvi::fail(HV_EINVAL, "internal: snapshot slot %d", slot);
+        auto &sb = slot_b[slot];
+        if (sb.first >= 0) --refs[sb.first];
+        if (sb.second >= 0) --refs[sb.second];
+        sb = {cur_i, prev_i};
+        if (cur_i >= 0) ++refs[cur_i];
+        if (prev_i >= 0) ++refs[prev_i];
         return HV_OK;
     }
 
     void restore(int slot, int state)
     {
         if (slot < 0) {
-            cur = prev = zero;
+            cur_i = prev_i = -1;
             j = 0;
         } else {
-            cur = slotA(slot);
-            prev = slotB(slot);
+            cur_i = slot_b[slot].first;
+            prev_i = slot_b[slot].second;
             j = state;
         }
+        cur = ptr(cur_i);
+        prev = ptr(prev_i);
     }
 
     int adjoint(int n, const float *u, const float *r, int r_per_vector, float rscale, int kk)
@@ -279,17 +305,17 @@ struct Exec {
         a.n = n;
         a.k = kk;
         a.G = L.G;
-        return hvk::launch_adj(h, rectiles_for(h, hvk::tiling_adj(h)), a, st);
+        return hvk::launch_adj(h, rectiles_for(h, hvk::tiling_adj(h)), maps, a, st);
     }
 
     // Zero the ghost bands of every field batch this call's kernels write:
-    // the zero state, the working levels, the stored levels, the Born/adjoint
-    // fields.  (Snapshot slots are filled by copies of these, ghosts included.)
+    // the zero state, the forward-level pool, the stored levels and the
+    // Born/adjoint fields.
     int zero_ghosts(bool with_store)
     {
         const long long per_batch = (long long)h->ns;
         HV_RT(hvk::launch_zero_ghosts(h, zero, per_batch, st));
-        if (L.work) HV_RT(hvk::launch_zero_ghosts(h, work[0], 3 * per_batch, st));
+        if (!pool.empty()) HV_RT(hvk::launch_zero_ghosts(h, pool[0], (long long)pool.size() * per_batch, st));
         if (with_store && L.history) HV_RT(hvk::launch_zero_ghosts(h, hist(1), (long long)h->nt * per_batch, st));
         if (L.D) HV_RT(hvk::launch_zero_ghosts(h, D, 2LL * k * per_batch, st));
         return HV_OK;
@@ -341,7 +367,7 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     HV_RT(check_common(h, ws, ws_bytes, op, kind == 2 ? k : 1, ckpt, L));
     const int kk = (kind == 2) ? k : 1;
     Exec E;
-    E.init(h, st, L, ws, kk);
+    HV_RT(E.init(h, st, L, ws, kk));
     const bool born = (kind == 2);
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
     HV_RT(E.zero_ghosts(true));
@@ -477,7 +503,8 @@ extern "C" int hv_create(const hv_grid *g, const hv_acq *a, hv_handle **out)
         (e = cudaMalloc(&h->az, sizeof(float) * h->NZ)) != cudaSuccess ||
         (e = cudaMalloc(&h->ax, sizeof(float) * h->NX)) != cudaSuccess ||
         (e = cudaMalloc(&h->src_zx, sizeof(int) * h->h_src_zx.size())) != cudaSuccess ||
-        (e = cudaMalloc(&h->rec_zx, sizeof(int) * h->h_rec_zx.size())) != cudaSuccess)
+        (e = cudaMalloc(&h->rec_zx, sizeof(int) * h->h_rec_zx.size())) != cudaSuccess ||
+        (e = cudaMalloc(&h->status, sizeof(int))) != cudaSuccess || (e = cudaMemset(h->status, 0, sizeof(int))) != cudaSuccess)
         return cleanup_fail(hvi::fail(HV_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e)));
     if ((e = cudaMemcpy(h->src_zx, h->h_src_zx.data(), sizeof(int) * h->h_src_zx.size(), cudaMemcpyHostToDevice)) !=
             cudaSuccess ||
@@ -503,6 +530,7 @@ extern "C" int hv_destroy(hv_handle *h)
     cudaFree(h->ax);
     cudaFree(h->src_zx);
     cudaFree(h->rec_zx);
+    cudaFree(h->status);
     for (auto &r : h->prof_rec) {
         cudaEventDestroy(r.second.first);
         cudaEventDestroy(r.second.second);
@@ -534,7 +562,7 @@ extern "C" int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, si
     if (!m || !d) return hvi::fail(HV_EINVAL, "null model or data pointer");
     cudaStream_t st = (cudaStream_t)stream;
     Exec E;
-    E.init(h, st, L, ws, 0);
+    HV_RT(E.init(h, st, L, ws, 0));
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
     HV_RT(E.zero_ghosts(false));
     HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
@@ -553,7 +581,7 @@ extern "C" int hv_wavefield(hv_handle *h, const float *m, int n_out, const int *
             return hvi::fail(HV_EINVAL, "steps must be ascending and in [0, nt)");
     cudaStream_t st = (cudaStream_t)stream;
     Exec E;
-    E.init(h, st, L, ws, 0);
+    HV_RT(E.init(h, st, L, ws, 0));
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
     HV_RT(E.zero_ghosts(false));
     HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
@@ -576,7 +604,7 @@ extern "C" int hv_born(hv_handle *h, const float *m, const float *dm, int k, flo
     if (!m || !dm || !dd) return hvi::fail(HV_EINVAL, "null model, perturbation or output");
     cudaStream_t st = (cudaStream_t)stream;
     Exec E;
-    E.init(h, st, L, ws, k);
+    HV_RT(E.init(h, st, L, ws, k));
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
     HV_RT(E.zero_ghosts(false));
     HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * k * L.fb, st));
@@ -758,6 +786,7 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
     h->ax = (float *)carve(sizeof(float) * h->NX);
     h->src_zx = (int *)carve(sizeof(int) * h->h_src_zx.size());
     h->rec_zx = (int *)carve(sizeof(int) * h->h_rec_zx.size());
+    h->status = (int *)carve(sizeof(int));
     hvi::RecTiles rf, ra;
     rf.TX = tf.TX; rf.TZ = tf.TZ; rf.ntiles = tf.ntiles;
     rf.off = (int *)carve(sizeof(int) * off_f.size());
@@ -790,6 +819,7 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
         HV_CK(cudaMemcpyAsync(ra.rec, rec_a.data(), sizeof(int) * rec_a.size(), cudaMemcpyHostToDevice, st));
         HV_CK(cudaMemcpyAsync(ra.pos, pos_a.data(), sizeof(int) * pos_a.size(), cudaMemcpyHostToDevice, st));
     }
+    HV_CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
     h->rectiles[(long long)rf.TX * 65536 + rf.TZ] = rf;
     if (!same_tiling) h->rectiles[(long long)ra.TX * 65536 + ra.TZ] = ra;
     HV_RT(hvk::launch_setup(h, st));
@@ -799,4 +829,16 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
     // belong to the static array).
     h->rectiles.clear();
     return rc;
+}
+
+extern "C" int hv_status(hv_handle *h, int *device_status)
+{
+    if (!h || !device_status) return hvi::fail(HV_EINVAL, "null handle or output");
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != h->device) return hvi::fail(HV_EINVAL, "current device %d is not the handle's device %d", dev, h->device);
+    HV_CK(cudaDeviceSynchronize());
+    HV_CK(cudaMemcpy(device_status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    HV_CK(cudaMemset(h->status, 0, sizeof(int)));
+    return HV_OK;
 }

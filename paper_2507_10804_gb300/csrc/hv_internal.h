@@ -13,6 +13,12 @@
 
 #include "hv.h"
 
+#define HV_RT_INTERNAL(call)                                                                          \
+    do {                                                                                              \
+        int r_ = (call);                                                                              \
+        if (r_ != HV_OK) return r_;                                                                   \
+    } while (0)
+
 namespace hvi {
 
 // ---------------------------------------------------------------- status
@@ -64,6 +70,7 @@ struct hv_handle {
     float *ax = nullptr;         // [NX]   sponge a = q dt / 2 along x
     int *src_zx = nullptr;       // [ns][2] padded (z, x) of each source
     int *rec_zx = nullptr;       // [ns*nr][2] padded (z, x) of each receiver
+    int *status = nullptr;       // device status word (HV_ETIMEOUT if a bounded wait ran out)
     std::vector<int> h_src_zx, h_rec_zx;
     std::mutex mu;
     std::map<long long, hvi::RecTiles> rectiles;                 // keyed by TX * 65536 + TZ
@@ -80,6 +87,17 @@ namespace hvk {
 hvi::Tiling tiling_fwd(const hv_handle *h);
 hvi::Tiling tiling_adj(const hv_handle *h);
 
+// Tensor maps of one call's workspace, viewed as an array of fields
+// (x, z, field index): `halo` copies a tile with its 4-cell halo, `pt` the
+// tile's own points.  Opaque CUtensorMap bytes (128 each).
+struct TmaMaps {
+    alignas(64) unsigned char halo[128];
+    alignas(64) unsigned char pt[128];
+    void *ws = nullptr;
+    long long nfields = 0;
+};
+int make_maps(const hv_handle *h, void *ws, long long nfields, TmaMaps *m);
+
 struct FwdLaunch {
     const float *u_cur, *u_prev;   // field batches [ns][fsize]
     float *u_next;                 // may be nullptr (Born-only groups never write u)
@@ -91,7 +109,8 @@ struct FwdLaunch {
     float *d_du;                   // [k][ns][nt][nr] samples of du^{n+1} or nullptr
     int n, k;
 };
-int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const FwdLaunch &a, cudaStream_t st);
+int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
+               cudaStream_t st);
 
 struct AdjLaunch {
     const float *u;                // u^n field batch [ns][fsize]
@@ -104,7 +123,8 @@ struct AdjLaunch {
     double *img;                   // [G][k][fsize] partial images
     int n, k, G;
 };
-int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const AdjLaunch &a, cudaStream_t st);
+int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
+               cudaStream_t st);
 int adj_groups(const hv_handle *h);
 
 int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float *C, float *b, cudaStream_t st);

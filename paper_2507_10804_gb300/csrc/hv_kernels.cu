@@ -1,26 +1,13 @@
-// hv_kernels.cu -- sm_103a kernels of the Gauss-Newton Hessian apply.
+// hv_kernels.cu -- the non-stencil kernels of the Gauss-Newton Hessian apply:
+// model preparation, image fold, misfit reduction, set-up and housekeeping
+// (the time-stepping kernels are in hv_stencil.cu).
 //
-// Discrete operator (section 2, eq. (pde), with a damping-rate sponge): with
-// C = m^2 dt^2 / h^2, a = q dt / 2 and the unscaled 8th-order stencil sum
-//   Lh w = 2 c0 w + sum_{k=1..4} c_k (w[x-k] + w[x+k] + w[z-k] + w[z+k]),
-//   c0 = -205/72, c1 = 8/5, c2 = -1/5, c3 = 8/315, c4 = -1/560
-// one leapfrog row reads
-//   (1 + a) u^{n+1} = 2 u^n - (1 - a) u^{n-1} + C (Lh u^n + s_n delta_src)
-// (the source s_n/h^2 times m^2 dt^2 is C s_n).  Because S depends on m only
-// through 1/m^2, the Born source is (2 dm / m^3) (T u)^n = (2 dm / m)(L u^n + f^n):
-//   (1 + a) du^{n+1} = 2 du^n - (1 - a) du^{n-1} + C (Lh du^n + b Q^n),
-//   b = 2 dm / m, Q^n = Lh u^n + s_n delta_src,
-// the adjoint is the same stepper run backward with receiver sources,
-//   (1 + a) lam^n = 2 lam^{n+1} - (1 - a) lam^{n+2} + C (Lh lam^{n+1} + h^2 g^n),
-// and the zero-lag image is G^T lam = (2 / (m h^2)) sum_n lam^n Q^n, accumulated
-// here as sum_n lam^n Q^n in FP64 and scaled at the end.  No step forms the
-// three-level difference u^{n+1} - 2u^n + u^{n-1}, so FP32 loses nothing to
-// cancellation.
-//
-// All stencil kernels share one engine: a CTA owns a TX x TZ tile, stages the
-// tile plus its 4-cell halo in shared memory with coalesced float4 loads
-// (the ghost band makes every load unconditional inside the allocation), and
-// each thread computes a 4 (x) x RZ (z) register block from shared memory.
+// The stencil coefficients, the sponge and the time-stepping identities they
+// serve are described in hv_stencil.cu.  Here: C = (m dt / h)^2 and the Born
+// coefficient b = 2 (E v) / (E m) on the padded grid (the model and vectors
+// are replicated into the sponge by E), the sponge rates a = q dt / 2 per
+// axis and the Ricker wavelet, the fold Hv = E^T ((2 / (m h^2)) image), the
+// FP64 misfit reduction, the ghost-band clearing and the wavefield export.
 #include "hv_internal.h"
 
 #include <atomic>
@@ -31,341 +18,6 @@ namespace hvk {
 using hvi::GH;
 
 namespace {
-
-constexpr float LC1 = (float)(8.0 / 5.0);
-constexpr float LC2 = (float)(-1.0 / 5.0);
-constexpr float LC3 = (float)(8.0 / 315.0);
-constexpr float LC4 = (float)(-1.0 / 560.0);
-
-// Stencil tile configuration: BX x BZ threads, each 4 x RZ points.
-template <int BX_, int BZ_, int RZ_>
-struct Cfg {
-    static constexpr int BX = BX_, BZ = BZ_, RZ = RZ_;
-    static constexpr int NT = BX * BZ;
-    static constexpr int TX = 4 * BX, TZ = RZ * BZ;
-    static constexpr int W = TX + 2 * GH, H = TZ + 2 * GH;
-    static constexpr int W4 = W / 4;
-};
-
-using CfgF = Cfg<16, 16, 2>;   // forward / Born / recompute: 64 x 32 tiles
-using CfgA = Cfg<16, 16, 2>;   // adjoint + imaging: 64 x 32 tiles
-
-struct Geo {
-    int P, rows, NZ, NX, ntx;
-    size_t fsize;
-};
-
-__device__ __forceinline__ Geo geo_of(int P, int rows, int NZ, int NX, int ntx, size_t fsize)
-{
-    return Geo{P, rows, NZ, NX, ntx, fsize};
-}
-
-// Stage allocation rows z0 .. z0+H-1, columns x0 .. x0+W-1 (z0, x0 = padded tile
-// origin, which is the allocation origin of its halo) into sm[H][W].
-template <class C>
-__device__ __forceinline__ void load_tile(float *__restrict__ sm, const float *__restrict__ g, const Geo &G,
-                                          int z0, int x0)
-{
-    float4 *s4 = reinterpret_cast<float4 *>(sm);
-    for (int idx = threadIdx.x; idx < C::H * C::W4; idx += C::NT) {
-        int i = idx / C::W4;
-        int q = idx - i * C::W4;
-        int gz = z0 + i, gx = x0 + 4 * q;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (gz < G.rows && gx < G.P) v = __ldg(reinterpret_cast<const float4 *>(g + (size_t)gz * G.P + gx));
-        s4[idx] = v;
-    }
-}
-
-__device__ __forceinline__ float comp(const float4 &v, int c)
-{
-    return c == 0 ? v.x : (c == 1 ? v.y : (c == 2 ? v.z : v.w));
-}
-
-// Lh at the thread's 4 x RZ block; also returns the centre values.  The sum is
-// taken over differences from the centre, sum_k c_k ((w[+k] - w0) + (w[-k] - w0)),
-// which equals Lh w because c0 + 2 sum_k c_k = 0; for smooth fields each
-// difference is small and nearly exact in FP32, so the rounding error of Lh
-// scales with |Lh w| rather than with |w| (about 7x lower wavefield error
-// after 600 steps than the direct sum, at no extra memory traffic).
-template <class C>
-__device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float (&L)[C::RZ][4],
-                                          float (&ctr)[C::RZ][4])
-{
-    const float4 *s4 = reinterpret_cast<const float4 *>(sm);
-    float4 col[C::RZ + 8];
-#pragma unroll
-    for (int i = 0; i < C::RZ + 8; ++i) col[i] = s4[(tz * C::RZ + i) * C::W4 + tx + 1];
-#pragma unroll
-    for (int r = 0; r < C::RZ; ++r) {
-        const int row = tz * C::RZ + r + GH;
-        float4 xm = s4[row * C::W4 + tx];
-        float4 xc = col[r + 4];
-        float4 xp = s4[row * C::W4 + tx + 2];
-        float v[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float cz = v[4 + c];
-            auto pair = [cz](float a, float b) { return (a - cz) + (b - cz); };
-            float acc = LC4 * (pair(v[c], v[8 + c]) + pair(comp(col[r], c), comp(col[r + 8], c)));
-            acc = fmaf(LC3, pair(v[1 + c], v[7 + c]) + pair(comp(col[r + 1], c), comp(col[r + 7], c)), acc);
-            acc = fmaf(LC2, pair(v[2 + c], v[6 + c]) + pair(comp(col[r + 2], c), comp(col[r + 6], c)), acc);
-            acc = fmaf(LC1, pair(v[3 + c], v[5 + c]) + pair(comp(col[r + 3], c), comp(col[r + 5], c)), acc);
-            L[r][c] = acc;
-            ctr[r][c] = cz;
-        }
-    }
-}
-
-__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
-__device__ __forceinline__ float4 ldg4(const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
-
-// Store 4 consecutive x values at padded (z, x..x+3), skipping x >= NX.
-__device__ __forceinline__ void st4(float *p, float4 v, int x, int NX)
-{
-    if (x + 3 < NX) {
-        *reinterpret_cast<float4 *>(p) = v;
-    } else {
-        if (x + 0 < NX) p[0] = v.x;
-        if (x + 1 < NX) p[1] = v.y;
-        if (x + 2 < NX) p[2] = v.z;
-        if (x + 3 < NX) p[3] = v.w;
-    }
-}
-
-struct FwdParams {
-    const float *u_cur, *u_prev;
-    float *u_next;
-    const float *C, *b, *az, *ax, *wavelet;
-    const float *du_cur;
-    float *du_io;
-    float *d_u, *d_du;
-    const int *src_zx;
-    const int *rt_off, *rt_rec, *rt_pos;
-    int n, nt, nr, ns, k, vpg;
-    int P, rows, NZ, NX, ntx, ntiles;
-    size_t fsize;
-};
-
-// One forward time step for one (tile, shot, vector group):
-//   u^{n+1} (group 0 only) and du_j^{n+1} for the group's vectors, with fused
-//   receiver sampling.  grid = (ntiles, ns, ngroups).
-template <class C, bool BORN>
-__global__ void __launch_bounds__(C::NT) k_fwd(const __grid_constant__ FwdParams p)
-{
-    __shared__ __align__(16) float su[C::H * C::W];
-    __shared__ __align__(16) float sd[BORN ? C::H * C::W : 4];
-    const Geo G = geo_of(p.P, p.rows, p.NZ, p.NX, p.ntx, p.fsize);
-    const int tile = blockIdx.x, s = blockIdx.y, grp = blockIdx.z;
-    const int tzi = tile / p.ntx, txi = tile - tzi * p.ntx;
-    const int z0 = tzi * C::TZ, x0 = txi * C::TX;          // padded tile origin
-    const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
-    const size_t so = (size_t)s * p.fsize;
-
-    load_tile<C>(su, p.u_cur + so, G, z0, x0);
-    __syncthreads();
-
-    float Q[C::RZ][4], uc[C::RZ][4];
-    lap_block<C>(su, tx, tz, Q, uc);
-    const int sz = p.src_zx[2 * s], sx = p.src_zx[2 * s + 1];
-    const float wav = p.wavelet[p.n];
-    const int xb = x0 + 4 * tx;                            // padded x of component 0
-    float axv[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.NX - 1)];
-    float Cc[C::RZ][4], inv[C::RZ][4], oma[C::RZ][4];
-#pragma unroll
-    for (int r = 0; r < C::RZ; ++r) {
-        const int z = z0 + tz * C::RZ + r;
-        const float azv = p.az[min(z, p.NZ - 1)];
-        const size_t off = (size_t)(z + GH) * p.P + (xb + GH);
-        float4 c4 = (z < p.NZ && xb < p.NX) ? ldg4(p.C + off) : make_float4(0.f, 0.f, 0.f, 0.f);
-        Cc[r][0] = c4.x; Cc[r][1] = c4.y; Cc[r][2] = c4.z; Cc[r][3] = c4.w;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            if (z == sz && xb + c == sx) Q[r][c] += wav;
-            float a = fmaxf(azv, axv[c]);
-            inv[r][c] = __frcp_rn(1.0f + a);
-            oma[r][c] = 1.0f - a;
-        }
-    }
-
-    const int tb = s * (p.ntiles + 1) + tile;
-    const int rb = p.rt_off[tb], re = p.rt_off[tb + 1];
-
-    if (grp == 0 && p.u_next) {
-        float *un = p.u_next + so;
-#pragma unroll
-        for (int r = 0; r < C::RZ; ++r) {
-            const int z = z0 + tz * C::RZ + r;
-            if (z >= p.NZ || xb >= p.NX) continue;
-            const size_t off = (size_t)(z + GH) * p.P + (xb + GH);
-            float4 pv = ldg4(p.u_prev + so + off);
-            float pr[4] = {pv.x, pv.y, pv.z, pv.w};
-            float o[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-                o[c] = inv[r][c] * (2.0f * uc[r][c] - oma[r][c] * pr[c] + Cc[r][c] * Q[r][c]);
-            st4(un + off, make_float4(o[0], o[1], o[2], o[3]), xb, p.NX);
-        }
-        if (p.d_u && rb < re) {
-            __syncthreads();
-            for (int i = rb + threadIdx.x; i < re; i += C::NT)
-                p.d_u[((size_t)s * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + i]] = un[p.rt_pos[s * p.nr + i]];
-        }
-    }
-
-    if constexpr (BORN) {
-        const int j0 = grp * p.vpg, j1 = min(p.k, j0 + p.vpg);
-        for (int j = j0; j < j1; ++j) {
-            const size_t fo = ((size_t)j * p.ns + s) * p.fsize;
-            __syncthreads();                       // sd reuse across vectors
-            load_tile<C>(sd, p.du_cur + fo, G, z0, x0);
-            __syncthreads();
-            float Ld[C::RZ][4], dc[C::RZ][4];
-            lap_block<C>(sd, tx, tz, Ld, dc);
-            float *dn = p.du_io + fo;
-#pragma unroll
-            for (int r = 0; r < C::RZ; ++r) {
-                const int z = z0 + tz * C::RZ + r;
-                if (z >= p.NZ || xb >= p.NX) continue;
-                const size_t off = (size_t)(z + GH) * p.P + (xb + GH);
-                float4 pv = ld4(dn + off);
-                float4 bv = ldg4(p.b + (size_t)j * p.fsize + off);
-                float pr[4] = {pv.x, pv.y, pv.z, pv.w};
-                float bb[4] = {bv.x, bv.y, bv.z, bv.w};
-                float o[4];
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    o[c] = inv[r][c] *
-                           (2.0f * dc[r][c] - oma[r][c] * pr[c] + Cc[r][c] * (Ld[r][c] + bb[c] * Q[r][c]));
-                st4(dn + off, make_float4(o[0], o[1], o[2], o[3]), xb, p.NX);
-            }
-            if (p.d_du && rb < re) {
-                __syncthreads();
-                for (int i = rb + threadIdx.x; i < re; i += C::NT)
-                    p.d_du[(((size_t)j * p.ns + s) * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + i]] =
-                        dn[p.rt_pos[s * p.nr + i]];
-            }
-        }
-    }
-}
-
-struct AdjParams {
-    const float *u, *lam1;
-    float *lam_io;
-    const float *C, *az, *ax, *wavelet;
-    const float *r;
-    size_t r_vstride;
-    float rscale;
-    double *img;
-    const int *src_zx;
-    const int *rt_off, *rt_rec, *rt_pos;
-    int n, nt, nr, ns, k, spg;
-    int P, rows, NZ, NX, ntx, ntiles;
-    size_t fsize;
-};
-
-// One adjoint time step with zero-lag imaging for one (tile, vector, shot
-// group); the CTA loops over its shots in order and adds its FP64 image
-// contribution once.  grid = (ntiles, k, G).
-template <class C>
-__global__ void __launch_bounds__(C::NT) k_adj(const __grid_constant__ AdjParams p)
-{
-    __shared__ __align__(16) float su[C::H * C::W];
-    __shared__ __align__(16) float sl[C::H * C::W];
-    __shared__ __align__(16) float ssrc[C::TZ * C::TX];
-    const Geo G = geo_of(p.P, p.rows, p.NZ, p.NX, p.ntx, p.fsize);
-    const int tile = blockIdx.x, j = blockIdx.y, g = blockIdx.z;
-    const int tzi = tile / p.ntx, txi = tile - tzi * p.ntx;
-    const int z0 = tzi * C::TZ, x0 = txi * C::TX;
-    const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
-    const int xb = x0 + 4 * tx;
-    const float wav = p.wavelet[p.n];
-
-    float axv[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.NX - 1)];
-    float Cc[C::RZ][4], inv[C::RZ][4], oma[C::RZ][4];
-#pragma unroll
-    for (int r = 0; r < C::RZ; ++r) {
-        const int z = z0 + tz * C::RZ + r;
-        const float azv = p.az[min(z, p.NZ - 1)];
-        const size_t off = (size_t)(z + GH) * p.P + (xb + GH);
-        float4 c4 = (z < p.NZ && xb < p.NX) ? ldg4(p.C + off) : make_float4(0.f, 0.f, 0.f, 0.f);
-        Cc[r][0] = c4.x; Cc[r][1] = c4.y; Cc[r][2] = c4.z; Cc[r][3] = c4.w;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            float a = fmaxf(azv, axv[c]);
-            inv[r][c] = __frcp_rn(1.0f + a);
-            oma[r][c] = 1.0f - a;
-        }
-    }
-    double acc[C::RZ][4];
-#pragma unroll
-    for (int r = 0; r < C::RZ; ++r)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
-
-    const int s0 = g * p.spg, s1 = min(p.ns, s0 + p.spg);
-    for (int s = s0; s < s1; ++s) {
-        const size_t so = (size_t)s * p.fsize;
-        const size_t fo = ((size_t)j * p.ns + s) * p.fsize;
-        const int tb = s * (p.ntiles + 1) + tile;
-        const int rb = p.rt_off[tb], re = p.rt_off[tb + 1];
-        __syncthreads();                           // smem reuse across shots
-        load_tile<C>(su, p.u + so, G, z0, x0);
-        load_tile<C>(sl, p.lam1 + fo, G, z0, x0);
-        if (rb < re) {
-            for (int i = threadIdx.x; i < C::TZ * C::TX; i += C::NT) ssrc[i] = 0.0f;
-            __syncthreads();
-            const float *rs = p.r + (size_t)j * p.r_vstride + ((size_t)s * p.nt + p.n) * p.nr;
-            for (int i = rb + threadIdx.x; i < re; i += C::NT) {
-                int pos = p.rt_pos[s * p.nr + i];
-                int zz = pos / p.P - GH - z0, xx = pos % p.P - GH - x0;
-                ssrc[zz * C::TX + xx] = p.rscale * rs[p.rt_rec[s * p.nr + i]];
-            }
-        }
-        __syncthreads();
-        float Qu[C::RZ][4], ucen[C::RZ][4], Ll[C::RZ][4], lc[C::RZ][4];
-        lap_block<C>(su, tx, tz, Qu, ucen);
-        lap_block<C>(sl, tx, tz, Ll, lc);
-        const int sz = p.src_zx[2 * s], sx = p.src_zx[2 * s + 1];
-        float *ln = p.lam_io + fo;
-#pragma unroll
-        for (int r = 0; r < C::RZ; ++r) {
-            const int z = z0 + tz * C::RZ + r;
-            const size_t off = (size_t)(z + GH) * p.P + (xb + GH);
-            float src[4] = {0.f, 0.f, 0.f, 0.f};
-            if (rb < re) {
-                float4 sv = *reinterpret_cast<const float4 *>(&ssrc[(tz * C::RZ + r) * C::TX + 4 * tx]);
-                src[0] = sv.x; src[1] = sv.y; src[2] = sv.z; src[3] = sv.w;
-            }
-            if (z >= p.NZ || xb >= p.NX) continue;
-            float4 pv = ld4(ln + off);
-            float pr[4] = {pv.x, pv.y, pv.z, pv.w};
-            float o[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                float q = Qu[r][c];
-                if (z == sz && xb + c == sx) q += wav;
-                o[c] = inv[r][c] * (2.0f * lc[r][c] - oma[r][c] * pr[c] + Cc[r][c] * (Ll[r][c] + src[c]));
-                acc[r][c] += (double)o[c] * (double)q;
-            }
-            st4(ln + off, make_float4(o[0], o[1], o[2], o[3]), xb, p.NX);
-        }
-    }
-    double *im = p.img + ((size_t)g * p.k + j) * p.fsize;
-#pragma unroll
-    for (int r = 0; r < C::RZ; ++r) {
-        const int z = z0 + tz * C::RZ + r;
-        if (z >= p.NZ || xb >= p.NX) continue;
-        const size_t off = (size_t)(z + GH) * p.P + (xb + GH);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (xb + c < p.NX) im[off + c] += acc[r][c];
-    }
-}
 
 // m (interior) -> C on the padded grid; v_j -> b_j = 2 (E v_j) / (E m).
 __global__ void k_prep(const float *__restrict__ m, const float *__restrict__ v, int k, float *__restrict__ Cc,
@@ -520,89 +172,11 @@ int cuda_check(const char *what)
     return HV_OK;
 }
 
-template <class C>
-hvi::Tiling make_tiling(const hv_handle *h)
-{
-    hvi::Tiling t;
-    t.TX = C::TX;
-    t.TZ = C::TZ;
-    t.ntx = (h->NX + C::TX - 1) / C::TX;
-    t.ntz = (h->NZ + C::TZ - 1) / C::TZ;
-    t.ntiles = t.ntx * t.ntz;
-    return t;
-}
-
 }  // namespace
 
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
-
-hvi::Tiling tiling_fwd(const hv_handle *h) { return make_tiling<CfgF>(h); }
-hvi::Tiling tiling_adj(const hv_handle *h) { return make_tiling<CfgA>(h); }
-
-// Shot groups of the adjoint kernel.  Each group sums its shots' image
-// contributions in shot order into its own FP64 partial image; the groups are
-// summed in group order at the end.  The count depends only on the grid and
-// the shot count (never on k), so a vector's result is bitwise the same
-// whether it is applied alone or in a batch.
-int adj_groups(const hv_handle *h)
-{
-    hvi::Tiling t = tiling_adj(h);
-    long long ctas = (long long)t.ntiles;
-    int G = (int)((608 + ctas - 1) / ctas);
-    if (G < 1) G = 1;
-    if (G > h->ns) G = h->ns;
-    int spg = (h->ns + G - 1) / G;
-    return (h->ns + spg - 1) / spg;
-}
-
-int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const FwdLaunch &a, cudaStream_t st)
-{
-    hvi::Tiling t = tiling_fwd(h);
-    FwdParams p{};
-    p.u_cur = a.u_cur; p.u_prev = a.u_prev; p.u_next = a.u_next;
-    p.C = a.C; p.b = a.b; p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
-    p.du_cur = a.du_cur; p.du_io = a.du_io; p.d_u = a.d_u; p.d_du = a.d_du;
-    p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
-    p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
-    p.P = h->P; p.rows = h->rows; p.NZ = h->NZ; p.NX = h->NX; p.ntx = t.ntx; p.ntiles = t.ntiles;
-    p.fsize = h->fsize;
-    const bool born = a.b != nullptr && a.k > 0;
-    int groups = 1;
-    if (born) {
-        // enough CTAs to fill the machine; each group recomputes Q from u
-        long long base = (long long)t.ntiles * h->ns;
-        groups = (int)((608 + base - 1) / base);
-        if (groups > a.k) groups = a.k;
-        if (groups < 1) groups = 1;
-        p.vpg = (a.k + groups - 1) / groups;
-        groups = (a.k + p.vpg - 1) / p.vpg;
-    } else {
-        p.vpg = 0;
-    }
-    dim3 grid(t.ntiles, h->ns, groups);
-    if (born) k_fwd<CfgF, true><<<grid, CfgF::NT, 0, st>>>(p);
-    else k_fwd<CfgF, false><<<grid, CfgF::NT, 0, st>>>(p);
-    return cuda_check("k_fwd launch");
-}
-
-int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const AdjLaunch &a, cudaStream_t st)
-{
-    hvi::Tiling t = tiling_adj(h);
-    AdjParams p{};
-    p.u = a.u; p.lam1 = a.lam1; p.lam_io = a.lam_io;
-    p.C = a.C; p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
-    p.r = a.r; p.r_vstride = a.r_per_vector ? (size_t)h->ns * h->nt * h->nr : 0; p.rscale = a.rscale;
-    p.img = a.img; p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
-    p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
-    p.spg = (h->ns + a.G - 1) / a.G;
-    p.P = h->P; p.rows = h->rows; p.NZ = h->NZ; p.NX = h->NX; p.ntx = t.ntx; p.ntiles = t.ntiles;
-    p.fsize = h->fsize;
-    dim3 grid(t.ntiles, a.k, a.G);
-    k_adj<CfgA><<<grid, CfgA::NT, 0, st>>>(p);
-    return cuda_check("k_adj launch");
-}
 
 int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float *C, float *b, cudaStream_t st)
 {

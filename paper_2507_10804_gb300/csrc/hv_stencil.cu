@@ -1,0 +1,671 @@
+// hv_stencil.cu -- the time-stepping kernels (forward / Born / recompute and
+// adjoint + imaging) on sm_103a: TMA-staged shared-memory tiles pipelined
+// across shots.
+//
+// Operator (section 2, eq. (pde) with the damping-rate sponge; C = (m dt/h)^2,
+// a = q dt / 2, Lh = h^2 L the unscaled 8th-order sum, s_n the source):
+//   (1 + a) u^{n+1}   = 2 u^n - (1 - a) u^{n-1} + C (Lh u^n + s_n delta_src)
+//   (1 + a) du^{n+1}  = 2 du^n - (1 - a) du^{n-1} + C (Lh du^n + b Q^n),  b = 2 dm / m
+//   (1 + a) lam^n     = 2 lam^{n+1} - (1 - a) lam^{n+2} + C (Lh lam^{n+1} + h^2 g^n)
+//   image            += lam^n Q^n,  Q^n = Lh u^n + s_n delta_src
+//                       (per step: FP32 over <= 8 shots, then added to an FP64 image)
+// The Born source and the image use (T u)^n = m^2 (L u^n + f^n), the exact
+// identity of the forward rows, so no FP32 step forms u^{n+1} - 2u^n + u^{n-1}.
+//
+// Work decomposition: a CTA owns one TX x TZ tile of the padded grid, one
+// vector j and a group of up to 8 shots, and walks its shots in order.  The
+// whole workspace is one 3D tensor (x, z, field index) for the Tensor Memory
+// Accelerator: for each shot one thread issues bulk tile copies of the
+// stencil inputs (with their 4-cell halo) and of the point inputs into a
+// shared-memory stage, and an mbarrier counts the bytes in.  Two stages:
+// while shot i is computed, shot i+1's tiles are in flight.  Every field
+// carries a zero ghost band and the tensor bounds fill zeros, so no load is
+// guarded.  Waits are bounded by a deadline; a timeout sets a device status
+// word and the CTA returns.
+#include "hv_internal.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
+
+namespace hvk {
+
+using hvi::GH;
+
+namespace {
+
+constexpr float LC1 = (float)(8.0 / 5.0);
+constexpr float LC2 = (float)(-1.0 / 5.0);
+constexpr float LC3 = (float)(8.0 / 315.0);
+constexpr float LC4 = (float)(-1.0 / 560.0);
+
+constexpr int kShotsPerGroup = 8;
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+template <int BX_, int BZ_, int RZ_>
+struct Cfg {
+    static constexpr int BX = BX_, BZ = BZ_, RZ = RZ_;
+    static constexpr int NT = BX * BZ;
+    static constexpr int TX = 4 * BX, TZ = RZ * BZ;
+    static constexpr int W = TX + 2 * GH, H = TZ + 2 * GH;
+    static constexpr int W4 = W / 4;
+    static constexpr int HALO = W * H * 4;   // bytes of a halo tile
+    static constexpr int PT = TX * TZ * 4;   // bytes of a point tile
+};
+using CfgS = Cfg<16, 16, 2>;   // 64 x 32 tiles, 256 threads, 4 x 2 points per thread
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for an mbarrier phase; false (and the status word set) after the deadline.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (globaltimer() - t0 > kWaitNs) {
+            atomicExch(status, HV_ETIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// 3D tiled bulk copy global -> shared, completion counted on `bar`.
+__device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int x, int z, int f, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(z), "r"(f), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ------------------------------------------------------------------ stencil
+// Lh at the thread's 4 x RZ block from a [H][W] halo tile, as
+// sum_k c_k ((w[+k] - w0) + (w[-k] - w0)) (equal to Lh because c0 + 2 sum c_k = 0;
+// each difference is small and nearly exact for smooth fields, so the FP32
+// error scales with |Lh w| rather than |w|).  Also returns the centre values.
+template <class C>
+__device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float (&L)[C::RZ][4],
+                                          float (&ctr)[C::RZ][4])
+{
+    const float4 *s4 = reinterpret_cast<const float4 *>(sm);
+    float4 col[C::RZ + 8];
+#pragma unroll
+    for (int i = 0; i < C::RZ + 8; ++i) col[i] = s4[(tz * C::RZ + i) * C::W4 + tx + 1];
+#pragma unroll
+    for (int r = 0; r < C::RZ; ++r) {
+        const int row = tz * C::RZ + r + GH;
+        const float4 xm = s4[row * C::W4 + tx];
+        const float4 xc = col[r + 4];
+        const float4 xp = s4[row * C::W4 + tx + 2];
+        const float v[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float cz = v[4 + c];
+            auto comp = [](const float4 &q, int cc) { return cc == 0 ? q.x : (cc == 1 ? q.y : (cc == 2 ? q.z : q.w)); };
+            auto pair = [cz](float a, float b) { return (a - cz) + (b - cz); };
+            float acc = LC4 * (pair(v[c], v[8 + c]) + pair(comp(col[r], c), comp(col[r + 8], c)));
+            acc = fmaf(LC3, pair(v[1 + c], v[7 + c]) + pair(comp(col[r + 1], c), comp(col[r + 7], c)), acc);
+            acc = fmaf(LC2, pair(v[2 + c], v[6 + c]) + pair(comp(col[r + 2], c), comp(col[r + 6], c)), acc);
+            acc = fmaf(LC1, pair(v[3 + c], v[5 + c]) + pair(comp(col[r + 3], c), comp(col[r + 5], c)), acc);
+            L[r][c] = acc;
+            ctr[r][c] = cz;
+        }
+    }
+}
+
+// Sponge factors of one row of the thread's block: inv = 1 / (1 + a),
+// oma = 1 - a with a = max(a_z, a_x); exactly 1 in tiles without sponge.
+__device__ __forceinline__ void sponge_row(bool sponge, const float *az, int z, int NZ, const float (&axv)[4],
+                                           float (&inv)[4], float (&oma)[4])
+{
+    if (!sponge) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            inv[c] = 1.0f;
+            oma[c] = 1.0f;
+        }
+        return;
+    }
+    const float azv = az[min(z, NZ - 1)];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const float a = fmaxf(azv, axv[c]);
+        inv[c] = __frcp_rn(1.0f + a);
+        oma[c] = 1.0f - a;
+    }
+}
+
+__device__ __forceinline__ void f4(const float *p, float (&o)[4])
+{
+    const float4 v = *reinterpret_cast<const float4 *>(p);
+    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+}
+
+// Store 4 consecutive x values at padded column x.. (skipping x >= NX).
+__device__ __forceinline__ void st4(float *p, const float (&o)[4], int x, int NX)
+{
+    if (x + 3 < NX) {
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+    } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (x + c < NX) p[c] = o[c];
+    }
+}
+
+struct Geo {
+    int P, NZ, NX, nz, nx, nb, ntx, ntiles;
+    unsigned long long fsize;   // floats per field
+};
+
+struct FwdParams {
+    CUtensorMap map_halo;       // box (TX+8) x (TZ+8) x 1
+    CUtensorMap map_pt;         // box TX x TZ x 1
+    float *ws;                  // workspace base (field 0)
+    int f_ucur, f_uprev, f_unext;   // field-batch starts (f_unext < 0: do not write u)
+    int f_C, f_b, f_du, f_dio;      // coefficient fields and Born field batches
+    float *d_u, *d_du;
+    const float *az, *ax, *wavelet;
+    const int *src_zx, *rt_off, *rt_rec, *rt_pos;
+    int *status;
+    int n, nt, nr, ns, k, spg;
+    Geo g;
+};
+
+template <class C, bool BORN>
+struct FwdSmem {
+    static constexpr int STAGE = C::HALO + C::PT + (BORN ? C::HALO + C::PT : 0);
+    static constexpr int COEF = C::PT * (BORN ? 2 : 1);
+    static constexpr int BYTES = 2 * STAGE + COEF + 64;
+};
+
+// One forward time step.  grid = (ntiles, k or 1, shot groups).  Vector j = 0
+// writes u^{n+1}; every CTA recomputes Q^n = Lh u^n + s_n from its own tile.
+template <class C, bool BORN>
+__global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdParams p)
+{
+    using S = FwdSmem<C, BORN>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *sC = reinterpret_cast<float *>(smem + 2 * S::STAGE);
+    float *sB = sC + C::TX * C::TZ;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + S::COEF);
+
+    const int tile = blockIdx.x, j = blockIdx.y, grp = blockIdx.z;
+    const int tzi = tile / p.g.ntx, txi = tile - tzi * p.g.ntx;
+    const int z0 = tzi * C::TZ, x0 = txi * C::TX;
+    const int s0 = grp * p.spg, s1 = min(p.ns, s0 + p.spg), nitems = s1 - s0;
+    const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
+    const int xb = x0 + 4 * tx;
+
+    auto issue = [&](int i) {
+        const int st = i & 1, s = s0 + i;
+        unsigned char *base = smem + st * S::STAGE;
+        mbar_expect_tx(&bars[st], S::STAGE);
+        tma_load(base, &p.map_halo, x0, z0, p.f_ucur + s, &bars[st]);
+        tma_load(base + C::HALO, &p.map_pt, x0 + GH, z0 + GH, p.f_uprev + s, &bars[st]);
+        if constexpr (BORN) {
+            const int fo = j * p.ns + s;
+            tma_load(base + C::HALO + C::PT, &p.map_halo, x0, z0, p.f_du + fo, &bars[st]);
+            tma_load(base + 2 * C::HALO + C::PT, &p.map_pt, x0 + GH, z0 + GH, p.f_dio + fo, &bars[st]);
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[2], S::COEF);
+        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[2]);
+        if constexpr (BORN) tma_load(sB, &p.map_pt, x0 + GH, z0 + GH, p.f_b + j, &bars[2]);
+        issue(0);
+        if (nitems > 1) issue(1);
+    }
+
+    // Sponge coefficients; tiles entirely inside the interior have a = 0.
+    const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
+                          x0 + C::TX <= p.g.nb + p.g.nx);
+    float axv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (sponge)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
+    const float wav = p.wavelet[p.n];
+
+    bool ok = mbar_wait(&bars[2], 0, p.status);
+    if (__syncthreads_or(!ok)) return;
+
+    for (int i = 0; i < nitems; ++i) {
+        const int st = i & 1, s = s0 + i;
+        ok = mbar_wait(&bars[st], (i >> 1) & 1, p.status);
+        if (__syncthreads_or(!ok)) {
+            // a copy did not arrive: let the other stage drain (bounded), then give up
+            if (i + 1 < nitems) mbar_wait(&bars[st ^ 1], ((i + 1) >> 1) & 1, p.status);
+            return;
+        }
+        const unsigned char *base = smem + st * S::STAGE;
+        const float *sU = reinterpret_cast<const float *>(base);
+        const float *sUp = reinterpret_cast<const float *>(base + C::HALO);
+
+        float Q[C::RZ][4], uc[C::RZ][4];
+        lap_block<C>(sU, tx, tz, Q, uc);
+        const int sz = p.src_zx[2 * s], sx = p.src_zx[2 * s + 1];
+#pragma unroll
+        for (int r = 0; r < C::RZ; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (z0 + tz * C::RZ + r == sz && xb + c == sx) Q[r][c] += wav;
+
+        const int tb = s * (p.g.ntiles + 1) + tile;
+        const int rb = p.rt_off[tb], re = p.rt_off[tb + 1];
+        if (p.f_unext >= 0 && j == 0) {
+            float *un = p.ws + (unsigned long long)(p.f_unext + s) * p.g.fsize;
+#pragma unroll
+            for (int r = 0; r < C::RZ; ++r) {
+                const int z = z0 + tz * C::RZ + r;
+                float up[4], cc[4], inv[4], oma[4], o[4];
+                f4(sUp + (tz * C::RZ + r) * C::TX + 4 * tx, up);
+                f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
+                sponge_row(sponge, p.az, z, p.g.NZ, axv, inv, oma);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) o[c] = inv[c] * (2.0f * uc[r][c] - oma[c] * up[c] + cc[c] * Q[r][c]);
+                if (z < p.g.NZ && xb < p.g.NX) st4(un + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
+            }
+            if (p.d_u && rb < re) {
+                __syncthreads();
+                for (int q = rb + threadIdx.x; q < re; q += C::NT)
+                    p.d_u[((size_t)s * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + q]] = un[p.rt_pos[s * p.nr + q]];
+            }
+        }
+        if constexpr (BORN) {
+            const float *sD = reinterpret_cast<const float *>(base + C::HALO + C::PT);
+            const float *sDp = reinterpret_cast<const float *>(base + 2 * C::HALO + C::PT);
+            float Ld[C::RZ][4], dc[C::RZ][4];
+            lap_block<C>(sD, tx, tz, Ld, dc);
+            const int fo = j * p.ns + s;
+            float *dn = p.ws + (unsigned long long)(p.f_dio + fo) * p.g.fsize;
+#pragma unroll
+            for (int r = 0; r < C::RZ; ++r) {
+                const int z = z0 + tz * C::RZ + r;
+                float dp[4], cc[4], bb[4], inv[4], oma[4], o[4];
+                f4(sDp + (tz * C::RZ + r) * C::TX + 4 * tx, dp);
+                f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
+                f4(sB + (tz * C::RZ + r) * C::TX + 4 * tx, bb);
+                sponge_row(sponge, p.az, z, p.g.NZ, axv, inv, oma);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    o[c] = inv[c] * (2.0f * dc[r][c] - oma[c] * dp[c] + cc[c] * (Ld[r][c] + bb[c] * Q[r][c]));
+                if (z < p.g.NZ && xb < p.g.NX) st4(dn + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
+            }
+            if (p.d_du && rb < re) {
+                __syncthreads();
+                for (int q = rb + threadIdx.x; q < re; q += C::NT)
+                    p.d_du[((size_t)fo * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + q]] = dn[p.rt_pos[s * p.nr + q]];
+            }
+        }
+        __syncthreads();                       // every thread is done with stage st
+        if (threadIdx.x == 0 && i + 2 < nitems) issue(i + 2);
+    }
+}
+
+struct AdjParams {
+    CUtensorMap map_halo, map_pt;
+    float *ws;
+    int f_u, f_lam1, f_lamio, f_C;
+    const float *r;
+    unsigned long long r_vstride;
+    float rscale;
+    double *img;
+    const float *az, *ax, *wavelet;
+    const int *src_zx, *rt_off, *rt_rec, *rt_pos;
+    int *status;
+    int n, nt, nr, ns, k, spg;
+    Geo g;
+};
+
+template <class C>
+struct AdjSmem {
+    static constexpr int STAGE = 2 * C::HALO + C::PT;
+    static constexpr int BYTES = 2 * STAGE + C::PT /* C */ + C::PT /* sources */ + 64;
+};
+
+// One adjoint time step with zero-lag imaging.  grid = (ntiles, k, shot
+// groups); the CTA sums its shots' image contributions in shot order and adds
+// them to its group's FP64 partial image once per step.
+template <class C>
+__global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjParams p)
+{
+    using S = AdjSmem<C>;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *sC = reinterpret_cast<float *>(smem + 2 * S::STAGE);
+    float *ssrc = sC + C::TX * C::TZ;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + 2 * C::PT);
+
+    const int tile = blockIdx.x, j = blockIdx.y, grp = blockIdx.z;
+    const int tzi = tile / p.g.ntx, txi = tile - tzi * p.g.ntx;
+    const int z0 = tzi * C::TZ, x0 = txi * C::TX;
+    const int s0 = grp * p.spg, s1 = min(p.ns, s0 + p.spg), nitems = s1 - s0;
+    const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
+    const int xb = x0 + 4 * tx;
+
+    auto issue = [&](int i) {
+        const int st = i & 1, s = s0 + i;
+        unsigned char *base = smem + st * S::STAGE;
+        const int fo = j * p.ns + s;
+        mbar_expect_tx(&bars[st], S::STAGE);
+        tma_load(base, &p.map_halo, x0, z0, p.f_u + s, &bars[st]);
+        tma_load(base + C::HALO, &p.map_halo, x0, z0, p.f_lam1 + fo, &bars[st]);
+        tma_load(base + 2 * C::HALO, &p.map_pt, x0 + GH, z0 + GH, p.f_lamio + fo, &bars[st]);
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        mbar_init(&bars[2], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[2], C::PT);
+        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[2]);
+        issue(0);
+        if (nitems > 1) issue(1);
+    }
+
+    const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
+                          x0 + C::TX <= p.g.nb + p.g.nx);
+    float axv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (sponge)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
+    const float wav = p.wavelet[p.n];
+    // This step's image contribution of the CTA's shots, summed in shot order
+    // in FP32 (at most 8 terms); it is added to the FP64 image once per step.
+    // Double-precision arithmetic is slow on this part, so none runs per shot.
+    float acc[C::RZ][4];
+#pragma unroll
+    for (int r = 0; r < C::RZ; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
+
+    bool ok = mbar_wait(&bars[2], 0, p.status);
+    if (__syncthreads_or(!ok)) return;
+
+    for (int i = 0; i < nitems; ++i) {
+        const int st = i & 1, s = s0 + i;
+        const int fo = j * p.ns + s;
+        const int tb = s * (p.g.ntiles + 1) + tile;
+        const int rb = p.rt_off[tb], re = p.rt_off[tb + 1];
+        if (rb < re) {                         // receivers in this tile: stage their sources
+            for (int q = threadIdx.x; q < C::TZ * C::TX; q += C::NT) ssrc[q] = 0.0f;
+            __syncthreads();
+            const float *rs = p.r + (size_t)j * p.r_vstride + ((size_t)s * p.nt + p.n) * p.nr;
+            for (int q = rb + threadIdx.x; q < re; q += C::NT) {
+                const int pos = p.rt_pos[s * p.nr + q];
+                const int zz = pos / p.g.P - GH - z0, xx = pos % p.g.P - GH - x0;
+                ssrc[zz * C::TX + xx] = p.rscale * rs[p.rt_rec[s * p.nr + q]];
+            }
+        }
+        ok = mbar_wait(&bars[st], (i >> 1) & 1, p.status);
+        if (__syncthreads_or(!ok)) {
+            if (i + 1 < nitems) mbar_wait(&bars[st ^ 1], ((i + 1) >> 1) & 1, p.status);
+            return;
+        }
+        const unsigned char *base = smem + st * S::STAGE;
+        const float *sU = reinterpret_cast<const float *>(base);
+        const float *sL1 = reinterpret_cast<const float *>(base + C::HALO);
+        const float *sL2 = reinterpret_cast<const float *>(base + 2 * C::HALO);
+        float Qu[C::RZ][4], ucen[C::RZ][4], Ll[C::RZ][4], lc[C::RZ][4];
+        lap_block<C>(sU, tx, tz, Qu, ucen);
+        lap_block<C>(sL1, tx, tz, Ll, lc);
+        const int sz = p.src_zx[2 * s], sx = p.src_zx[2 * s + 1];
+        float *ln = p.ws + (unsigned long long)(p.f_lamio + fo) * p.g.fsize;
+#pragma unroll
+        for (int r = 0; r < C::RZ; ++r) {
+            const int z = z0 + tz * C::RZ + r;
+            float l2[4], cc[4], inv[4], oma[4], src[4] = {0.f, 0.f, 0.f, 0.f}, o[4];
+            f4(sL2 + (tz * C::RZ + r) * C::TX + 4 * tx, l2);
+            f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
+            sponge_row(sponge, p.az, z, p.g.NZ, axv, inv, oma);
+            if (rb < re) f4(ssrc + (tz * C::RZ + r) * C::TX + 4 * tx, src);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float q = Qu[r][c];
+                if (z == sz && xb + c == sx) q += wav;
+                o[c] = inv[c] * (2.0f * lc[r][c] - oma[c] * l2[c] + cc[c] * (Ll[r][c] + src[c]));
+                acc[r][c] = fmaf(o[c], q, acc[r][c]);
+            }
+            if (z < p.g.NZ && xb < p.g.NX) st4(ln + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && i + 2 < nitems) issue(i + 2);
+    }
+    double *im = p.img + ((size_t)grp * p.k + j) * p.g.fsize;
+#pragma unroll
+    for (int r = 0; r < C::RZ; ++r) {
+        const int z = z0 + tz * C::RZ + r;
+        if (z >= p.g.NZ || xb >= p.g.NX) continue;
+        const size_t off = (size_t)(z + GH) * p.g.P + (xb + GH);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            if (xb + c < p.g.NX) im[off + c] += (double)acc[r][c];
+    }
+}
+
+// ------------------------------------------------------------------ host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    });
+    return fn;
+}
+
+int encode(CUtensorMap *map, const hv_handle *h, void *ws, long long nfields, int boxx, int boxz)
+{
+    auto fn = encode_fn();
+    if (!fn) return hvi::fail(HV_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    cuuint64_t dims[3] = {(cuuint64_t)h->P, (cuuint64_t)h->rows, (cuuint64_t)nfields};
+    cuuint64_t strides[2] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->fsize * 4};
+    cuuint32_t box[3] = {(cuuint32_t)boxx, (cuuint32_t)boxz, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return hvi::fail(HV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return HV_OK;
+}
+
+int field_index(const void *ws, const void *p, size_t fbytes, int *out)
+{
+    if (!p) {
+        *out = -1;
+        return HV_OK;
+    }
+    ptrdiff_t d = (const char *)p - (const char *)ws;
+    if (d < 0 || (size_t)d % fbytes != 0) return hvi::fail(HV_EINVAL, "internal: field not aligned in the workspace");
+    *out = (int)((size_t)d / fbytes);
+    return HV_OK;
+}
+
+template <class C>
+hvi::Tiling make_tiling(const hv_handle *h)
+{
+    hvi::Tiling t;
+    t.TX = C::TX;
+    t.TZ = C::TZ;
+    t.ntx = (h->NX + C::TX - 1) / C::TX;
+    t.ntz = (h->NZ + C::TZ - 1) / C::TZ;
+    t.ntiles = t.ntx * t.ntz;
+    return t;
+}
+
+template <class K>
+int set_smem(K kern, int bytes)
+{
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+    return HV_OK;
+}
+
+// Raise a kernel's dynamic shared memory limit once per (kernel slot, device).
+template <class K>
+int ensure_smem(int slot, int dev, K kern, int bytes)
+{
+    static std::mutex mu;
+    static bool done[8][64] = {};
+    if (dev < 0 || dev >= 64) return hvi::fail(HV_EINVAL, "device ordinal %d out of range", dev);
+    std::lock_guard<std::mutex> g(mu);
+    if (done[slot][dev]) return HV_OK;
+    HV_RT_INTERNAL(set_smem(kern, bytes));
+    done[slot][dev] = true;
+    return HV_OK;
+}
+
+int launched(const char *what)
+{
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return HV_OK;
+}
+
+Geo geo(const hv_handle *h, const hvi::Tiling &t)
+{
+    return Geo{h->P, h->NZ, h->NX, h->nz, h->nx, h->nb, t.ntx, t.ntiles, (unsigned long long)h->fsize};
+}
+
+}  // namespace
+
+hvi::Tiling tiling_fwd(const hv_handle *h) { return make_tiling<CfgS>(h); }
+hvi::Tiling tiling_adj(const hv_handle *h) { return make_tiling<CfgS>(h); }
+
+// Shot groups of the adjoint kernel: groups of up to 8 shots, summed in shot
+// order inside a CTA and in group order at the end.  The grouping depends
+// only on the shot count (never on k), so a vector's result is bitwise the
+// same whether it is applied alone or in a batch.
+int adj_groups(const hv_handle *h) { return (h->ns + kShotsPerGroup - 1) / kShotsPerGroup; }
+
+int make_maps(const hv_handle *h, void *ws, long long nfields, TmaMaps *m)
+{
+    HV_RT_INTERNAL(encode(reinterpret_cast<CUtensorMap *>(m->halo), h, ws, nfields, CfgS::W, CfgS::H));
+    HV_RT_INTERNAL(encode(reinterpret_cast<CUtensorMap *>(m->pt), h, ws, nfields, CfgS::TX, CfgS::TZ));
+    m->ws = ws;
+    m->nfields = nfields;
+    return HV_OK;
+}
+
+int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a, cudaStream_t st)
+{
+    const hvi::Tiling t = tiling_fwd(h);
+    const size_t fbytes = h->fsize * sizeof(float);
+    FwdParams p;
+    memcpy(&p.map_halo, maps.halo, sizeof(CUtensorMap));
+    memcpy(&p.map_pt, maps.pt, sizeof(CUtensorMap));
+    p.ws = reinterpret_cast<float *>(maps.ws);
+    HV_RT_INTERNAL(field_index(maps.ws, a.u_cur, fbytes, &p.f_ucur));
+    HV_RT_INTERNAL(field_index(maps.ws, a.u_prev, fbytes, &p.f_uprev));
+    HV_RT_INTERNAL(field_index(maps.ws, a.u_next, fbytes, &p.f_unext));
+    HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
+    const bool born = a.b != nullptr && a.k > 0;
+    HV_RT_INTERNAL(field_index(maps.ws, born ? a.b : nullptr, fbytes, &p.f_b));
+    HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_cur : nullptr, fbytes, &p.f_du));
+    HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_io : nullptr, fbytes, &p.f_dio));
+    p.d_u = a.d_u;
+    p.d_du = born ? a.d_du : nullptr;
+    p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
+    p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
+    p.status = h->status;
+    p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : 1;
+    p.spg = kShotsPerGroup < h->ns ? kShotsPerGroup : h->ns;
+    p.g = geo(h, t);
+    dim3 grid(t.ntiles, p.k, (h->ns + p.spg - 1) / p.spg);
+    if (born) {
+        HV_RT_INTERNAL(ensure_smem(0, h->device, k_fwd<CfgS, true>, FwdSmem<CfgS, true>::BYTES));
+        k_fwd<CfgS, true><<<grid, CfgS::NT, FwdSmem<CfgS, true>::BYTES, st>>>(p);
+    } else {
+        HV_RT_INTERNAL(ensure_smem(1, h->device, k_fwd<CfgS, false>, FwdSmem<CfgS, false>::BYTES));
+        k_fwd<CfgS, false><<<grid, CfgS::NT, FwdSmem<CfgS, false>::BYTES, st>>>(p);
+    }
+    return launched("k_fwd launch");
+}
+
+int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a, cudaStream_t st)
+{
+    const hvi::Tiling t = tiling_adj(h);
+    const size_t fbytes = h->fsize * sizeof(float);
+    AdjParams p;
+    memcpy(&p.map_halo, maps.halo, sizeof(CUtensorMap));
+    memcpy(&p.map_pt, maps.pt, sizeof(CUtensorMap));
+    p.ws = reinterpret_cast<float *>(maps.ws);
+    HV_RT_INTERNAL(field_index(maps.ws, a.u, fbytes, &p.f_u));
+    HV_RT_INTERNAL(field_index(maps.ws, a.lam1, fbytes, &p.f_lam1));
+    HV_RT_INTERNAL(field_index(maps.ws, a.lam_io, fbytes, &p.f_lamio));
+    HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
+    p.r = a.r;
+    p.r_vstride = a.r_per_vector ? (unsigned long long)h->ns * h->nt * h->nr : 0ull;
+    p.rscale = a.rscale;
+    p.img = a.img;
+    p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
+    p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
+    p.status = h->status;
+    p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
+    p.spg = (h->ns + a.G - 1) / a.G;
+    p.g = geo(h, t);
+    HV_RT_INTERNAL(ensure_smem(2, h->device, k_adj<CfgS>, AdjSmem<CfgS>::BYTES));
+    dim3 grid(t.ntiles, a.k, a.G);
+    k_adj<CfgS><<<grid, CfgS::NT, AdjSmem<CfgS>::BYTES, st>>>(p);
+    return launched("k_adj launch");
+}
+
+}  // namespace hvk
