@@ -45,7 +45,8 @@ def workload_config(w):
     return {
         "workload": f"GN Hessian apply, {w.nz}x{w.nx} grid at {w.h:g} m + {w.nb}-cell sponge "
                     f"({w.nz + 2 * w.nb}x{w.nx + 2 * w.nb} padded), {w.ns} shots x {w.nr} receivers, "
-                    f"{w.nt} steps, {w.k} vector, {CKPT} snapshots/shot (binomial checkpointing)",
+                    f"{w.nt} steps, {w.k} vector{'s' if w.k > 1 else ''}, "
+                    + (f"{CKPT} snapshots/shot (binomial checkpointing)" if CKPT > 0 else "every time level stored"),
         "grid": [w.nz, w.nx], "sponge": w.nb, "h_m": w.h, "shots": w.ns, "receivers": w.nr, "steps": w.nt,
         "dt_s": w.dt, "f0_hz": w.f0, "vectors": w.k, "snapshots_per_shot": CKPT,
         "l2": "inputs larger than L2 (per-step working set of fields and snapshots >> 129 MB)",
@@ -143,7 +144,10 @@ def oracle_sample(w, threads: int, nt_s: int):
     return upd / sec / 1e9, sec, desc
 
 
-def updates_per_hv(w) -> float:
+def updates_per_call(w) -> float:
+    """Grid-point updates of one call applying H to the workload's k vectors: 3 fields
+    (forward, Born, adjoint) for the first vector, 2 more per extra vector sharing u;
+    recomputation from snapshots is not counted."""
     return 3.0 * (w.nz + 2 * w.nb) * (w.nx + 2 * w.nb) * w.nt * w.ns * (1 + 2.0 * (w.k - 1) / 3.0)
 
 
@@ -163,7 +167,7 @@ def run_reference(args, w):
         upds.append(g)
         tot += sec
     gups = float(np.mean(upds))
-    val = gups * 1e9 / updates_per_hv(w)
+    val = gups * 1e9 / updates_per_call(w) * w.k
     line = {
         "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": tot / args.steps * 1e3,
@@ -193,6 +197,11 @@ def run_ours(args, w):
     m = torch.tensor(w.m, dtype=torch.float32, device=dev)
     v = torch.tensor(w.v, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
+    graphs = args.workload == "batched"
+    tiles = None
+    if graphs:
+        tiles = P.autotune(k=w.k)
+        P.set_graphs(True)
 
     for _ in range(args.warmup):
         P.hessian_apply(m, v, ckpt=CKPT)
@@ -201,8 +210,9 @@ def run_ours(args, w):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES")
     gpu_index = vis.split(",")[local] if vis else str(local)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    P.profile(True)
-    P.profile_read()
+    if not graphs:            # per-kernel events inside the timed region (graphs replay without them)
+        P.profile(True)
+        P.profile_read()
     with ClockSampler(gpu_index) as clk:
         if world > 1:
             dist.barrier()
@@ -216,14 +226,24 @@ def run_ours(args, w):
         n1 = kernel_launches()
         if world > 1:
             dist.barrier()
-    prof = P.profile_read()
+    if graphs:                # one extra profiled apply (no graph) for the per-kernel times
+        P.profile(True)
+        c0 = kernel_launches()
+        P.hessian_apply(m, v, ckpt=CKPT)
+        torch.cuda.synchronize(dev)
+        n1 = n0 + (kernel_launches() - c0) * args.steps   # a graph replay launches the same kernels
+        prof = P.profile_read()
+        prof = {kk: (n * args.steps, t * args.steps) for kk, (n, t) in prof.items()}
+    else:
+        prof = P.profile_read()
     P.profile(False)
     ms = e0.elapsed_time(e1)
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     ms_max = float(t.item())
-    value = args.steps * world / (ms_max / 1e3)
+    calls_per_s = args.steps * world / (ms_max / 1e3)
+    value = calls_per_s * w.k                      # H v products per second (k per call)
 
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     mh = torch.tensor(w.m, dtype=torch.float32).pin_memory()
@@ -245,7 +265,7 @@ def run_ours(args, w):
     t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_val = world / float(t.item())
+    e2e_val = world * w.k / float(t.item())
 
     if rank == 0:
         pk, pk_kind = peaks()
@@ -277,7 +297,7 @@ def run_ours(args, w):
         if world == 1 and not args.no_cpu_baseline:
             threads = min(os.cpu_count() or 1, 8)
             g, sec, desc = oracle_sample(w, threads, 120)
-            cpu = {"value": g * 1e9 / updates_per_hv(w), "unit": UNIT, "cores": threads, "kind": "oracle",
+            cpu = {"value": g * 1e9 / updates_per_call(w) * w.k, "unit": UNIT, "cores": threads, "kind": "oracle",
                    "sample": desc, "seconds": sec, "gpt_updates_per_s": g * 1e9}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -285,7 +305,7 @@ def run_ours(args, w):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded layered/faulted velocity model; stands in for the paper's Marmousi)",
             "config": workload_config(w),
-            "gpt_updates_per_s": value * updates_per_hv(w),
+            "gpt_updates_per_s": calls_per_s * updates_per_call(w),
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_val, "unit": UNIT,
@@ -295,6 +315,9 @@ def run_ours(args, w):
             "clocks": clk.summary(),
             "kernels": kernels,
         }
+        if graphs:
+            line["config"]["graphs"] = "H v launch sequence replayed as a CUDA graph; per-kernel times from one extra profiled apply"
+            line["config"]["tiles"] = list(tiles)
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
@@ -309,12 +332,19 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--nt", type=int, default=None, help="override the step count (profiling runs)")
     ap.add_argument("--shots", type=int, default=None, help="override the shot count (profiling runs)")
-    ap.add_argument("--ckpt", type=int, default=CKPT, help="snapshots per shot (profiling runs)")
+    ap.add_argument("--ckpt", type=int, default=None, help="snapshots per shot (profiling runs)")
+    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
+                    help="paper: 384x1152, 32 shots, 3000 steps, 1 vector (default); batched: the 64x64 model "
+                         "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     from paper_2507_10804_gb300 import synth
-    CKPT = args.ckpt
-    w = synth.workload(2, nt=args.nt, ns=args.shots)
+    if args.workload == "batched":
+        CKPT = args.ckpt if args.ckpt is not None else -1
+        w = synth.workload(3, nt=args.nt, ns=args.shots)
+    else:
+        CKPT = args.ckpt if args.ckpt is not None else 30
+        w = synth.workload(2, nt=args.nt, ns=args.shots)
     if args.impl == "reference":
         run_reference(args, w)
     else:

@@ -197,6 +197,30 @@ int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float 
  * Synchronises the device, then clears the status. */
 int hv_status(hv_handle *h, int *device_status);
 
+/* Tile configurations.  The stencil kernels come in a small menu of tile
+ * shapes (TX x TZ points per CTA); the choice per kernel kind (cfg[0]:
+ * forward + Born step, cfg[1]: forward-only step, cfg[2]: adjoint step) does
+ * not change any result bit, only speed.
+ *  - hv_tile_menu: shape of menu entry `index` (HV_EINVAL past the end).
+ *  - hv_autotune: times every entry for the three kernels on this handle's
+ *    grid with k vectors, using `ws` (at least hv_workspace_size(HV_OP_HV, k,
+ *    ckpt = 1) bytes; contents overwritten) on `stream`, keeps the fastest
+ *    in the handle and writes the choice to chosen[3] and the per-launch
+ *    times to ms[menu * 3] (either may be NULL).  Synchronous.
+ *  - hv_set_tiles / hv_get_tiles: apply or read a choice (e.g. a cached one). */
+int hv_tile_menu(int index, int *TX, int *TZ);
+int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void *stream, int *chosen, float *ms);
+int hv_set_tiles(hv_handle *h, const int *cfg);
+int hv_get_tiles(const hv_handle *h, int *cfg);
+
+/* CUDA graphs.  When enabled (and profiling is off), the first
+ * hv_hessian_apply with a given workspace pointer, size, k, budget and tile
+ * choice records its whole launch sequence between model preparation and the
+ * final fold as a CUDA graph (captured on a private stream); later calls with
+ * the same key replay it with one launch.  The workspace contents are not
+ * part of the key: they are rewritten by every call. */
+int hv_set_graphs(hv_handle *h, int enable);
+
 /* Profiling.  While enabled on a handle, each kernel launch the handle makes
  * is bracketed by CUDA events on the launching stream.  hv_profile_read waits
  * for those events and returns, per kernel kind (HV_K_*), the number of

@@ -50,6 +50,11 @@ _SIGS = {
     "hv_hessian_apply_static": ([ctypes.POINTER(HvGrid), ctypes.POINTER(HvAcq), fp, fp, c_int, fp, c_int,
                                  c_void_p], c_int),
     "hv_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
+    "hv_tile_menu": ([c_int, ip, ip], c_int),
+    "hv_autotune": ([c_void_p, c_int, fp, c_size_t, c_void_p, ip, ctypes.POINTER(ctypes.c_float)], c_int),
+    "hv_set_tiles": ([c_void_p, ip], c_int),
+    "hv_get_tiles": ([c_void_p, ip], c_int),
+    "hv_set_graphs": ([c_void_p, c_int], c_int),
     "hv_profile": ([c_void_p, c_int], c_int),
     "hv_profile_read": ([c_void_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(c_double)], c_int),
     "hv_kernel_launches": ([], ctypes.c_longlong),

@@ -254,7 +254,8 @@ struct Exec {
             a.d_du = d_du;
         }
         a.d_u = d_u;
-        HV_RT(hvk::launch_fwd(h, rectiles_for(h, hvk::tiling_fwd(h)), maps, a, st));
+        const int cfg = born ? h->cfg[0] : h->cfg[1];
+        HV_RT(hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), maps, a, st));
         prev = cur;
         prev_i = cur_i;
         cur = next;
@@ -305,7 +306,7 @@ struct Exec {
         a.n = n;
         a.k = kk;
         a.G = L.G;
-        return hvk::launch_adj(h, rectiles_for(h, hvk::tiling_adj(h)), maps, a, st);
+        return hvk::launch_adj(h, h->cfg[2], rectiles_for(h, hvk::tiling(h, h->cfg[2])), maps, a, st);
     }
 
     // Zero the ghost bands of every field batch this call's kernels write:
@@ -355,6 +356,16 @@ const std::vector<hvi::Action> *schedule_for(hv_handle *h, int slots)
     return &r.first->second;
 }
 
+int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
+                     const Layout &L, cudaStream_t st);
+
+std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg)
+{
+    char buf[160];
+    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2]);
+    return buf;
+}
+
 // The shared driver of migrate / misfit_grad / hessian_apply.
 //   kind 0: migrate   r = user data,                         scale h^2
 //   kind 1: gradient  r = f(m) - d_obs (computed),           scale h^2 / sigma^2
@@ -366,16 +377,58 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     Layout L;
     HV_RT(check_common(h, ws, ws_bytes, op, kind == 2 ? k : 1, ckpt, L));
     const int kk = (kind == 2) ? k : 1;
+    const bool born = (kind == 2);
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_prep(h, m, born ? in : nullptr, born ? kk : 0, reinterpret_cast<float *>((char *)ws + L.C),
+                               born ? reinterpret_cast<float *>((char *)ws + L.b) : nullptr, st));
+    }
+    // Everything between the model preparation and the final fold touches only
+    // the workspace and the handle, so for H v it can be captured once as a
+    // CUDA graph and replayed (hv_set_graphs).
+    const bool graph = born && h->graphs_on && !h->prof_on;
+    if (graph) {
+        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg);
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            cudaStream_t cs = h->capture_stream;
+            HV_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int rc = run_adjoint_body(h, kind, in, kk, phi, ckpt, ws, L, cs);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cs, &g);
+            if (rc != HV_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            it = h->graphs.emplace(key, ex).first;
+        }
+        HV_CK(cudaGraphLaunch(it->second, st));
+    } else {
+        HV_RT(run_adjoint_body(h, kind, in, kk, phi, ckpt, ws, L, st));
+    }
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>((char *)ws + L.img), L.G, kk, out32, out64, st));
+    }
+    return HV_OK;
+}
+
+// The part of run_adjoint between preparation and fold (all on `st`).
+int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
+                     const Layout &L, cudaStream_t st)
+{
+    (void)ckpt;
     Exec E;
     HV_RT(E.init(h, st, L, ws, kk));
     const bool born = (kind == 2);
     HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
     HV_RT(E.zero_ghosts(true));
     HV_CK(cudaMemsetAsync((char *)ws + L.D, 0, (size_t)2 * kk * L.fb, st));
-    {
-        ProfScope ps(h, st, HV_K_OTHER);
-        HV_RT(hvk::launch_prep(h, m, born ? in : nullptr, born ? kk : 0, E.C, born ? E.b : nullptr, st));
-    }
     float *dd = (kind != 0) ? reinterpret_cast<float *>((char *)ws + L.dd) : nullptr;
 
     const std::vector<hvi::Action> *sched = L.history ? nullptr : schedule_for(h, L.slots);
@@ -427,10 +480,6 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
             default: return hvi::fail(HV_EINVAL, "internal: forward step inside the reversal");
             }
         }
-    }
-    {
-        ProfScope ps(h, st, HV_K_OTHER);
-        HV_RT(hvk::launch_finalize(h, m, E.img, L.G, kk, out32, out64, st));
     }
     return HV_OK;
 }
@@ -515,8 +564,11 @@ extern "C" int hv_create(const hv_grid *g, const hv_acq *a, hv_handle **out)
     if (rc != HV_OK) return cleanup_fail(rc);
     if ((e = cudaDeviceSynchronize()) != cudaSuccess)
         return cleanup_fail(hvi::fail(HV_ECUDA, "set-up kernels: %s", cudaGetErrorString(e)));
-    if ((rc = build_rectiles(h, hvk::tiling_fwd(h))) != HV_OK) return cleanup_fail(rc);
-    if ((rc = build_rectiles(h, hvk::tiling_adj(h))) != HV_OK) return cleanup_fail(rc);
+    for (int c = 0; c < hvk::tile_menu_size(); ++c)
+        if ((rc = build_rectiles(h, hvk::tiling(h, c))) != HV_OK) return cleanup_fail(rc);
+    if ((rc = hvk::prepare_kernels(h)) != HV_OK) return cleanup_fail(rc);
+    if ((e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return cleanup_fail(hvi::fail(HV_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e)));
     *out = h;
     return HV_OK;
 }
@@ -531,6 +583,8 @@ extern "C" int hv_destroy(hv_handle *h)
     cudaFree(h->src_zx);
     cudaFree(h->rec_zx);
     cudaFree(h->status);
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.second);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (auto &r : h->prof_rec) {
         cudaEventDestroy(r.second.first);
         cudaEventDestroy(r.second.second);
@@ -768,7 +822,7 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
         h->h_rec_zx[2 * i] = a->rec_iz[i] + h->nb;
         h->h_rec_zx[2 * i + 1] = a->rec_ix[i] + h->nb;
     }
-    const hvi::Tiling tf = hvk::tiling_fwd(h), ta = hvk::tiling_adj(h);
+    const hvi::Tiling tf = hvk::tiling(h, 0), ta = hvk::tiling(h, 0);
     std::vector<int> off_f, rec_f, pos_f, off_a, rec_a, pos_a;
     static_rectile_tables(h, tf, off_f, rec_f, pos_f);
     const bool same_tiling = (tf.TX == ta.TX && tf.TZ == ta.TZ);
@@ -823,6 +877,7 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
     h->rectiles[(long long)rf.TX * 65536 + rf.TZ] = rf;
     if (!same_tiling) h->rectiles[(long long)ra.TX * 65536 + ra.TZ] = ra;
     HV_RT(hvk::launch_setup(h, st));
+    HV_RT(hvk::prepare_kernels(h));
     int rc = run_adjoint(h, 2, m, v, k, Hv, nullptr, nullptr, ckpt, ws, HV_STATIC_SCRATCH_BYTES - tables, st);
     // The pageable-host copies above are staged before cudaMemcpyAsync returns, so the
     // host tables may go out of scope now; the device pointers are not freed (they
@@ -840,5 +895,101 @@ extern "C" int hv_status(hv_handle *h, int *device_status)
     HV_CK(cudaDeviceSynchronize());
     HV_CK(cudaMemcpy(device_status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     HV_CK(cudaMemset(h->status, 0, sizeof(int)));
+    return HV_OK;
+}
+
+extern "C" int hv_tile_menu(int index, int *TX, int *TZ)
+{
+    if (index < 0 || index >= hvk::tile_menu_size()) return hvi::fail(HV_EINVAL, "tile configuration %d not in the menu", index);
+    hv_handle dummy;
+    dummy.NX = dummy.NZ = 1;
+    hvi::Tiling t = hvk::tiling(&dummy, index);
+    if (TX) *TX = t.TX;
+    if (TZ) *TZ = t.TZ;
+    return HV_OK;
+}
+
+extern "C" int hv_set_tiles(hv_handle *h, const int *cfg)
+{
+    if (!h || !cfg) return hvi::fail(HV_EINVAL, "null handle or configuration");
+    for (int i = 0; i < 3; ++i)
+        if (cfg[i] < 0 || cfg[i] >= hvk::tile_menu_size())
+            return hvi::fail(HV_EINVAL, "tile configuration %d not in the menu", cfg[i]);
+    for (int i = 0; i < 3; ++i) h->cfg[i] = cfg[i];
+    return HV_OK;
+}
+
+extern "C" int hv_get_tiles(const hv_handle *h, int *cfg)
+{
+    if (!h || !cfg) return hvi::fail(HV_EINVAL, "null handle or output");
+    for (int i = 0; i < 3; ++i) cfg[i] = h->cfg[i];
+    return HV_OK;
+}
+
+extern "C" int hv_set_graphs(hv_handle *h, int enable)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    h->graphs_on = enable != 0;
+    return HV_OK;
+}
+
+// Times every tile configuration of the three stencil kernels on this
+// handle's grid with k vectors (on zeroed fields: the kernels have no
+// data-dependent work) and keeps the fastest per kernel kind.
+extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void *stream, int *chosen, float *ms)
+{
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_HV, k, 1, L));
+    cudaStream_t st = (cudaStream_t)stream;
+    HV_CK(cudaMemsetAsync(ws, 0, L.total, st));
+    Exec E;
+    HV_RT(E.init(h, st, L, ws, k));
+    const float *dd = reinterpret_cast<const float *>((char *)ws + L.dd);
+    const int nmenu = hvk::tile_menu_size();
+    cudaEvent_t e0, e1;
+    HV_CK(cudaEventCreate(&e0));
+    HV_CK(cudaEventCreate(&e1));
+    constexpr int kReps = 6;
+    float best[3] = {1e30f, 1e30f, 1e30f};
+    int arg[3] = {0, 0, 0};
+    int rc = HV_OK;
+    for (int c = 0; c < nmenu && rc == HV_OK; ++c) {
+        const hvi::RecTiles &rt = rectiles_for(h, hvk::tiling(h, c));
+        for (int kind = 0; kind < 3 && rc == HV_OK; ++kind) {
+            for (int rep = 0; rep <= kReps && rc == HV_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, st);
+                if (kind == 2) {
+                    hvk::AdjLaunch a{};
+                    a.u = E.zero; a.lam1 = E.Dbuf(1); a.lam_io = E.Dbuf(0); a.C = E.C; a.r = dd;
+                    a.r_per_vector = 1; a.rscale = 1.0f; a.img = E.img; a.n = 0; a.k = k; a.G = L.G;
+                    rc = hvk::launch_adj(h, c, rt, E.maps, a, st);
+                } else {
+                    hvk::FwdLaunch a{};
+                    a.u_cur = E.zero; a.u_prev = E.zero; a.u_next = E.pool[0]; a.C = E.C; a.n = 0;
+                    if (kind == 0) {
+                        a.b = E.b; a.k = k; a.du_cur = E.Dbuf(0); a.du_io = E.Dbuf(1);
+                    }
+                    rc = hvk::launch_fwd(h, c, rt, E.maps, a, st);
+                }
+            }
+            cudaEventRecord(e1, st);
+            cudaError_t e = cudaEventSynchronize(e1);
+            if (e != cudaSuccess && rc == HV_OK) rc = hvi::fail(HV_ECUDA, "autotune: %s", cudaGetErrorString(e));
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            t /= kReps;
+            if (ms) ms[c * 3 + kind] = t;
+            if (t < best[kind]) {
+                best[kind] = t;
+                arg[kind] = c;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != HV_OK) return rc;
+    for (int i = 0; i < 3; ++i) h->cfg[i] = arg[i];
+    if (chosen)
+        for (int i = 0; i < 3; ++i) chosen[i] = arg[i];
     return HV_OK;
 }

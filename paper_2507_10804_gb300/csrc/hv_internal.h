@@ -75,6 +75,12 @@ struct hv_handle {
     std::mutex mu;
     std::map<long long, hvi::RecTiles> rectiles;                 // keyed by TX * 65536 + TZ
     std::map<int, std::vector<hvi::Action>> schedules;           // keyed by slots
+    // tile configuration per kernel kind (HV_K_FWD, HV_K_ADVANCE, HV_K_ADJ); see hv_autotune
+    int cfg[3] = {0, 0, 0};
+    // CUDA graphs of the H v launch sequence (hv_set_graphs), keyed by workspace and shape
+    bool graphs_on = false;
+    cudaStream_t capture_stream = nullptr;
+    std::map<std::string, cudaGraphExec_t> graphs;
     // profiling (hv_profile)
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -83,16 +89,18 @@ struct hv_handle {
 
 namespace hvk {
 
-// Kernel configurations (see hv_kernels.cu).
-hvi::Tiling tiling_fwd(const hv_handle *h);
-hvi::Tiling tiling_adj(const hv_handle *h);
+// Tile configurations (hv_stencil.cu): the menu size and the tiling of one entry.
+int tile_menu_size();
+hvi::Tiling tiling(const hv_handle *h, int cfg);
+int prepare_kernels(const hv_handle *h);
 
 // Tensor maps of one call's workspace, viewed as an array of fields
 // (x, z, field index): `halo` copies a tile with its 4-cell halo, `pt` the
 // tile's own points.  Opaque CUtensorMap bytes (128 each).
+constexpr int kMaxTileMenu = 4;
 struct TmaMaps {
-    alignas(64) unsigned char halo[128];
-    alignas(64) unsigned char pt[128];
+    alignas(64) unsigned char halo[kMaxTileMenu][128];   // per tile configuration
+    alignas(64) unsigned char pt[kMaxTileMenu][128];
     void *ws = nullptr;
     long long nfields = 0;
 };
@@ -109,7 +117,7 @@ struct FwdLaunch {
     float *d_du;                   // [k][ns][nt][nr] samples of du^{n+1} or nullptr
     int n, k;
 };
-int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
+int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
                cudaStream_t st);
 
 struct AdjLaunch {
@@ -123,7 +131,7 @@ struct AdjLaunch {
     double *img;                   // [G][k][fsize] partial images
     int n, k, G;
 };
-int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
+int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
                cudaStream_t st);
 int adj_groups(const hv_handle *h);
 

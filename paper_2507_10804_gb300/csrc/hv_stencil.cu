@@ -43,6 +43,7 @@ constexpr float LC3 = (float)(8.0 / 315.0);
 constexpr float LC4 = (float)(-1.0 / 560.0);
 
 constexpr int kShotsPerGroup = 8;
+constexpr int kTileMenu = 4;       // number of tile configurations (with_cfg)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 template <int BX_, int BZ_, int RZ_>
@@ -52,10 +53,16 @@ struct Cfg {
     static constexpr int TX = 4 * BX, TZ = RZ * BZ;
     static constexpr int W = TX + 2 * GH, H = TZ + 2 * GH;
     static constexpr int W4 = W / 4;
-    static constexpr int HALO = W * H * 4;   // bytes of a halo tile
+    static constexpr int HALO = W * H * 4;   // bytes of a halo tile (one bulk copy)
     static constexpr int PT = TX * TZ * 4;   // bytes of a point tile
+    static constexpr int HALOP = (HALO + 127) / 128 * 128;   // shared-memory slots, 128-byte aligned
+    static constexpr int PTP = (PT + 127) / 128 * 128;
 };
-using CfgS = Cfg<16, 16, 2>;   // 64 x 32 tiles, 256 threads, 4 x 2 points per thread
+// The tile menu (the autotuner picks one per kernel kind and problem):
+using Cfg64x32 = Cfg<16, 16, 2>;   // 256 threads, 4 x 2 points each
+using Cfg32x32 = Cfg<8, 16, 2>;    // 128 threads
+using Cfg64x16 = Cfg<16, 8, 2>;    // 128 threads
+using Cfg52x26 = Cfg<13, 13, 2>;   // 169 threads; tiles a 104-point padded axis exactly
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -151,7 +158,7 @@ __device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, 
             const float cz = v[4 + c];
             auto comp = [](const float4 &q, int cc) { return cc == 0 ? q.x : (cc == 1 ? q.y : (cc == 2 ? q.z : q.w)); };
             const float d1 = ((v[3 + c] - cz) + (v[5 + c] - cz)) + ((comp(col[r + 3], c) - cz) + (comp(col[r + 5], c) - cz));
-            float acc = LC4 * ((v[c] + v[8 + c]) + (comp(col[r], c) + comp(col[r + 8], c)));
+            float acc = __fmul_rn(LC4, (v[c] + v[8 + c]) + (comp(col[r], c) + comp(col[r + 8], c)));
             acc = fmaf(LC3, (v[1 + c] + v[7 + c]) + (comp(col[r + 1], c) + comp(col[r + 7], c)), acc);
             acc = fmaf(LC2, (v[2 + c] + v[6 + c]) + (comp(col[r + 2], c) + comp(col[r + 6], c)), acc);
             acc = fmaf(LCR, cz, acc);
@@ -222,8 +229,10 @@ struct FwdParams {
 
 template <class C, bool BORN>
 struct FwdSmem {
-    static constexpr int STAGE = C::HALO + C::PT + (BORN ? C::HALO + C::PT : 0);
-    static constexpr int COEF = C::PT * (BORN ? 2 : 1);
+    static constexpr int STAGE = C::HALOP + C::PTP + (BORN ? C::HALOP + C::PTP : 0);
+    static constexpr int STAGE_TX = C::HALO + C::PT + (BORN ? C::HALO + C::PT : 0);   // bytes each stage receives
+    static constexpr int COEF = C::PTP * (BORN ? 2 : 1);
+    static constexpr int COEF_TX = C::PT * (BORN ? 2 : 1);
     static constexpr int BYTES = 2 * STAGE + COEF + 64 + 128;   // + barriers + shot tables
 };
 
@@ -265,11 +274,13 @@ __device__ __forceinline__ void add_source(float (&Q)[C::RZ][4], int zrow0, int 
 }
 
 // o = (2 w - (1 - a) w_prev + C q) / (1 + a); a = 0 (SP false) off the sponge.
+// Every multiply-add is explicit (fmaf / __fmul_rn): the compiler has no
+// contraction freedom, so each tile shape computes bitwise the same values.
 template <bool SP>
-__device__ __forceinline__ float leapfrog(float w, float wprev, float cq, float inv, float oma)
+__device__ __forceinline__ float leapfrog(float w, float wprev, float cc, float q, float inv, float oma)
 {
-    if constexpr (SP) return inv * (2.0f * w - oma * wprev + cq);
-    else return fmaf(2.0f, w, cq - wprev);
+    if constexpr (SP) return __fmul_rn(inv, fmaf(cc, q, fmaf(-oma, wprev, w + w)));
+    else return fmaf(cc, q, fmaf(2.0f, w, -wprev));
 }
 
 // One forward time step.  grid = (ntiles, k or 1, shot groups).  Vector j = 0
@@ -280,7 +291,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     using S = FwdSmem<C, BORN>;
     extern __shared__ __align__(128) unsigned char smem[];
     float *sC = reinterpret_cast<float *>(smem + 2 * S::STAGE);
-    float *sB = sC + C::TX * C::TZ;
+    float *sB = sC + C::PTP / 4;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + S::COEF);
     ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + 2 * S::STAGE + S::COEF + 64);
 
@@ -295,13 +306,13 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     auto issue = [&](int i) {
         const int st = i & 1, s = s0 + i;
         unsigned char *base = smem + st * S::STAGE;
-        mbar_expect_tx(&bars[st], S::STAGE);
+        mbar_expect_tx(&bars[st], S::STAGE_TX);
         tma_load(base, &p.map_halo, x0, z0, p.f_ucur + s, &bars[st]);
-        tma_load(base + C::HALO, &p.map_pt, x0 + GH, z0 + GH, p.f_uprev + s, &bars[st]);
+        tma_load(base + C::HALOP, &p.map_pt, x0 + GH, z0 + GH, p.f_uprev + s, &bars[st]);
         if constexpr (BORN) {
             const int fo = j * p.ns + s;
-            tma_load(base + C::HALO + C::PT, &p.map_halo, x0, z0, p.f_du + fo, &bars[st]);
-            tma_load(base + 2 * C::HALO + C::PT, &p.map_pt, x0 + GH, z0 + GH, p.f_dio + fo, &bars[st]);
+            tma_load(base + C::HALOP + C::PTP, &p.map_halo, x0, z0, p.f_du + fo, &bars[st]);
+            tma_load(base + 2 * C::HALOP + C::PTP, &p.map_pt, x0 + GH, z0 + GH, p.f_dio + fo, &bars[st]);
         }
     };
 
@@ -314,7 +325,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&bars[2], S::COEF);
+        mbar_expect_tx(&bars[2], S::COEF_TX);
         tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[2]);
         if constexpr (BORN) tma_load(sB, &p.map_pt, x0 + GH, z0 + GH, p.f_b + j, &bars[2]);
         issue(0);
@@ -345,7 +356,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
             }
             const unsigned char *base = smem + st * S::STAGE;
             const float *sU = reinterpret_cast<const float *>(base);
-            const float *sUp = reinterpret_cast<const float *>(base + C::HALO);
+            const float *sUp = reinterpret_cast<const float *>(base + C::HALOP);
 
             float Q[C::RZ][4], uc[C::RZ][4];
             lap_block<C>(sU, tx, tz, Q, uc);
@@ -362,7 +373,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                     if constexpr (SP) sponge_row(true, p.az, z, p.g.NZ, axv, inv, oma);
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
-                        o[c] = leapfrog<SP>(uc[r][c], up[c], cc[c] * Q[r][c], SP ? inv[c] : 1.f, SP ? oma[c] : 1.f);
+                        o[c] = leapfrog<SP>(uc[r][c], up[c], cc[c], Q[r][c], SP ? inv[c] : 1.f, SP ? oma[c] : 1.f);
                     if (z < p.g.NZ && xb < p.g.NX) st4(un + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
                 }
                 if (p.d_u && rb < re) {
@@ -372,8 +383,8 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                 }
             }
             if constexpr (BORN) {
-                const float *sD = reinterpret_cast<const float *>(base + C::HALO + C::PT);
-                const float *sDp = reinterpret_cast<const float *>(base + 2 * C::HALO + C::PT);
+                const float *sD = reinterpret_cast<const float *>(base + C::HALOP + C::PTP);
+                const float *sDp = reinterpret_cast<const float *>(base + 2 * C::HALOP + C::PTP);
                 float Ld[C::RZ][4], dc[C::RZ][4];
                 lap_block<C>(sD, tx, tz, Ld, dc);
                 const int fo = j * p.ns + s;
@@ -388,7 +399,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                     if constexpr (SP) sponge_row(true, p.az, z, p.g.NZ, axv, inv, oma);
 #pragma unroll
                     for (int c = 0; c < 4; ++c)
-                        o[c] = leapfrog<SP>(dc[r][c], dp[c], cc[c] * fmaf(bb[c], Q[r][c], Ld[r][c]), SP ? inv[c] : 1.f,
+                        o[c] = leapfrog<SP>(dc[r][c], dp[c], cc[c], fmaf(bb[c], Q[r][c], Ld[r][c]), SP ? inv[c] : 1.f,
                                             SP ? oma[c] : 1.f);
                     if (z < p.g.NZ && xb < p.g.NX) st4(dn + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
                 }
@@ -423,8 +434,9 @@ struct AdjParams {
 
 template <class C>
 struct AdjSmem {
-    static constexpr int STAGE = 2 * C::HALO + C::PT;
-    static constexpr int BYTES = 2 * STAGE + C::PT /* C */ + C::PT /* sources */ + 64 + 128;
+    static constexpr int STAGE = 2 * C::HALOP + C::PTP;
+    static constexpr int STAGE_TX = 2 * C::HALO + C::PT;
+    static constexpr int BYTES = 2 * STAGE + C::PTP /* C */ + C::PTP /* sources */ + 64 + 128;
 };
 
 // One adjoint time step with zero-lag imaging.  grid = (ntiles, k, shot
@@ -436,9 +448,9 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     using S = AdjSmem<C>;
     extern __shared__ __align__(128) unsigned char smem[];
     float *sC = reinterpret_cast<float *>(smem + 2 * S::STAGE);
-    float *ssrc = sC + C::TX * C::TZ;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + 2 * C::PT);
-    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + 2 * S::STAGE + 2 * C::PT + 64);
+    float *ssrc = sC + C::PTP / 4;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + 2 * C::PTP);
+    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + 2 * S::STAGE + 2 * C::PTP + 64);
 
     const int tile = blockIdx.x, j = blockIdx.y, grp = blockIdx.z;
     const int tzi = tile / p.g.ntx, txi = tile - tzi * p.g.ntx;
@@ -451,10 +463,10 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
         const int st = i & 1, s = s0 + i;
         unsigned char *base = smem + st * S::STAGE;
         const int fo = j * p.ns + s;
-        mbar_expect_tx(&bars[st], S::STAGE);
+        mbar_expect_tx(&bars[st], S::STAGE_TX);
         tma_load(base, &p.map_halo, x0, z0, p.f_u + s, &bars[st]);
-        tma_load(base + C::HALO, &p.map_halo, x0, z0, p.f_lam1 + fo, &bars[st]);
-        tma_load(base + 2 * C::HALO, &p.map_pt, x0 + GH, z0 + GH, p.f_lamio + fo, &bars[st]);
+        tma_load(base + C::HALOP, &p.map_halo, x0, z0, p.f_lam1 + fo, &bars[st]);
+        tma_load(base + 2 * C::HALOP, &p.map_pt, x0 + GH, z0 + GH, p.f_lamio + fo, &bars[st]);
     };
 
     if (threadIdx.x == 0) {
@@ -514,8 +526,8 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
             }
             const unsigned char *base = smem + st * S::STAGE;
             const float *sU = reinterpret_cast<const float *>(base);
-            const float *sL1 = reinterpret_cast<const float *>(base + C::HALO);
-            const float *sL2 = reinterpret_cast<const float *>(base + 2 * C::HALO);
+            const float *sL1 = reinterpret_cast<const float *>(base + C::HALOP);
+            const float *sL2 = reinterpret_cast<const float *>(base + 2 * C::HALOP);
             float Qu[C::RZ][4], ucen[C::RZ][4], Ll[C::RZ][4], lc[C::RZ][4];
             lap_block<C>(sU, tx, tz, Qu, ucen);
             add_source<C>(Qu, zrow0, xb, tab.sz[i], tab.sx[i], wav);
@@ -536,7 +548,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
                 if constexpr (SP) sponge_row(true, p.az, z, p.g.NZ, axv, inv, oma);
 #pragma unroll
                 for (int c = 0; c < 4; ++c) {
-                    o[c] = leapfrog<SP>(lc[r][c], l2[c], cc[c] * Ll[r][c], SP ? inv[c] : 1.f, SP ? oma[c] : 1.f);
+                    o[c] = leapfrog<SP>(lc[r][c], l2[c], cc[c], Ll[r][c], SP ? inv[c] : 1.f, SP ? oma[c] : 1.f);
                     acc[r][c] = fmaf(o[c], Qu[r][c], acc[r][c]);
                 }
                 if (z < p.g.NZ && xb < p.g.NX) st4(ln + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
@@ -575,7 +587,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
-int encode(CUtensorMap *map, const hv_handle *h, void *ws, long long nfields, int boxx, int boxz)
+int encode(void *map, const hv_handle *h, void *ws, long long nfields, int boxx, int boxz)
 {
     auto fn = encode_fn();
     if (!fn) return hvi::fail(HV_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
@@ -583,8 +595,9 @@ int encode(CUtensorMap *map, const hv_handle *h, void *ws, long long nfields, in
     cuuint64_t strides[2] = {(cuuint64_t)h->P * 4, (cuuint64_t)h->fsize * 4};
     cuuint32_t box[3] = {(cuuint32_t)boxx, (cuuint32_t)boxz, 1};
     cuuint32_t es[3] = {1, 1, 1};
-    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = fn(reinterpret_cast<CUtensorMap *>(map), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ws, dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return hvi::fail(HV_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return HV_OK;
 }
@@ -601,16 +614,16 @@ int field_index(const void *ws, const void *p, size_t fbytes, int *out)
     return HV_OK;
 }
 
-template <class C>
-hvi::Tiling make_tiling(const hv_handle *h)
+// Calls f with a value of the tile configuration `id` (see kTileMenu).
+template <class F>
+auto with_cfg(int id, F &&f)
 {
-    hvi::Tiling t;
-    t.TX = C::TX;
-    t.TZ = C::TZ;
-    t.ntx = (h->NX + C::TX - 1) / C::TX;
-    t.ntz = (h->NZ + C::TZ - 1) / C::TZ;
-    t.ntiles = t.ntx * t.ntz;
-    return t;
+    switch (id) {
+    case 1: return f(Cfg32x32{});
+    case 2: return f(Cfg64x16{});
+    case 3: return f(Cfg52x26{});
+    default: return f(Cfg64x32{});
+    }
 }
 
 template <class K>
@@ -621,13 +634,13 @@ int set_smem(K kern, int bytes)
     return HV_OK;
 }
 
-// Raise a kernel's dynamic shared memory limit once per (kernel slot, device).
+// Raise a kernel's dynamic shared memory limit once per (kernel, device).
 template <class K>
 int ensure_smem(int slot, int dev, K kern, int bytes)
 {
     static std::mutex mu;
-    static bool done[8][64] = {};
-    if (dev < 0 || dev >= 64) return hvi::fail(HV_EINVAL, "device ordinal %d out of range", dev);
+    static bool done[64][64] = {};
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 64) return hvi::fail(HV_EINVAL, "internal: kernel slot %d/%d", slot, dev);
     std::lock_guard<std::mutex> g(mu);
     if (done[slot][dev]) return HV_OK;
     HV_RT_INTERNAL(set_smem(kern, bytes));
@@ -650,85 +663,130 @@ Geo geo(const hv_handle *h, const hvi::Tiling &t)
 
 }  // namespace
 
-hvi::Tiling tiling_fwd(const hv_handle *h) { return make_tiling<CfgS>(h); }
-hvi::Tiling tiling_adj(const hv_handle *h) { return make_tiling<CfgS>(h); }
+int tile_menu_size() { return kTileMenu; }
+
+hvi::Tiling tiling(const hv_handle *h, int cfg)
+{
+    return with_cfg(cfg, [&](auto c) {
+        using C = decltype(c);
+        hvi::Tiling t;
+        t.TX = C::TX;
+        t.TZ = C::TZ;
+        t.ntx = (h->NX + C::TX - 1) / C::TX;
+        t.ntz = (h->NZ + C::TZ - 1) / C::TZ;
+        t.ntiles = t.ntx * t.ntz;
+        return t;
+    });
+}
 
 // Shot groups of the adjoint kernel: groups of up to 8 shots, summed in shot
 // order inside a CTA and in group order at the end.  The grouping depends
-// only on the shot count (never on k), so a vector's result is bitwise the
-// same whether it is applied alone or in a batch.
+// only on the shot count (never on k or the tile shape), so a vector's result
+// is bitwise the same whether it is applied alone or in a batch.
 int adj_groups(const hv_handle *h) { return (h->ns + kShotsPerGroup - 1) / kShotsPerGroup; }
+
+// Raise the shared-memory limits of every stencil kernel on the handle's
+// device (done at set-up so that no attribute call happens during capture).
+int prepare_kernels(const hv_handle *h)
+{
+    for (int id = 0; id < kTileMenu; ++id) {
+        int rc = with_cfg(id, [&](auto c) -> int {
+            using C = decltype(c);
+            HV_RT_INTERNAL(ensure_smem(0 * kTileMenu + id, h->device, k_fwd<C, true>, FwdSmem<C, true>::BYTES));
+            HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + id, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
+            HV_RT_INTERNAL(ensure_smem(2 * kTileMenu + id, h->device, k_adj<C>, AdjSmem<C>::BYTES));
+            return HV_OK;
+        });
+        if (rc != HV_OK) return rc;
+    }
+    return HV_OK;
+}
 
 int make_maps(const hv_handle *h, void *ws, long long nfields, TmaMaps *m)
 {
-    HV_RT_INTERNAL(encode(reinterpret_cast<CUtensorMap *>(m->halo), h, ws, nfields, CfgS::W, CfgS::H));
-    HV_RT_INTERNAL(encode(reinterpret_cast<CUtensorMap *>(m->pt), h, ws, nfields, CfgS::TX, CfgS::TZ));
+    for (int id = 0; id < kTileMenu; ++id) {
+        int rc = with_cfg(id, [&](auto c) {
+            using C = decltype(c);
+            HV_RT_INTERNAL(encode(m->halo[id], h, ws, nfields, C::W, C::H));
+            HV_RT_INTERNAL(encode(m->pt[id], h, ws, nfields, C::TX, C::TZ));
+            return (int)HV_OK;
+        });
+        if (rc != HV_OK) return rc;
+    }
     m->ws = ws;
     m->nfields = nfields;
     return HV_OK;
 }
 
-int launch_fwd(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a, cudaStream_t st)
+int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
+               cudaStream_t st)
 {
-    const hvi::Tiling t = tiling_fwd(h);
-    const size_t fbytes = h->fsize * sizeof(float);
-    FwdParams p;
-    memcpy(&p.map_halo, maps.halo, sizeof(CUtensorMap));
-    memcpy(&p.map_pt, maps.pt, sizeof(CUtensorMap));
-    p.ws = reinterpret_cast<float *>(maps.ws);
-    HV_RT_INTERNAL(field_index(maps.ws, a.u_cur, fbytes, &p.f_ucur));
-    HV_RT_INTERNAL(field_index(maps.ws, a.u_prev, fbytes, &p.f_uprev));
-    HV_RT_INTERNAL(field_index(maps.ws, a.u_next, fbytes, &p.f_unext));
-    HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
-    const bool born = a.b != nullptr && a.k > 0;
-    HV_RT_INTERNAL(field_index(maps.ws, born ? a.b : nullptr, fbytes, &p.f_b));
-    HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_cur : nullptr, fbytes, &p.f_du));
-    HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_io : nullptr, fbytes, &p.f_dio));
-    p.d_u = a.d_u;
-    p.d_du = born ? a.d_du : nullptr;
-    p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
-    p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
-    p.status = h->status;
-    p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : 1;
-    p.spg = kShotsPerGroup < h->ns ? kShotsPerGroup : h->ns;
-    p.g = geo(h, t);
-    dim3 grid(t.ntiles, p.k, (h->ns + p.spg - 1) / p.spg);
-    if (born) {
-        HV_RT_INTERNAL(ensure_smem(0, h->device, k_fwd<CfgS, true>, FwdSmem<CfgS, true>::BYTES));
-        k_fwd<CfgS, true><<<grid, CfgS::NT, FwdSmem<CfgS, true>::BYTES, st>>>(p);
-    } else {
-        HV_RT_INTERNAL(ensure_smem(1, h->device, k_fwd<CfgS, false>, FwdSmem<CfgS, false>::BYTES));
-        k_fwd<CfgS, false><<<grid, CfgS::NT, FwdSmem<CfgS, false>::BYTES, st>>>(p);
-    }
-    return launched("k_fwd launch");
+    return with_cfg(cfg, [&](auto c) -> int {
+        using C = decltype(c);
+        const hvi::Tiling t = tiling(h, cfg);
+        const size_t fbytes = h->fsize * sizeof(float);
+        FwdParams p;
+        memcpy(&p.map_halo, maps.halo[cfg], sizeof(CUtensorMap));
+        memcpy(&p.map_pt, maps.pt[cfg], sizeof(CUtensorMap));
+        p.ws = reinterpret_cast<float *>(maps.ws);
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_cur, fbytes, &p.f_ucur));
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_prev, fbytes, &p.f_uprev));
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_next, fbytes, &p.f_unext));
+        HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
+        const bool born = a.b != nullptr && a.k > 0;
+        HV_RT_INTERNAL(field_index(maps.ws, born ? a.b : nullptr, fbytes, &p.f_b));
+        HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_cur : nullptr, fbytes, &p.f_du));
+        HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_io : nullptr, fbytes, &p.f_dio));
+        p.d_u = a.d_u;
+        p.d_du = born ? a.d_du : nullptr;
+        p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
+        p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
+        p.status = h->status;
+        p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : 1;
+        p.spg = kShotsPerGroup < h->ns ? kShotsPerGroup : h->ns;
+        p.g = geo(h, t);
+        dim3 grid(t.ntiles, p.k, (h->ns + p.spg - 1) / p.spg);
+        if (born) {
+            HV_RT_INTERNAL(ensure_smem(0 * kTileMenu + cfg, h->device, k_fwd<C, true>, FwdSmem<C, true>::BYTES));
+            k_fwd<C, true><<<grid, C::NT, FwdSmem<C, true>::BYTES, st>>>(p);
+        } else {
+            HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + cfg, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
+            k_fwd<C, false><<<grid, C::NT, FwdSmem<C, false>::BYTES, st>>>(p);
+        }
+        return launched("k_fwd launch");
+    });
 }
 
-int launch_adj(const hv_handle *h, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a, cudaStream_t st)
+int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
+               cudaStream_t st)
 {
-    const hvi::Tiling t = tiling_adj(h);
-    const size_t fbytes = h->fsize * sizeof(float);
-    AdjParams p;
-    memcpy(&p.map_halo, maps.halo, sizeof(CUtensorMap));
-    memcpy(&p.map_pt, maps.pt, sizeof(CUtensorMap));
-    p.ws = reinterpret_cast<float *>(maps.ws);
-    HV_RT_INTERNAL(field_index(maps.ws, a.u, fbytes, &p.f_u));
-    HV_RT_INTERNAL(field_index(maps.ws, a.lam1, fbytes, &p.f_lam1));
-    HV_RT_INTERNAL(field_index(maps.ws, a.lam_io, fbytes, &p.f_lamio));
-    HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
-    p.r = a.r;
-    p.r_vstride = a.r_per_vector ? (unsigned long long)h->ns * h->nt * h->nr : 0ull;
-    p.rscale = a.rscale;
-    p.img = a.img;
-    p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
-    p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
-    p.status = h->status;
-    p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
-    p.spg = (h->ns + a.G - 1) / a.G;
-    p.g = geo(h, t);
-    HV_RT_INTERNAL(ensure_smem(2, h->device, k_adj<CfgS>, AdjSmem<CfgS>::BYTES));
-    dim3 grid(t.ntiles, a.k, a.G);
-    k_adj<CfgS><<<grid, CfgS::NT, AdjSmem<CfgS>::BYTES, st>>>(p);
-    return launched("k_adj launch");
+    return with_cfg(cfg, [&](auto c) -> int {
+        using C = decltype(c);
+        const hvi::Tiling t = tiling(h, cfg);
+        const size_t fbytes = h->fsize * sizeof(float);
+        AdjParams p;
+        memcpy(&p.map_halo, maps.halo[cfg], sizeof(CUtensorMap));
+        memcpy(&p.map_pt, maps.pt[cfg], sizeof(CUtensorMap));
+        p.ws = reinterpret_cast<float *>(maps.ws);
+        HV_RT_INTERNAL(field_index(maps.ws, a.u, fbytes, &p.f_u));
+        HV_RT_INTERNAL(field_index(maps.ws, a.lam1, fbytes, &p.f_lam1));
+        HV_RT_INTERNAL(field_index(maps.ws, a.lam_io, fbytes, &p.f_lamio));
+        HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
+        p.r = a.r;
+        p.r_vstride = a.r_per_vector ? (unsigned long long)h->ns * h->nt * h->nr : 0ull;
+        p.rscale = a.rscale;
+        p.img = a.img;
+        p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
+        p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
+        p.status = h->status;
+        p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
+        p.spg = (h->ns + a.G - 1) / a.G;
+        p.g = geo(h, t);
+        HV_RT_INTERNAL(ensure_smem(2 * kTileMenu + cfg, h->device, k_adj<C>, AdjSmem<C>::BYTES));
+        dim3 grid(t.ntiles, a.k, a.G);
+        k_adj<C><<<grid, C::NT, AdjSmem<C>::BYTES, st>>>(p);
+        return launched("k_adj launch");
+    });
 }
 
 }  // namespace hvk

@@ -87,6 +87,53 @@ class Problem:
         names = ("fwd", "advance", "adj", "other")
         return {names[i]: (int(n[i]), float(t[i])) for i in range(_lib.HV_K_COUNT)}
 
+    # ---------------------------------------------------------------- tiles, autotuning, graphs
+    def tiles(self) -> tuple:
+        """Tile configuration per kernel kind (forward+Born, forward-only, adjoint)."""
+        c = (ctypes.c_int * 3)()
+        check(self.lib.hv_get_tiles(self._h, c))
+        return tuple(c)
+
+    def set_tiles(self, cfg) -> None:
+        c = (ctypes.c_int * 3)(*[int(x) for x in cfg])
+        check(self.lib.hv_set_tiles(self._h, c))
+
+    def set_graphs(self, enable: bool = True) -> None:
+        """Replay the H v launch sequence as a CUDA graph (hv_set_graphs)."""
+        check(self.lib.hv_set_graphs(self._h, int(bool(enable))))
+
+    def autotune(self, k: int = 1, cache: str | None = None) -> tuple:
+        """Pick the fastest tile shape per kernel kind for k vectors (hv_autotune).
+
+        The choice is cached in a JSON file (``cache``, else $HV_TUNE_CACHE, else
+        ~/.cache/hv_tiles.json) keyed by the padded grid, shot count and k, and
+        reused when present."""
+        import json
+        import os
+        path = cache or os.environ.get("HV_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache",
+                                                                       "hv_tiles.json")
+        key = f"{self.NZ}x{self.NX}/ns{self.ns}/k{int(k)}"
+        try:
+            table = json.load(open(path))
+        except Exception:
+            table = {}
+        if key in table:
+            self.set_tiles(table[key])
+            return tuple(table[key])
+        ws, nb = self._workspace(HV_OP_HV, k, 1)
+        chosen = (ctypes.c_int * 3)()
+        check(self.lib.hv_autotune(self._h, int(k), ws, nb, self._stream(), chosen, None))
+        table[key] = list(chosen)
+        try:
+            os.makedirs(os.path.dirname(path), exist_ok=True)
+            tmp = f"{path}.{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, path)
+        except OSError:
+            pass
+        return tuple(chosen)
+
     # ---------------------------------------------------------------- workspace
     def workspace_size(self, op: int, k: int = 1, ckpt: int = HV_CKPT_ALL) -> int:
         n = ctypes.c_size_t()
