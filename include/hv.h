@@ -81,6 +81,7 @@ extern "C" {
 #define HV_OP_GRAD 3        /* hv_misfit_grad                    */
 #define HV_OP_HV 4          /* hv_hessian_apply(_f64out)         */
 #define HV_OP_WAVEFIELD 5   /* hv_wavefield                      */
+#define HV_OP_MISFIT 6      /* hv_misfit                         */
 
 /* Interior grid and sponge.  h in metres. */
 typedef struct hv_grid {
@@ -152,6 +153,11 @@ int hv_migrate(hv_handle *h, const float *m, const float *r, float *g, int ckpt,
 int hv_misfit_grad(hv_handle *h, const float *m, const float *d_obs, double *phi, float *grad,
                    int ckpt, void *ws, size_t ws_bytes, void *stream);
 
+/* Misfit only: phi (DEVICE double) = (1/(2 sigma^2)) sum (f(m) - d_obs)^2, the
+ * negative log-likelihood of section 2 (one forward solve per shot; what a
+ * gpCN proposal needs, paper section 2.3). */
+int hv_misfit(hv_handle *h, const float *m, const float *d_obs, double *phi, void *ws, size_t ws_bytes, void *stream);
+
 /* Gauss-Newton Hessian apply: Hv[j] = F^T F v[j] / sigma^2 for j < k; v and Hv
  * are [k][nz][nx].  Images accumulate in FP64 and are summed over shots in a
  * fixed order, so results do not depend on batching. */
@@ -196,6 +202,48 @@ int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float 
  * ran out and the kernel returned early (its outputs are then invalid).
  * Synchronises the device, then clears the status. */
 int hv_status(hv_handle *h, int *device_status);
+
+/* Serving.  A server owns one device arena of hbm_budget bytes (allocated at
+ * creation) and max_concurrent CUDA streams on the current device.  Requests
+ * (H v, gradient, misfit) on any problems created on that device are queued
+ * by hv_submit; a scheduler thread admits them in arrival order, letting a
+ * later request pass one that is waiting for memory, whenever a stream is free
+ * and the request's workspace fits in the arena, and runs each on its own
+ * stream, so the work of requests that arrive while others run overlaps on
+ * the GPU.  Results are bitwise the same as the direct calls.  Inputs and
+ * outputs are caller-owned device buffers that must stay valid until the
+ * request is done.  Request status: HV_REQ_QUEUED, HV_REQ_RUNNING, HV_OK when
+ * done, or an HV_E* code. */
+#define HV_REQ_HV 0
+#define HV_REQ_GRAD 1
+#define HV_REQ_MISFIT 2
+#define HV_REQ_QUEUED 100
+#define HV_REQ_RUNNING 101
+typedef struct hv_server hv_server;
+typedef struct hv_request {
+    int kind;               /* HV_REQ_*                                           */
+    hv_handle *problem;     /* problem the request runs on                        */
+    const float *m;         /* model [nz][nx]                                     */
+    const float *v;         /* HV: vectors [k][nz][nx]                            */
+    int k;                  /* HV: number of vectors                              */
+    const float *d_obs;     /* GRAD, MISFIT: observed data [ns][nt][nr]           */
+    float *out;             /* HV: [k][nz][nx]; GRAD: gradient [nz][nx]           */
+    double *phi;            /* GRAD, MISFIT: device scalar                        */
+    int ckpt;               /* HV, GRAD: checkpoint budget                        */
+} hv_request;
+typedef struct hv_request_info {
+    int kind, status;
+    double t_submit, t_start, t_done;   /* seconds since the server started        */
+    size_t ws_bytes;                     /* arena bytes the request held             */
+} hv_request_info;
+int hv_server_create(size_t hbm_budget, int max_concurrent, hv_server **out);
+/* Stops admitting, waits (bounded by timeout_s) for running requests, frees the arena. */
+int hv_server_destroy(hv_server *s, double timeout_s);
+int hv_submit(hv_server *s, const hv_request *r, unsigned long long *id);
+int hv_poll(hv_server *s, unsigned long long id, int *status);
+/* Waits until the request is done or failed; HV_ETIMEOUT after timeout_s. */
+int hv_wait(hv_server *s, unsigned long long id, double timeout_s, int *status);
+int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *info);
 
 /* Tile configurations.  The stencil kernels come in a small menu of tile
  * shapes (TX x TZ points per CTA); the choice per kernel kind (cfg[0]:

@@ -19,7 +19,7 @@ HEADER = os.path.join(_build.INCLUDE, "hv.h")
 
 HV_OK, HV_EINVAL, HV_ENOMEM, HV_ECUDA, HV_ETIMEOUT, HV_EBUSY, HV_ENOTSUP = range(7)
 HV_CKPT_ALL = -1
-HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD = range(6)
+HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD, HV_OP_MISFIT = range(7)
 HV_K_FWD, HV_K_ADVANCE, HV_K_ADJ, HV_K_OTHER = range(4)
 HV_K_COUNT = 4
 
@@ -33,6 +33,19 @@ class HvAcq(ctypes.Structure):
                 ("nt", c_int), ("dt", c_double), ("f0", c_double), ("t0", c_double), ("vmax", c_double),
                 ("R", c_double), ("sigma", c_double)]
 
+
+class HvRequest(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("problem", c_void_p), ("m", fp), ("v", fp), ("k", c_int), ("d_obs", fp),
+                ("out", fp), ("phi", fp), ("ckpt", c_int)]
+
+
+class HvRequestInfo(ctypes.Structure):
+    _fields_ = [("kind", c_int), ("status", c_int), ("t_submit", c_double), ("t_start", c_double),
+                ("t_done", c_double), ("ws_bytes", c_size_t)]
+
+
+HV_REQ_HV, HV_REQ_GRAD, HV_REQ_MISFIT = 0, 1, 2
+HV_REQ_QUEUED, HV_REQ_RUNNING = 100, 101
 
 _SIGS = {
     "hv_last_error": ([], ctypes.c_char_p),
@@ -50,6 +63,13 @@ _SIGS = {
     "hv_hessian_apply_static": ([ctypes.POINTER(HvGrid), ctypes.POINTER(HvAcq), fp, fp, c_int, fp, c_int,
                                  c_void_p], c_int),
     "hv_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
+    "hv_misfit": ([c_void_p, fp, fp, fp, fp, c_size_t, c_void_p], c_int),
+    "hv_server_create": ([c_size_t, c_int, ctypes.POINTER(c_void_p)], c_int),
+    "hv_server_destroy": ([c_void_p, c_double], c_int),
+    "hv_submit": ([c_void_p, ctypes.POINTER(HvRequest), ctypes.POINTER(ctypes.c_ulonglong)], c_int),
+    "hv_poll": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(c_int)], c_int),
+    "hv_wait": ([c_void_p, ctypes.c_ulonglong, c_double, ctypes.POINTER(c_int)], c_int),
+    "hv_request_get_info": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(HvRequestInfo)], c_int),
     "hv_tile_menu": ([c_int, ip, ip], c_int),
     "hv_autotune": ([c_void_p, c_int, fp, c_size_t, c_void_p, ip, ctypes.POINTER(ctypes.c_float)], c_int),
     "hv_set_tiles": ([c_void_p, ip], c_int),

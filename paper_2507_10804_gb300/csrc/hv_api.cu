@@ -104,7 +104,7 @@ constexpr int kResidualBlocks = 1024;
 
 int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
 {
-    if (op < HV_OP_FWD || op > HV_OP_WAVEFIELD) return hvi::fail(HV_EINVAL, "unknown operation %d", op);
+    if (op < HV_OP_FWD || op > HV_OP_MISFIT) return hvi::fail(HV_EINVAL, "unknown operation %d", op);
     const bool adjoint = (op == HV_OP_MIGRATE || op == HV_OP_GRAD || op == HV_OP_HV);
     const bool born = (op == HV_OP_BORN || op == HV_OP_HV);
     if (born && (k < 1 || k > 65535)) return hvi::fail(HV_EINVAL, "k = %d vectors; need 1 <= k <= 65535", k);
@@ -133,9 +133,9 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
     L.fields_end = o;         // every region above is a whole number of fields (fsize is 64-float aligned)
     const size_t ndata = (size_t)h->ns * h->nt * h->nr;
     if (op == HV_OP_HV) L.dd = take((size_t)k * ndata * sizeof(float));
-    if (op == HV_OP_GRAD) L.dd = take(ndata * sizeof(float));
+    if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.dd = take(ndata * sizeof(float));
     if (adjoint) L.img = take((size_t)L.G * k * h->fsize * sizeof(double));
-    if (op == HV_OP_GRAD) L.part = take(kResidualBlocks * sizeof(double));
+    if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.part = take(kResidualBlocks * sizeof(double));
     L.total = o;
     return HV_OK;
 }
@@ -603,7 +603,7 @@ extern "C" int hv_workspace_size(const hv_handle *h, int op, int k, int ckpt, si
 {
     if (!h || !bytes) return hvi::fail(HV_EINVAL, "null handle or output");
     Layout L;
-    if (op == HV_OP_FWD || op == HV_OP_BORN || op == HV_OP_WAVEFIELD) ckpt = HV_CKPT_ALL;
+    if (op == HV_OP_FWD || op == HV_OP_BORN || op == HV_OP_WAVEFIELD || op == HV_OP_MISFIT) ckpt = HV_CKPT_ALL;
     HV_RT(make_layout(h, op, k, ckpt, L));
     *bytes = L.total;
     return HV_OK;
@@ -621,6 +621,26 @@ extern "C" int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, si
     HV_RT(E.zero_ghosts(false));
     HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
     for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, false, d, nullptr, nullptr));
+    return HV_OK;
+}
+
+extern "C" int hv_misfit(hv_handle *h, const float *m, const float *d_obs, double *phi, void *ws, size_t ws_bytes,
+                         void *stream)
+{
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_MISFIT, 1, HV_CKPT_ALL, L));
+    if (!m || !d_obs || !phi) return hvi::fail(HV_EINVAL, "null model, data or phi pointer");
+    cudaStream_t st = (cudaStream_t)stream;
+    Exec E;
+    HV_RT(E.init(h, st, L, ws, 0));
+    HV_CK(cudaMemsetAsync(E.zero, 0, L.fb, st));
+    HV_RT(E.zero_ghosts(false));
+    HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
+    float *dd = reinterpret_cast<float *>((char *)ws + L.dd);
+    for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, false, dd, nullptr, nullptr));
+    double *part = reinterpret_cast<double *>((char *)ws + L.part);
+    HV_RT(hvk::launch_residual(h, dd, d_obs, dd, part, kResidualBlocks, st));
+    HV_RT(hvk::launch_reduce_phi(part, kResidualBlocks, 0.5 / (h->sigma * h->sigma), phi, st));
     return HV_OK;
 }
 

@@ -1,0 +1,325 @@
+// hv_server.cpp -- request serving for many concurrent clients (MCMC chains
+// asking for misfits, optimisers asking for gradients and Hessian actions;
+// paper sections 2.2-2.3 use exactly these three quantities).
+//
+// One device arena holds every admitted request's workspace; a scheduler
+// thread admits queued requests when a stream and enough arena memory are
+// free and runs each on its own stream, so requests that arrive while others
+// run overlap with them on the GPU.  Completion is detected with events; the
+// scheduler never blocks on the device (event queries plus short sleeps), and
+// every host wait is bounded.
+#include "hv_internal.h"
+
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <thread>
+#include <unordered_map>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over [0, size) in 256-byte units, with coalescing.
+class Arena {
+  public:
+    explicit Arena(size_t size) { free_[0] = size; }
+    bool alloc(size_t bytes, size_t *off)
+    {
+        bytes = (bytes + 255) & ~(size_t)255;
+        if (bytes == 0) bytes = 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                size_t rest = it->second - bytes;
+                size_t start = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[start] = rest;
+                used_[*off] = bytes;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off)
+    {
+        auto u = used_.find(off);
+        if (u == used_.end()) return;
+        size_t bytes = u->second;
+        used_.erase(u);
+        auto nx = free_.lower_bound(off);
+        if (nx != free_.end() && off + bytes == nx->first) {
+            bytes += nx->second;
+            nx = free_.erase(nx);
+        }
+        if (nx != free_.begin()) {
+            auto pv = std::prev(nx);
+            if (pv->first + pv->second == off) {
+                pv->second += bytes;
+                return;
+            }
+        }
+        free_[off] = bytes;
+    }
+
+  private:
+    std::map<size_t, size_t> free_;   // offset -> length
+    std::map<size_t, size_t> used_;
+};
+
+struct Req {
+    unsigned long long id;
+    hv_request r;
+    int status = HV_REQ_QUEUED;
+    size_t ws = 0, off = 0;
+    int slot = -1;
+    double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct hv_server {
+    int device = 0;
+    size_t budget = 0;
+    char *arena_base = nullptr;
+    Arena *arena = nullptr;
+    std::vector<cudaStream_t> streams;
+    std::vector<cudaEvent_t> events;
+    std::vector<unsigned long long> slot_req;   // request id per slot (0 = free)
+    std::mutex mu;
+    std::condition_variable cv_work, cv_done;
+    std::deque<unsigned long long> queue;
+    std::unordered_map<unsigned long long, Req> reqs;
+    unsigned long long next_id = 1;
+    std::atomic<bool> stop{false};
+    std::thread worker;
+    Clock::time_point t0;
+
+    double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+int op_of(int kind)
+{
+    return kind == HV_REQ_HV ? HV_OP_HV : (kind == HV_REQ_GRAD ? HV_OP_GRAD : HV_OP_MISFIT);
+}
+
+int request_ws(const hv_request &r, size_t *bytes)
+{
+    return hv_workspace_size(r.problem, op_of(r.kind), r.kind == HV_REQ_HV ? r.k : 1, r.ckpt, bytes);
+}
+
+// Enqueue one request on its stream and record the slot's completion event
+// (also after a failed enqueue, so that its memory is released only once
+// whatever was enqueued has finished).
+int launch(hv_server *S, const Req &q)
+{
+    void *ws = S->arena_base + q.off;
+    void *st = (void *)S->streams[q.slot];
+    const hv_request &r = q.r;
+    int rc;
+    if (r.kind == HV_REQ_HV) rc = hv_hessian_apply(r.problem, r.m, r.v, r.k, r.out, r.ckpt, ws, q.ws, st);
+    else if (r.kind == HV_REQ_GRAD) rc = hv_misfit_grad(r.problem, r.m, r.d_obs, r.phi, r.out, r.ckpt, ws, q.ws, st);
+    else rc = hv_misfit(r.problem, r.m, r.d_obs, r.phi, ws, q.ws, st);
+    cudaError_t e = cudaEventRecord(S->events[q.slot], S->streams[q.slot]);
+    if (rc == HV_OK && e != cudaSuccess) rc = HV_ECUDA;
+    return rc;
+}
+
+void worker_loop(hv_server *S)
+{
+    cudaSetDevice(S->device);
+    std::vector<int> failed(S->slot_req.size(), HV_OK);   // enqueue status per running slot
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop.load()) {
+        bool progress = false;
+        // completions
+        for (size_t sl = 0; sl < S->slot_req.size(); ++sl) {
+            unsigned long long id = S->slot_req[sl];
+            if (!id) continue;
+            cudaError_t e = cudaEventQuery(S->events[sl]);
+            if (e == cudaErrorNotReady) continue;
+            Req &q = S->reqs[id];
+            q.status = failed[sl] != HV_OK ? failed[sl] : (e == cudaSuccess ? HV_OK : HV_ECUDA);
+            q.t_done = S->now();
+            S->arena->release(q.off);
+            S->slot_req[sl] = 0;
+            failed[sl] = HV_OK;
+            progress = true;
+        }
+        if (progress) S->cv_done.notify_all();
+        // admissions, in arrival order; a request that does not fit yet is passed
+        std::vector<Req> admitted;
+        for (auto it = S->queue.begin(); it != S->queue.end();) {
+            int slot = -1;
+            for (size_t sl = 0; sl < S->slot_req.size(); ++sl)
+                if (!S->slot_req[sl]) {
+                    slot = (int)sl;
+                    break;
+                }
+            if (slot < 0) break;
+            Req &q = S->reqs[*it];
+            size_t off = 0;
+            if (!S->arena->alloc(q.ws, &off)) {
+                ++it;
+                continue;
+            }
+            q.off = off;
+            q.slot = slot;
+            q.t_start = S->now();
+            q.status = HV_REQ_RUNNING;
+            S->slot_req[slot] = q.id;
+            admitted.push_back(q);
+            it = S->queue.erase(it);
+        }
+        if (!admitted.empty()) {
+            lk.unlock();                          // enqueueing thousands of launches takes a while
+            std::vector<int> rcs;
+            for (const Req &q : admitted) rcs.push_back(launch(S, q));
+            lk.lock();
+            for (size_t i = 0; i < admitted.size(); ++i) failed[admitted[i].slot] = rcs[i];
+            progress = true;
+        }
+        if (!progress) S->cv_work.wait_for(lk, std::chrono::microseconds(50));
+    }
+}
+
+}  // namespace
+
+extern "C" int hv_server_create(size_t hbm_budget, int max_concurrent, hv_server **out)
+{
+    if (!out || hbm_budget < 4096 || max_concurrent < 1 || max_concurrent > 256)
+        return hvi::fail(HV_EINVAL, "hv_server_create: need a budget >= 4 KiB and 1..256 concurrent requests");
+    *out = nullptr;
+    hv_server *S = new hv_server();
+    S->t0 = Clock::now();
+    cudaError_t e = cudaGetDevice(&S->device);
+    if (e == cudaSuccess) e = cudaMalloc(&S->arena_base, hbm_budget);
+    if (e != cudaSuccess) {
+        delete S;
+        return hvi::fail(e == cudaErrorMemoryAllocation ? HV_ENOMEM : HV_ECUDA, "hv_server_create: %s",
+                         cudaGetErrorString(e));
+    }
+    S->budget = hbm_budget;
+    S->arena = new Arena(hbm_budget);
+    S->streams.resize(max_concurrent);
+    S->events.resize(max_concurrent);
+    S->slot_req.assign(max_concurrent, 0);
+    for (int i = 0; i < max_concurrent; ++i) {
+        cudaStreamCreateWithFlags(&S->streams[i], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&S->events[i], cudaEventDisableTiming);
+    }
+    S->worker = std::thread(worker_loop, S);
+    *out = S;
+    return HV_OK;
+}
+
+extern "C" int hv_server_destroy(hv_server *S, double timeout_s)
+{
+    if (!S) return HV_OK;
+    int rc = HV_OK;
+    {
+        // wait (bounded) for running requests
+        auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0);
+        std::unique_lock<std::mutex> lk(S->mu);
+        S->queue.clear();
+        auto busy = [&] {
+            for (auto id : S->slot_req)
+                if (id) return true;
+            return false;
+        };
+        while (busy()) {
+            if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && busy()) {
+                rc = hvi::fail(HV_ETIMEOUT, "hv_server_destroy: requests still running after %.1f s", timeout_s);
+                break;
+            }
+        }
+    }
+    S->stop.store(true);
+    S->cv_work.notify_all();
+    S->worker.join();
+    if (rc == HV_OK) {
+        for (auto st : S->streams) cudaStreamDestroy(st);
+        for (auto ev : S->events) cudaEventDestroy(ev);
+        cudaFree(S->arena_base);
+        delete S->arena;
+        delete S;
+    }
+    // on timeout the server's device memory is left in place (work may still use it)
+    return rc;
+}
+
+extern "C" int hv_submit(hv_server *S, const hv_request *r, unsigned long long *id)
+{
+    if (!S || !r || !id) return hvi::fail(HV_EINVAL, "hv_submit: null argument");
+    if (!r->problem || !r->m || (r->kind == HV_REQ_HV && (!r->v || !r->out || r->k < 1)) ||
+        (r->kind == HV_REQ_GRAD && (!r->d_obs || !r->out || !r->phi)) || (r->kind == HV_REQ_MISFIT && (!r->d_obs || !r->phi)) ||
+        r->kind < HV_REQ_HV || r->kind > HV_REQ_MISFIT)
+        return hvi::fail(HV_EINVAL, "hv_submit: incomplete request of kind %d", r->kind);
+    if (r->problem->device != S->device) return hvi::fail(HV_EINVAL, "hv_submit: problem on another device");
+    size_t ws = 0;
+    HV_RT_INTERNAL(request_ws(*r, &ws));
+    if (((ws + 255) & ~(size_t)255) > S->budget)
+        return hvi::fail(HV_ENOMEM, "hv_submit: request needs %zu bytes, the server budget is %zu", ws, S->budget);
+    std::lock_guard<std::mutex> g(S->mu);
+    Req q;
+    q.id = S->next_id++;
+    q.r = *r;
+    q.ws = ws;
+    q.t_submit = S->now();
+    S->reqs[q.id] = q;
+    S->queue.push_back(q.id);
+    *id = q.id;
+    S->cv_work.notify_all();
+    return HV_OK;
+}
+
+extern "C" int hv_poll(hv_server *S, unsigned long long id, int *status)
+{
+    if (!S || !status) return hvi::fail(HV_EINVAL, "hv_poll: null argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return hvi::fail(HV_EINVAL, "hv_poll: unknown request %llu", id);
+    *status = it->second.status;
+    return HV_OK;
+}
+
+extern "C" int hv_wait(hv_server *S, unsigned long long id, double timeout_s, int *status)
+{
+    if (!S || !status) return hvi::fail(HV_EINVAL, "hv_wait: null argument");
+    std::unique_lock<std::mutex> lk(S->mu);
+    auto deadline = Clock::now() + std::chrono::duration<double>(timeout_s > 0 ? timeout_s : 0.0);
+    for (;;) {
+        auto it = S->reqs.find(id);
+        if (it == S->reqs.end()) return hvi::fail(HV_EINVAL, "hv_wait: unknown request %llu", id);
+        int st = it->second.status;
+        if (st != HV_REQ_QUEUED && st != HV_REQ_RUNNING) {
+            *status = st;
+            return HV_OK;
+        }
+        if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout) {
+            *status = S->reqs[id].status;
+            if (*status == HV_REQ_QUEUED || *status == HV_REQ_RUNNING)
+                return hvi::fail(HV_ETIMEOUT, "hv_wait: request %llu not done after %.3f s", id, timeout_s);
+            return HV_OK;
+        }
+    }
+}
+
+extern "C" int hv_request_get_info(hv_server *S, unsigned long long id, hv_request_info *info)
+{
+    if (!S || !info) return hvi::fail(HV_EINVAL, "hv_request_get_info: null argument");
+    std::lock_guard<std::mutex> g(S->mu);
+    auto it = S->reqs.find(id);
+    if (it == S->reqs.end()) return hvi::fail(HV_EINVAL, "hv_request_get_info: unknown request %llu", id);
+    const Req &q = it->second;
+    info->kind = q.r.kind;
+    info->status = q.status;
+    info->t_submit = q.t_submit;
+    info->t_start = q.t_start;
+    info->t_done = q.t_done;
+    info->ws_bytes = q.ws;
+    return HV_OK;
+}

@@ -1,0 +1,108 @@
+"""Serving: requests from many clients on grids of different sizes are
+admitted by memory budget and run concurrently; each result is bitwise the
+same alone and in the mix."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import oracle as O
+from paper_2507_10804_gb300 import synth
+from paper_2507_10804_gb300.hv import Problem
+from paper_2507_10804_gb300.serve import Server
+from tests._helpers import f32, oracle_problem, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def make(nz, nx, ns, nt, seed):
+    w = synth.workload(1, nt=nt)
+    m = synth.gradient_grf_model(seed, nz, nx, 10.0)
+    acq = synth.surface_acquisition(nx, ns, nx // 2)
+    w = synth.Workload(name=f"{nz}x{nx}", nz=nz, nx=nx, nb=20, h=10.0, nt=nt, dt=synth.cfl_dt(10.0, float(m.max())),
+                       f0=15.0, t0=0.1, vmax=float(m.max()), acq=acq, m=m,
+                       v=synth.smoothed_normal_vectors(seed + 1, 2, nz, nx))
+    return w, Problem.from_workload(w)
+
+
+def t(a):
+    return torch.tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+@pytest.fixture(scope="module")
+def problems():
+    return [make(48, 64, 4, 300, 11), make(96, 80, 6, 400, 12)]
+
+
+def requests(problems, n=24, seed=7):
+    u = synth.uniform(seed, 3 * n)
+    out = []
+    for i in range(n):
+        w, P = problems[int(u[3 * i] * len(problems))]
+        kind = ("hv", "grad", "misfit")[min(int(u[3 * i + 1] * 5) // 2, 2)]   # 40% / 40% / 20%
+        m = w.m * (1.0 + 0.01 * synth.smoothed_normal_vectors(seed + 100 + i, 1, w.nz, w.nx, 4.0)[0])
+        dobs = synth.normal(seed + 200 + i, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3
+        out.append((kind, w, P, t(m), t(w.v[:1 + i % 2]), t(dobs), 1 + (i % 3) * 5))
+    return out
+
+
+def run_direct(kind, w, P, m, v, dobs, ckpt):
+    if kind == "hv":
+        return [P.hessian_apply(m, v, ckpt=ckpt)]
+    if kind == "grad":
+        phi, g = P.misfit_grad(m, dobs, ckpt=ckpt)
+        return [phi, g]
+    phi, g = P.misfit_grad(m, dobs, ckpt=ckpt)
+    return [phi]
+
+
+def submit(S, kind, w, P, m, v, dobs, ckpt):
+    if kind == "hv":
+        rid, out = S.submit_hv(P, m, v, ckpt=ckpt)
+        return rid, [out]
+    if kind == "grad":
+        rid, phi, g = S.submit_grad(P, m, dobs, ckpt=ckpt)
+        return rid, [phi, g]
+    rid, phi = S.submit_misfit(P, m, dobs)
+    return rid, [phi]
+
+
+def test_mixed_requests_equal_direct_calls_bitwise(problems):
+    reqs = requests(problems)
+    direct = [[x.cpu().numpy() for x in run_direct(*r)] for r in reqs]
+    S = Server(hbm_budget=2 << 30, max_concurrent=8)
+    subs = [submit(S, *r) for r in reqs]                       # all arrive while others run
+    for (rid, outs), ref in zip(subs, direct):
+        assert S.wait(rid, timeout=300) == 0
+        for o, r_ in zip(outs, ref):
+            assert np.array_equal(o.cpu().numpy(), r_)
+    infos = [S.info(rid) for rid, _ in subs]
+    starts = sorted(i["t_start"] for i in infos)
+    dones = sorted(i["t_done"] for i in infos)
+    assert starts[1] < dones[0]                                 # requests overlapped on the device
+    S.close()
+
+
+def test_tight_budget_queues_and_rejects(problems):
+    reqs = requests(problems, n=8, seed=9)
+    op = {"hv": 4, "grad": 3, "misfit": 6}
+    need = max(P.workspace_size(op[kind], v.shape[0] if kind == "hv" else 1, ckpt)
+               for kind, w, P, m, v, dobs, ckpt in reqs)
+    S = Server(hbm_budget=need + 4096, max_concurrent=4)        # room for about one request
+    subs = [submit(S, *r) for r in reqs]
+    for rid, _ in subs:
+        assert S.wait(rid, timeout=300) == 0
+    with pytest.raises(Exception):
+        big = make(160, 160, 8, 500, 13)[1]
+        S.submit_hv(big, t(np.full((160, 160), 2000.0)), t(np.zeros((64, 160, 160))), ckpt=-1)
+    S.close()
+
+
+def test_misfit_matches_oracle(problems):
+    w, P = problems[0]
+    dobs = synth.normal(5, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3
+    S = Server(hbm_budget=1 << 30, max_concurrent=2)
+    rid, phi = S.submit_misfit(P, t(w.m), t(dobs))
+    assert S.wait(rid) == 0
+    ref = O.misfit_grad(oracle_problem(w), f32(w.m), f32(dobs))[0]
+    assert abs(float(phi) - ref) < 2e-4 * ref
+    S.close()
