@@ -245,6 +245,20 @@ def run_ours(args, w):
     calls_per_s = args.steps * world / (ms_max / 1e3)
     value = calls_per_s * w.k                      # H v products per second (k per call)
 
+    one_at_a_time = None
+    if graphs and rank == 0:
+        # the plain path: one vector per call, no graph, default tiles (8 of the 64 vectors)
+        Q = Problem.from_workload(w, device=dev)
+        vs = [v[j:j + 1].contiguous() for j in range(8)]
+        Q.hessian_apply(m, vs[0], ckpt=CKPT)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for x in vs:
+            Q.hessian_apply(m, x, ckpt=CKPT)
+        torch.cuda.synchronize(dev)
+        one_at_a_time = {"value": len(vs) / (time.perf_counter() - t0), "unit": UNIT,
+                         "what": "one vector per call, stream launches, default tiles (8 vectors timed)"}
+        Q.close()
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     mh = torch.tensor(w.m, dtype=torch.float32).pin_memory()
     vh = torch.tensor(w.v, dtype=torch.float32).pin_memory()
@@ -318,9 +332,123 @@ def run_ours(args, w):
         if graphs:
             line["config"]["graphs"] = "H v launch sequence replayed as a CUDA graph; per-kernel times from one extra profiled apply"
             line["config"]["tiles"] = list(tiles)
+            line["one_at_a_time"] = one_at_a_time
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def serve_requests(n, seed=20250719):
+    """The request stream of the serving workload: clients 0-63 are MCMC chains,
+    64-67 FWI runs; each request draws its kind (H v 40%, gradient 40%, misfit
+    20%), its grid from {128x128, 256x256, 384x1152} (steps 1000/1500/3000) and
+    its shot count from U{4..32}."""
+    from paper_2507_10804_gb300 import synth
+    u = synth.uniform(seed, 4 * n)
+    grids = [(128, 128, 1000), (256, 256, 1500), (384, 1152, 3000)]
+    out = []
+    for i in range(n):
+        kind = ("hv", "grad", "misfit")[min(int(u[4 * i] * 5) // 2, 2)]
+        g = grids[min(int(u[4 * i + 1] * 3), 2)]
+        ns = 4 + min(int(u[4 * i + 2] * 29), 28)
+        client = min(int(u[4 * i + 3] * 68), 67)
+        out.append({"kind": kind, "grid": g, "ns": ns, "client": client})
+    return out
+
+
+def run_serve(args):
+    """Serving workload: Poisson arrivals at fractions of the measured serial
+    capacity, memory-budgeted admission into a 150 GB pool."""
+    import torch
+
+    from paper_2507_10804_gb300 import synth
+    from paper_2507_10804_gb300.hv import Problem
+    from paper_2507_10804_gb300.serve import Server
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n = args.requests
+    reqs = serve_requests(n)
+    problems, models, data = {}, {}, {}
+    for r in reqs:
+        nz, nx, nt = r["grid"]
+        key = (nz, nx, r["ns"])
+        if key not in problems:
+            h = 10.0 if nx < 1000 else 8.0
+            nb = 20 if nx < 1000 else 40
+            if (nz, nx) not in models:
+                m = synth.gradient_grf_model(nz * 7 + nx, nz, nx, h) if nx < 1000 else \
+                    synth.layered_faulted_model(2025, nz, nx, h)[1]
+                models[(nz, nx)] = (m, torch.tensor(m, dtype=torch.float32, device=dev),
+                                    torch.tensor(synth.smoothed_normal_vectors(nz + nx, 1, nz, nx), dtype=torch.float32,
+                                                 device=dev))
+            m = models[(nz, nx)][0]
+            vmax = float(m.max())
+            acq = synth.surface_acquisition(nx, r["ns"], nx // 3)
+            w = synth.Workload(name="serve", nz=nz, nx=nx, nb=nb, h=h, nt=nt, dt=synth.cfl_dt(h, vmax), f0=10.0,
+                               t0=0.15, vmax=vmax, acq=acq, m=m, v=np.zeros((1, nz, nx)))
+            problems[key] = Problem.from_workload(w, device=dev)
+            data[key] = problems[key].fwd_model(models[(nz, nx)][1] * 1.02)
+    torch.cuda.synchronize()
+    ckpt = 30
+
+    def submit(S, r):
+        nz, nx, nt = r["grid"]
+        P = problems[(nz, nx, r["ns"])]
+        _, m, v = models[(nz, nx)]
+        d = data[(nz, nx, r["ns"])]
+        if r["kind"] == "hv":
+            return S.submit_hv(P, m, v, ckpt=ckpt)[0]
+        if r["kind"] == "grad":
+            return S.submit_grad(P, m, d, ckpt=ckpt)[0]
+        return S.submit_misfit(P, m, d)[0]
+
+    budget = 150 << 30
+    # serial: one request at a time through the same server
+    S = Server(hbm_budget=budget, max_concurrent=1, device=dev)
+    for r in reqs[:3]:
+        S.wait(submit(S, r))
+    t0 = time.perf_counter()
+    for r in reqs:
+        assert S.wait(submit(S, r)) == 0
+    t_serial = time.perf_counter() - t0
+    S.close()
+    serial_rate = n / t_serial
+    n_hv = sum(r["kind"] == "hv" for r in reqs)
+    rng = np.random.default_rng(7)
+    results = []
+    S = Server(hbm_budget=budget, max_concurrent=args.concurrency, device=dev)
+    for frac in args.rates:
+        lam = frac * serial_rate
+        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n))
+        ids = []
+        t0 = time.perf_counter()
+        for a, r in zip(arrivals, reqs):
+            dt_ = t0 + a - time.perf_counter()
+            if dt_ > 0:
+                time.sleep(dt_)
+            ids.append(submit(S, r))
+        for i in ids:
+            assert S.wait(i) == 0
+        infos = [S.info(i) for i in ids]
+        lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
+        span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        results.append({"rate_frac_of_serial": frac, "offered_req_s": lam, "p50_ms": float(np.percentile(lat, 50)),
+                        "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": n / span,
+                        "hv_per_s": n_hv / span})
+    S.close()
+    best = max(results, key=lambda x: x["throughput_req_s"])
+    line = {
+        "metric": METRIC, "value": best["hv_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 3,
+        "ms_per_step": 1e3 / best["throughput_req_s"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic request stream (seeded models; stands in for the paper's MCMC and FWI clients)",
+        "config": {"workload": "serving: 64 MCMC chains + 4 FWI runs, Poisson arrivals, H v 40% / gradient 40% / "
+                               "misfit 20%, grids {128x128, 256x256, 384x1152} x U{4..32} shots, 150 GB pool",
+                   "requests": n, "concurrency": args.concurrency, "snapshots_per_shot": ckpt},
+        "serve": {"serial_req_s": serial_rate, "serial_hv_per_s": n_hv / t_serial, "rates": results},
+    }
+    print(json.dumps(line))
 
 
 def main():
@@ -333,12 +461,18 @@ def main():
     ap.add_argument("--nt", type=int, default=None, help="override the step count (profiling runs)")
     ap.add_argument("--shots", type=int, default=None, help="override the shot count (profiling runs)")
     ap.add_argument("--ckpt", type=int, default=None, help="snapshots per shot (profiling runs)")
-    ap.add_argument("--workload", choices=["paper", "batched"], default="paper",
+    ap.add_argument("--requests", type=int, default=60, help="serving workload: requests per rate")
+    ap.add_argument("--concurrency", type=int, default=16, help="serving workload: concurrent requests")
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
+                    help="serving workload: arrival rates as fractions of the serial capacity")
+    ap.add_argument("--workload", choices=["paper", "batched", "serve"], default="paper",
                     help="paper: 384x1152, 32 shots, 3000 steps, 1 vector (default); batched: the 64x64 model "
                          "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     from paper_2507_10804_gb300 import synth
+    if args.workload == "serve":
+        return run_serve(args)
     if args.workload == "batched":
         CKPT = args.ckpt if args.ckpt is not None else -1
         w = synth.workload(3, nt=args.nt, ns=args.shots)
