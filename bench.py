@@ -185,6 +185,7 @@ def run_ours(args, w):
     import torch.distributed as dist
 
     from paper_2507_10804_gb300.hv import Problem, kernel_launches
+    from paper_2507_10804_gb300.parallel import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -238,10 +239,7 @@ def run_ours(args, w):
         prof = P.profile_read()
     P.profile(False)
     ms = e0.elapsed_time(e1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, device=dev)
     calls_per_s = args.steps * world / (ms_max / 1e3)
     value = calls_per_s * w.k                      # H v products per second (k per call)
 
@@ -276,10 +274,7 @@ def run_ours(args, w):
         out_h.copy_(Hv, non_blocking=True)
         torch.cuda.synchronize(dev)
     e2e_s = (time.perf_counter() - t0) / ke
-    t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_val = world * w.k / float(t.item())
+    e2e_val = world * w.k / max_over_ranks(e2e_s, device=dev)
 
     if rank == 0:
         pk, pk_kind = peaks()

@@ -203,6 +203,23 @@ int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float 
  * Synchronises the device, then clears the status. */
 int hv_status(hv_handle *h, int *device_status);
 
+/* Hessian approximations built from batched H v (section 3.2: point spread
+ * functions; section 3.4: pseudo-differential operator probing; section 3.6:
+ * PSF+), applied in low-rank-symbol form (section 3.3, eq. (lr-psido)).
+ * Declared for the interface; this version does not provide them: every
+ * call returns HV_ENOTSUP.  The H v products they consume are the batched
+ * hv_hessian_apply calls above (impulse lattices and probing vectors). */
+typedef struct hv_approx hv_approx;
+#define HV_APPROX_H 0           /* apply the approximation of H_d            */
+#define HV_APPROX_SQRT 1        /* apply its SPD square root                 */
+#define HV_APPROX_INVSQRT 2     /* apply the inverse square root             */
+int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, hv_approx **out, void *ws,
+                        size_t ws_bytes, void *stream);
+int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, hv_approx **out, void *ws, size_t ws_bytes,
+                        void *stream);
+int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream);
+int hv_approx_destroy(hv_approx *a);
+
 /* Serving.  A server owns one device arena of hbm_budget bytes (allocated at
  * creation) and max_concurrent CUDA streams on the current device.  Requests
  * (H v, gradient, misfit) on any problems created on that device are queued

@@ -70,6 +70,11 @@ _SIGS = {
     "hv_poll": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(c_int)], c_int),
     "hv_wait": ([c_void_p, ctypes.c_ulonglong, c_double, ctypes.POINTER(c_int)], c_int),
     "hv_request_get_info": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(HvRequestInfo)], c_int),
+    "hv_approx_build_psf": ([c_void_p, fp, c_int, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p], c_int),
+    "hv_approx_build_pdo": ([c_void_p, fp, c_double, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p],
+                            c_int),
+    "hv_approx_apply": ([c_void_p, fp, c_int, fp, c_int, c_void_p], c_int),
+    "hv_approx_destroy": ([c_void_p], c_int),
     "hv_tile_menu": ([c_int, ip, ip], c_int),
     "hv_autotune": ([c_void_p, c_int, fp, c_size_t, c_void_p, ip, ctypes.POINTER(ctypes.c_float)], c_int),
     "hv_set_tiles": ([c_void_p, ip], c_int),

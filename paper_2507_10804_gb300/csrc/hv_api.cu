@@ -1013,3 +1013,23 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
         for (int i = 0; i < 3; ++i) chosen[i] = arg[i];
     return HV_OK;
 }
+
+// Hessian approximations: declared, not provided in this version.
+extern "C" int hv_approx_build_psf(hv_handle *, const float *, int, int, hv_approx **out, void *, size_t, void *)
+{
+    if (out) *out = nullptr;
+    return hvi::fail(HV_ENOTSUP, "hv_approx_build_psf: not provided in this version");
+}
+
+extern "C" int hv_approx_build_pdo(hv_handle *, const float *, double, int, hv_approx **out, void *, size_t, void *)
+{
+    if (out) *out = nullptr;
+    return hvi::fail(HV_ENOTSUP, "hv_approx_build_pdo: not provided in this version");
+}
+
+extern "C" int hv_approx_apply(const hv_approx *, const float *, int, float *, int, void *)
+{
+    return hvi::fail(HV_ENOTSUP, "hv_approx_apply: not provided in this version");
+}
+
+extern "C" int hv_approx_destroy(hv_approx *) { return HV_OK; }

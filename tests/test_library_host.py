@@ -114,3 +114,13 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib, kw, needle):
     rc, msg = _create(lib, **kw)
     assert rc == _lib.HV_EINVAL
     assert needle in msg
+
+
+def test_approximation_entry_points_report_not_supported(lib):
+    out = ctypes.c_void_p(1)
+    assert lib.hv_approx_build_psf(None, None, 12, 4, ctypes.byref(out), None, 0, None) == _lib.HV_ENOTSUP
+    assert out.value is None
+    assert lib.hv_approx_build_pdo(None, None, ctypes.c_double(0.01), 8, ctypes.byref(out), None, 0, None) \
+        == _lib.HV_ENOTSUP
+    assert lib.hv_approx_apply(None, None, 1, None, 0, None) == _lib.HV_ENOTSUP
+    assert lib.hv_approx_destroy(None) == _lib.HV_OK
