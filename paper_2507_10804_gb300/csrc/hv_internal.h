@@ -97,7 +97,7 @@ int prepare_kernels(const hv_handle *h);
 // Tensor maps of one call's workspace, viewed as an array of fields
 // (x, z, field index): `halo` copies a tile with its 4-cell halo, `pt` the
 // tile's own points.  Opaque CUtensorMap bytes (128 each).
-constexpr int kMaxTileMenu = 6;
+constexpr int kMaxTileMenu = 8;
 struct TmaMaps {
     alignas(64) unsigned char halo[kMaxTileMenu][128];   // per tile configuration
     alignas(64) unsigned char pt[kMaxTileMenu][128];

@@ -43,7 +43,7 @@ constexpr float LC3 = (float)(8.0 / 315.0);
 constexpr float LC4 = (float)(-1.0 / 560.0);
 
 constexpr int kShotsPerGroup = 8;
-constexpr int kTileMenu = 6;       // number of tile configurations (with_cfg)
+constexpr int kTileMenu = 8;       // number of tile configurations (with_cfg)
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 template <int BX_, int BZ_, int RZ_>
@@ -63,8 +63,10 @@ using Cfg64x32 = Cfg<16, 16, 2>;   // 256 threads, 4 x 2 points each
 using Cfg32x32 = Cfg<8, 16, 2>;    // 128 threads
 using Cfg64x16 = Cfg<16, 8, 2>;    // 128 threads
 using Cfg52x26 = Cfg<13, 13, 2>;   // 169 threads; tiles a 104-point padded axis exactly
-using Cfg64x32r4 = Cfg<16, 8, 4>;  // 128 threads, 4 x 4 points each
-using Cfg64x64r4 = Cfg<16, 16, 4>; // 256 threads, 4 x 4 points each
+using Cfg128x16 = Cfg<32, 8, 2>;   // 256 threads
+using Cfg64x8 = Cfg<16, 4, 2>;     // 64 threads
+using Cfg32x16 = Cfg<8, 8, 2>;     // 64 threads
+using Cfg128x8 = Cfg<32, 4, 2>;    // 128 threads
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -624,8 +626,10 @@ auto with_cfg(int id, F &&f)
     case 1: return f(Cfg32x32{});
     case 2: return f(Cfg64x16{});
     case 3: return f(Cfg52x26{});
-    case 4: return f(Cfg64x32r4{});
-    case 5: return f(Cfg64x64r4{});
+    case 4: return f(Cfg128x16{});
+    case 5: return f(Cfg64x8{});
+    case 6: return f(Cfg32x16{});
+    case 7: return f(Cfg128x8{});
     default: return f(Cfg64x32{});
     }
 }

@@ -45,7 +45,7 @@ def test_tile_shapes_and_graphs_do_not_change_results(batched):
     P.set_graphs(False)
     P.set_tiles((0, 0, 0))
     ref = P.hessian_apply(m, vs, ckpt=7).cpu().numpy()
-    for cfg in [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 4, 4), (5, 5, 5), (3, 1, 2), (5, 4, 0)]:
+    for cfg in [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 4, 4), (5, 5, 5), (6, 6, 6), (7, 7, 7), (3, 1, 2), (5, 4, 0)]:
         P.set_tiles(cfg)
         for graphs in (False, True):
             P.set_graphs(graphs)
