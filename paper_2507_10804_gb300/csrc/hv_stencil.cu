@@ -133,7 +133,7 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int 
 }
 
 // ------------------------------------------------------------------ stencil
-// Lh at the thread's 4 x RZ block from a [H][W] halo tile.  The k = 1 term is
+// The Laplacian sum Lh: the k = 1 term is
 // summed over differences from the centre, c1 ((w[+1] - w0) + (w[-1] - w0)),
 // the k = 2..4 terms as plain pairs, and the centre coefficient of those terms
 // (-4 (c2 + c3 + c4), so that the total centre weight is 4 c0) is added last.
@@ -142,9 +142,39 @@ __device__ __forceinline__ void tma_load(void *dst, const CUtensorMap *map, int 
 // same as differencing every term) with 21 instead of 32 operations per point.
 constexpr float LCR = (float)(-4.0 * (-1.0 / 5.0 + 8.0 / 315.0 - 1.0 / 560.0));
 
+// ------------------------------------------------------------------ packed FP32
+// The stencil arithmetic runs on pairs of neighbouring x points with the
+// paired FP32 instructions (add / sub / mul / fma on .f32x2): one instruction
+// rounds each lane exactly as its scalar counterpart would, so every lane sees
+// the same sequence of correctly rounded operations as a scalar kernel.
+__device__ __forceinline__ float2 f2add(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 f2mul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 f2fma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 f2sub(float2 a, float2 b)
+{
+    unsigned long long x, y, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(x) : "f"(a.x), "f"(a.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(y) : "f"(b.x), "f"(b.y));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(x), "l"(y));
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(d));
+    return r;
+}
+__device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 lo(const float4 &q) { return make_float2(q.x, q.y); }
+__device__ __forceinline__ float2 hi(const float4 &q) { return make_float2(q.z, q.w); }
+
+// Lh at the thread's 4 x RZ block from a [H][W] halo tile, as RZ x 2 pairs
+// (points 4tx, 4tx+1 and 4tx+2, 4tx+3 of each row).  Per lane:
+//   d1  = ((w[x-1] - w0) + (w[x+1] - w0)) + ((w[z-1] - w0) + (w[z+1] - w0))
+//   acc = c4 ((w[x-4] + w[x+4]) + (w[z-4] + w[z+4]))
+//   acc = c3 ((w[x-3] + w[x+3]) + (w[z-3] + w[z+3])) + acc,  then c2 likewise
+//   Lh  = c1 d1 + (LCR w0 + acc)
+// The z neighbours of a pair are halves of the float4 columns; the x
+// neighbours at odd offsets are re-paired from adjacent float4s.
 template <class C>
-__device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float (&L)[C::RZ][4],
-                                          float (&ctr)[C::RZ][4])
+__device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float2 (&L)[C::RZ][2],
+                                          float2 (&ctr)[C::RZ][2])
 {
     const float4 *s4 = reinterpret_cast<const float4 *>(sm);
     float4 col[C::RZ + 8];
@@ -156,59 +186,64 @@ __device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, 
         const float4 xm = s4[row * C::W4 + tx];
         const float4 xc = col[r + 4];
         const float4 xp = s4[row * C::W4 + tx + 2];
-        const float v[12] = {xm.x, xm.y, xm.z, xm.w, xc.x, xc.y, xc.z, xc.w, xp.x, xp.y, xp.z, xp.w};
+        // e[i] = (v[2i], v[2i+1]), o[i] = (v[2i+1], v[2i+2]) over v = xm | xc | xp
+        const float2 e[6] = {lo(xm), hi(xm), lo(xc), hi(xc), lo(xp), hi(xp)};
+        const float2 o[5] = {make_float2(xm.y, xm.z), make_float2(xm.w, xc.x), make_float2(xc.y, xc.z),
+                             make_float2(xc.w, xp.x), make_float2(xp.y, xp.z)};
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float cz = v[4 + c];
-            auto comp = [](const float4 &q, int cc) { return cc == 0 ? q.x : (cc == 1 ? q.y : (cc == 2 ? q.z : q.w)); };
-            const float d1 = ((v[3 + c] - cz) + (v[5 + c] - cz)) + ((comp(col[r + 3], c) - cz) + (comp(col[r + 5], c) - cz));
-            float acc = __fmul_rn(LC4, (v[c] + v[8 + c]) + (comp(col[r], c) + comp(col[r + 8], c)));
-            acc = fmaf(LC3, (v[1 + c] + v[7 + c]) + (comp(col[r + 1], c) + comp(col[r + 7], c)), acc);
-            acc = fmaf(LC2, (v[2 + c] + v[6 + c]) + (comp(col[r + 2], c) + comp(col[r + 6], c)), acc);
-            acc = fmaf(LCR, cz, acc);
-            L[r][c] = fmaf(LC1, d1, acc);
-            ctr[r][c] = cz;
+        for (int pr = 0; pr < 2; ++pr) {
+            // x neighbour at offset k - 4 of lanes 2pr, 2pr+1; z neighbour in column i
+            auto hx = [&](int k) { return (k & 1) ? o[(k - 1) / 2 + pr] : e[k / 2 + pr]; };
+            auto zc = [&](int i) { return pr == 0 ? lo(col[i]) : hi(col[i]); };
+            const float2 cz = zc(r + 4);
+            const float2 d1 = f2add(f2add(f2sub(hx(3), cz), f2sub(hx(5), cz)),
+                                    f2add(f2sub(zc(r + 3), cz), f2sub(zc(r + 5), cz)));
+            float2 acc = f2mul(splat(LC4), f2add(f2add(hx(0), hx(8)), f2add(zc(r), zc(r + 8))));
+            acc = f2fma(splat(LC3), f2add(f2add(hx(1), hx(7)), f2add(zc(r + 1), zc(r + 7))), acc);
+            acc = f2fma(splat(LC2), f2add(f2add(hx(2), hx(6)), f2add(zc(r + 2), zc(r + 6))), acc);
+            acc = f2fma(splat(LCR), cz, acc);
+            L[r][pr] = f2fma(splat(LC1), d1, acc);
+            ctr[r][pr] = cz;
         }
     }
 }
 
-// Sponge factors of one row of the thread's block: inv = 1 / (1 + a),
-// oma = 1 - a with a = max(a_z, a_x); exactly 1 in tiles without sponge.
-__device__ __forceinline__ void sponge_row(bool sponge, const float *az, int z, int NZ, const float (&axv)[4],
-                                           float (&inv)[4], float (&oma)[4])
+// Sponge factors of one row of the thread's block, as pairs: inv = 1 / (1 + a)
+// and nom = a - 1 (= -(1 - a) exactly) with a = max(a_z, a_x).
+__device__ __forceinline__ void sponge_row(const float *az, int z, int NZ, const float (&axv)[4], float2 (&inv)[2],
+                                           float2 (&nom)[2])
 {
-    if (!sponge) {
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            inv[c] = 1.0f;
-            oma[c] = 1.0f;
-        }
-        return;
-    }
     const float azv = az[min(z, NZ - 1)];
+    float iv[4], nm[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
         const float a = fmaxf(azv, axv[c]);
-        inv[c] = __frcp_rn(1.0f + a);
-        oma[c] = 1.0f - a;
+        iv[c] = __frcp_rn(1.0f + a);
+        nm[c] = a - 1.0f;
     }
+    inv[0] = make_float2(iv[0], iv[1]);
+    inv[1] = make_float2(iv[2], iv[3]);
+    nom[0] = make_float2(nm[0], nm[1]);
+    nom[1] = make_float2(nm[2], nm[3]);
 }
 
-__device__ __forceinline__ void f4(const float *p, float (&o)[4])
+__device__ __forceinline__ void f4(const float *p, float2 (&o)[2])
 {
     const float4 v = *reinterpret_cast<const float4 *>(p);
-    o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    o[0] = lo(v);
+    o[1] = hi(v);
 }
 
 // Store 4 consecutive x values at padded column x.. (skipping x >= NX).
-__device__ __forceinline__ void st4(float *p, const float (&o)[4], int x, int NX)
+__device__ __forceinline__ void st4(float *p, const float2 (&o)[2], int x, int NX)
 {
     if (x + 3 < NX) {
-        *reinterpret_cast<float4 *>(p) = make_float4(o[0], o[1], o[2], o[3]);
+        *reinterpret_cast<float4 *>(p) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
     } else {
+        const float w[4] = {o[0].x, o[0].y, o[1].x, o[1].y};
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (x + c < NX) p[c] = o[c];
+            if (x + c < NX) p[c] = w[c];
     }
 }
 
@@ -265,7 +300,7 @@ __device__ __forceinline__ void load_shot_tables(ShotTables &t, const int *src_z
 
 // Adds s_n to Q at the source node if it lies in the thread's block.
 template <class C>
-__device__ __forceinline__ void add_source(float (&Q)[C::RZ][4], int zrow0, int xb, int sz, int sx, float wav)
+__device__ __forceinline__ void add_source(float2 (&Q)[C::RZ][2], int zrow0, int xb, int sz, int sx, float wav)
 {
     const int dz = sz - zrow0, dx = sx - xb;
     if ((unsigned)dz < (unsigned)C::RZ && (unsigned)dx < 4u) {
@@ -273,18 +308,22 @@ __device__ __forceinline__ void add_source(float (&Q)[C::RZ][4], int zrow0, int 
         for (int r = 0; r < C::RZ; ++r)
 #pragma unroll
             for (int c = 0; c < 4; ++c)
-                if (r == dz && c == dx) Q[r][c] += wav;
+                if (r == dz && c == dx) {
+                    if (c & 1) Q[r][c >> 1].y += wav;
+                    else Q[r][c >> 1].x += wav;
+                }
     }
 }
 
-// o = (2 w - (1 - a) w_prev + C q) / (1 + a); a = 0 (SP false) off the sponge.
-// Every multiply-add is explicit (fmaf / __fmul_rn): the compiler has no
-// contraction freedom, so each tile shape computes bitwise the same values.
+// o = (2 w - (1 - a) w_prev + C q) / (1 + a); a = 0 (SP false) off the sponge,
+// where 2 w - w_prev is one rounding (2 w is exact).  Every operation is an
+// explicit correctly rounded one: the compiler has no contraction freedom, so
+// each tile shape computes bitwise the same values.
 template <bool SP>
-__device__ __forceinline__ float leapfrog(float w, float wprev, float cc, float q, float inv, float oma)
+__device__ __forceinline__ float2 leapfrog(float2 w, float2 wprev, float2 cc, float2 q, float2 inv, float2 nom)
 {
-    if constexpr (SP) return __fmul_rn(inv, fmaf(cc, q, fmaf(-oma, wprev, w + w)));
-    else return fmaf(cc, q, fmaf(2.0f, w, -wprev));
+    if constexpr (SP) return f2mul(inv, f2fma(cc, q, f2fma(nom, wprev, f2add(w, w))));
+    else return f2fma(cc, q, f2sub(f2add(w, w), wprev));
 }
 
 // One forward time step.  grid = (ntiles, k or 1, shot groups).  Vector j = 0
@@ -362,7 +401,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
             const float *sU = reinterpret_cast<const float *>(base);
             const float *sUp = reinterpret_cast<const float *>(base + C::HALOP);
 
-            float Q[C::RZ][4], uc[C::RZ][4];
+            float2 Q[C::RZ][2], uc[C::RZ][2];
             lap_block<C>(sU, tx, tz, Q, uc);
             add_source<C>(Q, zrow0, xb, tab.sz[i], tab.sx[i], wav);
             const int rb = tab.rb[i], re = tab.re[i];
@@ -371,13 +410,12 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
 #pragma unroll
                 for (int r = 0; r < C::RZ; ++r) {
                     const int z = zrow0 + r;
-                    float up[4], cc[4], inv[4], oma[4], o[4];
+                    float2 up[2], cc[2], inv[2] = {}, nom[2] = {}, o[2];
                     f4(sUp + (tz * C::RZ + r) * C::TX + 4 * tx, up);
                     f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
-                    if constexpr (SP) sponge_row(true, p.az, z, p.g.NZ, axv, inv, oma);
+                    if constexpr (SP) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        o[c] = leapfrog<SP>(uc[r][c], up[c], cc[c], Q[r][c], SP ? inv[c] : 1.f, SP ? oma[c] : 1.f);
+                    for (int h = 0; h < 2; ++h) o[h] = leapfrog<SP>(uc[r][h], up[h], cc[h], Q[r][h], inv[h], nom[h]);
                     if (z < p.g.NZ && xb < p.g.NX) st4(un + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
                 }
                 if (p.d_u && rb < re) {
@@ -389,22 +427,21 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
             if constexpr (BORN) {
                 const float *sD = reinterpret_cast<const float *>(base + C::HALOP + C::PTP);
                 const float *sDp = reinterpret_cast<const float *>(base + 2 * C::HALOP + C::PTP);
-                float Ld[C::RZ][4], dc[C::RZ][4];
+                float2 Ld[C::RZ][2], dc[C::RZ][2];
                 lap_block<C>(sD, tx, tz, Ld, dc);
                 const int fo = j * p.ns + s;
                 float *dn = p.ws + (unsigned long long)(p.f_dio + fo) * p.g.fsize;
 #pragma unroll
                 for (int r = 0; r < C::RZ; ++r) {
                     const int z = zrow0 + r;
-                    float dp[4], cc[4], bb[4], inv[4], oma[4], o[4];
+                    float2 dp[2], cc[2], bb[2], inv[2] = {}, nom[2] = {}, o[2];
                     f4(sDp + (tz * C::RZ + r) * C::TX + 4 * tx, dp);
                     f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
                     f4(sB + (tz * C::RZ + r) * C::TX + 4 * tx, bb);
-                    if constexpr (SP) sponge_row(true, p.az, z, p.g.NZ, axv, inv, oma);
+                    if constexpr (SP) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        o[c] = leapfrog<SP>(dc[r][c], dp[c], cc[c], fmaf(bb[c], Q[r][c], Ld[r][c]), SP ? inv[c] : 1.f,
-                                            SP ? oma[c] : 1.f);
+                    for (int h = 0; h < 2; ++h)
+                        o[h] = leapfrog<SP>(dc[r][h], dp[h], cc[h], f2fma(bb[h], Q[r][h], Ld[r][h]), inv[h], nom[h]);
                     if (z < p.g.NZ && xb < p.g.NX) st4(dn + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
                 }
                 if (p.d_du && rb < re) {
@@ -498,11 +535,11 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     // This step's image contribution of the CTA's shots, summed in shot order
     // in FP32 (at most 8 terms); it is added to the FP64 image once per step.
     // Double-precision arithmetic is slow on this part, so none runs per shot.
-    float acc[C::RZ][4];
+    float2 acc[C::RZ][2];
 #pragma unroll
     for (int r = 0; r < C::RZ; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
+        for (int h = 0; h < 2; ++h) acc[r][h] = make_float2(0.0f, 0.0f);
 
     bool ok = mbar_wait(&bars[2], 0, p.status);
     if (__syncthreads_or(!ok)) return;
@@ -532,7 +569,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
             const float *sU = reinterpret_cast<const float *>(base);
             const float *sL1 = reinterpret_cast<const float *>(base + C::HALOP);
             const float *sL2 = reinterpret_cast<const float *>(base + 2 * C::HALOP);
-            float Qu[C::RZ][4], ucen[C::RZ][4], Ll[C::RZ][4], lc[C::RZ][4];
+            float2 Qu[C::RZ][2], ucen[C::RZ][2], Ll[C::RZ][2], lc[C::RZ][2];
             lap_block<C>(sU, tx, tz, Qu, ucen);
             add_source<C>(Qu, zrow0, xb, tab.sz[i], tab.sx[i], wav);
             lap_block<C>(sL1, tx, tz, Ll, lc);
@@ -540,20 +577,20 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
 #pragma unroll
             for (int r = 0; r < C::RZ; ++r) {
                 const int z = zrow0 + r;
-                float l2[4], cc[4], inv[4], oma[4], o[4];
+                float2 l2[2], cc[2], inv[2] = {}, nom[2] = {}, o[2];
                 f4(sL2 + (tz * C::RZ + r) * C::TX + 4 * tx, l2);
                 f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
                 if (rb < re) {
-                    float src[4];
+                    float2 src[2];
                     f4(ssrc + (tz * C::RZ + r) * C::TX + 4 * tx, src);
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) Ll[r][c] += src[c];
+                    for (int h = 0; h < 2; ++h) Ll[r][h] = f2add(Ll[r][h], src[h]);
                 }
-                if constexpr (SP) sponge_row(true, p.az, z, p.g.NZ, axv, inv, oma);
+                if constexpr (SP) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    o[c] = leapfrog<SP>(lc[r][c], l2[c], cc[c], Ll[r][c], SP ? inv[c] : 1.f, SP ? oma[c] : 1.f);
-                    acc[r][c] = fmaf(o[c], Qu[r][c], acc[r][c]);
+                for (int h = 0; h < 2; ++h) {
+                    o[h] = leapfrog<SP>(lc[r][h], l2[h], cc[h], Ll[r][h], inv[h], nom[h]);
+                    acc[r][h] = f2fma(o[h], Qu[r][h], acc[r][h]);
                 }
                 if (z < p.g.NZ && xb < p.g.NX) st4(ln + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
             }
@@ -571,7 +608,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
         const size_t off = (size_t)(z + GH) * p.g.P + (xb + GH);
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            if (xb + c < p.g.NX) im[off + c] += (double)acc[r][c];
+            if (xb + c < p.g.NX) im[off + c] += (double)((c & 1) ? acc[r][c >> 1].y : acc[r][c >> 1].x);
     }
 }
 
