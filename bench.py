@@ -68,6 +68,23 @@ def csrc_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def dram_traffic() -> dict:
+    """ncu DRAM bytes (read + write) per launch, per kernel kind, from profiles/dram_traffic.txt.
+
+    Each line: <kind> <hash of the kernel sources they were taken on> <bytes>; '#' starts a comment.
+    """
+    out = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
+            for ln in f:
+                ln = ln.split("#", 1)[0].split()
+                if len(ln) == 3:
+                    out[ln[0]] = (ln[1], int(ln[2]))
+    except OSError:
+        pass
+    return out
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -199,7 +216,11 @@ def run_ours(args, w):
     v = torch.tensor(w.v, dtype=torch.float32, device=dev)
     st = torch.cuda.current_stream(dev)
     graphs = args.workload == "batched"
-    tiles = P.autotune(k=w.k)                 # fastest tile shape per kernel kind for this grid
+    if args.tiles:                            # fixed tiles (profiling runs: no tuning launches)
+        P.set_tiles(args.tiles)
+        tiles = P.tiles()
+    else:
+        tiles = P.autotune(k=w.k)             # fastest tile shape per kernel kind for this grid
     if graphs:
         P.set_graphs(True)
 
@@ -283,7 +304,7 @@ def run_ours(args, w):
         pk, pk_kind = peaks()
         NZ, NX = w.nz + 2 * w.nb, w.nx + 2 * w.nb
         pts = NZ * NX * w.ns
-        alg = {"fwd": pts * (16 + 16 * w.k), "advance": pts * 16, "adj": pts * w.k * 20}
+        alg = {"fwd": pts * (16 + 16 * w.k), "advance": pts * 16, "adj": pts * (4 + 16 * w.k)}
         kernels = {}
         for kind, (n, tms) in prof.items():
             if n:
@@ -295,13 +316,9 @@ def run_ours(args, w):
         n_dom, t_dom = prof[dom]
         achieved = alg[dom] * n_dom / (t_dom / 1e3) / 1e9
         traffic = None
-        try:
-            tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
-            ent = tr.get(dom)
-            if ent and ent.get("csrc") == csrc_hash():
-                traffic = ent["dram_bytes_per_launch"]
-        except Exception:
-            pass
+        ent = dram_traffic().get(dom)
+        if ent and ent[0] == csrc_hash():
+            traffic = ent[1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
                 "algorithmic_bytes_per_launch": alg[dom], "peak_source": pk_kind}
@@ -469,6 +486,8 @@ def main():
                     help="paper: 384x1152, 32 shots, 3000 steps, 1 vector (default); batched: the 64x64 model "
                          "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tiles", type=int, nargs=3, default=None, metavar=("FWD", "ADVANCE", "ADJ"),
+                    help="tile configurations instead of autotuning (profiling runs)")
     args = ap.parse_args()
     from paper_2507_10804_gb300 import synth
     if args.workload == "serve":
