@@ -262,18 +262,28 @@ int hv_poll(hv_server *s, unsigned long long id, int *status);
 int hv_wait(hv_server *s, unsigned long long id, double timeout_s, int *status);
 int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *info);
 
-/* Tile configurations.  The stencil kernels come in a small menu of tile
- * shapes (TX x TZ points per CTA); the choice per kernel kind (cfg[0]:
- * forward + Born step, cfg[1]: forward-only step, cfg[2]: adjoint step) does
- * not change any result bit, only speed.
+/* Tile configurations.  The stencil kernels come in a small menu of
+ * configurations: a tile shape (TX x TZ points per CTA), a copy-pipeline depth
+ * (stages; stages - 1 shots in flight per CTA) and the number of 8-shot groups
+ * one CTA walks.  The choice per kernel kind (cfg[0]: forward + Born step,
+ * cfg[1]: forward-only step, cfg[2]: adjoint step) does not change any result
+ * bit, only speed.
+ *  - hv_tile_menu_size: number of menu entries.
  *  - hv_tile_menu: shape of menu entry `index` (HV_EINVAL past the end).
+ *  - hv_tile_menu_info: info[5] = {TX, TZ, threads per CTA, stages, shot
+ *    groups per CTA} of entry `index` (HV_EINVAL past the end or info NULL).
  *  - hv_autotune: times every entry for the three kernels on this handle's
  *    grid with k vectors, using `ws` (at least hv_workspace_size(HV_OP_HV, k,
  *    ckpt = 1) bytes; contents overwritten) on `stream`, keeps the fastest
  *    in the handle and writes the choice to chosen[3] and the per-launch
- *    times to ms[menu * 3] (either may be NULL).  Synchronous.
+ *    times to ms[menu * 3] (either may be NULL).  Synchronous.  In the
+ *    dataflow launch mode the three choices share one tile shape (the shape
+ *    of least weighted time, weights 1 / 1.8 / 1 for the three kinds).
+ *    Tune after setting the launch mode.
  *  - hv_set_tiles / hv_get_tiles: apply or read a choice (e.g. a cached one). */
+int hv_tile_menu_size(void);
 int hv_tile_menu(int index, int *TX, int *TZ);
+int hv_tile_menu_info(int index, int *info);
 int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void *stream, int *chosen, float *ms);
 int hv_set_tiles(hv_handle *h, const int *cfg);
 int hv_get_tiles(const hv_handle *h, int *cfg);
@@ -285,6 +295,27 @@ int hv_get_tiles(const hv_handle *h, int *cfg);
  * the same key replay it with one launch.  The workspace contents are not
  * part of the key: they are rewritten by every call. */
 int hv_set_graphs(hv_handle *h, int enable);
+
+/* Launch modes of the stencil steps (every mode gives bitwise the same
+ * results; graphs captured in one mode are not reused in another):
+ *  - HV_LAUNCH_PLAIN: each step starts after the previous kernel completes.
+ *  - HV_LAUNCH_PDL (default): programmatic dependent launch; a step's CTAs
+ *    become resident and do their set-up while the previous step's last CTAs
+ *    run, and touch no field before every earlier kernel has completed.
+ *  - HV_LAUNCH_DATAFLOW: as PDL, and a CTA starts its tile as soon as the
+ *    previous steps have finished that tile and its 8 neighbours (per-tile
+ *    completion counters in the workspace, acquire/release at GPU scope,
+ *    waits bounded by a deadline), so the tail of one step overlaps the start
+ *    of the next.  Used when the three kernel kinds share a tile shape and
+ *    nothing else was launched between two steps; otherwise the step falls
+ *    back to the PDL wait.  On GB300 the release each CTA makes before it
+ *    exits costs more than the overlap gains (about 3% slower than PDL on the
+ *    384 x 1152 benchmark grid), hence not the default.
+ * HV_EINVAL for another mode. */
+#define HV_LAUNCH_PLAIN 0
+#define HV_LAUNCH_PDL 1
+#define HV_LAUNCH_DATAFLOW 2
+int hv_set_launch_mode(hv_handle *h, int mode);
 
 /* Profiling.  While enabled on a handle, each kernel launch the handle makes
  * is bracketed by CUDA events on the launching stream.  hv_profile_read waits

@@ -22,6 +22,7 @@ HV_CKPT_ALL = -1
 HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD, HV_OP_MISFIT = range(7)
 HV_K_FWD, HV_K_ADVANCE, HV_K_ADJ, HV_K_OTHER = range(4)
 HV_K_COUNT = 4
+HV_LAUNCH_PLAIN, HV_LAUNCH_PDL, HV_LAUNCH_DATAFLOW = range(3)
 
 
 class HvGrid(ctypes.Structure):
@@ -75,7 +76,10 @@ _SIGS = {
                             c_int),
     "hv_approx_apply": ([c_void_p, fp, c_int, fp, c_int, c_void_p], c_int),
     "hv_approx_destroy": ([c_void_p], c_int),
+    "hv_tile_menu_size": ([], c_int),
+    "hv_set_launch_mode": ([c_void_p, c_int], c_int),
     "hv_tile_menu": ([c_int, ip, ip], c_int),
+    "hv_tile_menu_info": ([c_int, ip], c_int),
     "hv_autotune": ([c_void_p, c_int, fp, c_size_t, c_void_p, ip, ctypes.POINTER(ctypes.c_float)], c_int),
     "hv_set_tiles": ([c_void_p, ip], c_int),
     "hv_get_tiles": ([c_void_p, ip], c_int),

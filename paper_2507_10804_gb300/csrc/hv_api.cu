@@ -97,6 +97,7 @@ struct Layout {
     int G = 1;                // adjoint shot groups (partial images)
     size_t fb = 0;            // bytes of one field batch (all shots)
     size_t C = 0, b = 0, zero = 0, work = 0, store = 0, D = 0, dd = 0, img = 0, part = 0, total = 0;
+    size_t cnt = 0, cnt_bytes = 0;   // per (shot group, tile) step counters (dataflow launch mode)
     size_t fields_end = 0;    // the field regions (all first) end here: the tensor maps cover [0, fields_end)
 };
 
@@ -136,6 +137,8 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
     if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.dd = take(ndata * sizeof(float));
     if (adjoint) L.img = take((size_t)L.G * k * h->fsize * sizeof(double));
     if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.part = take(kResidualBlocks * sizeof(double));
+    L.cnt_bytes = (size_t)hvk::adj_groups(h) * hvk::max_tiles(h) * sizeof(int);
+    L.cnt = take(L.cnt_bytes);
     L.total = o;
     return HV_OK;
 }
@@ -197,6 +200,26 @@ struct Exec {
     int cur_i = -1, prev_i = -1;               // pool indices of the current state (-1: zero batch)
     const float *cur, *prev;
     int j;               // current state index: cur = u^j, prev = u^{j-1}
+    // Dataflow ordering of the stencil steps (HV_LAUNCH_DATAFLOW): the step
+    // counters, the items of all steps launched so far in this call, and the
+    // calling thread's launch count right after the last step.
+    int *cnt = nullptr;
+    int need = 0;
+    long long last_tl = -1;
+
+    // Ordering of the next stencil step, which completes `items` items per
+    // (shot group, tile): tile waits if the previous kernel this thread
+    // launched was the previous step, else a wait for every earlier kernel.
+    hvk::StepDeps deps(int items)
+    {
+        hvk::StepDeps d;
+        d.cnt = cnt;
+        d.need = need;
+        d.flow = cnt != nullptr && last_tl == hvk::thread_launches();
+        need += items;
+        return d;
+    }
+    void launched_step() { last_tl = hvk::thread_launches(); }
 
     float *batch(char *base, size_t i) const { return reinterpret_cast<float *>(base + i * L.fb); }
     float *Dbuf(int parity) const { return reinterpret_cast<float *>(reinterpret_cast<char *>(D) + (size_t)parity * k * L.fb); }
@@ -227,6 +250,12 @@ struct Exec {
         cur = prev = zero;
         cur_i = prev_i = -1;
         j = 0;
+        const hvi::Tiling t0 = hvk::tiling(h, h->cfg[0]), t1 = hvk::tiling(h, h->cfg[1]), t2 = hvk::tiling(h, h->cfg[2]);
+        const bool one_tiling = t0.TX == t1.TX && t0.TX == t2.TX && t0.TZ == t1.TZ && t0.TZ == t2.TZ;
+        if (h->launch_mode == HV_LAUNCH_DATAFLOW && one_tiling) {
+            cnt = reinterpret_cast<int *>(ws + L.cnt);
+            HV_CK(cudaMemsetAsync(cnt, 0, L.cnt_bytes, st));
+        }
         return hvk::make_maps(h, ws, (long long)(L.fields_end / (h->fsize * sizeof(float))), &maps);
     }
 
@@ -255,7 +284,9 @@ struct Exec {
         }
         a.d_u = d_u;
         const int cfg = born ? h->cfg[0] : h->cfg[1];
+        a.deps = deps(born ? k : 1);
         HV_RT(hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), maps, a, st));
+        launched_step();
         prev = cur;
         prev_i = cur_i;
         cur = next;
@@ -306,7 +337,10 @@ struct Exec {
         a.n = n;
         a.k = kk;
         a.G = L.G;
-        return hvk::launch_adj(h, h->cfg[2], rectiles_for(h, hvk::tiling(h, h->cfg[2])), maps, a, st);
+        a.deps = deps(kk);
+        HV_RT(hvk::launch_adj(h, h->cfg[2], rectiles_for(h, hvk::tiling(h, h->cfg[2])), maps, a, st));
+        launched_step();
+        return HV_OK;
     }
 
     // Zero the ghost bands of every field batch this call's kernels write:
@@ -359,10 +393,10 @@ const std::vector<hvi::Action> *schedule_for(hv_handle *h, int slots)
 int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
                      const Layout &L, cudaStream_t st);
 
-std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg)
+std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode)
 {
     char buf[160];
-    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2]);
+    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode);
     return buf;
 }
 
@@ -388,7 +422,7 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     // CUDA graph and replayed (hv_set_graphs).
     const bool graph = born && h->graphs_on && !h->prof_on;
     if (graph) {
-        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg);
+        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode);
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaStream_t cs = h->capture_stream;
@@ -929,6 +963,16 @@ extern "C" int hv_tile_menu(int index, int *TX, int *TZ)
     return HV_OK;
 }
 
+extern "C" int hv_tile_menu_size(void) { return hvk::tile_menu_size(); }
+
+extern "C" int hv_tile_menu_info(int index, int *info)
+{
+    if (index < 0 || index >= hvk::tile_menu_size()) return hvi::fail(HV_EINVAL, "tile configuration %d not in the menu", index);
+    if (!info) return hvi::fail(HV_EINVAL, "null output");
+    hvk::menu_info(index, info);
+    return HV_OK;
+}
+
 extern "C" int hv_set_tiles(hv_handle *h, const int *cfg)
 {
     if (!h || !cfg) return hvi::fail(HV_EINVAL, "null handle or configuration");
@@ -953,6 +997,14 @@ extern "C" int hv_set_graphs(hv_handle *h, int enable)
     return HV_OK;
 }
 
+extern "C" int hv_set_launch_mode(hv_handle *h, int mode)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    if (mode < HV_LAUNCH_PLAIN || mode > HV_LAUNCH_DATAFLOW) return hvi::fail(HV_EINVAL, "launch mode %d", mode);
+    h->launch_mode = mode;
+    return HV_OK;
+}
+
 // Times every tile configuration of the three stencil kernels on this
 // handle's grid with k vectors (on zeroed fields: the kernels have no
 // data-dependent work) and keeps the fastest per kernel kind.
@@ -970,6 +1022,7 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
     HV_CK(cudaEventCreate(&e0));
     HV_CK(cudaEventCreate(&e1));
     constexpr int kReps = 6;
+    std::vector<float> tm((size_t)nmenu * 3, 1e30f);
     float best[3] = {1e30f, 1e30f, 1e30f};
     int arg[3] = {0, 0, 0};
     int rc = HV_OK;
@@ -999,6 +1052,7 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
             cudaEventElapsedTime(&t, e0, e1);
             t /= kReps;
             if (ms) ms[c * 3 + kind] = t;
+            tm[c * 3 + kind] = t;
             if (t < best[kind]) {
                 best[kind] = t;
                 arg[kind] = c;
@@ -1008,6 +1062,34 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc != HV_OK) return rc;
+    if (h->launch_mode == HV_LAUNCH_DATAFLOW) {
+        // Dataflow ordering needs one tile shape for the three kinds: take the
+        // shape with the least weighted time (a binomially checkpointed H v
+        // runs about 1.8 recompute steps per forward+Born and adjoint step),
+        // then the fastest entry of that shape per kind.
+        const float wgt[3] = {1.0f, 1.8f, 1.0f};
+        float best_sum = 1e30f;
+        for (int s = 0; s < nmenu; ++s) {
+            const hvi::Tiling ts = hvk::tiling(h, s);
+            int pick[3] = {s, s, s};
+            float sum = 0.f;
+            for (int kind = 0; kind < 3; ++kind) {
+                float bt = 1e30f;
+                for (int c = 0; c < nmenu; ++c) {
+                    const hvi::Tiling tc = hvk::tiling(h, c);
+                    if (tc.TX == ts.TX && tc.TZ == ts.TZ && tm[c * 3 + kind] < bt) {
+                        bt = tm[c * 3 + kind];
+                        pick[kind] = c;
+                    }
+                }
+                sum += wgt[kind] * bt;
+            }
+            if (sum < best_sum) {
+                best_sum = sum;
+                for (int i = 0; i < 3; ++i) arg[i] = pick[i];
+            }
+        }
+    }
     for (int i = 0; i < 3; ++i) h->cfg[i] = arg[i];
     if (chosen)
         for (int i = 0; i < 3; ++i) chosen[i] = arg[i];

@@ -80,6 +80,8 @@ struct hv_handle {
     // CUDA graphs of the H v launch sequence (hv_set_graphs), keyed by workspace and shape
     bool graphs_on = false;
     cudaStream_t capture_stream = nullptr;
+    // how stencil steps are ordered after one another (hv_set_launch_mode)
+    int launch_mode = HV_LAUNCH_PDL;
     std::map<std::string, cudaGraphExec_t> graphs;
     // profiling (hv_profile)
     bool prof_on = false;
@@ -91,13 +93,15 @@ namespace hvk {
 
 // Tile configurations (hv_stencil.cu): the menu size and the tiling of one entry.
 int tile_menu_size();
+int max_tiles(const hv_handle *h);    // most tiles any menu entry cuts the handle's grid into
+void menu_info(int cfg, int *info);   // {TX, TZ, threads, stages, shot groups per CTA}
 hvi::Tiling tiling(const hv_handle *h, int cfg);
 int prepare_kernels(const hv_handle *h);
 
 // Tensor maps of one call's workspace, viewed as an array of fields
 // (x, z, field index): `halo` copies a tile with its 4-cell halo, `pt` the
 // tile's own points.  Opaque CUtensorMap bytes (128 each).
-constexpr int kMaxTileMenu = 8;
+constexpr int kMaxTileMenu = 16;
 struct TmaMaps {
     alignas(64) unsigned char halo[kMaxTileMenu][128];   // per tile configuration
     alignas(64) unsigned char pt[kMaxTileMenu][128];
@@ -105,6 +109,19 @@ struct TmaMaps {
     long long nfields = 0;
 };
 int make_maps(const hv_handle *h, void *ws, long long nfields, TmaMaps *m);
+
+// Ordering of a stencil step after the previous ones (see hv_set_launch_mode).
+// cnt: per (shot group, tile) counts of completed step items in this call, or
+// nullptr; a step adds one per (vector, group, tile) it finishes.  With
+// `flow`, a CTA waits only until its tile and the 8 neighbours have reached
+// `need` (the items of all earlier steps of the call) instead of waiting for
+// the whole previous grid; the caller sets it only when the previous kernel on
+// the stream was a counting stencil step with the same tiling.
+struct StepDeps {
+    int *cnt = nullptr;
+    int need = 0;
+    bool flow = false;
+};
 
 struct FwdLaunch {
     const float *u_cur, *u_prev;   // field batches [ns][fsize]
@@ -116,6 +133,7 @@ struct FwdLaunch {
     float *d_u;                    // [ns][nt][nr] samples of u^{n+1} or nullptr
     float *d_du;                   // [k][ns][nt][nr] samples of du^{n+1} or nullptr
     int n, k;
+    StepDeps deps;
 };
 int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
                cudaStream_t st);
@@ -130,6 +148,7 @@ struct AdjLaunch {
     float rscale;                  // multiplies r (h^2 / sigma^2 or h^2)
     double *img;                   // [G][k][fsize] partial images
     int n, k, G;
+    StepDeps deps;
 };
 int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
                cudaStream_t st);
@@ -148,5 +167,6 @@ int launch_setup(hv_handle *h, cudaStream_t st);
 // Process-wide kernel launch counter (hv_kernel_launches).
 void count_launch();
 long long launches_so_far();
+long long thread_launches();   // kernels launched by the calling thread
 
 }  // namespace hvk

@@ -175,8 +175,14 @@ int cuda_check(const char *what)
 }  // namespace
 
 static std::atomic<long long> g_launches{0};
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+static thread_local long long t_launches = 0;
+void count_launch()
+{
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    ++t_launches;
+}
 long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+long long thread_launches() { return t_launches; }
 
 int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float *C, float *b, cudaStream_t st)
 {

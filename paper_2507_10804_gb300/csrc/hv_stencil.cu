@@ -27,6 +27,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -43,12 +44,18 @@ constexpr float LC3 = (float)(8.0 / 315.0);
 constexpr float LC4 = (float)(-1.0 / 560.0);
 
 constexpr int kShotsPerGroup = 8;
-constexpr int kTileMenu = 8;       // number of tile configurations (with_cfg)
+constexpr int kTileMenu = 16;      // number of tile configurations (with_cfg)
+static_assert(kTileMenu <= kMaxTileMenu, "the bulk-copy descriptors have a slot per configuration");
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
-template <int BX_, int BZ_, int RZ_>
+// BX x BZ threads, each on 4 x RZ points; ST copy stages (shots in flight per
+// CTA = ST - 1); GPC shot groups of 8 walked by one CTA.  The last two change
+// neither the arithmetic nor its order: every configuration gives bitwise the
+// same fields and images.
+template <int BX_, int BZ_, int RZ_, int ST_ = 2, int GPC_ = 1>
 struct Cfg {
-    static constexpr int BX = BX_, BZ = BZ_, RZ = RZ_;
+    static constexpr int BX = BX_, BZ = BZ_, RZ = RZ_, ST = ST_, GPC = GPC_;
+    static_assert(ST >= 2 && ST <= 4 && GPC >= 1 && GPC <= 4, "pipeline depth and shot groups per CTA");
     static constexpr int NT = BX * BZ;
     static constexpr int TX = 4 * BX, TZ = RZ * BZ;
     static constexpr int W = TX + 2 * GH, H = TZ + 2 * GH;
@@ -67,6 +74,14 @@ using Cfg128x16 = Cfg<32, 8, 2>;   // 256 threads
 using Cfg64x8 = Cfg<16, 4, 2>;     // 64 threads
 using Cfg32x16 = Cfg<8, 8, 2>;     // 64 threads
 using Cfg128x8 = Cfg<32, 4, 2>;    // 128 threads
+using Cfg32x16s3 = Cfg<8, 8, 2, 3, 1>;     // three stages
+using Cfg32x16g4 = Cfg<8, 8, 2, 2, 4>;     // 32 shots per CTA
+using Cfg32x16s3g4 = Cfg<8, 8, 2, 3, 4>;
+using Cfg128x8s3 = Cfg<32, 4, 2, 3, 1>;
+using Cfg128x8g4 = Cfg<32, 4, 2, 2, 4>;
+using Cfg128x8s3g4 = Cfg<32, 4, 2, 3, 4>;
+using Cfg64x16s3g2 = Cfg<16, 8, 2, 3, 2>;
+using Cfg64x8s3g4 = Cfg<16, 4, 2, 3, 4>;
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
@@ -120,6 +135,84 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
         }
     }
     return true;
+}
+
+// Programmatic dependent launch.  A step launched with the programmatic
+// stream-serialization attribute may start while the previous step's last CTAs
+// still run; it reads nothing that an earlier kernel wrote, and writes nothing,
+// before grid_dependency_wait() returns (which is when every prerequisite grid
+// has completed and its memory operations are visible).  A step lets the next
+// one launch once it has passed its own wait, so at most two steps overlap and
+// everything before the previous step has finished.  Both are no-ops in a
+// kernel launched without the attribute.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_dependent_launch()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Dataflow between steps.  Every CTA adds one to the counter of each (shot
+// group, tile) item it finishes, after all its threads' stores (bar.sync, then
+// a releasing reduction at GPU scope by thread 0).  A CTA of a later step acquires the
+// counters of its tile and the 8 neighbours (the stencil reaches 4 cells,
+// less than a tile) until each has reached `need`, the items of all earlier
+// steps of the call; the neighbours' earlier steps then are complete too,
+// since each of their items waited the same way.  The bulk copies that follow
+// read through the async proxy, hence the proxy fence after the acquire.
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void publish_item(int *c)
+{
+    asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(c) : "memory");
+}
+
+// Thread 0: waits (bounded) until tile `tile` and its neighbours have `need`
+// completed items of shot group g.  false after the deadline (status set) or
+// when another CTA has already reported an error.
+__device__ bool wait_neighbourhood(const int *cnt, int g, int tile, int ntx, int ntiles, int need, int *status)
+{
+    const int ntz = ntiles / ntx;
+    const int tz = tile / ntx, tx = tile - tz * ntx;
+    const int *row = cnt + (size_t)g * ntiles;
+    unsigned long long t0 = 0;
+    for (int dz = -1; dz <= 1; ++dz)
+        for (int dx = -1; dx <= 1; ++dx) {
+            const int z = tz + dz, x = tx + dx;
+            if (z < 0 || z >= ntz || x < 0 || x >= ntx) continue;
+            const int *c = row + z * ntx + x;
+            while (ld_acquire(c) < need) {
+                if (t0 == 0) t0 = globaltimer();
+                if (*(volatile int *)status != 0) return false;
+                if (globaltimer() - t0 > kWaitNs) {
+                    atomicExch(status, HV_ETIMEOUT);
+                    return false;
+                }
+                __nanosleep(128);
+            }
+        }
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    return true;
+}
+
+// The CTA's wait for the data of earlier steps: tile waits for every shot
+// group of shots [s0, s1) in dataflow mode, else the grid-dependency wait.
+// false if the CTA must give up (every thread gets the same answer).
+__device__ __forceinline__ bool wait_for_inputs(bool flow, const int *cnt, int s0, int s1, int gsz, int tile, int ntx,
+                                                int ntiles, int need, int *status)
+{
+    bool ok = true;
+    if (flow) {
+        if (threadIdx.x == 0)
+            for (int g = s0 / gsz; g * gsz < s1 && ok; ++g) ok = wait_neighbourhood(cnt, g, tile, ntx, ntiles, need, status);
+    } else {
+        grid_dependency_wait();
+    }
+    return !__syncthreads_or(!ok);
 }
 
 // 3D tiled bulk copy global -> shared, completion counted on `bar`.
@@ -262,28 +355,33 @@ struct FwdParams {
     const float *az, *ax, *wavelet;
     const int *src_zx, *rt_off, *rt_rec, *rt_pos;
     int *status;
-    int n, nt, nr, ns, k, spg;
+    int n, nt, nr, ns, k, spg, gsz;
+    int *cnt;                   // step counters per (shot group, tile), or nullptr
+    int need, flow;             // dataflow ordering (StepDeps)
     Geo g;
 };
 
+constexpr int kMaxSpg = 32;   // shots per CTA, upper bound (per-CTA shot tables)
+
+// Per-CTA copy of the shot tables of its shots: source node and the range of
+// this tile's receivers, for every shot (read once instead of once per shot).
+struct ShotTables {
+    int sz[kMaxSpg], sx[kMaxSpg], rb[kMaxSpg], re[kMaxSpg];
+};
+constexpr int kTablesBytes = 512;
+static_assert(sizeof(ShotTables) <= kTablesBytes, "shot tables fit their shared-memory slot");
+static_assert(4 * kShotsPerGroup <= kMaxSpg, "four shot groups fit the shot tables");
+
+// Shared memory: ST stages, the coefficient tiles, ST + 1 mbarriers, the shot tables.
 template <class C, bool BORN>
 struct FwdSmem {
     static constexpr int STAGE = C::HALOP + C::PTP + (BORN ? C::HALOP + C::PTP : 0);
     static constexpr int STAGE_TX = C::HALO + C::PT + (BORN ? C::HALO + C::PT : 0);   // bytes each stage receives
     static constexpr int COEF = C::PTP * (BORN ? 2 : 1);
     static constexpr int COEF_TX = C::PT * (BORN ? 2 : 1);
-    static constexpr int BYTES = 2 * STAGE + COEF + 64 + 128;   // + barriers + shot tables
+    static constexpr int BARS = C::ST * STAGE + COEF;
+    static constexpr int BYTES = BARS + 64 + kTablesBytes;
 };
-
-constexpr int kMaxSpg = 8;   // shots per group, upper bound (per-CTA shot tables)
-
-// Per-CTA copy of the shot tables of its group: source node and the range of
-// this tile's receivers, for every shot (read once instead of once per shot).
-struct ShotTables {
-    int sz[kMaxSpg], sx[kMaxSpg], rb[kMaxSpg], re[kMaxSpg];
-};
-static_assert(sizeof(ShotTables) <= 128, "shot tables fit their shared-memory slot");
-static_assert(kShotsPerGroup <= kMaxSpg, "shot groups fit the shot tables");
 
 __device__ __forceinline__ void load_shot_tables(ShotTables &t, const int *src_zx, const int *rt_off, int s0, int n,
                                                  int tile, int ntiles)
@@ -326,6 +424,14 @@ __device__ __forceinline__ float2 leapfrog(float2 w, float2 wprev, float2 cc, fl
     else return f2fma(cc, q, f2sub(f2add(w, w), wprev));
 }
 
+// After a failed wait: wait (bounded) for the copies of items [from, to) still
+// in flight, so that none lands after the CTA has exited.
+template <int ST>
+__device__ __forceinline__ void drain_stages(uint64_t *bars, int from, int to, int *status)
+{
+    for (int q = from; q < to; ++q) mbar_wait(&bars[q % ST], (q / ST) & 1, status);
+}
+
 // One forward time step.  grid = (ntiles, k or 1, shot groups).  Vector j = 0
 // writes u^{n+1}; every CTA recomputes Q^n = Lh u^n + s_n from its own tile.
 template <class C, bool BORN>
@@ -333,10 +439,10 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
 {
     using S = FwdSmem<C, BORN>;
     extern __shared__ __align__(128) unsigned char smem[];
-    float *sC = reinterpret_cast<float *>(smem + 2 * S::STAGE);
+    float *sC = reinterpret_cast<float *>(smem + C::ST * S::STAGE);
     float *sB = sC + C::PTP / 4;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + S::COEF);
-    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + 2 * S::STAGE + S::COEF + 64);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::BARS);   // [0, ST): stages, [ST]: coefficients
+    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + S::BARS + 64);
 
     const int tile = blockIdx.x, j = blockIdx.y, grp = blockIdx.z;
     const int tzi = tile / p.g.ntx, txi = tile - tzi * p.g.ntx;
@@ -347,7 +453,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     const bool write_u = p.f_unext >= 0 && j == 0;
 
     auto issue = [&](int i) {
-        const int st = i & 1, s = s0 + i;
+        const int st = i % C::ST, s = s0 + i;
         unsigned char *base = smem + st * S::STAGE;
         mbar_expect_tx(&bars[st], S::STAGE_TX);
         tma_load(base, &p.map_halo, x0, z0, p.f_ucur + s, &bars[st]);
@@ -360,21 +466,12 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     };
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int q = 0; q <= C::ST; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
+    // Set-up from the handle's constant tables only (written before any step):
+    // with programmatic dependent launch this overlaps the previous step's tail.
     load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&bars[2], S::COEF_TX);
-        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[2]);
-        if constexpr (BORN) tma_load(sB, &p.map_pt, x0 + GH, z0 + GH, p.f_b + j, &bars[2]);
-        issue(0);
-        if (nitems > 1) issue(1);
-    }
-
     // Tiles entirely inside the interior have a = 0 and take the short update.
     const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
                           x0 + C::TX <= p.g.nb + p.g.nx);
@@ -383,18 +480,30 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
 #pragma unroll
         for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
     const float wav = p.wavelet[p.n];
+    // From here on the fields of earlier steps are complete and visible.
+    if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[C::ST], S::COEF_TX);
+        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[C::ST]);
+        if constexpr (BORN) tma_load(sB, &p.map_pt, x0 + GH, z0 + GH, p.f_b + j, &bars[C::ST]);
+        for (int q = 0; q < C::ST && q < nitems; ++q) issue(q);
+    }
+    allow_dependent_launch();
 
-    bool ok = mbar_wait(&bars[2], 0, p.status);
-    if (__syncthreads_or(!ok)) return;
+    bool ok = mbar_wait(&bars[C::ST], 0, p.status);
+    if (__syncthreads_or(!ok)) {
+        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
+        return;
+    }
 
     auto run = [&](auto sp_tag) {
         constexpr bool SP = decltype(sp_tag)::value;
         for (int i = 0; i < nitems; ++i) {
-            const int st = i & 1, s = s0 + i;
-            ok = mbar_wait(&bars[st], (i >> 1) & 1, p.status);
+            const int st = i % C::ST, s = s0 + i;
+            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status);
             if (__syncthreads_or(!ok)) {
-                // a copy did not arrive: let the other stage drain (bounded), then give up
-                if (i + 1 < nitems) mbar_wait(&bars[st ^ 1], ((i + 1) >> 1) & 1, p.status);
+                // a copy did not arrive: let the other stages drain (bounded), then give up
+                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status);
                 return;
             }
             const unsigned char *base = smem + st * S::STAGE;
@@ -451,7 +560,11 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                 }
             }
             __syncthreads();                       // every thread is done with stage st
-            if (threadIdx.x == 0 && i + 2 < nitems) issue(i + 2);
+            if (threadIdx.x == 0) {
+                if (p.cnt && ((s + 1) % p.gsz == 0 || i + 1 == nitems))
+                    publish_item(p.cnt + (size_t)(s / p.gsz) * p.g.ntiles + tile);
+                if (i + C::ST < nitems) issue(i + C::ST);
+            }
         }
     };
     if (sponge) run(std::true_type{});
@@ -469,7 +582,9 @@ struct AdjParams {
     const float *az, *ax, *wavelet;
     const int *src_zx, *rt_off, *rt_rec, *rt_pos;
     int *status;
-    int n, nt, nr, ns, k, spg;
+    int n, nt, nr, ns, k, spg, gsz;
+    int *cnt;
+    int need, flow;
     Geo g;
 };
 
@@ -477,21 +592,23 @@ template <class C>
 struct AdjSmem {
     static constexpr int STAGE = 2 * C::HALOP + C::PTP;
     static constexpr int STAGE_TX = 2 * C::HALO + C::PT;
-    static constexpr int BYTES = 2 * STAGE + C::PTP /* C */ + C::PTP /* sources */ + 64 + 128;
+    static constexpr int BARS = C::ST * STAGE + C::PTP /* C */ + C::PTP /* sources */;
+    static constexpr int BYTES = BARS + 64 + kTablesBytes;
 };
 
-// One adjoint time step with zero-lag imaging.  grid = (ntiles, k, shot
-// groups); the CTA sums its shots' image contributions in shot order and adds
-// them to its group's FP64 partial image once per step.
+// One adjoint time step with zero-lag imaging.  grid = (ntiles, k, blocks of
+// GPC shot groups); for each group of 8 shots the CTA sums the shots' image
+// contributions in shot order and adds them to the group's FP64 partial image
+// once per step.
 template <class C>
 __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjParams p)
 {
     using S = AdjSmem<C>;
     extern __shared__ __align__(128) unsigned char smem[];
-    float *sC = reinterpret_cast<float *>(smem + 2 * S::STAGE);
+    float *sC = reinterpret_cast<float *>(smem + C::ST * S::STAGE);
     float *ssrc = sC + C::PTP / 4;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + 2 * S::STAGE + 2 * C::PTP);
-    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + 2 * S::STAGE + 2 * C::PTP + 64);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::BARS);   // [0, ST): stages, [ST]: C
+    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + S::BARS + 64);
 
     const int tile = blockIdx.x, j = blockIdx.y, grp = blockIdx.z;
     const int tzi = tile / p.g.ntx, txi = tile - tzi * p.g.ntx;
@@ -501,7 +618,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     const int xb = x0 + 4 * tx, zrow0 = z0 + tz * C::RZ;
 
     auto issue = [&](int i) {
-        const int st = i & 1, s = s0 + i;
+        const int st = i % C::ST, s = s0 + i;
         unsigned char *base = smem + st * S::STAGE;
         const int fo = j * p.ns + s;
         mbar_expect_tx(&bars[st], S::STAGE_TX);
@@ -511,20 +628,10 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     };
 
     if (threadIdx.x == 0) {
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        mbar_init(&bars[2], 1);
+        for (int q = 0; q <= C::ST; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
     load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        mbar_expect_tx(&bars[2], C::PT);
-        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[2]);
-        issue(0);
-        if (nitems > 1) issue(1);
-    }
-
     const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
                           x0 + C::TX <= p.g.nb + p.g.nx);
     float axv[4] = {0.f, 0.f, 0.f, 0.f};
@@ -532,6 +639,13 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
 #pragma unroll
         for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
     const float wav = p.wavelet[p.n];
+    if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[C::ST], C::PT);
+        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[C::ST]);
+        for (int q = 0; q < C::ST && q < nitems; ++q) issue(q);
+    }
+    allow_dependent_launch();
     // This step's image contribution of the CTA's shots, summed in shot order
     // in FP32 (at most 8 terms); it is added to the FP64 image once per step.
     // Double-precision arithmetic is slow on this part, so none runs per shot.
@@ -541,13 +655,33 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
 #pragma unroll
         for (int h = 0; h < 2; ++h) acc[r][h] = make_float2(0.0f, 0.0f);
 
-    bool ok = mbar_wait(&bars[2], 0, p.status);
-    if (__syncthreads_or(!ok)) return;
+    // Adds the FP32 partial of a finished group of shots to that group's FP64 image.
+    auto flush = [&](int group) {
+        double *im = p.img + ((size_t)group * p.k + j) * p.g.fsize;
+#pragma unroll
+        for (int r = 0; r < C::RZ; ++r) {
+            const int z = zrow0 + r;
+            if (z < p.g.NZ && xb < p.g.NX) {
+                const size_t off = (size_t)(z + GH) * p.g.P + (xb + GH);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (xb + c < p.g.NX) im[off + c] += (double)((c & 1) ? acc[r][c >> 1].y : acc[r][c >> 1].x);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) acc[r][h] = make_float2(0.0f, 0.0f);
+        }
+    };
+
+    bool ok = mbar_wait(&bars[C::ST], 0, p.status);
+    if (__syncthreads_or(!ok)) {
+        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
+        return;
+    }
 
     auto run = [&](auto sp_tag) -> bool {
         constexpr bool SP = decltype(sp_tag)::value;
         for (int i = 0; i < nitems; ++i) {
-            const int st = i & 1, s = s0 + i;
+            const int st = i % C::ST, s = s0 + i;
             const int fo = j * p.ns + s;
             const int rb = tab.rb[i], re = tab.re[i];
             if (rb < re) {                         // receivers in this tile: stage their sources
@@ -560,9 +694,9 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
                     ssrc[zz * C::TX + xx] = p.rscale * rs[p.rt_rec[s * p.nr + q]];
                 }
             }
-            ok = mbar_wait(&bars[st], (i >> 1) & 1, p.status);
+            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status);
             if (__syncthreads_or(!ok)) {
-                if (i + 1 < nitems) mbar_wait(&bars[st ^ 1], ((i + 1) >> 1) & 1, p.status);
+                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status);
                 return false;
             }
             const unsigned char *base = smem + st * S::STAGE;
@@ -594,22 +728,18 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
                 }
                 if (z < p.g.NZ && xb < p.g.NX) st4(ln + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
             }
+            const bool group_end = (s + 1) % p.gsz == 0 || i + 1 == nitems;
+            if (group_end) flush(s / p.gsz);
             __syncthreads();
-            if (threadIdx.x == 0 && i + 2 < nitems) issue(i + 2);
+            if (threadIdx.x == 0) {
+                if (p.cnt && group_end) publish_item(p.cnt + (size_t)(s / p.gsz) * p.g.ntiles + tile);
+                if (i + C::ST < nitems) issue(i + C::ST);
+            }
         }
         return true;
     };
-    if (!(sponge ? run(std::true_type{}) : run(std::false_type{}))) return;
-    double *im = p.img + ((size_t)grp * p.k + j) * p.g.fsize;
-#pragma unroll
-    for (int r = 0; r < C::RZ; ++r) {
-        const int z = zrow0 + r;
-        if (z >= p.g.NZ || xb >= p.g.NX) continue;
-        const size_t off = (size_t)(z + GH) * p.g.P + (xb + GH);
-#pragma unroll
-        for (int c = 0; c < 4; ++c)
-            if (xb + c < p.g.NX) im[off + c] += (double)((c & 1) ? acc[r][c >> 1].y : acc[r][c >> 1].x);
-    }
+    if (sponge) run(std::true_type{});
+    else run(std::false_type{});
 }
 
 // ------------------------------------------------------------------ host side
@@ -667,6 +797,14 @@ auto with_cfg(int id, F &&f)
     case 5: return f(Cfg64x8{});
     case 6: return f(Cfg32x16{});
     case 7: return f(Cfg128x8{});
+    case 8: return f(Cfg32x16s3{});
+    case 9: return f(Cfg32x16g4{});
+    case 10: return f(Cfg32x16s3g4{});
+    case 11: return f(Cfg128x8s3{});
+    case 12: return f(Cfg128x8g4{});
+    case 13: return f(Cfg128x8s3g4{});
+    case 14: return f(Cfg64x16s3g2{});
+    case 15: return f(Cfg64x8s3g4{});
     default: return f(Cfg64x32{});
     }
 }
@@ -693,13 +831,29 @@ int ensure_smem(int slot, int dev, K kern, int bytes)
     return HV_OK;
 }
 
-int launched(const char *what)
+// Launches a stencil step, with programmatic dependent launch when enabled.
+template <class P>
+int launch_step(void (*kern)(P), dim3 grid, int threads, int smem, cudaStream_t st, bool pdl, const P &p,
+                const char *what)
 {
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = grid;
+    lc.blockDim = dim3(threads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = pdl ? 1 : 0;
     count_launch();
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = cudaLaunchKernelEx(&lc, kern, p);
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     return HV_OK;
 }
+
+bool pdl(const hv_handle *h) { return h->launch_mode >= HV_LAUNCH_PDL; }
 
 Geo geo(const hv_handle *h, const hvi::Tiling &t)
 {
@@ -709,6 +863,26 @@ Geo geo(const hv_handle *h, const hvi::Tiling &t)
 }  // namespace
 
 int tile_menu_size() { return kTileMenu; }
+
+int max_tiles(const hv_handle *h)
+{
+    int m = 0;
+    for (int c = 0; c < kTileMenu; ++c) m = std::max(m, tiling(h, c).ntiles);
+    return m;
+}
+
+void menu_info(int cfg, int *info)
+{
+    with_cfg(cfg, [&](auto c) {
+        using C = decltype(c);
+        info[0] = C::TX;
+        info[1] = C::TZ;
+        info[2] = C::NT;
+        info[3] = C::ST;
+        info[4] = C::GPC;
+        return 0;
+    });
+}
 
 hvi::Tiling tiling(const hv_handle *h, int cfg)
 {
@@ -724,10 +898,12 @@ hvi::Tiling tiling(const hv_handle *h, int cfg)
     });
 }
 
-// Shot groups of the adjoint kernel: groups of up to 8 shots, summed in shot
-// order inside a CTA and in group order at the end.  The grouping depends
-// only on the shot count (never on k or the tile shape), so a vector's result
-// is bitwise the same whether it is applied alone or in a batch.
+// Shot groups of the adjoint kernel: G = ceil(ns / 8) groups of ceil(ns / G)
+// consecutive shots, each summed in FP32 in shot order per step and added to
+// its own FP64 partial image; the partials are summed in group order at the
+// end.  The grouping depends only on the shot count (never on k, the tile
+// shape or how many groups a CTA walks), so a vector's result is bitwise the
+// same whether it is applied alone or in a batch.
 int adj_groups(const hv_handle *h) { return (h->ns + kShotsPerGroup - 1) / kShotsPerGroup; }
 
 // Raise the shared-memory limits of every stencil kernel on the handle's
@@ -788,17 +964,19 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
         p.status = h->status;
         p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : 1;
-        p.spg = kShotsPerGroup < h->ns ? kShotsPerGroup : h->ns;
+        p.gsz = (h->ns + adj_groups(h) - 1) / adj_groups(h);   // the adjoint's shot groups
+        p.spg = p.gsz * C::GPC;                                  // shots per CTA: GPC whole groups
+        p.cnt = a.deps.cnt;
+        p.need = a.deps.need;
+        p.flow = a.deps.flow ? 1 : 0;
         p.g = geo(h, t);
         dim3 grid(t.ntiles, p.k, (h->ns + p.spg - 1) / p.spg);
         if (born) {
             HV_RT_INTERNAL(ensure_smem(0 * kTileMenu + cfg, h->device, k_fwd<C, true>, FwdSmem<C, true>::BYTES));
-            k_fwd<C, true><<<grid, C::NT, FwdSmem<C, true>::BYTES, st>>>(p);
-        } else {
-            HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + cfg, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
-            k_fwd<C, false><<<grid, C::NT, FwdSmem<C, false>::BYTES, st>>>(p);
+            return launch_step(k_fwd<C, true>, grid, C::NT, FwdSmem<C, true>::BYTES, st, pdl(h), p, "k_fwd launch");
         }
-        return launched("k_fwd launch");
+        HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + cfg, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
+        return launch_step(k_fwd<C, false>, grid, C::NT, FwdSmem<C, false>::BYTES, st, pdl(h), p, "k_fwd launch");
     });
 }
 
@@ -825,12 +1003,15 @@ int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
         p.status = h->status;
         p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
-        p.spg = (h->ns + a.G - 1) / a.G;
+        p.gsz = (h->ns + a.G - 1) / a.G;    // shots per group (the last group may be shorter)
+        p.spg = p.gsz * C::GPC;             // shots per CTA: GPC whole groups
+        p.cnt = a.deps.cnt;
+        p.need = a.deps.need;
+        p.flow = a.deps.flow ? 1 : 0;
         p.g = geo(h, t);
         HV_RT_INTERNAL(ensure_smem(2 * kTileMenu + cfg, h->device, k_adj<C>, AdjSmem<C>::BYTES));
-        dim3 grid(t.ntiles, a.k, a.G);
-        k_adj<C><<<grid, C::NT, AdjSmem<C>::BYTES, st>>>(p);
-        return launched("k_adj launch");
+        dim3 grid(t.ntiles, a.k, (a.G + C::GPC - 1) / C::GPC);
+        return launch_step(k_adj<C>, grid, C::NT, AdjSmem<C>::BYTES, st, pdl(h), p, "k_adj launch");
     });
 }
 

@@ -13,7 +13,8 @@ import numpy as np
 import torch
 
 from . import _lib
-from ._lib import HV_CKPT_ALL, HV_OP_BORN, HV_OP_FWD, HV_OP_GRAD, HV_OP_HV, HV_OP_MIGRATE, HV_OP_WAVEFIELD, check
+from ._lib import (HV_CKPT_ALL, HV_LAUNCH_DATAFLOW, HV_LAUNCH_PDL, HV_LAUNCH_PLAIN, HV_OP_BORN, HV_OP_FWD, HV_OP_GRAD,
+                   HV_OP_HV, HV_OP_MIGRATE, HV_OP_WAVEFIELD, check)
 
 __all__ = ["Problem", "HV_CKPT_ALL", "checkpoint_schedule"]
 
@@ -102,17 +103,28 @@ class Problem:
         """Replay the H v launch sequence as a CUDA graph (hv_set_graphs)."""
         check(self.lib.hv_set_graphs(self._h, int(bool(enable))))
 
+    def status(self) -> int:
+        """Device status of the handle's kernels since the last call (HV_OK or HV_ETIMEOUT); resets it."""
+        c = ctypes.c_int()
+        check(self.lib.hv_status(self._h, ctypes.byref(c)))
+        return c.value
+
+    def set_launch_mode(self, mode: int) -> None:
+        """How stencil steps follow one another: HV_LAUNCH_PLAIN, _PDL or _DATAFLOW (hv_set_launch_mode)."""
+        check(self.lib.hv_set_launch_mode(self._h, int(mode)))
+
     def autotune(self, k: int = 1, cache: str | None = None) -> tuple:
         """Pick the fastest tile shape per kernel kind for k vectors (hv_autotune).
 
         The choice is cached in a JSON file (``cache``, else $HV_TUNE_CACHE, else
         ~/.cache/hv_tiles.json) keyed by the padded grid, shot count and k, and
-        reused when present."""
+        reused when present (the key includes the menu size, so a library with a
+        different menu tunes again)."""
         import json
         import os
         path = cache or os.environ.get("HV_TUNE_CACHE") or os.path.join(os.path.expanduser("~"), ".cache",
                                                                        "hv_tiles.json")
-        key = f"{self.NZ}x{self.NX}/ns{self.ns}/k{int(k)}"
+        key = f"{self.NZ}x{self.NX}/ns{self.ns}/k{int(k)}/menu{menu_size()}"
         try:
             table = json.load(open(path))
         except Exception:
@@ -229,3 +241,15 @@ def checkpoint_schedule(nt: int, slots: int):
 def kernel_launches() -> int:
     """Kernels launched by libhv in this process so far."""
     return int(_lib.load().hv_kernel_launches())
+
+
+def menu_size() -> int:
+    """Number of tile configurations the stencil kernels come in."""
+    return int(_lib.load().hv_tile_menu_size())
+
+
+def menu_info(index: int) -> dict:
+    """Tile shape, threads, copy stages and 8-shot groups per CTA of a menu entry."""
+    info = (ctypes.c_int * 5)()
+    check(_lib.load().hv_tile_menu_info(int(index), info))
+    return {"TX": info[0], "TZ": info[1], "threads": info[2], "stages": info[3], "groups_per_cta": info[4]}

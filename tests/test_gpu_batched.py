@@ -8,8 +8,9 @@ import torch
 
 from oracle import oracle as O
 from paper_2507_10804_gb300 import synth
-from paper_2507_10804_gb300.hv import HV_CKPT_ALL, Problem
-from tests._helpers import f32, oracle_problem, rel
+from paper_2507_10804_gb300.hv import (HV_CKPT_ALL, HV_LAUNCH_DATAFLOW, HV_LAUNCH_PDL, HV_LAUNCH_PLAIN, Problem,
+                                       menu_size)
+from tests._helpers import f32, oracle_problem, ragged_workload, rel
 
 pytestmark = pytest.mark.gpu
 TOL = 2e-4
@@ -45,11 +46,67 @@ def test_tile_shapes_and_graphs_do_not_change_results(batched):
     P.set_graphs(False)
     P.set_tiles((0, 0, 0))
     ref = P.hessian_apply(m, vs, ckpt=7).cpu().numpy()
-    for cfg in [(1, 1, 1), (2, 2, 2), (3, 3, 3), (4, 4, 4), (5, 5, 5), (6, 6, 6), (7, 7, 7), (3, 1, 2), (5, 4, 0)]:
+    n = menu_size()
+    cfgs = [(c, c, c) for c in range(1, n)] + [(3, 1, 2), (5, 4, 0), (9, 12, 13), (15, 8, 10)]
+    for cfg in cfgs:
         P.set_tiles(cfg)
         for graphs in (False, True):
             P.set_graphs(graphs)
             out = P.hessian_apply(m, vs, ckpt=7).cpu().numpy()
             assert np.array_equal(out, ref), (cfg, graphs)
+    for mode in (HV_LAUNCH_PLAIN, HV_LAUNCH_PDL, HV_LAUNCH_DATAFLOW):
+        P.set_launch_mode(mode)
+        for graphs in (False, True):
+            P.set_graphs(graphs)
+            out = P.hessian_apply(m, vs, ckpt=7).cpu().numpy()
+            assert np.array_equal(out, ref), (mode, graphs)
     P.set_graphs(False)
     P.set_tiles((0, 0, 0))
+
+
+def test_shot_groups_spanning_ctas_ragged_shot_count():
+    """20 shots form adjoint groups of 7, 7 and 6; configurations that walk two or
+    four groups per CTA, or keep two shots in flight, give bitwise the same H v."""
+    w = ragged_workload(nt=120, ns=20, nr=9, k=2)
+    P = Problem.from_workload(w)
+    m = torch.tensor(w.m, dtype=torch.float32, device="cuda")
+    v = torch.tensor(w.v[:2], dtype=torch.float32, device="cuda")
+    P.set_tiles((0, 0, 0))
+    ref = P.hessian_apply(m, v, ckpt=5).cpu().numpy()
+    for c in range(1, menu_size()):
+        P.set_tiles((c, c, c))
+        out = P.hessian_apply(m, v, ckpt=5).cpu().numpy()
+        assert np.array_equal(out, ref), c
+    want = O.hessian_apply(oracle_problem(w), f32(w.m), f32(w.v[:2]))
+    for j in range(2):
+        assert rel(ref[j], want[j]) < TOL, (j, rel(ref[j], want[j]))
+
+
+@pytest.mark.parametrize("tiles", [(6, 8, 6), (9, 10, 9), (7, 11, 13)])
+def test_dataflow_launch_mode_bitwise(tiles):
+    """Steps that start on tile-neighbourhood counters give the same bits as
+    fully serialised steps: H v (binomial and stored history, k = 3 with Born
+    items per vector), the gradient (a residual kernel between the sweeps) and
+    the Born map, on a ragged grid with 20 shots (groups of 7, 7, 6)."""
+    w = ragged_workload(nt=90, ns=20, nr=9, k=3)
+    P = Problem.from_workload(w)
+    m = torch.tensor(w.m, dtype=torch.float32, device="cuda")
+    v = torch.tensor(w.v[:3], dtype=torch.float32, device="cuda")
+    dobs = torch.tensor(O.fwd_model(oracle_problem(w), f32(w.m) * 1.01), dtype=torch.float32, device="cuda")
+    P.set_tiles(tiles)
+
+    def run():
+        out = [P.hessian_apply(m, v, ckpt=4), P.hessian_apply(m, v, ckpt=HV_CKPT_ALL), P.born(m, v)]
+        phi, g = P.misfit_grad(m, dobs, ckpt=6)
+        out += [g, phi.reshape(1)]
+        torch.cuda.synchronize()
+        return [x.cpu().numpy() for x in out]
+
+    P.set_launch_mode(HV_LAUNCH_PLAIN)
+    ref = run()
+    for mode in (HV_LAUNCH_DATAFLOW, HV_LAUNCH_PDL, HV_LAUNCH_DATAFLOW):
+        P.set_launch_mode(mode)
+        got = run()
+        for a, b in zip(got, ref):
+            assert np.array_equal(a, b), mode
+    assert P.status() == 0
