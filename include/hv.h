@@ -203,21 +203,53 @@ int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float 
  * Synchronises the device, then clears the status. */
 int hv_status(hv_handle *h, int *device_status);
 
-/* Hessian approximations built from batched H v (section 3.2: point spread
- * functions; section 3.4: pseudo-differential operator probing; section 3.6:
- * PSF+), applied in low-rank-symbol form (section 3.3, eq. (lr-psido)).
- * Declared for the interface; this version does not provide them: every
- * call returns HV_ENOTSUP.  The H v products they consume are the batched
- * hv_hessian_apply calls above (impulse lattices and probing vectors). */
+/* Hessian approximations built from batched H v.
+ *
+ * Point spread functions (section 3.2) in the PsiDO row form of section 3.5:
+ * a PSF is H_d applied to a delta at a sample point x_k, read around x_k,
+ *   p_k(d) = (H_d e_{x_k})[x_k + d],
+ * and H_d ~ (2 pi)^2 sum_k D_{w_k} F^-1 D_{conj(p_k^)} F, i.e. on the grid
+ *   (H~ v)(x) = sum_k w_k(x) sum_{|d|_inf <= R} p_k(d) v(x + d)   (v = 0 off the grid).
+ * Sample points: the lattice of spacing S = spacing_cells on the interior grid
+ * starting at (S/2, S/2) (integer division), all points with iz < nz, ix < nx,
+ * point (a, b) numbered k = a * nb + b.  n_batches = B * B (B = 1..8): batch
+ * (a mod B) * B + (b mod B) holds the sum of unit impulses at its points, and
+ * one hv_hessian_apply with k = B * B vectors yields every PSF.  Window radius
+ * R = (B S - 1) / 2 (windows of one batch never overlap; at most 40); PSF
+ * values whose x_k + d leaves the grid are zero.  Weights w_k: bilinear hat
+ * functions on the lattice (a partition of unity), constant beyond the
+ * outermost points.  The paper leaves the window, the weights and the batch
+ * layout open; these are this library's choices.
+ *
+ *  - hv_approx_psf_workspace_size: bytes of `ws` hv_approx_build_psf needs for
+ *    n_batches and checkpoint budget ckpt (as in hv_hessian_apply).
+ *  - hv_approx_build_psf: builds the approximation at model m ([nz][nx]
+ *    device) on `stream`; *out receives a new object that owns its device
+ *    memory (PSFs [r][2R+1][2R+1] floats).  HV_EINVAL on a bad argument
+ *    (spacing < 1, n_batches not a square of 1..8, R > 40, first sample point
+ *    off the grid), HV_ENOMEM if ws is too small.
+ *  - hv_approx_apply: out[k][nz][nx] = H~ v[k][nz][nx] (device, k >= 1) on
+ *    `stream`, mode HV_APPROX_H.  The square-root modes (for the SPD
+ *    approximation used in sampling, section 3.7) need the symbol in the
+ *    frequency domain and return HV_ENOTSUP in this version.
+ *  - hv_approx_info: info[11] = {kind (0 = PSF), r, R, na, nb, S, B, cz0,
+ *    cx0, nz, nx}.
+ *  - hv_approx_psfs: copies the PSFs [r][2R+1][2R+1] into a device buffer.
+ *  - hv_approx_destroy: frees the object (NULL is allowed).
+ * Probing (section 3.4) and PSF+ (section 3.6): hv_approx_build_pdo is
+ * declared and returns HV_ENOTSUP. */
 typedef struct hv_approx hv_approx;
 #define HV_APPROX_H 0           /* apply the approximation of H_d            */
 #define HV_APPROX_SQRT 1        /* apply its SPD square root                 */
 #define HV_APPROX_INVSQRT 2     /* apply the inverse square root             */
-int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, hv_approx **out, void *ws,
-                        size_t ws_bytes, void *stream);
+int hv_approx_psf_workspace_size(hv_handle *h, int n_batches, int ckpt, size_t *bytes);
+int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt, hv_approx **out,
+                        void *ws, size_t ws_bytes, void *stream);
 int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, hv_approx **out, void *ws, size_t ws_bytes,
                         void *stream);
 int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream);
+int hv_approx_info(const hv_approx *a, int *info);
+int hv_approx_psfs(const hv_approx *a, float *psf, void *stream);
 int hv_approx_destroy(hv_approx *a);
 
 /* Serving.  A server owns one device arena of hbm_budget bytes (allocated at

@@ -71,7 +71,11 @@ _SIGS = {
     "hv_poll": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(c_int)], c_int),
     "hv_wait": ([c_void_p, ctypes.c_ulonglong, c_double, ctypes.POINTER(c_int)], c_int),
     "hv_request_get_info": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(HvRequestInfo)], c_int),
-    "hv_approx_build_psf": ([c_void_p, fp, c_int, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p], c_int),
+    "hv_approx_psf_workspace_size": ([c_void_p, c_int, c_int, ctypes.POINTER(c_size_t)], c_int),
+    "hv_approx_build_psf": ([c_void_p, fp, c_int, c_int, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p],
+                            c_int),
+    "hv_approx_info": ([c_void_p, ip], c_int),
+    "hv_approx_psfs": ([c_void_p, fp, c_void_p], c_int),
     "hv_approx_build_pdo": ([c_void_p, fp, c_double, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p],
                             c_int),
     "hv_approx_apply": ([c_void_p, fp, c_int, fp, c_int, c_void_p], c_int),

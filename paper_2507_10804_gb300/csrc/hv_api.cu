@@ -1096,11 +1096,116 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
     return HV_OK;
 }
 
-// Hessian approximations: declared, not provided in this version.
-extern "C" int hv_approx_build_psf(hv_handle *, const float *, int, int, hv_approx **out, void *, size_t, void *)
+// ---------------------------------------------------------------- approximations
+// Point-spread-function approximation (section 3.2; PsiDO row form, section 3.5).
+struct hv_approx {
+    int kind = 0;           // 0: PSF
+    int device = -1;
+    hvk::PsfGeo g{};
+    float *psf = nullptr;   // [na * nb][2R+1][2R+1]
+};
+
+namespace {
+
+constexpr int kMaxPsfBatchesPerAxis = 8;
+constexpr int kMaxPsfRadius = 40;
+
+int psf_batches_per_axis(int n_batches)
+{
+    for (int B = 1; B <= kMaxPsfBatchesPerAxis; ++B)
+        if (B * B == n_batches) return B;
+    return 0;
+}
+
+int psf_geometry(const hv_handle *h, int S, int n_batches, hvk::PsfGeo &g)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    if (S < 1) return hvi::fail(HV_EINVAL, "PSF lattice spacing %d; need >= 1", S);
+    const int B = psf_batches_per_axis(n_batches);
+    if (B == 0) return hvi::fail(HV_EINVAL, "n_batches = %d; need B * B with 1 <= B <= %d", n_batches, kMaxPsfBatchesPerAxis);
+    g.nz = h->nz;
+    g.nx = h->nx;
+    g.S = S;
+    g.B = B;
+    g.R = (B * S - 1) / 2;
+    g.cz0 = S / 2;
+    g.cx0 = S / 2;
+    if (g.cz0 >= h->nz || g.cx0 >= h->nx)
+        return hvi::fail(HV_EINVAL, "first PSF sample point (%d, %d) is off the %d x %d grid", g.cz0, g.cx0, h->nz, h->nx);
+    if (g.R > kMaxPsfRadius) return hvi::fail(HV_EINVAL, "PSF window radius %d exceeds %d", g.R, kMaxPsfRadius);
+    g.na = (h->nz - 1 - g.cz0) / S + 1;
+    g.nb = (h->nx - 1 - g.cx0) / S + 1;
+    return HV_OK;
+}
+
+// Workspace of the build: impulse batches, their H v, then the H v workspace.
+struct PsfLayout {
+    size_t vec = 0, hv = 0, inner = 0, inner_bytes = 0, total = 0;
+};
+
+int psf_layout(hv_handle *h, int n_batches, int ckpt, PsfLayout &P)
+{
+    Layout L;
+    HV_RT(make_layout(h, HV_OP_HV, n_batches, ckpt, L));
+    const size_t vb = align256((size_t)n_batches * h->nz * h->nx * sizeof(float));
+    P.vec = 0;
+    P.hv = vb;
+    P.inner = 2 * vb;
+    P.inner_bytes = L.total;
+    P.total = P.inner + L.total;
+    return HV_OK;
+}
+
+}  // namespace
+
+extern "C" int hv_approx_psf_workspace_size(hv_handle *h, int n_batches, int ckpt, size_t *bytes)
+{
+    if (!h || !bytes) return hvi::fail(HV_EINVAL, "null handle or output");
+    if (psf_batches_per_axis(n_batches) == 0)
+        return hvi::fail(HV_EINVAL, "n_batches = %d; need B * B with 1 <= B <= %d", n_batches, kMaxPsfBatchesPerAxis);
+    PsfLayout P;
+    HV_RT(psf_layout(h, n_batches, ckpt, P));
+    *bytes = P.total;
+    return HV_OK;
+}
+
+extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt,
+                                   hv_approx **out, void *ws, size_t ws_bytes, void *stream)
 {
     if (out) *out = nullptr;
-    return hvi::fail(HV_ENOTSUP, "hv_approx_build_psf: not provided in this version");
+    if (!out || !m) return hvi::fail(HV_EINVAL, "null model or output");
+    hvk::PsfGeo g;
+    HV_RT(psf_geometry(h, spacing_cells, n_batches, g));
+    PsfLayout P;
+    HV_RT(psf_layout(h, n_batches, ckpt, P));
+    if (!ws) return hvi::fail(HV_EINVAL, "null workspace");
+    if (((uintptr_t)ws & 255u) != 0) return hvi::fail(HV_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < P.total) return hvi::fail(HV_ENOMEM, "workspace of %zu bytes; the PSF build needs %zu", ws_bytes, P.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    float *vec = reinterpret_cast<float *>(w + P.vec);
+    float *hv = reinterpret_cast<float *>(w + P.hv);
+    HV_CK(cudaMemsetAsync(vec, 0, (size_t)n_batches * h->nz * h->nx * sizeof(float), st));
+    HV_RT(hvk::launch_psf_impulses(g, vec, st));
+    HV_RT(run_adjoint(h, 2, m, vec, n_batches, hv, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st));
+    hv_approx *a = new hv_approx;
+    a->kind = 0;
+    a->device = h->device;
+    a->g = g;
+    const size_t W = 2 * (size_t)g.R + 1;
+    cudaError_t e = cudaMalloc(&a->psf, (size_t)g.na * g.nb * W * W * sizeof(float));
+    if (e != cudaSuccess) {
+        delete a;
+        return hvi::fail(HV_ECUDA, "cudaMalloc: %s", cudaGetErrorString(e));
+    }
+    int rc = hvk::launch_psf_extract(g, hv, a->psf, st);
+    if (rc != HV_OK) {
+        cudaFree(a->psf);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return HV_OK;
 }
 
 extern "C" int hv_approx_build_pdo(hv_handle *, const float *, double, int, hv_approx **out, void *, size_t, void *)
@@ -1109,9 +1214,42 @@ extern "C" int hv_approx_build_pdo(hv_handle *, const float *, double, int, hv_a
     return hvi::fail(HV_ENOTSUP, "hv_approx_build_pdo: not provided in this version");
 }
 
-extern "C" int hv_approx_apply(const hv_approx *, const float *, int, float *, int, void *)
+extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream)
 {
-    return hvi::fail(HV_ENOTSUP, "hv_approx_apply: not provided in this version");
+    if (!a) return hvi::fail(HV_EINVAL, "null approximation");
+    if (mode == HV_APPROX_SQRT || mode == HV_APPROX_INVSQRT)
+        return hvi::fail(HV_ENOTSUP, "square-root modes need the frequency-domain symbol; not provided in this version");
+    if (mode != HV_APPROX_H) return hvi::fail(HV_EINVAL, "unknown apply mode %d", mode);
+    if (!v || !out) return hvi::fail(HV_EINVAL, "null vector or output");
+    if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "k = %d vectors; need 1 <= k <= 65535", k);
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != a->device) return hvi::fail(HV_EINVAL, "current device %d is not the approximation's device %d", dev, a->device);
+    return hvk::launch_psf_apply(a->g, a->psf, v, k, out, (cudaStream_t)stream);
 }
 
-extern "C" int hv_approx_destroy(hv_approx *) { return HV_OK; }
+extern "C" int hv_approx_info(const hv_approx *a, int *info)
+{
+    if (!a || !info) return hvi::fail(HV_EINVAL, "null approximation or output");
+    const hvk::PsfGeo &g = a->g;
+    const int vals[11] = {a->kind, g.na * g.nb, g.R, g.na, g.nb, g.S, g.B, g.cz0, g.cx0, g.nz, g.nx};
+    for (int i = 0; i < 11; ++i) info[i] = vals[i];
+    return HV_OK;
+}
+
+extern "C" int hv_approx_psfs(const hv_approx *a, float *psf, void *stream)
+{
+    if (!a || !psf) return hvi::fail(HV_EINVAL, "null approximation or output");
+    const size_t W = 2 * (size_t)a->g.R + 1;
+    HV_CK(cudaMemcpyAsync(psf, a->psf, (size_t)a->g.na * a->g.nb * W * W * sizeof(float), cudaMemcpyDeviceToDevice,
+                          (cudaStream_t)stream));
+    return HV_OK;
+}
+
+extern "C" int hv_approx_destroy(hv_approx *a)
+{
+    if (!a) return HV_OK;
+    cudaFree(a->psf);
+    delete a;
+    return HV_OK;
+}

@@ -226,6 +226,64 @@ class Problem:
         return out
 
 
+    # ---------------------------------------------------------------- approximations
+    def approx_build_psf(self, m: torch.Tensor, spacing: int, n_batches: int = 4,
+                         ckpt: int = HV_CKPT_ALL) -> "PsfApprox":
+        """Point-spread-function approximation of H_d at m (hv_approx_build_psf): n_batches = B*B
+        Hessian applications to impulse lattices of spacing `spacing` cells."""
+        n = ctypes.c_size_t()
+        check(self.lib.hv_approx_psf_workspace_size(self._h, int(n_batches), int(ckpt), ctypes.byref(n)))
+        buf = self._ws.get("ws")
+        if buf is None or buf.numel() < n.value:
+            self._ws.pop("ws", None)
+            buf = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._ws["ws"] = buf
+        out = ctypes.c_void_p()
+        check(self.lib.hv_approx_build_psf(self._h, self._m(m), int(spacing), int(n_batches), int(ckpt),
+                                           ctypes.byref(out), buf.data_ptr(), buf.numel(), self._stream()))
+        return PsfApprox(self.lib, out, self.device)
+
+
+class PsfApprox:
+    """A built PSF approximation (owns its device memory; see hv_approx_build_psf)."""
+
+    def __init__(self, lib, handle, device):
+        self.lib, self._a, self.device = lib, handle, device
+        info = (ctypes.c_int * 11)()
+        check(self.lib.hv_approx_info(self._a, info))
+        keys = ("kind", "r", "R", "na", "nb", "S", "B", "cz0", "cx0", "nz", "nx")
+        self.info = dict(zip(keys, list(info)))
+
+    def apply(self, v: torch.Tensor) -> torch.Tensor:
+        """H~ v for v[k, nz, nx] -> [k, nz, nx] (hv_approx_apply, mode H)."""
+        nz, nx = self.info["nz"], self.info["nx"]
+        k = v.shape[0]
+        pv = _dev(v, torch.float32, (k, nz, nx), "v", self.device)
+        out = torch.empty((k, nz, nx), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_approx_apply(self._a, pv, k, out.data_ptr(), 0,
+                                       ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+        return out
+
+    def psfs(self) -> torch.Tensor:
+        """The PSFs [r, 2R+1, 2R+1] (a device copy)."""
+        W = 2 * self.info["R"] + 1
+        out = torch.empty((self.info["r"], W, W), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_approx_psfs(self._a, out.data_ptr(),
+                                      ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "_a", None):
+            self.lib.hv_approx_destroy(self._a)
+            self._a = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def checkpoint_schedule(nt: int, slots: int):
     """The library's checkpoint schedule: (actions[n, 3] int32, recomputed forward steps)."""
     lib = _lib.load()

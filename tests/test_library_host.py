@@ -116,11 +116,18 @@ def test_create_rejects_bad_arguments_before_touching_the_gpu(lib, kw, needle):
     assert needle in msg
 
 
-def test_approximation_entry_points_report_not_supported(lib):
+def test_approximation_entry_points_validate_before_touching_the_gpu(lib):
     out = ctypes.c_void_p(1)
-    assert lib.hv_approx_build_psf(None, None, 12, 4, ctypes.byref(out), None, 0, None) == _lib.HV_ENOTSUP
+    assert lib.hv_approx_build_psf(None, None, 12, 4, 8, ctypes.byref(out), None, 0, None) == _lib.HV_EINVAL
     assert out.value is None
+    assert "null" in lib.hv_last_error().decode()
+    out = ctypes.c_void_p(1)
     assert lib.hv_approx_build_pdo(None, None, ctypes.c_double(0.01), 8, ctypes.byref(out), None, 0, None) \
         == _lib.HV_ENOTSUP
-    assert lib.hv_approx_apply(None, None, 1, None, 0, None) == _lib.HV_ENOTSUP
+    assert out.value is None
+    assert lib.hv_approx_apply(None, None, 1, None, 0, None) == _lib.HV_EINVAL
+    n = ctypes.c_size_t()
+    assert lib.hv_approx_psf_workspace_size(None, 4, 8, ctypes.byref(n)) == _lib.HV_EINVAL
+    info = (ctypes.c_int * 11)()
+    assert lib.hv_approx_info(None, info) == _lib.HV_EINVAL
     assert lib.hv_approx_destroy(None) == _lib.HV_OK
