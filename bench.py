@@ -415,15 +415,17 @@ def run_ours(args, w):
 
 def serve_requests(n, seed=20250719):
     """The request stream of the serving workload: clients 0-63 are MCMC chains,
-    64-67 FWI runs; each request draws its kind (H v 40%, gradient 40%, misfit
-    20%), its grid from {128x128, 256x256, 384x1152} (steps 1000/1500/3000) and
-    its shot count from U{4..32}."""
+    64-67 FWI runs; each request draws its kind (H v 35%, gradient 35%, misfit
+    15%, apply of the grid's PSF Hessian approximation 15%), its grid from
+    {128x128, 256x256, 384x1152} (steps 1000/1500/3000) and its shot count from
+    U{4..32}."""
     from paper_2507_10804_gb300 import synth
     u = synth.uniform(seed, 4 * n)
     grids = [(128, 128, 1000), (256, 256, 1500), (384, 1152, 3000)]
     out = []
     for i in range(n):
-        kind = ("hv", "grad", "misfit")[min(int(u[4 * i] * 5) // 2, 2)]
+        x = u[4 * i]
+        kind = "hv" if x < 0.35 else ("grad" if x < 0.70 else ("misfit" if x < 0.85 else "approx"))
         g = grids[min(int(u[4 * i + 1] * 3), 2)]
         ns = 4 + min(int(u[4 * i + 2] * 29), 28)
         client = min(int(u[4 * i + 3] * 68), 67)
@@ -464,8 +466,15 @@ def run_serve(args):
                                t0=0.15, vmax=vmax, acq=acq, m=m, v=np.zeros((1, nz, nx)))
             problems[key] = Problem.from_workload(w, device=dev)
             data[key] = problems[key].fwd_model(models[(nz, nx)][1] * 1.02)
-    torch.cuda.synchronize()
     ckpt = 30
+    # one PSF approximation per grid (12-cell lattice, 4 batches), built at the grid's
+    # model with the first acquisition drawn on it; approximate-apply requests use it
+    approx = {}
+    for r in reqs:
+        nz, nx, nt = r["grid"]
+        if r["kind"] == "approx" and (nz, nx) not in approx:
+            approx[(nz, nx)] = problems[(nz, nx, r["ns"])].approx_build_psf(models[(nz, nx)][1], 12, 4, ckpt=ckpt)
+    torch.cuda.synchronize()
 
     def submit(S, r):
         nz, nx, nt = r["grid"]
@@ -476,6 +485,8 @@ def run_serve(args):
             return S.submit_hv(P, m, v, ckpt=ckpt)[0]
         if r["kind"] == "grad":
             return S.submit_grad(P, m, d, ckpt=ckpt)[0]
+        if r["kind"] == "approx":
+            return S.submit_approx(approx[(nz, nx)], v)[0]
         return S.submit_misfit(P, m, d)[0]
 
     budget = 150 << 30
@@ -508,9 +519,12 @@ def run_serve(args):
         infos = [S.info(i) for i in ids]
         lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
         span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+        kinds = np.array([r["kind"] for r in reqs])
+        by_kind = {k: {"p50_ms": float(np.percentile(lat[kinds == k], 50)), "p99_ms": float(np.percentile(lat[kinds == k], 99))}
+                   for k in ("hv", "grad", "misfit", "approx") if (kinds == k).any()}
         results.append({"rate_frac_of_serial": frac, "offered_req_s": lam, "p50_ms": float(np.percentile(lat, 50)),
                         "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": n / span,
-                        "hv_per_s": n_hv / span})
+                        "hv_per_s": n_hv / span, "by_kind": by_kind})
     S.close()
     best = max(results, key=lambda x: x["throughput_req_s"])
     line = {
@@ -518,8 +532,9 @@ def run_serve(args):
         "ms_per_step": 1e3 / best["throughput_req_s"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic request stream (seeded models; stands in for the paper's MCMC and FWI clients)",
-        "config": {"workload": "serving: 64 MCMC chains + 4 FWI runs, Poisson arrivals, H v 40% / gradient 40% / "
-                               "misfit 20%, grids {128x128, 256x256, 384x1152} x U{4..32} shots, 150 GB pool",
+        "config": {"workload": "serving: 64 MCMC chains + 4 FWI runs, Poisson arrivals, H v 35% / gradient 35% / "
+                               "misfit 15% / PSF-approximation apply 15%, grids {128x128, 256x256, 384x1152} x "
+                               "U{4..32} shots, 150 GB pool",
                    "requests": n, "concurrency": args.concurrency, "snapshots_per_shot": ckpt},
         "serve": {"serial_req_s": serial_rate, "serial_hv_per_s": n_hv / t_serial, "rates": results},
     }

@@ -254,7 +254,8 @@ int hv_approx_destroy(hv_approx *a);
 
 /* Serving.  A server owns one device arena of hbm_budget bytes (allocated at
  * creation) and max_concurrent CUDA streams on the current device.  Requests
- * (H v, gradient, misfit) on any problems created on that device are queued
+ * (H v, gradient, misfit, and the apply of a built Hessian approximation) on
+ * any problems or approximations created on that device are queued
  * by hv_submit; a scheduler thread admits them in arrival order, letting a
  * later request pass one that is waiting for memory, whenever a stream is free
  * and the request's workspace fits in the arena, and runs each on its own
@@ -266,19 +267,21 @@ int hv_approx_destroy(hv_approx *a);
 #define HV_REQ_HV 0
 #define HV_REQ_GRAD 1
 #define HV_REQ_MISFIT 2
+#define HV_REQ_APPROX 3         /* hv_approx_apply(approx, v, k, out, HV_APPROX_H); needs no workspace */
 #define HV_REQ_QUEUED 100
 #define HV_REQ_RUNNING 101
 typedef struct hv_server hv_server;
 typedef struct hv_request {
     int kind;               /* HV_REQ_*                                           */
-    hv_handle *problem;     /* problem the request runs on                        */
-    const float *m;         /* model [nz][nx]                                     */
-    const float *v;         /* HV: vectors [k][nz][nx]                            */
-    int k;                  /* HV: number of vectors                              */
+    hv_handle *problem;     /* problem the request runs on (unused by APPROX)     */
+    const float *m;         /* model [nz][nx] (unused by APPROX)                  */
+    const float *v;         /* HV, APPROX: vectors [k][nz][nx]                    */
+    int k;                  /* HV, APPROX: number of vectors                      */
     const float *d_obs;     /* GRAD, MISFIT: observed data [ns][nt][nr]           */
-    float *out;             /* HV: [k][nz][nx]; GRAD: gradient [nz][nx]           */
+    float *out;             /* HV, APPROX: [k][nz][nx]; GRAD: gradient [nz][nx]   */
     double *phi;            /* GRAD, MISFIT: device scalar                        */
     int ckpt;               /* HV, GRAD: checkpoint budget                        */
+    const hv_approx *approx; /* APPROX: a built approximation                     */
 } hv_request;
 typedef struct hv_request_info {
     int kind, status;

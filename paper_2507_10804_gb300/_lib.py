@@ -37,7 +37,7 @@ class HvAcq(ctypes.Structure):
 
 class HvRequest(ctypes.Structure):
     _fields_ = [("kind", c_int), ("problem", c_void_p), ("m", fp), ("v", fp), ("k", c_int), ("d_obs", fp),
-                ("out", fp), ("phi", fp), ("ckpt", c_int)]
+                ("out", fp), ("phi", fp), ("ckpt", c_int), ("approx", c_void_p)]
 
 
 class HvRequestInfo(ctypes.Structure):
@@ -45,7 +45,7 @@ class HvRequestInfo(ctypes.Structure):
                 ("t_done", c_double), ("ws_bytes", c_size_t)]
 
 
-HV_REQ_HV, HV_REQ_GRAD, HV_REQ_MISFIT = 0, 1, 2
+HV_REQ_HV, HV_REQ_GRAD, HV_REQ_MISFIT, HV_REQ_APPROX = 0, 1, 2, 3
 HV_REQ_QUEUED, HV_REQ_RUNNING = 100, 101
 
 _SIGS = {

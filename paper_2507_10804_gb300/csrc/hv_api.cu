@@ -1228,6 +1228,8 @@ extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float 
     return hvk::launch_psf_apply(a->g, a->psf, v, k, out, (cudaStream_t)stream);
 }
 
+int hvi::approx_device(const hv_approx *a) { return a ? a->device : -1; }
+
 extern "C" int hv_approx_info(const hv_approx *a, int *info)
 {
     if (!a || !info) return hvi::fail(HV_EINVAL, "null approximation or output");

@@ -24,6 +24,7 @@ namespace hvi {
 // ---------------------------------------------------------------- status
 int fail(int code, const char *fmt, ...);
 inline int ok() { return HV_OK; }
+int approx_device(const hv_approx *a);   // device a Hessian approximation lives on
 
 // ---------------------------------------------------------------- schedule
 enum { ACT_FORWARD = 0, ACT_SAVE = 1, ACT_RESTORE = 2, ACT_ADVANCE = 3, ACT_ADJOINT = 4 };

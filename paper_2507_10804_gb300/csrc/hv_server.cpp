@@ -108,6 +108,10 @@ int op_of(int kind)
 
 int request_ws(const hv_request &r, size_t *bytes)
 {
+    if (r.kind == HV_REQ_APPROX) {
+        *bytes = 0;
+        return HV_OK;
+    }
     return hv_workspace_size(r.problem, op_of(r.kind), r.kind == HV_REQ_HV ? r.k : 1, r.ckpt, bytes);
 }
 
@@ -122,6 +126,7 @@ int launch(hv_server *S, const Req &q)
     int rc;
     if (r.kind == HV_REQ_HV) rc = hv_hessian_apply(r.problem, r.m, r.v, r.k, r.out, r.ckpt, ws, q.ws, st);
     else if (r.kind == HV_REQ_GRAD) rc = hv_misfit_grad(r.problem, r.m, r.d_obs, r.phi, r.out, r.ckpt, ws, q.ws, st);
+    else if (r.kind == HV_REQ_APPROX) rc = hv_approx_apply(r.approx, r.v, r.k, r.out, HV_APPROX_H, st);
     else rc = hv_misfit(r.problem, r.m, r.d_obs, r.phi, ws, q.ws, st);
     cudaError_t e = cudaEventRecord(S->events[q.slot], S->streams[q.slot]);
     if (rc == HV_OK && e != cudaSuccess) rc = HV_ECUDA;
@@ -254,11 +259,13 @@ extern "C" int hv_server_destroy(hv_server *S, double timeout_s)
 extern "C" int hv_submit(hv_server *S, const hv_request *r, unsigned long long *id)
 {
     if (!S || !r || !id) return hvi::fail(HV_EINVAL, "hv_submit: null argument");
-    if (!r->problem || !r->m || (r->kind == HV_REQ_HV && (!r->v || !r->out || r->k < 1)) ||
+    const bool approx = r->kind == HV_REQ_APPROX;
+    if ((!approx && (!r->problem || !r->m)) || (r->kind == HV_REQ_HV && (!r->v || !r->out || r->k < 1)) ||
         (r->kind == HV_REQ_GRAD && (!r->d_obs || !r->out || !r->phi)) || (r->kind == HV_REQ_MISFIT && (!r->d_obs || !r->phi)) ||
-        r->kind < HV_REQ_HV || r->kind > HV_REQ_MISFIT)
+        (approx && (!r->approx || !r->v || !r->out || r->k < 1)) || r->kind < HV_REQ_HV || r->kind > HV_REQ_APPROX)
         return hvi::fail(HV_EINVAL, "hv_submit: incomplete request of kind %d", r->kind);
-    if (r->problem->device != S->device) return hvi::fail(HV_EINVAL, "hv_submit: problem on another device");
+    const int dev = approx ? hvi::approx_device(r->approx) : r->problem->device;
+    if (dev != S->device) return hvi::fail(HV_EINVAL, "hv_submit: %s on another device", approx ? "approximation" : "problem");
     size_t ws = 0;
     HV_RT_INTERNAL(request_ws(*r, &ws));
     if (((ws + 255) & ~(size_t)255) > S->budget)

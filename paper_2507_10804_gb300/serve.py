@@ -12,10 +12,10 @@ import ctypes
 import torch
 
 from . import _lib
-from ._lib import HV_REQ_GRAD, HV_REQ_HV, HV_REQ_MISFIT, HV_REQ_QUEUED, HV_REQ_RUNNING, check
+from ._lib import HV_REQ_APPROX, HV_REQ_GRAD, HV_REQ_HV, HV_REQ_MISFIT, HV_REQ_QUEUED, HV_REQ_RUNNING, check
 from .hv import Problem
 
-__all__ = ["Server", "HV_REQ_HV", "HV_REQ_GRAD", "HV_REQ_MISFIT"]
+__all__ = ["Server", "HV_REQ_HV", "HV_REQ_GRAD", "HV_REQ_MISFIT", "HV_REQ_APPROX"]
 
 
 class Server:
@@ -40,14 +40,16 @@ class Server:
         except Exception:
             pass
 
-    def _submit(self, kind, P: Problem, m, v=None, k=0, d_obs=None, out=None, phi=None, ckpt=-1):
-        r = _lib.HvRequest(kind, P._h, m.data_ptr(), v.data_ptr() if v is not None else None, int(k),
+    def _submit(self, kind, P: Problem | None, m, v=None, k=0, d_obs=None, out=None, phi=None, ckpt=-1, approx=None):
+        r = _lib.HvRequest(kind, P._h if P is not None else None, m.data_ptr() if m is not None else None,
+                           v.data_ptr() if v is not None else None, int(k),
                            d_obs.data_ptr() if d_obs is not None else None,
                            out.data_ptr() if out is not None else None,
-                           phi.data_ptr() if phi is not None else None, int(ckpt))
+                           phi.data_ptr() if phi is not None else None, int(ckpt),
+                           approx._a if approx is not None else None)
         rid = ctypes.c_ulonglong()
         check(self.lib.hv_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
-        self._keep[rid.value] = (P, m, v, d_obs, out, phi)
+        self._keep[rid.value] = (P, m, v, d_obs, out, phi, approx)
         return rid.value
 
     def submit_hv(self, P: Problem, m, v, ckpt=-1):
@@ -60,6 +62,12 @@ class Server:
         phi = torch.empty((), dtype=torch.float64, device=self.device)
         g = torch.empty((P.nz, P.nx), dtype=torch.float32, device=self.device)
         return self._submit(HV_REQ_GRAD, P, m, d_obs=d_obs, out=g, phi=phi, ckpt=ckpt), phi, g
+
+    def submit_approx(self, A, v):
+        """Queue the apply of a built Hessian approximation (PsfApprox) to v[k, nz, nx];
+        returns (request id, output tensor)."""
+        out = torch.empty(v.shape, dtype=torch.float32, device=self.device)
+        return self._submit(HV_REQ_APPROX, None, None, v=v, k=v.shape[0], out=out, approx=A), out
 
     def submit_misfit(self, P: Problem, m, d_obs):
         phi = torch.empty((), dtype=torch.float64, device=self.device)

@@ -106,3 +106,24 @@ def test_misfit_matches_oracle(problems):
     ref = O.misfit_grad(oracle_problem(w), f32(w.m), f32(dobs))[0]
     assert abs(float(phi) - ref) < 2e-4 * ref
     S.close()
+
+
+def test_approximate_hessian_requests_in_the_mix(problems):
+    """Apply requests of a built PSF approximation run among H v requests; every
+    result is bitwise that of the direct call."""
+    (w0, P0), (w1, P1) = problems
+    A = P0.approx_build_psf(t(w0.m), 8, 4, ckpt=5)
+    vs = [t(synth.smoothed_normal_vectors(300 + i, 1 + i % 3, w0.nz, w0.nx, 1.5)) for i in range(6)]
+    direct_a = [A.apply(v).cpu().numpy() for v in vs]
+    direct_h = P1.hessian_apply(t(w1.m), t(w1.v[:1]), ckpt=6).cpu().numpy()
+    S = Server(hbm_budget=1 << 30, max_concurrent=4)
+    rh, oh = S.submit_hv(P1, t(w1.m), t(w1.v[:1]), ckpt=6)
+    subs = [S.submit_approx(A, v) for v in vs]
+    assert S.wait(rh, timeout=300) == 0
+    assert np.array_equal(oh.cpu().numpy(), direct_h)
+    for (rid, out), ref in zip(subs, direct_a):
+        assert S.wait(rid, timeout=300) == 0
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert S.info(rid)["kind"] == 3
+    S.close()
+    A.close()
