@@ -163,11 +163,12 @@ struct PsfGeo {
     int S, B, R;      // lattice spacing, batches per axis, window radius (B S - 1) / 2
     int na, nb;       // sample points along z and x
     int cz0, cx0;     // first sample point
+    int k = 0, vpc = 1;   // apply launches: vectors, vectors per CTA
 };
 int launch_psf_impulses(const PsfGeo &g, float *v, cudaStream_t st);   // v zeroed, [B*B][nz][nx]
 int launch_psf_extract(const PsfGeo &g, const float *Hv, float *psf, cudaStream_t st);
 int launch_psf_apply(const PsfGeo &g, const float *psf, const float *v, int k, float *out, cudaStream_t st);
-int psf_apply_smem_bytes(int R);
+int psf_apply_smem_bytes(int S, int R, int nvec);   // dynamic shared memory of the apply kernel
 int launch_finalize(const hv_handle *h, const float *m, const double *img, int G, int k, float *out32,
                     double *out64, cudaStream_t st);
 int launch_residual(const hv_handle *h, const float *d, const float *dobs, float *r, double *partials,
