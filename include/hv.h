@@ -313,7 +313,9 @@ int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *in
  *    in the handle and writes the choice to chosen[3] and the per-launch
  *    times to ms[menu * 3] (either may be NULL).  Synchronous.  In the
  *    dataflow launch mode the three choices share one tile shape (the shape
- *    of least weighted time, weights 1 / 1.8 / 1 for the three kinds).
+ *    of least weighted time, weights 1 / 1.8 / 1 for the three kinds).  With
+ *    step fusion on, the forward-only kind is timed as fused double steps
+ *    (per step).
  *    Tune after setting the launch mode.
  *  - hv_set_tiles / hv_get_tiles: apply or read a choice (e.g. a cached one). */
 int hv_tile_menu_size(void);
@@ -347,6 +349,16 @@ int hv_set_graphs(hv_handle *h, int enable);
  *    exits costs more than the overlap gains (about 3% slower than PDL on the
  *    384 x 1152 benchmark grid), hence not the default.
  * HV_EINVAL for another mode. */
+/* Step fusion (off by default): the recomputation from snapshots runs two
+ * forward steps per launch wherever two follow each other, reading u^n (with
+ * an 8-cell halo) and u^{n-1} once (16 instead of 24 bytes per point for two
+ * steps); results are bitwise those of single steps.  Not used in the
+ * dataflow launch mode.  On GB300 the recomputed 4-cell ring (35-70% more
+ * stencil work on the benchmark's tiles) and the extra barrier cost more than
+ * the traffic saved: a fused launch takes about 120 us where two single steps
+ * take 94 us on the 384 x 1152, 32-shot grid. */
+int hv_set_step_fusion(hv_handle *h, int enable);
+
 #define HV_LAUNCH_PLAIN 0
 #define HV_LAUNCH_PDL 1
 #define HV_LAUNCH_DATAFLOW 2

@@ -82,6 +82,7 @@ _SIGS = {
     "hv_approx_destroy": ([c_void_p], c_int),
     "hv_tile_menu_size": ([], c_int),
     "hv_set_launch_mode": ([c_void_p, c_int], c_int),
+    "hv_set_step_fusion": ([c_void_p, c_int], c_int),
     "hv_tile_menu": ([c_int, ip, ip], c_int),
     "hv_tile_menu_info": ([c_int, ip], c_int),
     "hv_autotune": ([c_void_p, c_int, fp, c_size_t, c_void_p, ip, ctypes.POINTER(ctypes.c_float)], c_int),

@@ -102,6 +102,9 @@ struct Layout {
 };
 
 constexpr int kResidualBlocks = 1024;
+// Forward levels in flight besides the snapshots: the current state (2), and
+// the two outputs of a fused double step.
+constexpr int kWorkBatches = 4;
 
 int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
 {
@@ -128,7 +131,7 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
     L.C = take(fbytes);
     if (born) L.b = take((size_t)k * fbytes);
     L.zero = take(L.fb);
-    if (!adjoint || !L.history) L.work = take(3 * L.fb);
+    if (!adjoint || !L.history) L.work = take(kWorkBatches * L.fb);
     if (adjoint) L.store = take(L.history ? (size_t)h->nt * L.fb : (size_t)2 * L.slots * L.fb);
     if (born || adjoint) L.D = take((size_t)2 * k * L.fb);
     L.fields_end = o;         // every region above is a whole number of fields (fsize is 64-float aligned)
@@ -242,7 +245,7 @@ struct Exec {
         D = reinterpret_cast<float *>(ws + L.D);
         img = reinterpret_cast<double *>(ws + L.img);
         if (L.work) {
-            const int n = 3 + (L.history ? 0 : 2 * L.slots);   // work and snapshot batches are contiguous
+            const int n = kWorkBatches + (L.history ? 0 : 2 * L.slots);   // work and snapshot batches are contiguous
             for (int i = 0; i < n; ++i) pool.push_back(batch(ws + L.work, i));
             refs.assign(n, 0);
             slot_b.assign(L.slots, {-1, -1});
@@ -292,6 +295,35 @@ struct Exec {
         cur = next;
         cur_i = ni;
         j = n + 1;
+        return HV_OK;
+    }
+
+    // Two recomputation steps in one launch (k_fwd2): u^{j+1}, u^{j+2} into two
+    // free batches.  Falls back to two single steps where it does not apply.
+    int forward2(int n)
+    {
+        if (n != j) return hvi::fail(HV_EINVAL, "internal: forward step %d from state %d", n, j);
+        const int i1 = pick_free();
+        int i2 = -1;
+        for (size_t i = 0; i < pool.size(); ++i)
+            if (refs[i] == 0 && (int)i != cur_i && (int)i != prev_i && (int)i != i1) {
+                i2 = (int)i;
+                break;
+            }
+        if (!h->fuse_steps || cnt != nullptr || i1 < 0 || i2 < 0) {
+            HV_RT(forward(n, false, nullptr, nullptr, nullptr, HV_K_ADVANCE));
+            return forward(n + 1, false, nullptr, nullptr, nullptr, HV_K_ADVANCE);
+        }
+        ProfScope ps(h, st, HV_K_ADVANCE);
+        hvk::Fwd2Launch a{};
+        a.u_cur = cur; a.u_prev = prev; a.u_next1 = pool[i1]; a.u_next2 = pool[i2]; a.C = C; a.n = n;
+        HV_RT(hvk::launch_fwd2(h, h->cfg[1], rectiles_for(h, hvk::tiling(h, h->cfg[1])), maps, a, st));
+        launched_step();
+        prev = pool[i1];
+        prev_i = i1;
+        cur = pool[i2];
+        cur_i = i2;
+        j = n + 2;
         return HV_OK;
     }
 
@@ -393,10 +425,11 @@ const std::vector<hvi::Action> *schedule_for(hv_handle *h, int slots)
 int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
                      const Layout &L, cudaStream_t st);
 
-std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode)
+std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode, bool fuse)
 {
     char buf[160];
-    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode);
+    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d/%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode,
+             (int)fuse);
     return buf;
 }
 
@@ -422,7 +455,7 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     // CUDA graph and replayed (hv_set_graphs).
     const bool graph = born && h->graphs_on && !h->prof_on;
     if (graph) {
-        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode);
+        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode, h->fuse_steps);
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaStream_t cs = h->capture_stream;
@@ -504,7 +537,14 @@ int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *ph
             switch (a.op) {
             case hvi::ACT_SAVE: HV_RT(E.save(a.a0)); break;
             case hvi::ACT_RESTORE: E.restore(a.a0, a.a1); break;
-            case hvi::ACT_ADVANCE: HV_RT(E.forward(E.j, false, nullptr, nullptr, nullptr, HV_K_ADVANCE)); break;
+            case hvi::ACT_ADVANCE:
+                if (ai + 1 < sched->size() && (*sched)[ai + 1].op == hvi::ACT_ADVANCE) {
+                    HV_RT(E.forward2(E.j));             // two consecutive recomputation steps
+                    ++ai;
+                } else {
+                    HV_RT(E.forward(E.j, false, nullptr, nullptr, nullptr, HV_K_ADVANCE));
+                }
+                break;
             case hvi::ACT_ADJOINT: {
                 const float *u = E.u_for(a.a0);
                 if (!u) return hvi::fail(HV_EINVAL, "internal: adjoint step %d from state %d", a.a0, E.j);
@@ -997,6 +1037,13 @@ extern "C" int hv_set_graphs(hv_handle *h, int enable)
     return HV_OK;
 }
 
+extern "C" int hv_set_step_fusion(hv_handle *h, int enable)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    h->fuse_steps = enable != 0;
+    return HV_OK;
+}
+
 extern "C" int hv_set_launch_mode(hv_handle *h, int mode)
 {
     if (!h) return hvi::fail(HV_EINVAL, "null handle");
@@ -1022,6 +1069,7 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
     HV_CK(cudaEventCreate(&e0));
     HV_CK(cudaEventCreate(&e1));
     constexpr int kReps = 6;
+    const bool fused = h->fuse_steps && h->launch_mode != HV_LAUNCH_DATAFLOW && h->nt >= 2;
     std::vector<float> tm((size_t)nmenu * 3, 1e30f);
     float best[3] = {1e30f, 1e30f, 1e30f};
     int arg[3] = {0, 0, 0};
@@ -1036,6 +1084,11 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
                     a.u = E.zero; a.lam1 = E.Dbuf(1); a.lam_io = E.Dbuf(0); a.C = E.C; a.r = dd;
                     a.r_per_vector = 1; a.rscale = 1.0f; a.img = E.img; a.n = 0; a.k = k; a.G = L.G;
                     rc = hvk::launch_adj(h, c, rt, E.maps, a, st);
+                } else if (kind == 1 && fused) {
+                    hvk::Fwd2Launch a{};      // recomputation runs fused double steps: time one, halve it
+                    a.u_cur = E.zero; a.u_prev = E.zero; a.u_next1 = E.pool[0]; a.u_next2 = E.pool[1]; a.C = E.C;
+                    a.n = 0;
+                    rc = hvk::launch_fwd2(h, c, rt, E.maps, a, st);
                 } else {
                     hvk::FwdLaunch a{};
                     a.u_cur = E.zero; a.u_prev = E.zero; a.u_next = E.pool[0]; a.C = E.C; a.n = 0;
@@ -1051,6 +1104,7 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
             float t = 0.f;
             cudaEventElapsedTime(&t, e0, e1);
             t /= kReps;
+            if (kind == 1 && fused) t *= 0.5f;   // per step
             if (ms) ms[c * 3 + kind] = t;
             tm[c * 3 + kind] = t;
             if (t < best[kind]) {

@@ -83,6 +83,8 @@ struct hv_handle {
     cudaStream_t capture_stream = nullptr;
     // how stencil steps are ordered after one another (hv_set_launch_mode)
     int launch_mode = HV_LAUNCH_PDL;
+    // recomputation runs two steps per launch where it can (hv_set_step_fusion)
+    bool fuse_steps = false;
     std::map<std::string, cudaGraphExec_t> graphs;
     // profiling (hv_profile)
     bool prof_on = false;
@@ -106,6 +108,7 @@ constexpr int kMaxTileMenu = 16;
 struct TmaMaps {
     alignas(64) unsigned char halo[kMaxTileMenu][128];   // per tile configuration
     alignas(64) unsigned char pt[kMaxTileMenu][128];
+    alignas(64) unsigned char halo8[kMaxTileMenu][128];  // 8-cell halo (two fused steps)
     void *ws = nullptr;
     long long nfields = 0;
 };
@@ -138,6 +141,16 @@ struct FwdLaunch {
 };
 int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
                cudaStream_t st);
+
+// Two fused forward steps without Born fields or receivers (hv_stencil.cu, k_fwd2).
+struct Fwd2Launch {
+    const float *u_cur, *u_prev;   // u^n, u^{n-1}
+    float *u_next1, *u_next2;      // u^{n+1}, u^{n+2} (distinct from the inputs)
+    const float *C;
+    int n;                         // first step; n + 1 < nt
+};
+int launch_fwd2(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const Fwd2Launch &a,
+                cudaStream_t st);
 
 struct AdjLaunch {
     const float *u;                // u^n field batch [ns][fsize]

@@ -98,6 +98,35 @@ __device__ __forceinline__ void cp_async_wait_all()
 }
 constexpr int kApplyVectors = 4;   // vectors per CTA (they share the staged PSFs)
 
+// The correlations of 4 consecutive outputs of one row with the cell's NC PSFs:
+// acc[c][o] = sum_{dz, dx} p_c(dz, dx) v(row + dz, col + o + dx), from the patch
+// rows starting at `vrow` (pitch PWX floats, the strip's float4 column s) and
+// the PSFs at `sp` (NC of [W][W4]).
+template <int NC>
+__device__ __forceinline__ void correlate_strip(const float *__restrict__ vrow, int PWX, int s,
+                                                const float *__restrict__ sp, int W, int W4, float (&acc)[4][4])
+{
+    const int cstride = W * W4 / 4;   // float4s per PSF
+    for (int dz = 0; dz < W; ++dz) {
+        const float4 *vr = reinterpret_cast<const float4 *>(vrow + dz * PWX) + s;
+        const float4 *pr = reinterpret_cast<const float4 *>(sp + dz * W4);
+        float4 cur = vr[0];
+#pragma unroll 2
+        for (int d4 = 0; d4 < W4 / 4; ++d4) {
+            const float4 nxt = vr[d4 + 1];
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+                const float4 p = pr[c * cstride + d4];
+                acc[c][0] = fmaf(p.w, cur.w, fmaf(p.z, cur.z, fmaf(p.y, cur.y, fmaf(p.x, cur.x, acc[c][0]))));
+                acc[c][1] = fmaf(p.w, nxt.x, fmaf(p.z, cur.w, fmaf(p.y, cur.z, fmaf(p.x, cur.y, acc[c][1]))));
+                acc[c][2] = fmaf(p.w, nxt.y, fmaf(p.z, nxt.x, fmaf(p.y, cur.w, fmaf(p.x, cur.z, acc[c][2]))));
+                acc[c][3] = fmaf(p.w, nxt.z, fmaf(p.z, nxt.y, fmaf(p.y, nxt.x, fmaf(p.x, cur.w, acc[c][3]))));
+            }
+            cur = nxt;
+        }
+    }
+}
+
 // out_j(x) = sum over the cell's lattice points k of w_k(x) (p_k correlated with v_j)(x).
 // grid = (cells along x, cells along z, groups of 4 vectors).  The CTA stages
 // the cell's 1, 2 or 4 PSFs (rows zero-padded to a multiple of 4) and, per
@@ -147,25 +176,10 @@ __global__ void __launch_bounds__(kMaxApplyThreads) k_psf_apply(const float *__r
         for (int c = 0; c < 4; ++c)
 #pragma unroll
             for (int o = 0; o < 4; ++o) acc[c][o] = 0.0f;
-        for (int dz = 0; dz < W; ++dz) {
-            const float4 *vr = reinterpret_cast<const float4 *>(sv + (q * PH + r + dz) * PWX) + s;
-            const float4 *pr = reinterpret_cast<const float4 *>(sp + dz * W4);
-            float4 cur = vr[0];
-            for (int d4 = 0; d4 < W4 / 4; ++d4) {
-                const float4 nxt = vr[d4 + 1];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    if (c < nc) {
-                        const float4 p = pr[c * (W * W4 / 4) + d4];
-                        acc[c][0] = fmaf(p.w, cur.w, fmaf(p.z, cur.z, fmaf(p.y, cur.y, fmaf(p.x, cur.x, acc[c][0]))));
-                        acc[c][1] = fmaf(p.w, nxt.x, fmaf(p.z, cur.w, fmaf(p.y, cur.z, fmaf(p.x, cur.y, acc[c][1]))));
-                        acc[c][2] = fmaf(p.w, nxt.y, fmaf(p.z, nxt.x, fmaf(p.y, cur.w, fmaf(p.x, cur.z, acc[c][2]))));
-                        acc[c][3] = fmaf(p.w, nxt.z, fmaf(p.z, nxt.y, fmaf(p.y, nxt.x, fmaf(p.x, cur.w, acc[c][3]))));
-                    }
-                }
-                cur = nxt;
-            }
-        }
+        const float *vrow = sv + (q * PH + r) * PWX;
+        if (nc == 4) correlate_strip<4>(vrow, PWX, s, sp, W, W4, acc);
+        else if (nc == 2) correlate_strip<2>(vrow, PWX, s, sp, W, W4, acc);
+        else correlate_strip<1>(vrow, PWX, s, sp, W, W4, acc);
         const int iz = az.lo + r;
         float wz[2];
         cell_weights(az, iz, g.S, wz);

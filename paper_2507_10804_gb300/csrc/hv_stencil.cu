@@ -257,28 +257,30 @@ __device__ __forceinline__ float2 splat(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 lo(const float4 &q) { return make_float2(q.x, q.y); }
 __device__ __forceinline__ float2 hi(const float4 &q) { return make_float2(q.z, q.w); }
 
-// Lh at the thread's 4 x RZ block from a [H][W] halo tile, as RZ x 2 pairs
-// (points 4tx, 4tx+1 and 4tx+2, 4tx+3 of each row).  Per lane:
+// Lh at a 4 x RZ block of points of a shared-memory array (4 cells of halo
+// around them), as RZ x 2 pairs (points 0, 1 and 2, 3 of each row).  Per lane:
 //   d1  = ((w[x-1] - w0) + (w[x+1] - w0)) + ((w[z-1] - w0) + (w[z+1] - w0))
 //   acc = c4 ((w[x-4] + w[x+4]) + (w[z-4] + w[z+4]))
 //   acc = c3 ((w[x-3] + w[x+3]) + (w[z-3] + w[z+3])) + acc,  then c2 likewise
 //   Lh  = c1 d1 + (LCR w0 + acc)
 // The z neighbours of a pair are halves of the float4 columns; the x
-// neighbours at odd offsets are re-paired from adjacent float4s.
-template <class C>
-__device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float2 (&L)[C::RZ][2],
-                                          float2 (&ctr)[C::RZ][2])
+// neighbours at odd offsets are re-paired from adjacent float4s.  The points
+// sit at rows rbase + 4 .. rbase + 3 + RZ and float4 column c4 of an array of
+// W4 float4s per row.
+template <int RZ>
+__device__ __forceinline__ void lap_at(const float *__restrict__ sm, int W4, int rbase, int c4, float2 (&L)[RZ][2],
+                                       float2 (&ctr)[RZ][2])
 {
     const float4 *s4 = reinterpret_cast<const float4 *>(sm);
-    float4 col[C::RZ + 8];
+    float4 col[RZ + 8];
 #pragma unroll
-    for (int i = 0; i < C::RZ + 8; ++i) col[i] = s4[(tz * C::RZ + i) * C::W4 + tx + 1];
+    for (int i = 0; i < RZ + 8; ++i) col[i] = s4[(rbase + i) * W4 + c4];
 #pragma unroll
-    for (int r = 0; r < C::RZ; ++r) {
-        const int row = tz * C::RZ + r + GH;
-        const float4 xm = s4[row * C::W4 + tx];
+    for (int r = 0; r < RZ; ++r) {
+        const int row = rbase + r + GH;
+        const float4 xm = s4[row * W4 + c4 - 1];
         const float4 xc = col[r + 4];
-        const float4 xp = s4[row * C::W4 + tx + 2];
+        const float4 xp = s4[row * W4 + c4 + 1];
         // e[i] = (v[2i], v[2i+1]), o[i] = (v[2i+1], v[2i+2]) over v = xm | xc | xp
         const float2 e[6] = {lo(xm), hi(xm), lo(xc), hi(xc), lo(xp), hi(xp)};
         const float2 o[5] = {make_float2(xm.y, xm.z), make_float2(xm.w, xc.x), make_float2(xc.y, xc.z),
@@ -299,6 +301,14 @@ __device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, 
             ctr[r][pr] = cz;
         }
     }
+}
+
+// The thread's block of a CTA tile: rows tz*RZ .. of a [H][W] halo tile, float4 column tx + 1.
+template <class C>
+__device__ __forceinline__ void lap_block(const float *__restrict__ sm, int tx, int tz, float2 (&L)[C::RZ][2],
+                                          float2 (&ctr)[C::RZ][2])
+{
+    lap_at<C::RZ>(sm, C::W4, tz * C::RZ, tx + 1, L, ctr);
 }
 
 // Sponge factors of one row of the thread's block, as pairs: inv = 1 / (1 + a)
@@ -569,6 +579,166 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     };
     if (sponge) run(std::true_type{});
     else run(std::false_type{});
+}
+
+// ------------------------------------------------------------------ two fused steps
+// Two forward steps (no Born field, no receivers: the recomputation of the
+// reversal) in one pass over the fields.  The CTA computes u^{n+1} on its tile
+// extended by the 4-cell stencil reach (region E), from u^n with an 8-cell halo
+// and u^{n-1} on E; the extended ring is recomputed with exactly the arithmetic
+// of the single step (and set to zero off the padded grid, as the ghost band
+// is), so u^{n+1} and u^{n+2} are bitwise those of two single steps.  Reads
+// u^n and u^{n-1} once and writes u^{n+1} and u^{n+2}: 16 bytes per point for
+// two steps instead of 24 (plus the coefficient field, shared by the shots).
+struct Fwd2Params {
+    CUtensorMap map_halo;       // box (TX+8) x (TZ+8): u^{n-1} and C on E
+    CUtensorMap map_halo8;      // box (TX+16) x (TZ+16): u^n
+    float *ws;
+    int f_ucur, f_uprev, f_unext1, f_unext2, f_C;
+    const float *az, *ax, *wavelet;
+    const int *src_zx, *rt_off;
+    int *status;
+    int n, ns, spg;
+    Geo g;
+};
+
+template <class C>
+struct Fwd2Smem {
+    static constexpr int W8 = C::TX + 16, H8 = C::TZ + 16;
+    static constexpr int H8B = W8 * H8 * 4, H8P = (H8B + 127) / 128 * 128;
+    static constexpr int STAGE = H8P + C::HALOP;           // u^n (halo 8), u^{n-1} on E
+    static constexpr int STAGE_TX = H8B + C::HALO;
+    static constexpr int BARS = C::ST * STAGE + 2 * C::HALOP;   // + C on E, u^{n+1} on E
+    static constexpr int BYTES = BARS + 64 + kTablesBytes;
+};
+
+template <class C>
+__global__ void __launch_bounds__(C::NT, 1) k_fwd2(const __grid_constant__ Fwd2Params p)
+{
+    using S = Fwd2Smem<C>;
+    constexpr int EBX = C::BX + 2, EBZ = (C::TZ + 8) / C::RZ, NEB = EBX * EBZ;   // 4 x RZ blocks of E
+    static_assert((C::TZ + 8) % C::RZ == 0, "E rows split into whole register blocks");
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *sCe = reinterpret_cast<float *>(smem + C::ST * S::STAGE);   // C on E, [H][W]
+    float *sU1 = sCe + C::HALOP / 4;                                   // u^{n+1} on E, [H][W]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::BARS);
+    ShotTables &tab = *reinterpret_cast<ShotTables *>(smem + S::BARS + 64);
+
+    const int tile = blockIdx.x, grp = blockIdx.z;
+    const int tzi = tile / p.g.ntx, txi = tile - tzi * p.g.ntx;
+    const int z0 = tzi * C::TZ, x0 = txi * C::TX;
+    const int s0 = grp * p.spg, s1 = min(p.ns, s0 + p.spg), nitems = s1 - s0;
+    const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
+    const int xb = x0 + 4 * tx, zrow0 = z0 + tz * C::RZ;
+
+    auto issue = [&](int i) {
+        const int st = i % C::ST, s = s0 + i;
+        unsigned char *base = smem + st * S::STAGE;
+        mbar_expect_tx(&bars[st], S::STAGE_TX);
+        tma_load(base, &p.map_halo8, x0 - GH, z0 - GH, p.f_ucur + s, &bars[st]);
+        tma_load(base + S::H8P, &p.map_halo, x0, z0, p.f_uprev + s, &bars[st]);
+    };
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q <= C::ST; ++q) mbar_init(&bars[q], 1);
+        fence_mbar_init();
+    }
+    load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
+    // Sponge flags: E (tile + 4) for the first step, the tile for the second.
+    const bool sponge1 = !(z0 - GH >= p.g.nb && z0 + C::TZ + GH <= p.g.nb + p.g.nz && x0 - GH >= p.g.nb &&
+                           x0 + C::TX + GH <= p.g.nb + p.g.nx);
+    const bool sponge2 = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
+                           x0 + C::TX <= p.g.nb + p.g.nx);
+    float axv[4] = {0.f, 0.f, 0.f, 0.f};
+    if (sponge2)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
+    const float wav1 = p.wavelet[p.n], wav2 = p.wavelet[p.n + 1];
+    grid_dependency_wait();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&bars[C::ST], C::HALO);
+        tma_load(sCe, &p.map_halo, x0, z0, p.f_C, &bars[C::ST]);
+        for (int q = 0; q < C::ST && q < nitems; ++q) issue(q);
+    }
+    allow_dependent_launch();
+
+    bool ok = mbar_wait(&bars[C::ST], 0, p.status);
+    if (__syncthreads_or(!ok)) {
+        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
+        return;
+    }
+
+    auto run = [&](auto sp1_tag, auto sp2_tag) {
+        constexpr bool SP1 = decltype(sp1_tag)::value, SP2 = decltype(sp2_tag)::value;
+        for (int i = 0; i < nitems; ++i) {
+            const int st = i % C::ST, s = s0 + i;
+            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status);
+            if (__syncthreads_or(!ok)) {
+                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status);
+                return;
+            }
+            const unsigned char *base = smem + st * S::STAGE;
+            const float *sU8 = reinterpret_cast<const float *>(base);
+            const float *sUp = reinterpret_cast<const float *>(base + S::H8P);
+            float *u1g = p.ws + (unsigned long long)(p.f_unext1 + s) * p.g.fsize;
+            // ---- step n -> n+1 on E
+            for (int eb = threadIdx.x; eb < NEB; eb += C::NT) {
+                const int ebx = eb % EBX, ebz = eb / EBX;
+                const int ez0 = ebz * C::RZ, ex0 = 4 * ebx;            // E coordinates of the block
+                const int pz0 = z0 - GH + ez0, px0 = x0 - GH + ex0;    // padded-grid coordinates
+                float2 Q[C::RZ][2], uc[C::RZ][2];
+                lap_at<C::RZ>(sU8, S::W8 / 4, ez0, ebx + 1, Q, uc);
+                add_source<C>(Q, pz0, px0, tab.sz[i], tab.sx[i], wav1);
+                float axe[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) axe[c] = SP1 ? p.ax[min(max(px0 + c, 0), p.g.NX - 1)] : 0.0f;
+#pragma unroll
+                for (int r = 0; r < C::RZ; ++r) {
+                    const int pz = pz0 + r, er = ez0 + r;
+                    float2 up[2], cc[2], inv[2] = {}, nom[2] = {}, o[2];
+                    f4(sUp + er * C::W + ex0, up);
+                    f4(sCe + er * C::W + ex0, cc);
+                    if constexpr (SP1) sponge_row(p.az, min(max(pz, 0), p.g.NZ - 1), p.g.NZ, axe, inv, nom);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) o[h] = leapfrog<SP1>(uc[r][h], up[h], cc[h], Q[r][h], inv[h], nom[h]);
+                    float w[4] = {o[0].x, o[0].y, o[1].x, o[1].y};
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (pz < 0 || pz >= p.g.NZ || px0 + c < 0 || px0 + c >= p.g.NX) w[c] = 0.0f;   // ghost band
+                    *reinterpret_cast<float4 *>(sU1 + er * C::W + ex0) = make_float4(w[0], w[1], w[2], w[3]);
+                    if (er >= GH && er < C::TZ + GH && ebx >= 1 && ebx <= C::BX && pz < p.g.NZ && px0 < p.g.NX) {
+                        const float2 wo[2] = {make_float2(w[0], w[1]), make_float2(w[2], w[3])};
+                        st4(u1g + (size_t)(pz + GH) * p.g.P + (px0 + GH), wo, px0, p.g.NX);
+                    }
+                }
+            }
+            __syncthreads();
+            // ---- step n+1 -> n+2 on the tile
+            {
+                float2 Q[C::RZ][2], uc[C::RZ][2];
+                lap_block<C>(sU1, tx, tz, Q, uc);
+                add_source<C>(Q, zrow0, xb, tab.sz[i], tab.sx[i], wav2);
+                float *u2g = p.ws + (unsigned long long)(p.f_unext2 + s) * p.g.fsize;
+#pragma unroll
+                for (int r = 0; r < C::RZ; ++r) {
+                    const int z = zrow0 + r;
+                    float2 up[2], cc[2], inv[2] = {}, nom[2] = {}, o[2];
+                    f4(sU8 + (tz * C::RZ + r + 2 * GH) * S::W8 + 4 * tx + 2 * GH, up);
+                    f4(sCe + (tz * C::RZ + r + GH) * C::W + 4 * tx + GH, cc);
+                    if constexpr (SP2) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) o[h] = leapfrog<SP2>(uc[r][h], up[h], cc[h], Q[r][h], inv[h], nom[h]);
+                    if (z < p.g.NZ && xb < p.g.NX) st4(u2g + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
+                }
+            }
+            __syncthreads();                       // stage st and sU1 are free again
+            if (threadIdx.x == 0 && i + C::ST < nitems) issue(i + C::ST);
+        }
+    };
+    if (sponge2) run(std::true_type{}, std::true_type{});
+    else if (sponge1) run(std::true_type{}, std::false_type{});
+    else run(std::false_type{}, std::false_type{});
 }
 
 struct AdjParams {
@@ -916,6 +1086,7 @@ int prepare_kernels(const hv_handle *h)
             HV_RT_INTERNAL(ensure_smem(0 * kTileMenu + id, h->device, k_fwd<C, true>, FwdSmem<C, true>::BYTES));
             HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + id, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
             HV_RT_INTERNAL(ensure_smem(2 * kTileMenu + id, h->device, k_adj<C>, AdjSmem<C>::BYTES));
+            HV_RT_INTERNAL(ensure_smem(3 * kTileMenu + id, h->device, k_fwd2<C>, Fwd2Smem<C>::BYTES));
             return HV_OK;
         });
         if (rc != HV_OK) return rc;
@@ -930,6 +1101,7 @@ int make_maps(const hv_handle *h, void *ws, long long nfields, TmaMaps *m)
             using C = decltype(c);
             HV_RT_INTERNAL(encode(m->halo[id], h, ws, nfields, C::W, C::H));
             HV_RT_INTERNAL(encode(m->pt[id], h, ws, nfields, C::TX, C::TZ));
+            HV_RT_INTERNAL(encode(m->halo8[id], h, ws, nfields, C::TX + 16, C::TZ + 16));
             return (int)HV_OK;
         });
         if (rc != HV_OK) return rc;
@@ -977,6 +1149,39 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         }
         HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + cfg, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
         return launch_step(k_fwd<C, false>, grid, C::NT, FwdSmem<C, false>::BYTES, st, pdl(h), p, "k_fwd launch");
+    });
+}
+
+int launch_fwd2(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const Fwd2Launch &a,
+                cudaStream_t st)
+{
+    if (a.n + 1 >= h->nt) return hvi::fail(HV_EINVAL, "internal: fused steps %d, %d past nt = %d", a.n, a.n + 1, h->nt);
+    return with_cfg(cfg, [&](auto c) -> int {
+        using C = decltype(c);
+        const hvi::Tiling t = tiling(h, cfg);
+        const size_t fbytes = h->fsize * sizeof(float);
+        Fwd2Params p;
+        memcpy(&p.map_halo, maps.halo[cfg], sizeof(CUtensorMap));
+        memcpy(&p.map_halo8, maps.halo8[cfg], sizeof(CUtensorMap));
+        p.ws = reinterpret_cast<float *>(maps.ws);
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_cur, fbytes, &p.f_ucur));
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_prev, fbytes, &p.f_uprev));
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_next1, fbytes, &p.f_unext1));
+        HV_RT_INTERNAL(field_index(maps.ws, a.u_next2, fbytes, &p.f_unext2));
+        HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
+        if (p.f_unext1 < 0 || p.f_unext2 < 0 || p.f_unext1 == p.f_unext2 || p.f_unext1 == p.f_ucur ||
+            p.f_unext1 == p.f_uprev || p.f_unext2 == p.f_ucur || p.f_unext2 == p.f_uprev)
+            return hvi::fail(HV_EINVAL, "internal: fused steps need two outputs distinct from the inputs");
+        p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
+        p.src_zx = h->src_zx; p.rt_off = rt.off;
+        p.status = h->status;
+        p.n = a.n; p.ns = h->ns;
+        const int gsz = (h->ns + adj_groups(h) - 1) / adj_groups(h);
+        p.spg = gsz * C::GPC;
+        p.g = geo(h, t);
+        dim3 grid(t.ntiles, 1, (h->ns + p.spg - 1) / p.spg);
+        HV_RT_INTERNAL(ensure_smem(3 * kTileMenu + cfg, h->device, k_fwd2<C>, Fwd2Smem<C>::BYTES));
+        return launch_step(k_fwd2<C>, grid, C::NT, Fwd2Smem<C>::BYTES, st, pdl(h), p, "k_fwd2 launch");
     });
 }
 

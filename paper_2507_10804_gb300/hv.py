@@ -109,6 +109,10 @@ class Problem:
         check(self.lib.hv_status(self._h, ctypes.byref(c)))
         return c.value
 
+    def set_step_fusion(self, enable: bool = True) -> None:
+        """Recompute two forward steps per launch where possible (hv_set_step_fusion)."""
+        check(self.lib.hv_set_step_fusion(self._h, int(bool(enable))))
+
     def set_launch_mode(self, mode: int) -> None:
         """How stencil steps follow one another: HV_LAUNCH_PLAIN, _PDL or _DATAFLOW (hv_set_launch_mode)."""
         check(self.lib.hv_set_launch_mode(self._h, int(mode)))

@@ -110,3 +110,33 @@ def test_dataflow_launch_mode_bitwise(tiles):
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), mode
     assert P.status() == 0
+
+
+@pytest.mark.parametrize("tiles", [(0, 0, 0), (2, 6, 5), (4, 5, 7), (3, 3, 3), (9, 10, 13), (1, 15, 1)])
+def test_fused_double_steps_bitwise_equal_single_steps(tiles):
+    """The recomputation's fused double steps (u^n with an 8-cell halo, the extended
+    ring recomputed and zeroed off the padded grid) give the same bits as single steps:
+    H v with k = 2 and the gradient, binomial schedules with many recomputed steps, on a
+    ragged grid whose tiles and rings cross all four edges."""
+    w = ragged_workload(nt=140, ns=5, nr=6, k=2)
+    P = Problem.from_workload(w)
+    m = torch.tensor(w.m, dtype=torch.float32, device="cuda")
+    v = torch.tensor(w.v[:2], dtype=torch.float32, device="cuda")
+    dobs = torch.tensor(O.fwd_model(oracle_problem(w), f32(w.m) * 1.01), dtype=torch.float32, device="cuda")
+    P.set_tiles(tiles)
+
+    def run():
+        out = [P.hessian_apply(m, v, ckpt=3), P.hessian_apply(m, v, ckpt=9)]
+        phi, g = P.misfit_grad(m, dobs, ckpt=4)
+        out += [g, phi.reshape(1)]
+        torch.cuda.synchronize()
+        return [x.cpu().numpy() for x in out]
+
+    P.set_step_fusion(False)
+    ref = run()
+    P.set_step_fusion(True)
+    for graphs in (False, True):
+        P.set_graphs(graphs)
+        for a, b in zip(run(), ref):
+            assert np.array_equal(a, b), (tiles, graphs)
+    assert P.status() == 0
