@@ -72,6 +72,37 @@ def psf_fma_count(nz, nx, S, B):
     return int(np.outer(terms(nz), terms(nx)).sum()) * (2 * R + 1) ** 2
 
 
+def pdo_measure(P, m, w, dev, r=8, reps=10):
+    """Build time of the PDO approximation (one H v, cuFFT separation) and apply rate for the
+    workload's vectors; rho0 = 2 pi f_max / c_max with f_max = 2.5 f0 (the appendix's choice)."""
+    import torch
+
+    from paper_2507_10804_gb300.hv import HV_CKPT_ALL
+    rho0 = 2 * np.pi * 2.5 * w.f0 / float(w.vmax)
+    st = torch.cuda.current_stream(dev)
+    P.approx_build_pdo(m, rho0, r, ckpt=HV_CKPT_ALL).close()
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    A = P.approx_build_pdo(m, rho0, r, ckpt=HV_CKPT_ALL)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    build_ms = e0.elapsed_time(e1)
+    v = torch.tensor(w.v, dtype=torch.float32, device=dev)
+    A.apply(v)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for _ in range(reps):
+        A.apply(v)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    apply_s = e0.elapsed_time(e1) / 1e3 / reps
+    A.close()
+    return {"rho0_rad_per_m": rho0, "terms": r, "build_ms": build_ms,
+            "apply_us_per_vector": apply_s / v.shape[0] * 1e6, "apply_vectors_per_s": v.shape[0] / apply_s,
+            "what": "per vector: one forward and r inverse complex 2D FFTs (cuFFT) and two fused pointwise kernels"}
+
+
 def psf_measure(P, m, w, dev, S=12, n_batches=4, reps=10):
     """Build time of the PSF approximation (n_batches H v) and apply rate for the workload's vectors."""
     import torch
@@ -335,6 +366,7 @@ def run_ours(args, w):
                          "what": "one vector per call, stream launches, default tiles (8 vectors timed)"}
         Q.close()
     psf = psf_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
+    pdo = pdo_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     mh = torch.tensor(w.m, dtype=torch.float32).pin_memory()
     vh = torch.tensor(w.v, dtype=torch.float32).pin_memory()
@@ -416,6 +448,8 @@ def run_ours(args, w):
             line["one_at_a_time"] = one_at_a_time
         if psf is not None:
             line["psf_approximation"] = psf
+        if pdo is not None:
+            line["pdo_approximation"] = pdo
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()

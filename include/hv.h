@@ -236,8 +236,31 @@ int hv_status(hv_handle *h, int *device_status);
  *    cx0, nz, nx}.
  *  - hv_approx_psfs: copies the PSFs [r][2R+1][2R+1] into a device buffer.
  *  - hv_approx_destroy: frees the object (NULL is allowed).
- * Probing (section 3.4) and PSF+ (section 3.6): hv_approx_build_pdo is
- * declared and returns HV_ENOTSUP. */
+ *
+ * Pseudo-differential operator probing (section 3.4, appendix A), applied in
+ * the low-rank-symbol form of section 3.3, eq. (lr-psido):
+ *   H~ v = Re sum_k D_{a_k} F^-1 D_{b_k} F v,  F the 2D DFT of the nz x nx grid.
+ * Sample frequencies xi_k = rho0 (cos theta_k, sin theta_k) [rad/m], theta_k =
+ * 2 pi k / r (r even, 2..32; the paper uses 8), each snapped to the nearest
+ * DFT frequency (signed index rounded half to even), so the probe
+ * v_p = sum_k exp(i x . xi_k) is real.  One hv_hessian_apply to v_p; the
+ * symbol column a_k(x) = s(x, xi_k) is the part of the spectrum of H v_p
+ * inside the disc of radius rho0 sin(pi / r) around xi_k, moved to the origin
+ * and transformed back; b_k(xi) = (|xi| / |xi_k|) w_k(theta) with w_k the
+ * trigonometric interpolation basis of the r nominal angles (linear in the
+ * magnitude, Fourier over the angle).  rho0 + rho0 sin(pi / r) must stay below
+ * the Nyquist frequency pi / h; the paper's choice is rho0 ~ 2 pi f_max / c_max.
+ *  - hv_approx_pdo_workspace_size: bytes of `ws` the build needs for budget ckpt.
+ *  - hv_approx_build_pdo: builds it at model m on `stream` (one H v, cuFFT
+ *    transforms); the object owns its columns, weights, FFT plans and scratch.
+ *    HV_EINVAL on a bad r or rho0, HV_ENOMEM if ws is too small.
+ *  - hv_approx_apply on a PDO object: one forward and r inverse transforms per
+ *    vector; applies of one object from different streams run one after
+ *    another (they share its FFT scratch).
+ *  - hv_approx_pdo_symbol: copies a_k ([r][nz][nx] complex, interleaved
+ *    re/im floats) and/or b_k ([r][nz][nx] floats, DFT order) to device buffers.
+ *  - hv_approx_info on a PDO object: {1, r, 0, 0, 0, 0, 0, 0, 0, nz, nx}.
+ * PSF+ (section 3.6) is not provided. */
 typedef struct hv_approx hv_approx;
 #define HV_APPROX_H 0           /* apply the approximation of H_d            */
 #define HV_APPROX_SQRT 1        /* apply its SPD square root                 */
@@ -245,8 +268,10 @@ typedef struct hv_approx hv_approx;
 int hv_approx_psf_workspace_size(hv_handle *h, int n_batches, int ckpt, size_t *bytes);
 int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt, hv_approx **out,
                         void *ws, size_t ws_bytes, void *stream);
-int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, hv_approx **out, void *ws, size_t ws_bytes,
-                        void *stream);
+int hv_approx_pdo_workspace_size(hv_handle *h, int ckpt, size_t *bytes);
+int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, int ckpt, hv_approx **out, void *ws,
+                        size_t ws_bytes, void *stream);
+int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weights, void *stream);
 int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream);
 int hv_approx_info(const hv_approx *a, int *info);
 int hv_approx_psfs(const hv_approx *a, float *psf, void *stream);

@@ -76,8 +76,10 @@ _SIGS = {
                             c_int),
     "hv_approx_info": ([c_void_p, ip], c_int),
     "hv_approx_psfs": ([c_void_p, fp, c_void_p], c_int),
-    "hv_approx_build_pdo": ([c_void_p, fp, c_double, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p],
+    "hv_approx_pdo_workspace_size": ([c_void_p, c_int, ctypes.POINTER(c_size_t)], c_int),
+    "hv_approx_build_pdo": ([c_void_p, fp, c_double, c_int, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p],
                             c_int),
+    "hv_approx_pdo_symbol": ([c_void_p, fp, fp, c_void_p], c_int),
     "hv_approx_apply": ([c_void_p, fp, c_int, fp, c_int, c_void_p], c_int),
     "hv_approx_destroy": ([c_void_p], c_int),
     "hv_tile_menu_size": ([], c_int),

@@ -1153,10 +1153,11 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
 // ---------------------------------------------------------------- approximations
 // Point-spread-function approximation (section 3.2; PsiDO row form, section 3.5).
 struct hv_approx {
-    int kind = 0;           // 0: PSF
+    int kind = 0;           // 0: PSF, 1: PDO (low-rank symbol)
     int device = -1;
     hvk::PsfGeo g{};
     float *psf = nullptr;   // [na * nb][2R+1][2R+1]
+    hvk::LrSym lr;          // PDO: symbol columns, weights, FFT plans
 };
 
 namespace {
@@ -1262,10 +1263,76 @@ extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cel
     return HV_OK;
 }
 
-extern "C" int hv_approx_build_pdo(hv_handle *, const float *, double, int, hv_approx **out, void *, size_t, void *)
+// Pseudo-differential operator probing (section 3.4, appendix A).
+namespace {
+struct PdoLayout {
+    size_t vp = 0, hvp = 0, inner = 0, inner_bytes = 0, total = 0;
+};
+int pdo_layout(hv_handle *h, int ckpt, PdoLayout &P)
+{
+    Layout L;
+    HV_RT(make_layout(h, HV_OP_HV, 1, ckpt, L));
+    const size_t fb = align256((size_t)h->nz * h->nx * sizeof(float));
+    P.vp = 0;
+    P.hvp = fb;
+    P.inner = 2 * fb;
+    P.inner_bytes = L.total;
+    P.total = P.inner + L.total;
+    return HV_OK;
+}
+}  // namespace
+
+extern "C" int hv_approx_pdo_workspace_size(hv_handle *h, int ckpt, size_t *bytes)
+{
+    if (!h || !bytes) return hvi::fail(HV_EINVAL, "null handle or output");
+    PdoLayout P;
+    HV_RT(pdo_layout(h, ckpt, P));
+    *bytes = P.total;
+    return HV_OK;
+}
+
+extern "C" int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, int ckpt, hv_approx **out,
+                                   void *ws, size_t ws_bytes, void *stream)
 {
     if (out) *out = nullptr;
-    return hvi::fail(HV_ENOTSUP, "hv_approx_build_pdo: not provided in this version");
+    if (!h || !out || !m) return hvi::fail(HV_EINVAL, "null handle, model or output");
+    hvk::LrGeo g;
+    HV_RT(hvk::lr_samples(h->nz, h->nx, h->h, rho0, r, g));
+    PdoLayout P;
+    HV_RT(pdo_layout(h, ckpt, P));
+    if (!ws) return hvi::fail(HV_EINVAL, "null workspace");
+    if (((uintptr_t)ws & 255u) != 0) return hvi::fail(HV_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < P.total) return hvi::fail(HV_ENOMEM, "workspace of %zu bytes; the PDO build needs %zu", ws_bytes, P.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    float *vp = reinterpret_cast<float *>(w + P.vp);
+    float *hvp = reinterpret_cast<float *>(w + P.hvp);
+    HV_RT(hvk::launch_pdo_probe(g, vp, st));
+    HV_RT(run_adjoint(h, 2, m, vp, 1, hvp, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st));
+    hv_approx *a = new hv_approx;
+    a->kind = 1;
+    a->device = h->device;
+    int rc = hvk::lr_create(a->lr, g);
+    if (rc == HV_OK) rc = hvk::pdo_columns(a->lr, hvp, st);
+    if (rc != HV_OK) {
+        hvk::lr_destroy(a->lr);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return HV_OK;
+}
+
+extern "C" int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weights, void *stream)
+{
+    if (!a || a->kind != 1) return hvi::fail(HV_EINVAL, "not a PDO approximation");
+    if (!cols && !weights) return hvi::fail(HV_EINVAL, "null outputs");
+    const size_t n = (size_t)a->lr.g.r * a->lr.g.nz * a->lr.g.nx;
+    cudaStream_t st = (cudaStream_t)stream;
+    HV_CK(cudaStreamWaitEvent(st, a->lr.done, 0));
+    if (cols) HV_CK(cudaMemcpyAsync(cols, a->lr.a, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+    if (weights) HV_CK(cudaMemcpyAsync(weights, a->lr.b, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return HV_OK;
 }
 
 extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream)
@@ -1279,6 +1346,7 @@ extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float 
     int dev = -1;
     HV_CK(cudaGetDevice(&dev));
     if (dev != a->device) return hvi::fail(HV_EINVAL, "current device %d is not the approximation's device %d", dev, a->device);
+    if (a->kind == 1) return hvk::lr_apply(const_cast<hvk::LrSym &>(a->lr), v, k, out, (cudaStream_t)stream);
     return hvk::launch_psf_apply(a->g, a->psf, v, k, out, (cudaStream_t)stream);
 }
 
@@ -1287,6 +1355,12 @@ int hvi::approx_device(const hv_approx *a) { return a ? a->device : -1; }
 extern "C" int hv_approx_info(const hv_approx *a, int *info)
 {
     if (!a || !info) return hvi::fail(HV_EINVAL, "null approximation or output");
+    if (a->kind == 1) {
+        const hvk::LrGeo &l = a->lr.g;
+        const int vals[11] = {1, l.r, 0, 0, 0, 0, 0, 0, 0, l.nz, l.nx};
+        for (int i = 0; i < 11; ++i) info[i] = vals[i];
+        return HV_OK;
+    }
     const hvk::PsfGeo &g = a->g;
     const int vals[11] = {a->kind, g.na * g.nb, g.R, g.na, g.nb, g.S, g.B, g.cz0, g.cx0, g.nz, g.nx};
     for (int i = 0; i < 11; ++i) info[i] = vals[i];
@@ -1296,6 +1370,7 @@ extern "C" int hv_approx_info(const hv_approx *a, int *info)
 extern "C" int hv_approx_psfs(const hv_approx *a, float *psf, void *stream)
 {
     if (!a || !psf) return hvi::fail(HV_EINVAL, "null approximation or output");
+    if (a->kind != 0) return hvi::fail(HV_EINVAL, "not a PSF approximation");
     const size_t W = 2 * (size_t)a->g.R + 1;
     HV_CK(cudaMemcpyAsync(psf, a->psf, (size_t)a->g.na * a->g.nb * W * W * sizeof(float), cudaMemcpyDeviceToDevice,
                           (cudaStream_t)stream));
@@ -1305,6 +1380,10 @@ extern "C" int hv_approx_psfs(const hv_approx *a, float *psf, void *stream)
 extern "C" int hv_approx_destroy(hv_approx *a)
 {
     if (!a) return HV_OK;
+    if (a->kind == 1) {
+        cudaEventSynchronize(a->lr.done);
+        hvk::lr_destroy(a->lr);
+    }
     cudaFree(a->psf);
     delete a;
     return HV_OK;

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <cufft.h>
 
 #include <cstdarg>
 #include <cstddef>
@@ -178,6 +179,31 @@ struct PsfGeo {
     int cz0, cx0;     // first sample point
     int k = 0, vpc = 1;   // apply launches: vectors, vectors per CTA
 };
+// Low-rank-symbol PsiDO and PDO probing (hv_pdo.cu).
+constexpr int kLrMaxTerms = 32;
+struct LrGeo {
+    int nz = 0, nx = 0, r = 0;   // grid, terms (sample frequencies)
+    double h = 0, win = 0;       // spacing; separation window radius rho0 sin(pi / r) [rad/m]
+    int iz[kLrMaxTerms] = {}, ix[kLrMaxTerms] = {};   // signed DFT indices of the snapped samples
+    float rho[kLrMaxTerms] = {};                      // their radii [rad/m]
+};
+struct LrSym {
+    LrGeo g;
+    float2 *a = nullptr;   // [r][nz][nx] symbol columns a_k(x)
+    float *b = nullptr;    // [r][nz][nx] weights b_k(xi), DFT order
+    float2 *Y = nullptr, *V = nullptr;   // scratch: r spectra, one spectrum
+    cufftHandle pf = 0, pi = 0;          // single forward, r-batched inverse (C2C, nz x nx)
+    bool pf_ok = false, pi_ok = false;
+    cudaEvent_t done = nullptr;          // last use of the scratch
+    std::mutex *mu = nullptr;
+};
+int lr_samples(int nz, int nx, double h, double rho0, int r, LrGeo &g);
+int lr_create(LrSym &L, const LrGeo &g);
+void lr_destroy(LrSym &L);
+int launch_pdo_probe(const LrGeo &g, float *v, cudaStream_t st);
+int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st);
+int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st);
+
 int launch_psf_impulses(const PsfGeo &g, float *v, cudaStream_t st);   // v zeroed, [B*B][nz][nx]
 int launch_psf_extract(const PsfGeo &g, const float *Hv, float *psf, cudaStream_t st);
 int launch_psf_apply(const PsfGeo &g, const float *psf, const float *v, int k, float *out, cudaStream_t st);

@@ -1,0 +1,237 @@
+// hv_pdo.cu -- pseudo-differential operator probing (section 3.4, appendix A)
+// and the low-rank-symbol PsiDO apply (section 3.3, eq. (lr-psido)):
+//   H~ v = Re sum_k D_{a_k} F^-1 D_{b_k} F v
+// with F the 2D DFT of the interior grid (cuFFT, complex-to-complex).
+//
+// Build: the probe v_p = sum_k exp(i x . xi_k) (r sample frequencies on a
+// circle of radius rho0, snapped to DFT frequencies, +- pairs so v_p is
+// real), one Hessian application, the DFT of H v_p, and per sample the
+// spectrum inside a disc of radius rho0 sin(pi / r) around xi_k moved to the
+// origin (demodulation) and transformed back: the symbol column a_k(x) =
+// s(x, xi_k).  Weights b_k(xi) = (rho / rho_k) w_k(theta), w_k the
+// trigonometric interpolation basis of the r nominal angles.
+#include "hv_internal.h"
+
+#include <cmath>
+
+namespace hvk {
+
+namespace {
+
+__device__ __forceinline__ int signed_index(int i, int n) { return i < (n + 1) / 2 ? i : i - n; }
+
+// v_p(z, x) = sum_k cos(2 pi (iz_k z / nz + ix_k x / nx)) over the sample pairs,
+// phases reduced exactly in integers (the probe is sum_k exp(i x . xi_k)).
+__global__ void k_pdo_probe(float *v, LrGeo g)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= g.nz * g.nx) return;
+    const int z = i / g.nx, x = i - z * g.nx;
+    float s = 0.0f;
+    for (int k = 0; k < g.r; ++k) {
+        const long long pz = (((long long)g.iz[k] * z) % g.nz + g.nz) % g.nz;
+        const long long px = (((long long)g.ix[k] * x) % g.nx + g.nx) % g.nx;
+        const double ph = (double)pz / g.nz + (double)px / g.nx;   // in [0, 2)
+        s += cospif((float)(2.0 * ph));
+    }
+    v[i] = s;
+}
+
+__global__ void k_real_to_complex(const float *__restrict__ v, float2 *__restrict__ c, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) c[i] = make_float2(v[i], 0.0f);
+}
+
+// Y_k(i, j) = (U masked to the disc around xi_k)(i + iz_k, j + ix_k) / N: the
+// separated, demodulated spectrum of column k (the window decision in FP64).
+__global__ void k_pdo_separate(const float2 *__restrict__ U, float2 *__restrict__ Y, LrGeo g)
+{
+    const size_t N = (size_t)g.nz * g.nx;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)g.r * N) return;
+    const int k = (int)(t / N);
+    const int e = (int)(t - (size_t)k * N);
+    const int i = e / g.nx, j = e - i * g.nx;
+    const int si = ((i + g.iz[k]) % g.nz + g.nz) % g.nz, sj = ((j + g.ix[k]) % g.nx + g.nx) % g.nx;
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    const double fz = two_pi * ((double)signed_index(si, g.nz) / ((double)g.nz * g.h));
+    const double fx = two_pi * ((double)signed_index(sj, g.nx) / ((double)g.nx * g.h));
+    const double kz = two_pi * g.iz[k] / ((double)g.nz * g.h), kx = two_pi * g.ix[k] / ((double)g.nx * g.h);
+    const bool in = hypot(fz - kz, fx - kx) < g.win;
+    const float inv = 1.0f / (float)N;
+    const float2 u = U[(size_t)si * g.nx + sj];
+    Y[t] = in ? make_float2(u.x * inv, u.y * inv) : make_float2(0.0f, 0.0f);
+}
+
+// b_k(xi) = (rho / rho_k) (1/r) [1 + 2 sum_{m<r/2} cos(m (theta - theta_k)) + cos(r/2 (theta - theta_k))].
+__global__ void k_pdo_weights(float *__restrict__ b, LrGeo g)
+{
+    const size_t N = (size_t)g.nz * g.nx;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)g.r * N) return;
+    const int k = (int)(t / N);
+    const int e = (int)(t - (size_t)k * N);
+    const int i = e / g.nx, j = e - i * g.nx;
+    const float two_pi = 6.283185307179586f, hf = (float)g.h;
+    const float fz = two_pi * ((float)signed_index(i, g.nz) / ((float)g.nz * hf));
+    const float fx = two_pi * ((float)signed_index(j, g.nx) / ((float)g.nx * hf));
+    const float rho = hypotf(fz, fx);
+    const float d = atan2f(fz, fx) - two_pi * k / g.r;
+    float w = 1.0f;
+    for (int m = 1; m < g.r / 2; ++m) w += 2.0f * cosf(m * d);
+    w += cosf((g.r / 2) * d);
+    b[t] = rho / g.rho[k] * (w / g.r);
+}
+
+// Y_k = b_k V / N for the r terms.
+__global__ void k_lr_scale(const float2 *__restrict__ V, const float *__restrict__ b, float2 *__restrict__ Y, int r,
+                           size_t N)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)r * N) return;
+    const float2 v = V[t % N];
+    const float s = b[t] / (float)N;
+    Y[t] = make_float2(v.x * s, v.y * s);
+}
+
+// out = Re sum_k a_k y_k, summed in k order.
+__global__ void k_lr_combine(const float2 *__restrict__ A, const float2 *__restrict__ Y, float *__restrict__ out, int r,
+                             size_t N)
+{
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    float s = 0.0f;
+    for (int k = 0; k < r; ++k) {
+        const float2 a = A[(size_t)k * N + e], y = Y[(size_t)k * N + e];
+        s = fmaf(a.x, y.x, fmaf(-a.y, y.y, s));
+    }
+    out[e] = s;
+}
+
+int check(const char *what)
+{
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return HV_OK;
+}
+
+unsigned blocks_for(size_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+int cufft_check(cufftResult r, const char *what)
+{
+    if (r != CUFFT_SUCCESS) return hvi::fail(HV_ECUDA, "%s: cuFFT error %d", what, (int)r);
+    return HV_OK;
+}
+
+}  // namespace
+
+int lr_samples(int nz, int nx, double h, double rho0, int r, LrGeo &g)
+{
+    if (r < 2 || r % 2 || r > kLrMaxTerms) return hvi::fail(HV_EINVAL, "r = %d; need an even count in [2, %d]", r, kLrMaxTerms);
+    if (!(rho0 > 0)) return hvi::fail(HV_EINVAL, "rho0 must be > 0");
+    g.nz = nz;
+    g.nx = nx;
+    g.r = r;
+    g.h = h;
+    g.win = rho0 * std::sin(M_PI / r);
+    if (rho0 + g.win >= M_PI / h)
+        return hvi::fail(HV_EINVAL, "rho0 + window radius %g reaches the Nyquist frequency %g rad/m", rho0 + g.win, M_PI / h);
+    const double dz = 2.0 * M_PI / (nz * h), dx = 2.0 * M_PI / (nx * h);
+    for (int k = 0; k < r; ++k) {
+        const double th = 2.0 * M_PI * k / r;
+        g.iz[k] = (int)std::nearbyint(rho0 * std::sin(th) / dz);   // ties to even, as the oracle rounds
+        g.ix[k] = (int)std::nearbyint(rho0 * std::cos(th) / dx);
+        g.rho[k] = (float)std::hypot(g.iz[k] * dz, g.ix[k] * dx);
+        if (g.iz[k] == 0 && g.ix[k] == 0) return hvi::fail(HV_EINVAL, "rho0 %g snaps to the zero frequency", rho0);
+    }
+    return HV_OK;
+}
+
+int lr_create(LrSym &L, const LrGeo &g)
+{
+    L.g = g;
+    L.mu = new std::mutex;
+    const size_t N = (size_t)g.nz * g.nx;
+    cudaError_t e;
+    if ((e = cudaMalloc(&L.a, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&L.b, (size_t)g.r * N * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&L.Y, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&L.V, N * sizeof(float2))) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess)
+        return hvi::fail(HV_ECUDA, "low-rank symbol buffers: %s", cudaGetErrorString(e));
+    HV_RT_INTERNAL(cufft_check(cufftPlan2d(&L.pf, g.nz, g.nx, CUFFT_C2C), "cufftPlan2d"));
+    L.pf_ok = true;
+    int n[2] = {g.nz, g.nx};
+    HV_RT_INTERNAL(cufft_check(cufftPlanMany(&L.pi, 2, n, nullptr, 1, (int)N, nullptr, 1, (int)N, CUFFT_C2C, g.r),
+                               "cufftPlanMany"));
+    L.pi_ok = true;
+    return HV_OK;
+}
+
+void lr_destroy(LrSym &L)
+{
+    if (L.pf_ok) cufftDestroy(L.pf);
+    if (L.pi_ok) cufftDestroy(L.pi);
+    if (L.done) cudaEventDestroy(L.done);
+    cudaFree(L.a);
+    cudaFree(L.b);
+    cudaFree(L.Y);
+    cudaFree(L.V);
+    delete L.mu;
+    L = LrSym{};
+}
+
+int launch_pdo_probe(const LrGeo &g, float *v, cudaStream_t st)
+{
+    k_pdo_probe<<<blocks_for((size_t)g.nz * g.nx, 256), 256, 0, st>>>(v, g);
+    return check("k_pdo_probe");
+}
+
+// a_k from H v_p (real, [nz][nx]); uses L.V and L.Y as scratch.  Also fills b_k.
+int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st)
+{
+    const LrGeo &g = L.g;
+    const size_t N = (size_t)g.nz * g.nx;
+    k_real_to_complex<<<blocks_for(N, 256), 256, 0, st>>>(Hvp, L.V, (int)N);
+    HV_RT_INTERNAL(check("k_real_to_complex"));
+    std::lock_guard<std::mutex> lk(*L.mu);
+    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pf, st), "cufftSetStream"));
+    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pf, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD), "forward FFT"));
+    k_pdo_separate<<<blocks_for((size_t)g.r * N, 256), 256, 0, st>>>(L.V, L.a, g);
+    HV_RT_INTERNAL(check("k_pdo_separate"));
+    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pi, st), "cufftSetStream"));
+    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pi, (cufftComplex *)L.a, (cufftComplex *)L.a, CUFFT_INVERSE), "inverse FFT"));
+    k_pdo_weights<<<blocks_for((size_t)g.r * N, 256), 256, 0, st>>>(L.b, g);
+    HV_RT_INTERNAL(check("k_pdo_weights"));
+    cudaEventRecord(L.done, st);
+    return HV_OK;
+}
+
+int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st)
+{
+    const LrGeo &g = L.g;
+    const size_t N = (size_t)g.nz * g.nx;
+    // The object's scratch is shared: applies from different streams run one after another.
+    std::lock_guard<std::mutex> lk(*L.mu);
+    cudaError_t e = cudaStreamWaitEvent(st, L.done, 0);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
+    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pf, st), "cufftSetStream"));
+    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pi, st), "cufftSetStream"));
+    for (int j = 0; j < k; ++j) {
+        k_real_to_complex<<<blocks_for(N, 256), 256, 0, st>>>(v + (size_t)j * N, L.V, (int)N);
+        HV_RT_INTERNAL(check("k_real_to_complex"));
+        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pf, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD), "forward FFT"));
+        k_lr_scale<<<blocks_for((size_t)g.r * N, 256), 256, 0, st>>>(L.V, L.b, L.Y, g.r, N);
+        HV_RT_INTERNAL(check("k_lr_scale"));
+        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pi, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE), "inverse FFT"));
+        k_lr_combine<<<blocks_for(N, 256), 256, 0, st>>>(L.a, L.Y, out + (size_t)j * N, g.r, N);
+        HV_RT_INTERNAL(check("k_lr_combine"));
+    }
+    e = cudaEventRecord(L.done, st);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    return HV_OK;
+}
+
+}  // namespace hvk

@@ -247,9 +247,24 @@ class Problem:
                                            ctypes.byref(out), buf.data_ptr(), buf.numel(), self._stream()))
         return PsfApprox(self.lib, out, self.device)
 
+    def approx_build_pdo(self, m: torch.Tensor, rho0: float, r: int = 8, ckpt: int = HV_CKPT_ALL) -> "PdoApprox":
+        """Pseudo-differential-operator probing approximation of H_d at m (hv_approx_build_pdo): one
+        Hessian application to r sinusoids on the circle of radius rho0 [rad/m]."""
+        n = ctypes.c_size_t()
+        check(self.lib.hv_approx_pdo_workspace_size(self._h, int(ckpt), ctypes.byref(n)))
+        buf = self._ws.get("ws")
+        if buf is None or buf.numel() < n.value:
+            self._ws.pop("ws", None)
+            buf = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._ws["ws"] = buf
+        out = ctypes.c_void_p()
+        check(self.lib.hv_approx_build_pdo(self._h, self._m(m), float(rho0), int(r), int(ckpt), ctypes.byref(out),
+                                           buf.data_ptr(), buf.numel(), self._stream()))
+        return PdoApprox(self.lib, out, self.device)
 
-class PsfApprox:
-    """A built PSF approximation (owns its device memory; see hv_approx_build_psf)."""
+
+class Approx:
+    """A built Hessian approximation (owns its device memory; see hv_approx_*)."""
 
     def __init__(self, lib, handle, device):
         self.lib, self._a, self.device = lib, handle, device
@@ -268,14 +283,6 @@ class PsfApprox:
                                        ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
         return out
 
-    def psfs(self) -> torch.Tensor:
-        """The PSFs [r, 2R+1, 2R+1] (a device copy)."""
-        W = 2 * self.info["R"] + 1
-        out = torch.empty((self.info["r"], W, W), dtype=torch.float32, device=self.device)
-        check(self.lib.hv_approx_psfs(self._a, out.data_ptr(),
-                                      ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
-        return out
-
     def close(self):
         if getattr(self, "_a", None):
             self.lib.hv_approx_destroy(self._a)
@@ -286,6 +293,31 @@ class PsfApprox:
             self.close()
         except Exception:
             pass
+
+
+class PsfApprox(Approx):
+    """Point-spread-function approximation (hv_approx_build_psf)."""
+
+    def psfs(self) -> torch.Tensor:
+        """The PSFs [r, 2R+1, 2R+1] (a device copy)."""
+        W = 2 * self.info["R"] + 1
+        out = torch.empty((self.info["r"], W, W), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_approx_psfs(self._a, out.data_ptr(),
+                                      ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+        return out
+
+
+class PdoApprox(Approx):
+    """Pseudo-differential-operator probing approximation in low-rank-symbol form (hv_approx_build_pdo)."""
+
+    def symbol(self):
+        """(a [r, nz, nx] complex64 symbol columns, b [r, nz, nx] float32 weights in DFT order), device copies."""
+        r, nz, nx = self.info["r"], self.info["nz"], self.info["nx"]
+        a = torch.empty((r, nz, nx, 2), dtype=torch.float32, device=self.device)
+        b = torch.empty((r, nz, nx), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_approx_pdo_symbol(self._a, a.data_ptr(), b.data_ptr(),
+                                            ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+        return torch.view_as_complex(a), b
 
 
 def checkpoint_schedule(nt: int, slots: int):

@@ -6,8 +6,10 @@ from paper_2507_10804_gb300 import synth
 
 
 def rel(a, b) -> float:
-    a = np.asarray(a, dtype=np.float64).ravel()
-    b = np.asarray(b, dtype=np.float64).ravel()
+    """Relative L2 difference ||a - b|| / ||b|| (complex arrays keep their imaginary parts)."""
+    dt = np.complex128 if np.iscomplexobj(a) or np.iscomplexobj(b) else np.float64
+    a = np.asarray(a, dtype=dt).ravel()
+    b = np.asarray(b, dtype=dt).ravel()
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 

@@ -109,16 +109,19 @@ def test_misfit_matches_oracle(problems):
 
 
 def test_approximate_hessian_requests_in_the_mix(problems):
-    """Apply requests of a built PSF approximation run among H v requests; every
+    """Apply requests of built PSF and PDO approximations run among H v requests
+    (applies of one PDO object on different streams run one after another); every
     result is bitwise that of the direct call."""
     (w0, P0), (w1, P1) = problems
     A = P0.approx_build_psf(t(w0.m), 8, 4, ckpt=5)
+    D = P0.approx_build_pdo(t(w0.m), 0.15, 8, ckpt=5)
     vs = [t(synth.smoothed_normal_vectors(300 + i, 1 + i % 3, w0.nz, w0.nx, 1.5)) for i in range(6)]
-    direct_a = [A.apply(v).cpu().numpy() for v in vs]
+    objs = [A if i % 2 == 0 else D for i in range(6)]
+    direct_a = [o.apply(v).cpu().numpy() for o, v in zip(objs, vs)]
     direct_h = P1.hessian_apply(t(w1.m), t(w1.v[:1]), ckpt=6).cpu().numpy()
     S = Server(hbm_budget=1 << 30, max_concurrent=4)
     rh, oh = S.submit_hv(P1, t(w1.m), t(w1.v[:1]), ckpt=6)
-    subs = [S.submit_approx(A, v) for v in vs]
+    subs = [S.submit_approx(o, v) for o, v in zip(objs, vs)]
     assert S.wait(rh, timeout=300) == 0
     assert np.array_equal(oh.cpu().numpy(), direct_h)
     for (rid, out), ref in zip(subs, direct_a):
@@ -127,3 +130,4 @@ def test_approximate_hessian_requests_in_the_mix(problems):
         assert S.info(rid)["kind"] == 3
     S.close()
     A.close()
+    D.close()

@@ -122,8 +122,8 @@ def test_approximation_entry_points_validate_before_touching_the_gpu(lib):
     assert out.value is None
     assert "null" in lib.hv_last_error().decode()
     out = ctypes.c_void_p(1)
-    assert lib.hv_approx_build_pdo(None, None, ctypes.c_double(0.01), 8, ctypes.byref(out), None, 0, None) \
-        == _lib.HV_ENOTSUP
+    assert lib.hv_approx_build_pdo(None, None, ctypes.c_double(0.01), 8, 8, ctypes.byref(out), None, 0, None) \
+        == _lib.HV_EINVAL
     assert out.value is None
     assert lib.hv_approx_apply(None, None, 1, None, 0, None) == _lib.HV_EINVAL
     n = ctypes.c_size_t()
