@@ -191,9 +191,11 @@ struct LrSym {
     LrGeo g;
     float2 *a = nullptr;   // [r][nz][nx] symbol columns a_k(x)
     float *b = nullptr;    // [r][nz][nx] weights b_k(xi), DFT order
-    float2 *Y = nullptr, *V = nullptr;   // scratch: r spectra, one spectrum
-    cufftHandle pf = 0, pi = 0;          // single forward, r-batched inverse (C2C, nz x nx)
-    bool pf_ok = false, pi_ok = false;
+    float2 *Y = nullptr, *V = nullptr;   // scratch: r x kb spectra, kb spectra
+    int kb = 1;                          // vectors per apply batch
+    cufftHandle pf = 0, pi = 0;          // build: one forward, r inverse (C2C, nz x nx)
+    cufftHandle pfb = 0, pib = 0;        // apply: kb forward, r x kb inverse
+    bool pf_ok = false, pi_ok = false, pfb_ok = false, pib_ok = false;
     cudaEvent_t done = nullptr;          // last use of the scratch
     std::mutex *mu = nullptr;
 };

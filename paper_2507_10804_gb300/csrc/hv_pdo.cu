@@ -12,6 +12,7 @@
 // trigonometric interpolation basis of the r nominal angles.
 #include "hv_internal.h"
 
+#include <algorithm>
 #include <cmath>
 
 namespace hvk {
@@ -37,10 +38,10 @@ __global__ void k_pdo_probe(float *v, LrGeo g)
     v[i] = s;
 }
 
-__global__ void k_real_to_complex(const float *__restrict__ v, float2 *__restrict__ c, int n)
+__global__ void k_real_to_complex(const float *__restrict__ v, float2 *__restrict__ c, size_t n, size_t n_pad)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) c[i] = make_float2(v[i], 0.0f);
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n_pad) c[i] = make_float2(i < n ? v[i] : 0.0f, 0.0f);   // zero the unused vectors of a batch
 }
 
 // Y_k(i, j) = (U masked to the disc around xi_k)(i + iz_k, j + ix_k) / N: the
@@ -84,29 +85,33 @@ __global__ void k_pdo_weights(float *__restrict__ b, LrGeo g)
     b[t] = rho / g.rho[k] * (w / g.r);
 }
 
-// Y_k = b_k V / N for the r terms.
+// Y[k][q] = b_k V_q / N for the r terms and the kb vectors of a batch.
 __global__ void k_lr_scale(const float2 *__restrict__ V, const float *__restrict__ b, float2 *__restrict__ Y, int r,
-                           size_t N)
+                           int kb, size_t N)
 {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)r * N) return;
-    const float2 v = V[t % N];
-    const float s = b[t] / (float)N;
+    if (t >= (size_t)r * kb * N) return;
+    const size_t e = t % N, kq = t / N;
+    const int k = (int)(kq / kb), q = (int)(kq - (size_t)k * kb);
+    const float2 v = V[(size_t)q * N + e];
+    const float s = b[(size_t)k * N + e] / (float)N;
     Y[t] = make_float2(v.x * s, v.y * s);
 }
 
-// out = Re sum_k a_k y_k, summed in k order.
+// out_q = Re sum_k a_k y[k][q], summed in k order, for the nq valid vectors of a batch.
 __global__ void k_lr_combine(const float2 *__restrict__ A, const float2 *__restrict__ Y, float *__restrict__ out, int r,
-                             size_t N)
+                             int kb, int nq, size_t N)
 {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= N) return;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)nq * N) return;
+    const size_t e = t % N;
+    const int q = (int)(t / N);
     float s = 0.0f;
     for (int k = 0; k < r; ++k) {
-        const float2 a = A[(size_t)k * N + e], y = Y[(size_t)k * N + e];
+        const float2 a = A[(size_t)k * N + e], y = Y[((size_t)k * kb + q) * N + e];
         s = fmaf(a.x, y.x, fmaf(-a.y, y.y, s));
     }
-    out[e] = s;
+    out[t] = s;
 }
 
 int check(const char *what)
@@ -149,24 +154,41 @@ int lr_samples(int nz, int nx, double h, double rho0, int r, LrGeo &g)
     return HV_OK;
 }
 
+// Vectors per apply batch: up to 64, with the batch's r spectra within 256 MB.
+int lr_batch(const LrGeo &g)
+{
+    const size_t per = (size_t)g.r * g.nz * g.nx * sizeof(float2);
+    const size_t kb = per > 0 ? ((size_t)256 << 20) / per : 1;
+    return (int)std::max<size_t>(1, std::min<size_t>(64, kb));
+}
+
 int lr_create(LrSym &L, const LrGeo &g)
 {
     L.g = g;
     L.mu = new std::mutex;
+    L.kb = lr_batch(g);
     const size_t N = (size_t)g.nz * g.nx;
+    const size_t nY = (size_t)g.r * std::max(L.kb, 1) * N;   // apply: r x kb spectra; build: r spectra
     cudaError_t e;
     if ((e = cudaMalloc(&L.a, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&L.b, (size_t)g.r * N * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&L.Y, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
-        (e = cudaMalloc(&L.V, N * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&L.Y, nY * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&L.V, (size_t)L.kb * N * sizeof(float2))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "low-rank symbol buffers: %s", cudaGetErrorString(e));
+    int n[2] = {g.nz, g.nx};
     HV_RT_INTERNAL(cufft_check(cufftPlan2d(&L.pf, g.nz, g.nx, CUFFT_C2C), "cufftPlan2d"));
     L.pf_ok = true;
-    int n[2] = {g.nz, g.nx};
     HV_RT_INTERNAL(cufft_check(cufftPlanMany(&L.pi, 2, n, nullptr, 1, (int)N, nullptr, 1, (int)N, CUFFT_C2C, g.r),
                                "cufftPlanMany"));
     L.pi_ok = true;
+    HV_RT_INTERNAL(cufft_check(cufftPlanMany(&L.pfb, 2, n, nullptr, 1, (int)N, nullptr, 1, (int)N, CUFFT_C2C, L.kb),
+                               "cufftPlanMany"));
+    L.pfb_ok = true;
+    HV_RT_INTERNAL(cufft_check(cufftPlanMany(&L.pib, 2, n, nullptr, 1, (int)N, nullptr, 1, (int)N, CUFFT_C2C,
+                                             g.r * L.kb),
+                               "cufftPlanMany"));
+    L.pib_ok = true;
     return HV_OK;
 }
 
@@ -174,6 +196,8 @@ void lr_destroy(LrSym &L)
 {
     if (L.pf_ok) cufftDestroy(L.pf);
     if (L.pi_ok) cufftDestroy(L.pi);
+    if (L.pfb_ok) cufftDestroy(L.pfb);
+    if (L.pib_ok) cufftDestroy(L.pib);
     if (L.done) cudaEventDestroy(L.done);
     cudaFree(L.a);
     cudaFree(L.b);
@@ -194,7 +218,7 @@ int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st)
 {
     const LrGeo &g = L.g;
     const size_t N = (size_t)g.nz * g.nx;
-    k_real_to_complex<<<blocks_for(N, 256), 256, 0, st>>>(Hvp, L.V, (int)N);
+    k_real_to_complex<<<blocks_for(N, 256), 256, 0, st>>>(Hvp, L.V, N, N);
     HV_RT_INTERNAL(check("k_real_to_complex"));
     std::lock_guard<std::mutex> lk(*L.mu);
     HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pf, st), "cufftSetStream"));
@@ -217,16 +241,21 @@ int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st)
     std::lock_guard<std::mutex> lk(*L.mu);
     cudaError_t e = cudaStreamWaitEvent(st, L.done, 0);
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
-    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pf, st), "cufftSetStream"));
-    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pi, st), "cufftSetStream"));
-    for (int j = 0; j < k; ++j) {
-        k_real_to_complex<<<blocks_for(N, 256), 256, 0, st>>>(v + (size_t)j * N, L.V, (int)N);
+    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pfb, st), "cufftSetStream"));
+    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pib, st), "cufftSetStream"));
+    const int kb = L.kb;
+    for (int j0 = 0; j0 < k; j0 += kb) {            // batches of kb vectors (the last one zero-padded)
+        const int nq = std::min(kb, k - j0);
+        k_real_to_complex<<<blocks_for((size_t)kb * N, 256), 256, 0, st>>>(v + (size_t)j0 * N, L.V, (size_t)nq * N,
+                                                                           (size_t)kb * N);
         HV_RT_INTERNAL(check("k_real_to_complex"));
-        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pf, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD), "forward FFT"));
-        k_lr_scale<<<blocks_for((size_t)g.r * N, 256), 256, 0, st>>>(L.V, L.b, L.Y, g.r, N);
+        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD),
+                                   "forward FFT"));
+        k_lr_scale<<<blocks_for((size_t)g.r * kb * N, 256), 256, 0, st>>>(L.V, L.b, L.Y, g.r, kb, N);
         HV_RT_INTERNAL(check("k_lr_scale"));
-        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pi, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE), "inverse FFT"));
-        k_lr_combine<<<blocks_for(N, 256), 256, 0, st>>>(L.a, L.Y, out + (size_t)j * N, g.r, N);
+        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE),
+                                   "inverse FFT"));
+        k_lr_combine<<<blocks_for((size_t)nq * N, 256), 256, 0, st>>>(L.a, L.Y, out + (size_t)j0 * N, g.r, kb, nq, N);
         HV_RT_INTERNAL(check("k_lr_combine"));
     }
     e = cudaEventRecord(L.done, st);
