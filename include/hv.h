@@ -257,10 +257,28 @@ int hv_status(hv_handle *h, int *device_status);
  *  - hv_approx_apply on a PDO object: one forward and r inverse transforms per
  *    vector; applies of one object from different streams run one after
  *    another (they share its FFT scratch).
- *  - hv_approx_pdo_symbol: copies a_k ([r][nz][nx] complex, interleaved
- *    re/im floats) and/or b_k ([r][nz][nx] floats, DFT order) to device buffers.
+ *  - hv_approx_pdo_symbol: copies a_k and/or b_k ([r][nz][nx] complex each,
+ *    interleaved re/im floats; b in DFT order) to device buffers.
  *  - hv_approx_info on a PDO object: {1, r, 0, 0, 0, 0, 0, 0, 0, nz, nx}.
- * PSF+ (section 3.6) is not provided. */
+ *
+ * PSF+ (section 3.6): hv_approx_build_psfplus(psf, pdo, tol, out, stream)
+ * combines a PSF and a PDO approximation of the same grid and device into a
+ * low-rank symbol A B: the PSF symbol rows s(x_k, xi) = sum_d p_k(d) e^{i xi.d}
+ * (conjugated DFTs of the PSFs at the origin), their SVD through the Gram
+ * matrix (FP64, Hermitian Jacobi on the host) giving the
+ * basis B of the r' <= 32 singular directions with sigma >= tol sigma_1 and
+ * A0 = W U Sigma (W the PSF lattice weights), then A = (S_c B_c^H + alpha A0)
+ * (B_c B_c^H + alpha I)^-1 with S_c the PDO columns, B_c the basis at the PDO
+ * sample frequencies and alpha = ||B_c||_F^2 / ||B||_F^2.  At most 256 PSFs;
+ * synchronous on `stream` (waits for the PDO object's build).  The result is
+ * applied with hv_approx_apply (kind 2; hv_approx_pdo_symbol returns A and B);
+ * hv_approx_info gives {2, r', 0, ..., nz, nx}.  HV_EINVAL for mismatched
+ * inputs or tol outside (0, 1).
+ *
+ * hv_util_hermitian_eig: eigenvalues (descending) into w[n] and eigenvectors
+ * (columns, row-major, interleaved re/im doubles) into V[n*n*2] of the
+ * Hermitian matrix A[n*n*2] (interleaved re/im, row-major), n <= 4096: the host
+ * routine the PSF+ build uses.  HV_EINVAL if A is not Hermitian. */
 typedef struct hv_approx hv_approx;
 #define HV_APPROX_H 0           /* apply the approximation of H_d            */
 #define HV_APPROX_SQRT 1        /* apply its SPD square root                 */
@@ -272,6 +290,8 @@ int hv_approx_pdo_workspace_size(hv_handle *h, int ckpt, size_t *bytes);
 int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, int ckpt, hv_approx **out, void *ws,
                         size_t ws_bytes, void *stream);
 int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weights, void *stream);
+int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out, void *stream);
+int hv_util_hermitian_eig(int n, const double *A, double *w, double *V);
 int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream);
 int hv_approx_info(const hv_approx *a, int *info);
 int hv_approx_psfs(const hv_approx *a, float *psf, void *stream);

@@ -1153,7 +1153,7 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
 // ---------------------------------------------------------------- approximations
 // Point-spread-function approximation (section 3.2; PsiDO row form, section 3.5).
 struct hv_approx {
-    int kind = 0;           // 0: PSF, 1: PDO (low-rank symbol)
+    int kind = 0;           // 0: PSF, 1: PDO, 2: PSF+ (1 and 2: low-rank symbol)
     int device = -1;
     hvk::PsfGeo g{};
     float *psf = nullptr;   // [na * nb][2R+1][2R+1]
@@ -1323,15 +1323,41 @@ extern "C" int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, in
     return HV_OK;
 }
 
+extern "C" int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
+                                       void *stream)
+{
+    if (out) *out = nullptr;
+    if (!psf || !pdo || !out) return hvi::fail(HV_EINVAL, "null approximation or output");
+    if (psf->kind != 0 || pdo->kind != 1) return hvi::fail(HV_EINVAL, "PSF+ needs a PSF and a PDO approximation");
+    if (psf->device != pdo->device) return hvi::fail(HV_EINVAL, "the PSF and PDO approximations are on different devices");
+    if (psf->g.nz != pdo->lr.g.nz || psf->g.nx != pdo->lr.g.nx)
+        return hvi::fail(HV_EINVAL, "the PSF and PDO approximations are on different grids");
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != psf->device) return hvi::fail(HV_EINVAL, "current device %d is not the approximations' device", dev);
+    hv_approx *a = new hv_approx;
+    a->kind = 2;
+    a->device = psf->device;
+    a->g = psf->g;
+    int rc = hvk::build_psfplus(psf->g, psf->psf, pdo->lr, tol, a->lr, (cudaStream_t)stream);
+    if (rc != HV_OK) {
+        hvk::lr_destroy(a->lr);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return HV_OK;
+}
+
 extern "C" int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weights, void *stream)
 {
-    if (!a || a->kind != 1) return hvi::fail(HV_EINVAL, "not a PDO approximation");
+    if (!a || (a->kind != 1 && a->kind != 2)) return hvi::fail(HV_EINVAL, "not a low-rank-symbol approximation");
     if (!cols && !weights) return hvi::fail(HV_EINVAL, "null outputs");
     const size_t n = (size_t)a->lr.g.r * a->lr.g.nz * a->lr.g.nx;
     cudaStream_t st = (cudaStream_t)stream;
     HV_CK(cudaStreamWaitEvent(st, a->lr.done, 0));
     if (cols) HV_CK(cudaMemcpyAsync(cols, a->lr.a, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
-    if (weights) HV_CK(cudaMemcpyAsync(weights, a->lr.b, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (weights) HV_CK(cudaMemcpyAsync(weights, a->lr.b, n * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     return HV_OK;
 }
 
@@ -1346,7 +1372,7 @@ extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float 
     int dev = -1;
     HV_CK(cudaGetDevice(&dev));
     if (dev != a->device) return hvi::fail(HV_EINVAL, "current device %d is not the approximation's device %d", dev, a->device);
-    if (a->kind == 1) return hvk::lr_apply(const_cast<hvk::LrSym &>(a->lr), v, k, out, (cudaStream_t)stream);
+    if (a->kind != 0) return hvk::lr_apply(const_cast<hvk::LrSym &>(a->lr), v, k, out, (cudaStream_t)stream);
     return hvk::launch_psf_apply(a->g, a->psf, v, k, out, (cudaStream_t)stream);
 }
 
@@ -1355,9 +1381,9 @@ int hvi::approx_device(const hv_approx *a) { return a ? a->device : -1; }
 extern "C" int hv_approx_info(const hv_approx *a, int *info)
 {
     if (!a || !info) return hvi::fail(HV_EINVAL, "null approximation or output");
-    if (a->kind == 1) {
+    if (a->kind != 0) {
         const hvk::LrGeo &l = a->lr.g;
-        const int vals[11] = {1, l.r, 0, 0, 0, 0, 0, 0, 0, l.nz, l.nx};
+        const int vals[11] = {a->kind, l.r, 0, 0, 0, 0, 0, 0, 0, l.nz, l.nx};
         for (int i = 0; i < 11; ++i) info[i] = vals[i];
         return HV_OK;
     }
@@ -1380,11 +1406,11 @@ extern "C" int hv_approx_psfs(const hv_approx *a, float *psf, void *stream)
 extern "C" int hv_approx_destroy(hv_approx *a)
 {
     if (!a) return HV_OK;
-    if (a->kind == 1) {
-        cudaEventSynchronize(a->lr.done);
+    if (a->kind != 0) {
+        if (a->lr.done) cudaEventSynchronize(a->lr.done);
         hvk::lr_destroy(a->lr);
     }
-    cudaFree(a->psf);
+    if (a->kind == 0) cudaFree(a->psf);
     delete a;
     return HV_OK;
 }

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <complex>
 #include <cstdarg>
 #include <cstddef>
 #include <cstdint>
@@ -25,6 +26,11 @@ namespace hvi {
 // ---------------------------------------------------------------- status
 int fail(int code, const char *fmt, ...);
 inline int ok() { return HV_OK; }
+// hv_linalg.cpp: eigenvalues (descending) and eigenvectors (columns, row-major) of a
+// Hermitian n x n matrix; inverse of a small nonsingular matrix.
+int hermitian_eig(int n, std::vector<std::complex<double>> A, std::vector<double> &w,
+                  std::vector<std::complex<double>> &V);
+int small_inverse(int n, std::vector<std::complex<double>> M, std::vector<std::complex<double>> &inv);
 int approx_device(const hv_approx *a);   // device a Hessian approximation lives on
 
 // ---------------------------------------------------------------- schedule
@@ -189,8 +195,8 @@ struct LrGeo {
 };
 struct LrSym {
     LrGeo g;
-    float2 *a = nullptr;   // [r][nz][nx] symbol columns a_k(x)
-    float *b = nullptr;    // [r][nz][nx] weights b_k(xi), DFT order
+    float2 *a = nullptr;   // [r][nz][nx] symbol factors a_k(x)
+    float2 *b = nullptr;   // [r][nz][nx] symbol factors b_k(xi), DFT order
     float2 *Y = nullptr, *V = nullptr;   // scratch: r x kb spectra, kb spectra
     int kb = 1;                          // vectors per apply batch
     cufftHandle pf = 0, pi = 0;          // build: one forward, r inverse (C2C, nz x nx)
@@ -205,6 +211,8 @@ void lr_destroy(LrSym &L);
 int launch_pdo_probe(const LrGeo &g, float *v, cudaStream_t st);
 int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st);
 int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st);
+// PSF+ (hv_psfplus.cu): the low-rank symbol refined from PSF rows and PDO columns.
+int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double tol, LrSym &out, cudaStream_t st);
 
 int launch_psf_impulses(const PsfGeo &g, float *v, cudaStream_t st);   // v zeroed, [B*B][nz][nx]
 int launch_psf_extract(const PsfGeo &g, const float *Hv, float *psf, cudaStream_t st);

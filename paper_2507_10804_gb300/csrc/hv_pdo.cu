@@ -66,7 +66,7 @@ __global__ void k_pdo_separate(const float2 *__restrict__ U, float2 *__restrict_
 }
 
 // b_k(xi) = (rho / rho_k) (1/r) [1 + 2 sum_{m<r/2} cos(m (theta - theta_k)) + cos(r/2 (theta - theta_k))].
-__global__ void k_pdo_weights(float *__restrict__ b, LrGeo g)
+__global__ void k_pdo_weights(float2 *__restrict__ b, LrGeo g)
 {
     const size_t N = (size_t)g.nz * g.nx;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,11 +82,11 @@ __global__ void k_pdo_weights(float *__restrict__ b, LrGeo g)
     float w = 1.0f;
     for (int m = 1; m < g.r / 2; ++m) w += 2.0f * cosf(m * d);
     w += cosf((g.r / 2) * d);
-    b[t] = rho / g.rho[k] * (w / g.r);
+    b[t] = make_float2(rho / g.rho[k] * (w / g.r), 0.0f);
 }
 
-// Y[k][q] = b_k V_q / N for the r terms and the kb vectors of a batch.
-__global__ void k_lr_scale(const float2 *__restrict__ V, const float *__restrict__ b, float2 *__restrict__ Y, int r,
+// Y[k][q] = b_k V_q / N for the r terms and the kb vectors of a batch (complex products).
+__global__ void k_lr_scale(const float2 *__restrict__ V, const float2 *__restrict__ b, float2 *__restrict__ Y, int r,
                            int kb, size_t N)
 {
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -94,8 +94,9 @@ __global__ void k_lr_scale(const float2 *__restrict__ V, const float *__restrict
     const size_t e = t % N, kq = t / N;
     const int k = (int)(kq / kb), q = (int)(kq - (size_t)k * kb);
     const float2 v = V[(size_t)q * N + e];
-    const float s = b[(size_t)k * N + e] / (float)N;
-    Y[t] = make_float2(v.x * s, v.y * s);
+    const float2 w = b[(size_t)k * N + e];
+    const float inv = 1.0f / (float)N;
+    Y[t] = make_float2(fmaf(w.x, v.x, -w.y * v.y) * inv, fmaf(w.x, v.y, w.y * v.x) * inv);
 }
 
 // out_q = Re sum_k a_k y[k][q], summed in k order, for the nq valid vectors of a batch.
@@ -171,7 +172,7 @@ int lr_create(LrSym &L, const LrGeo &g)
     const size_t nY = (size_t)g.r * std::max(L.kb, 1) * N;   // apply: r x kb spectra; build: r spectra
     cudaError_t e;
     if ((e = cudaMalloc(&L.a, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
-        (e = cudaMalloc(&L.b, (size_t)g.r * N * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&L.b, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&L.Y, nY * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&L.V, (size_t)L.kb * N * sizeof(float2))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess)

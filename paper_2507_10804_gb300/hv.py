@@ -308,16 +308,37 @@ class PsfApprox(Approx):
 
 
 class PdoApprox(Approx):
-    """Pseudo-differential-operator probing approximation in low-rank-symbol form (hv_approx_build_pdo)."""
+    """A low-rank-symbol approximation: PDO probing (hv_approx_build_pdo) or PSF+ (psf_plus)."""
 
     def symbol(self):
-        """(a [r, nz, nx] complex64 symbol columns, b [r, nz, nx] float32 weights in DFT order), device copies."""
+        """(a, b): the symbol factors [r, nz, nx] complex64 each (b in DFT order), device copies."""
         r, nz, nx = self.info["r"], self.info["nz"], self.info["nx"]
         a = torch.empty((r, nz, nx, 2), dtype=torch.float32, device=self.device)
-        b = torch.empty((r, nz, nx), dtype=torch.float32, device=self.device)
+        b = torch.empty((r, nz, nx, 2), dtype=torch.float32, device=self.device)
         check(self.lib.hv_approx_pdo_symbol(self._a, a.data_ptr(), b.data_ptr(),
                                             ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
-        return torch.view_as_complex(a), b
+        return torch.view_as_complex(a), torch.view_as_complex(b)
+
+
+def psf_plus(psf: PsfApprox, pdo: PdoApprox, tol: float = 1e-3) -> PdoApprox:
+    """PSF+ (hv_approx_build_psfplus): the PSF symbol rows' dominant directions refined
+    against the PDO symbol columns; the result is a low-rank-symbol approximation."""
+    out = ctypes.c_void_p()
+    check(psf.lib.hv_approx_build_psfplus(psf._a, pdo._a, float(tol), ctypes.byref(out),
+                                          ctypes.c_void_p(torch.cuda.current_stream(psf.device).cuda_stream)))
+    return PdoApprox(psf.lib, out, psf.device)
+
+
+def hermitian_eig(A: np.ndarray):
+    """(w descending, V) of a Hermitian matrix by the library's host Jacobi routine (hv_util_hermitian_eig)."""
+    A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
+    n = A.shape[0]
+    w = np.empty(n)
+    V = np.empty((n, n), dtype=np.complex128)
+    dp = ctypes.POINTER(ctypes.c_double)
+    check(_lib.load().hv_util_hermitian_eig(n, A.view(np.float64).ctypes.data_as(dp), w.ctypes.data_as(dp),
+                                            V.view(np.float64).ctypes.data_as(dp)))
+    return w, V
 
 
 def checkpoint_schedule(nt: int, slots: int):

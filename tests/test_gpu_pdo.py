@@ -32,7 +32,7 @@ def test_pdo_columns_and_weights_match_oracle_on_the_same_hessian(ragged, r, ckp
     A = P.approx_build_pdo(m, RHO0, r, ckpt=ckpt)
     assert A.info["kind"] == 1 and A.info["r"] == r
     a, b = A.symbol()
-    a, b = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.float64)
+    a, b = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128)
     vp = torch.tensor(DO.probe(w.nz, w.nx, w.h, RHO0, r)[None], dtype=torch.float32, device="cuda")
     Hvp = P.hessian_apply(m, vp, ckpt=ckpt).cpu().numpy().astype(np.float64)[0]
     want_a = DO.extract_columns(Hvp, w.h, RHO0, r)
@@ -47,7 +47,7 @@ def test_pdo_apply_matches_oracle_on_the_same_symbol(ragged):
     w, P, m = ragged
     A = P.approx_build_pdo(m, RHO0, 8, ckpt=6)
     a, b = A.symbol()
-    a, b = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.float64)
+    a, b = a.cpu().numpy().astype(np.complex128), b.cpu().numpy().astype(np.complex128)
     v = synth.smoothed_normal_vectors(31, 3, w.nz, w.nx, 1.5)
     got = A.apply(torch.tensor(v, dtype=torch.float32, device="cuda")).cpu().numpy()
     want = DO.lr_apply(a, b, f32(v).astype(np.float64))

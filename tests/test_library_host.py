@@ -131,3 +131,32 @@ def test_approximation_entry_points_validate_before_touching_the_gpu(lib):
     info = (ctypes.c_int * 11)()
     assert lib.hv_approx_info(None, info) == _lib.HV_EINVAL
     assert lib.hv_approx_destroy(None) == _lib.HV_OK
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (2, 1), (5, 2), (40, 3), (64, 4)])
+def test_hermitian_eigensolver(n, seed):
+    """The host Jacobi routine behind the PSF+ build: A V = V diag(w), V unitary, w descending,
+    against numpy's eigh on random Hermitian matrices (with a repeated eigenvalue for n >= 5)."""
+    from paper_2507_10804_gb300.hv import hermitian_eig
+    rng = np.random.default_rng(seed)
+    X = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = X @ X.conj().T
+    if n >= 5:
+        Q, _ = np.linalg.qr(X)
+        d = np.sort(rng.standard_normal(n))[::-1]
+        d[1] = d[2]
+        A = (Q * d) @ Q.conj().T
+    w, V = hermitian_eig(A)
+    assert np.all(np.diff(w) <= 1e-12 * max(1.0, abs(w).max()))
+    np.testing.assert_allclose(w, np.sort(np.linalg.eigvalsh(A))[::-1], atol=1e-10 * max(1.0, abs(w).max()))
+    np.testing.assert_allclose(V.conj().T @ V, np.eye(n), atol=1e-12)
+    np.testing.assert_allclose(A @ V, V * w, atol=1e-10 * max(1.0, abs(w).max()))
+
+
+def test_hermitian_eigensolver_rejects_non_hermitian(lib):
+    A = np.array([[1.0, 2.0], [0.0, 1.0]], dtype=np.complex128)
+    w, V = np.empty(2), np.empty((2, 2), dtype=np.complex128)
+    dp = ctypes.POINTER(ctypes.c_double)
+    rc = lib.hv_util_hermitian_eig(2, A.view(np.float64).ctypes.data_as(dp), w.ctypes.data_as(dp),
+                                   V.view(np.float64).ctypes.data_as(dp))
+    assert rc == _lib.HV_EINVAL and "Hermitian" in lib.hv_last_error().decode()
