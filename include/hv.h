@@ -229,9 +229,9 @@ int hv_status(hv_handle *h, int *device_status);
  *    (spacing < 1, n_batches not a square of 1..8, R > 40, first sample point
  *    off the grid), HV_ENOMEM if ws is too small.
  *  - hv_approx_apply: out[k][nz][nx] = H~ v[k][nz][nx] (device, k >= 1) on
- *    `stream`, mode HV_APPROX_H.  The square-root modes (for the SPD
- *    approximation used in sampling, section 3.7) need the symbol in the
- *    frequency domain and return HV_ENOTSUP in this version.
+ *    `stream`, mode HV_APPROX_H.  The square-root modes of the PSF, PDO and
+ *    PSF+ approximations (section 3.7) return HV_ENOTSUP; the LR
+ *    approximation below has the sampling factor.
  *  - hv_approx_info: info[11] = {kind (0 = PSF), r, R, na, nb, S, B, cz0,
  *    cx0, nz, nx}.
  *  - hv_approx_psfs: copies the PSFs [r][2R+1][2R+1] into a device buffer.
@@ -275,6 +275,31 @@ int hv_status(hv_handle *h, int *device_status);
  * hv_approx_info gives {2, r', 0, ..., nz, nx}.  HV_EINVAL for mismatched
  * inputs or tol outside (0, 1).
  *
+ * Low-rank approximation (section 3.1) with the Matern prior of section 2.1,
+ * R = Gamma_pr^-1 = A^2, A = delta I - gamma Lap_h (Lap_h the 5-point
+ * Laplacian with homogeneous Neumann conditions, mirror ghost cells):
+ *  - hv_prior_apply: out = A v (op 0), A^-1 v (1), R v (2) or R^-1 v (3) for
+ *    k fields [k][nz][nx] on the device (A^-1 by the orthonormal 2D DCT-II
+ *    that diagonalises A, as dense cuBLAS SGEMMs).  Builds and frees its
+ *    tables on every call; synchronous on `stream`.
+ *  - hv_approx_lr_workspace_size: bytes of `ws` hv_approx_build_lr needs for
+ *    k test vectors and budget ckpt.
+ *  - hv_approx_build_lr: the `rank` leading eigenpairs of H_d v = lambda R v
+ *    (V^T R V = I) at model m by the randomized double pass with the caller's
+ *    test matrix omega [k][nz][nx] (device; normally standard Gaussian, drawn
+ *    by the caller): Y = R^-1 H_d omega, Q its R-orthonormal basis (the
+ *    eigen-decomposition of the R-Gram matrix in FP64, dropping directions
+ *    below 1e-12 of the largest, twice), T = Q^T H_d Q, V = Q S[:, :rank].
+ *    Two batched H v (k vectors each).  1 <= rank <= k <= 256; HV_EINVAL if
+ *    omega spans fewer than `rank` directions.  Synchronous on `stream`.
+ *  - hv_approx_apply on an LR object: HV_APPROX_H gives R V Lambda V^T R v
+ *    (the approximation of H_d, so that H~_d + R = R + R V Lambda V^T R);
+ *    HV_APPROX_INVSQRT gives (I - V S V^T R) A^-1 v with S = I - (Lambda +
+ *    I)^-1/2, which maps N(0, I) to N(0, (H~_d + R)^-1), the Laplace
+ *    approximation of the posterior; HV_APPROX_SQRT returns HV_ENOTSUP.
+ *  - hv_approx_lr_eigs: lambda[rank] (host, descending) and/or V (device
+ *    [rank][nz][nx]).  hv_approx_info gives {3, rank, 0, ..., nz, nx}.
+ *
  * hv_util_hermitian_eig: eigenvalues (descending) into w[n] and eigenvectors
  * (columns, row-major, interleaved re/im doubles) into V[n*n*2] of the
  * Hermitian matrix A[n*n*2] (interleaved re/im, row-major), n <= 4096: the host
@@ -292,6 +317,12 @@ int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, int ck
 int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weights, void *stream);
 int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out, void *stream);
 int hv_util_hermitian_eig(int n, const double *A, double *w, double *V);
+int hv_prior_apply(int nz, int nx, double h, double delta, double gamma, const float *v, int k, float *out, int op,
+                   void *stream);
+int hv_approx_lr_workspace_size(hv_handle *h, int k, int ckpt, size_t *bytes);
+int hv_approx_build_lr(hv_handle *h, const float *m, double delta, double gamma, int rank, const float *omega, int k,
+                       int ckpt, hv_approx **out, void *ws, size_t ws_bytes, void *stream);
+int hv_approx_lr_eigs(const hv_approx *a, double *lambda, float *V, void *stream);
 int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream);
 int hv_approx_info(const hv_approx *a, int *info);
 int hv_approx_psfs(const hv_approx *a, float *psf, void *stream);

@@ -83,6 +83,11 @@ _SIGS = {
     "hv_approx_build_psfplus": ([c_void_p, c_void_p, c_double, ctypes.POINTER(c_void_p), c_void_p], c_int),
     "hv_util_hermitian_eig": ([c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_double)],
                               c_int),
+    "hv_prior_apply": ([c_int, c_int, c_double, c_double, c_double, fp, c_int, fp, c_int, c_void_p], c_int),
+    "hv_approx_lr_workspace_size": ([c_void_p, c_int, c_int, ctypes.POINTER(c_size_t)], c_int),
+    "hv_approx_build_lr": ([c_void_p, fp, c_double, c_double, c_int, fp, c_int, c_int, ctypes.POINTER(c_void_p), fp,
+                            c_size_t, c_void_p], c_int),
+    "hv_approx_lr_eigs": ([c_void_p, ctypes.POINTER(c_double), fp, c_void_p], c_int),
     "hv_approx_apply": ([c_void_p, fp, c_int, fp, c_int, c_void_p], c_int),
     "hv_approx_destroy": ([c_void_p], c_int),
     "hv_tile_menu_size": ([], c_int),

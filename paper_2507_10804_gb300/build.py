@@ -16,8 +16,8 @@ BUILD = os.path.join(_PKG, "_build")
 LIB = os.path.join(BUILD, "libhv.so")
 INCLUDE = os.path.join(_ROOT, "include")
 
-SOURCES = ["hv_api.cu", "hv_kernels.cu", "hv_stencil.cu", "hv_psf.cu", "hv_pdo.cu", "hv_psfplus.cu", "hv_linalg.cpp",
-           "hv_schedule.cpp", "hv_server.cpp"]
+SOURCES = ["hv_api.cu", "hv_kernels.cu", "hv_stencil.cu", "hv_psf.cu", "hv_pdo.cu", "hv_psfplus.cu", "hv_lowrank.cu",
+           "hv_linalg.cpp", "hv_schedule.cpp", "hv_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",
               "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
@@ -60,7 +60,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcufft",
+    cmd = [nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs, "-lcufft", "-lcublas",
            "-Xlinker", "-rpath,/usr/local/cuda/lib64"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:

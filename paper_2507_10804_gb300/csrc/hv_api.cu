@@ -1153,11 +1153,13 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
 // ---------------------------------------------------------------- approximations
 // Point-spread-function approximation (section 3.2; PsiDO row form, section 3.5).
 struct hv_approx {
-    int kind = 0;           // 0: PSF, 1: PDO, 2: PSF+ (1 and 2: low-rank symbol)
+    int kind = 0;           // 0: PSF, 1: PDO, 2: PSF+ (1 and 2: low-rank symbol), 3: LR
     int device = -1;
     hvk::PsfGeo g{};
     float *psf = nullptr;   // [na * nb][2R+1][2R+1]
     hvk::LrSym lr;          // PDO: symbol columns, weights, FFT plans
+    hvk::LowRank low;       // LR: prior and generalised eigenpairs
+    int nz = 0, nx = 0;
 };
 
 namespace {
@@ -1323,6 +1325,85 @@ extern "C" int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, in
     return HV_OK;
 }
 
+// Low-rank approximation (section 3.1) with the Matern prior (section 2.1).
+extern "C" int hv_approx_lr_workspace_size(hv_handle *h, int k, int ckpt, size_t *bytes)
+{
+    if (!h || !bytes) return hvi::fail(HV_EINVAL, "null handle or output");
+    Layout L;
+    HV_RT(make_layout(h, HV_OP_HV, k, ckpt, L));
+    *bytes = align256((size_t)k * h->nz * h->nx * sizeof(float)) + L.total;
+    return HV_OK;
+}
+
+extern "C" int hv_approx_build_lr(hv_handle *h, const float *m, double delta, double gamma, int rank,
+                                  const float *omega, int k, int ckpt, hv_approx **out, void *ws, size_t ws_bytes,
+                                  void *stream)
+{
+    if (out) *out = nullptr;
+    if (!h || !m || !omega || !out) return hvi::fail(HV_EINVAL, "null handle, model, test vectors or output");
+    if (rank < 1 || k < rank || k > 256) return hvi::fail(HV_EINVAL, "rank %d with %d test vectors; need 1 <= rank <= k <= 256", rank, k);
+    Layout L;
+    HV_RT(make_layout(h, HV_OP_HV, k, ckpt, L));
+    const size_t N = (size_t)h->nz * h->nx, yb = align256((size_t)k * N * sizeof(float));
+    if (!ws) return hvi::fail(HV_EINVAL, "null workspace");
+    if (((uintptr_t)ws & 255u) != 0) return hvi::fail(HV_EINVAL, "workspace must be 256-byte aligned");
+    if (ws_bytes < yb + L.total) return hvi::fail(HV_ENOMEM, "workspace of %zu bytes; the LR build needs %zu", ws_bytes, yb + L.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    float *Y = reinterpret_cast<float *>(ws);
+    char *inner = (char *)ws + yb;
+    hv_approx *a = new hv_approx;
+    a->kind = 3;
+    a->device = h->device;
+    a->nz = h->nz;
+    a->nx = h->nx;
+    int rc = hvk::prior_create(a->low.prior, h->nz, h->nx, h->h, delta, gamma);
+    if (rc == HV_OK) rc = run_adjoint(h, 2, m, omega, k, Y, nullptr, nullptr, ckpt, inner, L.total, st);
+    if (rc == HV_OK) {
+        auto hess = [&](const float *X, int kk, float *Z) {
+            return run_adjoint(h, 2, m, X, kk, Z, nullptr, nullptr, ckpt, inner, L.total, st);
+        };
+        rc = hvk::build_lowrank(a->low, Y, k, rank, N, hess, st);
+    }
+    if (rc != HV_OK) {
+        hvk::lowrank_destroy(a->low);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return HV_OK;
+}
+
+extern "C" int hv_approx_lr_eigs(const hv_approx *a, double *lambda, float *V, void *stream)
+{
+    if (!a || a->kind != 3) return hvi::fail(HV_EINVAL, "not a low-rank approximation");
+    if (lambda)
+        for (int i = 0; i < a->low.r; ++i) lambda[i] = a->low.lam[i];
+    if (V)
+        HV_CK(cudaMemcpyAsync(V, a->low.V, (size_t)a->low.r * a->low.N * sizeof(float), cudaMemcpyDeviceToDevice,
+                              (cudaStream_t)stream));
+    return HV_OK;
+}
+
+extern "C" int hv_prior_apply(int nz, int nx, double h, double delta, double gamma, const float *v, int k, float *out,
+                              int op, void *stream)
+{
+    if (!v || !out || k < 1) return hvi::fail(HV_EINVAL, "null field or k < 1");
+    if (op < 0 || op > 3) return hvi::fail(HV_EINVAL, "prior operation %d", op);
+    hvk::Prior P;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = hvk::prior_create(P, nz, nx, h, delta, gamma);
+    if (rc == HV_OK) {
+        if (op == 0) rc = hvk::prior_A(P, v, out, k, st);
+        else if (op == 1) rc = hvk::prior_Ainv(P, v, out, k, st);
+        else if (op == 2) rc = hvk::prior_R(P, v, out, k, st);
+        else rc = hvk::prior_Rinv(P, v, out, k, st);
+    }
+    cudaError_t e = cudaStreamSynchronize(st);   // the tables are freed below
+    if (rc == HV_OK && e != cudaSuccess) rc = hvi::fail(HV_ECUDA, "prior apply: %s", cudaGetErrorString(e));
+    hvk::prior_destroy(P);
+    return rc;
+}
+
 extern "C" int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
                                        void *stream)
 {
@@ -1364,14 +1445,19 @@ extern "C" int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weig
 extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream)
 {
     if (!a) return hvi::fail(HV_EINVAL, "null approximation");
-    if (mode == HV_APPROX_SQRT || mode == HV_APPROX_INVSQRT)
-        return hvi::fail(HV_ENOTSUP, "square-root modes need the frequency-domain symbol; not provided in this version");
-    if (mode != HV_APPROX_H) return hvi::fail(HV_EINVAL, "unknown apply mode %d", mode);
+    if (mode != HV_APPROX_H && mode != HV_APPROX_SQRT && mode != HV_APPROX_INVSQRT)
+        return hvi::fail(HV_EINVAL, "unknown apply mode %d", mode);
+    if (mode == HV_APPROX_SQRT || (mode == HV_APPROX_INVSQRT && a->kind != 3))
+        return hvi::fail(HV_ENOTSUP, "this square-root mode is not provided for this approximation");
     if (!v || !out) return hvi::fail(HV_EINVAL, "null vector or output");
     if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "k = %d vectors; need 1 <= k <= 65535", k);
     int dev = -1;
     HV_CK(cudaGetDevice(&dev));
     if (dev != a->device) return hvi::fail(HV_EINVAL, "current device %d is not the approximation's device %d", dev, a->device);
+    if (a->kind == 3)
+        return hvk::lowrank_apply(const_cast<hvk::LowRank &>(a->low), v, k, out, mode == HV_APPROX_H ? 0 : 2,
+                                  (cudaStream_t)stream);
+    if (mode != HV_APPROX_H) return hvi::fail(HV_ENOTSUP, "this approximation supports only HV_APPROX_H");
     if (a->kind != 0) return hvk::lr_apply(const_cast<hvk::LrSym &>(a->lr), v, k, out, (cudaStream_t)stream);
     return hvk::launch_psf_apply(a->g, a->psf, v, k, out, (cudaStream_t)stream);
 }
@@ -1381,6 +1467,11 @@ int hvi::approx_device(const hv_approx *a) { return a ? a->device : -1; }
 extern "C" int hv_approx_info(const hv_approx *a, int *info)
 {
     if (!a || !info) return hvi::fail(HV_EINVAL, "null approximation or output");
+    if (a->kind == 3) {
+        const int vals[11] = {3, a->low.r, 0, 0, 0, 0, 0, 0, 0, a->nz, a->nx};
+        for (int i = 0; i < 11; ++i) info[i] = vals[i];
+        return HV_OK;
+    }
     if (a->kind != 0) {
         const hvk::LrGeo &l = a->lr.g;
         const int vals[11] = {a->kind, l.r, 0, 0, 0, 0, 0, 0, 0, l.nz, l.nx};
@@ -1406,7 +1497,10 @@ extern "C" int hv_approx_psfs(const hv_approx *a, float *psf, void *stream)
 extern "C" int hv_approx_destroy(hv_approx *a)
 {
     if (!a) return HV_OK;
-    if (a->kind != 0) {
+    if (a->kind == 3) {
+        cudaDeviceSynchronize();
+        hvk::lowrank_destroy(a->low);
+    } else if (a->kind != 0) {
         if (a->lr.done) cudaEventSynchronize(a->lr.done);
         hvk::lr_destroy(a->lr);
     }

@@ -1,6 +1,7 @@
 // hv_internal.h -- private declarations shared by the libhv translation units.
 #pragma once
 
+#include <cublas_v2.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 
@@ -8,6 +9,7 @@
 #include <cstdarg>
 #include <cstddef>
 #include <cstdint>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <string>
@@ -211,6 +213,43 @@ void lr_destroy(LrSym &L);
 int launch_pdo_probe(const LrGeo &g, float *v, cudaStream_t st);
 int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st);
 int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st);
+// Matern prior and the low-rank approximation (hv_lowrank.cu).
+struct Prior {
+    int nz = 0, nx = 0;
+    double h = 0, delta = 0, gamma = 0;
+    float *Cz = nullptr, *Cx = nullptr;   // orthonormal DCT-II matrices
+    float *inv = nullptr;                 // 1 / (delta + gamma lambda_kl) in DCT order
+    double *Czd = nullptr, *Cxd = nullptr, *invd = nullptr;   // the same in FP64 (low-rank build)
+    float *tmp = nullptr;                 // scratch, 2 tmp_k fields
+    double *tmpd = nullptr;
+    int tmp_k = 0, tmpd_k = 0;
+    cublasHandle_t blas = nullptr;
+    bool blas_ok = false;
+};
+int prior_create(Prior &P, int nz, int nx, double h, double delta, double gamma);
+void prior_destroy(Prior &P);
+int prior_A(const Prior &P, const float *v, float *out, int k, cudaStream_t st);
+int prior_Ainv(Prior &P, const float *v, float *out, int k, cudaStream_t st);
+int prior_R(Prior &P, const float *v, float *out, int k, cudaStream_t st);
+int prior_Rinv(Prior &P, const float *v, float *out, int k, cudaStream_t st);
+struct LowRank {
+    Prior prior;
+    int r = 0;
+    size_t N = 0;
+    std::vector<double> lam;   // eigenvalues, descending
+    float *V = nullptr;        // [r][N], V^T R V = I
+    float *W = nullptr;        // [r][N], W = A V
+    float *U = nullptr;        // [r][N], U = A W = R V
+    double *w = nullptr;       // [2r]: Lambda, then S_r = 1 - (Lambda + 1)^-1/2
+    double *c = nullptr;       // [r] scratch coefficients
+    float *x = nullptr;        // [N] scratch field
+};
+// Y_in = H_d Omega [k][N]; `hessian(X, kk, out)` applies H_d to kk fields.
+int build_lowrank(LowRank &L, const float *Y_in, int k, int rank, size_t N,
+                  const std::function<int(const float *, int, float *)> &hessian, cudaStream_t st);
+void lowrank_destroy(LowRank &L);
+int lowrank_apply(LowRank &L, const float *v, int k, float *out, int mode, cudaStream_t st);
+
 // PSF+ (hv_psfplus.cu): the low-rank symbol refined from PSF rows and PDO columns.
 int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double tol, LrSym &out, cudaStream_t st);
 

@@ -247,6 +247,24 @@ class Problem:
                                            ctypes.byref(out), buf.data_ptr(), buf.numel(), self._stream()))
         return PsfApprox(self.lib, out, self.device)
 
+    def approx_build_lr(self, m: torch.Tensor, delta: float, gamma: float, rank: int, omega: torch.Tensor,
+                        ckpt: int = HV_CKPT_ALL) -> "LrApprox":
+        """Low-rank approximation (hv_approx_build_lr): the `rank` leading eigenpairs of H_d v = lambda R v
+        with the Matern prior R = (delta I - gamma Lap)^2, from the test matrix omega [k, nz, nx]."""
+        k = omega.shape[0]
+        po = _dev(omega, torch.float32, (k, self.nz, self.nx), "omega", self.device)
+        n = ctypes.c_size_t()
+        check(self.lib.hv_approx_lr_workspace_size(self._h, int(k), int(ckpt), ctypes.byref(n)))
+        buf = self._ws.get("ws")
+        if buf is None or buf.numel() < n.value:
+            self._ws.pop("ws", None)
+            buf = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._ws["ws"] = buf
+        out = ctypes.c_void_p()
+        check(self.lib.hv_approx_build_lr(self._h, self._m(m), float(delta), float(gamma), int(rank), po, int(k),
+                                          int(ckpt), ctypes.byref(out), buf.data_ptr(), buf.numel(), self._stream()))
+        return LrApprox(self.lib, out, self.device)
+
     def approx_build_pdo(self, m: torch.Tensor, rho0: float, r: int = 8, ckpt: int = HV_CKPT_ALL) -> "PdoApprox":
         """Pseudo-differential-operator probing approximation of H_d at m (hv_approx_build_pdo): one
         Hessian application to r sinusoids on the circle of radius rho0 [rad/m]."""
@@ -273,13 +291,13 @@ class Approx:
         keys = ("kind", "r", "R", "na", "nb", "S", "B", "cz0", "cx0", "nz", "nx")
         self.info = dict(zip(keys, list(info)))
 
-    def apply(self, v: torch.Tensor) -> torch.Tensor:
-        """H~ v for v[k, nz, nx] -> [k, nz, nx] (hv_approx_apply, mode H)."""
+    def apply(self, v: torch.Tensor, mode: int = 0) -> torch.Tensor:
+        """H~ v (mode 0 = HV_APPROX_H) or the mode's operator for v[k, nz, nx] -> [k, nz, nx] (hv_approx_apply)."""
         nz, nx = self.info["nz"], self.info["nx"]
         k = v.shape[0]
         pv = _dev(v, torch.float32, (k, nz, nx), "v", self.device)
         out = torch.empty((k, nz, nx), dtype=torch.float32, device=self.device)
-        check(self.lib.hv_approx_apply(self._a, pv, k, out.data_ptr(), 0,
+        check(self.lib.hv_approx_apply(self._a, pv, k, out.data_ptr(), int(mode),
                                        ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
         return out
 
@@ -318,6 +336,33 @@ class PdoApprox(Approx):
         check(self.lib.hv_approx_pdo_symbol(self._a, a.data_ptr(), b.data_ptr(),
                                             ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
         return torch.view_as_complex(a), torch.view_as_complex(b)
+
+
+class LrApprox(Approx):
+    """Low-rank approximation with the Matern prior (hv_approx_build_lr)."""
+
+    def eigs(self):
+        """(lambda [rank] float64 numpy, V [rank, nz, nx] device tensor) of H_d v = lambda R v."""
+        r, nz, nx = self.info["r"], self.info["nz"], self.info["nx"]
+        lam = np.empty(r)
+        V = torch.empty((r, nz, nx), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_approx_lr_eigs(self._a, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), V.data_ptr(),
+                                         ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+        return lam, V
+
+    def sample_factor(self, n: torch.Tensor) -> torch.Tensor:
+        """(I - V S V^T R) A^-1 n: maps N(0, I) draws to the Laplace approximation N(0, (H~_d + R)^-1)."""
+        return self.apply(n, mode=2)
+
+
+def prior_apply(v: torch.Tensor, h: float, delta: float, gamma: float, op: int) -> torch.Tensor:
+    """A v (op 0), A^-1 v (1), R v (2) or R^-1 v (3) for the Matern prior, v [k, nz, nx] (hv_prior_apply)."""
+    k, nz, nx = v.shape
+    pv = _dev(v, torch.float32, (k, nz, nx), "v", v.device)
+    out = torch.empty_like(v, dtype=torch.float32)
+    check(_lib.load().hv_prior_apply(nz, nx, float(h), float(delta), float(gamma), pv, k, out.data_ptr(), int(op),
+                                     ctypes.c_void_p(torch.cuda.current_stream(v.device).cuda_stream)))
+    return out
 
 
 def psf_plus(psf: PsfApprox, pdo: PdoApprox, tol: float = 1e-3) -> PdoApprox:
