@@ -18,6 +18,9 @@ What it computes, in the paper's order:
    whose minimiser is A = (S~_c B_c^H + alpha A0)(B_c B_c^H + alpha I)^{-1}.
 The approximation is applied as sum_i D_{A[:, i]} F^-1 D_{B[i]} F (eq. (lr-psido)).
 
+With spd = True (section 3.7) the rows and columns are those of the square
+root, sqrt(max(Re s, 0)), and the result B is applied as B B^T.
+
 Readings (stated in the design notes): r' = the number of singular values at
 least tol * sigma_1 (tol = 1e-3), at most 32; the PSF weights are those of the
 PSF oracle (bilinear on the lattice); the DFT is the periodic transform of the
@@ -52,12 +55,17 @@ def rank_of(sv: np.ndarray, tol: float = 1e-3) -> int:
     return int(min(MAX_RANK, max(1, np.count_nonzero(sv >= tol * sv[0]))))
 
 
-def psf_plus(P: np.ndarray, S: int, B: int, cols: np.ndarray, h: float, rho0: float, r_c: int, tol: float = 1e-3):
+def psf_plus(P: np.ndarray, S: int, B: int, cols: np.ndarray, h: float, rho0: float, r_c: int, tol: float = 1e-3,
+             spd: bool = False):
     """(a [r', nz, nx], b [r', nz, nx]) of the PSF+ symbol from PSFs P (lattice S, batches B x B) and
-    PDO columns cols [r_c, nz, nx] at the snapped samples of (rho0, r_c)."""
+    PDO columns cols [r_c, nz, nx] at the snapped samples of (rho0, r_c).  spd: the symbol of the
+    square root (section 3.7): rows and columns replaced by sqrt(max(Re s, 0)) before the SVD."""
     _, nz, nx = cols.shape
     N = nz * nx
     rows = psf_rows(P, nz, nx).reshape(P.shape[0], N)
+    if spd:
+        rows = np.sqrt(np.maximum(rows.real, 0.0)).astype(np.complex128)
+        cols = np.sqrt(np.maximum(cols.real, 0.0)).astype(np.complex128)
     Wt = PO.weights(nz, nx, S).reshape(P.shape[0], N).T            # N x r
     U, sv, Vh = np.linalg.svd(rows, full_matrices=False)
     rr = rank_of(sv, tol)
