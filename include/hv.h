@@ -229,9 +229,9 @@ int hv_status(hv_handle *h, int *device_status);
  *    (spacing < 1, n_batches not a square of 1..8, R > 40, first sample point
  *    off the grid), HV_ENOMEM if ws is too small.
  *  - hv_approx_apply: out[k][nz][nx] = H~ v[k][nz][nx] (device, k >= 1) on
- *    `stream`, mode HV_APPROX_H.  The square-root modes of the PSF, PDO and
- *    PSF+ approximations (section 3.7) return HV_ENOTSUP; the LR
- *    approximation below has the sampling factor.
+ *    `stream`, mode HV_APPROX_H.  The other modes return HV_ENOTSUP for a PSF
+ *    approximation; the square-root forms below and the LR approximation
+ *    provide them.
  *  - hv_approx_info: info[11] = {kind (0 = PSF), r, R, na, nb, S, B, cz0,
  *    cx0, nz, nx}.
  *  - hv_approx_psfs: copies the PSFs [r][2R+1][2R+1] into a device buffer.
@@ -259,7 +259,8 @@ int hv_status(hv_handle *h, int *device_status);
  *    another (they share its FFT scratch).
  *  - hv_approx_pdo_symbol: copies a_k and/or b_k ([r][nz][nx] complex each,
  *    interleaved re/im floats; b in DFT order) to device buffers.
- *  - hv_approx_info on a PDO object: {1, r, 0, 0, 0, 0, 0, 0, 0, nz, nx}.
+ *  - hv_approx_info on a PDO object: {1, r, spd, 0, 0, 0, 0, 0, 0, nz, nx}
+ *    (spd = 1 for the square-root form below).
  *
  * PSF+ (section 3.6): hv_approx_build_psfplus(psf, pdo, tol, out, stream)
  * combines a PSF and a PDO approximation of the same grid and device into a
@@ -272,7 +273,7 @@ int hv_status(hv_handle *h, int *device_status);
  * sample frequencies and alpha = ||B_c||_F^2 / ||B||_F^2.  At most 256 PSFs;
  * synchronous on `stream` (waits for the PDO object's build).  The result is
  * applied with hv_approx_apply (kind 2; hv_approx_pdo_symbol returns A and B);
- * hv_approx_info gives {2, r', 0, ..., nz, nx}.  HV_EINVAL for mismatched
+ * hv_approx_info gives {2, r', spd, 0, ..., nz, nx}.  HV_EINVAL for mismatched
  * inputs or tol outside (0, 1).
  *
  * Low-rank approximation (section 3.1) with the Matern prior of section 2.1,
@@ -300,14 +301,34 @@ int hv_status(hv_handle *h, int *device_status);
  *  - hv_approx_lr_eigs: lambda[rank] (host, descending) and/or V (device
  *    [rank][nz][nx]).  hv_approx_info gives {3, rank, 0, ..., nz, nx}.
  *
+ * Square-root (SPD) forms (section 3.7): the square root of H_d is
+ * approximated by the same procedure with the pointwise square root
+ * sqrt(max(Re s, 0)) of the computed symbol columns (PDO) or rows and columns
+ * (PSF+), giving a factor B = Re sum_k D_{a_k} F^-1 D_{b_k} F, and H~_d = B B^T
+ * is symmetric positive semi-definite.
+ *  - hv_approx_sqrt_pdo: from a PDO approximation of H_d (kind 1, not itself a
+ *    square root), a new object with a_k = sqrt(max(Re a_k, 0)) and weights
+ *    of radial order 1/2: b_k(xi) = (|xi| / |xi_k|)^(1/2) w_k(theta) (the
+ *    square root of the order-1 symbol is of order 1/2).
+ *  - hv_approx_build_psfplus_sqrt: as hv_approx_build_psfplus with the PSF
+ *    symbol rows and the PDO columns replaced by sqrt(max(Re s, 0)) before the
+ *    SVD and the refinement.
+ *  - hv_approx_apply on such an object (hv_approx_info()[2] == 1):
+ *    HV_APPROX_H gives B B^T v, HV_APPROX_SQRT B v, HV_APPROX_SQRT_T
+ *    B^T v = Re F^-1 sum_k conj(b_k) F (conj(a_k) v); HV_APPROX_INVSQRT returns
+ *    HV_ENOTSUP (posterior samples need a solve with B B^T + R: see
+ *    hv_sample_posterior).  On a PDO or PSF+ approximation of H_d itself only
+ *    HV_APPROX_H (B v) is provided.
+ *
  * hv_util_hermitian_eig: eigenvalues (descending) into w[n] and eigenvectors
  * (columns, row-major, interleaved re/im doubles) into V[n*n*2] of the
  * Hermitian matrix A[n*n*2] (interleaved re/im, row-major), n <= 4096: the host
  * routine the PSF+ build uses.  HV_EINVAL if A is not Hermitian. */
 typedef struct hv_approx hv_approx;
 #define HV_APPROX_H 0           /* apply the approximation of H_d            */
-#define HV_APPROX_SQRT 1        /* apply its SPD square root                 */
-#define HV_APPROX_INVSQRT 2     /* apply the inverse square root             */
+#define HV_APPROX_SQRT 1        /* apply its square-root factor B            */
+#define HV_APPROX_INVSQRT 2     /* apply the posterior sampling factor       */
+#define HV_APPROX_SQRT_T 3      /* apply the transpose B^T of the factor     */
 int hv_approx_psf_workspace_size(hv_handle *h, int n_batches, int ckpt, size_t *bytes);
 int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt, hv_approx **out,
                         void *ws, size_t ws_bytes, void *stream);
@@ -316,6 +337,9 @@ int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, int ck
                         size_t ws_bytes, void *stream);
 int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weights, void *stream);
 int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out, void *stream);
+int hv_approx_sqrt_pdo(const hv_approx *pdo, hv_approx **out, void *stream);
+int hv_approx_build_psfplus_sqrt(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
+                                 void *stream);
 int hv_util_hermitian_eig(int n, const double *A, double *w, double *V);
 int hv_prior_apply(int nz, int nx, double h, double delta, double gamma, const float *v, int k, float *out, int op,
                    void *stream);

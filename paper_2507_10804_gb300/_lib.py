@@ -46,6 +46,7 @@ class HvRequestInfo(ctypes.Structure):
 
 
 HV_REQ_HV, HV_REQ_GRAD, HV_REQ_MISFIT, HV_REQ_APPROX = 0, 1, 2, 3
+HV_APPROX_H, HV_APPROX_SQRT, HV_APPROX_INVSQRT, HV_APPROX_SQRT_T = 0, 1, 2, 3
 HV_REQ_QUEUED, HV_REQ_RUNNING = 100, 101
 
 _SIGS = {
@@ -81,6 +82,8 @@ _SIGS = {
                             c_int),
     "hv_approx_pdo_symbol": ([c_void_p, fp, fp, c_void_p], c_int),
     "hv_approx_build_psfplus": ([c_void_p, c_void_p, c_double, ctypes.POINTER(c_void_p), c_void_p], c_int),
+    "hv_approx_build_psfplus_sqrt": ([c_void_p, c_void_p, c_double, ctypes.POINTER(c_void_p), c_void_p], c_int),
+    "hv_approx_sqrt_pdo": ([c_void_p, ctypes.POINTER(c_void_p), c_void_p], c_int),
     "hv_util_hermitian_eig": ([c_int, ctypes.POINTER(c_double), ctypes.POINTER(c_double), ctypes.POINTER(c_double)],
                               c_int),
     "hv_prior_apply": ([c_int, c_int, c_double, c_double, c_double, fp, c_int, fp, c_int, c_void_p], c_int),

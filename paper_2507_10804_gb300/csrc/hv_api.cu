@@ -1404,8 +1404,8 @@ extern "C" int hv_prior_apply(int nz, int nx, double h, double delta, double gam
     return rc;
 }
 
-extern "C" int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
-                                       void *stream)
+static int build_psfplus_common(const hv_approx *psf, const hv_approx *pdo, double tol, bool spd, hv_approx **out,
+                                void *stream)
 {
     if (out) *out = nullptr;
     if (!psf || !pdo || !out) return hvi::fail(HV_EINVAL, "null approximation or output");
@@ -1420,7 +1420,40 @@ extern "C" int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pd
     a->kind = 2;
     a->device = psf->device;
     a->g = psf->g;
-    int rc = hvk::build_psfplus(psf->g, psf->psf, pdo->lr, tol, a->lr, (cudaStream_t)stream);
+    int rc = hvk::build_psfplus(psf->g, psf->psf, pdo->lr, tol, spd, a->lr, (cudaStream_t)stream);
+    if (rc != HV_OK) {
+        hvk::lr_destroy(a->lr);
+        delete a;
+        return rc;
+    }
+    *out = a;
+    return HV_OK;
+}
+
+extern "C" int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
+                                       void *stream)
+{
+    return build_psfplus_common(psf, pdo, tol, false, out, stream);
+}
+
+extern "C" int hv_approx_build_psfplus_sqrt(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
+                                            void *stream)
+{
+    return build_psfplus_common(psf, pdo, tol, true, out, stream);
+}
+
+extern "C" int hv_approx_sqrt_pdo(const hv_approx *pdo, hv_approx **out, void *stream)
+{
+    if (out) *out = nullptr;
+    if (!pdo || !out) return hvi::fail(HV_EINVAL, "null approximation or output");
+    if (pdo->kind != 1 || pdo->lr.spd) return hvi::fail(HV_EINVAL, "the square root is taken of a PDO approximation of H_d");
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != pdo->device) return hvi::fail(HV_EINVAL, "current device %d is not the approximation's device", dev);
+    hv_approx *a = new hv_approx;
+    a->kind = 1;
+    a->device = pdo->device;
+    int rc = hvk::pdo_sqrt(pdo->lr, a->lr, (cudaStream_t)stream);
     if (rc != HV_OK) {
         hvk::lr_destroy(a->lr);
         delete a;
@@ -1445,10 +1478,11 @@ extern "C" int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weig
 extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream)
 {
     if (!a) return hvi::fail(HV_EINVAL, "null approximation");
-    if (mode != HV_APPROX_H && mode != HV_APPROX_SQRT && mode != HV_APPROX_INVSQRT)
-        return hvi::fail(HV_EINVAL, "unknown apply mode %d", mode);
-    if (mode == HV_APPROX_SQRT || (mode == HV_APPROX_INVSQRT && a->kind != 3))
-        return hvi::fail(HV_ENOTSUP, "this square-root mode is not provided for this approximation");
+    if (mode < HV_APPROX_H || mode > HV_APPROX_SQRT_T) return hvi::fail(HV_EINVAL, "unknown apply mode %d", mode);
+    const bool spd = (a->kind == 1 || a->kind == 2) && a->lr.spd;
+    const bool ok = mode == HV_APPROX_H || (a->kind == 3 && mode == HV_APPROX_INVSQRT) ||
+                    (spd && (mode == HV_APPROX_SQRT || mode == HV_APPROX_SQRT_T));
+    if (!ok) return hvi::fail(HV_ENOTSUP, "apply mode %d is not provided for this approximation", mode);
     if (!v || !out) return hvi::fail(HV_EINVAL, "null vector or output");
     if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "k = %d vectors; need 1 <= k <= 65535", k);
     int dev = -1;
@@ -1457,8 +1491,12 @@ extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float 
     if (a->kind == 3)
         return hvk::lowrank_apply(const_cast<hvk::LowRank &>(a->low), v, k, out, mode == HV_APPROX_H ? 0 : 2,
                                   (cudaStream_t)stream);
-    if (mode != HV_APPROX_H) return hvi::fail(HV_ENOTSUP, "this approximation supports only HV_APPROX_H");
-    if (a->kind != 0) return hvk::lr_apply(const_cast<hvk::LrSym &>(a->lr), v, k, out, (cudaStream_t)stream);
+    if (a->kind != 0) {
+        const int op = mode == HV_APPROX_SQRT ? hvk::kLrForward
+                       : mode == HV_APPROX_SQRT_T ? hvk::kLrTranspose
+                       : spd ? hvk::kLrGram : hvk::kLrForward;
+        return hvk::lr_apply(const_cast<hvk::LrSym &>(a->lr), v, k, out, (cudaStream_t)stream, op);
+    }
     return hvk::launch_psf_apply(a->g, a->psf, v, k, out, (cudaStream_t)stream);
 }
 
@@ -1474,7 +1512,7 @@ extern "C" int hv_approx_info(const hv_approx *a, int *info)
     }
     if (a->kind != 0) {
         const hvk::LrGeo &l = a->lr.g;
-        const int vals[11] = {a->kind, l.r, 0, 0, 0, 0, 0, 0, 0, l.nz, l.nx};
+        const int vals[11] = {a->kind, l.r, a->lr.spd ? 1 : 0, 0, 0, 0, 0, 0, 0, l.nz, l.nx};
         for (int i = 0; i < 11; ++i) info[i] = vals[i];
         return HV_OK;
     }

@@ -200,6 +200,8 @@ struct LrSym {
     float2 *a = nullptr;   // [r][nz][nx] symbol factors a_k(x)
     float2 *b = nullptr;   // [r][nz][nx] symbol factors b_k(xi), DFT order
     float2 *Y = nullptr, *V = nullptr;   // scratch: r x kb spectra, kb spectra
+    float *T = nullptr;                  // scratch: kb real fields (B^T v of B B^T v)
+    bool spd = false;                    // square-root symbol: the approximation is B B^T
     int kb = 1;                          // vectors per apply batch
     cufftHandle pf = 0, pi = 0;          // build: one forward, r inverse (C2C, nz x nx)
     cufftHandle pfb = 0, pib = 0;        // apply: kb forward, r x kb inverse
@@ -212,7 +214,10 @@ int lr_create(LrSym &L, const LrGeo &g);
 void lr_destroy(LrSym &L);
 int launch_pdo_probe(const LrGeo &g, float *v, cudaStream_t st);
 int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st);
-int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st);
+constexpr int kLrForward = 0, kLrTranspose = 1, kLrGram = 2;   // B v, B^T v, B B^T v
+int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st, int op = kLrForward);
+int pdo_sqrt(const LrSym &src, LrSym &out, cudaStream_t st);
+void launch_sqrt_real(const float2 *in, float2 *out, size_t n, cudaStream_t st);
 // Matern prior and the low-rank approximation (hv_lowrank.cu).
 struct Prior {
     int nz = 0, nx = 0;
@@ -251,7 +256,8 @@ void lowrank_destroy(LowRank &L);
 int lowrank_apply(LowRank &L, const float *v, int k, float *out, int mode, cudaStream_t st);
 
 // PSF+ (hv_psfplus.cu): the low-rank symbol refined from PSF rows and PDO columns.
-int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double tol, LrSym &out, cudaStream_t st);
+int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double tol, bool spd, LrSym &out,
+                  cudaStream_t st);
 
 int launch_psf_impulses(const PsfGeo &g, float *v, cudaStream_t st);   // v zeroed, [B*B][nz][nx]
 int launch_psf_extract(const PsfGeo &g, const float *Hv, float *psf, cudaStream_t st);

@@ -10,6 +10,9 @@
 // origin (demodulation) and transformed back: the symbol column a_k(x) =
 // s(x, xi_k).  Weights b_k(xi) = (rho / rho_k) w_k(theta), w_k the
 // trigonometric interpolation basis of the r nominal angles.
+// The transposed apply B^T w = Re F^-1 sum_k conj(b_k) F (conj(a_k) w) and the
+// square-root form of section 3.7 (columns sqrt(max(Re a_k, 0)), weights with
+// radial order 1/2, approximation B B^T) live here too.
 #include "hv_internal.h"
 
 #include <algorithm>
@@ -65,8 +68,9 @@ __global__ void k_pdo_separate(const float2 *__restrict__ U, float2 *__restrict_
     Y[t] = in ? make_float2(u.x * inv, u.y * inv) : make_float2(0.0f, 0.0f);
 }
 
-// b_k(xi) = (rho / rho_k) (1/r) [1 + 2 sum_{m<r/2} cos(m (theta - theta_k)) + cos(r/2 (theta - theta_k))].
-__global__ void k_pdo_weights(float2 *__restrict__ b, LrGeo g)
+// b_k(xi) = (rho / rho_k)^p (1/r) [1 + 2 sum_{m<r/2} cos(m (theta - theta_k)) + cos(r/2 (theta - theta_k))],
+// p = 1 (the order of H_d) or 1/2 (its square root).
+__global__ void k_pdo_weights(float2 *__restrict__ b, LrGeo g, bool half_order)
 {
     const size_t N = (size_t)g.nz * g.nx;
     const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -82,7 +86,15 @@ __global__ void k_pdo_weights(float2 *__restrict__ b, LrGeo g)
     float w = 1.0f;
     for (int m = 1; m < g.r / 2; ++m) w += 2.0f * cosf(m * d);
     w += cosf((g.r / 2) * d);
-    b[t] = make_float2(rho / g.rho[k] * (w / g.r), 0.0f);
+    const float radial = rho / g.rho[k];
+    b[t] = make_float2((half_order ? sqrtf(radial) : radial) * (w / g.r), 0.0f);
+}
+
+// a <- (sqrt(max(Re a, 0)), 0): the symbol of the square root (section 3.7).
+__global__ void k_sqrt_real(const float2 *in, float2 *out, size_t n)   // in == out allowed
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = make_float2(sqrtf(fmaxf(in[i].x, 0.0f)), 0.0f);
 }
 
 // Y[k][q] = b_k V_q / N for the r terms and the kb vectors of a batch (complex products).
@@ -113,6 +125,43 @@ __global__ void k_lr_combine(const float2 *__restrict__ A, const float2 *__restr
         s = fmaf(a.x, y.x, fmaf(-a.y, y.y, s));
     }
     out[t] = s;
+}
+
+// Transposed apply, first half: Y[k][q] = conj(a_k) w_q (complex times real).
+__global__ void k_lrT_premul(const float *__restrict__ w, const float2 *__restrict__ A, float2 *__restrict__ Y, int r,
+                             int kb, int nq, size_t N)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)r * kb * N) return;
+    const size_t e = t % N, kq = t / N;
+    const int k = (int)(kq / kb), q = (int)(kq - (size_t)k * kb);
+    const float x = q < nq ? w[(size_t)q * N + e] : 0.0f;
+    const float2 a = A[(size_t)k * N + e];
+    Y[t] = make_float2(a.x * x, -a.y * x);
+}
+
+// Transposed apply, second half: V_q = (1/N) sum_k conj(b_k) Y[k][q], in k order.
+__global__ void k_lrT_sum(const float2 *__restrict__ Y, const float2 *__restrict__ b, float2 *__restrict__ V, int r,
+                          int kb, size_t N)
+{
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)kb * N) return;
+    const size_t e = t % N;
+    const int q = (int)(t / N);
+    float re = 0.0f, im = 0.0f;
+    for (int k = 0; k < r; ++k) {
+        const float2 w = b[(size_t)k * N + e], y = Y[((size_t)k * kb + q) * N + e];
+        re = fmaf(w.x, y.x, fmaf(w.y, y.y, re));     // conj(w) y
+        im = fmaf(w.x, y.y, fmaf(-w.y, y.x, im));
+    }
+    const float inv = 1.0f / (float)N;
+    V[t] = make_float2(re * inv, im * inv);
+}
+
+__global__ void k_real_part(const float2 *__restrict__ V, float *__restrict__ out, size_t n)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = V[i].x;
 }
 
 int check(const char *what)
@@ -175,6 +224,7 @@ int lr_create(LrSym &L, const LrGeo &g)
         (e = cudaMalloc(&L.b, (size_t)g.r * N * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&L.Y, nY * sizeof(float2))) != cudaSuccess ||
         (e = cudaMalloc(&L.V, (size_t)L.kb * N * sizeof(float2))) != cudaSuccess ||
+        (e = cudaMalloc(&L.T, (size_t)L.kb * N * sizeof(float))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "low-rank symbol buffers: %s", cudaGetErrorString(e));
     int n[2] = {g.nz, g.nx};
@@ -204,6 +254,7 @@ void lr_destroy(LrSym &L)
     cudaFree(L.b);
     cudaFree(L.Y);
     cudaFree(L.V);
+    cudaFree(L.T);
     delete L.mu;
     L = LrSym{};
 }
@@ -228,13 +279,49 @@ int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st)
     HV_RT_INTERNAL(check("k_pdo_separate"));
     HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pi, st), "cufftSetStream"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pi, (cufftComplex *)L.a, (cufftComplex *)L.a, CUFFT_INVERSE), "inverse FFT"));
-    k_pdo_weights<<<blocks_for((size_t)g.r * N, 256), 256, 0, st>>>(L.b, g);
+    k_pdo_weights<<<blocks_for((size_t)g.r * N, 256), 256, 0, st>>>(L.b, g, false);
     HV_RT_INTERNAL(check("k_pdo_weights"));
     cudaEventRecord(L.done, st);
     return HV_OK;
 }
 
-int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st)
+// One batch (nq <= kb vectors) of the forward apply B v = Re sum_k a_k F^-1 (b_k F v).
+static int lr_batch_forward(LrSym &L, const float *v, int nq, float *out, cudaStream_t st)
+{
+    const LrGeo &g = L.g;
+    const size_t N = (size_t)g.nz * g.nx;
+    const int kb = L.kb;
+    k_real_to_complex<<<blocks_for((size_t)kb * N, 256), 256, 0, st>>>(v, L.V, (size_t)nq * N, (size_t)kb * N);
+    HV_RT_INTERNAL(check("k_real_to_complex"));
+    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD),
+                               "forward FFT"));
+    k_lr_scale<<<blocks_for((size_t)g.r * kb * N, 256), 256, 0, st>>>(L.V, L.b, L.Y, g.r, kb, N);
+    HV_RT_INTERNAL(check("k_lr_scale"));
+    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE),
+                               "inverse FFT"));
+    k_lr_combine<<<blocks_for((size_t)nq * N, 256), 256, 0, st>>>(L.a, L.Y, out, g.r, kb, nq, N);
+    return check("k_lr_combine");
+}
+
+// One batch of the transposed apply B^T w = Re F^-1 sum_k conj(b_k) F (conj(a_k) w).
+static int lr_batch_transpose(LrSym &L, const float *w, int nq, float *out, cudaStream_t st)
+{
+    const LrGeo &g = L.g;
+    const size_t N = (size_t)g.nz * g.nx;
+    const int kb = L.kb;
+    k_lrT_premul<<<blocks_for((size_t)g.r * kb * N, 256), 256, 0, st>>>(w, L.a, L.Y, g.r, kb, nq, N);
+    HV_RT_INTERNAL(check("k_lrT_premul"));
+    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_FORWARD),
+                               "forward FFT"));
+    k_lrT_sum<<<blocks_for((size_t)kb * N, 256), 256, 0, st>>>(L.Y, L.b, L.V, g.r, kb, N);
+    HV_RT_INTERNAL(check("k_lrT_sum"));
+    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_INVERSE),
+                               "inverse FFT"));
+    k_real_part<<<blocks_for((size_t)nq * N, 256), 256, 0, st>>>(L.V, out, (size_t)nq * N);
+    return check("k_real_part");
+}
+
+int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st, int op)
 {
     const LrGeo &g = L.g;
     const size_t N = (size_t)g.nz * g.nx;
@@ -247,21 +334,44 @@ int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st)
     const int kb = L.kb;
     for (int j0 = 0; j0 < k; j0 += kb) {            // batches of kb vectors (the last one zero-padded)
         const int nq = std::min(kb, k - j0);
-        k_real_to_complex<<<blocks_for((size_t)kb * N, 256), 256, 0, st>>>(v + (size_t)j0 * N, L.V, (size_t)nq * N,
-                                                                           (size_t)kb * N);
-        HV_RT_INTERNAL(check("k_real_to_complex"));
-        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD),
-                                   "forward FFT"));
-        k_lr_scale<<<blocks_for((size_t)g.r * kb * N, 256), 256, 0, st>>>(L.V, L.b, L.Y, g.r, kb, N);
-        HV_RT_INTERNAL(check("k_lr_scale"));
-        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE),
-                                   "inverse FFT"));
-        k_lr_combine<<<blocks_for((size_t)nq * N, 256), 256, 0, st>>>(L.a, L.Y, out + (size_t)j0 * N, g.r, kb, nq, N);
-        HV_RT_INTERNAL(check("k_lr_combine"));
+        const float *vj = v + (size_t)j0 * N;
+        float *oj = out + (size_t)j0 * N;
+        if (op == kLrForward) {
+            HV_RT_INTERNAL(lr_batch_forward(L, vj, nq, oj, st));
+        } else if (op == kLrTranspose) {
+            HV_RT_INTERNAL(lr_batch_transpose(L, vj, nq, oj, st));
+        } else {                                     // B B^T
+            HV_RT_INTERNAL(lr_batch_transpose(L, vj, nq, L.T, st));
+            HV_RT_INTERNAL(lr_batch_forward(L, L.T, nq, oj, st));
+        }
     }
     e = cudaEventRecord(L.done, st);
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
     return HV_OK;
+}
+
+// The square-root PDO approximation (section 3.7) of the PDO approximation src.
+int pdo_sqrt(const LrSym &src, LrSym &out, cudaStream_t st)
+{
+    HV_RT_INTERNAL(lr_create(out, src.g));
+    out.spd = true;
+    cudaError_t e = cudaStreamWaitEvent(st, src.done, 0);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
+    const size_t n = (size_t)src.g.r * src.g.nz * src.g.nx;
+    k_sqrt_real<<<blocks_for(n, 256), 256, 0, st>>>(src.a, out.a, n);
+    HV_RT_INTERNAL(check("k_sqrt_real"));
+    k_pdo_weights<<<blocks_for(n, 256), 256, 0, st>>>(out.b, out.g, true);
+    HV_RT_INTERNAL(check("k_pdo_weights"));
+    e = cudaEventRecord(out.done, st);
+    if (e == cudaSuccess) e = cudaEventRecord(src.done, st);   // destroying src now waits for the copy
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    return HV_OK;
+}
+
+void launch_sqrt_real(const float2 *in, float2 *out, size_t n, cudaStream_t st)
+{
+    k_sqrt_real<<<blocks_for(n, 256), 256, 0, st>>>(in, out, n);
+    count_launch();
 }
 
 }  // namespace hvk

@@ -10,7 +10,9 @@
 //     A = (S~_c B_c^H + alpha A0)(B_c B_c^H + alpha I)^-1,
 //     alpha = ||B_c||_F^2 / ||B||_F^2 (= ||B_c||_F^2 / r', B has orthonormal rows).
 // The result is applied by the low-rank-symbol engine (hv_pdo.cu) with a_i =
-// A[:, i], b_i = B[i].
+// A[:, i], b_i = B[i].  The square-root form (section 3.7) replaces the rows
+// and the PDO columns by sqrt(max(Re s, 0)) before step 2; it is applied as
+// B B^T.
 #include "hv_internal.h"
 
 #include <algorithm>
@@ -194,7 +196,8 @@ struct Scratch {
 
 }  // namespace
 
-int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double tol, LrSym &out, cudaStream_t st)
+int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double tol, bool spd, LrSym &out,
+                  cudaStream_t st)
 {
     const int r = pg.na * pg.nb, nz = pg.nz, nx = pg.nx, W = 2 * pg.R + 1, rc = pdo.g.r;
     const size_t N = (size_t)nz * nx;
@@ -223,6 +226,16 @@ int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double t
     if (fr != CUFFT_SUCCESS) return hvi::fail(HV_ECUDA, "PSF row transforms: cuFFT error %d", (int)fr);
     k_conj<<<nblk((size_t)r * N, 256), 256, 0, st>>>(S, (size_t)r * N);
     HV_RT_INTERNAL(launched("k_conj"));
+    const float2 *cols = pdo.a;
+    if (spd) {   // section 3.7: rows and columns of the square root, sqrt(max(Re s, 0))
+        float2 *sc_cols = nullptr;
+        HV_RT_INTERNAL(sc.get(&sc_cols, (size_t)rc * N * sizeof(float2)));
+        launch_sqrt_real(S, S, (size_t)r * N, st);
+        launch_sqrt_real(pdo.a, sc_cols, (size_t)rc * N, st);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "k_sqrt_real: %s", cudaGetErrorString(e));
+        cols = sc_cols;
+    }
     // 2. Gram matrix, eigen-decomposition on the host, basis and A0
     k_gram<<<dim3(r, r), 256, 0, st>>>(S, G, r, N);
     HV_RT_INTERNAL(launched("k_gram"));
@@ -266,6 +279,7 @@ int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double t
     g.r = rr;
     g.h = pdo.g.h;
     HV_RT_INTERNAL(lr_create(out, g));
+    out.spd = spd;
     k_basis<<<nblk((size_t)rr * N, 256), 256, 0, st>>>(S, Ud, sigd, out.b, r, rr, N);
     HV_RT_INTERNAL(launched("k_basis"));
     k_a0<<<nblk((size_t)rr * N, 256), 256, 0, st>>>(Ud, sigd, A0, pg, rr);
@@ -294,7 +308,7 @@ int build_psfplus(const PsfGeo &pg, const float *psf, const LrSym &pdo, double t
     for (size_t i = 0; i < Mh.size(); ++i) Mh[i] = make_float2((float)Minv[i].real(), (float)Minv[i].imag());
     e = cudaMemcpyAsync(Minvd, Mh.data(), Mh.size() * sizeof(float2), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "PSF+ upload: %s", cudaGetErrorString(e));
-    k_refine<<<nblk(N, 128), 128, 0, st>>>(pdo.a, Bc, A0, Minvd, (float)alpha, out.a, rr, rc, N);
+    k_refine<<<nblk(N, 128), 128, 0, st>>>(cols, Bc, A0, Minvd, (float)alpha, out.a, rr, rc, N);
     HV_RT_INTERNAL(launched("k_refine"));
     e = cudaStreamSynchronize(st);   // the scratch is freed on return
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "PSF+ build: %s", cudaGetErrorString(e));

@@ -290,6 +290,8 @@ class Approx:
         check(self.lib.hv_approx_info(self._a, info))
         keys = ("kind", "r", "R", "na", "nb", "S", "B", "cz0", "cx0", "nz", "nx")
         self.info = dict(zip(keys, list(info)))
+        if self.info["kind"] in (1, 2):
+            self.info["spd"] = self.info.pop("R")
 
     def apply(self, v: torch.Tensor, mode: int = 0) -> torch.Tensor:
         """H~ v (mode 0 = HV_APPROX_H) or the mode's operator for v[k, nz, nx] -> [k, nz, nx] (hv_approx_apply)."""
@@ -337,6 +339,14 @@ class PdoApprox(Approx):
                                             ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
         return torch.view_as_complex(a), torch.view_as_complex(b)
 
+    def sqrt(self) -> "PdoApprox":
+        """The square-root form (section 3.7) of a PDO approximation (hv_approx_sqrt_pdo): apply gives
+        B B^T v, apply(v, HV_APPROX_SQRT) B v and apply(v, HV_APPROX_SQRT_T) B^T v."""
+        out = ctypes.c_void_p()
+        check(self.lib.hv_approx_sqrt_pdo(self._a, ctypes.byref(out),
+                                          ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)))
+        return PdoApprox(self.lib, out, self.device)
+
 
 class LrApprox(Approx):
     """Low-rank approximation with the Matern prior (hv_approx_build_lr)."""
@@ -365,12 +375,14 @@ def prior_apply(v: torch.Tensor, h: float, delta: float, gamma: float, op: int) 
     return out
 
 
-def psf_plus(psf: PsfApprox, pdo: PdoApprox, tol: float = 1e-3) -> PdoApprox:
+def psf_plus(psf: PsfApprox, pdo: PdoApprox, tol: float = 1e-3, spd: bool = False) -> PdoApprox:
     """PSF+ (hv_approx_build_psfplus): the PSF symbol rows' dominant directions refined
-    against the PDO symbol columns; the result is a low-rank-symbol approximation."""
+    against the PDO symbol columns; the result is a low-rank-symbol approximation.  spd: the
+    square-root form of section 3.7 (hv_approx_build_psfplus_sqrt), applied as B B^T."""
     out = ctypes.c_void_p()
-    check(psf.lib.hv_approx_build_psfplus(psf._a, pdo._a, float(tol), ctypes.byref(out),
-                                          ctypes.c_void_p(torch.cuda.current_stream(psf.device).cuda_stream)))
+    fn = psf.lib.hv_approx_build_psfplus_sqrt if spd else psf.lib.hv_approx_build_psfplus
+    check(fn(psf._a, pdo._a, float(tol), ctypes.byref(out),
+             ctypes.c_void_p(torch.cuda.current_stream(psf.device).cuda_stream)))
     return PdoApprox(psf.lib, out, psf.device)
 
 
