@@ -352,6 +352,71 @@ int hv_approx_info(const hv_approx *a, int *info);
 int hv_approx_psfs(const hv_approx *a, float *psf, void *stream);
 int hv_approx_destroy(hv_approx *a);
 
+/* Operators given by the caller.  hv_operator describes a linear operator on
+ * nz x nx fields with spacing h: apply(ctx, v, k, out, stream) writes
+ * out[k][nz][nx] = Op v[k][nz][nx] (device buffers, stream-ordered on
+ * `stream`) and returns HV_OK or an HV_E* code.  The *_op builds construct the
+ * approximations of such an operator exactly as the builds above do from
+ * hv_hessian_apply (same arguments and results; the build's scratch is
+ * allocated on the device and freed before return).  The operator is called
+ * with k = n_batches (PSF), 1 (PDO) or k then at most k (LR) vectors. */
+typedef int (*hv_op_fn)(void *ctx, const float *v, int k, float *out, void *stream);
+typedef struct hv_operator {
+    int nz, nx;
+    double h;
+    hv_op_fn apply;
+    void *ctx;
+} hv_operator;
+int hv_approx_build_psf_op(const hv_operator *op, int spacing_cells, int n_batches, hv_approx **out, void *stream);
+int hv_approx_build_pdo_op(const hv_operator *op, double rho0, int r, hv_approx **out, void *stream);
+int hv_approx_build_lr_op(const hv_operator *op, double delta, double gamma, int rank, const float *omega, int k,
+                          hv_approx **out, void *stream);
+
+/* The ideal quadratic test model (section 4.1).  Misfit Hessian
+ *   H_d = A A^T + V_r Lambda_r V_r^T                        (eq. (toy-hess))
+ * with A the order-1/2 PsiDO of eq. (toy-symbol),
+ *   s_A(x, xi) = w(x) P(|xi|) (0.1 + cos^2(arg xi + pi x / x_max)) / (0.1 + (z / z_max)^2),
+ * applied through its rank-3 expansion (compound angle) a_1 = w / d(z),
+ * a_2 = w cos(2 pi x / x_max) / d(z), a_3 = w sin(2 pi x / x_max) / d(z),
+ * b_1 = 0.6 P, b_2 = cos(2 arg xi) P / 2, b_3 = -sin(2 arg xi) P / 2,
+ * d(z) = 0.1 + (z / z_max)^2, as A v = Re sum_k a_k F^-1 b_k F v.  The paper
+ * describes P, w and V_r qualitatively; this library takes
+ * P(rho) = (rho / rho_c)^(1/2) exp(-(rho / rho_c)^4) (rho in rad/m), w = the
+ * window W = the product of 1D tapers sin^2(pi/2 (i + 1/2) / L) over the L =
+ * taper_cells cells next to each edge, z = iz h, x = ix h, z_max = nz h,
+ * x_max = nx h, arg xi = atan2(xi_z, xi_x), and for p = 1 .. nlr/2 the unit-norm
+ * modes e^{-8 z / z_max} cos(2 pi p x / x_max) and e^{-8 z / z_max} sin(...)
+ * (orthonormal on the grid) with eigenvalues lam[nlr] >= 0.  The objective is
+ * Phi(m) = Phi_d(W m) + 1/2 m^T R m = 1/2 (W m - m*)^T H_d (W m - m*) + 1/2 m^T R m
+ * with the Matern prior R = (delta I - gamma Lap_h)^2 (as hv_prior_apply).
+ *  - hv_quad_create: builds the tables (FP64 on the host, stored FP32) on the
+ *    current device; HV_EINVAL for nz, nx < 4, h or rho_c <= 0, a taper wider
+ *    than half the grid, an odd nlr, nlr / 2 >= nx / 2 or a negative lam.
+ *  - hv_quad_apply: out = op v for k fields [k][nz][nx] (device):
+ *    HV_QUAD_HD the misfit Hessian of Phi_d(W m), W (A A^T + V Lambda V^T) W;
+ *    HV_QUAD_A, HV_QUAD_AT: A and A^T; HV_QUAD_HD_RAW: A A^T + V Lambda V^T.
+ *  - hv_quad_objective: phi[k] (device doubles, FP64 sums) and, unless grad
+ *    is NULL, grad[k][nz][nx] = W H_d (W m - m*) + R m for k states m (device);
+ *    one_target != 0: mstar is one field for every state, else k fields.
+ *  - hv_quad_tables: device copies of a, b ([3][nz][nx] complex each, b in
+ *    DFT order), V [nlr][nz][nx] and W [nz][nx] (any may be NULL).
+ *  - hv_quad_operator: fills *op with HV_QUAD_HD of q (valid while q lives).
+ * Calls on one model from several streams run one after another (shared
+ * scratch). */
+typedef struct hv_quad hv_quad;
+#define HV_QUAD_HD 0
+#define HV_QUAD_A 1
+#define HV_QUAD_AT 2
+#define HV_QUAD_HD_RAW 3
+int hv_quad_create(int nz, int nx, double h, double rho_c, int taper_cells, int nlr, const double *lam, double delta,
+                   double gamma, hv_quad **out);
+int hv_quad_apply(hv_quad *q, int op, const float *v, int k, float *out, void *stream);
+int hv_quad_objective(hv_quad *q, const float *m, const float *mstar, int k, int one_target, double *phi, float *grad,
+                      void *stream);
+int hv_quad_tables(const hv_quad *q, float *a, float *b, float *V, float *W, void *stream);
+int hv_quad_operator(hv_quad *q, hv_operator *op);
+int hv_quad_destroy(hv_quad *q);
+
 /* Serving.  A server owns one device arena of hbm_budget bytes (allocated at
  * creation) and max_concurrent CUDA streams on the current device.  Requests
  * (H v, gradient, misfit, and the apply of a built Hessian approximation) on

@@ -45,6 +45,14 @@ class HvRequestInfo(ctypes.Structure):
                 ("t_done", c_double), ("ws_bytes", c_size_t)]
 
 
+HV_OP_FN = ctypes.CFUNCTYPE(c_int, c_void_p, fp, c_int, fp, c_void_p)
+
+
+class HvOperator(ctypes.Structure):
+    _fields_ = [("nz", c_int), ("nx", c_int), ("h", c_double), ("apply", HV_OP_FN), ("ctx", c_void_p)]
+
+
+HV_QUAD_HD, HV_QUAD_A, HV_QUAD_AT, HV_QUAD_HD_RAW = 0, 1, 2, 3
 HV_REQ_HV, HV_REQ_GRAD, HV_REQ_MISFIT, HV_REQ_APPROX = 0, 1, 2, 3
 HV_APPROX_H, HV_APPROX_SQRT, HV_APPROX_INVSQRT, HV_APPROX_SQRT_T = 0, 1, 2, 3
 HV_REQ_QUEUED, HV_REQ_RUNNING = 100, 101
@@ -92,6 +100,18 @@ _SIGS = {
                             c_size_t, c_void_p], c_int),
     "hv_approx_lr_eigs": ([c_void_p, ctypes.POINTER(c_double), fp, c_void_p], c_int),
     "hv_approx_apply": ([c_void_p, fp, c_int, fp, c_int, c_void_p], c_int),
+    "hv_approx_build_psf_op": ([ctypes.POINTER(HvOperator), c_int, c_int, ctypes.POINTER(c_void_p), c_void_p], c_int),
+    "hv_approx_build_pdo_op": ([ctypes.POINTER(HvOperator), c_double, c_int, ctypes.POINTER(c_void_p), c_void_p],
+                               c_int),
+    "hv_approx_build_lr_op": ([ctypes.POINTER(HvOperator), c_double, c_double, c_int, fp, c_int,
+                               ctypes.POINTER(c_void_p), c_void_p], c_int),
+    "hv_quad_create": ([c_int, c_int, c_double, c_double, c_int, c_int, ctypes.POINTER(c_double), c_double, c_double,
+                        ctypes.POINTER(c_void_p)], c_int),
+    "hv_quad_apply": ([c_void_p, c_int, fp, c_int, fp, c_void_p], c_int),
+    "hv_quad_objective": ([c_void_p, fp, fp, c_int, c_int, fp, fp, c_void_p], c_int),
+    "hv_quad_tables": ([c_void_p, fp, fp, fp, fp, c_void_p], c_int),
+    "hv_quad_operator": ([c_void_p, ctypes.POINTER(HvOperator)], c_int),
+    "hv_quad_destroy": ([c_void_p], c_int),
     "hv_approx_destroy": ([c_void_p], c_int),
     "hv_tile_menu_size": ([], c_int),
     "hv_set_launch_mode": ([c_void_p, c_int], c_int),

@@ -1174,24 +1174,23 @@ int psf_batches_per_axis(int n_batches)
     return 0;
 }
 
-int psf_geometry(const hv_handle *h, int S, int n_batches, hvk::PsfGeo &g)
+int psf_geometry(int nz, int nx, int S, int n_batches, hvk::PsfGeo &g)
 {
-    if (!h) return hvi::fail(HV_EINVAL, "null handle");
     if (S < 1) return hvi::fail(HV_EINVAL, "PSF lattice spacing %d; need >= 1", S);
     const int B = psf_batches_per_axis(n_batches);
     if (B == 0) return hvi::fail(HV_EINVAL, "n_batches = %d; need B * B with 1 <= B <= %d", n_batches, kMaxPsfBatchesPerAxis);
-    g.nz = h->nz;
-    g.nx = h->nx;
+    g.nz = nz;
+    g.nx = nx;
     g.S = S;
     g.B = B;
     g.R = (B * S - 1) / 2;
     g.cz0 = S / 2;
     g.cx0 = S / 2;
-    if (g.cz0 >= h->nz || g.cx0 >= h->nx)
-        return hvi::fail(HV_EINVAL, "first PSF sample point (%d, %d) is off the %d x %d grid", g.cz0, g.cx0, h->nz, h->nx);
+    if (g.cz0 >= nz || g.cx0 >= nx)
+        return hvi::fail(HV_EINVAL, "first PSF sample point (%d, %d) is off the %d x %d grid", g.cz0, g.cx0, nz, nx);
     if (g.R > kMaxPsfRadius) return hvi::fail(HV_EINVAL, "PSF window radius %d exceeds %d", g.R, kMaxPsfRadius);
-    g.na = (h->nz - 1 - g.cz0) / S + 1;
-    g.nb = (h->nx - 1 - g.cx0) / S + 1;
+    g.na = (nz - 1 - g.cz0) / S + 1;
+    g.nb = (nx - 1 - g.cx0) / S + 1;
     return HV_OK;
 }
 
@@ -1226,13 +1225,21 @@ extern "C" int hv_approx_psf_workspace_size(hv_handle *h, int n_batches, int ckp
     return HV_OK;
 }
 
+using HessFn = std::function<int(const float *, int, float *)>;
+static int psf_finish(const hvk::PsfGeo &g, int device, float *vec, float *hv, const HessFn &hess, cudaStream_t st,
+                      hv_approx **out);
+static int pdo_finish(const hvk::LrGeo &g, int device, float *vp, float *hvp, const HessFn &hess, cudaStream_t st,
+                      hv_approx **out);
+static int lr_finish(int nz, int nx, double hh, int device, double delta, double gamma, int rank, const float *omega,
+                     int k, float *Y, const HessFn &hess, cudaStream_t st, hv_approx **out);
+
 extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt,
                                    hv_approx **out, void *ws, size_t ws_bytes, void *stream)
 {
     if (out) *out = nullptr;
-    if (!out || !m) return hvi::fail(HV_EINVAL, "null model or output");
+    if (!h || !out || !m) return hvi::fail(HV_EINVAL, "null handle, model or output");
     hvk::PsfGeo g;
-    HV_RT(psf_geometry(h, spacing_cells, n_batches, g));
+    HV_RT(psf_geometry(h->nz, h->nx, spacing_cells, n_batches, g));
     PsfLayout P;
     HV_RT(psf_layout(h, n_batches, ckpt, P));
     if (!ws) return hvi::fail(HV_EINVAL, "null workspace");
@@ -1242,12 +1249,25 @@ extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cel
     char *w = (char *)ws;
     float *vec = reinterpret_cast<float *>(w + P.vec);
     float *hv = reinterpret_cast<float *>(w + P.hv);
-    HV_CK(cudaMemsetAsync(vec, 0, (size_t)n_batches * h->nz * h->nx * sizeof(float), st));
+    return psf_finish(g, h->device, vec, hv,
+                      [&](const float *X, int k, float *Z) {
+                          return run_adjoint(h, 2, m, X, k, Z, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st);
+                      },
+                      st, out);
+}
+
+// The PSF build after the geometry: impulse batches, one batched operator
+// application, window extraction.
+static int psf_finish(const hvk::PsfGeo &g, int device, float *vec, float *hv, const HessFn &hess, cudaStream_t st,
+                      hv_approx **out)
+{
+    const int n_batches = g.B * g.B;
+    HV_CK(cudaMemsetAsync(vec, 0, (size_t)n_batches * g.nz * g.nx * sizeof(float), st));
     HV_RT(hvk::launch_psf_impulses(g, vec, st));
-    HV_RT(run_adjoint(h, 2, m, vec, n_batches, hv, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st));
+    HV_RT(hess(vec, n_batches, hv));
     hv_approx *a = new hv_approx;
     a->kind = 0;
-    a->device = h->device;
+    a->device = device;
     a->g = g;
     const size_t W = 2 * (size_t)g.R + 1;
     cudaError_t e = cudaMalloc(&a->psf, (size_t)g.na * g.nb * W * W * sizeof(float));
@@ -1309,11 +1329,23 @@ extern "C" int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, in
     char *w = (char *)ws;
     float *vp = reinterpret_cast<float *>(w + P.vp);
     float *hvp = reinterpret_cast<float *>(w + P.hvp);
+    return pdo_finish(g, h->device, vp, hvp,
+                      [&](const float *X, int k, float *Z) {
+                          return run_adjoint(h, 2, m, X, k, Z, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st);
+                      },
+                      st, out);
+}
+
+// The PDO build after the sample geometry: probe, one operator application,
+// spectral separation and weights.
+static int pdo_finish(const hvk::LrGeo &g, int device, float *vp, float *hvp, const HessFn &hess, cudaStream_t st,
+                      hv_approx **out)
+{
     HV_RT(hvk::launch_pdo_probe(g, vp, st));
-    HV_RT(run_adjoint(h, 2, m, vp, 1, hvp, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st));
+    HV_RT(hess(vp, 1, hvp));
     hv_approx *a = new hv_approx;
     a->kind = 1;
-    a->device = h->device;
+    a->device = device;
     int rc = hvk::lr_create(a->lr, g);
     if (rc == HV_OK) rc = hvk::pdo_columns(a->lr, hvp, st);
     if (rc != HV_OK) {
@@ -1351,19 +1383,25 @@ extern "C" int hv_approx_build_lr(hv_handle *h, const float *m, double delta, do
     cudaStream_t st = (cudaStream_t)stream;
     float *Y = reinterpret_cast<float *>(ws);
     char *inner = (char *)ws + yb;
+    return lr_finish(h->nz, h->nx, h->h, h->device, delta, gamma, rank, omega, k, Y,
+                     [&](const float *X, int kk, float *Z) {
+                         return run_adjoint(h, 2, m, X, kk, Z, nullptr, nullptr, ckpt, inner, L.total, st);
+                     },
+                     st, out);
+}
+
+// The LR build after the argument checks: Y = H_d omega, then the double pass.
+static int lr_finish(int nz, int nx, double hh, int device, double delta, double gamma, int rank, const float *omega,
+                     int k, float *Y, const HessFn &hess, cudaStream_t st, hv_approx **out)
+{
     hv_approx *a = new hv_approx;
     a->kind = 3;
-    a->device = h->device;
-    a->nz = h->nz;
-    a->nx = h->nx;
-    int rc = hvk::prior_create(a->low.prior, h->nz, h->nx, h->h, delta, gamma);
-    if (rc == HV_OK) rc = run_adjoint(h, 2, m, omega, k, Y, nullptr, nullptr, ckpt, inner, L.total, st);
-    if (rc == HV_OK) {
-        auto hess = [&](const float *X, int kk, float *Z) {
-            return run_adjoint(h, 2, m, X, kk, Z, nullptr, nullptr, ckpt, inner, L.total, st);
-        };
-        rc = hvk::build_lowrank(a->low, Y, k, rank, N, hess, st);
-    }
+    a->device = device;
+    a->nz = nz;
+    a->nx = nx;
+    int rc = hvk::prior_create(a->low.prior, nz, nx, hh, delta, gamma);
+    if (rc == HV_OK) rc = hess(omega, k, Y);
+    if (rc == HV_OK) rc = hvk::build_lowrank(a->low, Y, k, rank, (size_t)nz * nx, hess, st);
     if (rc != HV_OK) {
         hvk::lowrank_destroy(a->low);
         delete a;
@@ -1371,6 +1409,98 @@ extern "C" int hv_approx_build_lr(hv_handle *h, const float *m, double delta, do
     }
     *out = a;
     return HV_OK;
+}
+
+namespace {
+
+// Device scratch of the *_op builds, freed after the stream has drained.
+struct OpScratch {
+    std::vector<void *> p;
+    cudaStream_t st = nullptr;
+    int get(float **out, size_t n)
+    {
+        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(out), n * sizeof(float));
+        if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "build scratch: %s", cudaGetErrorString(e));
+        p.push_back(*out);
+        return HV_OK;
+    }
+    ~OpScratch()
+    {
+        if (st) cudaStreamSynchronize(st);
+        for (void *q : p) cudaFree(q);
+    }
+};
+
+int check_operator(const hv_operator *op)
+{
+    if (!op || !op->apply) return hvi::fail(HV_EINVAL, "null operator or apply function");
+    if (op->nz < 1 || op->nx < 1 || !(op->h > 0)) return hvi::fail(HV_EINVAL, "operator grid %d x %d, h = %g", op->nz, op->nx, op->h);
+    return HV_OK;
+}
+
+HessFn op_fn(const hv_operator *op, cudaStream_t st)
+{
+    return [op, st](const float *X, int k, float *Z) {
+        const int rc = op->apply(op->ctx, X, k, Z, (void *)st);
+        return rc == HV_OK ? HV_OK : hvi::fail(rc, "the operator's apply returned %d", rc);
+    };
+}
+
+}  // namespace
+
+extern "C" int hv_approx_build_psf_op(const hv_operator *op, int spacing_cells, int n_batches, hv_approx **out,
+                                      void *stream)
+{
+    if (out) *out = nullptr;
+    if (!out) return hvi::fail(HV_EINVAL, "null output");
+    HV_RT(check_operator(op));
+    hvk::PsfGeo g;
+    HV_RT(psf_geometry(op->nz, op->nx, spacing_cells, n_batches, g));
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    OpScratch sc;
+    sc.st = st;
+    float *vec = nullptr, *hv = nullptr;
+    const size_t n = (size_t)n_batches * op->nz * op->nx;
+    HV_RT(sc.get(&vec, n));
+    HV_RT(sc.get(&hv, n));
+    return psf_finish(g, dev, vec, hv, op_fn(op, st), st, out);
+}
+
+extern "C" int hv_approx_build_pdo_op(const hv_operator *op, double rho0, int r, hv_approx **out, void *stream)
+{
+    if (out) *out = nullptr;
+    if (!out) return hvi::fail(HV_EINVAL, "null output");
+    HV_RT(check_operator(op));
+    hvk::LrGeo g;
+    HV_RT(hvk::lr_samples(op->nz, op->nx, op->h, rho0, r, g));
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    OpScratch sc;
+    sc.st = st;
+    float *vp = nullptr, *hvp = nullptr;
+    HV_RT(sc.get(&vp, (size_t)op->nz * op->nx));
+    HV_RT(sc.get(&hvp, (size_t)op->nz * op->nx));
+    return pdo_finish(g, dev, vp, hvp, op_fn(op, st), st, out);
+}
+
+extern "C" int hv_approx_build_lr_op(const hv_operator *op, double delta, double gamma, int rank, const float *omega,
+                                     int k, hv_approx **out, void *stream)
+{
+    if (out) *out = nullptr;
+    if (!out || !omega) return hvi::fail(HV_EINVAL, "null test vectors or output");
+    HV_RT(check_operator(op));
+    if (rank < 1 || k < rank || k > 256) return hvi::fail(HV_EINVAL, "rank %d with %d test vectors; need 1 <= rank <= k <= 256", rank, k);
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    cudaStream_t st = (cudaStream_t)stream;
+    OpScratch sc;
+    sc.st = st;
+    float *Y = nullptr;
+    HV_RT(sc.get(&Y, (size_t)k * op->nz * op->nx));
+    return lr_finish(op->nz, op->nx, op->h, dev, delta, gamma, rank, omega, k, Y, op_fn(op, st), st, out);
 }
 
 extern "C" int hv_approx_lr_eigs(const hv_approx *a, double *lambda, float *V, void *stream)

@@ -386,6 +386,109 @@ def psf_plus(psf: PsfApprox, pdo: PdoApprox, tol: float = 1e-3, spd: bool = Fals
     return PdoApprox(psf.lib, out, psf.device)
 
 
+class Quad:
+    """The ideal quadratic test model of section 4.1 on one GPU (hv_quad_*): misfit Hessian
+    W (A A^T + V Lambda V^T) W, A the order-1/2 PsiDO of the rank-3 symbol, and the objective
+    Phi(m) = 1/2 (W m - m*)^T H_d (W m - m*) + 1/2 m^T R m with the Matern prior (delta, gamma)."""
+
+    def __init__(self, nz: int, nx: int, h: float, lam, delta: float, gamma: float, rho_c: float | None = None,
+                 taper: int | None = None, device=None):
+        self.lib = _lib.load()
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        self.nz, self.nx, self.h = int(nz), int(nx), float(h)
+        self.rho_c = np.pi / (2 * h) if rho_c is None else float(rho_c)
+        self.taper = max(1, min(nz, nx) // 8) if taper is None else int(taper)
+        self.lam = np.ascontiguousarray(np.asarray(lam, dtype=np.float64))
+        self.delta, self.gamma = float(delta), float(gamma)
+        q = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hv_quad_create(self.nz, self.nx, self.h, self.rho_c, self.taper, len(self.lam),
+                                          self.lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), self.delta,
+                                          self.gamma, ctypes.byref(q)))
+        self._q = q
+        self._op = _lib.HvOperator()
+        check(self.lib.hv_quad_operator(self._q, ctypes.byref(self._op)))
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def apply(self, v: torch.Tensor, op: int = _lib.HV_QUAD_HD) -> torch.Tensor:
+        k = v.shape[0]
+        pv = _dev(v, torch.float32, (k, self.nz, self.nx), "v", self.device)
+        out = torch.empty((k, self.nz, self.nx), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_quad_apply(self._q, int(op), pv, k, out.data_ptr(), self._stream()))
+        return out
+
+    def objective(self, m: torch.Tensor, mstar: torch.Tensor, grad: bool = True):
+        """(phi [k] float64 device, grad [k, nz, nx] or None) for states m [k, nz, nx]; mstar [nz, nx] or [k, nz, nx]."""
+        k = m.shape[0]
+        pm = _dev(m, torch.float32, (k, self.nz, self.nx), "m", self.device)
+        one = mstar.dim() == 2
+        ps = _dev(mstar, torch.float32, (self.nz, self.nx) if one else (k, self.nz, self.nx), "mstar", self.device)
+        phi = torch.empty(k, dtype=torch.float64, device=self.device)
+        g = torch.empty((k, self.nz, self.nx), dtype=torch.float32, device=self.device) if grad else None
+        check(self.lib.hv_quad_objective(self._q, pm, ps, k, int(one), phi.data_ptr(),
+                                         g.data_ptr() if grad else None, self._stream()))
+        return phi, g
+
+    def tables(self):
+        """(a [3, nz, nx] complex, b [3, nz, nx] complex (DFT order), V [nlr, nz, nx], W [nz, nx]) device copies."""
+        N = (self.nz, self.nx)
+        a = torch.empty((3, *N, 2), dtype=torch.float32, device=self.device)
+        b = torch.empty((3, *N, 2), dtype=torch.float32, device=self.device)
+        V = torch.empty((len(self.lam), *N), dtype=torch.float32, device=self.device)
+        W = torch.empty(N, dtype=torch.float32, device=self.device)
+        check(self.lib.hv_quad_tables(self._q, a.data_ptr(), b.data_ptr(), V.data_ptr() if len(self.lam) else None,
+                                      W.data_ptr(), self._stream()))
+        return torch.view_as_complex(a), torch.view_as_complex(b), V, W
+
+    def operator(self):
+        """The misfit Hessian as an hv_operator (for the *_op approximation builds)."""
+        return self._op
+
+    def close(self):
+        if getattr(self, "_q", None):
+            self.lib.hv_quad_destroy(self._q)
+            self._q = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _op_stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def approx_build_psf_op(src, spacing: int, n_batches: int = 4) -> PsfApprox:
+    """PSF approximation of the operator of `src` (an object with .operator(), .device, e.g. Quad)."""
+    out = ctypes.c_void_p()
+    check(src.lib.hv_approx_build_psf_op(ctypes.byref(src.operator()), int(spacing), int(n_batches), ctypes.byref(out),
+                                         _op_stream(src.device)))
+    return PsfApprox(src.lib, out, src.device)
+
+
+def approx_build_pdo_op(src, rho0: float, r: int = 8) -> PdoApprox:
+    """PDO approximation of the operator of `src`."""
+    out = ctypes.c_void_p()
+    check(src.lib.hv_approx_build_pdo_op(ctypes.byref(src.operator()), float(rho0), int(r), ctypes.byref(out),
+                                         _op_stream(src.device)))
+    return PdoApprox(src.lib, out, src.device)
+
+
+def approx_build_lr_op(src, delta: float, gamma: float, rank: int, omega: torch.Tensor) -> LrApprox:
+    """Low-rank approximation of the operator of `src` with the Matern prior (delta, gamma)."""
+    op = src.operator()
+    k = omega.shape[0]
+    po = _dev(omega, torch.float32, (k, op.nz, op.nx), "omega", src.device)
+    out = ctypes.c_void_p()
+    check(src.lib.hv_approx_build_lr_op(ctypes.byref(op), float(delta), float(gamma), int(rank), po, int(k),
+                                        ctypes.byref(out), _op_stream(src.device)))
+    return LrApprox(src.lib, out, src.device)
+
+
 def hermitian_eig(A: np.ndarray):
     """(w descending, V) of a Hermitian matrix by the library's host Jacobi routine (hv_util_hermitian_eig)."""
     A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
