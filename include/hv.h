@@ -317,7 +317,7 @@ int hv_status(hv_handle *h, int *device_status);
  *    HV_APPROX_H gives B B^T v, HV_APPROX_SQRT B v, HV_APPROX_SQRT_T
  *    B^T v = Re F^-1 sum_k conj(b_k) F (conj(a_k) v); HV_APPROX_INVSQRT returns
  *    HV_ENOTSUP (posterior samples need a solve with B B^T + R: see
- *    hv_sample_posterior).  On a PDO or PSF+ approximation of H_d itself only
+ *    hv_posterior_sample).  On a PDO or PSF+ approximation of H_d itself only
  *    HV_APPROX_H (B v) is provided.
  *
  * hv_util_hermitian_eig: eigenvalues (descending) into w[n] and eigenvectors
@@ -416,6 +416,69 @@ int hv_quad_objective(hv_quad *q, const float *m, const float *mstar, int k, int
 int hv_quad_tables(const hv_quad *q, float *a, float *b, float *V, float *W, void *stream);
 int hv_quad_operator(hv_quad *q, hv_operator *op);
 int hv_quad_destroy(hv_quad *q);
+
+/* Laplace approximation of the posterior (sections 2.2, 3.1, 3.7).  A
+ * posterior object holds H0 = H~_d + R, R = (delta I - gamma Lap_h)^2 the
+ * Matern prior (as hv_prior_apply) and H~_d = B B^T the square-root
+ * approximation `approx` (hv_approx_sqrt_pdo / hv_approx_build_psfplus_sqrt;
+ * borrowed, it must outlive the posterior) or H~_d = 0 (approx NULL), plus an
+ * optional low-rank correction, H~ = H0 + H0 V Lambda V^T H0.
+ *  - hv_posterior_create: on the current device; HV_EINVAL for an approx that
+ *    is not a square-root form or lives on another grid or device.
+ *  - hv_posterior_solve: x = (Op + R)^-1 b for k fields, Op = the caller's
+ *    operator or, if op is NULL, H~_d (so H0 x = b; the correction is not
+ *    included).  Preconditioned conjugate gradients (preconditioner R^-1),
+ *    FP32 vectors with FP64 dot products and step lengths, started from 0, until
+ *    every ||r_j|| <= rtol ||b_j||; *iters = the iterations taken.  HV_ETIMEOUT
+ *    after max_iter iterations (x then holds the last iterate).
+ *  - hv_posterior_apply: out = H~ v.
+ *  - hv_posterior_sample: zeta ~ N(0, H~^-1) from standard normals n1, n2
+ *    [k][nz][nx] (caller-drawn, device): z = H0^-1 (A n1 + B n2) (by the solve
+ *    above; for approx NULL z = A^-1 n1 exactly and n2 is unused), then
+ *    zeta = (I - V S_r V^T H0) z, S_r = I - (Lambda + I)^-1/2.
+ *  - hv_posterior_correct: the low-rank correction: the `rank` leading
+ *    eigenpairs of (H_d - H~_d) v = lambda H0 v, V^T H0 V = I, H_d the operator
+ *    hd, by the randomized double pass with the test matrix omega [k][nz][nx]
+ *    (the section 3.1 method with H0 in place of R; the solves with H0 as
+ *    above): Z = (H_d - H~_d) omega, Y = H0^-1 Z, Q = Y M from the
+ *    eigen-decomposition of Y^T Z (= Y^T H0 Y; FP64, directions below 1e-12 of
+ *    the largest dropped; twice), T = Q^T (H_d - H~_d) Q = S Lambda S^T,
+ *    V = Q S[:, :rank].  1 <= rank <= k <= 256; HV_EINVAL if a kept eigenvalue
+ *    is <= -1 (H~ would not be positive definite).  Replaces an earlier
+ *    correction.  With approx NULL this is the low-rank approximation of
+ *    section 3.1.
+ *  - hv_posterior_eigs: lambda[rank] (host) and/or V [rank][nz][nx] (device).
+ *  - hv_posterior_rank: the correction rank (0 without one; -1 for NULL).
+ * Calls on one posterior are serialised (shared scratch); they synchronise
+ * `stream` where a solve checks convergence.
+ *
+ * gpCN (section 2.3), c chains of n = nz * nx values each (device arrays):
+ *  - hv_gpcn_propose: m_new[c] = m_map + sqrt(1 - beta^2)(m[c] - m_map) +
+ *    beta zeta[c] and, unless d_new is NULL, d_new[c] = m_new[c] - m_map;
+ *    0 < beta < 1.
+ *  - hv_gpcn_accept: Delta' = phi_new[c] - 1/2 d_new[c] . Hd_new[c] (FP64;
+ *    Hd_new = H~ d_new, e.g. by hv_posterior_apply); the proposal is accepted
+ *    iff log_u[c] < delta_cur[c] - Delta', u ~ U(0, 1) drawn by the caller,
+ *    i.e. with probability min(1, exp(Delta(m_k) - Delta(m'))); then m[c] <-
+ *    m_new[c] and delta_cur[c] <- Delta'.  accepted[c] = 1 or 0.  log_u = -inf
+ *    accepts unconditionally (initialises delta_cur). */
+typedef struct hv_posterior hv_posterior;
+int hv_posterior_create(int nz, int nx, double h, double delta, double gamma, const hv_approx *approx,
+                        hv_posterior **out);
+int hv_posterior_solve(hv_posterior *p, const hv_operator *op, const float *b, int k, float *x, double rtol,
+                       int max_iter, int *iters, void *stream);
+int hv_posterior_apply(hv_posterior *p, const float *v, int k, float *out, void *stream);
+int hv_posterior_sample(hv_posterior *p, const float *n1, const float *n2, int k, float *zeta, double rtol,
+                        int max_iter, int *iters, void *stream);
+int hv_posterior_correct(hv_posterior *p, const hv_operator *hd, const float *omega, int k, int rank, double rtol,
+                         int max_iter, void *stream);
+int hv_posterior_eigs(const hv_posterior *p, double *lambda, float *V, void *stream);
+int hv_posterior_rank(const hv_posterior *p);
+int hv_posterior_destroy(hv_posterior *p);
+int hv_gpcn_propose(int n, int c, const float *m, const float *m_map, const float *zeta, double beta, float *m_new,
+                    float *d_new, void *stream);
+int hv_gpcn_accept(int n, int c, const double *phi_new, const float *m_new, const float *d_new, const float *Hd_new,
+                   const double *log_u, float *m, double *delta_cur, int *accepted, void *stream);
 
 /* Serving.  A server owns one device arena of hbm_budget bytes (allocated at
  * creation) and max_concurrent CUDA streams on the current device.  Requests

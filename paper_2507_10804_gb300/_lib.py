@@ -113,6 +113,18 @@ _SIGS = {
     "hv_quad_operator": ([c_void_p, ctypes.POINTER(HvOperator)], c_int),
     "hv_quad_destroy": ([c_void_p], c_int),
     "hv_approx_destroy": ([c_void_p], c_int),
+    "hv_posterior_create": ([c_int, c_int, c_double, c_double, c_double, c_void_p, ctypes.POINTER(c_void_p)], c_int),
+    "hv_posterior_solve": ([c_void_p, ctypes.POINTER(HvOperator), fp, c_int, fp, c_double, c_int, ip, c_void_p],
+                           c_int),
+    "hv_posterior_apply": ([c_void_p, fp, c_int, fp, c_void_p], c_int),
+    "hv_posterior_sample": ([c_void_p, fp, fp, c_int, fp, c_double, c_int, ip, c_void_p], c_int),
+    "hv_posterior_correct": ([c_void_p, ctypes.POINTER(HvOperator), fp, c_int, c_int, c_double, c_int, c_void_p],
+                             c_int),
+    "hv_posterior_eigs": ([c_void_p, ctypes.POINTER(c_double), fp, c_void_p], c_int),
+    "hv_posterior_rank": ([c_void_p], c_int),
+    "hv_posterior_destroy": ([c_void_p], c_int),
+    "hv_gpcn_propose": ([c_int, c_int, fp, fp, fp, c_double, fp, fp, c_void_p], c_int),
+    "hv_gpcn_accept": ([c_int, c_int, fp, fp, fp, fp, fp, fp, fp, fp, c_void_p], c_int),
     "hv_tile_menu_size": ([], c_int),
     "hv_set_launch_mode": ([c_void_p, c_int], c_int),
     "hv_set_step_fusion": ([c_void_p, c_int], c_int),

@@ -1152,15 +1152,6 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
 
 // ---------------------------------------------------------------- approximations
 // Point-spread-function approximation (section 3.2; PsiDO row form, section 3.5).
-struct hv_approx {
-    int kind = 0;           // 0: PSF, 1: PDO, 2: PSF+ (1 and 2: low-rank symbol), 3: LR
-    int device = -1;
-    hvk::PsfGeo g{};
-    float *psf = nullptr;   // [na * nb][2R+1][2R+1]
-    hvk::LrSym lr;          // PDO: symbol columns, weights, FFT plans
-    hvk::LowRank low;       // LR: prior and generalised eigenpairs
-    int nz = 0, nx = 0;
-};
 
 namespace {
 

@@ -278,3 +278,14 @@ long long launches_so_far();
 long long thread_launches();   // kernels launched by the calling thread
 
 }  // namespace hvk
+
+// A built Hessian approximation (hv_approx_*).
+struct hv_approx {
+    int kind = 0;           // 0: PSF, 1: PDO, 2: PSF+ (1 and 2: low-rank symbol), 3: LR
+    int device = -1;
+    hvk::PsfGeo g{};
+    float *psf = nullptr;   // [na * nb][2R+1][2R+1]
+    hvk::LrSym lr;          // PDO / PSF+: symbol factors, weights, FFT plans
+    hvk::LowRank low;       // LR: prior and generalised eigenpairs
+    int nz = 0, nx = 0;
+};

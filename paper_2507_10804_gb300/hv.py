@@ -489,6 +489,106 @@ def approx_build_lr_op(src, delta: float, gamma: float, rank: int, omega: torch.
     return LrApprox(src.lib, out, src.device)
 
 
+class Posterior:
+    """Laplace approximation H~ = H~_d + R (+ a low-rank correction) of the posterior (hv_posterior_*):
+    H~_d = B B^T from a square-root approximation `approx` (or 0), R the Matern prior (delta, gamma)."""
+
+    def __init__(self, nz: int, nx: int, h: float, delta: float, gamma: float, approx: "Approx | None" = None,
+                 device=None):
+        self.lib = _lib.load()
+        self.device = (approx.device if approx is not None else
+                       torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device))
+        self.nz, self.nx = int(nz), int(nx)
+        self.approx = approx                      # kept alive: the posterior borrows it
+        p = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hv_posterior_create(self.nz, self.nx, float(h), float(delta), float(gamma),
+                                               approx._a if approx is not None else None, ctypes.byref(p)))
+        self._p = p
+
+    def _stream(self):
+        return ctypes.c_void_p(torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _f(self, t, name, k=None):
+        k = t.shape[0] if k is None else k
+        return _dev(t, torch.float32, (k, self.nz, self.nx), name, self.device)
+
+    def solve(self, b: torch.Tensor, op=None, rtol: float = 1e-6, max_iter: int = 1000):
+        """(x, iterations): x = (Op + R)^-1 b, Op = op.operator() of an operator source or H~_d."""
+        k = b.shape[0]
+        x = torch.empty_like(b)
+        it = ctypes.c_int()
+        opp = ctypes.byref(op.operator()) if op is not None else None
+        check(self.lib.hv_posterior_solve(self._p, opp, self._f(b, "b"), k, x.data_ptr(), float(rtol), int(max_iter),
+                                          ctypes.byref(it), self._stream()))
+        return x, it.value
+
+    def apply(self, v: torch.Tensor) -> torch.Tensor:
+        out = torch.empty_like(v)
+        check(self.lib.hv_posterior_apply(self._p, self._f(v, "v"), v.shape[0], out.data_ptr(), self._stream()))
+        return out
+
+    def sample(self, n1: torch.Tensor, n2: torch.Tensor | None = None, rtol: float = 1e-6, max_iter: int = 1000):
+        """(zeta, iterations): zeta ~ N(0, H~^-1) from standard normals n1, n2 [k, nz, nx]."""
+        k = n1.shape[0]
+        zeta = torch.empty_like(n1)
+        it = ctypes.c_int()
+        p2 = self._f(n2, "n2", k) if n2 is not None else None
+        check(self.lib.hv_posterior_sample(self._p, self._f(n1, "n1"), p2, k, zeta.data_ptr(), float(rtol),
+                                           int(max_iter), ctypes.byref(it), self._stream()))
+        return zeta, it.value
+
+    def correct(self, src, omega: torch.Tensor, rank: int, rtol: float = 1e-6, max_iter: int = 1000):
+        """Low-rank correction against the operator of `src` (e.g. Quad) with test matrix omega [k, nz, nx]."""
+        k = omega.shape[0]
+        check(self.lib.hv_posterior_correct(self._p, ctypes.byref(src.operator()), self._f(omega, "omega"), k,
+                                            int(rank), float(rtol), int(max_iter), self._stream()))
+
+    def eigs(self):
+        r = self.lib.hv_posterior_rank(self._p)
+        lam = np.empty(r)
+        V = torch.empty((r, self.nz, self.nx), dtype=torch.float32, device=self.device)
+        check(self.lib.hv_posterior_eigs(self._p, lam.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                         V.data_ptr() if r else None, self._stream()))
+        return lam, V
+
+    def close(self):
+        if getattr(self, "_p", None):
+            self.lib.hv_posterior_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def gpcn_propose(m: torch.Tensor, m_map: torch.Tensor, zeta: torch.Tensor, beta: float):
+    """(m_new, d_new = m_new - m_map) for chains m [c, nz, nx] (hv_gpcn_propose)."""
+    c = m.shape[0]
+    n = m[0].numel()
+    m_new, d_new = torch.empty_like(m), torch.empty_like(m)
+    check(_lib.load().hv_gpcn_propose(n, c, m.data_ptr(), m_map.data_ptr(), zeta.data_ptr(), float(beta),
+                                      m_new.data_ptr(), d_new.data_ptr(),
+                                      ctypes.c_void_p(torch.cuda.current_stream(m.device).cuda_stream)))
+    return m_new, d_new
+
+
+def gpcn_accept(phi_new: torch.Tensor, m_new: torch.Tensor, d_new: torch.Tensor, Hd_new: torch.Tensor,
+                log_u: torch.Tensor, m: torch.Tensor, delta_cur: torch.Tensor) -> torch.Tensor:
+    """Accept/reject every chain (hv_gpcn_accept); updates m and delta_cur in place, returns accepted [c] int32."""
+    c = m.shape[0]
+    for t, dt in ((phi_new, torch.float64), (log_u, torch.float64), (delta_cur, torch.float64)):
+        if t.dtype != dt or t.shape != (c,) or not t.is_cuda:
+            raise ValueError("phi_new, log_u, delta_cur: float64 [c] CUDA tensors")
+    acc = torch.empty(c, dtype=torch.int32, device=m.device)
+    check(_lib.load().hv_gpcn_accept(m[0].numel(), c, phi_new.data_ptr(), m_new.data_ptr(), d_new.data_ptr(),
+                                     Hd_new.data_ptr(), log_u.data_ptr(), m.data_ptr(), delta_cur.data_ptr(),
+                                     acc.data_ptr(), ctypes.c_void_p(torch.cuda.current_stream(m.device).cuda_stream)))
+    return acc
+
+
 def hermitian_eig(A: np.ndarray):
     """(w descending, V) of a Hermitian matrix by the library's host Jacobi routine (hv_util_hermitian_eig)."""
     A = np.ascontiguousarray(np.asarray(A, dtype=np.complex128))
