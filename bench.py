@@ -171,6 +171,93 @@ def lr_measure(P, m, w, dev, rank=16, k=24, delta=1.0, gamma=2500.0, reps=10):
     return res
 
 
+def quad_measure(dev, nz=256, nx=256, h=10.0, chains=64, steps=10, warm=3, beta=0.5, delta=1.0, gamma=2500.0):
+    """The quadratic test model: H_d apply rate, the square-root PSF+ approximation built through the
+    operator interface, the corrected posterior (rank 32 of 40 test vectors), posterior samples by
+    preconditioned CG, and gpCN steps of `chains` chains (sample, propose, objective, H~ apply, accept)."""
+    import torch
+
+    from paper_2507_10804_gb300 import synth
+    from paper_2507_10804_gb300.hv import (Posterior, Quad, approx_build_pdo_op, approx_build_psf_op, gpcn_accept,
+                                           gpcn_propose, psf_plus)
+    lam = [40.0 * 0.8 ** j for j in range(10)]
+    Q = Quad(nz, nx, h, lam, delta, gamma, device=dev)
+    st = torch.cuda.current_stream(dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    v = torch.tensor(synth.smoothed_normal_vectors(5, chains, nz, nx, 2.0), dtype=torch.float32, device=dev)
+    Q.apply(v)
+    torch.cuda.synchronize(dev)
+    e0, e1 = ev(), ev()
+    e0.record(st)
+    for _ in range(5):
+        Q.apply(v)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    hd_us = e0.elapsed_time(e1) / 5 / chains * 1e3
+    t0 = time.perf_counter()
+    A = approx_build_psf_op(Q, 16, 4)                  # 16 x 16 PSFs: PSF+ takes at most 256
+    D = approx_build_pdo_op(Q, 0.08, 8)
+    C = psf_plus(A, D, 1e-3, spd=True)
+    post = Posterior(nz, nx, h, delta, gamma, approx=C)
+    torch.cuda.synchronize(dev)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    omega = torch.tensor(synth.normal(2026, 40 * nz * nx).reshape(40, nz, nx), dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    post.correct(Q, omega, 32)
+    torch.cuda.synchronize(dev)
+    correct_ms = (time.perf_counter() - t0) * 1e3
+    lam_c, _ = post.eigs()
+    mstar = torch.tensor(synth.smoothed_normal_vectors(6, 1, nz, nx, 4.0)[0], dtype=torch.float32, device=dev)
+    _, g0 = Q.objective(torch.zeros((1, nz, nx), device=dev), mstar)
+    t0 = time.perf_counter()
+    m_map, map_iters = post.solve(-g0, op=Q, rtol=1e-6)
+    torch.cuda.synchronize(dev)
+    map_ms = (time.perf_counter() - t0) * 1e3
+    gen = torch.Generator(device=dev).manual_seed(11)
+    m = m_map.repeat(chains, 1, 1).contiguous()
+    phi, _ = Q.objective(m, mstar, grad=False)
+    delta_cur = torch.empty(chains, dtype=torch.float64, device=dev)
+    zero = torch.zeros_like(m)
+    gpcn_accept(phi, m, zero, zero, torch.full((chains,), -float("inf"), dtype=torch.float64, device=dev), m,
+                delta_cur)
+    mp = m_map[0].contiguous()
+    acc, iters = 0, []
+
+    def step():
+        nonlocal acc
+        n1 = torch.randn((chains, nz, nx), device=dev, generator=gen)
+        n2 = torch.randn((chains, nz, nx), device=dev, generator=gen)
+        zeta, it = post.sample(n1, n2)
+        iters.append(it)
+        m_new, d_new = gpcn_propose(m, mp, zeta, beta)
+        phi_new, _ = Q.objective(m_new, mstar, grad=False)
+        Hd = post.apply(d_new)
+        log_u = torch.log(torch.rand(chains, dtype=torch.float64, device=dev, generator=gen))
+        return gpcn_accept(phi_new, m_new, d_new, Hd, log_u, m, delta_cur)
+
+    for _ in range(warm):
+        step()
+    torch.cuda.synchronize(dev)
+    iters.clear()
+    accs = []
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        accs.append(step())
+    torch.cuda.synchronize(dev)
+    dt = time.perf_counter() - t0
+    acc = float(torch.stack(accs).double().mean())
+    res = {"grid": [nz, nx], "h_m": h, "lowrank_part": len(lam), "hd_apply_us_per_vector": hd_us,
+           "psfplus_sqrt_rank": C.info["r"], "build_ms": build_ms, "correction_rank": 32, "correction_ms": correct_ms,
+           "correction_lambda_1": float(lam_c[0]), "correction_lambda_r": float(lam_c[-1]),
+           "map_solve_ms": map_ms, "map_cg_iterations": map_iters, "chains": chains, "beta": beta,
+           "gpcn_steps_per_s": steps * chains / dt, "gpcn_ms_per_step": dt / steps * 1e3,
+           "sample_cg_iterations": float(np.mean(iters)), "acceptance": acc,
+           "what": "host clock around synchronised phases; a gpCN step advances every chain once"}
+    for x in (post, C, D, A, Q):
+        x.close()
+    return res
+
+
 def psf_measure(P, m, w, dev, S=12, n_batches=4, reps=10):
     """Build time of the PSF approximation (n_batches H v) and apply rate for the workload's vectors."""
     import torch
@@ -437,6 +524,7 @@ def run_ours(args, w):
     pdo = pdo_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
     psfplus = psfplus_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
     lowrank = lr_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
+    quad = quad_measure(dev) if args.workload == "batched" and rank == 0 else None
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     mh = torch.tensor(w.m, dtype=torch.float32).pin_memory()
     vh = torch.tensor(w.v, dtype=torch.float32).pin_memory()
@@ -524,6 +612,8 @@ def run_ours(args, w):
             line["psfplus_approximation"] = psfplus
         if lowrank is not None:
             line["lowrank_approximation"] = lowrank
+        if quad is not None:
+            line["quadratic_model"] = quad
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
