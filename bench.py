@@ -639,6 +639,127 @@ def serve_requests(n, seed=20250719):
     return out
 
 
+def serve_chains(dev, concurrency, chains=64, fwi=4, steps=4, fwi_iters=2, beta=0.5):
+    """Closed-loop request source: `chains` gpCN chains on a 128x128, 8-shot, 1000-step problem
+    and `fwi` FWI-like clients (gradient then H v, repeated) on a 256x256, 16-shot, 1500-step problem,
+    all submitting to one server.  A chain step: a sample of the Laplace approximation (low-rank
+    approximation with the Matern prior, HV_APPROX_INVSQRT request), the gpCN proposal, the misfit of
+    the proposal (request), H~ d = H~_d d (HV_APPROX_H request) + R d, and the FP64 acceptance."""
+    import threading
+
+    import torch
+
+    from paper_2507_10804_gb300 import synth
+    from paper_2507_10804_gb300._lib import HV_APPROX_H, HV_APPROX_INVSQRT
+    from paper_2507_10804_gb300.hv import HV_CKPT_ALL, Posterior, Problem, gpcn_accept, gpcn_propose
+    from paper_2507_10804_gb300.serve import Server
+
+    def problem(nz, nx, ns, nt, seed):
+        h = 10.0
+        m = synth.gradient_grf_model(seed, nz, nx, h)
+        vmax = float(m.max())
+        acq = synth.surface_acquisition(nx, ns, nx // 3)
+        w = synth.Workload(name="serve", nz=nz, nx=nx, nb=20, h=h, nt=nt, dt=synth.cfl_dt(h, vmax), f0=10.0, t0=0.15,
+                           vmax=vmax, acq=acq, m=m, v=np.zeros((1, nz, nx)))
+        P = Problem.from_workload(w, device=dev)
+        mt = torch.tensor(m, dtype=torch.float32, device=dev)
+        return P, mt, P.fwd_model(mt * 1.02)
+
+    Pc, mc, dc = problem(128, 128, 8, 1000, 31)
+    Pf, mf, df = problem(256, 256, 16, 1500, 32)
+    delta, gamma = 1.0, 2500.0
+    omega = torch.tensor(synth.normal(33, 24 * 128 * 128).reshape(24, 128, 128), dtype=torch.float32, device=dev)
+    LR = Pc.approx_build_lr(mc, delta, gamma, 16, omega, ckpt=30)
+    prior = Posterior(128, 128, 10.0, delta, gamma, device=dev)
+    vf = torch.tensor(synth.smoothed_normal_vectors(34, 1, 256, 256), dtype=torch.float32, device=dev)
+    torch.cuda.synchronize(dev)
+    S = Server(hbm_budget=150 << 30, max_concurrent=concurrency, device=dev)
+    rids = {"sample": [], "misfit": [], "hd": [], "grad": [], "hv": []}
+    lock = threading.Lock()
+    accepted = []
+    errors = []
+
+    def note(kind, rid):
+        with lock:
+            rids[kind].append(rid)
+
+    def chain(c):
+        try:
+            st = torch.cuda.Stream(device=dev)
+            gen = torch.Generator(device=dev).manual_seed(100 + c)
+            with torch.cuda.stream(st):
+                m = mc.clone()[None].contiguous()
+                delta_cur = torch.zeros(1, dtype=torch.float64, device=dev)
+                st.synchronize()
+                rid, phi0 = S.submit_misfit(Pc, m[0], dc)        # at m0: no prior term
+                assert S.wait(rid) == 0
+                note("misfit", rid)
+                zero = torch.zeros_like(m)
+                gpcn_accept(phi0.reshape(1), m, zero, zero, torch.full((1,), -float("inf"), dtype=torch.float64,
+                                                                           device=dev), m, delta_cur)
+                acc = 0
+                for _ in range(steps):
+                    n = torch.randn((1, 128, 128), device=dev, generator=gen)
+                    st.synchronize()
+                    rid, zeta = S.submit_approx(LR, n, HV_APPROX_INVSQRT)
+                    assert S.wait(rid) == 0
+                    note("sample", rid)
+                    m_new, d_new = gpcn_propose(m, mc, zeta, beta)
+                    st.synchronize()
+                    rid, phi = S.submit_misfit(Pc, m_new[0], dc)
+                    rid2, hd = S.submit_approx(LR, d_new, HV_APPROX_H)
+                    assert S.wait(rid) == 0 and S.wait(rid2) == 0
+                    note("misfit", rid)
+                    note("hd", rid2)
+                    Rd = prior.apply(d_new)
+                    Hd = hd + Rd
+                    # Phi = data misfit + prior term 1/2 (m' - m_pr)^T R (m' - m_pr); here m_map = m_pr = m0
+                    phi_full = phi.reshape(1) + 0.5 * (d_new.double() * Rd.double()).sum()
+                    log_u = torch.log(torch.rand(1, dtype=torch.float64, device=dev, generator=gen))
+                    acc += int(gpcn_accept(phi_full, m_new, d_new, Hd, log_u, m, delta_cur).item())
+                with lock:
+                    accepted.append(acc)
+        except Exception as ex:       # reported below
+            errors.append(repr(ex))
+
+    def fwi_client(i):
+        try:
+            for _ in range(fwi_iters):
+                rid, _, _ = S.submit_grad(Pf, mf, df, ckpt=30)
+                assert S.wait(rid) == 0
+                note("grad", rid)
+                rid, _ = S.submit_hv(Pf, mf, vf, ckpt=30)
+                assert S.wait(rid) == 0
+                note("hv", rid)
+        except Exception as ex:
+            errors.append(repr(ex))
+
+    threads = [threading.Thread(target=chain, args=(c,)) for c in range(chains)]
+    threads += [threading.Thread(target=fwi_client, args=(i,)) for i in range(fwi)]
+    t0 = time.perf_counter()
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    span = time.perf_counter() - t0
+    if errors:
+        raise RuntimeError("chain clients failed: " + errors[0])
+    out = {"chains": chains, "fwi_clients": fwi, "chain_steps": chains * steps, "span_s": span,
+           "chain_steps_per_s": chains * steps / span, "acceptance": sum(accepted) / (chains * steps),
+           "requests": sum(len(v) for v in rids.values()), "requests_per_s": sum(len(v) for v in rids.values()) / span}
+    for kind, ids in rids.items():
+        lat = np.array([(lambda i: i["t_done"] - i["t_submit"])(S.info(r)) for r in ids]) * 1e3
+        if len(lat):
+            out[kind] = {"n": len(lat), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+    S.close()
+    for x in (LR, prior):
+        x.close()
+    out["what"] = ("closed loop: each chain waits for its requests; sample = LR sampling factor, hd = LR H~_d apply "
+                   "(both approximation requests), misfit on the 128x128 problem; FWI clients: gradient and H v on "
+                   "256x256")
+    return out
+
+
 def run_serve(args):
     """Serving workload: Poisson arrivals at fractions of the measured serial
     capacity, memory-budgeted admission into a 150 GB pool."""
@@ -744,6 +865,7 @@ def run_serve(args):
                    "requests": n, "concurrency": args.concurrency, "snapshots_per_shot": ckpt},
         "serve": {"serial_req_s": serial_rate, "serial_hv_per_s": n_hv / t_serial, "rates": results},
     }
+    line["serve"]["gpcn_request_source"] = serve_chains(dev, args.concurrency)
     print(json.dumps(line))
 
 

@@ -495,7 +495,7 @@ int hv_gpcn_accept(int n, int c, const double *phi_new, const float *m_new, cons
 #define HV_REQ_HV 0
 #define HV_REQ_GRAD 1
 #define HV_REQ_MISFIT 2
-#define HV_REQ_APPROX 3         /* hv_approx_apply(approx, v, k, out, HV_APPROX_H); needs no workspace */
+#define HV_REQ_APPROX 3         /* hv_approx_apply(approx, v, k, out, approx_mode); needs no workspace */
 #define HV_REQ_QUEUED 100
 #define HV_REQ_RUNNING 101
 typedef struct hv_server hv_server;
@@ -510,6 +510,7 @@ typedef struct hv_request {
     double *phi;            /* GRAD, MISFIT: device scalar                        */
     int ckpt;               /* HV, GRAD: checkpoint budget                        */
     const hv_approx *approx; /* APPROX: a built approximation                     */
+    int approx_mode;        /* APPROX: HV_APPROX_* mode of hv_approx_apply         */
 } hv_request;
 typedef struct hv_request_info {
     int kind, status;

@@ -37,7 +37,7 @@ class HvAcq(ctypes.Structure):
 
 class HvRequest(ctypes.Structure):
     _fields_ = [("kind", c_int), ("problem", c_void_p), ("m", fp), ("v", fp), ("k", c_int), ("d_obs", fp),
-                ("out", fp), ("phi", fp), ("ckpt", c_int), ("approx", c_void_p)]
+                ("out", fp), ("phi", fp), ("ckpt", c_int), ("approx", c_void_p), ("approx_mode", c_int)]
 
 
 class HvRequestInfo(ctypes.Structure):

@@ -246,8 +246,11 @@ struct LowRank {
     float *W = nullptr;        // [r][N], W = A V
     float *U = nullptr;        // [r][N], U = A W = R V
     double *w = nullptr;       // [2r]: Lambda, then S_r = 1 - (Lambda + 1)^-1/2
-    double *c = nullptr;       // [r] scratch coefficients
-    float *x = nullptr;        // [N] scratch field
+    double *c = nullptr;       // [xk][r] scratch coefficients
+    float *x = nullptr;        // [xk][N] scratch fields
+    int xk = 0;                // vectors the scratch holds
+    cudaEvent_t done = nullptr;   // last use of the scratch
+    std::mutex *mu = nullptr;     // applies from several streams run one after another
 };
 // Y_in = H_d Omega [k][N]; `hessian(X, kk, out)` applies H_d to kk fields.
 int build_lowrank(LowRank &L, const float *Y_in, int k, int rank, size_t N,

@@ -109,14 +109,14 @@ __global__ void k_combine(const double *__restrict__ M, const double *__restrict
     out[t] = s;
 }
 
-// c[i] = w[i] * sum_e V[i][e] x[e] (FP64); one CTA per i.
-__global__ void k_dots(const float *__restrict__ V, const float *__restrict__ x, const double *__restrict__ w,
-                       double *__restrict__ c, size_t N)
+// C[q][i] = w[i] sum_e M[i][e] X[q][e] (FP64); one CTA per (i, q).
+__global__ void k_coef_batch(const float *__restrict__ M, const float *__restrict__ X, const double *__restrict__ w,
+                             double *__restrict__ C, int r, size_t N)
 {
-    const int i = blockIdx.x;
-    const float *a = V + (size_t)i * N;
+    const int i = blockIdx.x, q = blockIdx.y;
+    const float *a = M + (size_t)i * N, *b = X + (size_t)q * N;
     double s = 0.0;
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) s = fma((double)a[e], (double)x[e], s);
+    for (size_t e = threadIdx.x; e < N; e += blockDim.x) s = fma((double)a[e], (double)b[e], s);
     __shared__ double sh[256];
     sh[threadIdx.x] = s;
     __syncthreads();
@@ -124,18 +124,20 @@ __global__ void k_dots(const float *__restrict__ V, const float *__restrict__ x,
         if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
         __syncthreads();
     }
-    if (threadIdx.x == 0) c[i] = sh[0] * w[i];
+    if (threadIdx.x == 0) C[(size_t)q * r + i] = sh[0] * w[i];
 }
 
-// out[e] = base[e] + sign * sum_i c[i] V[i][e]  (base may be null: 0).
-__global__ void k_lincomb(const float *__restrict__ V, const double *__restrict__ c, const float *__restrict__ base,
-                          float sign, float *__restrict__ out, int r, size_t N)
+// out[q][e] = base[q][e] + sign sum_i C[q][i] M[i][e]  (base may be null: 0).
+__global__ void k_lincomb_batch(const float *__restrict__ M, const double *__restrict__ C, const float *__restrict__ base,
+                                float sign, float *__restrict__ out, int r, int k, size_t N)
 {
-    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= N) return;
+    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (size_t)k * N) return;
+    const int q = (int)(t / N);
+    const size_t e = t - (size_t)q * N;
     double s = 0.0;
-    for (int i = 0; i < r; ++i) s = fma(c[i], (double)V[(size_t)i * N + e], s);
-    out[e] = (base ? base[e] : 0.0f) + sign * (float)s;
+    for (int i = 0; i < r; ++i) s = fma(C[(size_t)q * r + i], (double)M[(size_t)i * N + e], s);
+    out[t] = (base ? base[t] : 0.0f) + sign * (float)s;
 }
 
 }  // namespace
@@ -389,6 +391,7 @@ int build_lowrank(LowRank &L, const float *Y_in, int k, int rank, size_t N,
     HV_RT_INTERNAL(hvi::hermitian_eig(kk, Tc, lam, S));
     L.r = rank;
     L.N = N;
+    L.mu = new std::mutex;
     L.lam.assign(lam.begin(), lam.begin() + rank);
     std::vector<double> Sh((size_t)kk * rank), wh(2 * (size_t)rank);
     for (int i = 0; i < kk; ++i)
@@ -402,8 +405,7 @@ int build_lowrank(LowRank &L, const float *Y_in, int k, int rank, size_t N,
         (e = cudaMalloc(&L.W, (size_t)rank * N * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&L.U, (size_t)rank * N * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&L.w, wh.size() * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&L.c, (size_t)rank * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&L.x, N * sizeof(float))) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaMemcpyAsync(L.w, wh.data(), wh.size() * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess ||
         (e = cudaMemcpyAsync(M, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st)) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "low-rank factors: %s", cudaGetErrorString(e));
@@ -431,29 +433,44 @@ void lowrank_destroy(LowRank &L)
     cudaFree(L.w);
     cudaFree(L.c);
     cudaFree(L.x);
+    if (L.done) cudaEventDestroy(L.done);
+    delete L.mu;
     L = LowRank{};
 }
 
 // mode 0: out = U Lambda U^T v (U = R V: R V Lambda V^T R v); mode 2: out = A^-1 v - V S_r W^T v.
+// k vectors at once: one coefficient kernel (FP64 sums), one combination kernel.
 int lowrank_apply(LowRank &L, const float *v, int k, float *out, int mode, cudaStream_t st)
 {
     const size_t N = L.N;
-    for (int j = 0; j < k; ++j) {
-        const float *vj = v + (size_t)j * N;
-        float *oj = out + (size_t)j * N;
-        if (mode == 0) {
-            k_dots<<<L.r, 256, 0, st>>>(L.U, vj, L.w, L.c, N);
-            HV_RT_INTERNAL(launched("k_dots"));
-            k_lincomb<<<nb(N, 256), 256, 0, st>>>(L.U, L.c, nullptr, 1.0f, oj, L.r, N);
-            HV_RT_INTERNAL(launched("k_lincomb"));
-        } else {
-            HV_RT_INTERNAL(prior_Ainv(L.prior, vj, L.x, 1, st));
-            k_dots<<<L.r, 256, 0, st>>>(L.W, vj, L.w + L.r, L.c, N);
-            HV_RT_INTERNAL(launched("k_dots"));
-            k_lincomb<<<nb(N, 256), 256, 0, st>>>(L.V, L.c, L.x, -1.0f, oj, L.r, N);
-            HV_RT_INTERNAL(launched("k_lincomb"));
-        }
+    std::lock_guard<std::mutex> lk(*L.mu);
+    cudaError_t e = cudaStreamWaitEvent(st, L.done, 0);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
+    if (L.xk < k) {
+        cudaFree(L.x);   // synchronises: nothing in flight uses the old scratch afterwards
+        cudaFree(L.c);
+        L.x = nullptr;
+        L.c = nullptr;
+        L.xk = 0;
+        if ((e = cudaMalloc(&L.x, (size_t)k * N * sizeof(float))) != cudaSuccess ||
+            (e = cudaMalloc(&L.c, (size_t)k * L.r * sizeof(double))) != cudaSuccess)
+            return hvi::fail(HV_ECUDA, "low-rank apply scratch: %s", cudaGetErrorString(e));
+        L.xk = k;
     }
+    if (mode == 0) {
+        k_coef_batch<<<dim3(L.r, k), 256, 0, st>>>(L.U, v, L.w, L.c, L.r, N);
+        HV_RT_INTERNAL(launched("k_coef_batch"));
+        k_lincomb_batch<<<nb((size_t)k * N, 256), 256, 0, st>>>(L.U, L.c, nullptr, 1.0f, out, L.r, k, N);
+        HV_RT_INTERNAL(launched("k_lincomb_batch"));
+    } else {
+        HV_RT_INTERNAL(prior_Ainv(L.prior, v, L.x, k, st));
+        k_coef_batch<<<dim3(L.r, k), 256, 0, st>>>(L.W, v, L.w + L.r, L.c, L.r, N);
+        HV_RT_INTERNAL(launched("k_coef_batch"));
+        k_lincomb_batch<<<nb((size_t)k * N, 256), 256, 0, st>>>(L.V, L.c, L.x, -1.0f, out, L.r, k, N);
+        HV_RT_INTERNAL(launched("k_lincomb_batch"));
+    }
+    e = cudaEventRecord(L.done, st);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
     return HV_OK;
 }
 

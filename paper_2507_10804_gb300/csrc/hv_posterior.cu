@@ -54,6 +54,7 @@ struct hv_posterior {
     float *V = nullptr, *U = nullptr;     // [r][N]
     double *w = nullptr;                  // [2r]: Lambda, S_r
     PostWork work;
+    cudaEvent_t done = nullptr;           // last use of the scratch and the prior's tables
     std::mutex *mu = nullptr;
 };
 
@@ -255,6 +256,16 @@ __global__ void k_gpcn_accept(const double *__restrict__ phi_new, const float *_
 
 constexpr int kWorkFields = 7, kMaxCorrection = 256;
 
+// Holds the posterior's lock and orders `st` after the previous user of its
+// scratch (which may have run on another stream); records the next use on exit.
+struct Session {
+    std::lock_guard<std::mutex> lk;
+    hv_posterior *p;
+    cudaStream_t st;
+    Session(hv_posterior *p_, cudaStream_t st_) : lk(*p_->mu), p(p_), st(st_) { cudaStreamWaitEvent(st, p->done, 0); }
+    ~Session() { cudaEventRecord(p->done, st); }
+};
+
 int ensure_work(PostWork &w, int k, size_t N)
 {
     if (w.k >= k) return HV_OK;
@@ -407,7 +418,9 @@ extern "C" int hv_posterior_create(int nz, int nx, double h, double delta, doubl
     p->h = h;
     p->approx = approx;
     p->mu = new std::mutex;
-    const int rc = hvk::prior_create(p->prior, nz, nx, h, delta, gamma);
+    int rc = hvk::prior_create(p->prior, nz, nx, h, delta, gamma);
+    if (rc == HV_OK && cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess)
+        rc = hvi::fail(HV_ECUDA, "cudaEventCreate failed");
     if (rc != HV_OK) {
         hv_posterior_destroy(p);
         return rc;
@@ -427,6 +440,7 @@ extern "C" int hv_posterior_destroy(hv_posterior *p)
     cudaFree(p->work.f);
     cudaFree(p->work.d);
     cudaFree(p->work.act);
+    if (p->done) cudaEventDestroy(p->done);
     delete p->mu;
     delete p;
     return HV_OK;
@@ -443,7 +457,7 @@ extern "C" int hv_posterior_solve(hv_posterior *p, const hv_operator *op, const 
         return hvi::fail(HV_EINVAL, "the operator does not act on the posterior's grid");
     HV_RT_INTERNAL(check_device(p->device));
     cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lk(*p->mu);
+    Session ses(p, st);
     HV_RT_INTERNAL(ensure_work(p->work, k, (size_t)p->nz * p->nx));
     return pcg(p->prior, op ? user_op(op, st) : gram_op(p, st), b, k, x, rtol, max_iter, iters, st, p->work);
 }
@@ -454,7 +468,7 @@ extern "C" int hv_posterior_apply(hv_posterior *p, const float *v, int k, float 
     if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "k = %d; need 1 <= k <= 65535", k);
     HV_RT_INTERNAL(check_device(p->device));
     cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lk(*p->mu);
+    Session ses(p, st);
     const size_t N = (size_t)p->nz * p->nx;
     HV_RT_INTERNAL(ensure_work(p->work, k, N));
     float *t = work_field(p->work, 4, N);
@@ -478,7 +492,7 @@ extern "C" int hv_posterior_sample(hv_posterior *p, const float *n1, const float
     if (!(rtol > 0 && rtol < 1) || max_iter < 1) return hvi::fail(HV_EINVAL, "rtol %g, max_iter %d", rtol, max_iter);
     HV_RT_INTERNAL(check_device(p->device));
     cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lk(*p->mu);
+    Session ses(p, st);
     const size_t N = (size_t)p->nz * p->nx, n = (size_t)k * N;
     HV_RT_INTERNAL(ensure_work(p->work, k, N));
     if (!p->approx) {
@@ -510,7 +524,7 @@ extern "C" int hv_posterior_correct(hv_posterior *p, const hv_operator *hd, cons
     if (!(rtol > 0 && rtol < 1) || max_iter < 1) return hvi::fail(HV_EINVAL, "rtol %g, max_iter %d", rtol, max_iter);
     HV_RT_INTERNAL(check_device(p->device));
     cudaStream_t st = (cudaStream_t)stream;
-    std::lock_guard<std::mutex> lk(*p->mu);
+    Session ses(p, st);
     const size_t N = (size_t)p->nz * p->nx, n = (size_t)k * N;
     Bufs bf;
     bf.st = st;

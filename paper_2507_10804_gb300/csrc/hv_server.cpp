@@ -126,7 +126,7 @@ int launch(hv_server *S, const Req &q)
     int rc;
     if (r.kind == HV_REQ_HV) rc = hv_hessian_apply(r.problem, r.m, r.v, r.k, r.out, r.ckpt, ws, q.ws, st);
     else if (r.kind == HV_REQ_GRAD) rc = hv_misfit_grad(r.problem, r.m, r.d_obs, r.phi, r.out, r.ckpt, ws, q.ws, st);
-    else if (r.kind == HV_REQ_APPROX) rc = hv_approx_apply(r.approx, r.v, r.k, r.out, HV_APPROX_H, st);
+    else if (r.kind == HV_REQ_APPROX) rc = hv_approx_apply(r.approx, r.v, r.k, r.out, r.approx_mode, st);
     else rc = hv_misfit(r.problem, r.m, r.d_obs, r.phi, ws, q.ws, st);
     cudaError_t e = cudaEventRecord(S->events[q.slot], S->streams[q.slot]);
     if (rc == HV_OK && e != cudaSuccess) rc = HV_ECUDA;
@@ -262,7 +262,8 @@ extern "C" int hv_submit(hv_server *S, const hv_request *r, unsigned long long *
     const bool approx = r->kind == HV_REQ_APPROX;
     if ((!approx && (!r->problem || !r->m)) || (r->kind == HV_REQ_HV && (!r->v || !r->out || r->k < 1)) ||
         (r->kind == HV_REQ_GRAD && (!r->d_obs || !r->out || !r->phi)) || (r->kind == HV_REQ_MISFIT && (!r->d_obs || !r->phi)) ||
-        (approx && (!r->approx || !r->v || !r->out || r->k < 1)) || r->kind < HV_REQ_HV || r->kind > HV_REQ_APPROX)
+        (approx && (!r->approx || !r->v || !r->out || r->k < 1 || r->approx_mode < HV_APPROX_H ||
+                    r->approx_mode > HV_APPROX_SQRT_T)) || r->kind < HV_REQ_HV || r->kind > HV_REQ_APPROX)
         return hvi::fail(HV_EINVAL, "hv_submit: incomplete request of kind %d", r->kind);
     const int dev = approx ? hvi::approx_device(r->approx) : r->problem->device;
     if (dev != S->device) return hvi::fail(HV_EINVAL, "hv_submit: %s on another device", approx ? "approximation" : "problem");

@@ -40,13 +40,14 @@ class Server:
         except Exception:
             pass
 
-    def _submit(self, kind, P: Problem | None, m, v=None, k=0, d_obs=None, out=None, phi=None, ckpt=-1, approx=None):
+    def _submit(self, kind, P: Problem | None, m, v=None, k=0, d_obs=None, out=None, phi=None, ckpt=-1, approx=None,
+                mode=0):
         r = _lib.HvRequest(kind, P._h if P is not None else None, m.data_ptr() if m is not None else None,
                            v.data_ptr() if v is not None else None, int(k),
                            d_obs.data_ptr() if d_obs is not None else None,
                            out.data_ptr() if out is not None else None,
                            phi.data_ptr() if phi is not None else None, int(ckpt),
-                           approx._a if approx is not None else None)
+                           approx._a if approx is not None else None, int(mode))
         rid = ctypes.c_ulonglong()
         check(self.lib.hv_submit(self._s, ctypes.byref(r), ctypes.byref(rid)))
         self._keep[rid.value] = (P, m, v, d_obs, out, phi, approx)
@@ -63,11 +64,11 @@ class Server:
         g = torch.empty((P.nz, P.nx), dtype=torch.float32, device=self.device)
         return self._submit(HV_REQ_GRAD, P, m, d_obs=d_obs, out=g, phi=phi, ckpt=ckpt), phi, g
 
-    def submit_approx(self, A, v):
-        """Queue the apply of a built Hessian approximation (PsfApprox) to v[k, nz, nx];
-        returns (request id, output tensor)."""
+    def submit_approx(self, A, v, mode: int = 0):
+        """Queue the apply of a built Hessian approximation to v[k, nz, nx] in an HV_APPROX_* mode
+        (hv_approx_apply); returns (request id, output tensor)."""
         out = torch.empty(v.shape, dtype=torch.float32, device=self.device)
-        return self._submit(HV_REQ_APPROX, None, None, v=v, k=v.shape[0], out=out, approx=A), out
+        return self._submit(HV_REQ_APPROX, None, None, v=v, k=v.shape[0], out=out, approx=A, mode=mode), out
 
     def submit_misfit(self, P: Problem, m, d_obs):
         phi = torch.empty((), dtype=torch.float64, device=self.device)

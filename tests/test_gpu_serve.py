@@ -131,3 +131,29 @@ def test_approximate_hessian_requests_in_the_mix(problems):
     S.close()
     A.close()
     D.close()
+
+
+def test_approximation_modes_in_the_mix(problems):
+    """LR sampling-factor and H~_d requests and square-root PDO requests on several streams at
+    once: the shared scratch of each object is ordered across streams, so every result is bitwise
+    that of the direct call; an unknown mode is rejected at submission."""
+    from paper_2507_10804_gb300._lib import HV_APPROX_H, HV_APPROX_INVSQRT, HV_APPROX_SQRT, HV_APPROX_SQRT_T
+    w0, P0 = problems[0]
+    omega = t(synth.normal(401, 8 * w0.nz * w0.nx).reshape(8, w0.nz, w0.nx))
+    L = P0.approx_build_lr(t(w0.m), 1.0, 2500.0, 6, omega, ckpt=5)
+    Q = P0.approx_build_pdo(t(w0.m), 0.15, 8, ckpt=5).sqrt()
+    jobs = []
+    for i in range(12):
+        v = t(synth.smoothed_normal_vectors(410 + i, 1 + i % 2, w0.nz, w0.nx, 1.5))
+        obj, mode = [(L, HV_APPROX_INVSQRT), (L, HV_APPROX_H), (Q, HV_APPROX_SQRT), (Q, HV_APPROX_SQRT_T)][i % 4]
+        jobs.append((obj, mode, v, obj.apply(v, mode).cpu().numpy()))
+    S = Server(hbm_budget=1 << 30, max_concurrent=4)
+    subs = [S.submit_approx(o, v, mode) for o, mode, v, _ in jobs]
+    for (rid, out), (_, _, _, ref) in zip(subs, jobs):
+        assert S.wait(rid, timeout=300) == 0
+        assert np.array_equal(out.cpu().numpy(), ref)
+    with pytest.raises(Exception):
+        S.submit_approx(L, jobs[0][2], 7)
+    S.close()
+    L.close()
+    Q.close()
