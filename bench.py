@@ -400,6 +400,55 @@ def oracle_sample(w, threads: int, nt_s: int):
     return upd / sec / 1e9, sec, desc
 
 
+def oracle_rows(w):
+    """The FP64 oracle of each approximation row timed on the host on one vector (the batched
+    workload's 64x64 grid; the quadratic model on 256x256), as it stands: microseconds per vector."""
+    from oracle import lowrank_oracle as LO
+    from oracle import pdo_oracle as DO
+    from oracle import psf_oracle as PO
+    from oracle import quadratic_oracle as QO
+    from oracle import spd_oracle as SO
+    rng = np.random.default_rng(3)
+    nz, nx = w.nz, w.nx
+    v = rng.standard_normal((nz, nx))
+
+    def per_call(f, min_s=0.2):
+        f()
+        n, t = 0, time.perf_counter()
+        while True:
+            f()
+            n += 1
+            if time.perf_counter() - t > min_s:
+                return (time.perf_counter() - t) / n * 1e6
+
+    S, B = 12, 2
+    R = (B * S - 1) // 2
+    na = (nz - 1 - S // 2) // S + 1
+    nb = (nx - 1 - S // 2) // S + 1
+    P = rng.standard_normal((na * nb, 2 * R + 1, 2 * R + 1))
+    cplx = lambda r, a, b: rng.standard_normal((r, a, b)) + 1j * rng.standard_normal((r, a, b))
+    a8, b8 = cplx(8, nz, nx), cplx(8, nz, nx)
+    a22, b22 = cplx(22, nz, nx), cplx(22, nz, nx)
+    V16 = rng.standard_normal((16, nz, nx))
+    lam16 = np.linspace(1.0, 0.1, 16)
+    q = QO.make(256, 256, 10.0, [40.0 * 0.8 ** j for j in range(10)])
+    v2 = rng.standard_normal((256, 256))
+    a32, b32 = np.abs(cplx(32, 256, 256)), cplx(32, 256, 256)
+    out = {
+        "psf_apply_us": per_call(lambda: PO.apply(P, v[None], S, B)),
+        "pdo_apply_us": per_call(lambda: DO.lr_apply(a8, b8, v)),
+        "psfplus_apply_us": per_call(lambda: DO.lr_apply(a22, b22, v)),
+        "lr_apply_us": per_call(lambda: LO.apply_H(V16, lam16, v, w.h, 1.0, 2500.0)),
+        "lr_sample_us": per_call(lambda: LO.apply_sample_factor(V16, lam16, v, w.h, 1.0, 2500.0)),
+        "quad_hd_apply_256_us": per_call(lambda: QO.apply_Hd(q, v2)),
+        "quad_objective_256_us": per_call(lambda: QO.objective(q, v2, v2, 1.0, 2500.0)),
+        "spd_apply_256_rank32_us": per_call(lambda: SO.spd_apply(a32, b32, v2)),
+        "cores": 1,
+        "what": "numpy FP64 oracle, one vector per call, as it stands; random factors of the benchmark's shapes",
+    }
+    return out
+
+
 def updates_per_call(w) -> float:
     """Grid-point updates of one call applying H to the workload's k vectors: 3 fields
     (forward, Born, adjoint) for the first vector, 2 more per extra vector sharing u;
@@ -580,6 +629,8 @@ def run_ours(args, w):
             g, sec, desc = oracle_sample(w, threads, 120)
             cpu = {"value": g * 1e9 / updates_per_call(w) * w.k, "unit": UNIT, "cores": threads, "kind": "oracle",
                    "sample": desc, "seconds": sec, "gpt_updates_per_s": g * 1e9}
+            if args.workload == "batched":
+                cpu["rows"] = oracle_rows(w)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -883,9 +934,10 @@ def main():
     ap.add_argument("--concurrency", type=int, default=16, help="serving workload: concurrent requests")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
                     help="serving workload: arrival rates as fractions of the serial capacity")
-    ap.add_argument("--workload", choices=["paper", "batched", "serve"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "batched", "serve", "quadratic"], default="paper",
                     help="paper: 384x1152, 32 shots, 3000 steps, 1 vector (default); batched: the 64x64 model "
-                         "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph")
+                         "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph; quadratic: "
+                         "the quadratic test model's approximation, posterior and gpCN measurements alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tiles", type=int, nargs=3, default=None, metavar=("FWD", "ADVANCE", "ADJ"),
                     help="tile configurations instead of autotuning (profiling runs)")
@@ -893,6 +945,18 @@ def main():
     from paper_2507_10804_gb300 import synth
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "quadratic":
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        res = quad_measure(dev, steps=args.steps, warm=args.warmup)
+        print(json.dumps({"metric": "gpCN chain steps/s on the quadratic test model (section 4.1)",
+                          "value": res["gpcn_steps_per_s"], "unit": "chain steps/s", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["gpcn_ms_per_step"],
+                          "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": f"quadratic model {res['grid'][0]}x{res['grid'][1]}, "
+                                                 f"{res['chains']} chains"}, "quadratic_model": res}))
+        return
     if args.workload == "batched":
         CKPT = args.ckpt if args.ckpt is not None else -1
         w = synth.workload(3, nt=args.nt, ns=args.shots)
