@@ -248,6 +248,7 @@ struct LowRank {
     double *w = nullptr;       // [2r]: Lambda, then S_r = 1 - (Lambda + 1)^-1/2
     double *c = nullptr;       // [xk][r] scratch coefficients
     float *x = nullptr;        // [xk][N] scratch fields
+    double *red = nullptr;     // reduction partials for xk vectors
     int xk = 0;                // vectors the scratch holds
     cudaEvent_t done = nullptr;   // last use of the scratch
     std::mutex *mu = nullptr;     // applies from several streams run one after another
@@ -274,6 +275,22 @@ int launch_reduce_phi(const double *partials, int nblocks, double scale, double 
 int launch_copy_wavefield(const hv_handle *h, const float *u, float *out, cudaStream_t st);
 int launch_zero_ghosts(const hv_handle *h, float *f, long long nfields, cudaStream_t st);
 int launch_setup(hv_handle *h, cudaStream_t st);
+
+// Skinny dense products over grid fields (hv_blas.cu); deterministic chunked
+// reductions (rows_dot: FP64; coef: FP32 inside a chunk, FP64 across chunks).
+// scratch: the FP64 partials, rows_dot_scratch / coef_scratch doubles.
+int chunks_of(size_t N);
+size_t rows_dot_scratch(int k, size_t N);
+size_t coef_scratch(int r, int k, size_t N);
+// out[q] = scale sum_e A[q][e] B[q][e], q < k
+int rows_dot(const float *A, const float *B, double *out, int k, size_t N, double scale, double *scratch,
+             cudaStream_t st);
+// C[q][j] = w[j] sum_e M[j][e] X[q][e] (w may be null: 1), j < r, q < k
+int coef(const float *M, int r, const float *X, int k, size_t N, const double *w, double *C, double *scratch,
+         cudaStream_t st);
+// out[q][e] = base[q][e] + sign sum_j C[q][j] M[j][e] (base may be null: 0; out may be base), r <= 256
+int combine(const float *M, int r, const double *C, int k, size_t N, const float *base, float sign, float *out,
+            cudaStream_t st);
 
 // Process-wide kernel launch counter (hv_kernel_launches).
 void count_launch();

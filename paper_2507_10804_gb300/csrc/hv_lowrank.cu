@@ -109,37 +109,6 @@ __global__ void k_combine(const double *__restrict__ M, const double *__restrict
     out[t] = s;
 }
 
-// C[q][i] = w[i] sum_e M[i][e] X[q][e] (FP64); one CTA per (i, q).
-__global__ void k_coef_batch(const float *__restrict__ M, const float *__restrict__ X, const double *__restrict__ w,
-                             double *__restrict__ C, int r, size_t N)
-{
-    const int i = blockIdx.x, q = blockIdx.y;
-    const float *a = M + (size_t)i * N, *b = X + (size_t)q * N;
-    double s = 0.0;
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) s = fma((double)a[e], (double)b[e], s);
-    __shared__ double sh[256];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) C[(size_t)q * r + i] = sh[0] * w[i];
-}
-
-// out[q][e] = base[q][e] + sign sum_i C[q][i] M[i][e]  (base may be null: 0).
-__global__ void k_lincomb_batch(const float *__restrict__ M, const double *__restrict__ C, const float *__restrict__ base,
-                                float sign, float *__restrict__ out, int r, int k, size_t N)
-{
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const int q = (int)(t / N);
-    const size_t e = t - (size_t)q * N;
-    double s = 0.0;
-    for (int i = 0; i < r; ++i) s = fma(C[(size_t)q * r + i], (double)M[(size_t)i * N + e], s);
-    out[t] = (base ? base[t] : 0.0f) + sign * (float)s;
-}
-
 }  // namespace
 
 // ------------------------------------------------------------------ prior
@@ -433,13 +402,14 @@ void lowrank_destroy(LowRank &L)
     cudaFree(L.w);
     cudaFree(L.c);
     cudaFree(L.x);
+    cudaFree(L.red);
     if (L.done) cudaEventDestroy(L.done);
     delete L.mu;
     L = LowRank{};
 }
 
 // mode 0: out = U Lambda U^T v (U = R V: R V Lambda V^T R v); mode 2: out = A^-1 v - V S_r W^T v.
-// k vectors at once: one coefficient kernel (FP64 sums), one combination kernel.
+// k vectors at once: the coefficient and combination products of hv_blas.cu.
 int lowrank_apply(LowRank &L, const float *v, int k, float *out, int mode, cudaStream_t st)
 {
     const size_t N = L.N;
@@ -449,25 +419,24 @@ int lowrank_apply(LowRank &L, const float *v, int k, float *out, int mode, cudaS
     if (L.xk < k) {
         cudaFree(L.x);   // synchronises: nothing in flight uses the old scratch afterwards
         cudaFree(L.c);
+        cudaFree(L.red);
         L.x = nullptr;
         L.c = nullptr;
+        L.red = nullptr;
         L.xk = 0;
         if ((e = cudaMalloc(&L.x, (size_t)k * N * sizeof(float))) != cudaSuccess ||
-            (e = cudaMalloc(&L.c, (size_t)k * L.r * sizeof(double))) != cudaSuccess)
+            (e = cudaMalloc(&L.c, (size_t)k * L.r * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc(&L.red, coef_scratch(L.r, k, N) * sizeof(double))) != cudaSuccess)
             return hvi::fail(HV_ECUDA, "low-rank apply scratch: %s", cudaGetErrorString(e));
         L.xk = k;
     }
     if (mode == 0) {
-        k_coef_batch<<<dim3(L.r, k), 256, 0, st>>>(L.U, v, L.w, L.c, L.r, N);
-        HV_RT_INTERNAL(launched("k_coef_batch"));
-        k_lincomb_batch<<<nb((size_t)k * N, 256), 256, 0, st>>>(L.U, L.c, nullptr, 1.0f, out, L.r, k, N);
-        HV_RT_INTERNAL(launched("k_lincomb_batch"));
+        HV_RT_INTERNAL(coef(L.U, L.r, v, k, N, L.w, L.c, L.red, st));
+        HV_RT_INTERNAL(combine(L.U, L.r, L.c, k, N, nullptr, 1.0f, out, st));
     } else {
         HV_RT_INTERNAL(prior_Ainv(L.prior, v, L.x, k, st));
-        k_coef_batch<<<dim3(L.r, k), 256, 0, st>>>(L.W, v, L.w + L.r, L.c, L.r, N);
-        HV_RT_INTERNAL(launched("k_coef_batch"));
-        k_lincomb_batch<<<nb((size_t)k * N, 256), 256, 0, st>>>(L.V, L.c, L.x, -1.0f, out, L.r, k, N);
-        HV_RT_INTERNAL(launched("k_lincomb_batch"));
+        HV_RT_INTERNAL(coef(L.W, L.r, v, k, N, L.w + L.r, L.c, L.red, st));
+        HV_RT_INTERNAL(combine(L.V, L.r, L.c, k, N, L.x, -1.0f, out, st));
     }
     e = cudaEventRecord(L.done, st);
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));

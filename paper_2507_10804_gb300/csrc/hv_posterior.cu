@@ -40,6 +40,7 @@ struct PostWork {
     int k = 0;
     float *f = nullptr;
     double *d = nullptr;
+    double *red = nullptr;   // reduction partials (hv_blas.cu)
     int *act = nullptr;
 };
 
@@ -90,23 +91,9 @@ struct Bufs {   // device scratch freed (after the stream drains) on every exit 
     }
 };
 
-// s[q] = sum_e a[q][e] b[q][e] in FP64; one CTA per q.
-__global__ void k_dot_rows(const float *__restrict__ a, const float *__restrict__ b, double *__restrict__ s, size_t N)
-{
-    const size_t o = (size_t)blockIdx.x * N;
-    double acc = 0.0;
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) acc = fma((double)a[o + e], (double)b[o + e], acc);
-    __shared__ double sh[256];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) s[blockIdx.x] = sh[0];
-}
-
-// G[i][j] = sum_e X[i][e] Y[j][e] in FP64; one CTA per (i, j).
+// Build-time products of the correction (FP64 accumulation throughout: the
+// orthonormalisation combines nearly dependent vectors with large weights).
+// G[i][j] = sum_e X[i][e] Y[j][e]; one CTA per (i, j).
 __global__ void k_gram_rows(const float *__restrict__ X, const float *__restrict__ Y, double *__restrict__ G, int kb,
                             size_t N)
 {
@@ -124,7 +111,7 @@ __global__ void k_gram_rows(const float *__restrict__ X, const float *__restrict
     if (threadIdx.x == 0) G[(size_t)i * kb + j] = sh[0];
 }
 
-// out[j][e] = sum_i M[i][j] X[i][e] (M: ki x ko, FP64 sums).
+// out[j][e] = sum_i M[i][j] X[i][e] (M: ki x ko).
 __global__ void k_combine_rows(const double *__restrict__ M, const float *__restrict__ X, float *__restrict__ out,
                                int ki, int ko, size_t N)
 {
@@ -135,37 +122,6 @@ __global__ void k_combine_rows(const double *__restrict__ M, const float *__rest
     double s = 0.0;
     for (int i = 0; i < ki; ++i) s = fma(M[(size_t)i * ko + j], (double)X[(size_t)i * N + e], s);
     out[t] = (float)s;
-}
-
-// C[q][j] = w[j] sum_e M[j][e] X[q][e]; one CTA per (j, q).
-__global__ void k_coef(const float *__restrict__ M, const float *__restrict__ X, const double *__restrict__ w,
-                       double *__restrict__ C, int r, size_t N)
-{
-    const int j = blockIdx.x, q = blockIdx.y;
-    const float *a = M + (size_t)j * N, *b = X + (size_t)q * N;
-    double acc = 0.0;
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) acc = fma((double)a[e], (double)b[e], acc);
-    __shared__ double sh[256];
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) C[(size_t)q * r + j] = sh[0] * w[j];
-}
-
-// out[q][e] = base[q][e] + sign sum_j C[q][j] M[j][e]  (out may be base).
-__global__ void k_add_coef(const float *__restrict__ M, const double *__restrict__ C, const float *base, float *out,
-                           float sign, int r, int k, size_t N)
-{
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const int q = (int)(t / N);
-    const size_t e = t - (size_t)q * N;
-    double s = 0.0;
-    for (int j = 0; j < r; ++j) s = fma(C[(size_t)q * r + j], (double)M[(size_t)j * N + e], s);
-    out[t] = (float)((double)base[t] + (double)sign * s);
 }
 
 // out = a + s b  (out may be a).
@@ -224,34 +180,27 @@ __global__ void k_gpcn_propose(const float *__restrict__ m, const float *__restr
     if (d) d[t] = dd;
 }
 
-// gpCN acceptance, one CTA per chain: Delta' = phi' - 1/2 d . Hd (FP64); accept
-// iff log_u < Delta_cur - Delta'; on acceptance m <- m' and Delta_cur <- Delta'.
-__global__ void k_gpcn_accept(const double *__restrict__ phi_new, const float *__restrict__ mp,
-                              const float *__restrict__ d, const float *__restrict__ Hd,
-                              const double *__restrict__ log_u, float *__restrict__ m, double *__restrict__ delta_cur,
-                              int *__restrict__ accepted, size_t N)
+// gpCN acceptance after the FP64 dots dHd[c] = d . Hd: Delta' = phi' - 1/2 dHd;
+// accept iff log_u < Delta_cur - Delta'; on acceptance Delta_cur <- Delta'.
+__global__ void k_gpcn_decide(const double *__restrict__ phi_new, const double *__restrict__ dHd,
+                              const double *__restrict__ log_u, double *__restrict__ delta_cur,
+                              int *__restrict__ accepted, int c)
 {
-    const int c = blockIdx.x;
-    const size_t o = (size_t)c * N;
-    double acc = 0.0;
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) acc = fma((double)d[o + e], (double)Hd[o + e], acc);
-    __shared__ double sh[256];
-    __shared__ int take;
-    sh[threadIdx.x] = acc;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const double dn = phi_new[c] - 0.5 * sh[0];
-        take = log_u[c] < delta_cur[c] - dn;
-        if (take) delta_cur[c] = dn;
-        accepted[c] = take;
-    }
-    __syncthreads();
-    if (take)
-        for (size_t e = threadIdx.x; e < N; e += blockDim.x) m[o + e] = mp[o + e];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= c) return;
+    const double dn = phi_new[i] - 0.5 * dHd[i];
+    const int take = log_u[i] < delta_cur[i] - dn;
+    if (take) delta_cur[i] = dn;
+    accepted[i] = take;
+}
+
+// m[c] <- m_new[c] for the accepted chains; grid (points / 256, c).
+__global__ void k_gpcn_take(const float *__restrict__ mp, const int *__restrict__ accepted, float *__restrict__ m,
+                            size_t N)
+{
+    const int c = blockIdx.y;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < N && accepted[c]) m[(size_t)c * N + e] = mp[(size_t)c * N + e];
 }
 
 constexpr int kWorkFields = 7, kMaxCorrection = 256;
@@ -271,11 +220,13 @@ int ensure_work(PostWork &w, int k, size_t N)
     if (w.k >= k) return HV_OK;
     cudaFree(w.f);   // synchronises: nothing in flight uses the old scratch afterwards
     cudaFree(w.d);
+    cudaFree(w.red);
     cudaFree(w.act);
     w = PostWork{};
     cudaError_t e;
     if ((e = cudaMalloc(&w.f, (size_t)kWorkFields * k * N * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&w.d, (size_t)(5 + kMaxCorrection) * k * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&w.red, hvk::coef_scratch(kMaxCorrection, k, N) * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&w.act, (size_t)k * sizeof(int))) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "posterior scratch: %s", cudaGetErrorString(e));
     w.k = k;
@@ -316,8 +267,7 @@ int pcg(hvk::Prior &P, const OpFn &op, const float *b, int k, float *x, double r
     int *act = w.act;
     PCK(cudaMemsetAsync(x, 0, n * sizeof(float), st));
     PCK(cudaMemcpyAsync(r, b, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    k_dot_rows<<<k, 256, 0, st>>>(b, b, rr, N);
-    HV_RT_INTERNAL(launched("k_dot_rows"));
+    HV_RT_INTERNAL(hvk::rows_dot(b, b, rr, k, N, 1.0, w.red, st));
     std::vector<double> bb(k), rh(k);
     std::vector<int> ah(k);
     PCK(cudaMemcpyAsync(bb.data(), rr, k * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -327,8 +277,7 @@ int pcg(hvk::Prior &P, const OpFn &op, const float *b, int k, float *x, double r
     PCK(cudaMemcpyAsync(act, ah.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
     HV_RT_INTERNAL(hvk::prior_Rinv(P, r, z, k, st));
     PCK(cudaMemcpyAsync(p, z, n * sizeof(float), cudaMemcpyDeviceToDevice, st));
-    k_dot_rows<<<k, 256, 0, st>>>(r, z, rz, N);
-    HV_RT_INTERNAL(launched("k_dot_rows"));
+    HV_RT_INTERNAL(hvk::rows_dot(r, z, rz, k, N, 1.0, w.red, st));
     int it = 0;
     while (live > 0) {
         if (it >= max_iter) {
@@ -338,14 +287,12 @@ int pcg(hvk::Prior &P, const OpFn &op, const float *b, int k, float *x, double r
         }
         ++it;
         HV_RT_INTERNAL(apply_op_plus_R(P, op, p, k, q, t, st));
-        k_dot_rows<<<k, 256, 0, st>>>(p, q, pq, N);
-        HV_RT_INTERNAL(launched("k_dot_rows"));
+        HV_RT_INTERNAL(hvk::rows_dot(p, q, pq, k, N, 1.0, w.red, st));
         k_cg_alpha<<<nblk(k, 128), 128, 0, st>>>(rz, pq, act, alpha, k);
         HV_RT_INTERNAL(launched("k_cg_alpha"));
         k_cg_xr<<<nblk(n, 256), 256, 0, st>>>(x, r, p, q, alpha, k, N);
         HV_RT_INTERNAL(launched("k_cg_xr"));
-        k_dot_rows<<<k, 256, 0, st>>>(r, r, rr, N);
-        HV_RT_INTERNAL(launched("k_dot_rows"));
+        HV_RT_INTERNAL(hvk::rows_dot(r, r, rr, k, N, 1.0, w.red, st));
         PCK(cudaMemcpyAsync(rh.data(), rr, k * sizeof(double), cudaMemcpyDeviceToHost, st));
         PCK(cudaStreamSynchronize(st));
         live = 0;
@@ -353,8 +300,7 @@ int pcg(hvk::Prior &P, const OpFn &op, const float *b, int k, float *x, double r
         if (live == 0) break;
         PCK(cudaMemcpyAsync(act, ah.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
         HV_RT_INTERNAL(hvk::prior_Rinv(P, r, z, k, st));
-        k_dot_rows<<<k, 256, 0, st>>>(r, z, rz_new, N);
-        HV_RT_INTERNAL(launched("k_dot_rows"));
+        HV_RT_INTERNAL(hvk::rows_dot(r, z, rz_new, k, N, 1.0, w.red, st));
         k_cg_p<<<nblk(n, 256), 256, 0, st>>>(p, z, rz_new, rz, act, k, N);
         HV_RT_INTERNAL(launched("k_cg_p"));
         k_store_rz<<<nblk(k, 128), 128, 0, st>>>(rz, rz_new, k);
@@ -475,10 +421,8 @@ extern "C" int hv_posterior_apply(hv_posterior *p, const float *v, int k, float 
     double *C = p->work.d + 5 * (size_t)p->work.k;
     HV_RT_INTERNAL(apply_op_plus_R(p->prior, gram_op(p, st), v, k, out, t, st));
     if (p->r > 0) {
-        k_coef<<<dim3(p->r, k), 256, 0, st>>>(p->U, v, p->w, C, p->r, N);
-        HV_RT_INTERNAL(launched("k_coef"));
-        k_add_coef<<<nblk((size_t)k * N, 256), 256, 0, st>>>(p->U, C, out, out, 1.0f, p->r, k, N);
-        HV_RT_INTERNAL(launched("k_add_coef"));
+        HV_RT_INTERNAL(hvk::coef(p->U, p->r, v, k, N, p->w, C, p->work.red, st));
+        HV_RT_INTERNAL(hvk::combine(p->U, p->r, C, k, N, out, 1.0f, out, st));
     }
     return HV_OK;
 }
@@ -507,10 +451,8 @@ extern "C" int hv_posterior_sample(hv_posterior *p, const float *n1, const float
     }
     if (p->r > 0) {
         double *C = p->work.d + 5 * (size_t)p->work.k;
-        k_coef<<<dim3(p->r, k), 256, 0, st>>>(p->U, zeta, p->w + p->r, C, p->r, N);
-        HV_RT_INTERNAL(launched("k_coef"));
-        k_add_coef<<<nblk(n, 256), 256, 0, st>>>(p->V, C, zeta, zeta, -1.0f, p->r, k, N);
-        HV_RT_INTERNAL(launched("k_add_coef"));
+        HV_RT_INTERNAL(hvk::coef(p->U, p->r, zeta, k, N, p->w + p->r, C, p->work.red, st));
+        HV_RT_INTERNAL(hvk::combine(p->V, p->r, C, k, N, zeta, -1.0f, zeta, st));
     }
     return HV_OK;
 }
@@ -656,7 +598,20 @@ extern "C" int hv_gpcn_accept(int n, int c, const double *phi_new, const float *
     if (n < 1 || c < 1 || c > 65535 || !phi_new || !m_new || !d_new || !Hd_new || !log_u || !m || !delta_cur ||
         !accepted)
         return hvi::fail(HV_EINVAL, "bad gpCN acceptance arguments");
-    k_gpcn_accept<<<c, 256, 0, (cudaStream_t)stream>>>(phi_new, m_new, d_new, Hd_new, log_u, m, delta_cur, accepted,
-                                                        (size_t)n);
-    return launched("k_gpcn_accept");
+    cudaStream_t st = (cudaStream_t)stream;
+    double *scratch = nullptr;   // stream-ordered: the dots and their chunk partials
+    const size_t ns = hvk::rows_dot_scratch(c, (size_t)n) + (size_t)c;
+    PCK(cudaMallocAsync(reinterpret_cast<void **>(&scratch), ns * sizeof(double), st));
+    double *dHd = scratch + hvk::rows_dot_scratch(c, (size_t)n);
+    int rc = hvk::rows_dot(d_new, Hd_new, dHd, c, (size_t)n, 1.0, scratch, st);
+    if (rc == HV_OK) {
+        k_gpcn_decide<<<nblk(c, 128), 128, 0, st>>>(phi_new, dHd, log_u, delta_cur, accepted, c);
+        rc = launched("k_gpcn_decide");
+    }
+    if (rc == HV_OK) {
+        k_gpcn_take<<<dim3(nblk(n, 256), c), 256, 0, st>>>(m_new, accepted, m, (size_t)n);
+        rc = launched("k_gpcn_take");
+    }
+    cudaFreeAsync(scratch, st);
+    return rc;
 }

@@ -37,6 +37,7 @@ struct hv_quad {
     hvk::Prior prior;
     float *t1 = nullptr, *t2 = nullptr;   // scratch, tk fields each
     double *c = nullptr;                  // scratch, tk * nlr coefficients
+    double *red = nullptr;                // reduction partials, then 2 tk dot products
     int tk = 0;
     cudaEvent_t done = nullptr;
     std::mutex *mu = nullptr;
@@ -61,37 +62,6 @@ __global__ void k_window(const float *__restrict__ W, const float *v, float *out
     if (t < (size_t)k * N) out[t] = W[t % N] * v[t];
 }
 
-// C[q][j] = lam_j sum_e V[j][e] X[q][e] in FP64; one CTA per (j, q).
-__global__ void k_mode_dots(const float *__restrict__ V, const float *__restrict__ X, const double *__restrict__ lam,
-                            double *__restrict__ C, int nlr, size_t N)
-{
-    const int j = blockIdx.x, q = blockIdx.y;
-    const float *a = V + (size_t)j * N, *b = X + (size_t)q * N;
-    double s = 0.0;
-    for (size_t e = threadIdx.x; e < N; e += blockDim.x) s = fma((double)a[e], (double)b[e], s);
-    __shared__ double sh[256];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) C[(size_t)q * nlr + j] = sh[0] * lam[j];
-}
-
-// out[q][e] += sum_j C[q][j] V[j][e] (FP64 sum over the modes).
-__global__ void k_add_modes(const float *__restrict__ V, const double *__restrict__ C, float *__restrict__ out, int nlr,
-                            int k, size_t N)
-{
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const int q = (int)(t / N);
-    const size_t e = t - (size_t)q * N;
-    double s = 0.0;
-    for (int j = 0; j < nlr; ++j) s = fma(C[(size_t)q * nlr + j], (double)V[(size_t)j * N + e], s);
-    out[t] = (float)((double)out[t] + s);
-}
-
 // e[q] = W m[q] - m*[q]  (mstar broadcast when it holds one field)
 __global__ void k_residual_field(const float *__restrict__ W, const float *__restrict__ m,
                                  const float *__restrict__ mstar, float *__restrict__ e, int k, size_t N,
@@ -103,23 +73,10 @@ __global__ void k_residual_field(const float *__restrict__ W, const float *__res
     e[t] = fmaf(W[i], m[t], -mstar[one_target ? i : t]);
 }
 
-// phi[q] = 1/2 e.He + 1/2 m.Rm in FP64; one CTA per q.
-__global__ void k_phi(const float *__restrict__ e, const float *__restrict__ He, const float *__restrict__ m,
-                      const float *__restrict__ Rm, double *__restrict__ phi, size_t N)
+__global__ void k_add2(const double *__restrict__ a, const double *__restrict__ b, double *__restrict__ out, int k)
 {
-    const int q = blockIdx.x;
-    const size_t o = (size_t)q * N;
-    double s = 0.0;
-    for (size_t i = threadIdx.x; i < N; i += blockDim.x)
-        s = fma((double)e[o + i], (double)He[o + i], fma((double)m[o + i], (double)Rm[o + i], s));
-    __shared__ double sh[256];
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) phi[q] = 0.5 * sh[0];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < k) out[i] = a[i] + b[i];
 }
 
 // grad[q] = W He[q] + Rm[q]
@@ -149,14 +106,17 @@ int grow(hv_quad *q, int k)
     cudaFree(q->t1);   // synchronises: earlier work on the old scratch is done
     cudaFree(q->t2);
     cudaFree(q->c);
+    cudaFree(q->red);
     q->t1 = q->t2 = nullptr;
-    q->c = nullptr;
+    q->c = q->red = nullptr;
     q->tk = 0;
     const size_t N = (size_t)q->nz * q->nx;
+    const size_t nred = std::max(hvk::coef_scratch(std::max(q->nlr, 1), k, N), hvk::rows_dot_scratch(k, N)) + 2 * (size_t)k;
     cudaError_t e;
     if ((e = cudaMalloc(&q->t1, (size_t)k * N * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&q->t2, (size_t)k * N * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&q->c, (size_t)k * std::max(q->nlr, 1) * sizeof(double))) != cudaSuccess)
+        (e = cudaMalloc(&q->c, (size_t)k * std::max(q->nlr, 1) * sizeof(double))) != cudaSuccess ||
+        (e = cudaMalloc(&q->red, nred * sizeof(double))) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "quadratic-model scratch: %s", cudaGetErrorString(e));
     q->tk = k;
     return HV_OK;
@@ -168,11 +128,9 @@ int hd_raw(hv_quad *q, const float *v, int k, float *out, cudaStream_t st)
     const size_t N = (size_t)q->nz * q->nx;
     HV_RT_INTERNAL(hvk::lr_apply(q->lr, v, k, q->t2, st, hvk::kLrTranspose));
     HV_RT_INTERNAL(hvk::lr_apply(q->lr, q->t2, k, out, st, hvk::kLrForward));
-    if (q->nlr > 0) {
-        k_mode_dots<<<dim3(q->nlr, k), 256, 0, st>>>(q->V, v, q->lam, q->c, q->nlr, N);
-        HV_RT_INTERNAL(launched("k_mode_dots"));
-        k_add_modes<<<nblk((size_t)k * N, 256), 256, 0, st>>>(q->V, q->c, out, q->nlr, k, N);
-        HV_RT_INTERNAL(launched("k_add_modes"));
+    if (q->nlr > 0) {   // + V Lambda V^T v
+        HV_RT_INTERNAL(hvk::coef(q->V, q->nlr, v, k, N, q->lam, q->c, q->red, st));
+        HV_RT_INTERNAL(hvk::combine(q->V, q->nlr, q->c, k, N, out, 1.0f, out, st));
     }
     return HV_OK;
 }
@@ -291,6 +249,7 @@ extern "C" int hv_quad_destroy(hv_quad *q)
     cudaFree(q->t1);
     cudaFree(q->t2);
     cudaFree(q->c);
+    cudaFree(q->red);
     if (q->done) cudaEventDestroy(q->done);
     delete q->mu;
     delete q;
@@ -346,8 +305,12 @@ extern "C" int hv_quad_objective(hv_quad *q, const float *m, const float *mstar,
     HV_RT_INTERNAL(launched("k_residual_field"));
     HV_RT_INTERNAL(hd_raw(q, e, k, He, st));
     HV_RT_INTERNAL(hvk::prior_R(q->prior, m, Rm, k, st));
-    k_phi<<<k, 256, 0, st>>>(e, He, m, Rm, phi, N);
-    HV_RT_INTERNAL(launched("k_phi"));
+    // phi = 1/2 e.He + 1/2 m.Rm (FP64)
+    double *s1 = q->red + hvk::rows_dot_scratch(k, N) + 0, *s2 = s1 + k;
+    HV_RT_INTERNAL(hvk::rows_dot(e, He, s1, k, N, 0.5, q->red, st));
+    HV_RT_INTERNAL(hvk::rows_dot(m, Rm, s2, k, N, 0.5, q->red, st));
+    k_add2<<<nblk(k, 128), 128, 0, st>>>(s1, s2, phi, k);
+    HV_RT_INTERNAL(launched("k_add2"));
     if (grad) {
         k_grad<<<nblk((size_t)k * N, 256), 256, 0, st>>>(q->W, He, Rm, grad, k, N);
         HV_RT_INTERNAL(launched("k_grad"));
