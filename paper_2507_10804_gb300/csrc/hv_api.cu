@@ -1508,7 +1508,7 @@ extern "C" int hv_approx_lr_eigs(const hv_approx *a, double *lambda, float *V, v
 extern "C" int hv_prior_apply(int nz, int nx, double h, double delta, double gamma, const float *v, int k, float *out,
                               int op, void *stream)
 {
-    if (!v || !out || k < 1) return hvi::fail(HV_EINVAL, "null field or k < 1");
+    if (!v || !out || k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "null field or k outside [1, 65535]");
     if (op < 0 || op > 3) return hvi::fail(HV_EINVAL, "prior operation %d", op);
     hvk::Prior P;
     cudaStream_t st = (cudaStream_t)stream;

@@ -6,8 +6,9 @@
 // Reductions over the field run in chunks of kChunk points, one CTA per chunk
 // and row, the chunks summed in a fixed order by a second kernel --
 // deterministic, with the whole device busy even for a few long rows (one CTA
-// per row left most SMs idle).  rows_dot sums in FP64 throughout (it decides
-// CG step lengths and gpCN acceptances); coef sums in FP32 inside a chunk and
+// per row left most SMs idle).  rows_dot keeps FP64 accuracy (it decides CG
+// step lengths and gpCN acceptances) with double-float arithmetic on the FP32
+// pipe inside a thread and FP64 above; coef sums in FP32 inside a chunk and
 // FP64 across chunks (r x k dots: FP64 throughout would run at the FP64 rate).
 // The sums over j in combine (at most 256 terms) run in FP32 with the
 // coefficients rounded to FP32.
@@ -52,9 +53,20 @@ __global__ void k_rows_dot_part(const float *__restrict__ A, const float *__rest
     __shared__ double sh[256];
     const int c = blockIdx.x, q = blockIdx.y;
     const size_t o = (size_t)q * N, e0 = (size_t)c * kChunk, e1 = min(N, e0 + kChunk);
-    double s = 0.0;                  // FP64: the products of FP32 values are exact, so is their sum up to rounding
-    for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) s = fma((double)A[o + e], (double)B[o + e], s);
-    const double t = block_sum(s, sh);
+    // Double-float accumulation on the FP32 pipe (the FP64 pipe and its conversions are
+    // slow on this part): each product is split exactly into p + pe (fmaf), the running
+    // sum hi is kept with TwoSum, the rounding errors collect in lo; the thread's
+    // partial hi + lo is then exact to about 2^-44 of the sum of |products|.
+    float hi = 0.0f, lo = 0.0f;
+    for (size_t e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
+        const float a = A[o + e], b = B[o + e];
+        // explicit round-to-nearest intrinsics: no contraction may merge these steps
+        const float p = __fmul_rn(a, b), pe = fmaf(a, b, -p);
+        const float s = __fadd_rn(hi, p), bv = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv)), pe));
+        hi = s;
+    }
+    const double t = block_sum((double)hi + (double)lo, sh);
     if (threadIdx.x == 0) part[(size_t)q * nch + c] = t;
 }
 

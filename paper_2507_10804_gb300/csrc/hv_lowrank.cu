@@ -47,26 +47,26 @@ int blas(cublasStatus_t s, const char *what)
     return HV_OK;
 }
 
-// out = delta v - gamma Lap_h v for k fields [nz][nx] (mirror ghost cells).
+// out = delta v - gamma Lap_h v for k fields [nz][nx] (mirror ghost cells);
+// grid (columns / 128, nz, k).
 template <class T>
 __global__ void k_prior_A(const T *__restrict__ v, T *__restrict__ out, int nz, int nx, int k, T delta, T g_h2)
 {
-    const size_t N = (size_t)nz * nx;
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const size_t base = t - t % N;
-    const int e = (int)(t % N), z = e / nx, x = e - z * nx;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
+    if (x >= nx) return;
+    const size_t base = (size_t)blockIdx.z * nz * nx, t = base + (size_t)z * nx + x;
     const T c = v[t];
     const T n_ = v[base + (size_t)max(z - 1, 0) * nx + x], s_ = v[base + (size_t)min(z + 1, nz - 1) * nx + x];
     const T w_ = v[base + (size_t)z * nx + max(x - 1, 0)], e_ = v[base + (size_t)z * nx + min(x + 1, nx - 1)];
     out[t] = delta * c - g_h2 * (((n_ + s_) + (w_ + e_)) - T(4) * c);
 }
 
+// X[q][e] *= s[e]; grid (points / 256, k).
 template <class T>
 __global__ void k_scale_rows(T *__restrict__ X, const T *__restrict__ s, size_t N, int k)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < (size_t)k * N) X[t] *= s[t % N];
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < N) X[(size_t)blockIdx.y * N + e] *= s[e];
 }
 
 template <class A, class B>
@@ -207,8 +207,8 @@ int gemm_batched(cublasHandle_t hb, cublasOperation_t ta, cublasOperation_t tb, 
 template <class T>
 int prior_A_t(const Prior &P, const T *v, T *out, int k, cudaStream_t st)
 {
-    const size_t N = (size_t)P.nz * P.nx;
-    k_prior_A<T><<<nb((size_t)k * N, 256), 256, 0, st>>>(v, out, P.nz, P.nx, k, (T)P.delta, (T)(P.gamma / (P.h * P.h)));
+    k_prior_A<T><<<dim3(nb((size_t)P.nx, 128), P.nz, k), 128, 0, st>>>(v, out, P.nz, P.nx, k, (T)P.delta,
+                                                                   (T)(P.gamma / (P.h * P.h)));
     return launched("k_prior_A");
 }
 
@@ -225,7 +225,7 @@ int prior_Ainv_t(Prior &P, const T *Cz, const T *Cx, const T *inv, const T *v, T
     HV_RT_INTERNAL(blas(cublasSetStream(P.blas, st), "cublasSetStream"));
     HV_RT_INTERNAL(gemm_batched(P.blas, CUBLAS_OP_T, CUBLAS_OP_N, nx, nz, nx, Cx, nx, 0, v, nx, N, U, nx, N, k));
     HV_RT_INTERNAL(gemm_batched(P.blas, CUBLAS_OP_N, CUBLAS_OP_N, nx, nz, nz, U, nx, N, Cz, nz, 0, Tm, nx, N, k));
-    k_scale_rows<T><<<nb((size_t)k * N, 256), 256, 0, st>>>(Tm, inv, (size_t)N, k);
+    k_scale_rows<T><<<dim3(nb((size_t)N, 256), k), 256, 0, st>>>(Tm, inv, (size_t)N, k);
     HV_RT_INTERNAL(launched("k_scale_rows"));
     HV_RT_INTERNAL(gemm_batched(P.blas, CUBLAS_OP_N, CUBLAS_OP_N, nx, nz, nx, Cx, nx, 0, Tm, nx, N, U, nx, N, k));
     HV_RT_INTERNAL(gemm_batched(P.blas, CUBLAS_OP_N, CUBLAS_OP_T, nx, nz, nz, U, nx, N, Cz, nz, 0, out, nx, N, k));

@@ -97,28 +97,33 @@ __global__ void k_sqrt_real(const float2 *in, float2 *out, size_t n)   // in == 
     if (i < n) out[i] = make_float2(sqrtf(fmaxf(in[i].x, 0.0f)), 0.0f);
 }
 
-// Y[k][q] = b_k V_q / N for the r terms and the kb vectors of a batch (complex products).
+// The elementwise kernels of the apply index points by blockIdx.x (and the
+// vector and term by blockIdx.y / blockIdx.z): no 64-bit division per element.
+
+// Y[k][q] = b_k V_q / N for the r terms and the kb vectors of a batch (complex
+// products); grid (points / 256, kb, r).
 __global__ void k_lr_scale(const float2 *__restrict__ V, const float2 *__restrict__ b, float2 *__restrict__ Y, int r,
                            int kb, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)r * kb * N) return;
-    const size_t e = t % N, kq = t / N;
-    const int k = (int)(kq / kb), q = (int)(kq - (size_t)k * kb);
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int q = blockIdx.y, k = blockIdx.z;
+    const size_t t = ((size_t)k * kb + q) * N + e;
     const float2 v = V[(size_t)q * N + e];
     const float2 w = b[(size_t)k * N + e];
     const float inv = 1.0f / (float)N;
     Y[t] = make_float2(fmaf(w.x, v.x, -w.y * v.y) * inv, fmaf(w.x, v.y, w.y * v.x) * inv);
 }
 
-// out_q = Re sum_k a_k y[k][q], summed in k order, for the nq valid vectors of a batch.
+// out_q = Re sum_k a_k y[k][q], summed in k order, for the nq valid vectors of a
+// batch; grid (points / 256, nq).
 __global__ void k_lr_combine(const float2 *__restrict__ A, const float2 *__restrict__ Y, float *__restrict__ out, int r,
                              int kb, int nq, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)nq * N) return;
-    const size_t e = t % N;
-    const int q = (int)(t / N);
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int q = blockIdx.y;
+    const size_t t = (size_t)q * N + e;
     float s = 0.0f;
     for (int k = 0; k < r; ++k) {
         const float2 a = A[(size_t)k * N + e], y = Y[((size_t)k * kb + q) * N + e];
@@ -127,27 +132,29 @@ __global__ void k_lr_combine(const float2 *__restrict__ A, const float2 *__restr
     out[t] = s;
 }
 
-// Transposed apply, first half: Y[k][q] = conj(a_k) w_q (complex times real).
+// Transposed apply, first half: Y[k][q] = conj(a_k) w_q (complex times real);
+// grid (points / 256, kb, r).
 __global__ void k_lrT_premul(const float *__restrict__ w, const float2 *__restrict__ A, float2 *__restrict__ Y, int r,
                              int kb, int nq, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)r * kb * N) return;
-    const size_t e = t % N, kq = t / N;
-    const int k = (int)(kq / kb), q = (int)(kq - (size_t)k * kb);
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int q = blockIdx.y, k = blockIdx.z;
+    const size_t t = ((size_t)k * kb + q) * N + e;
     const float x = q < nq ? w[(size_t)q * N + e] : 0.0f;
     const float2 a = A[(size_t)k * N + e];
     Y[t] = make_float2(a.x * x, -a.y * x);
 }
 
-// Transposed apply, second half: V_q = (1/N) sum_k conj(b_k) Y[k][q], in k order.
+// Transposed apply, second half: V_q = (1/N) sum_k conj(b_k) Y[k][q], in k
+// order; grid (points / 256, kb).
 __global__ void k_lrT_sum(const float2 *__restrict__ Y, const float2 *__restrict__ b, float2 *__restrict__ V, int r,
                           int kb, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)kb * N) return;
-    const size_t e = t % N;
-    const int q = (int)(t / N);
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const int q = blockIdx.y;
+    const size_t t = (size_t)q * N + e;
     float re = 0.0f, im = 0.0f;
     for (int k = 0; k < r; ++k) {
         const float2 w = b[(size_t)k * N + e], y = Y[((size_t)k * kb + q) * N + e];
@@ -295,11 +302,11 @@ static int lr_batch_forward(LrSym &L, const float *v, int nq, float *out, cudaSt
     HV_RT_INTERNAL(check("k_real_to_complex"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD),
                                "forward FFT"));
-    k_lr_scale<<<blocks_for((size_t)g.r * kb * N, 256), 256, 0, st>>>(L.V, L.b, L.Y, g.r, kb, N);
+    k_lr_scale<<<dim3(blocks_for(N, 256), kb, g.r), 256, 0, st>>>(L.V, L.b, L.Y, g.r, kb, N);
     HV_RT_INTERNAL(check("k_lr_scale"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE),
                                "inverse FFT"));
-    k_lr_combine<<<blocks_for((size_t)nq * N, 256), 256, 0, st>>>(L.a, L.Y, out, g.r, kb, nq, N);
+    k_lr_combine<<<dim3(blocks_for(N, 256), nq), 256, 0, st>>>(L.a, L.Y, out, g.r, kb, nq, N);
     return check("k_lr_combine");
 }
 
@@ -309,11 +316,11 @@ static int lr_batch_transpose(LrSym &L, const float *w, int nq, float *out, cuda
     const LrGeo &g = L.g;
     const size_t N = (size_t)g.nz * g.nx;
     const int kb = L.kb;
-    k_lrT_premul<<<blocks_for((size_t)g.r * kb * N, 256), 256, 0, st>>>(w, L.a, L.Y, g.r, kb, nq, N);
+    k_lrT_premul<<<dim3(blocks_for(N, 256), kb, g.r), 256, 0, st>>>(w, L.a, L.Y, g.r, kb, nq, N);
     HV_RT_INTERNAL(check("k_lrT_premul"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_FORWARD),
                                "forward FFT"));
-    k_lrT_sum<<<blocks_for((size_t)kb * N, 256), 256, 0, st>>>(L.Y, L.b, L.V, g.r, kb, N);
+    k_lrT_sum<<<dim3(blocks_for(N, 256), kb), 256, 0, st>>>(L.Y, L.b, L.V, g.r, kb, N);
     HV_RT_INTERNAL(check("k_lrT_sum"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_INVERSE),
                                "inverse FFT"));

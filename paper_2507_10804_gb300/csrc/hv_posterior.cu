@@ -131,7 +131,7 @@ __global__ void k_axpy(const float *a, const float *__restrict__ b, float s, flo
     if (t < n) out[t] = fmaf(s, b[t], a[t]);
 }
 
-// CG step lengths: alpha[q] = active ? rz[q] / pq[q] : 0.
+// CG step lengths (FP64 quotients, once per vector): alpha[q] = active ? rz[q] / pq[q] : 0.
 __global__ void k_cg_alpha(const double *__restrict__ rz, const double *__restrict__ pq, const int *__restrict__ act,
                            double *__restrict__ alpha, int k)
 {
@@ -139,42 +139,47 @@ __global__ void k_cg_alpha(const double *__restrict__ rz, const double *__restri
     if (q < k) alpha[q] = (act[q] && pq[q] > 0.0) ? rz[q] / pq[q] : 0.0;
 }
 
-// x += alpha p, r -= alpha q (per vector).
+// beta[q] = active ? rz_new[q] / rz[q] : 0, then rz <- rz_new.
+__global__ void k_cg_beta(const double *__restrict__ rz_new, double *__restrict__ rz, const int *__restrict__ act,
+                          double *__restrict__ beta, int k)
+{
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= k) return;
+    beta[q] = (act[q] && rz[q] > 0.0) ? rz_new[q] / rz[q] : 0.0;
+    rz[q] = rz_new[q];
+}
+
+// x += alpha p, r -= alpha q (per vector); grid (points / 256, k).
 __global__ void k_cg_xr(float *__restrict__ x, float *__restrict__ r, const float *__restrict__ p,
                         const float *__restrict__ q, const double *__restrict__ alpha, int k, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const double a = alpha[t / N];
-    x[t] = (float)((double)x[t] + a * (double)p[t]);
-    r[t] = (float)((double)r[t] - a * (double)q[t]);
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const size_t t = (size_t)blockIdx.y * N + e;
+    const float a = (float)alpha[blockIdx.y];   // FP32 updates: the vectors are FP32
+    x[t] = fmaf(a, p[t], x[t]);
+    r[t] = fmaf(-a, q[t], r[t]);
 }
 
-// beta = active ? rz_new / rz : 0; rz <- rz_new; p = z + beta p.
-__global__ void k_cg_p(float *__restrict__ p, const float *__restrict__ z, const double *__restrict__ rz_new,
-                       double *__restrict__ rz, const int *__restrict__ act, int k, size_t N)
+// p = z + beta p (beta from k_cg_beta); grid (points / 256, k).
+__global__ void k_cg_p(float *__restrict__ p, const float *__restrict__ z, const double *__restrict__ beta, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const int q = (int)(t / N);
-    const double b = (act[q] && rz[q] > 0.0) ? rz_new[q] / rz[q] : 0.0;
-    p[t] = (float)((double)z[t] + b * (double)p[t]);
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const size_t t = (size_t)blockIdx.y * N + e;
+    p[t] = fmaf((float)beta[blockIdx.y], p[t], z[t]);
 }
 
-__global__ void k_store_rz(double *__restrict__ rz, const double *__restrict__ rz_new, int k)
-{
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < k) rz[q] = rz_new[q];
-}
-
-// gpCN proposal: m' = map + sqrt(1 - beta^2)(m - map) + beta zeta, d = m' - map.
+// gpCN proposal: m' = map + sqrt(1 - beta^2)(m - map) + beta zeta, d = m' - map;
+// grid (points / 256, c).
 __global__ void k_gpcn_propose(const float *__restrict__ m, const float *__restrict__ map,
                                const float *__restrict__ zeta, float s, float beta, float *__restrict__ mp,
                                float *__restrict__ d, int c, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)c * N) return;
-    const float m0 = map[t % N];
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const size_t t = (size_t)blockIdx.y * N + e;
+    const float m0 = map[e];
     const float dd = fmaf(s, m[t] - m0, beta * zeta[t]);
     mp[t] = m0 + dd;
     if (d) d[t] = dd;
@@ -290,7 +295,7 @@ int pcg(hvk::Prior &P, const OpFn &op, const float *b, int k, float *x, double r
         HV_RT_INTERNAL(hvk::rows_dot(p, q, pq, k, N, 1.0, w.red, st));
         k_cg_alpha<<<nblk(k, 128), 128, 0, st>>>(rz, pq, act, alpha, k);
         HV_RT_INTERNAL(launched("k_cg_alpha"));
-        k_cg_xr<<<nblk(n, 256), 256, 0, st>>>(x, r, p, q, alpha, k, N);
+        k_cg_xr<<<dim3(nblk(N, 256), k), 256, 0, st>>>(x, r, p, q, alpha, k, N);
         HV_RT_INTERNAL(launched("k_cg_xr"));
         HV_RT_INTERNAL(hvk::rows_dot(r, r, rr, k, N, 1.0, w.red, st));
         PCK(cudaMemcpyAsync(rh.data(), rr, k * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -301,10 +306,10 @@ int pcg(hvk::Prior &P, const OpFn &op, const float *b, int k, float *x, double r
         PCK(cudaMemcpyAsync(act, ah.data(), k * sizeof(int), cudaMemcpyHostToDevice, st));
         HV_RT_INTERNAL(hvk::prior_Rinv(P, r, z, k, st));
         HV_RT_INTERNAL(hvk::rows_dot(r, z, rz_new, k, N, 1.0, w.red, st));
-        k_cg_p<<<nblk(n, 256), 256, 0, st>>>(p, z, rz_new, rz, act, k, N);
+        k_cg_beta<<<nblk(k, 128), 128, 0, st>>>(rz_new, rz, act, alpha, k);   // alpha's slot holds beta now
+        HV_RT_INTERNAL(launched("k_cg_beta"));
+        k_cg_p<<<dim3(nblk(N, 256), k), 256, 0, st>>>(p, z, alpha, N);
         HV_RT_INTERNAL(launched("k_cg_p"));
-        k_store_rz<<<nblk(k, 128), 128, 0, st>>>(rz, rz_new, k);
-        HV_RT_INTERNAL(launched("k_store_rz"));
     }
     if (iters) *iters = it;
     return HV_OK;
@@ -583,10 +588,10 @@ extern "C" int hv_posterior_rank(const hv_posterior *p) { return p ? p->r : -1; 
 extern "C" int hv_gpcn_propose(int n, int c, const float *m, const float *m_map, const float *zeta, double beta,
                                float *m_new, float *d_new, void *stream)
 {
-    if (n < 1 || c < 1 || !m || !m_map || !zeta || !m_new) return hvi::fail(HV_EINVAL, "bad gpCN proposal arguments");
+    if (n < 1 || c < 1 || c > 65535 || !m || !m_map || !zeta || !m_new)
+        return hvi::fail(HV_EINVAL, "bad gpCN proposal arguments");
     if (!(beta > 0 && beta < 1)) return hvi::fail(HV_EINVAL, "beta = %g; need 0 < beta < 1", beta);
-    const size_t total = (size_t)c * n;
-    k_gpcn_propose<<<nblk(total, 256), 256, 0, (cudaStream_t)stream>>>(
+    k_gpcn_propose<<<dim3(nblk((size_t)n, 256), c), 256, 0, (cudaStream_t)stream>>>(
         m, m_map, zeta, (float)std::sqrt(1.0 - beta * beta), (float)beta, m_new, d_new, c, (size_t)n);
     return launched("k_gpcn_propose");
 }

@@ -55,11 +55,14 @@ int launched(const char *what)
     return HV_OK;
 }
 
+// Elementwise kernels: grid (points / 256, k), no 64-bit division per element.
 // out[q][e] = W[e] v[q][e]
 __global__ void k_window(const float *__restrict__ W, const float *v, float *out, int k, size_t N)   // out may be v
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < (size_t)k * N) out[t] = W[t % N] * v[t];
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N) return;
+    const size_t t = (size_t)blockIdx.y * N + e;
+    out[t] = W[e] * v[t];
 }
 
 // e[q] = W m[q] - m*[q]  (mstar broadcast when it holds one field)
@@ -67,9 +70,9 @@ __global__ void k_residual_field(const float *__restrict__ W, const float *__res
                                  const float *__restrict__ mstar, float *__restrict__ e, int k, size_t N,
                                  bool one_target)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= (size_t)k * N) return;
-    const size_t i = t % N;
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const size_t t = (size_t)blockIdx.y * N + i;
     e[t] = fmaf(W[i], m[t], -mstar[one_target ? i : t]);
 }
 
@@ -83,8 +86,10 @@ __global__ void k_add2(const double *__restrict__ a, const double *__restrict__ 
 __global__ void k_grad(const float *__restrict__ W, const float *__restrict__ He, const float *__restrict__ Rm,
                        float *__restrict__ g, int k, size_t N)
 {
-    const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < (size_t)k * N) g[t] = fmaf(W[t % N], He[t], Rm[t]);
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    const size_t t = (size_t)blockIdx.y * N + i;
+    g[t] = fmaf(W[i], He[t], Rm[t]);
 }
 
 std::vector<double> taper(int n, int L)
@@ -276,10 +281,10 @@ extern "C" int hv_quad_apply(hv_quad *q, int op, const float *v, int k, float *o
     } else if (op == HV_QUAD_HD_RAW) {
         HV_RT_INTERNAL(hd_raw(q, v, k, out, st));
     } else {   // W (A A^T + V Lambda V^T) W v
-        k_window<<<nblk((size_t)k * N, 256), 256, 0, st>>>(q->W, v, q->t1, k, N);
+        k_window<<<dim3(nblk(N, 256), k), 256, 0, st>>>(q->W, v, q->t1, k, N);
         HV_RT_INTERNAL(launched("k_window"));
         HV_RT_INTERNAL(hd_raw(q, q->t1, k, out, st));
-        k_window<<<nblk((size_t)k * N, 256), 256, 0, st>>>(q->W, out, out, k, N);
+        k_window<<<dim3(nblk(N, 256), k), 256, 0, st>>>(q->W, out, out, k, N);
         HV_RT_INTERNAL(launched("k_window"));
     }
     QCK(cudaEventRecord(q->done, st));
@@ -301,7 +306,7 @@ extern "C" int hv_quad_objective(hv_quad *q, const float *m, const float *mstar,
     // t1: the residual e, then R m; He in a scratch of its own
     HV_RT_INTERNAL(grow(q, 2 * k));
     float *e = q->t1, *Rm = q->t1 + (size_t)k * N, *He = q->t2 + (size_t)k * N;
-    k_residual_field<<<nblk((size_t)k * N, 256), 256, 0, st>>>(q->W, m, mstar, e, k, N, one_target != 0);
+    k_residual_field<<<dim3(nblk(N, 256), k), 256, 0, st>>>(q->W, m, mstar, e, k, N, one_target != 0);
     HV_RT_INTERNAL(launched("k_residual_field"));
     HV_RT_INTERNAL(hd_raw(q, e, k, He, st));
     HV_RT_INTERNAL(hvk::prior_R(q->prior, m, Rm, k, st));
@@ -312,7 +317,7 @@ extern "C" int hv_quad_objective(hv_quad *q, const float *m, const float *mstar,
     k_add2<<<nblk(k, 128), 128, 0, st>>>(s1, s2, phi, k);
     HV_RT_INTERNAL(launched("k_add2"));
     if (grad) {
-        k_grad<<<nblk((size_t)k * N, 256), 256, 0, st>>>(q->W, He, Rm, grad, k, N);
+        k_grad<<<dim3(nblk(N, 256), k), 256, 0, st>>>(q->W, He, Rm, grad, k, N);
         HV_RT_INTERNAL(launched("k_grad"));
     }
     QCK(cudaEventRecord(q->done, st));
