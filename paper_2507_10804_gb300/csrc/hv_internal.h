@@ -169,7 +169,7 @@ struct AdjLaunch {
     const float *r;                // adjoint source data, [k or 1][ns][nt][nr]
     int r_per_vector;              // 1 if r has a vector dimension
     float rscale;                  // multiplies r (h^2 / sigma^2 or h^2)
-    double *img;                   // [G][k][fsize] partial images
+    double *img;                   // [G][k][fsize] partial images, double-float (hi, lo) FP32 pairs
     int n, k, G;
     StepDeps deps;
 };

@@ -37,7 +37,8 @@ __global__ void k_prep(const float *__restrict__ m, const float *__restrict__ v,
             b[(size_t)j * fsize + off] = (float)(2.0 * (double)v[((size_t)j * nz + iz) * nx + ix] / mm);
 }
 
-// Hv[j][iz][ix] = (2 / (m h^2)) sum over the E-preimage of (iz, ix) of sum_g img[g][j].
+// Hv[j][iz][ix] = (2 / (m h^2)) sum over the E-preimage of (iz, ix) of sum_g img[g][j],
+// the partial images held as double-float pairs (hi, lo), summed in FP64.
 __global__ void k_finalize(const float *__restrict__ m, const double *__restrict__ img, int G, int k, int nz, int nx,
                            int nb, int NZ, int NX, int P, size_t fsize, double h, float *out32, double *out64)
 {
@@ -51,7 +52,10 @@ __global__ void k_finalize(const float *__restrict__ m, const double *__restrict
     for (int z = zlo; z <= zhi; ++z)
         for (int x = xlo; x <= xhi; ++x) {
             const size_t off = (size_t)(z + GH) * P + (x + GH);
-            for (int g = 0; g < G; ++g) acc += img[((size_t)g * k + j) * fsize + off];
+            for (int g = 0; g < G; ++g) {
+                const float2 v = reinterpret_cast<const float2 *>(img)[((size_t)g * k + j) * fsize + off];
+                acc += (double)v.x + (double)v.y;
+            }
         }
     const double mm = (double)m[(size_t)iz * nx + ix];
     const double val = 2.0 / (mm * h * h) * acc;

@@ -8,7 +8,7 @@
 //   (1 + a) du^{n+1}  = 2 du^n - (1 - a) du^{n-1} + C (Lh du^n + b Q^n),  b = 2 dm / m
 //   (1 + a) lam^n     = 2 lam^{n+1} - (1 - a) lam^{n+2} + C (Lh lam^{n+1} + h^2 g^n)
 //   image            += lam^n Q^n,  Q^n = Lh u^n + s_n delta_src
-//                       (per step: FP32 over <= 8 shots, then added to an FP64 image)
+//                       (per step: FP32 over <= 8 shots, then added to a double-float image)
 // The Born source and the image use (T u)^n = m^2 (L u^n + f^n), the exact
 // identity of the forward rows, so no FP32 step forms u^{n+1} - 2u^n + u^{n-1}.
 //
@@ -748,7 +748,7 @@ struct AdjParams {
     const float *r;
     unsigned long long r_vstride;
     float rscale;
-    double *img;
+    double *img;    // [G][k][fsize] double-float (hi, lo) pairs, 8 bytes per point
     const float *az, *ax, *wavelet;
     const int *src_zx, *rt_off, *rt_rec, *rt_pos;
     int *status;
@@ -768,7 +768,7 @@ struct AdjSmem {
 
 // One adjoint time step with zero-lag imaging.  grid = (ntiles, k, blocks of
 // GPC shot groups); for each group of 8 shots the CTA sums the shots' image
-// contributions in shot order and adds them to the group's FP64 partial image
+// contributions in shot order and adds them to the group's double-float partial image
 // once per step.
 template <class C>
 __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjParams p)
@@ -817,7 +817,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     }
     allow_dependent_launch();
     // This step's image contribution of the CTA's shots, summed in shot order
-    // in FP32 (at most 8 terms); it is added to the FP64 image once per step.
+    // in FP32 (at most 8 terms); it is added to the double-float image once per step.
     // Double-precision arithmetic is slow on this part, so none runs per shot.
     float2 acc[C::RZ][2];
 #pragma unroll
@@ -825,17 +825,42 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
 #pragma unroll
         for (int h = 0; h < 2; ++h) acc[r][h] = make_float2(0.0f, 0.0f);
 
-    // Adds the FP32 partial of a finished group of shots to that group's FP64 image.
+    // Adds the FP32 partial of a finished group of shots to that group's image.
+    // The image is held as double-float pairs (hi, lo) and added to by TwoSum on
+    // the FP32 pipe -- about 2^-44 relative accuracy, where FP64 arithmetic (and
+    // its conversions) would run on this part's slow FP64 pipe; k_finalize sums
+    // the pairs in FP64.
+    auto add_df = [](float2 &v, float a) {
+        const float s = __fadd_rn(v.x, a), bv = __fsub_rn(s, v.x);
+        v.y = __fadd_rn(v.y, __fadd_rn(__fsub_rn(v.x, __fsub_rn(s, bv)), __fsub_rn(a, bv)));
+        v.x = s;
+    };
     auto flush = [&](int group) {
-        double *im = p.img + ((size_t)group * p.k + j) * p.g.fsize;
+        float2 *im = reinterpret_cast<float2 *>(p.img) + ((size_t)group * p.k + j) * p.g.fsize;
 #pragma unroll
         for (int r = 0; r < C::RZ; ++r) {
             const int z = zrow0 + r;
             if (z < p.g.NZ && xb < p.g.NX) {
-                const size_t off = (size_t)(z + GH) * p.g.P + (xb + GH);
+                const size_t off = (size_t)(z + GH) * p.g.P + (xb + GH);   // a multiple of 4 pairs: 32-byte aligned
+                const float a4[4] = {acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y};
+                if (xb + 3 < p.g.NX) {
+                    float4 *q4 = reinterpret_cast<float4 *>(im + off);
+                    const float4 w0 = q4[0], w1 = q4[1];
+                    float2 v[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
+                                   make_float2(w1.z, w1.w)};
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (xb + c < p.g.NX) im[off + c] += (double)((c & 1) ? acc[r][c >> 1].y : acc[r][c >> 1].x);
+                    for (int c = 0; c < 4; ++c) add_df(v[c], a4[c]);
+                    q4[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+                    q4[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (xb + c < p.g.NX) {
+                            float2 v = im[off + c];
+                            add_df(v, a4[c]);
+                            im[off + c] = v;
+                        }
+                }
             }
 #pragma unroll
             for (int h = 0; h < 2; ++h) acc[r][h] = make_float2(0.0f, 0.0f);
@@ -1070,7 +1095,7 @@ hvi::Tiling tiling(const hv_handle *h, int cfg)
 
 // Shot groups of the adjoint kernel: G = ceil(ns / 8) groups of ceil(ns / G)
 // consecutive shots, each summed in FP32 in shot order per step and added to
-// its own FP64 partial image; the partials are summed in group order at the
+// its own double-float partial image; the partials are summed in group order at the
 // end.  The grouping depends only on the shot count (never on k, the tile
 // shape or how many groups a CTA walks), so a vector's result is bitwise the
 // same whether it is applied alone or in a batch.
