@@ -308,17 +308,19 @@ def csrc_hash() -> str:
 
 
 def dram_traffic() -> dict:
-    """ncu DRAM bytes (read + write) per launch, per kernel kind, from profiles/dram_traffic.txt.
+    """ncu DRAM bytes (read + write) per launch from profiles/dram_traffic.txt.
 
-    Each line: <kind> <hash of the kernel sources they were taken on> <bytes>; '#' starts a comment.
+    Each line: <workload>:<kind> <hash of the kernel sources they were taken on> <bytes> <tile ids>;
+    '#' starts a comment.  Returns {(workload, kind): (hash, bytes, [tile ids])}.
     """
     out = {}
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as f:
             for ln in f:
                 ln = ln.split("#", 1)[0].split()
-                if len(ln) == 3:
-                    out[ln[0]] = (ln[1], int(ln[2]))
+                if len(ln) == 4 and ":" in ln[0]:
+                    wl, kind = ln[0].split(":", 1)
+                    out[(wl, kind)] = (ln[1], int(ln[2]), [int(t) for t in ln[3].split(",")])
     except OSError:
         pass
     return out
@@ -616,8 +618,9 @@ def run_ours(args, w):
         n_dom, t_dom = prof[dom]
         achieved = alg[dom] * steps_of.get(dom, n_dom) / (t_dom / 1e3) / 1e9
         traffic = None
-        ent = dram_traffic().get(dom)
-        if ent and ent[0] == csrc_hash():
+        # counters recorded for this workload, these kernel sources and these tiles (full-size launches)
+        ent = dram_traffic().get((args.workload, dom))
+        if ent and ent[0] == csrc_hash() and ent[2] == list(tiles) and args.nt is None and args.shots is None:
             traffic = ent[1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
