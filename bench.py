@@ -620,7 +620,8 @@ def run_ours(args, w):
         traffic = None
         # counters recorded for this workload, these kernel sources and these tiles (full-size launches)
         ent = dram_traffic().get((args.workload, dom))
-        if ent and ent[0] == csrc_hash() and ent[2] == list(tiles) and args.nt is None and args.shots is None:
+        ti = {"fwd": 0, "advance": 1, "adj": 2}[dom]          # the dominant kernel's own tile configuration
+        if ent and ent[0] == csrc_hash() and ent[2][ti] == list(tiles)[ti] and args.nt is None and args.shots is None:
             traffic = ent[1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
