@@ -587,6 +587,21 @@ int hv_set_graphs(hv_handle *h, int enable);
  * the traffic saved: a fused launch takes about 120 us where two single steps
  * take 94 us on the 384 x 1152, 32-shot grid. */
 int hv_set_step_fusion(hv_handle *h, int enable);
+/* Shared-memory-resident H v.  With resident enabled, hv_hessian_apply with
+ * every forward level stored (HV_CKPT_ALL, or a budget >= nt - 1) runs, on
+ * grids whose padded field fits twice in one CTA's shared memory (NX a multiple
+ * of 4; hv_resident_fits), three persistent kernels instead of one launch per
+ * time step: the forward field of each shot (writing Q^n = Lh u^n + s_n for
+ * every step), then the Born field of each (shot, vector) pair, then its
+ * adjoint field, each held in shared memory for all nt steps.  Q^n, the Born
+ * data and the adjoint fields are bitwise those of the tiled kernels; the image
+ * is accumulated per pair over all steps in double-float arithmetic and summed
+ * over shots in FP64, an order different from the tiled path's shot-group sums,
+ * so results agree with it to rounding (about 1e-7 relative), not bitwise, and
+ * are bitwise the same for any k and with or without graphs.  The workspace
+ * size (hv_workspace_size) depends on the setting.  Off by default. */
+int hv_set_resident(hv_handle *h, int enable);
+int hv_resident_fits(const hv_handle *h);
 
 #define HV_LAUNCH_PLAIN 0
 #define HV_LAUNCH_PDL 1

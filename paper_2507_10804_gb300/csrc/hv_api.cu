@@ -93,6 +93,7 @@ const hvi::RecTiles &rectiles_for(const hv_handle *h, const hvi::Tiling &t)
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
     bool history = false;     // keep every time level instead of snapshots
+    bool resident = false;    // H v on the shared-memory-resident kernels (history of Q^n, per-pair images)
     int slots = 0;            // snapshot pairs per shot (binomial mode)
     int G = 1;                // adjoint shot groups (partial images)
     size_t fb = 0;            // bytes of one field batch (all shots)
@@ -138,7 +139,8 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
     const size_t ndata = (size_t)h->ns * h->nt * h->nr;
     if (op == HV_OP_HV) L.dd = take((size_t)k * ndata * sizeof(float));
     if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.dd = take(ndata * sizeof(float));
-    if (adjoint) L.img = take((size_t)L.G * k * h->fsize * sizeof(double));
+    L.resident = op == HV_OP_HV && L.history && h->resident && hvk::resident_fits(h);
+    if (adjoint) L.img = take((size_t)(L.resident ? h->ns : L.G) * k * h->fsize * sizeof(double));
     if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.part = take(kResidualBlocks * sizeof(double));
     L.cnt_bytes = (size_t)hvk::adj_groups(h) * hvk::max_tiles(h) * sizeof(int);
     L.cnt = take(L.cnt_bytes);
@@ -424,12 +426,13 @@ const std::vector<hvi::Action> *schedule_for(hv_handle *h, int slots)
 
 int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
                      const Layout &L, cudaStream_t st);
+int run_resident_hv(hv_handle *h, int kk, void *ws, const Layout &L, cudaStream_t st);
 
-std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode, bool fuse)
+std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode, bool fuse, bool res)
 {
-    char buf[160];
-    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d/%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode,
-             (int)fuse);
+    char buf[176];
+    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d/%d/%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode,
+             (int)fuse, (int)res);
     return buf;
 }
 
@@ -455,7 +458,7 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     // CUDA graph and replayed (hv_set_graphs).
     const bool graph = born && h->graphs_on && !h->prof_on;
     if (graph) {
-        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode, h->fuse_steps);
+        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode, h->fuse_steps, L.resident);
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaStream_t cs = h->capture_stream;
@@ -480,9 +483,37 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     }
     {
         ProfScope ps(h, st, HV_K_OTHER);
-        HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>((char *)ws + L.img), L.G, kk, out32, out64, st));
+        HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>((char *)ws + L.img), L.resident ? h->ns : L.G, kk,
+                                   out32, out64, st));
     }
     return HV_OK;
+}
+
+// H v with every level stored on the shared-memory-resident kernels: the
+// forward fields write Q^n into the history region, the Born fields of every
+// (shot, vector) pair write the Born data, and the adjoint fields of every pair
+// write the pair's image; the fold sums the pairs' images over shots.
+int run_resident_hv(hv_handle *h, int kk, void *ws, const Layout &L, cudaStream_t st)
+{
+    const hvi::RecTiles &rt = rectiles_for(h, hvk::tiling(h, h->cfg[2]));
+    hvk::ResLaunch a{};
+    a.base = ws;
+    a.C = reinterpret_cast<const float *>((char *)ws + L.C);
+    a.b = reinterpret_cast<const float *>((char *)ws + L.b);
+    a.q = reinterpret_cast<float *>((char *)ws + L.store);
+    a.dd = reinterpret_cast<float *>((char *)ws + L.dd);
+    a.rscale = (float)(h->h * h->h / (h->sigma * h->sigma));
+    a.img = (char *)ws + L.img;
+    a.rec = rt.rec;
+    a.pos = rt.pos;
+    a.k = kk;
+    {
+        ProfScope ps(h, st, HV_K_FWD);
+        HV_RT(hvk::launch_resident(h, 0, a, st));
+        HV_RT(hvk::launch_resident(h, 1, a, st));
+    }
+    ProfScope ps(h, st, HV_K_ADJ);
+    return hvk::launch_resident(h, 2, a, st);
 }
 
 // The part of run_adjoint between preparation and fold (all on `st`).
@@ -490,6 +521,7 @@ int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *ph
                      const Layout &L, cudaStream_t st)
 {
     (void)ckpt;
+    if (L.resident) return run_resident_hv(h, kk, ws, L, st);
     Exec E;
     HV_RT(E.init(h, st, L, ws, kk));
     const bool born = (kind == 2);
@@ -1035,6 +1067,18 @@ extern "C" int hv_set_graphs(hv_handle *h, int enable)
     if (!h) return hvi::fail(HV_EINVAL, "null handle");
     h->graphs_on = enable != 0;
     return HV_OK;
+}
+
+extern "C" int hv_set_resident(hv_handle *h, int enable)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    h->resident = enable != 0;
+    return HV_OK;
+}
+
+extern "C" int hv_resident_fits(const hv_handle *h)
+{
+    return h && hvk::resident_fits(h) ? 1 : 0;
 }
 
 extern "C" int hv_set_step_fusion(hv_handle *h, int enable)

@@ -94,6 +94,8 @@ struct hv_handle {
     int launch_mode = HV_LAUNCH_PDL;
     // recomputation runs two steps per launch where it can (hv_set_step_fusion)
     bool fuse_steps = false;
+    // H v with every level stored on the shared-memory-resident kernels (hv_set_resident)
+    bool resident = false;
     std::map<std::string, cudaGraphExec_t> graphs;
     // profiling (hv_profile)
     bool prof_on = false;
@@ -176,6 +178,24 @@ struct AdjLaunch {
 int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
                cudaStream_t st);
 int adj_groups(const hv_handle *h);
+
+// Shared-memory-resident H v kernels (every forward level stored, grids whose
+// padded field fits twice in a CTA's shared memory): which = 0 the forward
+// fields of all shots (writes Q^n = Lh u^n + s_n into the history), 1 the Born
+// fields of all (shot, vector) pairs (writes the Born data), 2 the adjoint
+// fields and per-pair images.
+struct ResLaunch {
+    void *base;                    // workspace base (field 0)
+    const float *C, *b;            // C, b [k]
+    float *q;                      // Q history: nt batches of ns fields
+    float *dd;                     // Born data [k][ns][nt][nr]
+    float rscale;                  // adjoint source scale
+    void *img;                     // per-pair images [ns][k][fsize] double-float pairs
+    const int *rec, *pos;          // receivers of each shot ([ns][nr], any order)
+    int k;
+};
+bool resident_fits(const hv_handle *h);
+int launch_resident(const hv_handle *h, int which, const ResLaunch &a, cudaStream_t st);
 
 int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float *C, float *b, cudaStream_t st);
 

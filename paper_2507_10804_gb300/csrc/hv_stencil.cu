@@ -937,6 +937,354 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     else run(std::false_type{});
 }
 
+// ------------------------------------------------------------------ resident kernels
+// For grids whose padded field fits twice in one CTA's shared memory, H v with
+// every forward level stored runs three persistent kernels instead of one
+// launch per step: the forward field of each shot, and the Born field and the
+// adjoint field of each (shot, vector) pair, stay in shared memory for all nt
+// steps (zero initial and final conditions), so their only DRAM traffic is the
+// per-step Q^n = Lh u^n + s_n (written once per shot, read by every pair), the
+// coefficient fields and the receiver data.  Each thread owns blocks of 4 x 2
+// points in a fixed order and computes them with the tiled kernels' exact
+// arithmetic (lap_at, leapfrog, the Born source), so Q, the Born data and the
+// adjoint fields are bitwise those of the tiled path; the image is accumulated
+// per pair over all steps in double-float registers (each product split exactly)
+// and the pairs' images are summed over shots in FP64 by the fold, an order
+// that differs from the tiled path's per-step shot-group sums.
+constexpr int kResNT = 512;      // threads per resident CTA
+constexpr int kResRZ = 2;        // rows per thread block
+constexpr int kResMaxB = 4;      // blocks per thread, upper bound
+constexpr int kSmemCapResident = 227 * 1024;
+
+struct ResParams {
+    float *ws;                   // workspace base (field 0)
+    int f_C, f_b, f_q;           // C, b [k], Q history: Q^n of shot s in field f_q + n ns + s
+    float *dd;                   // Born data [k][ns][nt][nr]: written by the Born kernel, read by the adjoint
+    float rscale;                // the adjoint source scale
+    float2 *img;                 // per-pair images [ns][k][fsize], double-float (hi, lo)
+    const float *az, *ax, *wavelet;
+    const int *src_zx, *rt_rec, *rt_pos;
+    int nt, nr, ns, k;
+    int NZ, NX, P, W, nbx, nblocks;   // padded grid, global pitch, shared pitch NX + 8, blocks of 4 x 2
+    unsigned long long fsize;
+};
+
+__device__ __forceinline__ void res_add_source(float2 (&Q)[kResRZ][2], int z0, int xb, int sz, int sx, float wav)
+{
+    const int dz = sz - z0, dx = sx - xb;
+    if ((unsigned)dz < (unsigned)kResRZ && (unsigned)dx < 4u) {
+#pragma unroll
+        for (int r = 0; r < kResRZ; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (r == dz && c == dx) {
+                    if (c & 1) Q[r][c >> 1].y += wav;
+                    else Q[r][c >> 1].x += wav;
+                }
+    }
+}
+
+__device__ __forceinline__ size_t res_goff(const ResParams &p, int z, int xb)
+{
+    return (size_t)(z + GH) * p.P + (xb + GH);
+}
+
+// Shared memory of the resident kernels (floats): two fields [NZ + 9][W] (the
+// padded field with its 4-cell ghost band and one spare row), then dense
+// [NZ][NX] copies of the pointwise coefficients the kernel needs (C, and b or
+// the image's low words), the damping profiles az [NZ] and ax [NX], and the
+// adjoint's receiver tables.  Everything a step reads besides Q^n is on chip.
+struct ResSmem {
+    float *F0, *F1, *C, *X, *az, *ax, *iz, *ix;   // iz, ix: 1 / (1 + az), 1 / (1 + ax), correctly rounded
+    int *tab;
+};
+__device__ __forceinline__ ResSmem res_smem(const ResParams &p, float *base, bool second_dense)
+{
+    const int rowsW = (p.NZ + 2 * GH + 1) * p.W, N = p.NZ * p.NX;
+    ResSmem m;
+    m.F0 = base;
+    m.F1 = base + rowsW;
+    m.C = base + 2 * rowsW;
+    m.X = m.C + N;
+    m.az = m.X + (second_dense ? N : 0);
+    m.ax = m.az + p.NZ;
+    m.iz = m.ax + p.NX;
+    m.ix = m.iz + p.NZ;
+    m.tab = reinterpret_cast<int *>(m.ix + p.NX);
+    return m;
+}
+
+// Zero both fields, stage C (and `extra`, a [fsize] field, or zeros) densely, and the damping profiles.
+__device__ __forceinline__ void res_setup(const ResParams &p, const ResSmem &m, const float *extra, bool second_dense)
+{
+    const int rowsW = (p.NZ + 2 * GH + 1) * p.W;
+    for (int q = threadIdx.x; q < 2 * rowsW; q += kResNT) m.F0[q] = 0.0f;
+    const float *C = p.ws + (unsigned long long)p.f_C * p.fsize;
+    for (int q = threadIdx.x; q < p.NZ * p.NX; q += kResNT) {
+        const int z = q / p.NX, x = q - z * p.NX;
+        const size_t go = (size_t)(z + GH) * p.P + (x + GH);
+        m.C[q] = C[go];
+        if (second_dense) m.X[q] = extra ? extra[go] : 0.0f;
+    }
+    for (int q = threadIdx.x; q < p.NZ; q += kResNT) {
+        m.az[q] = p.az[q];
+        m.iz[q] = __frcp_rn(1.0f + p.az[q]);
+    }
+    for (int q = threadIdx.x; q < p.NX; q += kResNT) {
+        m.ax[q] = p.ax[q];
+        m.ix[q] = __frcp_rn(1.0f + p.ax[q]);
+    }
+}
+
+// The sponge factors of sponge_row from per-row and per-column tables: rounding
+// is monotone, so 1 / (1 + max(az, ax)) rounded equals min(1 / (1 + az),
+// 1 / (1 + ax)) rounded, and max(az, ax) - 1 equals max(az - 1, ax - 1):
+// bitwise the values sponge_row computes, without a division per point.
+__device__ __forceinline__ void res_sponge_row(const ResSmem &m, int z, int xb, float2 (&inv)[2], float2 (&nom)[2])
+{
+    const float azv = m.az[z], izv = m.iz[z];
+    float iv[4], nm[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        iv[c] = fminf(izv, m.ix[xb + c]);
+        nm[c] = fmaxf(azv, m.ax[xb + c]) - 1.0f;
+    }
+    inv[0] = make_float2(iv[0], iv[1]);
+    inv[1] = make_float2(iv[2], iv[3]);
+    nom[0] = make_float2(nm[0], nm[1]);
+    nom[1] = make_float2(nm[2], nm[3]);
+}
+
+__device__ __forceinline__ void res_block(const ResParams &p, int b, int &z0, int &xb, int &bx)
+{
+    const int bz = b / p.nbx;
+    bx = b - bz * p.nbx;
+    z0 = bz * kResRZ;
+    xb = 4 * bx;
+}
+
+// The forward field of shot blockIdx.x: writes Q^n for n = 0 .. nt-1.
+__global__ void __launch_bounds__(kResNT, 1) k_res_fwd(const __grid_constant__ ResParams p)
+{
+    extern __shared__ __align__(128) float rsm[];
+    const ResSmem m = res_smem(p, rsm, false);
+    res_setup(p, m, nullptr, false);
+    const int s = blockIdx.x, sz = p.src_zx[2 * s], sx = p.src_zx[2 * s + 1];
+    __syncthreads();
+    for (int n = 0; n < p.nt; ++n) {
+        const float *cur = (n & 1) ? m.F0 : m.F1;      // u^n
+        float *prv = (n & 1) ? m.F1 : m.F0;            // u^{n-1}, overwritten by u^{n+1}
+        const float wav = p.wavelet[n];
+        float *qg = p.ws + (unsigned long long)(p.f_q + (long long)n * p.ns + s) * p.fsize;
+        for (int b = threadIdx.x; b < p.nblocks; b += kResNT) {
+            int z0, xb, bx;
+            res_block(p, b, z0, xb, bx);
+            float2 Q[kResRZ][2], uc[kResRZ][2];
+            lap_at<kResRZ>(cur, p.W / 4, z0, bx + 1, Q, uc);
+            res_add_source(Q, z0, xb, sz, sx, wav);
+#pragma unroll
+            for (int r = 0; r < kResRZ; ++r) {
+                const int z = z0 + r;
+                if (z >= p.NZ) continue;
+                *reinterpret_cast<float4 *>(qg + res_goff(p, z, xb)) =
+                    make_float4(Q[r][0].x, Q[r][0].y, Q[r][1].x, Q[r][1].y);
+                float2 up[2], cc[2], inv[2], nom[2], o[2];
+                float *sp = prv + (z + GH) * p.W + xb + GH;
+                f4(sp, up);
+                f4(m.C + z * p.NX + xb, cc);
+                res_sponge_row(m, z, xb, inv, nom);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) o[h] = leapfrog<true>(uc[r][h], up[h], cc[h], Q[r][h], inv[h], nom[h]);
+                *reinterpret_cast<float4 *>(sp) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// Q^n at the thread's blocks, issued before the step's Laplacians so that the
+// global loads overlap them.
+template <int MAXB>
+__device__ __forceinline__ void res_load_q(const ResParams &p, const float *qg, float4 (&qv)[MAXB][kResRZ])
+{
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i) {
+        const int b = threadIdx.x + i * kResNT;
+        if (b >= p.nblocks) break;
+        int z0, xb, bx;
+        res_block(p, b, z0, xb, bx);
+#pragma unroll
+        for (int r = 0; r < kResRZ; ++r)
+            qv[i][r] = z0 + r < p.NZ ? __ldg(reinterpret_cast<const float4 *>(qg + res_goff(p, z0 + r, xb)))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// The Born field of pair (shot blockIdx.x, vector blockIdx.y): writes the Born data.
+template <int MAXB>
+__global__ void __launch_bounds__(kResNT, 1) k_res_born(const __grid_constant__ ResParams p)
+{
+    extern __shared__ __align__(128) float rsm[];
+    const ResSmem m = res_smem(p, rsm, true);
+    const int s = blockIdx.x, j = blockIdx.y;
+    res_setup(p, m, p.ws + (unsigned long long)(p.f_b + j) * p.fsize, true);   // X = b_j
+    float *dd = p.dd + ((size_t)j * p.ns + s) * p.nt * p.nr;
+    __syncthreads();
+    for (int n = 0; n < p.nt; ++n) {
+        const float *cur = (n & 1) ? m.F0 : m.F1;      // du^n
+        float *prv = (n & 1) ? m.F1 : m.F0;            // du^{n-1}, overwritten by du^{n+1}
+        float4 qv[MAXB][kResRZ];
+        res_load_q<MAXB>(p, p.ws + (unsigned long long)(p.f_q + (long long)n * p.ns + s) * p.fsize, qv);
+#pragma unroll
+        for (int i = 0; i < MAXB; ++i) {
+            const int b = threadIdx.x + i * kResNT;
+            if (b >= p.nblocks) break;
+            int z0, xb, bx;
+            res_block(p, b, z0, xb, bx);
+            float2 Ld[kResRZ][2], dc[kResRZ][2];
+            lap_at<kResRZ>(cur, p.W / 4, z0, bx + 1, Ld, dc);
+#pragma unroll
+            for (int r = 0; r < kResRZ; ++r) {
+                const int z = z0 + r;
+                if (z >= p.NZ) continue;
+                float2 dp[2], cc[2], bb[2], inv[2], nom[2], o[2];
+                const float2 Q[2] = {lo(qv[i][r]), hi(qv[i][r])};
+                float *sp = prv + (z + GH) * p.W + xb + GH;
+                f4(sp, dp);
+                f4(m.C + z * p.NX + xb, cc);
+                f4(m.X + z * p.NX + xb, bb);
+                res_sponge_row(m, z, xb, inv, nom);
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+                    o[h] = leapfrog<true>(dc[r][h], dp[h], cc[h], f2fma(bb[h], Q[h], Ld[r][h]), inv[h], nom[h]);
+                *reinterpret_cast<float4 *>(sp) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+            }
+        }
+        __syncthreads();
+        for (int q = threadIdx.x; q < p.nr; q += kResNT) {   // du^{n+1} at the receivers
+            const int pos = p.rt_pos[s * p.nr + q];
+            const int z = pos / p.P - GH, x = pos - (pos / p.P) * p.P - GH;
+            dd[(size_t)n * p.nr + p.rt_rec[s * p.nr + q]] = prv[(z + GH) * p.W + x + GH];
+        }
+    }
+}
+
+// The adjoint field of pair (shot blockIdx.x, vector blockIdx.y) and its image:
+// the image's high words in registers, its low words in shared memory (X).
+template <int MAXB>
+__global__ void __launch_bounds__(kResNT, 1) k_res_adj(const __grid_constant__ ResParams p)
+{
+    extern __shared__ __align__(128) float rsm[];
+    const ResSmem m = res_smem(p, rsm, true);
+    res_setup(p, m, nullptr, true);                   // X = 0: the image's low words
+    int *cnt = m.tab;                                 // [nblocks + 1]: receivers per block, then starts
+    int *fill = cnt + p.nblocks + 1;                  // [nblocks]
+    int *ent = fill + p.nblocks;                      // [nr]: (lane << 16) | receiver slot q
+    for (int q = threadIdx.x; q <= p.nblocks; q += kResNT) cnt[q] = 0;
+    for (int q = threadIdx.x; q < p.nblocks; q += kResNT) fill[q] = 0;
+    const int s = blockIdx.x, j = blockIdx.y;
+    __syncthreads();
+    // receivers of the shot by thread block (a block holds at most one receiver per point)
+    auto rec_block = [&](int q, int &lane) {
+        const int pos = p.rt_pos[s * p.nr + q];
+        const int z = pos / p.P - GH, x = pos - (pos / p.P) * p.P - GH;
+        lane = (z % kResRZ) * 4 + (x & 3);
+        return (z / kResRZ) * p.nbx + (x >> 2);
+    };
+    for (int q = threadIdx.x; q < p.nr; q += kResNT) {
+        int lane;
+        atomicAdd(&cnt[rec_block(q, lane) + 1], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int b = 0; b < p.nblocks; ++b) cnt[b + 1] += cnt[b];
+    __syncthreads();
+    for (int q = threadIdx.x; q < p.nr; q += kResNT) {
+        int lane;
+        const int b = rec_block(q, lane);
+        ent[cnt[b] + atomicAdd(&fill[b], 1)] = (lane << 16) | q;
+    }
+    const float *rs0 = p.dd + ((size_t)j * p.ns + s) * p.nt * p.nr;
+    float4 hi4[MAXB][kResRZ];
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i)
+#pragma unroll
+        for (int r = 0; r < kResRZ; ++r) hi4[i][r] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    // (h, l) += a exactly-split product: TwoSum of the rounded product, its rounding error to l
+    auto acc = [](float &h_, float &l_, float o, float q) {
+        const float pr = __fmul_rn(o, q), pe = fmaf(o, q, -pr);
+        const float t = __fadd_rn(h_, pr), bv = __fsub_rn(t, h_);
+        l_ = __fadd_rn(l_, __fadd_rn(__fadd_rn(__fsub_rn(h_, __fsub_rn(t, bv)), __fsub_rn(pr, bv)), pe));
+        h_ = t;
+    };
+    for (int mstep = 0; mstep < p.nt; ++mstep) {
+        const int n = p.nt - 1 - mstep;
+        const float *cur = (mstep & 1) ? m.F0 : m.F1;   // lambda^{n+1}
+        float *prv = (mstep & 1) ? m.F1 : m.F0;         // lambda^{n+2}, overwritten by lambda^n
+        const float *rs = rs0 + (size_t)n * p.nr;
+        float4 qv[MAXB][kResRZ];
+        res_load_q<MAXB>(p, p.ws + (unsigned long long)(p.f_q + (long long)n * p.ns + s) * p.fsize, qv);
+#pragma unroll
+        for (int i = 0; i < MAXB; ++i) {
+            const int b = threadIdx.x + i * kResNT;
+            if (b >= p.nblocks) break;
+            int z0, xb, bx;
+            res_block(p, b, z0, xb, bx);
+            float2 Ll[kResRZ][2], lc[kResRZ][2];
+            lap_at<kResRZ>(cur, p.W / 4, z0, bx + 1, Ll, lc);
+            for (int e = cnt[b]; e < cnt[b + 1]; ++e) {          // receiver sources: added to Lh lambda
+                const int lane = ent[e] >> 16, q = ent[e] & 0xffff;
+                const float v = p.rscale * rs[p.rt_rec[s * p.nr + q]];
+                float2 &t = Ll[lane >> 2][(lane & 3) >> 1];
+                if (lane & 1) t.y = __fadd_rn(t.y, v);
+                else t.x = __fadd_rn(t.x, v);
+            }
+#pragma unroll
+            for (int r = 0; r < kResRZ; ++r) {
+                const int z = z0 + r;
+                if (z >= p.NZ) continue;
+                float2 l2[2], cc[2], inv[2], nom[2], o[2];
+                float *sp = prv + (z + GH) * p.W + xb + GH;
+                f4(sp, l2);
+                f4(m.C + z * p.NX + xb, cc);
+                res_sponge_row(m, z, xb, inv, nom);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) o[h] = leapfrog<true>(lc[r][h], l2[h], cc[h], Ll[r][h], inv[h], nom[h]);
+                *reinterpret_cast<float4 *>(sp) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
+                // image += lambda^n Q^n (double-float: high words here, low words in shared memory)
+                float4 *lw = reinterpret_cast<float4 *>(m.X + z * p.NX + xb);
+                float4 l4 = *lw;
+                float4 &h4 = hi4[i][r];
+                const float4 q4 = qv[i][r];
+                acc(h4.x, l4.x, o[0].x, q4.x);
+                acc(h4.y, l4.y, o[0].y, q4.y);
+                acc(h4.z, l4.z, o[1].x, q4.z);
+                acc(h4.w, l4.w, o[1].y, q4.w);
+                *lw = l4;
+            }
+        }
+        __syncthreads();
+    }
+    float2 *im = p.img + ((size_t)s * p.k + j) * p.fsize;
+#pragma unroll
+    for (int i = 0; i < MAXB; ++i) {
+        const int b = threadIdx.x + i * kResNT;
+        if (b >= p.nblocks) break;
+        int z0, xb, bx;
+        res_block(p, b, z0, xb, bx);
+#pragma unroll
+        for (int r = 0; r < kResRZ; ++r) {
+            const int z = z0 + r;
+            if (z >= p.NZ) continue;
+            float2 *q = im + res_goff(p, z, xb);
+            const float4 h4 = hi4[i][r], l4 = *reinterpret_cast<const float4 *>(m.X + z * p.NX + xb);
+            reinterpret_cast<float4 *>(q)[0] = make_float4(h4.x, l4.x, h4.y, l4.y);
+            reinterpret_cast<float4 *>(q)[1] = make_float4(h4.z, l4.z, h4.w, l4.w);
+        }
+    }
+}
+
 // ------------------------------------------------------------------ host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 {
@@ -1208,6 +1556,100 @@ int launch_fwd2(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaM
         HV_RT_INTERNAL(ensure_smem(3 * kTileMenu + cfg, h->device, k_fwd2<C>, Fwd2Smem<C>::BYTES));
         return launch_step(k_fwd2<C>, grid, C::NT, Fwd2Smem<C>::BYTES, st, pdl(h), p, "k_fwd2 launch");
     });
+}
+
+// ------------------------------------------------------------------ resident path (host)
+namespace {
+struct ResGeo {
+    int W, nbx, nblocks, maxb;
+    size_t smem_fwd, smem_born, smem_adj;
+};
+int res_launched(const char *what)
+{
+    count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+    return HV_OK;
+}
+
+ResGeo res_geo(const hv_handle *h)
+{
+    ResGeo g;
+    g.W = h->NX + 2 * GH;
+    g.nbx = h->NX / 4;
+    g.nblocks = g.nbx * ((h->NZ + kResRZ - 1) / kResRZ);
+    g.maxb = (g.nblocks + kResNT - 1) / kResNT;
+    const size_t field = (size_t)(h->NZ + 2 * GH + 1) * g.W * sizeof(float);
+    const size_t dense = (size_t)h->NZ * h->NX * sizeof(float), prof = 2 * (size_t)(h->NZ + h->NX) * sizeof(float);
+    g.smem_fwd = 2 * field + dense + prof;                       // fields, C, profiles
+    g.smem_born = 2 * field + 2 * dense + prof;                  // + b_j
+    g.smem_adj = 2 * field + 2 * dense + prof + (size_t)(2 * g.nblocks + 1 + h->nr) * sizeof(int);   // + image low words, tables
+    return g;
+}
+}  // namespace
+
+bool resident_fits(const hv_handle *h)
+{
+    if (h->NX % 4 != 0 || h->nr >= 65536) return false;
+    const ResGeo g = res_geo(h);
+    return g.maxb >= 1 && g.maxb <= kResMaxB && g.smem_adj <= (size_t)kSmemCapResident;
+}
+
+int launch_resident(const hv_handle *h, int which, const ResLaunch &a, cudaStream_t st)
+{
+    if (!resident_fits(h)) return hvi::fail(HV_EINVAL, "internal: the grid does not fit the resident kernels");
+    const ResGeo g = res_geo(h);
+    const size_t fbytes = h->fsize * sizeof(float);
+    ResParams p;
+    p.ws = reinterpret_cast<float *>(a.base);
+    HV_RT_INTERNAL(field_index(a.base, a.C, fbytes, &p.f_C));
+    HV_RT_INTERNAL(field_index(a.base, a.b, fbytes, &p.f_b));
+    HV_RT_INTERNAL(field_index(a.base, a.q, fbytes, &p.f_q));
+    p.dd = a.dd;
+    p.rscale = a.rscale;
+    p.img = reinterpret_cast<float2 *>(a.img);
+    p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
+    p.src_zx = h->src_zx; p.rt_rec = a.rec; p.rt_pos = a.pos;
+    p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
+    p.NZ = h->NZ; p.NX = h->NX; p.P = h->P; p.W = g.W; p.nbx = g.nbx; p.nblocks = g.nblocks;
+    p.fsize = h->fsize;
+    static std::mutex mu;
+    static bool attr[64][1 + 2 * kResMaxB] = {};
+    auto prep = [&](auto kern, int slot, size_t bytes) -> int {
+        std::lock_guard<std::mutex> lk(mu);
+        if (h->device < 0 || h->device >= 64) return hvi::fail(HV_EINVAL, "internal: device %d", h->device);
+        if (!attr[h->device][slot]) {
+            HV_RT_INTERNAL(set_smem(kern, kSmemCapResident));
+            attr[h->device][slot] = true;
+        }
+        (void)bytes;
+        return HV_OK;
+    };
+    if (which == 0) {
+        HV_RT_INTERNAL(prep(k_res_fwd, 0, g.smem_fwd));
+        k_res_fwd<<<h->ns, kResNT, g.smem_fwd, st>>>(p);
+        return res_launched("k_res_fwd launch");
+    }
+    auto pair = [&](auto kern, int slot, size_t bytes, const char *what) -> int {
+        HV_RT_INTERNAL(prep(kern, slot, bytes));
+        kern<<<dim3(h->ns, a.k), kResNT, bytes, st>>>(p);
+        return res_launched(what);
+    };
+    const int mb = std::min(g.maxb, kResMaxB);
+    if (which == 1) {
+        switch (mb) {
+        case 1: return pair(k_res_born<1>, 1, g.smem_born, "k_res_born launch");
+        case 2: return pair(k_res_born<2>, 2, g.smem_born, "k_res_born launch");
+        case 3: return pair(k_res_born<3>, 3, g.smem_born, "k_res_born launch");
+        default: return pair(k_res_born<4>, 4, g.smem_born, "k_res_born launch");
+        }
+    }
+    switch (mb) {
+    case 1: return pair(k_res_adj<1>, 5, g.smem_adj, "k_res_adj launch");
+    case 2: return pair(k_res_adj<2>, 6, g.smem_adj, "k_res_adj launch");
+    case 3: return pair(k_res_adj<3>, 7, g.smem_adj, "k_res_adj launch");
+    default: return pair(k_res_adj<4>, 8, g.smem_adj, "k_res_adj launch");
+    }
 }
 
 int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,

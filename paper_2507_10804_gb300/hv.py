@@ -113,6 +113,12 @@ class Problem:
         """Recompute two forward steps per launch where possible (hv_set_step_fusion)."""
         check(self.lib.hv_set_step_fusion(self._h, int(bool(enable))))
 
+    def set_resident(self, enable: bool = True) -> bool:
+        """Shared-memory-resident H v with every level stored (hv_set_resident); returns whether this
+        problem's grid fits the resident kernels."""
+        check(self.lib.hv_set_resident(self._h, int(bool(enable))))
+        return bool(self.lib.hv_resident_fits(self._h))
+
     def set_launch_mode(self, mode: int) -> None:
         """How stencil steps follow one another: HV_LAUNCH_PLAIN, _PDL or _DATAFLOW (hv_set_launch_mode)."""
         check(self.lib.hv_set_launch_mode(self._h, int(mode)))
