@@ -951,7 +951,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
 // per pair over all steps in double-float registers (each product split exactly)
 // and the pairs' images are summed over shots in FP64 by the fold, an order
 // that differs from the tiled path's per-step shot-group sums.
-constexpr int kResNT = 512;      // threads per resident CTA
+constexpr int kResNT = 480;      // threads per resident CTA (15 warps: 1352 blocks of the 104 x 104 grid spread ~2.8 each)
 constexpr int kResRZ = 2;        // rows per thread block
 constexpr int kResMaxB = 4;      // blocks per thread, upper bound
 constexpr int kSmemCapResident = 227 * 1024;
@@ -1006,10 +1006,11 @@ __device__ __forceinline__ ResSmem res_smem(const ResParams &p, float *base, boo
     m.F1 = base + rowsW;
     m.C = base + 2 * rowsW;
     m.X = m.C + N;
+    const int NZ4 = (p.NZ + 3) & ~3;                 // keeps ax and ix 16-byte aligned (NX is a multiple of 4)
     m.az = m.X + (second_dense ? N : 0);
-    m.ax = m.az + p.NZ;
+    m.ax = m.az + NZ4;
     m.iz = m.ax + p.NX;
-    m.ix = m.iz + p.NZ;
+    m.ix = m.iz + NZ4;
     m.tab = reinterpret_cast<int *>(m.ix + p.NX);
     return m;
 }
@@ -1043,11 +1044,13 @@ __device__ __forceinline__ void res_setup(const ResParams &p, const ResSmem &m, 
 __device__ __forceinline__ void res_sponge_row(const ResSmem &m, int z, int xb, float2 (&inv)[2], float2 (&nom)[2])
 {
     const float azv = m.az[z], izv = m.iz[z];
+    const float4 ix4 = *reinterpret_cast<const float4 *>(m.ix + xb), ax4 = *reinterpret_cast<const float4 *>(m.ax + xb);
+    const float ixv[4] = {ix4.x, ix4.y, ix4.z, ix4.w}, axv[4] = {ax4.x, ax4.y, ax4.z, ax4.w};
     float iv[4], nm[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-        iv[c] = fminf(izv, m.ix[xb + c]);
-        nm[c] = fmaxf(azv, m.ax[xb + c]) - 1.0f;
+        iv[c] = fminf(izv, ixv[c]);
+        nm[c] = fmaxf(azv, axv[c]) - 1.0f;
     }
     inv[0] = make_float2(iv[0], iv[1]);
     inv[1] = make_float2(iv[2], iv[3]);
@@ -1580,7 +1583,8 @@ ResGeo res_geo(const hv_handle *h)
     g.nblocks = g.nbx * ((h->NZ + kResRZ - 1) / kResRZ);
     g.maxb = (g.nblocks + kResNT - 1) / kResNT;
     const size_t field = (size_t)(h->NZ + 2 * GH + 1) * g.W * sizeof(float);
-    const size_t dense = (size_t)h->NZ * h->NX * sizeof(float), prof = 2 * (size_t)(h->NZ + h->NX) * sizeof(float);
+    const size_t dense = (size_t)h->NZ * h->NX * sizeof(float),
+                 prof = 2 * (size_t)(((h->NZ + 3) & ~3) + h->NX) * sizeof(float);
     g.smem_fwd = 2 * field + dense + prof;                       // fields, C, profiles
     g.smem_born = 2 * field + 2 * dense + prof;                  // + b_j
     g.smem_adj = 2 * field + 2 * dense + prof + (size_t)(2 * g.nblocks + 1 + h->nr) * sizeof(int);   // + image low words, tables
