@@ -299,11 +299,15 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def csrc_hash() -> str:
-    """Hash of the stencil kernels' source (csrc/hv_stencil.cu): DRAM counters recorded under
-    profiles/ apply only while it is unchanged."""
+def csrc_hash(resident: bool = False) -> str:
+    """Hash of the device code the DRAM counters under profiles/ were taken on: the tiled stencil kernels
+    (csrc/hv_stencil.cu up to the resident kernels) or, for the resident kernels, the file's device code
+    up to the host side.  Counters apply only while that code is unchanged."""
+    text = open(os.path.join(ROOT, "paper_2507_10804_gb300", "csrc", "hv_stencil.cu"), "rb").read()
+    mark = b"// ------------------------------------------------------------------ "
+    cut = text.find(mark + (b"host side" if resident else b"resident kernels"))
     h = hashlib.sha256()
-    h.update(open(os.path.join(ROOT, "paper_2507_10804_gb300", "csrc", "hv_stencil.cu"), "rb").read())
+    h.update(text[:cut] if cut >= 0 else text)
     return h.hexdigest()[:16]
 
 
@@ -625,7 +629,7 @@ def run_ours(args, w):
         # counters recorded for this workload, these kernel sources and these tiles (full-size launches)
         ent = dram_traffic().get((args.workload + ("-resident" if resident else ""), dom))
         ti = {"fwd": 0, "advance": 1, "adj": 2}[dom]          # the dominant kernel's own tile configuration
-        if ent and ent[0] == csrc_hash() and (resident or ent[2][ti] == list(tiles)[ti]) and args.nt is None \
+        if ent and ent[0] == csrc_hash(resident) and (resident or ent[2][ti] == list(tiles)[ti]) and args.nt is None \
                 and args.shots is None:
             traffic = ent[1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
