@@ -314,8 +314,9 @@ def csrc_hash(resident: bool = False) -> str:
 def dram_traffic() -> dict:
     """ncu DRAM bytes (read + write) per launch from profiles/dram_traffic.txt.
 
-    Each line: <workload>:<kind> <hash of the kernel sources they were taken on> <bytes> <tile ids>;
-    '#' starts a comment.  Returns {(workload, kind): (hash, bytes, [tile ids])}.
+    Each line: <workload>:<kind> <hash of the kernel sources they were taken on> <bytes> <tile ids of the
+    forward, recompute and adjoint kernels>; '#' starts a comment.  Returns {(workload, kind, tile id of that
+    kind): (hash, bytes)}, so a kind may have a line for each tile shape the autotuner picks.
     """
     out = {}
     try:
@@ -324,7 +325,9 @@ def dram_traffic() -> dict:
                 ln = ln.split("#", 1)[0].split()
                 if len(ln) == 4 and ":" in ln[0]:
                     wl, kind = ln[0].split(":", 1)
-                    out[(wl, kind)] = (ln[1], int(ln[2]), [int(t) for t in ln[3].split(",")])
+                    tiles = [int(t) for t in ln[3].split(",")]
+                    tid = tiles[{"fwd": 0, "advance": 1, "adj": 2}.get(kind, 0)]
+                    out[(wl, kind, tid)] = (ln[1], int(ln[2]))
     except OSError:
         pass
     return out
@@ -627,10 +630,9 @@ def run_ours(args, w):
         achieved = alg[dom] * steps_of.get(dom, n_dom) / (t_dom / 1e3) / 1e9
         traffic = None
         # counters recorded for this workload, these kernel sources and these tiles (full-size launches)
-        ent = dram_traffic().get((args.workload + ("-resident" if resident else ""), dom))
-        ti = {"fwd": 0, "advance": 1, "adj": 2}[dom]          # the dominant kernel's own tile configuration
-        if ent and ent[0] == csrc_hash(resident) and (resident or ent[2][ti] == list(tiles)[ti]) and args.nt is None \
-                and args.shots is None:
+        tid = 0 if resident else list(tiles)[{"fwd": 0, "advance": 1, "adj": 2}[dom]]   # the kernel's own tiles
+        ent = dram_traffic().get((args.workload + ("-resident" if resident else ""), dom, tid))
+        if ent and ent[0] == csrc_hash(resident) and args.nt is None and args.shots is None:
             traffic = ent[1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic,

@@ -330,6 +330,47 @@ __device__ __forceinline__ void sponge_row(const float *az, int z, int NZ, const
     nom[1] = make_float2(nm[2], nm[3]);
 }
 
+// The same factors from values fixed per thread: the damping rates of the
+// thread's RZ rows and 4 columns and their reciprocal factors 1 / (1 + a),
+// computed once per CTA.  Rounding is monotone, so 1 / (1 + max(az, ax))
+// rounded equals min(1 / (1 + az), 1 / (1 + ax)) rounded: bitwise the values
+// sponge_row computes, without a load or a division per shot.
+template <int RZ>
+struct SpongeRegs {
+    float az[RZ], iz[RZ], ax[4], ix[4];
+};
+
+template <int RZ>
+__device__ __forceinline__ void sponge_regs(SpongeRegs<RZ> &sp, const float *az, const float *ax, int zrow0, int xb,
+                                            int NZ, int NX)
+{
+#pragma unroll
+    for (int r = 0; r < RZ; ++r) {
+        sp.az[r] = az[min(zrow0 + r, NZ - 1)];
+        sp.iz[r] = __frcp_rn(1.0f + sp.az[r]);
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        sp.ax[c] = ax[min(xb + c, NX - 1)];
+        sp.ix[c] = __frcp_rn(1.0f + sp.ax[c]);
+    }
+}
+
+template <int RZ>
+__device__ __forceinline__ void sponge_row(const SpongeRegs<RZ> &sp, int r, float2 (&inv)[2], float2 (&nom)[2])
+{
+    float iv[4], nm[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        iv[c] = fminf(sp.iz[r], sp.ix[c]);
+        nm[c] = fmaxf(sp.az[r], sp.ax[c]) - 1.0f;
+    }
+    inv[0] = make_float2(iv[0], iv[1]);
+    inv[1] = make_float2(iv[2], iv[3]);
+    nom[0] = make_float2(nm[0], nm[1]);
+    nom[1] = make_float2(nm[2], nm[3]);
+}
+
 __device__ __forceinline__ void f4(const float *p, float2 (&o)[2])
 {
     const float4 v = *reinterpret_cast<const float4 *>(p);
@@ -485,10 +526,8 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     // Tiles entirely inside the interior have a = 0 and take the short update.
     const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
                           x0 + C::TX <= p.g.nb + p.g.nx);
-    float axv[4] = {0.f, 0.f, 0.f, 0.f};
-    if (sponge)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
+    SpongeRegs<C::RZ> spr{};
+    if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
     const float wav = p.wavelet[p.n];
     // From here on the fields of earlier steps are complete and visible.
     if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
@@ -532,7 +571,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                     float2 up[2], cc[2], inv[2] = {}, nom[2] = {}, o[2];
                     f4(sUp + (tz * C::RZ + r) * C::TX + 4 * tx, up);
                     f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
-                    if constexpr (SP) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
+                    if constexpr (SP) sponge_row<C::RZ>(spr, r, inv, nom);
 #pragma unroll
                     for (int h = 0; h < 2; ++h) o[h] = leapfrog<SP>(uc[r][h], up[h], cc[h], Q[r][h], inv[h], nom[h]);
                     if (z < p.g.NZ && xb < p.g.NX) st4(un + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
@@ -557,7 +596,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                     f4(sDp + (tz * C::RZ + r) * C::TX + 4 * tx, dp);
                     f4(sC + (tz * C::RZ + r) * C::TX + 4 * tx, cc);
                     f4(sB + (tz * C::RZ + r) * C::TX + 4 * tx, bb);
-                    if constexpr (SP) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
+                    if constexpr (SP) sponge_row<C::RZ>(spr, r, inv, nom);
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
                         o[h] = leapfrog<SP>(dc[r][h], dp[h], cc[h], f2fma(bb[h], Q[r][h], Ld[r][h]), inv[h], nom[h]);
@@ -771,7 +810,7 @@ struct AdjSmem {
 // contributions in shot order and adds them to the group's double-float partial image
 // once per step.
 template <class C>
-__global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjParams p)
+__global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2) k_adj(const __grid_constant__ AdjParams p)
 {
     using S = AdjSmem<C>;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -804,10 +843,8 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
     load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
     const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
                           x0 + C::TX <= p.g.nb + p.g.nx);
-    float axv[4] = {0.f, 0.f, 0.f, 0.f};
-    if (sponge)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) axv[c] = p.ax[min(xb + c, p.g.NX - 1)];
+    SpongeRegs<C::RZ> spr{};
+    if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
     const float wav = p.wavelet[p.n];
     if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
     if (threadIdx.x == 0) {
@@ -835,8 +872,26 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
         v.y = __fadd_rn(v.y, __fadd_rn(__fsub_rn(v.x, __fsub_rn(s, bv)), __fsub_rn(a, bv)));
         v.x = s;
     };
+    // The group's image words under the thread's full-width rows are loaded when
+    // the group's first shot starts, so that the flush does not wait on them.
+    float4 imv[C::RZ][2];
+    auto img_of = [&](int group) {
+        return reinterpret_cast<float2 *>(p.img) + ((size_t)group * p.k + j) * p.g.fsize;
+    };
+    auto prefetch = [&](int group) {
+        const float2 *im = img_of(group);
+#pragma unroll
+        for (int r = 0; r < C::RZ; ++r) {
+            const int z = zrow0 + r;
+            if (z < p.g.NZ && xb + 3 < p.g.NX) {
+                const float4 *q4 = reinterpret_cast<const float4 *>(im + (size_t)(z + GH) * p.g.P + (xb + GH));
+                imv[r][0] = q4[0];
+                imv[r][1] = q4[1];
+            }
+        }
+    };
     auto flush = [&](int group) {
-        float2 *im = reinterpret_cast<float2 *>(p.img) + ((size_t)group * p.k + j) * p.g.fsize;
+        float2 *im = img_of(group);
 #pragma unroll
         for (int r = 0; r < C::RZ; ++r) {
             const int z = zrow0 + r;
@@ -845,7 +900,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
                 const float a4[4] = {acc[r][0].x, acc[r][0].y, acc[r][1].x, acc[r][1].y};
                 if (xb + 3 < p.g.NX) {
                     float4 *q4 = reinterpret_cast<float4 *>(im + off);
-                    const float4 w0 = q4[0], w1 = q4[1];
+                    const float4 w0 = imv[r][0], w1 = imv[r][1];
                     float2 v[4] = {make_float2(w0.x, w0.y), make_float2(w0.z, w0.w), make_float2(w1.x, w1.y),
                                    make_float2(w1.z, w1.w)};
 #pragma unroll
@@ -879,6 +934,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
             const int st = i % C::ST, s = s0 + i;
             const int fo = j * p.ns + s;
             const int rb = tab.rb[i], re = tab.re[i];
+            if (i == 0 || s % p.gsz == 0) prefetch(s / p.gsz);
             if (rb < re) {                         // receivers in this tile: stage their sources
                 for (int q = threadIdx.x; q < C::TZ * C::TX; q += C::NT) ssrc[q] = 0.0f;
                 __syncthreads();
@@ -915,7 +971,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_adj(const __grid_constant__ AdjPar
 #pragma unroll
                     for (int h = 0; h < 2; ++h) Ll[r][h] = f2add(Ll[r][h], src[h]);
                 }
-                if constexpr (SP) sponge_row(p.az, z, p.g.NZ, axv, inv, nom);
+                if constexpr (SP) sponge_row<C::RZ>(spr, r, inv, nom);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     o[h] = leapfrog<SP>(lc[r][h], l2[h], cc[h], Ll[r][h], inv[h], nom[h]);
