@@ -1048,12 +1048,16 @@ __device__ __forceinline__ size_t res_goff(const ResParams &p, int z, int xb)
 // Shared memory of the resident kernels (floats): two fields [NZ + 9][W] (the
 // padded field with its 4-cell ghost band and one spare row), then dense
 // [NZ][NX] copies of the pointwise coefficients the kernel needs (C, and b or
-// the image's low words), the damping profiles az [NZ] and ax [NX], and the
-// adjoint's receiver tables.  Everything a step reads besides Q^n is on chip.
+// the image's low words), the damping profiles, and the adjoint's receiver
+// tables.  Everything a step reads besides Q^n is on chip.  iz, ix = 1 / (1 +
+// az), 1 / (1 + ax), correctly rounded; zt holds the row profile once more per
+// pair of rows (the rows of one thread block) as (az, iz, az, iz), one 16-byte
+// load per block.
 struct ResSmem {
-    float *F0, *F1, *C, *X, *az, *ax, *iz, *ix;   // iz, ix: 1 / (1 + az), 1 / (1 + ax), correctly rounded
+    float *F0, *F1, *C, *X, *az, *ax, *iz, *ix, *zt;
     int *tab;
 };
+static_assert(kResRZ == 2, "the row-profile table holds two rows per entry");
 __device__ __forceinline__ ResSmem res_smem(const ResParams &p, float *base, bool second_dense)
 {
     const int rowsW = (p.NZ + 2 * GH + 1) * p.W, N = p.NZ * p.NX;
@@ -1063,7 +1067,8 @@ __device__ __forceinline__ ResSmem res_smem(const ResParams &p, float *base, boo
     m.C = base + 2 * rowsW;
     m.X = m.C + N;
     const int NZ4 = (p.NZ + 3) & ~3;                 // keeps ax and ix 16-byte aligned (NX is a multiple of 4)
-    m.az = m.X + (second_dense ? N : 0);
+    m.zt = m.X + (second_dense ? N : 0);
+    m.az = m.zt + 2 * NZ4;
     m.ax = m.az + NZ4;
     m.iz = m.ax + p.NX;
     m.ix = m.iz + NZ4;
@@ -1087,6 +1092,11 @@ __device__ __forceinline__ void res_setup(const ResParams &p, const ResSmem &m, 
         m.az[q] = p.az[q];
         m.iz[q] = __frcp_rn(1.0f + p.az[q]);
     }
+    for (int q = threadIdx.x; q < ((p.NZ + 3) & ~3); q += kResNT) {   // rows past NZ: a = 0
+        const float a = q < p.NZ ? p.az[q] : 0.0f;
+        m.zt[2 * q] = a;
+        m.zt[2 * q + 1] = __frcp_rn(1.0f + a);
+    }
     for (int q = threadIdx.x; q < p.NX; q += kResNT) {
         m.ax[q] = p.ax[q];
         m.ix[q] = __frcp_rn(1.0f + p.ax[q]);
@@ -1097,11 +1107,22 @@ __device__ __forceinline__ void res_setup(const ResParams &p, const ResSmem &m, 
 // is monotone, so 1 / (1 + max(az, ax)) rounded equals min(1 / (1 + az),
 // 1 / (1 + ax)) rounded, and max(az, ax) - 1 equals max(az - 1, ax - 1):
 // bitwise the values sponge_row computes, without a division per point.
-__device__ __forceinline__ void res_sponge_row(const ResSmem &m, int z, int xb, float2 (&inv)[2], float2 (&nom)[2])
+// For the two rows z0, z0 + 1 (z0 even) of a thread block: three 16-byte loads
+// per block (res_sponge_tabs), the factors of row r formed where they are used.
+struct ResSpongeTabs {
+    float4 z4, ix4, ax4;   // (az, iz) of both rows; ix and ax of the 4 columns
+};
+
+__device__ __forceinline__ ResSpongeTabs res_sponge_tabs(const ResSmem &m, int z0, int xb)
 {
-    const float azv = m.az[z], izv = m.iz[z];
-    const float4 ix4 = *reinterpret_cast<const float4 *>(m.ix + xb), ax4 = *reinterpret_cast<const float4 *>(m.ax + xb);
-    const float ixv[4] = {ix4.x, ix4.y, ix4.z, ix4.w}, axv[4] = {ax4.x, ax4.y, ax4.z, ax4.w};
+    return ResSpongeTabs{*reinterpret_cast<const float4 *>(m.zt + 2 * z0), *reinterpret_cast<const float4 *>(m.ix + xb),
+                         *reinterpret_cast<const float4 *>(m.ax + xb)};
+}
+
+__device__ __forceinline__ void res_sponge_row(const ResSpongeTabs &t, int r, float2 (&inv)[2], float2 (&nom)[2])
+{
+    const float azv = r ? t.z4.z : t.z4.x, izv = r ? t.z4.w : t.z4.y;
+    const float ixv[4] = {t.ix4.x, t.ix4.y, t.ix4.z, t.ix4.w}, axv[4] = {t.ax4.x, t.ax4.y, t.ax4.z, t.ax4.w};
     float iv[4], nm[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
@@ -1112,6 +1133,16 @@ __device__ __forceinline__ void res_sponge_row(const ResSmem &m, int z, int xb, 
     inv[1] = make_float2(iv[2], iv[3]);
     nom[0] = make_float2(nm[0], nm[1]);
     nom[1] = make_float2(nm[2], nm[3]);
+}
+
+// The same for one row z from the separate profiles (two 4-byte and two
+// 16-byte loads; the adjoint has no registers to spare for a block's tables).
+__device__ __forceinline__ void res_sponge_row_at(const ResSmem &m, int z, int xb, float2 (&inv)[2], float2 (&nom)[2])
+{
+    const float azv = m.az[z], izv = m.iz[z];
+    res_sponge_row(ResSpongeTabs{make_float4(azv, izv, azv, izv), *reinterpret_cast<const float4 *>(m.ix + xb),
+                                 *reinterpret_cast<const float4 *>(m.ax + xb)},
+                   0, inv, nom);
 }
 
 __device__ __forceinline__ void res_block(const ResParams &p, int b, int &z0, int &xb, int &bx)
@@ -1141,6 +1172,7 @@ __global__ void __launch_bounds__(kResNT, 1) k_res_fwd(const __grid_constant__ R
             float2 Q[kResRZ][2], uc[kResRZ][2];
             lap_at<kResRZ>(cur, p.W / 4, z0, bx + 1, Q, uc);
             res_add_source(Q, z0, xb, sz, sx, wav);
+            const ResSpongeTabs spt = res_sponge_tabs(m, z0, xb);
 #pragma unroll
             for (int r = 0; r < kResRZ; ++r) {
                 const int z = z0 + r;
@@ -1151,7 +1183,7 @@ __global__ void __launch_bounds__(kResNT, 1) k_res_fwd(const __grid_constant__ R
                 float *sp = prv + (z + GH) * p.W + xb + GH;
                 f4(sp, up);
                 f4(m.C + z * p.NX + xb, cc);
-                res_sponge_row(m, z, xb, inv, nom);
+                res_sponge_row(spt, r, inv, nom);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) o[h] = leapfrog<true>(uc[r][h], up[h], cc[h], Q[r][h], inv[h], nom[h]);
                 *reinterpret_cast<float4 *>(sp) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
@@ -1202,6 +1234,7 @@ __global__ void __launch_bounds__(kResNT, 1) k_res_born(const __grid_constant__ 
             res_block(p, b, z0, xb, bx);
             float2 Ld[kResRZ][2], dc[kResRZ][2];
             lap_at<kResRZ>(cur, p.W / 4, z0, bx + 1, Ld, dc);
+            const ResSpongeTabs spt = res_sponge_tabs(m, z0, xb);
 #pragma unroll
             for (int r = 0; r < kResRZ; ++r) {
                 const int z = z0 + r;
@@ -1212,7 +1245,7 @@ __global__ void __launch_bounds__(kResNT, 1) k_res_born(const __grid_constant__ 
                 f4(sp, dp);
                 f4(m.C + z * p.NX + xb, cc);
                 f4(m.X + z * p.NX + xb, bb);
-                res_sponge_row(m, z, xb, inv, nom);
+                res_sponge_row(spt, r, inv, nom);
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
                     o[h] = leapfrog<true>(dc[r][h], dp[h], cc[h], f2fma(bb[h], Q[h], Ld[r][h]), inv[h], nom[h]);
@@ -1307,7 +1340,7 @@ __global__ void __launch_bounds__(kResNT, 1) k_res_adj(const __grid_constant__ R
                 float *sp = prv + (z + GH) * p.W + xb + GH;
                 f4(sp, l2);
                 f4(m.C + z * p.NX + xb, cc);
-                res_sponge_row(m, z, xb, inv, nom);
+                res_sponge_row_at(m, z, xb, inv, nom);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) o[h] = leapfrog<true>(lc[r][h], l2[h], cc[h], Ll[r][h], inv[h], nom[h]);
                 *reinterpret_cast<float4 *>(sp) = make_float4(o[0].x, o[0].y, o[1].x, o[1].y);
@@ -1640,7 +1673,7 @@ ResGeo res_geo(const hv_handle *h)
     g.maxb = (g.nblocks + kResNT - 1) / kResNT;
     const size_t field = (size_t)(h->NZ + 2 * GH + 1) * g.W * sizeof(float);
     const size_t dense = (size_t)h->NZ * h->NX * sizeof(float),
-                 prof = 2 * (size_t)(((h->NZ + 3) & ~3) + h->NX) * sizeof(float);
+                 prof = (4 * (size_t)((h->NZ + 3) & ~3) + 2 * (size_t)h->NX) * sizeof(float);   // ResSmem profiles
     g.smem_fwd = 2 * field + dense + prof;                       // fields, C, profiles
     g.smem_born = 2 * field + 2 * dense + prof;                  // + b_j
     g.smem_adj = 2 * field + 2 * dense + prof + (size_t)(2 * g.nblocks + 1 + h->nr) * sizeof(int);   // + image low words, tables
