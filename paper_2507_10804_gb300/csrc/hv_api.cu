@@ -1107,6 +1107,7 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
     HV_CK(cudaMemsetAsync(ws, 0, L.total, st));
     Exec E;
     HV_RT(E.init(h, st, L, ws, k));
+    if (E.pool.size() < 4) return hvi::fail(HV_EINVAL, "internal: autotune needs four forward batches");
     const float *dd = reinterpret_cast<const float *>((char *)ws + L.dd);
     const int nmenu = hvk::tile_menu_size();
     cudaEvent_t e0, e1;
@@ -1121,23 +1122,30 @@ extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void 
     for (int c = 0; c < nmenu && rc == HV_OK; ++c) {
         const hvi::RecTiles &rt = rectiles_for(h, hvk::tiling(h, c));
         for (int kind = 0; kind < 3 && rc == HV_OK; ++kind) {
+            // The fields rotate through three pool batches (and the two vector
+            // batches) as in a sweep, so each launch reads what the one before it
+            // wrote, with the cache behaviour of the real sequence.
             for (int rep = 0; rep <= kReps && rc == HV_OK; ++rep) {
                 if (rep == 1) cudaEventRecord(e0, st);
+                float *f0 = E.pool[rep % 3], *f1 = E.pool[(rep + 1) % 3], *f2 = E.pool[(rep + 2) % 3];
+                float *d0 = E.Dbuf(rep % 2), *d1 = E.Dbuf((rep + 1) % 2);
                 if (kind == 2) {
                     hvk::AdjLaunch a{};
-                    a.u = E.zero; a.lam1 = E.Dbuf(1); a.lam_io = E.Dbuf(0); a.C = E.C; a.r = dd;
+                    a.u = f1; a.lam1 = d1; a.lam_io = d0; a.C = E.C; a.r = dd;
                     a.r_per_vector = 1; a.rscale = 1.0f; a.img = E.img; a.n = 0; a.k = k; a.G = L.G;
                     rc = hvk::launch_adj(h, c, rt, E.maps, a, st);
                 } else if (kind == 1 && fused) {
                     hvk::Fwd2Launch a{};      // recomputation runs fused double steps: time one, halve it
-                    a.u_cur = E.zero; a.u_prev = E.zero; a.u_next1 = E.pool[0]; a.u_next2 = E.pool[1]; a.C = E.C;
+                    const int q = 2 * rep;   // two levels per launch, over four batches
+                    a.u_prev = E.pool[q % 4]; a.u_cur = E.pool[(q + 1) % 4];
+                    a.u_next1 = E.pool[(q + 2) % 4]; a.u_next2 = E.pool[(q + 3) % 4]; a.C = E.C;
                     a.n = 0;
                     rc = hvk::launch_fwd2(h, c, rt, E.maps, a, st);
                 } else {
                     hvk::FwdLaunch a{};
-                    a.u_cur = E.zero; a.u_prev = E.zero; a.u_next = E.pool[0]; a.C = E.C; a.n = 0;
+                    a.u_cur = f1; a.u_prev = f0; a.u_next = f2; a.C = E.C; a.n = 0;
                     if (kind == 0) {
-                        a.b = E.b; a.k = k; a.du_cur = E.Dbuf(0); a.du_io = E.Dbuf(1);
+                        a.b = E.b; a.k = k; a.du_cur = d1; a.du_io = d0;
                     }
                     rc = hvk::launch_fwd(h, c, rt, E.maps, a, st);
                 }
