@@ -520,15 +520,6 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
         for (int q = 0; q <= C::ST; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
-    // Set-up from the handle's constant tables only (written before any step):
-    // with programmatic dependent launch this overlaps the previous step's tail.
-    load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
-    // Tiles entirely inside the interior have a = 0 and take the short update.
-    const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
-                          x0 + C::TX <= p.g.nb + p.g.nx);
-    SpongeRegs<C::RZ> spr{};
-    if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
-    const float wav = p.wavelet[p.n];
     // From here on the fields of earlier steps are complete and visible.
     if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
     if (threadIdx.x == 0) {
@@ -538,6 +529,16 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
         for (int q = 0; q < C::ST && q < nitems; ++q) issue(q);
     }
     allow_dependent_launch();
+    // Set-up from the handle's constant tables (written before any step) while
+    // the first copies are in flight; the barrier after the coefficient wait
+    // publishes the shot tables.
+    load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
+    // Tiles entirely inside the interior have a = 0 and take the short update.
+    const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
+                          x0 + C::TX <= p.g.nb + p.g.nx);
+    SpongeRegs<C::RZ> spr{};
+    if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
+    const float wav = p.wavelet[p.n];
 
     bool ok = mbar_wait(&bars[C::ST], 0, p.status);
     if (__syncthreads_or(!ok)) {
@@ -840,12 +841,6 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
         for (int q = 0; q <= C::ST; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
-    load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
-    const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
-                          x0 + C::TX <= p.g.nb + p.g.nx);
-    SpongeRegs<C::RZ> spr{};
-    if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
-    const float wav = p.wavelet[p.n];
     if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bars[C::ST], C::PT);
@@ -853,6 +848,13 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
         for (int q = 0; q < C::ST && q < nitems; ++q) issue(q);
     }
     allow_dependent_launch();
+    // constant tables while the first copies are in flight (published by the barrier after the C wait)
+    load_shot_tables(tab, p.src_zx, p.rt_off, s0, nitems, tile, p.g.ntiles);
+    const bool sponge = !(z0 >= p.g.nb && z0 + C::TZ <= p.g.nb + p.g.nz && x0 >= p.g.nb &&
+                          x0 + C::TX <= p.g.nb + p.g.nx);
+    SpongeRegs<C::RZ> spr{};
+    if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
+    const float wav = p.wavelet[p.n];
     // This step's image contribution of the CTA's shots, summed in shot order
     // in FP32 (at most 8 terms); it is added to the double-float image once per step.
     // Double-precision arithmetic is slow on this part, so none runs per shot.
@@ -922,6 +924,7 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
         }
     };
 
+    if (nitems > 0) prefetch(s0 / p.gsz);
     bool ok = mbar_wait(&bars[C::ST], 0, p.status);
     if (__syncthreads_or(!ok)) {
         drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
@@ -934,7 +937,7 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
             const int st = i % C::ST, s = s0 + i;
             const int fo = j * p.ns + s;
             const int rb = tab.rb[i], re = tab.re[i];
-            if (i == 0 || s % p.gsz == 0) prefetch(s / p.gsz);
+            if (i > 0 && s % p.gsz == 0) prefetch(s / p.gsz);
             if (rb < re) {                         // receivers in this tile: stage their sources
                 for (int q = threadIdx.x; q < C::TZ * C::TX; q += C::NT) ssrc[q] = 0.0f;
                 __syncthreads();
