@@ -40,6 +40,9 @@ CASES = {
     # padded 49 x 84: an odd row count (the last thread block is half outside)
     "ragged": lambda: ragged_workload(nz=37, nx=72, nb=6, nt=150, ns=3, nr=7, k=3),
     "dense_receivers": lambda: _dense_receivers(ragged_workload(nz=30, nx=60, nb=6, nt=120, ns=2, nr=4, k=2)),
+    # padded 100 x 116: 1450 thread blocks, more than three per thread (the four-block kernels), and shared
+    # memory near the per-CTA limit
+    "four_blocks": lambda: ragged_workload(nz=88, nx=104, nb=6, nt=60, ns=2, nr=5, k=2),
 }
 
 
