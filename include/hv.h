@@ -320,6 +320,15 @@ int hv_status(hv_handle *h, int *device_status);
  *    hv_posterior_sample).  On a PDO or PSF+ approximation of H_d itself only
  *    HV_APPROX_H (B v) is provided.
  *
+ * hv_set_fused_transforms(enable): for PDO, PSF+ and quadratic-model objects
+ * created afterwards in this process (default on), the applies of the
+ * low-rank-symbol form run the library's own 2D DFTs with the symbol products
+ * fused into them where nz and nx are powers of two from 16 to 512 (the r-term
+ * spectra are written once and read once per vector); other grids, and
+ * objects created with the setting off, use cuFFT transforms and separate
+ * product kernels.  The two agree to FP32 rounding (about 1e-6 relative), not
+ * bitwise.  Returns HV_OK.
+ *
  * hv_util_hermitian_eig: eigenvalues (descending) into w[n] and eigenvectors
  * (columns, row-major, interleaved re/im doubles) into V[n*n*2] of the
  * Hermitian matrix A[n*n*2] (interleaved re/im, row-major), n <= 4096: the host
@@ -348,6 +357,7 @@ int hv_approx_build_lr(hv_handle *h, const float *m, double delta, double gamma,
                        int ckpt, hv_approx **out, void *ws, size_t ws_bytes, void *stream);
 int hv_approx_lr_eigs(const hv_approx *a, double *lambda, float *V, void *stream);
 int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream);
+int hv_set_fused_transforms(int enable);
 int hv_approx_info(const hv_approx *a, int *info);
 int hv_approx_psfs(const hv_approx *a, float *psf, void *stream);
 int hv_approx_destroy(hv_approx *a);

@@ -128,6 +128,7 @@ _SIGS = {
     "hv_tile_menu_size": ([], c_int),
     "hv_set_launch_mode": ([c_void_p, c_int], c_int),
     "hv_set_step_fusion": ([c_void_p, c_int], c_int),
+    "hv_set_fused_transforms": ([c_int], c_int),
     "hv_set_resident": ([c_void_p, c_int], c_int),
     "hv_resident_fits": ([c_void_p], c_int),
     "hv_tile_menu": ([c_int, ip, ip], c_int),

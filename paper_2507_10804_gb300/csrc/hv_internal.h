@@ -224,8 +224,10 @@ struct LrSym {
     bool spd = false;                    // square-root symbol: the approximation is B B^T
     int kb = 1;                          // vectors per apply batch
     cufftHandle pf = 0, pi = 0;          // build: one forward, r inverse (C2C, nz x nx)
-    cufftHandle pfb = 0, pib = 0;        // apply: kb forward, r x kb inverse
+    cufftHandle pfb = 0, pib = 0;        // apply: kb forward, r x kb inverse (pib: not with fused transforms)
     bool pf_ok = false, pi_ok = false, pfb_ok = false, pib_ok = false;
+    bool fused = false;                  // applies through the fused transforms of hv_lrfft.cu
+    float2 *tw = nullptr;                // their twiddle tables: nz, then nx entries
     cudaEvent_t done = nullptr;          // last use of the scratch
     std::mutex *mu = nullptr;
 };
@@ -237,6 +239,14 @@ int pdo_columns(LrSym &L, const float *Hvp, cudaStream_t st);
 constexpr int kLrForward = 0, kLrTranspose = 1, kLrGram = 2;   // B v, B^T v, B B^T v
 int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st, int op = kLrForward);
 int pdo_sqrt(const LrSym &src, LrSym &out, cudaStream_t st);
+// The fused transforms of the low-rank-symbol applies (hv_lrfft.cu): power-of-two
+// grids with 16 <= nz, nx <= 512.  forward: out = Re sum_k a_k F^-1 (b_k V) from
+// the spectra V of nq vectors; transpose: V = (1/N) sum_k conj(b_k) F (conj(a_k) w).
+bool lr_fused_default();
+bool lr_fused_supported(int nz, int nx);
+int lr_fused_init(LrSym &L);
+int lr_fused_forward(const LrSym &L, const float2 *V, int nq, float *out, cudaStream_t st);
+int lr_fused_transpose(const LrSym &L, const float *w, int nq, float2 *V, cudaStream_t st);
 void launch_sqrt_real(const float2 *in, float2 *out, size_t n, cudaStream_t st);
 // Matern prior and the low-rank approximation (hv_lowrank.cu).
 struct Prior {

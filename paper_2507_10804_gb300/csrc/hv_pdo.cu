@@ -211,11 +211,13 @@ int lr_samples(int nz, int nx, double h, double rho0, int r, LrGeo &g)
     return HV_OK;
 }
 
-// Vectors per apply batch: up to 64, with the batch's r spectra within 256 MB.
-int lr_batch(const LrGeo &g)
+// Vectors per apply batch: up to 64, with the batch's r spectra within 256 MB
+// (1 GB with the fused transforms, which need no library plan of r x kb
+// transforms and its work area).
+int lr_batch(const LrGeo &g, bool fused)
 {
     const size_t per = (size_t)g.r * g.nz * g.nx * sizeof(float2);
-    const size_t kb = per > 0 ? ((size_t)256 << 20) / per : 1;
+    const size_t kb = per > 0 ? ((size_t)(fused ? 1024 : 256) << 20) / per : 1;
     return (int)std::max<size_t>(1, std::min<size_t>(64, kb));
 }
 
@@ -223,7 +225,8 @@ int lr_create(LrSym &L, const LrGeo &g)
 {
     L.g = g;
     L.mu = new std::mutex;
-    L.kb = lr_batch(g);
+    L.fused = lr_fused_default() && lr_fused_supported(g.nz, g.nx);
+    L.kb = lr_batch(g, L.fused);
     const size_t N = (size_t)g.nz * g.nx;
     const size_t nY = (size_t)g.r * std::max(L.kb, 1) * N;   // apply: r x kb spectra; build: r spectra
     cudaError_t e;
@@ -243,6 +246,7 @@ int lr_create(LrSym &L, const LrGeo &g)
     HV_RT_INTERNAL(cufft_check(cufftPlanMany(&L.pfb, 2, n, nullptr, 1, (int)N, nullptr, 1, (int)N, CUFFT_C2C, L.kb),
                                "cufftPlanMany"));
     L.pfb_ok = true;
+    if (L.fused) return lr_fused_init(L);
     HV_RT_INTERNAL(cufft_check(cufftPlanMany(&L.pib, 2, n, nullptr, 1, (int)N, nullptr, 1, (int)N, CUFFT_C2C,
                                              g.r * L.kb),
                                "cufftPlanMany"));
@@ -262,6 +266,7 @@ void lr_destroy(LrSym &L)
     cudaFree(L.Y);
     cudaFree(L.V);
     cudaFree(L.T);
+    cudaFree(L.tw);
     delete L.mu;
     L = LrSym{};
 }
@@ -302,6 +307,7 @@ static int lr_batch_forward(LrSym &L, const float *v, int nq, float *out, cudaSt
     HV_RT_INTERNAL(check("k_real_to_complex"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_FORWARD),
                                "forward FFT"));
+    if (L.fused) return lr_fused_forward(L, L.V, nq, out, st);
     k_lr_scale<<<dim3(blocks_for(N, 256), kb, g.r), 256, 0, st>>>(L.V, L.b, L.Y, g.r, kb, N);
     HV_RT_INTERNAL(check("k_lr_scale"));
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_INVERSE),
@@ -316,12 +322,16 @@ static int lr_batch_transpose(LrSym &L, const float *w, int nq, float *out, cuda
     const LrGeo &g = L.g;
     const size_t N = (size_t)g.nz * g.nx;
     const int kb = L.kb;
-    k_lrT_premul<<<dim3(blocks_for(N, 256), kb, g.r), 256, 0, st>>>(w, L.a, L.Y, g.r, kb, nq, N);
-    HV_RT_INTERNAL(check("k_lrT_premul"));
-    HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_FORWARD),
-                               "forward FFT"));
-    k_lrT_sum<<<dim3(blocks_for(N, 256), kb), 256, 0, st>>>(L.Y, L.b, L.V, g.r, kb, N);
-    HV_RT_INTERNAL(check("k_lrT_sum"));
+    if (L.fused) {
+        HV_RT_INTERNAL(lr_fused_transpose(L, w, nq, L.V, st));
+    } else {
+        k_lrT_premul<<<dim3(blocks_for(N, 256), kb, g.r), 256, 0, st>>>(w, L.a, L.Y, g.r, kb, nq, N);
+        HV_RT_INTERNAL(check("k_lrT_premul"));
+        HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pib, (cufftComplex *)L.Y, (cufftComplex *)L.Y, CUFFT_FORWARD),
+                                   "forward FFT"));
+        k_lrT_sum<<<dim3(blocks_for(N, 256), kb), 256, 0, st>>>(L.Y, L.b, L.V, g.r, kb, N);
+        HV_RT_INTERNAL(check("k_lrT_sum"));
+    }
     HV_RT_INTERNAL(cufft_check(cufftExecC2C(L.pfb, (cufftComplex *)L.V, (cufftComplex *)L.V, CUFFT_INVERSE),
                                "inverse FFT"));
     k_real_part<<<blocks_for((size_t)nq * N, 256), 256, 0, st>>>(L.V, out, (size_t)nq * N);
@@ -337,7 +347,7 @@ int lr_apply(LrSym &L, const float *v, int k, float *out, cudaStream_t st, int o
     cudaError_t e = cudaStreamWaitEvent(st, L.done, 0);
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamWaitEvent: %s", cudaGetErrorString(e));
     HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pfb, st), "cufftSetStream"));
-    HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pib, st), "cufftSetStream"));
+    if (L.pib_ok) HV_RT_INTERNAL(cufft_check(cufftSetStream(L.pib, st), "cufftSetStream"));
     const int kb = L.kb;
     for (int j0 = 0; j0 < k; j0 += kb) {            // batches of kb vectors (the last one zero-padded)
         const int nq = std::min(kb, k - j0);

@@ -607,6 +607,11 @@ def hermitian_eig(A: np.ndarray):
     return w, V
 
 
+def set_fused_transforms(enable: bool = True) -> None:
+    """Fused low-rank-symbol transforms for approximations created afterwards (hv_set_fused_transforms)."""
+    check(_lib.load().hv_set_fused_transforms(int(bool(enable))))
+
+
 def checkpoint_schedule(nt: int, slots: int):
     """The library's checkpoint schedule: (actions[n, 3] int32, recomputed forward steps)."""
     lib = _lib.load()
