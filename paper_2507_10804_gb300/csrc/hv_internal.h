@@ -228,6 +228,7 @@ struct LrSym {
     bool pf_ok = false, pi_ok = false, pfb_ok = false, pib_ok = false;
     bool fused = false;                  // applies through the fused transforms of hv_lrfft.cu
     float2 *tw = nullptr;                // their twiddle tables: nz, then nx entries
+    void *part = nullptr;                // their partial sums over term chunks (more than 8 terms)
     cudaEvent_t done = nullptr;          // last use of the scratch
     std::mutex *mu = nullptr;
 };

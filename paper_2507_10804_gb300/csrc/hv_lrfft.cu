@@ -145,12 +145,15 @@ __global__ void __launch_bounds__(S *Split<R1, R2>::TP, R1 <= 16 ? 2 : 1) k_lrf_
 }
 
 // ---- forward apply: rows.  out_q = Re sum_k a_k (row DFT^-1 of T_k[q]), summed
-// in k order; grid (nz / S, nq); thread = s TP + t.
+// in k order over the terms of this CTA's chunk; grid (nz / S, nq, term
+// chunks); thread = s TP + t.  With one chunk the sum goes to out[q], else to
+// part[chunk][q] for k_sum_real.
 template <int R1, int R2, int S>
 __global__ void __launch_bounds__(S *Split<R1, R2>::TP) k_lrf_rows(const float2 *__restrict__ T,
                                                                    const float2 *__restrict__ A,
                                                                    const float2 *__restrict__ tw, float *__restrict__ out,
-                                                                   int r, int kb, int nz)
+                                                                   float *__restrict__ part, int r, int kb, int nz,
+                                                                   int kchunk)
 {
     constexpr int L = R1 * R2, TP = Split<R1, R2>::TP;
     __shared__ float2 sY[S][R1][R2 + 1];
@@ -160,7 +163,8 @@ __global__ void __launch_bounds__(S *Split<R1, R2>::TP) k_lrf_rows(const float2 
     float acc[R1];
 #pragma unroll
     for (int j = 0; j < R1; ++j) acc[j] = 0.0f;
-    for (int k = 0; k < r; ++k) {
+    const int k0 = blockIdx.z * kchunk, k1 = min(r, k0 + kchunk);
+    for (int k = k0; k < k1; ++k) {
         if (t < R1) {
             const float2 *Tk = T + ((size_t)k * kb + q) * N + row;
             float2 v[R2];
@@ -185,9 +189,10 @@ __global__ void __launch_bounds__(S *Split<R1, R2>::TP) k_lrf_rows(const float2 
         }
         __syncthreads();
     }
+    float *dst = gridDim.z == 1 ? out + (size_t)q * N : part + ((size_t)blockIdx.z * gridDim.y + q) * N;
     if (t < R2)
 #pragma unroll
-        for (int j = 0; j < R1; ++j) out[(size_t)q * N + row + t + R2 * j] = acc[j];
+        for (int j = 0; j < R1; ++j) dst[row + t + R2 * j] = acc[j];
 }
 
 // ---- transposed apply: rows.  T_k[q] = row DFT of conj(a_k) w_q for the terms
@@ -236,12 +241,15 @@ __global__ void __launch_bounds__(S *Split<R1, R2>::TP) k_lrt_rows(const float *
 }
 
 // ---- transposed apply: columns.  V_q = (1/N) sum_k conj(b_k) (column DFT of
-// T_k[q]), summed in k order; grid (nx / S, nq); thread = t S + s.
+// T_k[q]), summed in k order over the terms of this CTA's chunk; grid (nx / S,
+// nq, term chunks); thread = t S + s.  With one chunk the scaled sum goes to
+// V[q], else the unscaled one to part[chunk][q] for k_sum_cplx.
 template <int R1, int R2, int S>
 __global__ void __launch_bounds__(S *Split<R1, R2>::TP, R1 <= 16 ? 2 : 1) k_lrt_cols(const float2 *__restrict__ T,
                                                                    const float2 *__restrict__ B,
                                                                    const float2 *__restrict__ tw, float2 *__restrict__ V,
-                                                                   int r, int kb, int nx)
+                                                                   float2 *__restrict__ part, int r, int kb, int nx,
+                                                                   int kchunk)
 {
     constexpr int L = R1 * R2;
     __shared__ float2 sY[R1][R2][S];
@@ -251,7 +259,8 @@ __global__ void __launch_bounds__(S *Split<R1, R2>::TP, R1 <= 16 ? 2 : 1) k_lrt_
     float re[R1], im[R1];
 #pragma unroll
     for (int j = 0; j < R1; ++j) re[j] = im[j] = 0.0f;
-    for (int k = 0; k < r; ++k) {
+    const int k0 = blockIdx.z * kchunk, k1 = min(r, k0 + kchunk);
+    for (int k = k0; k < k1; ++k) {
         if (t < R1) {
             const float2 *Tk = T + ((size_t)k * kb + q) * N + (t * nx + c);
             float2 v[R2];
@@ -277,10 +286,37 @@ __global__ void __launch_bounds__(S *Split<R1, R2>::TP, R1 <= 16 ? 2 : 1) k_lrt_
         }
         __syncthreads();
     }
-    const float inv = 1.0f / (float)N;
+    const bool one = gridDim.z == 1;
+    const float inv = one ? 1.0f / (float)N : 1.0f;
+    float2 *dst = one ? V + (size_t)q * N : part + ((size_t)blockIdx.z * gridDim.y + q) * N;
     if (t < R2)
 #pragma unroll
-        for (int j = 0; j < R1; ++j) V[(size_t)q * N + (t * nx + c) + j * (R2 * nx)] = make_float2(re[j] * inv, im[j] * inv);
+        for (int j = 0; j < R1; ++j) dst[(t * nx + c) + j * (R2 * nx)] = make_float2(re[j] * inv, im[j] * inv);
+}
+
+// out[q][e] = sum_c part[c][q][e] in chunk order; grid (N / 256, nq).
+__global__ void k_sum_real(const float *__restrict__ part, float *__restrict__ out, int nc, int nq, int N)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (e >= N) return;
+    float s = 0.0f;
+    for (int c = 0; c < nc; ++c) s += part[((size_t)c * nq + q) * N + e];
+    out[(size_t)q * N + e] = s;
+}
+
+// V[q][e] = (1/N) sum_c part[c][q][e] in chunk order; grid (N / 256, nq).
+__global__ void k_sum_cplx(const float2 *__restrict__ part, float2 *__restrict__ V, int nc, int nq, int N)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x, q = blockIdx.y;
+    if (e >= N) return;
+    float re = 0.0f, im = 0.0f;
+    for (int c = 0; c < nc; ++c) {
+        const float2 v = part[((size_t)c * nq + q) * N + e];
+        re += v.x;
+        im += v.y;
+    }
+    const float inv = 1.0f / (float)N;
+    V[(size_t)q * N + e] = make_float2(re * inv, im * inv);
 }
 
 // Runs f(Split<R1, R2>{}, S-tag) for a supported length, else returns HV_ENOTSUP.
@@ -313,6 +349,7 @@ int launched(const char *what)
 }
 
 constexpr int kTermChunk = 4;   // terms per CTA in the passes that write T
+constexpr int kSumChunk = 8;    // terms per CTA in the passes that sum over the terms
 
 std::mutex g_mu;
 bool g_fused_default = true;
@@ -340,8 +377,10 @@ int lr_fused_init(LrSym &L)
     fill(h.data(), 32);
     fill(h.data() + 32, nz);
     fill(h.data() + 32 + nz, nx);
+    const int nc = (L.g.r + kSumChunk - 1) / kSumChunk;   // partial sums of the term chunks
     cudaError_t e;
     if ((e = cudaMemcpyToSymbol(c_w32, h.data(), 32 * sizeof(float2))) != cudaSuccess ||
+        (nc > 1 && (e = cudaMalloc(&L.part, (size_t)nc * L.kb * nz * nx * sizeof(float2))) != cudaSuccess) ||
         (e = cudaMalloc(&L.tw, (size_t)(nz + nx) * sizeof(float2))) != cudaSuccess ||
         (e = cudaMemcpy(L.tw, h.data() + 32, (size_t)(nz + nx) * sizeof(float2), cudaMemcpyHostToDevice)) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "fused transform tables: %s", cudaGetErrorString(e));
@@ -359,12 +398,17 @@ int lr_fused_forward(const LrSym &L, const float2 *V, int nq, float *out, cudaSt
         return launched("k_lrf_cols");
     });
     if (rc != HV_OK) return rc;
-    return with_split(g.nx, [&](auto r1, auto r2, auto sz) -> int {
+    const int nc = (g.r + kSumChunk - 1) / kSumChunk, N = g.nz * g.nx;
+    float *part = reinterpret_cast<float *>(L.part);
+    rc = with_split(g.nx, [&](auto r1, auto r2, auto sz) -> int {
         constexpr int R1 = decltype(r1)::value, R2 = decltype(r2)::value, S = decltype(sz)::value;
-        k_lrf_rows<R1, R2, S><<<dim3(g.nz / S, nq), S * Split<R1, R2>::TP, 0, st>>>(L.Y, L.a, twx, out, g.r, L.kb,
-                                                                                   g.nz);
+        k_lrf_rows<R1, R2, S><<<dim3(g.nz / S, nq, nc), S * Split<R1, R2>::TP, 0, st>>>(L.Y, L.a, twx, out, part,
+                                                                                       g.r, L.kb, g.nz, kSumChunk);
         return launched("k_lrf_rows");
     });
+    if (rc != HV_OK || nc == 1) return rc;
+    k_sum_real<<<dim3((N + 255) / 256, nq), 256, 0, st>>>(part, out, nc, nq, N);
+    return launched("k_sum_real");
 }
 
 int lr_fused_transpose(const LrSym &L, const float *w, int nq, float2 *V, cudaStream_t st)
@@ -378,12 +422,17 @@ int lr_fused_transpose(const LrSym &L, const float *w, int nq, float2 *V, cudaSt
         return launched("k_lrt_rows");
     });
     if (rc != HV_OK) return rc;
-    return with_split(g.nz, [&](auto r1, auto r2, auto sz) -> int {
+    const int nc = (g.r + kSumChunk - 1) / kSumChunk, N = g.nz * g.nx;
+    float2 *part = reinterpret_cast<float2 *>(L.part);
+    rc = with_split(g.nz, [&](auto r1, auto r2, auto sz) -> int {
         constexpr int R1 = decltype(r1)::value, R2 = decltype(r2)::value, S = decltype(sz)::value;
-        k_lrt_cols<R1, R2, S><<<dim3(g.nx / S, nq), S * Split<R1, R2>::TP, 0, st>>>(L.Y, L.b, twz, V, g.r, L.kb,
-                                                                                   g.nx);
+        k_lrt_cols<R1, R2, S><<<dim3(g.nx / S, nq, nc), S * Split<R1, R2>::TP, 0, st>>>(L.Y, L.b, twz, V, part,
+                                                                                       g.r, L.kb, g.nx, kSumChunk);
         return launched("k_lrt_cols");
     });
+    if (rc != HV_OK || nc == 1) return rc;
+    k_sum_cplx<<<dim3((N + 255) / 256, nq), 256, 0, st>>>(part, V, nc, nq, N);
+    return launched("k_sum_cplx");
 }
 
 }  // namespace hvk

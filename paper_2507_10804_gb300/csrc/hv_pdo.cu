@@ -267,6 +267,7 @@ void lr_destroy(LrSym &L)
     cudaFree(L.V);
     cudaFree(L.T);
     cudaFree(L.tw);
+    cudaFree(L.part);
     delete L.mu;
     L = LrSym{};
 }
