@@ -49,6 +49,23 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
+// b = w v for the twiddle w = exp(-+2 pi i m / 32) of a radix-2 butterfly; m is
+// a constant once the loops are unrolled, so the multiplications by 1, -+i and
+// the odd multiples of pi / 4 reduce to sign changes, swaps and one scale.
+template <bool INV>
+__device__ __forceinline__ float2 twiddle32(int m, float2 x)
+{
+    constexpr float c = 0.70710678118654752f;   // 1 / sqrt(2)
+    if (m == 0) return x;
+    if (m == 8) return INV ? make_float2(-x.y, x.x) : make_float2(x.y, -x.x);
+    if (m == 4) return INV ? make_float2(c * (x.x - x.y), c * (x.x + x.y)) : make_float2(c * (x.x + x.y), c * (x.y - x.x));
+    if (m == 12)
+        return INV ? make_float2(-c * (x.x + x.y), c * (x.x - x.y)) : make_float2(c * (x.y - x.x), -c * (x.x + x.y));
+    float2 w = c_w32[m];
+    if (INV) w.y = -w.y;
+    return cmul(w, x);
+}
+
 // In-register DFT of length R (2..32): radix-2 decimation in time after a
 // bit-reversal permutation; INV conjugates the twiddles.
 template <int R, bool INV>
@@ -69,9 +86,8 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R])
         for (int g = 0; g < R; g += 2 * half) {
 #pragma unroll
             for (int p = 0; p < half; ++p) {
-                float2 w = c_w32[p * (16 / half)];   // exp(-2 pi i p / (2 half))
-                if (INV) w.y = -w.y;
-                const float2 a = v[g + p], b = cmul(w, v[g + p + half]);
+                // exp(-2 pi i p / (2 half)) v = W_32^(p 16 / half) v
+                const float2 a = v[g + p], b = twiddle32<INV>(p * (16 / half), v[g + p + half]);
                 v[g + p] = make_float2(a.x + b.x, a.y + b.y);
                 v[g + p + half] = make_float2(a.x - b.x, a.y - b.y);
             }
