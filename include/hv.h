@@ -548,7 +548,9 @@ int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *in
  *    groups per CTA} of entry `index` (HV_EINVAL past the end or info NULL).
  *  - hv_autotune: times every entry for the three kernels on this handle's
  *    grid with k vectors, using `ws` (at least hv_workspace_size(HV_OP_HV, k,
- *    ckpt = 1) bytes; contents overwritten) on `stream`, keeps the fastest
+ *    ckpt = 1) bytes; contents overwritten) on `stream`, the timed launches'
+ *    fields rotating through the workspace's batches as in a sweep (each
+ *    launch reads what the previous one wrote), keeps the fastest
  *    in the handle and writes the choice to chosen[3] and the per-launch
  *    times to ms[menu * 3] (either may be NULL).  Synchronous.  In the
  *    dataflow launch mode the three choices share one tile shape (the shape
