@@ -25,6 +25,12 @@ def test_library_exports_every_header_symbol(lib):
     assert lib.hv_version() >= 100
 
 
+def test_fused_transform_switch_is_host_only(lib):
+    """The process-wide default for new approximations is set without touching a GPU."""
+    assert lib.hv_set_fused_transforms(0) == 0
+    assert lib.hv_set_fused_transforms(1) == 0
+
+
 def simulate(actions, nt, slots):
     """Replay a schedule: every adjoint step exactly once in reverse order, each
     with u^n available; snapshot slots within budget and never clobbered while in use."""
