@@ -168,6 +168,60 @@ int hv_hessian_apply(hv_handle *h, const float *m, const float *v, int k, float 
 int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k, double *Hv, int ckpt,
                             void *ws, size_t ws_bytes, void *stream);
 
+/* Merged calls on one model: Hessian applies, misfit gradients and misfits
+ * at the same m (the quantities sections 2.1-2.3 ask for: an optimiser's
+ * gradient and Gauss-Newton products, an MCMC chain's misfit) share one
+ * forward sweep.  The H v vectors of all entries and one vector per gradient
+ * run as one batch of Born vectors; a gradient's vector is zero (its Born
+ * field stays zero) and its adjoint source is the residual f(m) - d_obs
+ * instead of Born data; misfits are reduced from the forward data.  Every
+ * output is bitwise what the separate call gives (hv_hessian_apply per entry,
+ * hv_misfit_grad, hv_misfit).
+ *  - hv_batch: HOST arrays of DEVICE pointers.  Entry i of n_hv: v[i]
+ *    [k[i]][nz][nx] -> Hv[i] [k[i]][nz][nx]; gradient g of n_grad:
+ *    grad_dobs[g] [ns][nt][nr] -> grad_phi[g] (device double), grad[g]
+ *    [nz][nx]; misfit q of n_misfit: misfit_dobs[q] -> misfit_phi[q].  At
+ *    least one entry in all; sum k[i] + n_grad <= 65535.
+ *  - hv_batch_workspace_size: bytes of `ws` hv_apply_batch needs for this
+ *    batch shape and checkpoint budget.
+ *  - hv_apply_batch: enqueues the batch on `stream` (no CUDA graph).  The
+ *    library's request server merges queued requests on one problem and
+ *    model into such calls. */
+typedef struct hv_batch {
+    int n_hv;
+    const float *const *v;
+    const int *k;
+    float *const *Hv;
+    int n_grad;
+    const float *const *grad_dobs;
+    double *const *grad_phi;
+    float *const *grad;
+    int n_misfit;
+    const float *const *misfit_dobs;
+    double *const *misfit_phi;
+} hv_batch;
+int hv_batch_workspace_size(const hv_handle *h, const hv_batch *b, int ckpt, size_t *bytes);
+int hv_apply_batch(hv_handle *h, const float *m, const hv_batch *b, int ckpt, void *ws, size_t ws_bytes, void *stream);
+
+/* The Hessian apply split over sources (section 3: H_d v is a sum over
+ * sources of two wave solves each; eq. (grad) sums the imaging over
+ * sources), for one process per GPU, each owning a block of shots:
+ *  - hv_hessian_apply_partial: the extended image of this handle's shots,
+ *    before the fold E^T: ext[k][NZ][NX] (DEVICE doubles, padded grid NZ =
+ *    nz + 2 nb, NX = nx + 2 nb, x fastest) = G^T S^-T P^T Gamma^-1 P S^-1 G E v
+ *    restricted to the handle's shots, i.e. 2 / (m_ext h^2) sum_s sum_n
+ *    lam_s^n (L_h u_s^n + s_n) with the shot groups summed in FP64.  Same
+ *    workspace (HV_OP_HV), arguments and checkpointing as hv_hessian_apply.
+ *  - hv_image_fold: out[k][nz][nx] = E^T ext (the sponge nodes added onto
+ *    their nearest interior nodes, FP64 sums), written as float (out) and/or
+ *    double (out64); either may be NULL, not both.  Any handle of the same
+ *    grid may fold.
+ * The ranks' extended images summed in a fixed rank order, then folded once,
+ * give H_d v of all shots (to FP64 rounding of the order of the sums). */
+int hv_hessian_apply_partial(hv_handle *h, const float *m, const float *v, int k, double *ext, int ckpt,
+                             void *ws, size_t ws_bytes, void *stream);
+int hv_image_fold(hv_handle *h, const double *ext, int k, float *out, double *out64, void *stream);
+
 /* Allocation-free Gauss-Newton Hessian apply.  The paper has no counterpart;
  * this entry point exists for callers that cannot allocate device memory
  * where they call it (an application that owns every byte of device memory
@@ -186,22 +240,49 @@ int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k,
  *    104 x 104 padded grid, 1 shot, 600 steps, k = 1, with every time level
  *    stored).
  *  - The first call on a device looks up the array's device address
- *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
+ *    (cudaGetSymbolAddress) with that device current.
+ *  - Never call it while `stream` is being captured into a CUDA graph: it
+ *    copies its tables from host memory that is freed when it returns, so it
+ *    returns HV_EINVAL under capture.
  *  - Every call shares the one array and overwrites the previous call's
  *    contents (whatever must start at zero is cleared on each call): calls
  *    that may overlap on the GPU (different streams, different host threads
  *    on the same device) race and must be serialised by the caller.
- *  - Asynchronous on `stream` like the other compute calls. */
+ *  - It runs tile configuration 0 for every kernel kind and the default
+ *    (programmatic dependent launch) ordering, so its results are bitwise
+ *    those of hv_hessian_apply with the same settings (and of any tiles).
+ *  - Asynchronous on `stream` like the other compute calls.
+ *  - hv_static_status reports a bounded device wait that ran out in any
+ *    call since it was last read: it synchronises the device, writes HV_OK
+ *    or HV_ETIMEOUT (the outputs of those calls are then invalid) and clears
+ *    the word, which sits at the start of the array. */
 #define HV_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
 int hv_hessian_apply_static(const hv_grid *grid, const hv_acq *acq, const float *m, const float *v, int k,
                             float *Hv, int ckpt, void *stream);
+int hv_static_status(int *device_status);
 
 /* Device status of the handle's kernels since the last call of hv_status:
- * HV_OK, or HV_ETIMEOUT if a bounded on-device wait (for a bulk tile copy)
- * ran out and the kernel returned early (its outputs are then invalid).
- * Synchronises the device, then clears the status. */
+ * HV_OK, or HV_ETIMEOUT if a bounded on-device wait (for a bulk tile copy, or
+ * in the dataflow launch mode for the neighbouring tiles of an earlier step)
+ * ran out and the kernel returned early (the outputs of the calls since the
+ * last hv_status are then invalid).  Synchronises the device, then clears the
+ * status. */
 int hv_status(hv_handle *h, int *device_status);
+
+/* Limit of every bounded wait inside the handle's stencil kernels, in seconds
+ * (default 2; 1e-4 <= seconds <= 60, else HV_EINVAL).  A wait that runs out
+ * sets the device status (hv_status) and the CTA returns without leaving a
+ * copy in flight.  Applies to calls enqueued afterwards. */
+int hv_set_wait_limit(hv_handle *h, double seconds);
+
+/* Testing the timeout path without a fault: the next stencil step that the
+ * dataflow launch mode orders by tile counters (HV_LAUNCH_DATAFLOW, see
+ * hv_set_launch_mode) waits for a count that no step reaches.  Its CTAs wait
+ * out the limit before they issue any copy, the first one sets HV_ETIMEOUT,
+ * and every later wait of the call gives up at once on seeing the status;
+ * the call's outputs are invalid and hv_status reports HV_ETIMEOUT.  One-shot:
+ * cleared when a step takes it.  No effect in the other launch modes. */
+int hv_inject_wait_timeout(hv_handle *h);
 
 /* Hessian approximations built from batched H v.
  *
@@ -434,7 +515,11 @@ int hv_quad_destroy(hv_quad *q);
  * borrowed, it must outlive the posterior) or H~_d = 0 (approx NULL), plus an
  * optional low-rank correction, H~ = H0 + H0 V Lambda V^T H0.
  *  - hv_posterior_create: on the current device; HV_EINVAL for an approx that
- *    is not a square-root form or lives on another grid or device.
+ *    is not a square-root form or lives on another grid or device, or for
+ *    max_k outside 1..256.  All device memory the object needs is allocated
+ *    here, sized for calls of at most max_k fields (solves, applies, samples
+ *    and correction test vectors; a correction's rank is at most max_k):
+ *    the calls below allocate nothing and return HV_EINVAL for a larger k.
  *  - hv_posterior_solve: x = (Op + R)^-1 b for k fields, Op = the caller's
  *    operator or, if op is NULL, H~_d (so H0 x = b; the correction is not
  *    included).  Preconditioned conjugate gradients (preconditioner R^-1),
@@ -466,14 +551,14 @@ int hv_quad_destroy(hv_quad *q);
  *  - hv_gpcn_propose: m_new[c] = m_map + sqrt(1 - beta^2)(m[c] - m_map) +
  *    beta zeta[c] and, unless d_new is NULL, d_new[c] = m_new[c] - m_map;
  *    0 < beta < 1.
- *  - hv_gpcn_accept: Delta' = phi_new[c] - 1/2 d_new[c] . Hd_new[c] (FP64;
+ *  - hv_gpcn_accept (allocates nothing): Delta' = phi_new[c] - 1/2 d_new[c] . Hd_new[c] (FP64;
  *    Hd_new = H~ d_new, e.g. by hv_posterior_apply); the proposal is accepted
  *    iff log_u[c] < delta_cur[c] - Delta', u ~ U(0, 1) drawn by the caller,
  *    i.e. with probability min(1, exp(Delta(m_k) - Delta(m'))); then m[c] <-
  *    m_new[c] and delta_cur[c] <- Delta'.  accepted[c] = 1 or 0.  log_u = -inf
  *    accepts unconditionally (initialises delta_cur). */
 typedef struct hv_posterior hv_posterior;
-int hv_posterior_create(int nz, int nx, double h, double delta, double gamma, const hv_approx *approx,
+int hv_posterior_create(int nz, int nx, double h, double delta, double gamma, const hv_approx *approx, int max_k,
                         hv_posterior **out);
 int hv_posterior_solve(hv_posterior *p, const hv_operator *op, const float *b, int k, float *x, double rtol,
                        int max_iter, int *iters, void *stream);
@@ -498,7 +583,8 @@ int hv_gpcn_accept(int n, int c, const double *phi_new, const float *m_new, cons
  * later request pass one that is waiting for memory, whenever a stream is free
  * and the request's workspace fits in the arena, and runs each on its own
  * stream, so the work of requests that arrive while others run overlaps on
- * the GPU.  Results are bitwise the same as the direct calls.  Inputs and
+ * the GPU; queued requests on one problem and model are merged into one call
+ * (hv_server_set_batching).  Results are bitwise the same as the direct calls.  Inputs and
  * outputs are caller-owned device buffers that must stay valid until the
  * request is done.  Request status: HV_REQ_QUEUED, HV_REQ_RUNNING, HV_OK when
  * done, or an HV_E* code. */
@@ -525,7 +611,8 @@ typedef struct hv_request {
 typedef struct hv_request_info {
     int kind, status;
     double t_submit, t_start, t_done;   /* seconds since the server started        */
-    size_t ws_bytes;                     /* arena bytes the request held             */
+    size_t ws_bytes;                     /* arena bytes the request held (alone)     */
+    int batch;                           /* requests that ran merged with it (1: alone) */
 } hv_request_info;
 int hv_server_create(size_t hbm_budget, int max_concurrent, hv_server **out);
 /* Stops admitting, waits (bounded by timeout_s) for running requests, frees the arena. */
@@ -535,6 +622,14 @@ int hv_poll(hv_server *s, unsigned long long id, int *status);
 /* Waits until the request is done or failed; HV_ETIMEOUT after timeout_s. */
 int hv_wait(hv_server *s, unsigned long long id, double timeout_s, int *status);
 int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *info);
+/* Continuous batching: when the scheduler admits an H v, gradient or misfit
+ * request, the queued requests on the same problem and model (H v and
+ * gradients with the same checkpoint budget) join it, up to max_vectors Born
+ * vectors in all (a gradient counts as one, a misfit as none), and run as one
+ * hv_apply_batch on one stream and one arena block, if that fits; their
+ * results are bitwise those of separate calls.  max_vectors < 2 turns merging
+ * off (each request runs alone).  Default 64.  Applies to later admissions. */
+int hv_server_set_batching(hv_server *s, int max_vectors);
 
 /* Tile configurations.  The stencil kernels come in a small menu of
  * configurations: a tile shape (TX x TZ points per CTA), a copy-pipeline depth
@@ -614,6 +709,20 @@ int hv_set_step_fusion(hv_handle *h, int enable);
  * size (hv_workspace_size) depends on the setting.  Off by default. */
 int hv_set_resident(hv_handle *h, int enable);
 int hv_resident_fits(const hv_handle *h);
+
+/* Precision of the zero-lag imaging sum (section 3, the sum over time steps
+ * and sources of the Hessian action and the gradient).
+ *  - HV_IMAGE_PAIRS (default): per step, a CTA sums the products lam^n Q^n of
+ *    the (at most 8) shots of its shot group in FP32 in shot order and adds
+ *    that sum to the group's image held as a double-float pair (hi, lo) of
+ *    FP32 values by an error-free TwoSum; the groups are summed in FP64.
+ *  - HV_IMAGE_FP64: a check of the default's rounding: every shot's product,
+ *    exact in FP64, is added to an FP64 image of its group in every step
+ *    (a slower adjoint on a fixed 64 x 8 tile; not with the resident kernels).
+ * Applies to calls enqueued afterwards; HV_EINVAL for another mode. */
+#define HV_IMAGE_PAIRS 0
+#define HV_IMAGE_FP64 1
+int hv_set_image_precision(hv_handle *h, int mode);
 
 #define HV_LAUNCH_PLAIN 0
 #define HV_LAUNCH_PDL 1

@@ -541,6 +541,29 @@ int or_hessian_apply(const or_problem *P, const double *m, int k, const double *
     return rc;
 }
 
+/* The extended image before the fold E^T: ext[j] = sum over shots (in shot
+ * order) of G^T S^-T P^T Gamma^-1 P S^-1 G E v[j] on the padded grid, so that
+ * or_fold(ext[j]) is or_hessian_apply's Hv[j] (section 3, the sum over sources). */
+int or_hessian_image(const or_problem *P, const double *m, int k, const double *v, double *ext, int nthreads)
+{
+    size_t N = (size_t)NZ_(P) * NX_(P);
+    double *mext = extend_new(P, m);
+    double *vext = malloc(sizeof(double) * N * k);
+    for (int j = 0; j < k; ++j) or_extend(P, v + (size_t)j * P->nz * P->nx, vext + (size_t)j * N);
+    double *imgs = malloc(sizeof(double) * N * k * P->ns);
+    job J = {.P = P, .kind = JOB_HV, .mext = mext, .in = vext, .k = k, .out = imgs};
+    int rc = run_job(&J, nthreads);
+    if (rc == 0)
+        for (int j = 0; j < k; ++j) {
+            double *acc = ext + (size_t)j * N;
+            memset(acc, 0, sizeof(double) * N);
+            for (int s = 0; s < P->ns; ++s)
+                for (size_t p = 0; p < N; ++p) acc[p] += imgs[((size_t)s * k + j) * N + p];
+        }
+    free(mext); free(vext); free(imgs);
+    return rc;
+}
+
 /* Raw solves on the padded grid for the operator-level dot test
  * <S^{-1} F, G> = <F, S^{-T} G>: F, G, U, Lam are [nt][NZ*NX]. */
 int or_solve_S(const or_problem *P, const double *m, const double *F, double *U)

@@ -17,6 +17,8 @@ writes out the plain definitions of the paper's operators:
 * ``hessian_apply`` -- H_d v = F^T Gamma^{-1} F v, the matrix-free
                        Gauss-Newton Hessian action of section 3 ("two wave
                        equations per source", the forward field a third).
+* ``hessian_image`` -- the same before the fold E^T: the sum over the
+                       problem's sources of their extended images.
 * ``wavefield``, ``solve_S``, ``solve_ST`` -- raw solves for the wavefield and
                        operator-level checks.
 
@@ -89,6 +91,7 @@ def _load():
             "or_adjoint": [pp, dp, dp, dp, ctypes.c_int],
             "or_misfit_grad": [pp, dp, dp, dp, dp, ctypes.c_int],
             "or_hessian_apply": [pp, dp, ctypes.c_int, dp, dp, ctypes.c_int],
+            "or_hessian_image": [pp, dp, ctypes.c_int, dp, dp, ctypes.c_int],
             "or_solve_S": [pp, dp, dp, dp],
             "or_solve_ST": [pp, dp, dp, dp],
         }.items():
@@ -266,6 +269,19 @@ def hessian_apply(P: Problem, m, v, nthreads=None) -> np.ndarray:
     _check(_load().or_hessian_apply(ctypes.byref(c), _d(m), k, _d(v3), _d(out), _threads(nthreads)),
            "hessian_apply")
     return out.reshape(v_in.shape)
+
+
+def hessian_image(P: Problem, m, v, nthreads=None) -> np.ndarray:
+    """The extended image before the fold: [k, NZ, NX] with fold(P, ext[j]) == hessian_apply(P, m, v)[j]
+    (the per-shot images of section 3 summed over the problem's shots in shot order)."""
+    m = _f64(m)
+    v3 = _f64(v).reshape(-1, P.nz, P.nx)
+    k = v3.shape[0]
+    out = np.empty((k, P.NZ, P.NX))
+    c = P._c()
+    _check(_load().or_hessian_image(ctypes.byref(c), _d(m), k, _d(v3), _d(out), _threads(nthreads)),
+           "hessian_image")
+    return out
 
 
 def solve_S(P: Problem, m, F) -> np.ndarray:

@@ -23,6 +23,7 @@ HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD, HV_
 HV_K_FWD, HV_K_ADVANCE, HV_K_ADJ, HV_K_OTHER = range(4)
 HV_K_COUNT = 4
 HV_LAUNCH_PLAIN, HV_LAUNCH_PDL, HV_LAUNCH_DATAFLOW = range(3)
+HV_IMAGE_PAIRS, HV_IMAGE_FP64 = 0, 1
 
 
 class HvGrid(ctypes.Structure):
@@ -42,7 +43,14 @@ class HvRequest(ctypes.Structure):
 
 class HvRequestInfo(ctypes.Structure):
     _fields_ = [("kind", c_int), ("status", c_int), ("t_submit", c_double), ("t_start", c_double),
-                ("t_done", c_double), ("ws_bytes", c_size_t)]
+                ("t_done", c_double), ("ws_bytes", c_size_t), ("batch", c_int)]
+
+
+class HvBatch(ctypes.Structure):
+    _fields_ = [("n_hv", c_int), ("v", ctypes.POINTER(c_void_p)), ("k", ctypes.POINTER(c_int)),
+                ("Hv", ctypes.POINTER(c_void_p)), ("n_grad", c_int), ("grad_dobs", ctypes.POINTER(c_void_p)),
+                ("grad_phi", ctypes.POINTER(c_void_p)), ("grad", ctypes.POINTER(c_void_p)), ("n_misfit", c_int),
+                ("misfit_dobs", ctypes.POINTER(c_void_p)), ("misfit_phi", ctypes.POINTER(c_void_p))]
 
 
 HV_OP_FN = ctypes.CFUNCTYPE(c_int, c_void_p, fp, c_int, fp, c_void_p)
@@ -70,9 +78,14 @@ _SIGS = {
     "hv_misfit_grad": ([c_void_p, fp, fp, fp, fp, c_int, fp, c_size_t, c_void_p], c_int),
     "hv_hessian_apply": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
     "hv_hessian_apply_f64out": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_hessian_apply_partial": ([c_void_p, fp, fp, c_int, fp, c_int, fp, c_size_t, c_void_p], c_int),
+    "hv_image_fold": ([c_void_p, fp, c_int, fp, fp, c_void_p], c_int),
     "hv_hessian_apply_static": ([ctypes.POINTER(HvGrid), ctypes.POINTER(HvAcq), fp, fp, c_int, fp, c_int,
                                  c_void_p], c_int),
     "hv_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
+    "hv_static_status": ([ctypes.POINTER(c_int)], c_int),
+    "hv_set_wait_limit": ([c_void_p, c_double], c_int),
+    "hv_inject_wait_timeout": ([c_void_p], c_int),
     "hv_misfit": ([c_void_p, fp, fp, fp, fp, c_size_t, c_void_p], c_int),
     "hv_server_create": ([c_size_t, c_int, ctypes.POINTER(c_void_p)], c_int),
     "hv_server_destroy": ([c_void_p, c_double], c_int),
@@ -80,6 +93,9 @@ _SIGS = {
     "hv_poll": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(c_int)], c_int),
     "hv_wait": ([c_void_p, ctypes.c_ulonglong, c_double, ctypes.POINTER(c_int)], c_int),
     "hv_request_get_info": ([c_void_p, ctypes.c_ulonglong, ctypes.POINTER(HvRequestInfo)], c_int),
+    "hv_server_set_batching": ([c_void_p, c_int], c_int),
+    "hv_batch_workspace_size": ([c_void_p, ctypes.POINTER(HvBatch), c_int, ctypes.POINTER(c_size_t)], c_int),
+    "hv_apply_batch": ([c_void_p, fp, ctypes.POINTER(HvBatch), c_int, fp, c_size_t, c_void_p], c_int),
     "hv_approx_psf_workspace_size": ([c_void_p, c_int, c_int, ctypes.POINTER(c_size_t)], c_int),
     "hv_approx_build_psf": ([c_void_p, fp, c_int, c_int, c_int, ctypes.POINTER(c_void_p), fp, c_size_t, c_void_p],
                             c_int),
@@ -113,7 +129,8 @@ _SIGS = {
     "hv_quad_operator": ([c_void_p, ctypes.POINTER(HvOperator)], c_int),
     "hv_quad_destroy": ([c_void_p], c_int),
     "hv_approx_destroy": ([c_void_p], c_int),
-    "hv_posterior_create": ([c_int, c_int, c_double, c_double, c_double, c_void_p, ctypes.POINTER(c_void_p)], c_int),
+    "hv_posterior_create": ([c_int, c_int, c_double, c_double, c_double, c_void_p, c_int, ctypes.POINTER(c_void_p)],
+                            c_int),
     "hv_posterior_solve": ([c_void_p, ctypes.POINTER(HvOperator), fp, c_int, fp, c_double, c_int, ip, c_void_p],
                            c_int),
     "hv_posterior_apply": ([c_void_p, fp, c_int, fp, c_void_p], c_int),
@@ -130,6 +147,7 @@ _SIGS = {
     "hv_set_step_fusion": ([c_void_p, c_int], c_int),
     "hv_set_fused_transforms": ([c_int], c_int),
     "hv_set_resident": ([c_void_p, c_int], c_int),
+    "hv_set_image_precision": ([c_void_p, c_int], c_int),
     "hv_resident_fits": ([c_void_p], c_int),
     "hv_tile_menu": ([c_int, ip, ip], c_int),
     "hv_tile_menu_info": ([c_int, ip], c_int),

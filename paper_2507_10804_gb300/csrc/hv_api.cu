@@ -4,6 +4,8 @@
 // plus the forward field; section 2.1, eq. (grad): misfit gradient).
 #include "hv_internal.h"
 
+#include <functional>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -139,7 +141,7 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
     const size_t ndata = (size_t)h->ns * h->nt * h->nr;
     if (op == HV_OP_HV) L.dd = take((size_t)k * ndata * sizeof(float));
     if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.dd = take(ndata * sizeof(float));
-    L.resident = op == HV_OP_HV && L.history && h->resident && hvk::resident_fits(h);
+    L.resident = op == HV_OP_HV && L.history && h->resident && !h->img_f64 && hvk::resident_fits(h);
     if (adjoint) L.img = take((size_t)(L.resident ? h->ns : L.G) * k * h->fsize * sizeof(double));
     if (op == HV_OP_GRAD || op == HV_OP_MISFIT) L.part = take(kResidualBlocks * sizeof(double));
     L.cnt_bytes = (size_t)hvk::adj_groups(h) * hvk::max_tiles(h) * sizeof(int);
@@ -222,9 +224,15 @@ struct Exec {
         d.need = need;
         d.flow = cnt != nullptr && last_tl == hvk::thread_launches();
         need += items;
+        if (d.flow && h->inject_wait) {   // testing the timeout path: a count no step reaches
+            d.need += 1 << 24;
+            h->inject_wait = false;
+        }
         return d;
     }
     void launched_step() { last_tl = hvk::thread_launches(); }
+    // The adjoint's tile configuration: the FP64-image check has one of its own.
+    int adj_cfg() const { return h->img_f64 ? hvk::adj_f64_cfg() : h->cfg[2]; }
 
     float *batch(char *base, size_t i) const { return reinterpret_cast<float *>(base + i * L.fb); }
     float *Dbuf(int parity) const { return reinterpret_cast<float *>(reinterpret_cast<char *>(D) + (size_t)parity * k * L.fb); }
@@ -255,7 +263,7 @@ struct Exec {
         cur = prev = zero;
         cur_i = prev_i = -1;
         j = 0;
-        const hvi::Tiling t0 = hvk::tiling(h, h->cfg[0]), t1 = hvk::tiling(h, h->cfg[1]), t2 = hvk::tiling(h, h->cfg[2]);
+        const hvi::Tiling t0 = hvk::tiling(h, h->cfg[0]), t1 = hvk::tiling(h, h->cfg[1]), t2 = hvk::tiling(h, adj_cfg());
         const bool one_tiling = t0.TX == t1.TX && t0.TX == t2.TX && t0.TZ == t1.TZ && t0.TZ == t2.TZ;
         if (h->launch_mode == HV_LAUNCH_DATAFLOW && one_tiling) {
             cnt = reinterpret_cast<int *>(ws + L.cnt);
@@ -368,11 +376,12 @@ struct Exec {
         a.r_per_vector = r_per_vector;
         a.rscale = rscale;
         a.img = img;
+        a.img_f64 = h->img_f64;
         a.n = n;
         a.k = kk;
         a.G = L.G;
         a.deps = deps(kk);
-        HV_RT(hvk::launch_adj(h, h->cfg[2], rectiles_for(h, hvk::tiling(h, h->cfg[2])), maps, a, st));
+        HV_RT(hvk::launch_adj(h, adj_cfg(), rectiles_for(h, hvk::tiling(h, adj_cfg())), maps, a, st));
         launched_step();
         return HV_OK;
     }
@@ -424,15 +433,23 @@ const std::vector<hvi::Action> *schedule_for(hv_handle *h, int slots)
     return &r.first->second;
 }
 
+// Extra work of a merged call (hv_apply_batch): the forward data are sampled
+// into fwd_data during the first sweep and after_sweep runs (the residuals
+// of the gradient slots, which overwrite those slots' Born data, and the misfits).
+struct BatchExtra {
+    float *fwd_data = nullptr;
+    std::function<int(cudaStream_t)> after_sweep;
+};
 int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
-                     const Layout &L, cudaStream_t st);
+                     const Layout &L, cudaStream_t st, const BatchExtra *bx = nullptr);
 int run_resident_hv(hv_handle *h, int kk, void *ws, const Layout &L, cudaStream_t st);
 
-std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode, bool fuse, bool res)
+std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *cfg, int mode, bool fuse, bool res,
+                      unsigned long long wait_ns)
 {
-    char buf[176];
-    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d/%d/%d", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode,
-             (int)fuse, (int)res);
+    char buf[208];
+    snprintf(buf, sizeof(buf), "%p/%zu/%d/%d/%d.%d.%d/%d/%d/%d/%llu", ws, bytes, k, ckpt, cfg[0], cfg[1], cfg[2], mode,
+             (int)fuse, (int)res, wait_ns);
     return buf;
 }
 
@@ -441,7 +458,7 @@ std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *
 //   kind 1: gradient  r = f(m) - d_obs (computed),           scale h^2 / sigma^2
 //   kind 2: H v       r = F v (Born data, computed),         scale h^2 / sigma^2
 int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, float *out32, double *out64,
-                double *phi, int ckpt, void *ws, size_t ws_bytes, cudaStream_t st)
+                double *phi, int ckpt, void *ws, size_t ws_bytes, cudaStream_t st, double *ext = nullptr)
 {
     const int op = kind == 0 ? HV_OP_MIGRATE : (kind == 1 ? HV_OP_GRAD : HV_OP_HV);
     Layout L;
@@ -456,9 +473,12 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     // Everything between the model preparation and the final fold touches only
     // the workspace and the handle, so for H v it can be captured once as a
     // CUDA graph and replayed (hv_set_graphs).
-    const bool graph = born && h->graphs_on && !h->prof_on;
+    // (A pending wait-timeout injection runs eagerly: a graph would keep it.)
+    const bool graph = born && h->graphs_on && !h->prof_on && !h->inject_wait;
     if (graph) {
-        const std::string key = graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode, h->fuse_steps, L.resident);
+        const std::string key =
+            graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode + 16 * (int)h->img_f64, h->fuse_steps, L.resident,
+                      h->wait_ns);
         auto it = h->graphs.find(key);
         if (it == h->graphs.end()) {
             cudaStream_t cs = h->capture_stream;
@@ -483,7 +503,11 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
     }
     {
         ProfScope ps(h, st, HV_K_OTHER);
-        HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>((char *)ws + L.img), L.resident ? h->ns : L.G, kk,
+        const int fmt = h->img_f64 && !L.resident ? hvk::kImgF64 : hvk::kImgPairs;
+        if (ext)   // the extended image of this handle's shots, not folded (hv_hessian_apply_partial)
+            return hvk::launch_partial_image(h, m, reinterpret_cast<double *>((char *)ws + L.img), fmt,
+                                             L.resident ? h->ns : L.G, kk, ext, st);
+        HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>((char *)ws + L.img), fmt, L.resident ? h->ns : L.G, kk,
                                    out32, out64, st));
     }
     return HV_OK;
@@ -518,10 +542,10 @@ int run_resident_hv(hv_handle *h, int kk, void *ws, const Layout &L, cudaStream_
 
 // The part of run_adjoint between preparation and fold (all on `st`).
 int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *phi, int ckpt, void *ws,
-                     const Layout &L, cudaStream_t st)
+                     const Layout &L, cudaStream_t st, const BatchExtra *bx)
 {
     (void)ckpt;
-    if (L.resident) return run_resident_hv(h, kk, ws, L, st);
+    if (L.resident && !bx) return run_resident_hv(h, kk, ws, L, st);
     Exec E;
     HV_RT(E.init(h, st, L, ws, kk));
     const bool born = (kind == 2);
@@ -539,7 +563,8 @@ int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *ph
             const hvi::Action &a = (*sched)[ai++];
             if (a.op != hvi::ACT_FORWARD || a.a0 != n) return hvi::fail(HV_EINVAL, "internal: schedule order");
         }
-        HV_RT(E.forward(n, born, kind == 1 ? dd : nullptr, kind == 2 ? dd : nullptr, target));
+        float *d_u = bx ? bx->fwd_data : (kind == 1 ? dd : nullptr);
+        HV_RT(E.forward(n, born, d_u, kind == 2 ? dd : nullptr, target));
         if (sched && ai < sched->size() && (*sched)[ai].op == hvi::ACT_SAVE) HV_RT(E.save((*sched)[ai++].a0));
     }
     // ---- adjoint sources
@@ -554,6 +579,10 @@ int run_adjoint_body(hv_handle *h, int kind, const float *in, int kk, double *ph
         r = dd;
         rscale = (float)(h->h * h->h / (h->sigma * h->sigma));
     } else if (kind == 2) {
+        if (bx && bx->after_sweep) {
+            ProfScope ps(h, st, HV_K_OTHER);
+            HV_RT(bx->after_sweep(st));
+        }
         r = dd;
         r_per_vector = 1;
         rscale = (float)(h->h * h->h / (h->sigma * h->sigma));
@@ -821,6 +850,168 @@ extern "C" int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float
     return run_adjoint(h, 2, m, v, k, nullptr, Hv, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
 }
 
+extern "C" int hv_hessian_apply_partial(hv_handle *h, const float *m, const float *v, int k, double *ext, int ckpt,
+                                        void *ws, size_t ws_bytes, void *stream)
+{
+    if (!m || !v || !ext) return hvi::fail(HV_EINVAL, "null model, vector or output");
+    return run_adjoint(h, 2, m, v, k, nullptr, nullptr, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream, ext);
+}
+
+extern "C" int hv_image_fold(hv_handle *h, const double *ext, int k, float *out, double *out64, void *stream)
+{
+    if (!h || !ext || (!out && !out64)) return hvi::fail(HV_EINVAL, "null handle, image or output");
+    if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "k = %d; need 1 <= k <= 65535", k);
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != h->device) return hvi::fail(HV_EINVAL, "current device %d is not the handle's device %d", dev, h->device);
+    return hvk::launch_fold_ext(h, ext, k, out, out64, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------- merged calls
+namespace {
+
+struct BatchLayout {
+    int K = 0;                 // Born vectors: the Hessian vectors, then one per gradient
+    Layout L;                  // HV_OP_HV with K vectors, or HV_OP_MISFIT when K = 0
+    size_t vstage = 0, ostage = 0, fwd = 0, rscr = 0, part = 0, total = 0;
+};
+
+int batch_check(const hv_handle *h, const hv_batch *b)
+{
+    if (!h || !b) return hvi::fail(HV_EINVAL, "null handle or batch");
+    if (b->n_hv < 0 || b->n_grad < 0 || b->n_misfit < 0 || b->n_hv + b->n_grad + b->n_misfit == 0)
+        return hvi::fail(HV_EINVAL, "empty batch or negative counts");
+    if ((b->n_hv && (!b->v || !b->k || !b->Hv)) || (b->n_grad && (!b->grad_dobs || !b->grad_phi || !b->grad)) ||
+        (b->n_misfit && (!b->misfit_dobs || !b->misfit_phi)))
+        return hvi::fail(HV_EINVAL, "batch: null array");
+    long long K = b->n_grad;
+    for (int i = 0; i < b->n_hv; ++i) {
+        if (b->k[i] < 1 || !b->v[i] || !b->Hv[i]) return hvi::fail(HV_EINVAL, "batch: H v entry %d is empty", i);
+        K += b->k[i];
+    }
+    for (int g = 0; g < b->n_grad; ++g)
+        if (!b->grad_dobs[g] || !b->grad_phi[g] || !b->grad[g]) return hvi::fail(HV_EINVAL, "batch: gradient %d", g);
+    for (int q = 0; q < b->n_misfit; ++q)
+        if (!b->misfit_dobs[q] || !b->misfit_phi[q]) return hvi::fail(HV_EINVAL, "batch: misfit %d", q);
+    if (K > 65535) return hvi::fail(HV_EINVAL, "batch: %lld vectors; at most 65535", K);
+    return HV_OK;
+}
+
+int batch_layout(const hv_handle *h, const hv_batch *b, int ckpt, BatchLayout &B)
+{
+    HV_RT(batch_check(h, b));
+    B.K = b->n_grad;
+    for (int i = 0; i < b->n_hv; ++i) B.K += b->k[i];
+    if (B.K > 0) HV_RT(make_layout(h, HV_OP_HV, B.K, ckpt, B.L));
+    else HV_RT(make_layout(h, HV_OP_MISFIT, 1, HV_CKPT_ALL, B.L));
+    const size_t N = (size_t)h->nz * h->nx, ndata = (size_t)h->ns * h->nt * h->nr;
+    size_t o = B.L.total;
+    auto take = [&](size_t bytes) {
+        size_t at = o;
+        o += align256(bytes);
+        return at;
+    };
+    if (B.K > 0) {
+        B.vstage = take((size_t)B.K * N * sizeof(float));
+        B.ostage = take((size_t)B.K * N * sizeof(float));
+        B.fwd = take(ndata * sizeof(float));
+    }
+    B.rscr = take(ndata * sizeof(float));
+    B.part = take((size_t)(b->n_grad + b->n_misfit) * kResidualBlocks * sizeof(double));
+    B.total = o;
+    return HV_OK;
+}
+
+}  // namespace
+
+extern "C" int hv_batch_workspace_size(const hv_handle *h, const hv_batch *b, int ckpt, size_t *bytes)
+{
+    if (!bytes) return hvi::fail(HV_EINVAL, "null output");
+    BatchLayout B;
+    HV_RT(batch_layout(h, b, ckpt, B));
+    *bytes = B.total;
+    return HV_OK;
+}
+
+extern "C" int hv_apply_batch(hv_handle *h, const float *m, const hv_batch *b, int ckpt, void *ws, size_t ws_bytes,
+                              void *stream)
+{
+    if (!m) return hvi::fail(HV_EINVAL, "null model");
+    BatchLayout B;
+    HV_RT(batch_layout(h, b, ckpt, B));
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    if (dev != h->device) return hvi::fail(HV_EINVAL, "current device %d is not the handle's device %d", dev, h->device);
+    if (!ws || ((uintptr_t)ws & 255u) != 0) return hvi::fail(HV_EINVAL, "workspace must be non-null and 256-byte aligned");
+    if (ws_bytes < B.total) return hvi::fail(HV_ENOMEM, "workspace of %zu bytes; this batch needs %zu", ws_bytes, B.total);
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    const size_t N = (size_t)h->nz * h->nx, ndata = (size_t)h->ns * h->nt * h->nr;
+    const double phi_scale = 0.5 / (h->sigma * h->sigma);
+    double *part = reinterpret_cast<double *>(w + B.part);
+    float *rscr = reinterpret_cast<float *>(w + B.rscr);
+    // The misfits of the batch from the forward data: r = d - d_obs (discarded), phi in FP64.
+    auto misfits = [&](const float *fwd, cudaStream_t s) -> int {
+        for (int q = 0; q < b->n_misfit; ++q) {
+            double *pq = part + (size_t)(b->n_grad + q) * kResidualBlocks;
+            HV_RT(hvk::launch_residual(h, fwd, b->misfit_dobs[q], rscr, pq, kResidualBlocks, s));
+            HV_RT(hvk::launch_reduce_phi(pq, kResidualBlocks, phi_scale, b->misfit_phi[q], s));
+        }
+        return HV_OK;
+    };
+    if (B.K == 0) {                               // misfits only: one forward sweep
+        Exec E;
+        HV_RT(E.init(h, st, B.L, ws, 0));
+        HV_CK(cudaMemsetAsync(E.zero, 0, B.L.fb, st));
+        HV_RT(E.zero_ghosts(false));
+        HV_RT(hvk::launch_prep(h, m, nullptr, 0, E.C, nullptr, st));
+        float *fwd = reinterpret_cast<float *>(w + B.L.dd);
+        for (int n = 0; n < h->nt; ++n) HV_RT(E.forward(n, false, fwd, nullptr, nullptr));
+        return misfits(fwd, st);
+    }
+    // Gather the vectors: the H v vectors in entry order, then a zero vector per gradient
+    // (its Born field stays zero; its adjoint source becomes the residual).
+    float *V = reinterpret_cast<float *>(w + B.vstage), *O = reinterpret_cast<float *>(w + B.ostage);
+    float *fwd = reinterpret_cast<float *>(w + B.fwd);
+    size_t at = 0;
+    for (int i = 0; i < b->n_hv; ++i) {
+        HV_CK(cudaMemcpyAsync(V + at * N, b->v[i], (size_t)b->k[i] * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        at += b->k[i];
+    }
+    const size_t g0 = at;
+    if (b->n_grad) HV_CK(cudaMemsetAsync(V + g0 * N, 0, (size_t)b->n_grad * N * sizeof(float), st));
+    const Layout &L = B.L;
+    float *dd = reinterpret_cast<float *>(w + L.dd);
+    BatchExtra bx;
+    bx.fwd_data = fwd;
+    bx.after_sweep = [&](cudaStream_t s) -> int {
+        for (int g = 0; g < b->n_grad; ++g) {       // gradient slot: r = f(m) - d_obs replaces its Born data
+            double *pg = part + (size_t)g * kResidualBlocks;
+            HV_RT(hvk::launch_residual(h, fwd, b->grad_dobs[g], dd + (g0 + g) * ndata, pg, kResidualBlocks, s));
+            HV_RT(hvk::launch_reduce_phi(pg, kResidualBlocks, phi_scale, b->grad_phi[g], s));
+        }
+        return misfits(fwd, s);
+    };
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_prep(h, m, V, B.K, reinterpret_cast<float *>(w + L.C), reinterpret_cast<float *>(w + L.b), st));
+    }
+    HV_RT(run_adjoint_body(h, 2, V, B.K, nullptr, ckpt, ws, L, st, &bx));
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>(w + L.img), h->img_f64 ? hvk::kImgF64 : hvk::kImgPairs,
+                                   L.G, B.K, O, nullptr, st));
+    }
+    at = 0;
+    for (int i = 0; i < b->n_hv; ++i) {
+        HV_CK(cudaMemcpyAsync(b->Hv[i], O + at * N, (size_t)b->k[i] * N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        at += b->k[i];
+    }
+    for (int g = 0; g < b->n_grad; ++g)
+        HV_CK(cudaMemcpyAsync(b->grad[g], O + (g0 + g) * N, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return HV_OK;
+}
+
 extern "C" int hv_profile(hv_handle *h, int enable)
 {
     if (!h) return hvi::fail(HV_EINVAL, "null handle");
@@ -921,6 +1112,12 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
     HV_RT(validate_create(g, a));
     if (!m || !v || !Hv) return hvi::fail(HV_EINVAL, "null model, vector or output");
     cudaStream_t st = (cudaStream_t)stream;
+    // The tables below are copied from host vectors that die with this call;
+    // a capture would record copies from freed host memory.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    HV_CK(cudaStreamIsCapturing(st, &cap));
+    if (cap != cudaStreamCaptureStatusNone)
+        return hvi::fail(HV_EINVAL, "hv_hessian_apply_static: the stream is being captured; call it outside capture");
     int dev = -1;
     HV_CK(cudaGetDevice(&dev));
     void *base = nullptr;
@@ -948,36 +1145,31 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
         h->h_rec_zx[2 * i] = a->rec_iz[i] + h->nb;
         h->h_rec_zx[2 * i + 1] = a->rec_ix[i] + h->nb;
     }
-    const hvi::Tiling tf = hvk::tiling(h, 0), ta = hvk::tiling(h, 0);
-    std::vector<int> off_f, rec_f, pos_f, off_a, rec_a, pos_a;
+    // This path always runs tile configuration 0 for all three kernel kinds
+    // (the temporary handle's default), so one set of receiver tables serves.
+    const hvi::Tiling tf = hvk::tiling(h, 0);
+    std::vector<int> off_f, rec_f, pos_f;
     static_rectile_tables(h, tf, off_f, rec_f, pos_f);
-    const bool same_tiling = (tf.TX == ta.TX && tf.TZ == ta.TZ);
-    if (!same_tiling) static_rectile_tables(h, ta, off_a, rec_a, pos_a);
 
-    // Carve the array: tables first, then the workspace of hv_hessian_apply.
+    // Carve the array: the status word (always at offset 0, read by
+    // hv_static_status), the tables, then the workspace of hv_hessian_apply.
     size_t o = 0;
     auto carve = [&](size_t bytes) {
         size_t at = o;
         o += align256(bytes);
         return (char *)base + at;
     };
+    h->status = (int *)carve(sizeof(int));
     h->wavelet = (float *)carve(sizeof(float) * h->nt);
     h->az = (float *)carve(sizeof(float) * h->NZ);
     h->ax = (float *)carve(sizeof(float) * h->NX);
     h->src_zx = (int *)carve(sizeof(int) * h->h_src_zx.size());
     h->rec_zx = (int *)carve(sizeof(int) * h->h_rec_zx.size());
-    h->status = (int *)carve(sizeof(int));
-    hvi::RecTiles rf, ra;
+    hvi::RecTiles rf;
     rf.TX = tf.TX; rf.TZ = tf.TZ; rf.ntiles = tf.ntiles;
     rf.off = (int *)carve(sizeof(int) * off_f.size());
     rf.rec = (int *)carve(sizeof(int) * rec_f.size());
     rf.pos = (int *)carve(sizeof(int) * pos_f.size());
-    if (!same_tiling) {
-        ra.TX = ta.TX; ra.TZ = ta.TZ; ra.ntiles = ta.ntiles;
-        ra.off = (int *)carve(sizeof(int) * off_a.size());
-        ra.rec = (int *)carve(sizeof(int) * rec_a.size());
-        ra.pos = (int *)carve(sizeof(int) * pos_a.size());
-    }
     const size_t tables = o;
     Layout L;
     HV_RT(make_layout(h, HV_OP_HV, k, ckpt, L));
@@ -994,14 +1186,9 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
     HV_CK(cudaMemcpyAsync(rf.off, off_f.data(), sizeof(int) * off_f.size(), cudaMemcpyHostToDevice, st));
     HV_CK(cudaMemcpyAsync(rf.rec, rec_f.data(), sizeof(int) * rec_f.size(), cudaMemcpyHostToDevice, st));
     HV_CK(cudaMemcpyAsync(rf.pos, pos_f.data(), sizeof(int) * pos_f.size(), cudaMemcpyHostToDevice, st));
-    if (!same_tiling) {
-        HV_CK(cudaMemcpyAsync(ra.off, off_a.data(), sizeof(int) * off_a.size(), cudaMemcpyHostToDevice, st));
-        HV_CK(cudaMemcpyAsync(ra.rec, rec_a.data(), sizeof(int) * rec_a.size(), cudaMemcpyHostToDevice, st));
-        HV_CK(cudaMemcpyAsync(ra.pos, pos_a.data(), sizeof(int) * pos_a.size(), cudaMemcpyHostToDevice, st));
-    }
-    HV_CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    // The status word is not cleared here: it collects timeouts of every call
+    // until hv_static_status reads and clears it (the array starts zeroed).
     h->rectiles[(long long)rf.TX * 65536 + rf.TZ] = rf;
-    if (!same_tiling) h->rectiles[(long long)ra.TX * 65536 + ra.TZ] = ra;
     HV_RT(hvk::launch_setup(h, st));
     HV_RT(hvk::prepare_kernels(h));
     int rc = run_adjoint(h, 2, m, v, k, Hv, nullptr, nullptr, ckpt, ws, HV_STATIC_SCRATCH_BYTES - tables, st);
@@ -1010,6 +1197,19 @@ extern "C" int hv_hessian_apply_static(const hv_grid *g, const hv_acq *a, const 
     // belong to the static array).
     h->rectiles.clear();
     return rc;
+}
+
+extern "C" int hv_static_status(int *device_status)
+{
+    if (!device_status) return hvi::fail(HV_EINVAL, "null output");
+    int dev = -1;
+    HV_CK(cudaGetDevice(&dev));
+    void *base = nullptr;
+    HV_RT(static_scratch_base(dev, &base));
+    HV_CK(cudaDeviceSynchronize());
+    HV_CK(cudaMemcpy(device_status, base, sizeof(int), cudaMemcpyDeviceToHost));
+    HV_CK(cudaMemset(base, 0, sizeof(int)));
+    return HV_OK;
 }
 
 extern "C" int hv_status(hv_handle *h, int *device_status)
@@ -1021,6 +1221,30 @@ extern "C" int hv_status(hv_handle *h, int *device_status)
     HV_CK(cudaDeviceSynchronize());
     HV_CK(cudaMemcpy(device_status, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     HV_CK(cudaMemset(h->status, 0, sizeof(int)));
+    return HV_OK;
+}
+
+extern "C" int hv_set_image_precision(hv_handle *h, int mode)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    if (mode != HV_IMAGE_PAIRS && mode != HV_IMAGE_FP64) return hvi::fail(HV_EINVAL, "image precision mode %d", mode);
+    h->img_f64 = mode == HV_IMAGE_FP64;
+    return HV_OK;
+}
+
+extern "C" int hv_set_wait_limit(hv_handle *h, double seconds)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    if (!(seconds >= 1e-4 && seconds <= 60.0))
+        return hvi::fail(HV_EINVAL, "wait limit %g s; need 1e-4 <= limit <= 60", seconds);
+    h->wait_ns = (unsigned long long)(seconds * 1e9);
+    return HV_OK;
+}
+
+extern "C" int hv_inject_wait_timeout(hv_handle *h)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    h->inject_wait = true;
     return HV_OK;
 }
 

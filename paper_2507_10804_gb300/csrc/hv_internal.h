@@ -81,6 +81,8 @@ struct hv_handle {
     int *src_zx = nullptr;       // [ns][2] padded (z, x) of each source
     int *rec_zx = nullptr;       // [ns*nr][2] padded (z, x) of each receiver
     int *status = nullptr;       // device status word (HV_ETIMEOUT if a bounded wait ran out)
+    unsigned long long wait_ns = 2000000000ull;   // limit of every device wait (hv_set_wait_limit)
+    bool inject_wait = false;    // next dataflow-ordered step waits for a count nothing reaches (hv_inject_wait_timeout)
     std::vector<int> h_src_zx, h_rec_zx;
     std::mutex mu;
     std::map<long long, hvi::RecTiles> rectiles;                 // keyed by TX * 65536 + TZ
@@ -96,6 +98,9 @@ struct hv_handle {
     bool fuse_steps = false;
     // H v with every level stored on the shared-memory-resident kernels (hv_set_resident)
     bool resident = false;
+    // imaging accumulation (hv_set_image_precision): false = per-step FP32 sums over
+    // a shot group added to double-float images; true = every shot's product added in FP64
+    bool img_f64 = false;
     std::map<std::string, cudaGraphExec_t> graphs;
     // profiling (hv_profile)
     bool prof_on = false;
@@ -111,6 +116,7 @@ int max_tiles(const hv_handle *h);    // most tiles any menu entry cuts the hand
 void menu_info(int cfg, int *info);   // {TX, TZ, threads, stages, shot groups per CTA}
 hvi::Tiling tiling(const hv_handle *h, int cfg);
 int prepare_kernels(const hv_handle *h);
+int adj_f64_cfg();   // tile configuration of the FP64-image adjoint (hv_set_image_precision)
 
 // Tensor maps of one call's workspace, viewed as an array of fields
 // (x, z, field index): `halo` copies a tile with its 4-cell halo, `pt` the
@@ -171,7 +177,8 @@ struct AdjLaunch {
     const float *r;                // adjoint source data, [k or 1][ns][nt][nr]
     int r_per_vector;              // 1 if r has a vector dimension
     float rscale;                  // multiplies r (h^2 / sigma^2 or h^2)
-    double *img;                   // [G][k][fsize] partial images, double-float (hi, lo) FP32 pairs
+    double *img;                   // [G][k][fsize] partial images, double-float (hi, lo) FP32 pairs (or FP64)
+    bool img_f64;                  // every shot's product added in FP64 (hv_set_image_precision)
     int n, k, G;
     StepDeps deps;
 };
@@ -264,6 +271,7 @@ struct Prior {
 };
 int prior_create(Prior &P, int nz, int nx, double h, double delta, double gamma);
 void prior_destroy(Prior &P);
+int prior_reserve(Prior &P, int k);   // scratch for applies of up to k fields (allocated here, not later)
 int prior_A(const Prior &P, const float *v, float *out, int k, cudaStream_t st);
 int prior_Ainv(Prior &P, const float *v, float *out, int k, cudaStream_t st);
 int prior_R(Prior &P, const float *v, float *out, int k, cudaStream_t st);
@@ -298,8 +306,14 @@ int launch_psf_impulses(const PsfGeo &g, float *v, cudaStream_t st);   // v zero
 int launch_psf_extract(const PsfGeo &g, const float *Hv, float *psf, cudaStream_t st);
 int launch_psf_apply(const PsfGeo &g, const float *psf, const float *v, int k, float *out, cudaStream_t st);
 int psf_apply_smem_bytes(int S, int R, int nvec);   // dynamic shared memory of the apply kernel
-int launch_finalize(const hv_handle *h, const float *m, const double *img, int G, int k, float *out32,
+// Image formats (see k_finalize): 0 double-float pairs per shot group, 1 FP64
+// per shot group (both in the field layout), 2 one dense FP64 [k][NZ][NX] image.
+constexpr int kImgPairs = 0, kImgF64 = 1, kImgDense = 2;
+int launch_finalize(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, float *out32,
                     double *out64, cudaStream_t st);
+int launch_partial_image(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, double *out,
+                         cudaStream_t st);
+int launch_fold_ext(const hv_handle *h, const double *ext, int k, float *out32, double *out64, cudaStream_t st);
 int launch_residual(const hv_handle *h, const float *d, const float *dobs, float *r, double *partials,
                     int nblocks, cudaStream_t st);
 int launch_reduce_phi(const double *partials, int nblocks, double scale, double *phi, cudaStream_t st);

@@ -39,8 +39,24 @@ __global__ void k_prep(const float *__restrict__ m, const float *__restrict__ v,
 
 // Hv[j][iz][ix] = (2 / (m h^2)) sum over the E-preimage of (iz, ix) of sum_g img[g][j],
 // the partial images held as double-float pairs (hi, lo), summed in FP64.
-__global__ void k_finalize(const float *__restrict__ m, const double *__restrict__ img, int G, int k, int nz, int nx,
-                           int nb, int NZ, int NX, int P, size_t fsize, double h, float *out32, double *out64)
+// The image of group g, vector j at padded node offset `off` in format fmt:
+// 0: double-float (hi, lo) FP32 pairs per group in the field layout, 1: FP64
+// per group in the field layout, 2: one dense FP64 image [k][NZ][NX] (g = 0).
+__device__ __forceinline__ double img_at(const double *img, int fmt, int g, int k, int j, size_t fsize, size_t off,
+                                         int z, int x, int NZ, int NX)
+{
+    if (fmt == 0) {
+        const float2 v = reinterpret_cast<const float2 *>(img)[((size_t)g * k + j) * fsize + off];
+        return (double)v.x + (double)v.y;
+    }
+    if (fmt == 1) return img[((size_t)g * k + j) * fsize + off];
+    return img[((size_t)j * NZ + z) * NX + x];
+}
+
+// Hv[j][iz][ix] = 2 / (m h^2) * (E^T sum_g img_g)[iz][ix]: the group images
+// summed in group order in FP64, then folded onto the interior.
+__global__ void k_finalize(const float *__restrict__ m, const double *__restrict__ img, int fmt, int G, int k, int nz,
+                           int nx, int nb, int NZ, int NX, int P, size_t fsize, double h, float *out32, double *out64)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iz = blockIdx.y;
@@ -52,16 +68,47 @@ __global__ void k_finalize(const float *__restrict__ m, const double *__restrict
     for (int z = zlo; z <= zhi; ++z)
         for (int x = xlo; x <= xhi; ++x) {
             const size_t off = (size_t)(z + GH) * P + (x + GH);
-            for (int g = 0; g < G; ++g) {
-                const float2 v = reinterpret_cast<const float2 *>(img)[((size_t)g * k + j) * fsize + off];
-                acc += (double)v.x + (double)v.y;
-            }
+            for (int g = 0; g < G; ++g) acc += img_at(img, fmt, g, k, j, fsize, off, z, x, NZ, NX);
         }
     const double mm = (double)m[(size_t)iz * nx + ix];
     const double val = 2.0 / (mm * h * h) * acc;
     const size_t o = ((size_t)j * nz + iz) * nx + ix;
     if (out32) out32[o] = (float)val;
     if (out64) out64[o] = val;
+}
+
+// The extended image of this handle's shots on the padded grid (before the
+// fold E^T): out[j][z][x] = 2 / (m_ext h^2) * sum_g img_g, the groups summed
+// in group order in FP64, m_ext = E m (the nearest interior value).
+__global__ void k_partial_image(const float *__restrict__ m, const double *__restrict__ img, int fmt, int G, int k,
+                                int nz, int nx, int nb, int NZ, int NX, int P, size_t fsize, double h,
+                                double *__restrict__ out)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y, j = blockIdx.z;
+    if (x >= NX) return;
+    const size_t off = (size_t)(z + GH) * P + (x + GH);
+    double acc = 0.0;
+    for (int g = 0; g < G; ++g) acc += img_at(img, fmt, g, k, j, fsize, off, z, x, NZ, NX);
+    const int iz = min(max(z - nb, 0), nz - 1), ix = min(max(x - nb, 0), nx - 1);
+    const double mm = (double)m[(size_t)iz * nx + ix];
+    out[((size_t)j * NZ + z) * NX + x] = 2.0 / (mm * h * h) * acc;
+}
+
+// The fold E^T of extended images ext[k][NZ][NX] (FP64) onto the interior:
+// every sponge node adds onto its nearest interior node.
+__global__ void k_fold_ext(const double *__restrict__ ext, int nz, int nx, int nb, int NZ, int NX, float *out32,
+                           double *out64)
+{
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x, iz = blockIdx.y, j = blockIdx.z;
+    if (ix >= nx) return;
+    const int zlo = (iz == 0) ? 0 : iz + nb, zhi = (iz == nz - 1) ? NZ - 1 : iz + nb;
+    const int xlo = (ix == 0) ? 0 : ix + nb, xhi = (ix == nx - 1) ? NX - 1 : ix + nb;
+    double acc = 0.0;
+    for (int z = zlo; z <= zhi; ++z)
+        for (int x = xlo; x <= xhi; ++x) acc += ext[((size_t)j * NZ + z) * NX + x];
+    const size_t o = ((size_t)j * nz + iz) * nx + ix;
+    if (out32) out32[o] = (float)acc;
+    if (out64) out64[o] = acc;
 }
 
 // r = d - dobs and per-block FP64 partial sums of r^2 (fixed assignment, fixed tree).
@@ -195,13 +242,29 @@ int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float
     return cuda_check("k_prep launch");
 }
 
-int launch_finalize(const hv_handle *h, const float *m, const double *img, int G, int k, float *out32,
+int launch_finalize(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, float *out32,
                     double *out64, cudaStream_t st)
 {
     dim3 grid((h->nx + 127) / 128, h->nz, k);
-    k_finalize<<<grid, 128, 0, st>>>(m, img, G, k, h->nz, h->nx, h->nb, h->NZ, h->NX, h->P, h->fsize, h->h, out32,
-                                     out64);
+    k_finalize<<<grid, 128, 0, st>>>(m, img, fmt, G, k, h->nz, h->nx, h->nb, h->NZ, h->NX, h->P, h->fsize, h->h,
+                                     out32, out64);
     return cuda_check("k_finalize launch");
+}
+
+int launch_partial_image(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, double *out,
+                         cudaStream_t st)
+{
+    dim3 grid((h->NX + 127) / 128, h->NZ, k);
+    k_partial_image<<<grid, 128, 0, st>>>(m, img, fmt, G, k, h->nz, h->nx, h->nb, h->NZ, h->NX, h->P, h->fsize, h->h,
+                                          out);
+    return cuda_check("k_partial_image launch");
+}
+
+int launch_fold_ext(const hv_handle *h, const double *ext, int k, float *out32, double *out64, cudaStream_t st)
+{
+    dim3 grid((h->nx + 127) / 128, h->nz, k);
+    k_fold_ext<<<grid, 128, 0, st>>>(ext, h->nz, h->nx, h->nb, h->NZ, h->NX, out32, out64);
+    return cuda_check("k_fold_ext launch");
 }
 
 int launch_residual(const hv_handle *h, const float *d, const float *dobs, float *r, double *partials, int nblocks,

@@ -188,6 +188,18 @@ int prior_tmp(Prior &P, int k, T **buf)
     return HV_OK;
 }
 
+}  // namespace
+
+// Sizes the prior's FP32 scratch for k fields now, so that later applies with
+// at most k fields allocate nothing.
+int prior_reserve(Prior &P, int k)
+{
+    float *buf = nullptr;
+    return prior_tmp<float>(P, k, &buf);
+}
+
+namespace {
+
 // C = op(A) op(B), column-major, k-batched with the given strides.
 int gemm_batched(cublasHandle_t hb, cublasOperation_t ta, cublasOperation_t tb, int m, int n, int kk, const float *A,
                  int lda, long long sa, const float *B, int ldb, long long sb, float *C, int ldc, long long sc, int batch)

@@ -33,15 +33,19 @@
         if (e_ != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", #call, cudaGetErrorString(e_));   \
     } while (0)
 
-// Cached scratch of the solves and applies: 7 k-field buffers (CG r, z, p, q,
-// R p, and two for the sampler), 5 k-vectors of FP64 CG scalars, k x 256
-// correction coefficients and k activity flags.
+// Scratch of the solves, applies and the correction, allocated once at
+// hv_posterior_create for at most k = max_k fields: 7 k-field buffers (CG r,
+// z, p, q, R p, and two for the sampler), 5 k-vectors of FP64 CG scalars,
+// k x 256 correction coefficients, k activity flags; for the correction 6
+// k-field buffers and two k x k FP64 matrices.
 struct PostWork {
     int k = 0;
     float *f = nullptr;
     double *d = nullptr;
     double *red = nullptr;   // reduction partials (hv_blas.cu)
     int *act = nullptr;
+    float *cf = nullptr;     // correction fields [6][k][N]
+    double *cm = nullptr;    // correction matrices [2][k][k]
 };
 
 struct hv_posterior {
@@ -52,8 +56,8 @@ struct hv_posterior {
     const hv_approx *approx = nullptr;    // borrowed square-root approximation, or null
     int r = 0;                            // correction rank
     std::vector<double> lam;
-    float *V = nullptr, *U = nullptr;     // [r][N]
-    double *w = nullptr;                  // [2r]: Lambda, S_r
+    float *V = nullptr, *U = nullptr;     // [r][N] (room for max_k rows)
+    double *w = nullptr;                  // [2r]: Lambda, S_r (room for 2 max_k)
     PostWork work;
     cudaEvent_t done = nullptr;           // last use of the scratch and the prior's tables
     std::mutex *mu = nullptr;
@@ -72,24 +76,6 @@ int launched(const char *what)
     if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "%s: %s", what, cudaGetErrorString(e));
     return HV_OK;
 }
-
-struct Bufs {   // device scratch freed (after the stream drains) on every exit path
-    std::vector<void *> p;
-    cudaStream_t st = nullptr;
-    template <class T>
-    int get(T **out, size_t n)
-    {
-        cudaError_t e = cudaMalloc(reinterpret_cast<void **>(out), std::max<size_t>(n, 1) * sizeof(T));
-        if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "posterior scratch: %s", cudaGetErrorString(e));
-        p.push_back(*out);
-        return HV_OK;
-    }
-    ~Bufs()
-    {
-        if (st) cudaStreamSynchronize(st);
-        for (void *q : p) cudaFree(q);
-    }
-};
 
 // Build-time products of the correction (FP64 accumulation throughout: the
 // orthonormalisation combines nearly dependent vectors with large weights).
@@ -185,18 +171,39 @@ __global__ void k_gpcn_propose(const float *__restrict__ m, const float *__restr
     if (d) d[t] = dd;
 }
 
-// gpCN acceptance after the FP64 dots dHd[c] = d . Hd: Delta' = phi' - 1/2 dHd;
-// accept iff log_u < Delta_cur - Delta'; on acceptance Delta_cur <- Delta'.
-__global__ void k_gpcn_decide(const double *__restrict__ phi_new, const double *__restrict__ dHd,
-                              const double *__restrict__ log_u, double *__restrict__ delta_cur,
-                              int *__restrict__ accepted, int c)
+// gpCN acceptance, one CTA of 256 threads per chain: the dot dHd = d . Hd of
+// the chain's n values (double-float accumulation on the FP32 pipe inside a
+// thread -- each product split exactly, about 2^-44 relative -- then an FP64
+// tree over the threads, a fixed order), Delta' = phi' - 1/2 dHd, and the
+// decision: accept iff log_u < Delta_cur - Delta'; on acceptance Delta_cur <- Delta'.
+__global__ void __launch_bounds__(256) k_gpcn_decide(const double *__restrict__ phi_new, const float *__restrict__ d,
+                                                     const float *__restrict__ Hd, const double *__restrict__ log_u,
+                                                     double *__restrict__ delta_cur, int *__restrict__ accepted,
+                                                     size_t n)
 {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= c) return;
-    const double dn = phi_new[i] - 0.5 * dHd[i];
-    const int take = log_u[i] < delta_cur[i] - dn;
-    if (take) delta_cur[i] = dn;
-    accepted[i] = take;
+    __shared__ double sh[256];
+    const int c = blockIdx.x;
+    const float *a = d + (size_t)c * n, *b = Hd + (size_t)c * n;
+    float hi = 0.0f, lo = 0.0f;
+    for (size_t e = threadIdx.x; e < n; e += blockDim.x) {
+        const float x = a[e], y = b[e];
+        const float p = __fmul_rn(x, y), pe = fmaf(x, y, -p);
+        const float s = __fadd_rn(hi, p), bv = __fsub_rn(s, hi);
+        lo = __fadd_rn(lo, __fadd_rn(__fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(p, bv)), pe));
+        hi = s;
+    }
+    sh[threadIdx.x] = (double)hi + (double)lo;
+    __syncthreads();
+    for (int h = 128; h > 0; h >>= 1) {
+        if ((int)threadIdx.x < h) sh[threadIdx.x] += sh[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const double dn = phi_new[c] - 0.5 * sh[0];
+        const int take = log_u[c] < delta_cur[c] - dn;
+        if (take) delta_cur[c] = dn;
+        accepted[c] = take;
+    }
 }
 
 // m[c] <- m_new[c] for the accepted chains; grid (points / 256, c).
@@ -220,21 +227,25 @@ struct Session {
     ~Session() { cudaEventRecord(p->done, st); }
 };
 
-int ensure_work(PostWork &w, int k, size_t N)
+// Allocates the scratch for up to k fields (at create only).
+int alloc_work(PostWork &w, int k, size_t N)
 {
-    if (w.k >= k) return HV_OK;
-    cudaFree(w.f);   // synchronises: nothing in flight uses the old scratch afterwards
-    cudaFree(w.d);
-    cudaFree(w.red);
-    cudaFree(w.act);
-    w = PostWork{};
     cudaError_t e;
     if ((e = cudaMalloc(&w.f, (size_t)kWorkFields * k * N * sizeof(float))) != cudaSuccess ||
         (e = cudaMalloc(&w.d, (size_t)(5 + kMaxCorrection) * k * sizeof(double))) != cudaSuccess ||
         (e = cudaMalloc(&w.red, hvk::coef_scratch(kMaxCorrection, k, N) * sizeof(double))) != cudaSuccess ||
-        (e = cudaMalloc(&w.act, (size_t)k * sizeof(int))) != cudaSuccess)
+        (e = cudaMalloc(&w.act, (size_t)k * sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&w.cf, (size_t)6 * k * N * sizeof(float))) != cudaSuccess ||
+        (e = cudaMalloc(&w.cm, (size_t)2 * k * k * sizeof(double))) != cudaSuccess)
         return hvi::fail(HV_ECUDA, "posterior scratch: %s", cudaGetErrorString(e));
     w.k = k;
+    return HV_OK;
+}
+
+// Calls take at most the k fields the scratch was sized for.
+int check_k(const PostWork &w, int k)
+{
+    if (k > w.k) return hvi::fail(HV_EINVAL, "k = %d fields; this posterior was created for at most %d", k, w.k);
     return HV_OK;
 }
 
@@ -348,10 +359,12 @@ int device_eig(const double *G, int n, std::vector<double> &w, std::vector<doubl
 }  // namespace
 
 extern "C" int hv_posterior_create(int nz, int nx, double h, double delta, double gamma, const hv_approx *approx,
-                                   hv_posterior **out)
+                                   int max_k, hv_posterior **out)
 {
     if (out) *out = nullptr;
     if (!out) return hvi::fail(HV_EINVAL, "null output");
+    if (max_k < 1 || max_k > kMaxCorrection)
+        return hvi::fail(HV_EINVAL, "max_k = %d; need 1 <= max_k <= %d", max_k, kMaxCorrection);
     if (approx) {
         if ((approx->kind != 1 && approx->kind != 2) || !approx->lr.spd)
             return hvi::fail(HV_EINVAL, "the posterior takes a square-root (SPD) PDO or PSF+ approximation");
@@ -369,7 +382,14 @@ extern "C" int hv_posterior_create(int nz, int nx, double h, double delta, doubl
     p->h = h;
     p->approx = approx;
     p->mu = new std::mutex;
+    const size_t N = (size_t)nz * nx;
     int rc = hvk::prior_create(p->prior, nz, nx, h, delta, gamma);
+    if (rc == HV_OK) rc = hvk::prior_reserve(p->prior, max_k);
+    if (rc == HV_OK) rc = alloc_work(p->work, max_k, N);
+    if (rc == HV_OK && (cudaMalloc(&p->V, (size_t)max_k * N * sizeof(float)) != cudaSuccess ||
+                        cudaMalloc(&p->U, (size_t)max_k * N * sizeof(float)) != cudaSuccess ||
+                        cudaMalloc(&p->w, (size_t)2 * max_k * sizeof(double)) != cudaSuccess))
+        rc = hvi::fail(HV_ECUDA, "posterior correction factors: out of device memory");
     if (rc == HV_OK && cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess)
         rc = hvi::fail(HV_ECUDA, "cudaEventCreate failed");
     if (rc != HV_OK) {
@@ -390,7 +410,10 @@ extern "C" int hv_posterior_destroy(hv_posterior *p)
     cudaFree(p->w);
     cudaFree(p->work.f);
     cudaFree(p->work.d);
+    cudaFree(p->work.red);
     cudaFree(p->work.act);
+    cudaFree(p->work.cf);
+    cudaFree(p->work.cm);
     if (p->done) cudaEventDestroy(p->done);
     delete p->mu;
     delete p;
@@ -409,7 +432,7 @@ extern "C" int hv_posterior_solve(hv_posterior *p, const hv_operator *op, const 
     HV_RT_INTERNAL(check_device(p->device));
     cudaStream_t st = (cudaStream_t)stream;
     Session ses(p, st);
-    HV_RT_INTERNAL(ensure_work(p->work, k, (size_t)p->nz * p->nx));
+    HV_RT_INTERNAL(check_k(p->work, k));
     return pcg(p->prior, op ? user_op(op, st) : gram_op(p, st), b, k, x, rtol, max_iter, iters, st, p->work);
 }
 
@@ -421,7 +444,7 @@ extern "C" int hv_posterior_apply(hv_posterior *p, const float *v, int k, float 
     cudaStream_t st = (cudaStream_t)stream;
     Session ses(p, st);
     const size_t N = (size_t)p->nz * p->nx;
-    HV_RT_INTERNAL(ensure_work(p->work, k, N));
+    HV_RT_INTERNAL(check_k(p->work, k));
     float *t = work_field(p->work, 4, N);
     double *C = p->work.d + 5 * (size_t)p->work.k;
     HV_RT_INTERNAL(apply_op_plus_R(p->prior, gram_op(p, st), v, k, out, t, st));
@@ -443,7 +466,7 @@ extern "C" int hv_posterior_sample(hv_posterior *p, const float *n1, const float
     cudaStream_t st = (cudaStream_t)stream;
     Session ses(p, st);
     const size_t N = (size_t)p->nz * p->nx, n = (size_t)k * N;
-    HV_RT_INTERNAL(ensure_work(p->work, k, N));
+    HV_RT_INTERNAL(check_k(p->work, k));
     if (!p->approx) {
         HV_RT_INTERNAL(hvk::prior_Ainv(p->prior, n1, zeta, k, st));   // H0^-1 A n1 = A^-1 n1
     } else {
@@ -468,23 +491,16 @@ extern "C" int hv_posterior_correct(hv_posterior *p, const hv_operator *hd, cons
     if (!p || !hd || !hd->apply || !omega) return hvi::fail(HV_EINVAL, "null posterior, operator or test vectors");
     if (hd->nz != p->nz || hd->nx != p->nx) return hvi::fail(HV_EINVAL, "the operator does not act on the posterior's grid");
     if (rank < 1 || k < rank || k > kMaxCorrection) return hvi::fail(HV_EINVAL, "rank %d with %d test vectors; need 1 <= rank <= k <= 256", rank, k);
+    HV_RT_INTERNAL(check_k(p->work, k));
     if (!(rtol > 0 && rtol < 1) || max_iter < 1) return hvi::fail(HV_EINVAL, "rtol %g, max_iter %d", rtol, max_iter);
     HV_RT_INTERNAL(check_device(p->device));
     cudaStream_t st = (cudaStream_t)stream;
     Session ses(p, st);
     const size_t N = (size_t)p->nz * p->nx, n = (size_t)k * N;
-    Bufs bf;
-    bf.st = st;
-    float *Z = nullptr, *Y = nullptr, *HQ = nullptr, *t = nullptr, *Q2 = nullptr, *HQ2 = nullptr;
-    double *G = nullptr, *M = nullptr;
-    HV_RT_INTERNAL(bf.get(&Z, n));
-    HV_RT_INTERNAL(bf.get(&Y, n));
-    HV_RT_INTERNAL(bf.get(&HQ, n));
-    HV_RT_INTERNAL(bf.get(&t, n));
-    HV_RT_INTERNAL(bf.get(&Q2, n));
-    HV_RT_INTERNAL(bf.get(&HQ2, n));
-    HV_RT_INTERNAL(bf.get(&G, (size_t)k * k));
-    HV_RT_INTERNAL(bf.get(&M, (size_t)k * k));
+    // the correction's scratch, sized at create for max_k fields
+    const size_t cap = (size_t)p->work.k * N;
+    float *Z = p->work.cf, *Y = Z + cap, *HQ = Y + cap, *t = HQ + cap, *Q2 = t + cap, *HQ2 = Q2 + cap;
+    double *G = p->work.cm, *M = G + (size_t)p->work.k * p->work.k;
     const OpFn H = user_op(hd, st), B = gram_op(p, st);
     auto resid = [&](const float *X, int kk, float *out) {   // (H_d - H~_d) X
         HV_RT_INTERNAL(H(X, kk, out));
@@ -499,7 +515,6 @@ extern "C" int hv_posterior_correct(hv_posterior *p, const hv_operator *hd, cons
     if (!p->approx) {
         HV_RT_INTERNAL(hvk::prior_Rinv(p->prior, Z, Y, k, st));
     } else {
-        HV_RT_INTERNAL(ensure_work(p->work, k, N));
         HV_RT_INTERNAL(pcg(p->prior, B, Z, k, Y, rtol, max_iter, nullptr, st, p->work));
     }
     // H0-orthonormalise Y, carrying H0 Y = Z along: Q <- Y, HQ <- Z
@@ -544,29 +559,15 @@ extern "C" int hv_posterior_correct(hv_posterior *p, const hv_operator *hd, cons
         wh[j] = lam[j];
         wh[rank + j] = 1.0 - 1.0 / std::sqrt(lam[j] + 1.0);
     }
-    float *V = nullptr, *U = nullptr;
-    double *wd = nullptr;
-    cudaError_t e;
-    if ((e = cudaMalloc(&V, (size_t)rank * N * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&U, (size_t)rank * N * sizeof(float))) != cudaSuccess ||
-        (e = cudaMalloc(&wd, wh.size() * sizeof(double))) != cudaSuccess) {
-        cudaFree(V);
-        cudaFree(U);
-        return hvi::fail(HV_ECUDA, "correction factors: %s", cudaGetErrorString(e));
-    }
-    PCK(cudaMemcpyAsync(wd, wh.data(), wh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    // The new factors replace the old ones in place (the session orders this
+    // stream after every earlier use of them).
+    PCK(cudaMemcpyAsync(p->w, wh.data(), wh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     PCK(cudaMemcpyAsync(M, Sh.data(), Sh.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-    k_combine_rows<<<nblk((size_t)rank * N, 256), 256, 0, st>>>(M, Q, V, kk, rank, N);
+    k_combine_rows<<<nblk((size_t)rank * N, 256), 256, 0, st>>>(M, Q, p->V, kk, rank, N);
     HV_RT_INTERNAL(launched("k_combine_rows"));
-    k_combine_rows<<<nblk((size_t)rank * N, 256), 256, 0, st>>>(M, HQ, U, kk, rank, N);
+    k_combine_rows<<<nblk((size_t)rank * N, 256), 256, 0, st>>>(M, HQ, p->U, kk, rank, N);
     HV_RT_INTERNAL(launched("k_combine_rows"));
     PCK(cudaStreamSynchronize(st));
-    cudaFree(p->V);
-    cudaFree(p->U);
-    cudaFree(p->w);
-    p->V = V;
-    p->U = U;
-    p->w = wd;
     p->r = rank;
     p->lam.assign(lam.begin(), lam.begin() + rank);
     return HV_OK;
@@ -604,19 +605,8 @@ extern "C" int hv_gpcn_accept(int n, int c, const double *phi_new, const float *
         !accepted)
         return hvi::fail(HV_EINVAL, "bad gpCN acceptance arguments");
     cudaStream_t st = (cudaStream_t)stream;
-    double *scratch = nullptr;   // stream-ordered: the dots and their chunk partials
-    const size_t ns = hvk::rows_dot_scratch(c, (size_t)n) + (size_t)c;
-    PCK(cudaMallocAsync(reinterpret_cast<void **>(&scratch), ns * sizeof(double), st));
-    double *dHd = scratch + hvk::rows_dot_scratch(c, (size_t)n);
-    int rc = hvk::rows_dot(d_new, Hd_new, dHd, c, (size_t)n, 1.0, scratch, st);
-    if (rc == HV_OK) {
-        k_gpcn_decide<<<nblk(c, 128), 128, 0, st>>>(phi_new, dHd, log_u, delta_cur, accepted, c);
-        rc = launched("k_gpcn_decide");
-    }
-    if (rc == HV_OK) {
-        k_gpcn_take<<<dim3(nblk(n, 256), c), 256, 0, st>>>(m_new, accepted, m, (size_t)n);
-        rc = launched("k_gpcn_take");
-    }
-    cudaFreeAsync(scratch, st);
-    return rc;
+    k_gpcn_decide<<<c, 256, 0, st>>>(phi_new, d_new, Hd_new, log_u, delta_cur, accepted, (size_t)n);
+    HV_RT_INTERNAL(launched("k_gpcn_decide"));
+    k_gpcn_take<<<dim3(nblk(n, 256), c), 256, 0, st>>>(m_new, accepted, m, (size_t)n);
+    return launched("k_gpcn_take");
 }

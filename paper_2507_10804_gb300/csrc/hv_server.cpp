@@ -5,11 +5,17 @@
 // One device arena holds every admitted request's workspace; a scheduler
 // thread admits queued requests when a stream and enough arena memory are
 // free and runs each on its own stream, so requests that arrive while others
-// run overlap with them on the GPU.  Completion is detected with events; the
-// scheduler never blocks on the device (event queries plus short sleeps), and
-// every host wait is bounded.
+// run overlap with them on the GPU.  Continuous batching: when it admits an
+// H v, gradient or misfit request, the queued requests on the same problem
+// and model join it (up to the server's vector limit, if the merged
+// workspace fits) and run as one merged call (hv_apply_batch: one forward
+// sweep, the H v vectors and the gradients as one batch of Born vectors),
+// whose results are bitwise those of separate calls.  Completion is detected
+// with events; the scheduler never blocks on the device (event queries plus
+// short sleeps), and every host wait is bounded.
 #include "hv_internal.h"
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -74,6 +80,7 @@ struct Req {
     int status = HV_REQ_QUEUED;
     size_t ws = 0, off = 0;
     int slot = -1;
+    int batch = 1;            // requests that ran in the same launch sequence
     double t_submit = 0, t_start = 0, t_done = 0;
 };
 
@@ -86,7 +93,9 @@ struct hv_server {
     Arena *arena = nullptr;
     std::vector<cudaStream_t> streams;
     std::vector<cudaEvent_t> events;
-    std::vector<unsigned long long> slot_req;   // request id per slot (0 = free)
+    std::vector<std::vector<unsigned long long>> slot_reqs;   // request ids per slot (empty = free)
+    std::vector<size_t> slot_off;                              // arena offset held by the slot
+    int merge_max = 64;                                        // vectors per merged call (< 2: no merging)
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<unsigned long long> queue;
@@ -133,58 +142,179 @@ int launch(hv_server *S, const Req &q)
     return rc;
 }
 
+// The merged call of several requests on one problem and model.
+struct Merged {
+    std::vector<const float *> v, gd, md;
+    std::vector<int> k;
+    std::vector<float *> out, g;
+    std::vector<double *> gp, mp;
+    int ckpt = HV_CKPT_ALL;
+    hv_batch b{};
+    void add(const hv_request &r)
+    {
+        if (r.kind == HV_REQ_HV) {
+            v.push_back(r.v);
+            k.push_back(r.k);
+            out.push_back(r.out);
+        } else if (r.kind == HV_REQ_GRAD) {
+            gd.push_back(r.d_obs);
+            gp.push_back(r.phi);
+            g.push_back(r.out);
+        } else {
+            md.push_back(r.d_obs);
+            mp.push_back(r.phi);
+        }
+    }
+    const hv_batch *make()
+    {
+        b.n_hv = (int)v.size();
+        b.v = v.data();
+        b.k = k.data();
+        b.Hv = out.data();
+        b.n_grad = (int)gd.size();
+        b.grad_dobs = gd.data();
+        b.grad_phi = gp.data();
+        b.grad = g.data();
+        b.n_misfit = (int)md.size();
+        b.misfit_dobs = md.data();
+        b.misfit_phi = mp.data();
+        return &b;
+    }
+};
+
+int launch_merged(hv_server *S, const std::vector<Req> &qs, size_t ws_bytes)
+{
+    const int slot = qs[0].slot;
+    Merged M;
+    for (const Req &q : qs) {
+        M.add(q.r);
+        if (q.r.kind != HV_REQ_MISFIT) M.ckpt = q.r.ckpt;
+    }
+    int rc = hv_apply_batch(qs[0].r.problem, qs[0].r.m, M.make(), M.ckpt, S->arena_base + qs[0].off, ws_bytes,
+                            (void *)S->streams[slot]);
+    cudaError_t e = cudaEventRecord(S->events[slot], S->streams[slot]);
+    if (rc == HV_OK && e != cudaSuccess) rc = HV_ECUDA;
+    return rc;
+}
+
+bool mergeable(const hv_request &r) { return r.kind == HV_REQ_HV || r.kind == HV_REQ_GRAD || r.kind == HV_REQ_MISFIT; }
+
+// The queued requests that can run merged with the one at `head`: same problem
+// and model; H v and gradients with the same checkpoint budget; at most
+// merge_max Born vectors in all.
+std::vector<unsigned long long> merge_group(hv_server *S, std::deque<unsigned long long>::iterator head)
+{
+    std::vector<unsigned long long> ids{*head};
+    const hv_request &r0 = S->reqs[*head].r;
+    if (S->merge_max < 2 || !mergeable(r0)) return ids;
+    int ckpt = r0.kind == HV_REQ_MISFIT ? 0 : r0.ckpt;
+    bool have_ckpt = r0.kind != HV_REQ_MISFIT;
+    int vecs = r0.kind == HV_REQ_HV ? r0.k : (r0.kind == HV_REQ_GRAD ? 1 : 0);
+    for (auto it = std::next(head); it != S->queue.end(); ++it) {
+        const hv_request &r = S->reqs[*it].r;
+        if (!mergeable(r) || r.problem != r0.problem || r.m != r0.m) continue;
+        if (r.kind != HV_REQ_MISFIT) {
+            if (have_ckpt && r.ckpt != ckpt) continue;
+            const int add = r.kind == HV_REQ_HV ? r.k : 1;
+            if (vecs + add > S->merge_max) continue;
+            vecs += add;
+            ckpt = r.ckpt;
+            have_ckpt = true;
+        }
+        ids.push_back(*it);
+    }
+    return ids;
+}
+
+int merged_ws(hv_server *S, const std::vector<unsigned long long> &ids, size_t *bytes)
+{
+    Merged M;
+    for (auto id : ids) {
+        const hv_request &r = S->reqs[id].r;
+        M.add(r);
+        if (r.kind != HV_REQ_MISFIT) M.ckpt = r.ckpt;
+    }
+    return hv_batch_workspace_size(S->reqs[ids[0]].r.problem, M.make(), M.ckpt, bytes);
+}
+
 void worker_loop(hv_server *S)
 {
     cudaSetDevice(S->device);
-    std::vector<int> failed(S->slot_req.size(), HV_OK);   // enqueue status per running slot
+    std::vector<int> failed(S->slot_reqs.size(), HV_OK);   // enqueue status per running slot
     std::unique_lock<std::mutex> lk(S->mu);
     while (!S->stop.load()) {
         bool progress = false;
         // completions
-        for (size_t sl = 0; sl < S->slot_req.size(); ++sl) {
-            unsigned long long id = S->slot_req[sl];
-            if (!id) continue;
+        for (size_t sl = 0; sl < S->slot_reqs.size(); ++sl) {
+            if (S->slot_reqs[sl].empty()) continue;
             cudaError_t e = cudaEventQuery(S->events[sl]);
             if (e == cudaErrorNotReady) continue;
-            Req &q = S->reqs[id];
-            q.status = failed[sl] != HV_OK ? failed[sl] : (e == cudaSuccess ? HV_OK : HV_ECUDA);
-            q.t_done = S->now();
-            S->arena->release(q.off);
-            S->slot_req[sl] = 0;
+            const double t = S->now();
+            for (auto id : S->slot_reqs[sl]) {
+                Req &q = S->reqs[id];
+                q.status = failed[sl] != HV_OK ? failed[sl] : (e == cudaSuccess ? HV_OK : HV_ECUDA);
+                q.t_done = t;
+            }
+            S->arena->release(S->slot_off[sl]);
+            S->slot_reqs[sl].clear();
             failed[sl] = HV_OK;
             progress = true;
         }
         if (progress) S->cv_done.notify_all();
         // admissions, in arrival order; a request that does not fit yet is passed
-        std::vector<Req> admitted;
+        std::vector<std::vector<Req>> admitted;
+        std::vector<size_t> admitted_ws;
         for (auto it = S->queue.begin(); it != S->queue.end();) {
             int slot = -1;
-            for (size_t sl = 0; sl < S->slot_req.size(); ++sl)
-                if (!S->slot_req[sl]) {
+            for (size_t sl = 0; sl < S->slot_reqs.size(); ++sl)
+                if (S->slot_reqs[sl].empty()) {
                     slot = (int)sl;
                     break;
                 }
             if (slot < 0) break;
-            Req &q = S->reqs[*it];
-            size_t off = 0;
-            if (!S->arena->alloc(q.ws, &off)) {
+            std::vector<unsigned long long> ids = merge_group(S, it);
+            size_t ws = S->reqs[*it].ws, off = 0;
+            if (ids.size() > 1 && merged_ws(S, ids, &ws) != HV_OK) {
+                ids.resize(1);
+                ws = S->reqs[*it].ws;
+            }
+            bool fits = S->arena->alloc(ws, &off);
+            if (!fits && ids.size() > 1) {        // the merged call does not fit: try the request alone
+                ids.resize(1);
+                ws = S->reqs[*it].ws;
+                fits = S->arena->alloc(ws, &off);
+            }
+            if (!fits) {
                 ++it;
                 continue;
             }
-            q.off = off;
-            q.slot = slot;
-            q.t_start = S->now();
-            q.status = HV_REQ_RUNNING;
-            S->slot_req[slot] = q.id;
-            admitted.push_back(q);
+            std::vector<Req> group;
+            const double t = S->now();
+            for (auto id : ids) {
+                Req &q = S->reqs[id];
+                q.off = off;
+                q.slot = slot;
+                q.t_start = t;
+                q.status = HV_REQ_RUNNING;
+                q.batch = (int)ids.size();
+                group.push_back(q);
+            }
+            S->slot_reqs[slot] = ids;
+            S->slot_off[slot] = off;
+            admitted.push_back(group);
+            admitted_ws.push_back(ws);
+            for (size_t i = 1; i < ids.size(); ++i)
+                S->queue.erase(std::find(std::next(it), S->queue.end(), ids[i]));
             it = S->queue.erase(it);
         }
         if (!admitted.empty()) {
             lk.unlock();                          // enqueueing thousands of launches takes a while
             std::vector<int> rcs;
-            for (const Req &q : admitted) rcs.push_back(launch(S, q));
+            for (size_t i = 0; i < admitted.size(); ++i)
+                rcs.push_back(admitted[i].size() > 1 ? launch_merged(S, admitted[i], admitted_ws[i])
+                                                     : launch(S, admitted[i][0]));
             lk.lock();
-            for (size_t i = 0; i < admitted.size(); ++i) failed[admitted[i].slot] = rcs[i];
+            for (size_t i = 0; i < admitted.size(); ++i) failed[admitted[i][0].slot] = rcs[i];
             progress = true;
         }
         if (!progress) S->cv_work.wait_for(lk, std::chrono::microseconds(50));
@@ -211,7 +341,8 @@ extern "C" int hv_server_create(size_t hbm_budget, int max_concurrent, hv_server
     S->arena = new Arena(hbm_budget);
     S->streams.resize(max_concurrent);
     S->events.resize(max_concurrent);
-    S->slot_req.assign(max_concurrent, 0);
+    S->slot_reqs.assign(max_concurrent, {});
+    S->slot_off.assign(max_concurrent, 0);
     for (int i = 0; i < max_concurrent; ++i) {
         cudaStreamCreateWithFlags(&S->streams[i], cudaStreamNonBlocking);
         cudaEventCreateWithFlags(&S->events[i], cudaEventDisableTiming);
@@ -231,8 +362,8 @@ extern "C" int hv_server_destroy(hv_server *S, double timeout_s)
         std::unique_lock<std::mutex> lk(S->mu);
         S->queue.clear();
         auto busy = [&] {
-            for (auto id : S->slot_req)
-                if (id) return true;
+            for (auto &ids : S->slot_reqs)
+                if (!ids.empty()) return true;
             return false;
         };
         while (busy()) {
@@ -329,5 +460,15 @@ extern "C" int hv_request_get_info(hv_server *S, unsigned long long id, hv_reque
     info->t_start = q.t_start;
     info->t_done = q.t_done;
     info->ws_bytes = q.ws;
+    info->batch = q.batch;
+    return HV_OK;
+}
+
+extern "C" int hv_server_set_batching(hv_server *S, int max_vectors)
+{
+    if (!S || max_vectors < 0 || max_vectors > 65535)
+        return hvi::fail(HV_EINVAL, "hv_server_set_batching: null server or max_vectors outside 0..65535");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->merge_max = max_vectors;
     return HV_OK;
 }

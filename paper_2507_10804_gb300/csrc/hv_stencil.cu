@@ -46,7 +46,6 @@ constexpr float LC4 = (float)(-1.0 / 560.0);
 constexpr int kShotsPerGroup = 8;
 constexpr int kTileMenu = 16;      // number of tile configurations (with_cfg)
 static_assert(kTileMenu <= kMaxTileMenu, "the bulk-copy descriptors have a slot per configuration");
-constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 // BX x BZ threads, each on 4 x RZ points; ST copy stages (shots in flight per
 // CTA = ST - 1); GPC shot groups of 8 walked by one CTA.  The last two change
@@ -123,13 +122,14 @@ __device__ __forceinline__ unsigned long long globaltimer()
     return t;
 }
 
-// Wait for an mbarrier phase; false (and the status word set) after the deadline.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status)
+// Wait for an mbarrier phase; false (and the status word set) once wait_ns
+// nanoseconds have passed (the handle's wait limit, hv_set_wait_limit).
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *status, unsigned long long wait_ns)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (globaltimer() - t0 > kWaitNs) {
+        if (globaltimer() - t0 > wait_ns) {
             atomicExch(status, HV_ETIMEOUT);
             return false;
         }
@@ -171,10 +171,11 @@ __device__ __forceinline__ void publish_item(int *c)
     asm volatile("red.release.gpu.global.add.s32 [%0], 1;" ::"l"(c) : "memory");
 }
 
-// Thread 0: waits (bounded) until tile `tile` and its neighbours have `need`
-// completed items of shot group g.  false after the deadline (status set) or
-// when another CTA has already reported an error.
-__device__ bool wait_neighbourhood(const int *cnt, int g, int tile, int ntx, int ntiles, int need, int *status)
+// Thread 0: waits (bounded by wait_ns) until tile `tile` and its neighbours
+// have `need` completed items of shot group g.  false after the deadline
+// (status set) or when another CTA has already reported an error.
+__device__ bool wait_neighbourhood(const int *cnt, int g, int tile, int ntx, int ntiles, int need, int *status,
+                                   unsigned long long wait_ns)
 {
     const int ntz = ntiles / ntx;
     const int tz = tile / ntx, tx = tile - tz * ntx;
@@ -188,7 +189,7 @@ __device__ bool wait_neighbourhood(const int *cnt, int g, int tile, int ntx, int
             while (ld_acquire(c) < need) {
                 if (t0 == 0) t0 = globaltimer();
                 if (*(volatile int *)status != 0) return false;
-                if (globaltimer() - t0 > kWaitNs) {
+                if (globaltimer() - t0 > wait_ns) {
                     atomicExch(status, HV_ETIMEOUT);
                     return false;
                 }
@@ -203,12 +204,13 @@ __device__ bool wait_neighbourhood(const int *cnt, int g, int tile, int ntx, int
 // group of shots [s0, s1) in dataflow mode, else the grid-dependency wait.
 // false if the CTA must give up (every thread gets the same answer).
 __device__ __forceinline__ bool wait_for_inputs(bool flow, const int *cnt, int s0, int s1, int gsz, int tile, int ntx,
-                                                int ntiles, int need, int *status)
+                                                int ntiles, int need, int *status, unsigned long long wait_ns)
 {
     bool ok = true;
     if (flow) {
         if (threadIdx.x == 0)
-            for (int g = s0 / gsz; g * gsz < s1 && ok; ++g) ok = wait_neighbourhood(cnt, g, tile, ntx, ntiles, need, status);
+            for (int g = s0 / gsz; g * gsz < s1 && ok; ++g)
+                ok = wait_neighbourhood(cnt, g, tile, ntx, ntiles, need, status, wait_ns);
     } else {
         grid_dependency_wait();
     }
@@ -406,6 +408,7 @@ struct FwdParams {
     const float *az, *ax, *wavelet;
     const int *src_zx, *rt_off, *rt_rec, *rt_pos;
     int *status;
+    unsigned long long wait_ns;  // limit of every device wait [ns]
     int n, nt, nr, ns, k, spg, gsz;
     int *cnt;                   // step counters per (shot group, tile), or nullptr
     int need, flow;             // dataflow ordering (StepDeps)
@@ -478,9 +481,9 @@ __device__ __forceinline__ float2 leapfrog(float2 w, float2 wprev, float2 cc, fl
 // After a failed wait: wait (bounded) for the copies of items [from, to) still
 // in flight, so that none lands after the CTA has exited.
 template <int ST>
-__device__ __forceinline__ void drain_stages(uint64_t *bars, int from, int to, int *status)
+__device__ __forceinline__ void drain_stages(uint64_t *bars, int from, int to, int *status, unsigned long long wait_ns)
 {
-    for (int q = from; q < to; ++q) mbar_wait(&bars[q % ST], (q / ST) & 1, status);
+    for (int q = from; q < to; ++q) mbar_wait(&bars[q % ST], (q / ST) & 1, status, wait_ns);
 }
 
 // One forward time step.  grid = (ntiles, k or 1, shot groups).  Vector j = 0
@@ -521,7 +524,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
         fence_mbar_init();
     }
     // From here on the fields of earlier steps are complete and visible.
-    if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
+    if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status, p.wait_ns)) return;
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bars[C::ST], S::COEF_TX);
         tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[C::ST]);
@@ -540,9 +543,9 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
     const float wav = p.wavelet[p.n];
 
-    bool ok = mbar_wait(&bars[C::ST], 0, p.status);
+    bool ok = mbar_wait(&bars[C::ST], 0, p.status, p.wait_ns);
     if (__syncthreads_or(!ok)) {
-        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
+        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status, p.wait_ns);
         return;
     }
 
@@ -550,10 +553,10 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
         constexpr bool SP = decltype(sp_tag)::value;
         for (int i = 0; i < nitems; ++i) {
             const int st = i % C::ST, s = s0 + i;
-            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status);
+            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status, p.wait_ns);
             if (__syncthreads_or(!ok)) {
                 // a copy did not arrive: let the other stages drain (bounded), then give up
-                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status);
+                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status, p.wait_ns);
                 return;
             }
             const unsigned char *base = smem + st * S::STAGE;
@@ -638,6 +641,7 @@ struct Fwd2Params {
     const float *az, *ax, *wavelet;
     const int *src_zx, *rt_off;
     int *status;
+    unsigned long long wait_ns;
     int n, ns, spg;
     Geo g;
 };
@@ -703,9 +707,9 @@ __global__ void __launch_bounds__(C::NT, 1) k_fwd2(const __grid_constant__ Fwd2P
     }
     allow_dependent_launch();
 
-    bool ok = mbar_wait(&bars[C::ST], 0, p.status);
+    bool ok = mbar_wait(&bars[C::ST], 0, p.status, p.wait_ns);
     if (__syncthreads_or(!ok)) {
-        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
+        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status, p.wait_ns);
         return;
     }
 
@@ -713,9 +717,9 @@ __global__ void __launch_bounds__(C::NT, 1) k_fwd2(const __grid_constant__ Fwd2P
         constexpr bool SP1 = decltype(sp1_tag)::value, SP2 = decltype(sp2_tag)::value;
         for (int i = 0; i < nitems; ++i) {
             const int st = i % C::ST, s = s0 + i;
-            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status);
+            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status, p.wait_ns);
             if (__syncthreads_or(!ok)) {
-                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status);
+                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status, p.wait_ns);
                 return;
             }
             const unsigned char *base = smem + st * S::STAGE;
@@ -792,6 +796,7 @@ struct AdjParams {
     const float *az, *ax, *wavelet;
     const int *src_zx, *rt_off, *rt_rec, *rt_pos;
     int *status;
+    unsigned long long wait_ns;
     int n, nt, nr, ns, k, spg, gsz;
     int *cnt;
     int need, flow;
@@ -809,8 +814,10 @@ struct AdjSmem {
 // One adjoint time step with zero-lag imaging.  grid = (ntiles, k, blocks of
 // GPC shot groups); for each group of 8 shots the CTA sums the shots' image
 // contributions in shot order and adds them to the group's double-float partial image
-// once per step.
-template <class C>
+// once per step.  IMG64 (the precision check of hv_set_image_precision): each
+// shot's product lam^n Q^n, exact in FP64, is added to the group's FP64 image
+// instead (the CTA owns its tile's points of that image).
+template <class C, bool IMG64 = false>
 __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2) k_adj(const __grid_constant__ AdjParams p)
 {
     using S = AdjSmem<C>;
@@ -841,7 +848,7 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
         for (int q = 0; q <= C::ST; ++q) mbar_init(&bars[q], 1);
         fence_mbar_init();
     }
-    if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status)) return;
+    if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status, p.wait_ns)) return;
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bars[C::ST], C::PT);
         tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[C::ST]);
@@ -924,10 +931,10 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
         }
     };
 
-    if (nitems > 0) prefetch(s0 / p.gsz);
-    bool ok = mbar_wait(&bars[C::ST], 0, p.status);
+    if (!IMG64 && nitems > 0) prefetch(s0 / p.gsz);
+    bool ok = mbar_wait(&bars[C::ST], 0, p.status, p.wait_ns);
     if (__syncthreads_or(!ok)) {
-        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status);
+        drain_stages<C::ST>(bars, 0, min(C::ST, nitems), p.status, p.wait_ns);
         return;
     }
 
@@ -937,7 +944,7 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
             const int st = i % C::ST, s = s0 + i;
             const int fo = j * p.ns + s;
             const int rb = tab.rb[i], re = tab.re[i];
-            if (i > 0 && s % p.gsz == 0) prefetch(s / p.gsz);
+            if (!IMG64 && i > 0 && s % p.gsz == 0) prefetch(s / p.gsz);
             if (rb < re) {                         // receivers in this tile: stage their sources
                 for (int q = threadIdx.x; q < C::TZ * C::TX; q += C::NT) ssrc[q] = 0.0f;
                 __syncthreads();
@@ -948,9 +955,9 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
                     ssrc[zz * C::TX + xx] = p.rscale * rs[p.rt_rec[s * p.nr + q]];
                 }
             }
-            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status);
+            ok = mbar_wait(&bars[st], (i / C::ST) & 1, p.status, p.wait_ns);
             if (__syncthreads_or(!ok)) {
-                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status);
+                drain_stages<C::ST>(bars, i + 1, min(i + C::ST, nitems), p.status, p.wait_ns);
                 return false;
             }
             const unsigned char *base = smem + st * S::STAGE;
@@ -978,12 +985,23 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     o[h] = leapfrog<SP>(lc[r][h], l2[h], cc[h], Ll[r][h], inv[h], nom[h]);
-                    acc[r][h] = f2fma(o[h], Qu[r][h], acc[r][h]);
+                    if constexpr (!IMG64) acc[r][h] = f2fma(o[h], Qu[r][h], acc[r][h]);
                 }
                 if (z < p.g.NZ && xb < p.g.NX) st4(ln + (size_t)(z + GH) * p.g.P + (xb + GH), o, xb, p.g.NX);
+                if constexpr (IMG64) {
+                    if (z < p.g.NZ) {
+                        double *im = p.img + ((size_t)(s / p.gsz) * p.k + j) * p.g.fsize + (size_t)(z + GH) * p.g.P +
+                                     (xb + GH);
+                        const float ov[4] = {o[0].x, o[0].y, o[1].x, o[1].y};
+                        const float qv[4] = {Qu[r][0].x, Qu[r][0].y, Qu[r][1].x, Qu[r][1].y};
+#pragma unroll
+                        for (int c = 0; c < 4; ++c)
+                            if (xb + c < p.g.NX) im[c] += (double)ov[c] * (double)qv[c];
+                    }
+                }
             }
             const bool group_end = (s + 1) % p.gsz == 0 || i + 1 == nitems;
-            if (group_end) flush(s / p.gsz);
+            if (!IMG64 && group_end) flush(s / p.gsz);
             __syncthreads();
             if (threadIdx.x == 0) {
                 if (p.cnt && group_end) publish_item(p.cnt + (size_t)(s / p.gsz) * p.g.ntiles + tile);
@@ -1460,8 +1478,8 @@ template <class K>
 int ensure_smem(int slot, int dev, K kern, int bytes)
 {
     static std::mutex mu;
-    static bool done[64][64] = {};
-    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 64) return hvi::fail(HV_EINVAL, "internal: kernel slot %d/%d", slot, dev);
+    static bool done[96][64] = {};
+    if (dev < 0 || dev >= 64 || slot < 0 || slot >= 96) return hvi::fail(HV_EINVAL, "internal: kernel slot %d/%d", slot, dev);
     std::lock_guard<std::mutex> g(mu);
     if (done[slot][dev]) return HV_OK;
     HV_RT_INTERNAL(set_smem(kern, bytes));
@@ -1559,8 +1577,10 @@ int prepare_kernels(const hv_handle *h)
         });
         if (rc != HV_OK) return rc;
     }
-    return HV_OK;
+    return ensure_smem(4 * kTileMenu, h->device, k_adj<Cfg64x8, true>, AdjSmem<Cfg64x8>::BYTES);
 }
+
+int adj_f64_cfg() { return 5; }   // the menu entry (64 x 8) that has the FP64-image adjoint
 
 int make_maps(const hv_handle *h, void *ws, long long nfields, TmaMaps *m)
 {
@@ -1603,6 +1623,7 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
         p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
         p.status = h->status;
+        p.wait_ns = h->wait_ns;
         p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : 1;
         p.gsz = (h->ns + adj_groups(h) - 1) / adj_groups(h);   // the adjoint's shot groups
         p.spg = p.gsz * C::GPC;                                  // shots per CTA: GPC whole groups
@@ -1643,6 +1664,7 @@ int launch_fwd2(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaM
         p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
         p.src_zx = h->src_zx; p.rt_off = rt.off;
         p.status = h->status;
+        p.wait_ns = h->wait_ns;
         p.n = a.n; p.ns = h->ns;
         const int gsz = (h->ns + adj_groups(h) - 1) / adj_groups(h);
         p.spg = gsz * C::GPC;
@@ -1770,6 +1792,7 @@ int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
         p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
         p.status = h->status;
+        p.wait_ns = h->wait_ns;
         p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = a.k;
         p.gsz = (h->ns + a.G - 1) / a.G;    // shots per group (the last group may be shorter)
         p.spg = p.gsz * C::GPC;             // shots per CTA: GPC whole groups
@@ -1777,8 +1800,14 @@ int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         p.need = a.deps.need;
         p.flow = a.deps.flow ? 1 : 0;
         p.g = geo(h, t);
-        HV_RT_INTERNAL(ensure_smem(2 * kTileMenu + cfg, h->device, k_adj<C>, AdjSmem<C>::BYTES));
         dim3 grid(t.ntiles, a.k, (a.G + C::GPC - 1) / C::GPC);
+        if constexpr (std::is_same<C, Cfg64x8>::value) {
+            if (a.img_f64) {
+                HV_RT_INTERNAL(ensure_smem(4 * kTileMenu, h->device, k_adj<C, true>, AdjSmem<C>::BYTES));
+                return launch_step(k_adj<C, true>, grid, C::NT, AdjSmem<C>::BYTES, st, pdl(h), p, "k_adj launch");
+            }
+        }
+        HV_RT_INTERNAL(ensure_smem(2 * kTileMenu + cfg, h->device, k_adj<C>, AdjSmem<C>::BYTES));
         return launch_step(k_adj<C>, grid, C::NT, AdjSmem<C>::BYTES, st, pdl(h), p, "k_adj launch");
     });
 }

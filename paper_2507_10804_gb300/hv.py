@@ -222,6 +222,26 @@ class Problem:
                                       self._stream()))
         return phi, g
 
+    def misfit(self, m: torch.Tensor, d_obs: torch.Tensor) -> torch.Tensor:
+        """phi = 1/(2 sigma^2) sum (f(m) - d_obs)^2 as a 0-d float64 CUDA tensor (hv_misfit)."""
+        pd = _dev(d_obs, torch.float32, (self.ns, self.nt, self.nr), "d_obs", self.device)
+        phi = torch.empty((), dtype=torch.float64, device=self.device)
+        ws, nb = self._workspace(_lib.HV_OP_MISFIT, 1, HV_CKPT_ALL)
+        check(self.lib.hv_misfit(self._h, self._m(m), pd, phi.data_ptr(), ws, nb, self._stream()))
+        return phi
+
+    def set_image_precision(self, mode: int) -> None:
+        """Imaging sum: HV_IMAGE_PAIRS (default) or the FP64 check HV_IMAGE_FP64 (hv_set_image_precision)."""
+        check(self.lib.hv_set_image_precision(self._h, int(mode)))
+
+    def set_wait_limit(self, seconds: float) -> None:
+        """Limit of every bounded device wait of this problem's kernels (hv_set_wait_limit)."""
+        check(self.lib.hv_set_wait_limit(self._h, float(seconds)))
+
+    def inject_wait_timeout(self) -> None:
+        """Make the next dataflow-ordered stencil step's waits run out (hv_inject_wait_timeout; testing)."""
+        check(self.lib.hv_inject_wait_timeout(self._h))
+
     def hessian_apply(self, m: torch.Tensor, v: torch.Tensor, ckpt: int = HV_CKPT_ALL,
                       out_dtype=torch.float32) -> torch.Tensor:
         """H_d v for v[k, nz, nx] -> [k, nz, nx] (float32 or float64 output)."""
@@ -235,6 +255,30 @@ class Problem:
         check(fn(self._h, self._m(m), pv, k, out.data_ptr(), int(ckpt), ws, nb, self._stream()))
         return out
 
+
+    def hessian_apply_partial(self, m: torch.Tensor, v: torch.Tensor, ckpt: int = HV_CKPT_ALL) -> torch.Tensor:
+        """The extended image of this problem's shots before the fold, [k, NZ, NX] float64
+        (hv_hessian_apply_partial); sum it over shot blocks, then fold."""
+        k = v.shape[0]
+        pv = _dev(v, torch.float32, (k, self.nz, self.nx), "v", self.device)
+        ext = torch.empty((k, self.NZ, self.NX), dtype=torch.float64, device=self.device)
+        ws, nb = self._workspace(HV_OP_HV, k, ckpt)
+        check(self.lib.hv_hessian_apply_partial(self._h, self._m(m), pv, k, ext.data_ptr(), int(ckpt), ws, nb,
+                                                self._stream()))
+        return ext
+
+    def fold(self, ext: torch.Tensor, out_dtype=torch.float32) -> torch.Tensor:
+        """E^T of extended images [k, NZ, NX] float64 -> [k, nz, nx] (hv_image_fold)."""
+        k = ext.shape[0]
+        pe = _dev(ext, torch.float64, (k, self.NZ, self.NX), "ext", self.device)
+        out = torch.empty((k, self.nz, self.nx), dtype=out_dtype, device=self.device)
+        if out_dtype == torch.float32:
+            check(self.lib.hv_image_fold(self._h, pe, k, out.data_ptr(), None, self._stream()))
+        elif out_dtype == torch.float64:
+            check(self.lib.hv_image_fold(self._h, pe, k, None, out.data_ptr(), self._stream()))
+        else:
+            raise ValueError("out_dtype must be float32 or float64")
+        return out
 
     # ---------------------------------------------------------------- approximations
     def approx_build_psf(self, m: torch.Tensor, spacing: int, n_batches: int = 4,
@@ -500,7 +544,7 @@ class Posterior:
     H~_d = B B^T from a square-root approximation `approx` (or 0), R the Matern prior (delta, gamma)."""
 
     def __init__(self, nz: int, nx: int, h: float, delta: float, gamma: float, approx: "Approx | None" = None,
-                 device=None):
+                 device=None, max_k: int = 64):
         self.lib = _lib.load()
         self.device = (approx.device if approx is not None else
                        torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device))
@@ -509,7 +553,8 @@ class Posterior:
         p = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             check(self.lib.hv_posterior_create(self.nz, self.nx, float(h), float(delta), float(gamma),
-                                               approx._a if approx is not None else None, ctypes.byref(p)))
+                                               approx._a if approx is not None else None, int(max_k),
+                                               ctypes.byref(p)))
         self._p = p
 
     def _stream(self):

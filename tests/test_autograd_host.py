@@ -19,6 +19,14 @@ class LinearProblem:
     def migrate(self, m, r, ckpt=-1):
         return (self.A.T @ r.reshape(-1).to(torch.float64)).reshape(self.shape_m).to(m.dtype)
 
+    def misfit_grad(self, m, d_obs, ckpt=-1):
+        r = self.fwd_model(m).to(torch.float64) - d_obs.to(torch.float64)
+        phi = 0.5 * (r * r).sum() / self.sigma ** 2
+        return phi, self.migrate(m, (r / self.sigma ** 2).to(m.dtype))
+
+    def misfit(self, m, d_obs):
+        return self.misfit_grad(m, d_obs)[0]
+
     def born(self, m, dm):
         return (self.A @ dm.reshape(dm.shape[0], -1).T.to(torch.float64)).T.reshape(dm.shape[0], *self.shape_d)
 
@@ -32,6 +40,12 @@ def test_backward_is_migration_and_gradcheck():
     phi.backward()
     r = (P.A @ m.detach().reshape(-1) - dobs.reshape(-1)) / P.sigma ** 2
     assert torch.allclose(m.grad.reshape(-1), P.A.T @ r)
+    # the chain rule scales by the incoming gradient; no gradient wanted: the misfit alone
+    m.grad = None
+    (3.0 * misfit(P, m, dobs)).backward()
+    assert torch.allclose(m.grad.reshape(-1), 3.0 * (P.A.T @ r))
+    with torch.no_grad():
+        assert torch.allclose(misfit(P, m, dobs), 0.5 * (r * r).sum() * P.sigma ** 2)
 
 
 def test_forward_mode_is_born():

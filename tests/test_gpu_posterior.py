@@ -191,3 +191,31 @@ def test_gpcn_chain_on_the_quadratic_model(model):
     assert torch.isfinite(m).all() and torch.isfinite(delta).all()
     assert 0 < total <= c * steps
     P.close()
+
+
+def test_posterior_calls_allocate_nothing_and_respect_max_k(model):
+    """All scratch is sized at create for max_k fields: later calls allocate no device memory,
+    and a call with more fields is rejected."""
+    Q, D, S, a, b = model
+    from paper_2507_10804_gb300._lib import HvError
+    P = Posterior(NZ, NX, H, DELTA, GAMMA, approx=S, max_k=8)
+    n1, n1t = _normals(31, 8)
+    n2, n2t = _normals(32, 8)
+    omega = torch.tensor(synth.normal(33, 8 * NZ * NX).reshape(8, NZ, NX), dtype=torch.float32, device="cuda")
+    for rep in range(2):        # the first pass warms the operator's and torch's own caches
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        P.correct(Q, omega, 4, rtol=1e-6)
+        z, _ = P.sample(n1t, n2t)
+        x, _ = P.solve(n1t, rtol=1e-6)
+        y = P.apply(n1t)
+        torch.cuda.synchronize()
+    # the outputs above are torch's (3 x 8 fields, reused from its cache); nothing else may appear
+    assert torch.cuda.mem_get_info()[0] >= free0 - (2 << 20)
+    assert torch.isfinite(z).all() and torch.isfinite(x).all() and torch.isfinite(y).all()
+    big = torch.zeros((9, NZ, NX), dtype=torch.float32, device="cuda")
+    with pytest.raises(HvError):
+        P.solve(big)
+    with pytest.raises(HvError):
+        P.apply(big)
+    P.close()

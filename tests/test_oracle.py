@@ -248,6 +248,26 @@ def test_dense_hessian_bruteforce_8x8():
     assert np.linalg.eigvalsh(H_dense).min() > -1e-10 * np.abs(H_dense).max()
 
 
+def test_extended_image_folds_to_the_hessian_and_adds_over_shots():
+    """The extended image before the fold (the per-source sum of section 3): its fold is the
+    Hessian apply; <E u, ext> is the Born-data inner product <F u, F v> / sigma^2 (no adjoint
+    solve on that side); the images of two shot blocks add up to the image of all shots."""
+    P, m = small_problem(ns=3, sigma=0.8)
+    u, v = synth.smoothed_normal_vectors(12, 2, P.nz, P.nx, 1.5)
+    ext = O.hessian_image(P, m, v)[0]
+    assert np.array_equal(O.fold(P, ext), O.hessian_apply(P, m, v))
+    Fu, Fv = O.born(P, m, u[None])[0], O.born(P, m, v[None])[0]
+    a, b = np.vdot(O.extend(P, u), ext), np.vdot(Fu, Fv) / P.sigma ** 2
+    assert abs(a - b) <= 1e-12 * abs(b)
+    parts = []
+    for idx in ([0, 2], [1]):
+        Q = O.Problem(nz=P.nz, nx=P.nx, nb=P.nb, h=P.h, nt=P.nt, dt=P.dt, f0=P.f0, t0=P.t0, vmax=P.vmax,
+                      src_iz=np.asarray(P.src_iz)[idx], src_ix=np.asarray(P.src_ix)[idx],
+                      rec_iz=np.asarray(P.rec_iz)[idx], rec_ix=np.asarray(P.rec_ix)[idx], sigma=P.sigma)
+        parts.append(O.hessian_image(Q, m, v)[0])
+    assert rel(parts[0] + parts[1], ext) < 1e-13
+
+
 def test_multithreaded_oracle_is_deterministic():
     P, m = small_problem(ns=4)
     v = synth.smoothed_normal_vectors(10, 1, P.nz, P.nx, 1.5)
