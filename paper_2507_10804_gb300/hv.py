@@ -256,6 +256,39 @@ class Problem:
         return out
 
 
+    def apply_batch(self, m: torch.Tensor, hv=(), grads=(), misfits=(), ckpt: int = HV_CKPT_ALL):
+        """One merged call at model m (hv_apply_batch): H v for each v[k, nz, nx] in ``hv``, (phi, gradient)
+        for each observed data set in ``grads``, phi for each in ``misfits``; every result bitwise that of
+        the separate call.  Returns (list of H v, list of (phi, grad), list of phi)."""
+        hv, grads, misfits = list(hv), list(grads), list(misfits)
+        dshape = (self.ns, self.nt, self.nr)
+        pv = [_dev(v, torch.float32, (v.shape[0], self.nz, self.nx), "v", self.device) for v in hv]
+        outs = [torch.empty(v.shape, dtype=torch.float32, device=self.device) for v in hv]
+        pg = [_dev(d, torch.float32, dshape, "d_obs", self.device) for d in grads]
+        gphi = [torch.empty((), dtype=torch.float64, device=self.device) for _ in grads]
+        gout = [torch.empty((self.nz, self.nx), dtype=torch.float32, device=self.device) for _ in grads]
+        pm = [_dev(d, torch.float32, dshape, "d_obs", self.device) for d in misfits]
+        mphi = [torch.empty((), dtype=torch.float64, device=self.device) for _ in misfits]
+
+        def arr(ptrs, t=ctypes.c_void_p):
+            return (t * max(len(ptrs), 1))(*ptrs)
+
+        keep = [arr(pv), arr([v.shape[0] for v in hv], ctypes.c_int), arr([o.data_ptr() for o in outs]),
+                arr(pg), arr([x.data_ptr() for x in gphi]), arr([x.data_ptr() for x in gout]),
+                arr(pm), arr([x.data_ptr() for x in mphi])]
+        b = _lib.HvBatch(len(hv), keep[0], keep[1], keep[2], len(grads), keep[3], keep[4], keep[5],
+                         len(misfits), keep[6], keep[7])
+        n = ctypes.c_size_t()
+        check(self.lib.hv_batch_workspace_size(self._h, ctypes.byref(b), int(ckpt), ctypes.byref(n)))
+        buf = self._ws.get("ws")
+        if buf is None or buf.numel() < n.value:
+            self._ws.pop("ws", None)
+            buf = torch.empty(max(n.value, 256), dtype=torch.uint8, device=self.device)
+            self._ws["ws"] = buf
+        check(self.lib.hv_apply_batch(self._h, self._m(m), ctypes.byref(b), int(ckpt), buf.data_ptr(), buf.numel(),
+                                      self._stream()))
+        return outs, list(zip(gphi, gout)), mphi
+
     def hessian_apply_partial(self, m: torch.Tensor, v: torch.Tensor, ckpt: int = HV_CKPT_ALL) -> torch.Tensor:
         """The extended image of this problem's shots before the fold, [k, NZ, NX] float64
         (hv_hessian_apply_partial); sum it over shot blocks, then fold."""

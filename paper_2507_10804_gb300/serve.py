@@ -1,6 +1,7 @@
 """Python face of the request server (hv_server_*): submit H v, gradient and
 misfit requests from many clients; the library's scheduler admits them by
-device-memory budget and runs them concurrently on its streams.
+device-memory budget, merges queued requests on one problem and model into
+one call, and runs them concurrently on its streams.
 
 Tensors passed to ``submit`` are kept alive by the server object until the
 request is done.
@@ -74,6 +75,11 @@ class Server:
         phi = torch.empty((), dtype=torch.float64, device=self.device)
         return self._submit(HV_REQ_MISFIT, P, m, d_obs=d_obs, phi=phi), phi
 
+    def set_batching(self, max_vectors: int) -> None:
+        """Merge queued requests on one problem and model into one call of up to max_vectors Born
+        vectors (< 2: no merging; hv_server_set_batching)."""
+        check(self.lib.hv_server_set_batching(self._s, int(max_vectors)))
+
     def poll(self, rid: int) -> int:
         st = ctypes.c_int()
         check(self.lib.hv_poll(self._s, int(rid), ctypes.byref(st)))
@@ -91,4 +97,4 @@ class Server:
         i = _lib.HvRequestInfo()
         check(self.lib.hv_request_get_info(self._s, int(rid), ctypes.byref(i)))
         return {"kind": i.kind, "status": i.status, "t_submit": i.t_submit, "t_start": i.t_start,
-                "t_done": i.t_done, "ws_bytes": i.ws_bytes}
+                "t_done": i.t_done, "ws_bytes": i.ws_bytes, "batch": i.batch}

@@ -157,3 +157,52 @@ def test_approximation_modes_in_the_mix(problems):
     S.close()
     L.close()
     Q.close()
+
+
+def test_merged_call_equals_separate_calls_bitwise(problems):
+    """hv_apply_batch: H v entries, gradients and misfits at one model share one forward sweep;
+    every output is bitwise that of its separate call (and a misfit-only batch too)."""
+    w, P = problems[0]
+    m = t(w.m)
+    v1, v2 = t(w.v[:1]), t(w.v[:2])
+    d1 = t(synth.normal(61, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3)
+    d2 = t(synth.normal(62, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3)
+    ref_h = [P.hessian_apply(m, v, ckpt=5).cpu().numpy() for v in (v1, v2)]
+    ref_g = [[x.cpu().numpy() for x in P.misfit_grad(m, d, ckpt=5)] for d in (d1, d2)]
+    ref_m = P.misfit(m, d2).cpu().numpy()
+    hv, gr, mi = P.apply_batch(m, hv=[v1, v2], grads=[d1, d2], misfits=[d2], ckpt=5)
+    for a, b in zip(hv, ref_h):
+        assert np.array_equal(a.cpu().numpy(), b)
+    for (phi, g), (rphi, rg) in zip(gr, ref_g):
+        assert np.array_equal(phi.cpu().numpy(), rphi) and np.array_equal(g.cpu().numpy(), rg)
+    assert np.array_equal(mi[0].cpu().numpy(), ref_m)
+    _, _, only = P.apply_batch(m, misfits=[d1, d2])
+    assert np.array_equal(only[1].cpu().numpy(), ref_m)
+
+
+def test_queued_requests_on_one_model_run_as_one_call(problems):
+    """Continuous batching: requests queued behind a running one, on one problem and model, are
+    admitted together as one merged call (info()["batch"]) with results bitwise equal to direct calls;
+    with batching off the same requests run one by one."""
+    (w, P), (w2, P2) = problems
+    m = t(w.m)
+    vs = [t(w.v[:1]), t(w.v[1:2])]
+    d = t(synth.normal(71, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3)
+    ref_h = [P.hessian_apply(m, v, ckpt=5).cpu().numpy() for v in vs]
+    ref_phi, ref_g = (x.cpu().numpy() for x in P.misfit_grad(m, d, ckpt=5))
+    ref_m = P.misfit(m, d).cpu().numpy()
+    for batching in (64, 0):
+        S = Server(hbm_budget=2 << 30, max_concurrent=1)
+        S.set_batching(batching)
+        blocker, _ = S.submit_hv(P2, t(w2.m), t(w2.v), ckpt=1)        # about 80k recomputed steps
+        (r1, o1), (r2, o2) = (S.submit_hv(P, m, v, ckpt=5) for v in vs)
+        r3, phi, g = S.submit_grad(P, m, d, ckpt=5)
+        r4, phm = S.submit_misfit(P, m, d)
+        for rid in (blocker, r1, r2, r3, r4):
+            assert S.wait(rid, timeout=300) == 0
+        assert S.info(blocker)["batch"] == 1
+        assert [S.info(r)["batch"] for r in (r1, r2, r3, r4)] == ([4] * 4 if batching else [1] * 4)
+        assert np.array_equal(o1.cpu().numpy(), ref_h[0]) and np.array_equal(o2.cpu().numpy(), ref_h[1])
+        assert np.array_equal(phi.cpu().numpy(), ref_phi) and np.array_equal(g.cpu().numpy(), ref_g)
+        assert np.array_equal(phm.cpu().numpy(), ref_m)
+        S.close()
