@@ -463,6 +463,33 @@ int hv_approx_build_pdo_op(const hv_operator *op, double rho0, int r, hv_approx 
 int hv_approx_build_lr_op(const hv_operator *op, double delta, double gamma, int rank, const float *omega, int k,
                           hv_approx **out, void *stream);
 
+/* High-pass filter before the PSF and PDO approximations (sections 3.2 and
+ * 3.7: the low-frequency part of H_d -- transmission, non-local PSFs, too low
+ * for spectral separation -- is removed before approximating and left to the
+ * low-rank correction).  The paper does not specify the filter; this library
+ * uses the radial Gaussian high-pass on the periodic 2D DFT of the nz x nx
+ * grid, F_hp v = Re F^-1 (phi(|xi|) F v), phi(rho) = 1 - exp(-rho^2 /
+ * (2 rho_c^2)), xi = (2 pi k_z / (nz h), 2 pi k_x / (nx h)) for the signed DFT
+ * indices, rho_c [rad/m] the cutoff, and applies it on both sides,
+ * F_hp H_d F_hp, so the approximated operator stays symmetric.
+ *  - hv_highpass_apply: out = F_hp v for k fields [k][nz][nx] (device; out
+ *    may be v); builds and frees its transforms; synchronous on `stream`.
+ *  - hv_set_highpass(h, rho_c): hv_approx_build_psf and hv_approx_build_pdo on
+ *    this handle approximate F_hp H_d F_hp (rho_c > 0) or H_d (0, the default).
+ *    The filtered builds allocate the filter's transforms and a scratch of
+ *    n_batches (PSF) or 1 (PDO) fields, freed before they return.
+ *  - hv_filtered_create(inner, rho_c, max_k, out): F_hp inner F_hp as an
+ *    object that owns the transforms and a scratch of max_k fields;
+ *    hv_filtered_operator fills an hv_operator that applies it (in chunks of
+ *    max_k fields; applies on one object run one after another), for the *_op
+ *    builds; hv_filtered_destroy frees it (the inner operator must outlive it). */
+typedef struct hv_filtered hv_filtered;
+int hv_highpass_apply(int nz, int nx, double h, double rho_c, const float *v, int k, float *out, void *stream);
+int hv_set_highpass(hv_handle *h, double rho_c);
+int hv_filtered_create(const hv_operator *inner, double rho_c, int max_k, hv_filtered **out);
+int hv_filtered_operator(hv_filtered *f, hv_operator *op);
+int hv_filtered_destroy(hv_filtered *f);
+
 /* The ideal quadratic test model (section 4.1).  Misfit Hessian
  *   H_d = A A^T + V_r Lambda_r V_r^T                        (eq. (toy-hess))
  * with A the order-1/2 PsiDO of eq. (toy-symbol),

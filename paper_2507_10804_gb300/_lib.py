@@ -121,6 +121,11 @@ _SIGS = {
                                c_int),
     "hv_approx_build_lr_op": ([ctypes.POINTER(HvOperator), c_double, c_double, c_int, fp, c_int,
                                ctypes.POINTER(c_void_p), c_void_p], c_int),
+    "hv_highpass_apply": ([c_int, c_int, c_double, c_double, fp, c_int, fp, c_void_p], c_int),
+    "hv_set_highpass": ([c_void_p, c_double], c_int),
+    "hv_filtered_create": ([ctypes.POINTER(HvOperator), c_double, c_int, ctypes.POINTER(c_void_p)], c_int),
+    "hv_filtered_operator": ([c_void_p, ctypes.POINTER(HvOperator)], c_int),
+    "hv_filtered_destroy": ([c_void_p], c_int),
     "hv_quad_create": ([c_int, c_int, c_double, c_double, c_int, c_int, ctypes.POINTER(c_double), c_double, c_double,
                         ctypes.POINTER(c_void_p)], c_int),
     "hv_quad_apply": ([c_void_p, c_int, fp, c_int, fp, c_void_p], c_int),

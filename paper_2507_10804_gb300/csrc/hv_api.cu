@@ -1500,6 +1500,134 @@ static int pdo_finish(const hvk::LrGeo &g, int device, float *vp, float *hvp, co
 static int lr_finish(int nz, int nx, double hh, int device, double delta, double gamma, int rank, const float *omega,
                      int k, float *Y, const HessFn &hess, cudaStream_t st, hv_approx **out);
 
+// The high-pass filter around an operator during a build (sections 3.2, 3.7):
+// X -> F_hp Op(F_hp X), the filter's transforms and a scratch of kmax fields
+// allocated here and freed (after the stream drains) when the build returns.
+namespace {
+struct Filter {
+    hvk::Highpass F;
+    float *T = nullptr;
+    cudaStream_t st = nullptr;
+    bool made = false;
+    int init(int nz, int nx, double hh, double rho_c, int kmax, cudaStream_t s)
+    {
+        st = s;
+        made = true;
+        HV_RT(hvk::highpass_create(F, nz, nx, hh, rho_c, kmax));
+        HV_CK(cudaMalloc(&T, (size_t)kmax * nz * nx * sizeof(float)));
+        return HV_OK;
+    }
+    HessFn wrap(const HessFn &inner)
+    {
+        return [this, inner](const float *X, int k, float *Z) {
+            const size_t N = (size_t)F.nz * F.nx;
+            for (int q0 = 0; q0 < k; q0 += F.kmax) {
+                const int kb = std::min(F.kmax, k - q0);
+                HV_RT(hvk::highpass_apply(F, X + q0 * N, kb, T, st));
+                HV_RT(inner(T, kb, Z + q0 * N));
+                HV_RT(hvk::highpass_apply(F, Z + q0 * N, kb, Z + q0 * N, st));
+            }
+            return HV_OK;
+        };
+    }
+    ~Filter()
+    {
+        if (!made) return;
+        if (st) cudaStreamSynchronize(st);
+        cudaFree(T);
+        hvk::highpass_destroy(F);
+    }
+};
+}  // namespace
+
+extern "C" int hv_set_highpass(hv_handle *h, double rho_c)
+{
+    if (!h) return hvi::fail(HV_EINVAL, "null handle");
+    if (!(rho_c >= 0)) return hvi::fail(HV_EINVAL, "high-pass cutoff %g; need >= 0 (0: off)", rho_c);
+    h->highpass = rho_c;
+    return HV_OK;
+}
+
+extern "C" int hv_highpass_apply(int nz, int nx, double h, double rho_c, const float *v, int k, float *out,
+                                 void *stream)
+{
+    if (!v || !out || k < 1) return hvi::fail(HV_EINVAL, "null field or k < 1");
+    cudaStream_t st = (cudaStream_t)stream;
+    hvk::Highpass F;
+    int rc = hvk::highpass_create(F, nz, nx, h, rho_c, std::min(k, 64));
+    if (rc == HV_OK) rc = hvk::highpass_apply(F, v, k, out, st);
+    cudaStreamSynchronize(st);
+    hvk::highpass_destroy(F);
+    return rc;
+}
+
+// An operator wrapped in the high-pass filter: F_hp Op F_hp.
+struct hv_filtered {
+    hv_operator inner{};
+    hvk::Highpass F;
+    float *T = nullptr;
+    int max_k = 0;
+    std::mutex mu;
+};
+
+namespace {
+int filtered_apply(void *ctx, const float *v, int k, float *out, void *stream)
+{
+    hv_filtered *f = static_cast<hv_filtered *>(ctx);
+    std::lock_guard<std::mutex> g(f->mu);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t N = (size_t)f->inner.nz * f->inner.nx;
+    for (int q0 = 0; q0 < k; q0 += f->max_k) {
+        const int kb = std::min(f->max_k, k - q0);
+        HV_RT(hvk::highpass_apply(f->F, v + q0 * N, kb, f->T, st));
+        const int rc = f->inner.apply(f->inner.ctx, f->T, kb, out + q0 * N, stream);
+        if (rc != HV_OK) return hvi::fail(rc, "the inner operator's apply returned %d", rc);
+        HV_RT(hvk::highpass_apply(f->F, out + q0 * N, kb, out + q0 * N, st));
+    }
+    return HV_OK;
+}
+}  // namespace
+
+extern "C" int hv_filtered_create(const hv_operator *inner, double rho_c, int max_k, hv_filtered **out)
+{
+    if (out) *out = nullptr;
+    if (!out || !inner || !inner->apply) return hvi::fail(HV_EINVAL, "null operator or output");
+    if (max_k < 1 || max_k > 4096) return hvi::fail(HV_EINVAL, "max_k = %d; need 1..4096", max_k);
+    hv_filtered *f = new hv_filtered;
+    f->inner = *inner;
+    f->max_k = max_k;
+    int rc = hvk::highpass_create(f->F, inner->nz, inner->nx, inner->h, rho_c, max_k);
+    if (rc == HV_OK && cudaMalloc(&f->T, (size_t)max_k * inner->nz * inner->nx * sizeof(float)) != cudaSuccess)
+        rc = hvi::fail(HV_ECUDA, "high-pass scratch: out of device memory");
+    if (rc != HV_OK) {
+        hv_filtered_destroy(f);
+        return rc;
+    }
+    *out = f;
+    return HV_OK;
+}
+
+extern "C" int hv_filtered_operator(hv_filtered *f, hv_operator *op)
+{
+    if (!f || !op) return hvi::fail(HV_EINVAL, "null filtered operator or output");
+    op->nz = f->inner.nz;
+    op->nx = f->inner.nx;
+    op->h = f->inner.h;
+    op->apply = filtered_apply;
+    op->ctx = f;
+    return HV_OK;
+}
+
+extern "C" int hv_filtered_destroy(hv_filtered *f)
+{
+    if (!f) return HV_OK;
+    cudaDeviceSynchronize();
+    cudaFree(f->T);
+    hvk::highpass_destroy(f->F);
+    delete f;
+    return HV_OK;
+}
+
 extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt,
                                    hv_approx **out, void *ws, size_t ws_bytes, void *stream)
 {
@@ -1516,11 +1644,15 @@ extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cel
     char *w = (char *)ws;
     float *vec = reinterpret_cast<float *>(w + P.vec);
     float *hv = reinterpret_cast<float *>(w + P.hv);
-    return psf_finish(g, h->device, vec, hv,
-                      [&](const float *X, int k, float *Z) {
-                          return run_adjoint(h, 2, m, X, k, Z, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st);
-                      },
-                      st, out);
+    HessFn hess = [&](const float *X, int k, float *Z) {
+        return run_adjoint(h, 2, m, X, k, Z, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st);
+    };
+    if (h->highpass > 0) {
+        Filter F;
+        HV_RT(F.init(h->nz, h->nx, h->h, h->highpass, n_batches, st));
+        return psf_finish(g, h->device, vec, hv, F.wrap(hess), st, out);
+    }
+    return psf_finish(g, h->device, vec, hv, hess, st, out);
 }
 
 // The PSF build after the geometry: impulse batches, one batched operator
@@ -1596,11 +1728,15 @@ extern "C" int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, in
     char *w = (char *)ws;
     float *vp = reinterpret_cast<float *>(w + P.vp);
     float *hvp = reinterpret_cast<float *>(w + P.hvp);
-    return pdo_finish(g, h->device, vp, hvp,
-                      [&](const float *X, int k, float *Z) {
-                          return run_adjoint(h, 2, m, X, k, Z, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st);
-                      },
-                      st, out);
+    HessFn hess = [&](const float *X, int k, float *Z) {
+        return run_adjoint(h, 2, m, X, k, Z, nullptr, nullptr, ckpt, w + P.inner, P.inner_bytes, st);
+    };
+    if (h->highpass > 0) {
+        Filter F;
+        HV_RT(F.init(h->nz, h->nx, h->h, h->highpass, 1, st));
+        return pdo_finish(g, h->device, vp, hvp, F.wrap(hess), st, out);
+    }
+    return pdo_finish(g, h->device, vp, hvp, hess, st, out);
 }
 
 // The PDO build after the sample geometry: probe, one operator application,

@@ -98,6 +98,8 @@ struct hv_handle {
     bool fuse_steps = false;
     // H v with every level stored on the shared-memory-resident kernels (hv_set_resident)
     bool resident = false;
+    // high-pass filter of the PSF and PDO builds (hv_set_highpass): cutoff rho_c [rad/m], 0 = off
+    double highpass = 0.0;
     // imaging accumulation (hv_set_image_precision): false = per-step FP32 sums over
     // a shot group added to double-float images; true = every shot's product added in FP64
     bool img_f64 = false;
@@ -256,6 +258,19 @@ int lr_fused_init(LrSym &L);
 int lr_fused_forward(const LrSym &L, const float2 *V, int nq, float *out, cudaStream_t st);
 int lr_fused_transpose(const LrSym &L, const float *w, int nq, float2 *V, cudaStream_t st);
 void launch_sqrt_real(const float2 *in, float2 *out, size_t n, cudaStream_t st);
+// The high-pass filter of the approximations (hv_highpass.cu): F_hp v =
+// Re F^-1 (phi(|xi|) F v), phi(rho) = 1 - exp(-rho^2 / (2 rho_c^2)).
+struct Highpass {
+    int nz = 0, nx = 0, kmax = 0;
+    double h = 0, rho_c = 0;
+    float *tab = nullptr;        // [nz][nx/2+1] phi / (nz nx)
+    float2 *spec = nullptr;      // [kmax][nz][nx/2+1]
+    cufftHandle fwd = 0, inv = 0, fwd1 = 0, inv1 = 0;   // R2C / C2R, batch kmax and batch 1
+    bool fwd_ok = false, inv_ok = false, fwd1_ok = false, inv1_ok = false;
+};
+int highpass_create(Highpass &F, int nz, int nx, double h, double rho_c, int kmax);
+void highpass_destroy(Highpass &F);
+int highpass_apply(Highpass &F, const float *v, int k, float *out, cudaStream_t st);   // out may be v
 // Matern prior and the low-rank approximation (hv_lowrank.cu).
 struct Prior {
     int nz = 0, nx = 0;

@@ -230,6 +230,11 @@ class Problem:
         check(self.lib.hv_misfit(self._h, self._m(m), pd, phi.data_ptr(), ws, nb, self._stream()))
         return phi
 
+    def set_highpass(self, rho_c: float) -> None:
+        """PSF and PDO builds on this problem approximate F_hp H_d F_hp (rho_c > 0 [rad/m]) or H_d (0)
+        (hv_set_highpass)."""
+        check(self.lib.hv_set_highpass(self._h, float(rho_c)))
+
     def set_image_precision(self, mode: int) -> None:
         """Imaging sum: HV_IMAGE_PAIRS (default) or the FP64 check HV_IMAGE_FP64 (hv_set_image_precision)."""
         check(self.lib.hv_set_image_precision(self._h, int(mode)))
@@ -456,6 +461,45 @@ def prior_apply(v: torch.Tensor, h: float, delta: float, gamma: float, op: int) 
     check(_lib.load().hv_prior_apply(nz, nx, float(h), float(delta), float(gamma), pv, k, out.data_ptr(), int(op),
                                      ctypes.c_void_p(torch.cuda.current_stream(v.device).cuda_stream)))
     return out
+
+
+def highpass_apply(v: torch.Tensor, h: float, rho_c: float) -> torch.Tensor:
+    """F_hp v = Re F^-1 (phi(|xi|) F v), phi(rho) = 1 - exp(-rho^2 / (2 rho_c^2)), for v [k, nz, nx]
+    (hv_highpass_apply): the high-pass filter applied before the PSF and PDO approximations."""
+    k, nz, nx = v.shape
+    pv = _dev(v, torch.float32, (k, nz, nx), "v", v.device)
+    out = torch.empty_like(v, dtype=torch.float32)
+    check(_lib.load().hv_highpass_apply(nz, nx, float(h), float(rho_c), pv, k, out.data_ptr(),
+                                        ctypes.c_void_p(torch.cuda.current_stream(v.device).cuda_stream)))
+    return out
+
+
+class Filtered:
+    """F_hp Op F_hp for the operator of `src` (an object with .operator(), .device, .lib, e.g. Quad): the
+    filtered operator the PSF and PDO approximations are built from (hv_filtered_*).  Keeps `src` alive."""
+
+    def __init__(self, src, rho_c: float, max_k: int = 64):
+        self.lib, self.device, self.src = src.lib, src.device, src
+        f = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            check(self.lib.hv_filtered_create(ctypes.byref(src.operator()), float(rho_c), int(max_k), ctypes.byref(f)))
+        self._f = f
+        self._op = _lib.HvOperator()
+        check(self.lib.hv_filtered_operator(self._f, ctypes.byref(self._op)))
+
+    def operator(self):
+        return self._op
+
+    def close(self):
+        if getattr(self, "_f", None):
+            self.lib.hv_filtered_destroy(self._f)
+            self._f = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def psf_plus(psf: PsfApprox, pdo: PdoApprox, tol: float = 1e-3, spd: bool = False) -> PdoApprox:
