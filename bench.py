@@ -599,6 +599,11 @@ def run_ours(args, w):
     psfplus = psfplus_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
     lowrank = lr_measure(P, m, w, dev) if args.workload == "batched" and rank == 0 else None
     quad = quad_measure(dev) if args.workload == "batched" and rank == 0 else None
+    # serving sample (1 GPU): the request mix of the serving workload, 36 requests with 8, 16 or 32 shots, at 2x
+    # the serial capacity, with and without merging, against one request at a time
+    serve = None
+    if args.workload == "paper" and world == 1 and not args.no_serve and args.nt is None and args.shots is None:
+        serve = serve_measure(dev, serve_requests(36, shots=[8, 16, 32]), [2.0], 16, batching=(64, 0))
     # end to end through the public API with host buffers (pinned), copies inside the timed region
     mh = torch.tensor(w.m, dtype=torch.float32).pin_memory()
     vh = torch.tensor(w.v, dtype=torch.float32).pin_memory()
@@ -690,6 +695,19 @@ def run_ours(args, w):
                                          if world > 1 else "1 GPU, all shots")
         if one_at_a_time is not None:
             line["one_at_a_time"] = one_at_a_time
+        if serve is not None:
+            on = [r for r in serve["runs"] if r["batching_max_vectors"] > 0][0]
+            off = [r for r in serve["runs"] if r["batching_max_vectors"] == 0][0]
+            line["serve"] = {
+                "what": "36 requests (H v 35% / gradient 35% / misfit 15% / PSF-approximation apply 15%) on "
+                        "{128x128, 256x256, 384x1152} x {8, 16, 32} shots, Poisson arrivals at 2x the serial "
+                        "capacity, 16 streams, 150 GB pool; latency from submission to completion",
+                "p50_ms": on["p50_ms"], "p99_ms": on["p99_ms"], "throughput_req_s": on["throughput_req_s"],
+                "hv_per_s": on["hv_per_s"], "merged_requests": on["merged_requests"],
+                "no_merging": {"p50_ms": off["p50_ms"], "p99_ms": off["p99_ms"],
+                               "throughput_req_s": off["throughput_req_s"], "hv_per_s": off["hv_per_s"]},
+                "one_at_a_time": {"throughput_req_s": serve["serial_req_s"], "hv_per_s": serve["serial_hv_per_s"]},
+                "by_kind": on["by_kind"]}
         if psf is not None:
             line["psf_approximation"] = psf
         if pdo is not None:
@@ -705,12 +723,12 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
-def serve_requests(n, seed=20250719):
+def serve_requests(n, seed=20250719, shots=None):
     """The request stream of the serving workload: clients 0-63 are MCMC chains,
     64-67 FWI runs; each request draws its kind (H v 35%, gradient 35%, misfit
     15%, apply of the grid's PSF Hessian approximation 15%), its grid from
     {128x128, 256x256, 384x1152} (steps 1000/1500/3000) and its shot count from
-    U{4..32}."""
+    U{4..32} (or uniformly from the list `shots`)."""
     from paper_2507_10804_gb300 import synth
     u = synth.uniform(seed, 4 * n)
     grids = [(128, 128, 1000), (256, 256, 1500), (384, 1152, 3000)]
@@ -719,10 +737,117 @@ def serve_requests(n, seed=20250719):
         x = u[4 * i]
         kind = "hv" if x < 0.35 else ("grad" if x < 0.70 else ("misfit" if x < 0.85 else "approx"))
         g = grids[min(int(u[4 * i + 1] * 3), 2)]
-        ns = 4 + min(int(u[4 * i + 2] * 29), 28)
+        if shots:
+            ns = shots[min(int(u[4 * i + 2] * len(shots)), len(shots) - 1)]
+        else:
+            ns = 4 + min(int(u[4 * i + 2] * 29), 28)
         client = min(int(u[4 * i + 3] * 68), 67)
         out.append({"kind": kind, "grid": g, "ns": ns, "client": client})
     return out
+
+
+def serve_measure(dev, reqs, rates, concurrency, batching=(64,), seed=7):
+    """Serial (one request at a time) and concurrent serving of `reqs` with Poisson arrivals at the
+    given fractions of the serial capacity, for each server batching limit (vectors per merged call;
+    0: no merging); every request on a grid uses that grid's model (so requests on one problem merge).
+    Returns {"serial_req_s", "serial_hv_per_s", "runs": [...]}; latencies from the server's own clock."""
+    import torch
+
+    from paper_2507_10804_gb300 import synth
+    from paper_2507_10804_gb300.hv import Problem
+    from paper_2507_10804_gb300.serve import Server
+
+    n = len(reqs)
+    problems, models, data = {}, {}, {}
+    for r in reqs:
+        nz, nx, nt = r["grid"]
+        key = (nz, nx, r["ns"])
+        if key not in problems:
+            h = 10.0 if nx < 1000 else 8.0
+            nb = 20 if nx < 1000 else 40
+            if (nz, nx) not in models:
+                m = synth.gradient_grf_model(nz * 7 + nx, nz, nx, h) if nx < 1000 else \
+                    synth.layered_faulted_model(2025, nz, nx, h)[1]
+                models[(nz, nx)] = (m, torch.tensor(m, dtype=torch.float32, device=dev),
+                                    torch.tensor(synth.smoothed_normal_vectors(nz + nx, 1, nz, nx), dtype=torch.float32,
+                                                 device=dev))
+            m = models[(nz, nx)][0]
+            vmax = float(m.max())
+            acq = synth.surface_acquisition(nx, r["ns"], nx // 3)
+            w = synth.Workload(name="serve", nz=nz, nx=nx, nb=nb, h=h, nt=nt, dt=synth.cfl_dt(h, vmax), f0=10.0,
+                               t0=0.15, vmax=vmax, acq=acq, m=m, v=np.zeros((1, nz, nx)))
+            problems[key] = Problem.from_workload(w, device=dev)
+            data[key] = problems[key].fwd_model(models[(nz, nx)][1] * 1.02)
+    ckpt = 30
+    # one PSF approximation per grid (12-cell lattice, 4 batches), built at the grid's
+    # model with the first acquisition drawn on it; approximate-apply requests use it
+    approx = {}
+    for r in reqs:
+        nz, nx, nt = r["grid"]
+        if r["kind"] == "approx" and (nz, nx) not in approx:
+            approx[(nz, nx)] = problems[(nz, nx, r["ns"])].approx_build_psf(models[(nz, nx)][1], 12, 4, ckpt=ckpt)
+    torch.cuda.synchronize()
+
+    def submit(S, r):
+        nz, nx, nt = r["grid"]
+        P = problems[(nz, nx, r["ns"])]
+        _, m, v = models[(nz, nx)]
+        d = data[(nz, nx, r["ns"])]
+        if r["kind"] == "hv":
+            return S.submit_hv(P, m, v, ckpt=ckpt)[0]
+        if r["kind"] == "grad":
+            return S.submit_grad(P, m, d, ckpt=ckpt)[0]
+        if r["kind"] == "approx":
+            return S.submit_approx(approx[(nz, nx)], v)[0]
+        return S.submit_misfit(P, m, d)[0]
+
+    budget = 150 << 30
+    # serial: one request at a time through the same server (the one-request-at-a-time GPU path)
+    S = Server(hbm_budget=budget, max_concurrent=1, device=dev)
+    S.set_batching(0)
+    for r in reqs[:3]:
+        S.wait(submit(S, r))
+    t0 = time.perf_counter()
+    for r in reqs:
+        assert S.wait(submit(S, r)) == 0
+    t_serial = time.perf_counter() - t0
+    S.close()
+    serial_rate = n / t_serial
+    n_hv = sum(r["kind"] == "hv" for r in reqs)
+    kinds = np.array([r["kind"] for r in reqs])
+    runs = []
+    S = Server(hbm_budget=budget, max_concurrent=concurrency, device=dev)
+    for limit in batching:
+        S.set_batching(limit)
+        rng = np.random.default_rng(seed)
+        for frac in rates:
+            lam = frac * serial_rate
+            arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n))
+            ids = []
+            t0 = time.perf_counter()
+            for a, r in zip(arrivals, reqs):
+                dt_ = t0 + a - time.perf_counter()
+                if dt_ > 0:
+                    time.sleep(dt_)
+                ids.append(submit(S, r))
+            for i in ids:
+                assert S.wait(i) == 0
+            infos = [S.info(i) for i in ids]
+            lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
+            span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
+            by_kind = {k: {"p50_ms": float(np.percentile(lat[kinds == k], 50)),
+                           "p99_ms": float(np.percentile(lat[kinds == k], 99))}
+                       for k in ("hv", "grad", "misfit", "approx") if (kinds == k).any()}
+            runs.append({"batching_max_vectors": limit, "rate_frac_of_serial": frac, "offered_req_s": lam,
+                         "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "throughput_req_s": n / span, "hv_per_s": n_hv / span,
+                         "merged_requests": int(sum(i["batch"] > 1 for i in infos)), "by_kind": by_kind})
+    S.close()
+    for A in approx.values():
+        A.close()
+    for P in problems.values():
+        P.close()
+    return {"serial_req_s": serial_rate, "serial_hv_per_s": n_hv / t_serial, "runs": runs}
 
 
 def serve_chains(dev, concurrency, chains=64, fwi=4, steps=4, fwi_iters=2, beta=0.5):
@@ -848,98 +973,16 @@ def serve_chains(dev, concurrency, chains=64, fwi=4, steps=4, fwi_iters=2, beta=
 
 def run_serve(args):
     """Serving workload: Poisson arrivals at fractions of the measured serial
-    capacity, memory-budgeted admission into a 150 GB pool."""
+    capacity, memory-budgeted admission into a 150 GB pool, with and without
+    merging queued requests on one problem and model."""
     import torch
-
-    from paper_2507_10804_gb300 import synth
-    from paper_2507_10804_gb300.hv import Problem
-    from paper_2507_10804_gb300.serve import Server
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
     n = args.requests
     reqs = serve_requests(n)
-    problems, models, data = {}, {}, {}
-    for r in reqs:
-        nz, nx, nt = r["grid"]
-        key = (nz, nx, r["ns"])
-        if key not in problems:
-            h = 10.0 if nx < 1000 else 8.0
-            nb = 20 if nx < 1000 else 40
-            if (nz, nx) not in models:
-                m = synth.gradient_grf_model(nz * 7 + nx, nz, nx, h) if nx < 1000 else \
-                    synth.layered_faulted_model(2025, nz, nx, h)[1]
-                models[(nz, nx)] = (m, torch.tensor(m, dtype=torch.float32, device=dev),
-                                    torch.tensor(synth.smoothed_normal_vectors(nz + nx, 1, nz, nx), dtype=torch.float32,
-                                                 device=dev))
-            m = models[(nz, nx)][0]
-            vmax = float(m.max())
-            acq = synth.surface_acquisition(nx, r["ns"], nx // 3)
-            w = synth.Workload(name="serve", nz=nz, nx=nx, nb=nb, h=h, nt=nt, dt=synth.cfl_dt(h, vmax), f0=10.0,
-                               t0=0.15, vmax=vmax, acq=acq, m=m, v=np.zeros((1, nz, nx)))
-            problems[key] = Problem.from_workload(w, device=dev)
-            data[key] = problems[key].fwd_model(models[(nz, nx)][1] * 1.02)
-    ckpt = 30
-    # one PSF approximation per grid (12-cell lattice, 4 batches), built at the grid's
-    # model with the first acquisition drawn on it; approximate-apply requests use it
-    approx = {}
-    for r in reqs:
-        nz, nx, nt = r["grid"]
-        if r["kind"] == "approx" and (nz, nx) not in approx:
-            approx[(nz, nx)] = problems[(nz, nx, r["ns"])].approx_build_psf(models[(nz, nx)][1], 12, 4, ckpt=ckpt)
-    torch.cuda.synchronize()
-
-    def submit(S, r):
-        nz, nx, nt = r["grid"]
-        P = problems[(nz, nx, r["ns"])]
-        _, m, v = models[(nz, nx)]
-        d = data[(nz, nx, r["ns"])]
-        if r["kind"] == "hv":
-            return S.submit_hv(P, m, v, ckpt=ckpt)[0]
-        if r["kind"] == "grad":
-            return S.submit_grad(P, m, d, ckpt=ckpt)[0]
-        if r["kind"] == "approx":
-            return S.submit_approx(approx[(nz, nx)], v)[0]
-        return S.submit_misfit(P, m, d)[0]
-
-    budget = 150 << 30
-    # serial: one request at a time through the same server
-    S = Server(hbm_budget=budget, max_concurrent=1, device=dev)
-    for r in reqs[:3]:
-        S.wait(submit(S, r))
-    t0 = time.perf_counter()
-    for r in reqs:
-        assert S.wait(submit(S, r)) == 0
-    t_serial = time.perf_counter() - t0
-    S.close()
-    serial_rate = n / t_serial
-    n_hv = sum(r["kind"] == "hv" for r in reqs)
-    rng = np.random.default_rng(7)
-    results = []
-    S = Server(hbm_budget=budget, max_concurrent=args.concurrency, device=dev)
-    for frac in args.rates:
-        lam = frac * serial_rate
-        arrivals = np.cumsum(rng.exponential(1.0 / lam, size=n))
-        ids = []
-        t0 = time.perf_counter()
-        for a, r in zip(arrivals, reqs):
-            dt_ = t0 + a - time.perf_counter()
-            if dt_ > 0:
-                time.sleep(dt_)
-            ids.append(submit(S, r))
-        for i in ids:
-            assert S.wait(i) == 0
-        infos = [S.info(i) for i in ids]
-        lat = np.array([i["t_done"] - i["t_submit"] for i in infos]) * 1e3
-        span = max(i["t_done"] for i in infos) - min(i["t_submit"] for i in infos)
-        kinds = np.array([r["kind"] for r in reqs])
-        by_kind = {k: {"p50_ms": float(np.percentile(lat[kinds == k], 50)), "p99_ms": float(np.percentile(lat[kinds == k], 99))}
-                   for k in ("hv", "grad", "misfit", "approx") if (kinds == k).any()}
-        results.append({"rate_frac_of_serial": frac, "offered_req_s": lam, "p50_ms": float(np.percentile(lat, 50)),
-                        "p99_ms": float(np.percentile(lat, 99)), "throughput_req_s": n / span,
-                        "hv_per_s": n_hv / span, "by_kind": by_kind})
-    S.close()
-    best = max(results, key=lambda x: x["throughput_req_s"])
+    res = serve_measure(dev, reqs, args.rates, args.concurrency, batching=(64, 0))
+    best = max(res["runs"], key=lambda x: x["throughput_req_s"])
     line = {
         "metric": METRIC, "value": best["hv_per_s"], "unit": UNIT, "n_gpus": 1, "steps": n, "warmup": 3,
         "ms_per_step": 1e3 / best["throughput_req_s"], "higher_is_better": True, "scaling": "weak",
@@ -948,8 +991,8 @@ def run_serve(args):
         "config": {"workload": "serving: 64 MCMC chains + 4 FWI runs, Poisson arrivals, H v 35% / gradient 35% / "
                                "misfit 15% / PSF-approximation apply 15%, grids {128x128, 256x256, 384x1152} x "
                                "U{4..32} shots, 150 GB pool",
-                   "requests": n, "concurrency": args.concurrency, "snapshots_per_shot": ckpt},
-        "serve": {"serial_req_s": serial_rate, "serial_hv_per_s": n_hv / t_serial, "rates": results},
+                   "requests": n, "concurrency": args.concurrency, "snapshots_per_shot": 30},
+        "serve": res,
     }
     line["serve"]["gpcn_request_source"] = serve_chains(dev, args.concurrency)
     print(json.dumps(line))
@@ -974,6 +1017,7 @@ def main():
                          "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph; quadratic: "
                          "the quadratic test model's approximation, posterior and gpCN measurements alone")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true", help="paper workload: skip the serving sample")
     ap.add_argument("--no-resident", action="store_true", help="batched workload: the tiled per-step kernels")
     ap.add_argument("--tiles", type=int, nargs=3, default=None, metavar=("FWD", "ADVANCE", "ADJ"),
                     help="tile configurations instead of autotuning (profiling runs)")

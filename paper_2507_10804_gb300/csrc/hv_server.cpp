@@ -303,9 +303,12 @@ void worker_loop(hv_server *S)
             S->slot_off[slot] = off;
             admitted.push_back(group);
             admitted_ws.push_back(ws);
+            // Erasing from a deque invalidates its iterators: work by index.  The merged
+            // requests all sit behind the head, so removing them leaves the head's index.
+            const size_t head = (size_t)(it - S->queue.begin());
             for (size_t i = 1; i < ids.size(); ++i)
-                S->queue.erase(std::find(std::next(it), S->queue.end(), ids[i]));
-            it = S->queue.erase(it);
+                S->queue.erase(std::find(S->queue.begin() + head + 1, S->queue.end(), ids[i]));
+            it = S->queue.erase(S->queue.begin() + head);
         }
         if (!admitted.empty()) {
             lk.unlock();                          // enqueueing thousands of launches takes a while

@@ -206,3 +206,28 @@ def test_queued_requests_on_one_model_run_as_one_call(problems):
         assert np.array_equal(phi.cpu().numpy(), ref_phi) and np.array_equal(g.cpu().numpy(), ref_g)
         assert np.array_equal(phm.cpu().numpy(), ref_m)
         S.close()
+
+
+def test_interleaved_queue_merges_every_request_once(problems):
+    """Requests on two problems queued alternately behind a running one: each admission merges the
+    queued requests of one problem out of the middle of the queue; every request completes exactly once
+    with its direct result."""
+    (w, P), (w2, P2) = problems
+    m, m2 = t(w.m), t(w2.m)
+    vs = [t(w.v[i % 2:i % 2 + 1]) for i in range(6)]
+    vs2 = [t(w2.v[i % 2:i % 2 + 1]) for i in range(6)]
+    ref = [P.hessian_apply(m, v, ckpt=5).cpu().numpy() for v in vs]
+    ref2 = [P2.hessian_apply(m2, v, ckpt=4).cpu().numpy() for v in vs2]
+    S = Server(hbm_budget=4 << 30, max_concurrent=2)
+    blockers = [S.submit_hv(P2, m2, t(w2.v), ckpt=1)[0] for _ in range(2)]     # both streams busy
+    subs = []
+    for i in range(6):
+        subs.append((S.submit_hv(P, m, vs[i], ckpt=5), ref[i]))
+        subs.append((S.submit_hv(P2, m2, vs2[i], ckpt=4), ref2[i]))
+    for rid in blockers:
+        assert S.wait(rid, timeout=300) == 0
+    for (rid, out), r in subs:
+        assert S.wait(rid, timeout=300) == 0
+        assert np.array_equal(out.cpu().numpy(), r)
+    assert sum(S.info(rid)["batch"] > 1 for (rid, _), _ in subs) >= 6
+    S.close()
