@@ -16,7 +16,7 @@ BUILD = os.path.join(_PKG, "_build")
 LIB = os.path.join(BUILD, "libhv.so")
 INCLUDE = os.path.join(_ROOT, "include")
 
-SOURCES = ["hv_api.cu", "hv_kernels.cu", "hv_stencil.cu", "hv_psf.cu", "hv_pdo.cu", "hv_psfplus.cu", "hv_lowrank.cu", "hv_quad.cu", "hv_posterior.cu", "hv_blas.cu", "hv_lrfft.cu", "hv_highpass.cu",
+SOURCES = ["hv_api.cu", "hv_kernels.cu", "hv_stencil.cu", "hv_psf.cu", "hv_pdo.cu", "hv_psfplus.cu", "hv_lowrank.cu", "hv_quad.cu", "hv_posterior.cu", "hv_blas.cu", "hv_lrfft.cu", "hv_highpass.cu", "hv_dct.cu",
            "hv_linalg.cpp", "hv_schedule.cpp", "hv_server.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xptxas", "-v",

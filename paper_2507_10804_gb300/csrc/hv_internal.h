@@ -271,6 +271,21 @@ struct Highpass {
 int highpass_create(Highpass &F, int nz, int nx, double h, double rho_c, int kmax);
 void highpass_destroy(Highpass &F);
 int highpass_apply(Highpass &F, const float *v, int k, float *out, cudaStream_t st);   // out may be v
+// A^-1 of the Matern prior by the 2D DCT (hv_dct.cu): one real 2D DFT of the
+// reordered field, a kernel that forms the DCT coefficients, divides by the
+// eigenvalues and rebuilds the half spectrum, and the inverse DFT.
+struct Dct2 {
+    int n1 = 0, n2 = 0, kmax = 0;   // transform grid (a one-column field is taken as 1 x nz)
+    float2 *tw = nullptr;           // (cos, sin)(pi a / (2 n1)), a <= n1, then the same for n2
+    float *inv = nullptr;           // [nz][nx] 1 / (lambda nz nx)
+    float *w = nullptr;             // [kmax][nz][nx] reordered fields
+    float2 *s1 = nullptr, *s2 = nullptr;   // [kmax][n1][n2/2+1] half spectra
+    cufftHandle f = 0, i = 0, f1 = 0, i1 = 0;
+    bool f_ok = false, i_ok = false, f1_ok = false, i1_ok = false;
+};
+int dct_create(Dct2 &D, int nz, int nx, double h, double delta, double gamma, int kmax);
+void dct_destroy(Dct2 &D);
+int dct_apply(Dct2 &D, const float *v, int k, float *out, cudaStream_t st);   // out = A^-1 v, out may be v
 // Matern prior and the low-rank approximation (hv_lowrank.cu).
 struct Prior {
     int nz = 0, nx = 0;
@@ -278,6 +293,7 @@ struct Prior {
     float *Cz = nullptr, *Cx = nullptr;   // orthonormal DCT-II matrices
     float *inv = nullptr;                 // 1 / (delta + gamma lambda_kl) in DCT order
     double *Czd = nullptr, *Cxd = nullptr, *invd = nullptr;   // the same in FP64 (low-rank build)
+    Dct2 dct;                             // A^-1 in FP32 (fields in batches of up to dct.kmax)
     float *tmp = nullptr;                 // scratch, 2 tmp_k fields
     double *tmpd = nullptr;
     int tmp_k = 0, tmpd_k = 0;

@@ -4,9 +4,8 @@
 // Prior: R = A^2, A = delta I - gamma Lap_h, Lap_h the 5-point Laplacian with
 // homogeneous Neumann conditions (mirror ghost cells).  A is a stencil kernel;
 // A^-1 = C^T diag(1 / (delta + gamma lambda)) C with C the orthonormal 2D
-// DCT-II, applied as dense GEMMs (Cz V Cx^T and back; FP32 in the applies,
-// FP64 in the low-rank build) on the cuBLAS library -- a plain dense
-// contraction of a few hundred to a thousand points per side.
+// DCT-II: in FP32 (the applies) by the fast transform of hv_dct.cu; in the FP64
+// low-rank build as dense DGEMMs (Cz V Cx^T and back) on the cuBLAS library.
 //
 // LR: the r leading eigenpairs of H_d v = lambda R v by the randomized
 // double-pass method with a caller-drawn Gaussian test matrix Omega:
@@ -23,6 +22,7 @@
 // A^-1 v - V S_r W^T v (V^T R A^-1 v = W^T v), with no product with R.
 #include "hv_internal.h"
 
+#include <algorithm>
 #include <cmath>
 #include <type_traits>
 #include <vector>
@@ -157,6 +157,7 @@ int prior_create(Prior &P, int nz, int nx, double h, double delta, double gamma)
 
 void prior_destroy(Prior &P)
 {
+    dct_destroy(P.dct);
     if (P.blas_ok) cublasDestroy(P.blas);
     cudaFree(P.Cz);
     cudaFree(P.Cx);
@@ -190,12 +191,25 @@ int prior_tmp(Prior &P, int k, T **buf)
 
 }  // namespace
 
-// Sizes the prior's FP32 scratch for k fields now, so that later applies with
-// at most k fields allocate nothing.
+// The FP32 A^-1 transform for batches of min(k, 64) fields (created once, or
+// again for a larger batch while below 64).
+constexpr int kDctBatch = 64;
+int prior_dct(Prior &P, int k)
+{
+    const int want = std::min(std::max(k, 1), kDctBatch);
+    if (P.dct.kmax >= want) return HV_OK;
+    cudaDeviceSynchronize();   // nothing in flight uses the old transform afterwards
+    dct_destroy(P.dct);
+    return dct_create(P.dct, P.nz, P.nx, P.h, P.delta, P.gamma, want);
+}
+
+// Sizes the prior's FP32 scratch and transform for k fields now, so that later
+// applies with at most k fields allocate nothing.
 int prior_reserve(Prior &P, int k)
 {
     float *buf = nullptr;
-    return prior_tmp<float>(P, k, &buf);
+    HV_RT_INTERNAL(prior_tmp<float>(P, k, &buf));
+    return prior_dct(P, k);
 }
 
 namespace {
@@ -250,7 +264,8 @@ int prior_A(const Prior &P, const float *v, float *out, int k, cudaStream_t st) 
 
 int prior_Ainv(Prior &P, const float *v, float *out, int k, cudaStream_t st)
 {
-    return prior_Ainv_t(P, P.Cz, P.Cx, P.inv, v, out, k, st);
+    HV_RT_INTERNAL(prior_dct(P, k));
+    return dct_apply(P.dct, v, k, out, st);
 }
 
 int prior_R(Prior &P, const float *v, float *out, int k, cudaStream_t st)
