@@ -361,9 +361,9 @@ int hv_inject_wait_timeout(hv_handle *h);
  * R = Gamma_pr^-1 = A^2, A = delta I - gamma Lap_h (Lap_h the 5-point
  * Laplacian with homogeneous Neumann conditions, mirror ghost cells):
  *  - hv_prior_apply: out = A v (op 0), A^-1 v (1), R v (2) or R^-1 v (3) for
- *    k fields [k][nz][nx] on the device (A^-1 by the orthonormal 2D DCT-II
- *    that diagonalises A, as dense cuBLAS SGEMMs).  Builds and frees its
- *    tables on every call; synchronous on `stream`.
+ *    k fields [k][nz][nx] on the device (A^-1 by the 2D DCT-II that
+ *    diagonalises A, computed with one real 2D DFT of the reordered field).
+ *    Builds and frees its tables on every call; synchronous on `stream`.
  *  - hv_approx_lr_workspace_size: bytes of `ws` hv_approx_build_lr needs for
  *    k test vectors and budget ckpt.
  *  - hv_approx_build_lr: the `rank` leading eigenpairs of H_d v = lambda R v
