@@ -481,8 +481,9 @@ int hv_approx_build_lr_op(const hv_operator *op, double delta, double gamma, int
  *  - hv_filtered_create(inner, rho_c, max_k, out): F_hp inner F_hp as an
  *    object that owns the transforms and a scratch of max_k fields;
  *    hv_filtered_operator fills an hv_operator that applies it (in chunks of
- *    max_k fields; applies on one object run one after another), for the *_op
- *    builds; hv_filtered_destroy frees it (the inner operator must outlive it). */
+ *    max_k fields; applies on one object are ordered by an event, also across
+ *    streams), for the *_op builds; hv_filtered_destroy frees it (the inner
+ *    operator must outlive it). */
 typedef struct hv_filtered hv_filtered;
 int hv_highpass_apply(int nz, int nx, double h, double rho_c, const float *v, int k, float *out, void *stream);
 int hv_set_highpass(hv_handle *h, double rho_c);

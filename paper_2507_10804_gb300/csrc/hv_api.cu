@@ -1568,6 +1568,7 @@ struct hv_filtered {
     float *T = nullptr;
     int max_k = 0;
     std::mutex mu;
+    cudaEvent_t done = nullptr;   // the last apply's use of T and the transforms
 };
 
 namespace {
@@ -1576,15 +1577,22 @@ int filtered_apply(void *ctx, const float *v, int k, float *out, void *stream)
     hv_filtered *f = static_cast<hv_filtered *>(ctx);
     std::lock_guard<std::mutex> g(f->mu);
     cudaStream_t st = (cudaStream_t)stream;
+    // applies from different streams share the scratch: order this one after the last
+    HV_CK(cudaStreamWaitEvent(st, f->done, 0));
     const size_t N = (size_t)f->inner.nz * f->inner.nx;
-    for (int q0 = 0; q0 < k; q0 += f->max_k) {
+    int rc = HV_OK;
+    for (int q0 = 0; q0 < k && rc == HV_OK; q0 += f->max_k) {
         const int kb = std::min(f->max_k, k - q0);
-        HV_RT(hvk::highpass_apply(f->F, v + q0 * N, kb, f->T, st));
-        const int rc = f->inner.apply(f->inner.ctx, f->T, kb, out + q0 * N, stream);
-        if (rc != HV_OK) return hvi::fail(rc, "the inner operator's apply returned %d", rc);
-        HV_RT(hvk::highpass_apply(f->F, out + q0 * N, kb, out + q0 * N, st));
+        rc = hvk::highpass_apply(f->F, v + q0 * N, kb, f->T, st);
+        if (rc == HV_OK) {
+            const int r = f->inner.apply(f->inner.ctx, f->T, kb, out + q0 * N, stream);
+            if (r != HV_OK) rc = hvi::fail(r, "the inner operator's apply returned %d", r);
+        }
+        if (rc == HV_OK) rc = hvk::highpass_apply(f->F, out + q0 * N, kb, out + q0 * N, st);
     }
-    return HV_OK;
+    const cudaError_t e = cudaEventRecord(f->done, st);
+    if (rc == HV_OK && e != cudaSuccess) rc = hvi::fail(HV_ECUDA, "cudaEventRecord: %s", cudaGetErrorString(e));
+    return rc;
 }
 }  // namespace
 
@@ -1599,6 +1607,8 @@ extern "C" int hv_filtered_create(const hv_operator *inner, double rho_c, int ma
     int rc = hvk::highpass_create(f->F, inner->nz, inner->nx, inner->h, rho_c, max_k);
     if (rc == HV_OK && cudaMalloc(&f->T, (size_t)max_k * inner->nz * inner->nx * sizeof(float)) != cudaSuccess)
         rc = hvi::fail(HV_ECUDA, "high-pass scratch: out of device memory");
+    if (rc == HV_OK && cudaEventCreateWithFlags(&f->done, cudaEventDisableTiming) != cudaSuccess)
+        rc = hvi::fail(HV_ECUDA, "cudaEventCreate failed");
     if (rc != HV_OK) {
         hv_filtered_destroy(f);
         return rc;
@@ -1624,6 +1634,7 @@ extern "C" int hv_filtered_destroy(hv_filtered *f)
     cudaDeviceSynchronize();
     cudaFree(f->T);
     hvk::highpass_destroy(f->F);
+    if (f->done) cudaEventDestroy(f->done);
     delete f;
     return HV_OK;
 }

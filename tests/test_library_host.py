@@ -166,3 +166,24 @@ def test_hermitian_eigensolver_rejects_non_hermitian(lib):
     rc = lib.hv_util_hermitian_eig(2, A.view(np.float64).ctypes.data_as(dp), w.ctypes.data_as(dp),
                                    V.view(np.float64).ctypes.data_as(dp))
     assert rc == _lib.HV_EINVAL and "Hermitian" in lib.hv_last_error().decode()
+
+
+def test_new_entry_points_validate_before_touching_a_gpu(lib):
+    """Null handles, empty batches and bad limits are rejected with HV_EINVAL on the host."""
+    E = _lib.HV_EINVAL
+    assert lib.hv_set_wait_limit(None, 1.0) == E
+    assert lib.hv_inject_wait_timeout(None) == E
+    assert lib.hv_set_image_precision(None, _lib.HV_IMAGE_FP64) == E
+    assert lib.hv_set_highpass(None, 0.1) == E
+    assert lib.hv_static_status(None) == E
+    assert lib.hv_server_set_batching(None, 8) == E
+    assert lib.hv_filtered_create(None, 0.1, 4, ctypes.byref(ctypes.c_void_p())) == E
+    assert lib.hv_filtered_operator(None, None) == E
+    assert lib.hv_filtered_destroy(None) == 0
+    assert lib.hv_highpass_apply(8, 8, 10.0, 0.1, None, 1, None, None) == E
+    assert lib.hv_image_fold(None, None, 1, None, None, None) == E
+    b = _lib.HvBatch()                                   # no entries at all
+    n = ctypes.c_size_t()
+    assert lib.hv_batch_workspace_size(None, ctypes.byref(b), -1, ctypes.byref(n)) == E
+    assert "batch" in lib.hv_last_error().decode() or "handle" in lib.hv_last_error().decode()
+    assert lib.hv_hessian_apply_partial(None, None, None, 1, None, -1, None, 0, None) == E
