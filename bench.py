@@ -650,7 +650,8 @@ def run_ours(args, w):
         # counters recorded for this workload, these kernel sources and these tiles (full-size launches)
         tid = 0 if resident else list(tiles)[{"fwd": 0, "advance": 1, "adj": 2}[dom]]   # the kernel's own tiles
         ent = dram_traffic().get((args.workload + ("-resident" if resident else ""), dom, tid))
-        if ent and ent[0] == csrc_hash(resident) and args.nt is None and args.shots is None:
+        # (taken on all 32 shots: a rank's shot block has other per-launch bytes)
+        if ent and ent[0] == csrc_hash(resident) and args.nt is None and args.shots is None and world == 1:
             traffic = ent[1]
         roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
