@@ -655,8 +655,11 @@ int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *in
  * gradients with the same checkpoint budget) join it, up to max_vectors Born
  * vectors in all (a gradient counts as one, a misfit as none), and run as one
  * hv_apply_batch on one stream and one arena block, if that fits; their
- * results are bitwise those of separate calls.  max_vectors < 2 turns merging
- * off (each request runs alone).  Default 64.  Applies to later admissions. */
+ * results are bitwise those of separate calls.  Queued applies of one
+ * approximation in one mode likewise join into one hv_approx_apply of up to
+ * max_vectors vectors (gathered into and scattered from an arena block of
+ * 2 x vectors x nz x nx floats).  max_vectors < 2 turns merging off (each
+ * request runs alone).  Default 64.  Applies to later admissions. */
 int hv_server_set_batching(hv_server *s, int max_vectors);
 
 /* Tile configurations.  The stencil kernels come in a small menu of

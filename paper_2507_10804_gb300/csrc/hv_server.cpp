@@ -10,7 +10,8 @@
 // and model join it (up to the server's vector limit, if the merged
 // workspace fits) and run as one merged call (hv_apply_batch: one forward
 // sweep, the H v vectors and the gradients as one batch of Born vectors),
-// whose results are bitwise those of separate calls.  Completion is detected
+// whose results are bitwise those of separate calls; queued applies of one
+// Hessian approximation in one mode join into one apply of all their vectors.  Completion is detected
 // with events; the scheduler never blocks on the device (event queries plus
 // short sleeps), and every host wait is bounded.
 #include "hv_internal.h"
@@ -199,6 +200,47 @@ int launch_merged(hv_server *S, const std::vector<Req> &qs, size_t ws_bytes)
 
 bool mergeable(const hv_request &r) { return r.kind == HV_REQ_HV || r.kind == HV_REQ_GRAD || r.kind == HV_REQ_MISFIT; }
 
+// Points per field of an approximation (its grid).
+size_t approx_points(const hv_approx *a)
+{
+    int info[11] = {};
+    if (hv_approx_info(a, info) != HV_OK) return 0;
+    return (size_t)info[9] * info[10];
+}
+
+// Applies of one approximation in one mode, merged: the vectors gathered into
+// the arena block (vectors, then outputs), one apply of all of them, the
+// outputs scattered back.
+int launch_merged_approx(hv_server *S, const std::vector<Req> &qs)
+{
+    const int slot = qs[0].slot;
+    cudaStream_t st = S->streams[slot];
+    const hv_approx *a = qs[0].r.approx;
+    const size_t N = approx_points(a);
+    int K = 0;
+    for (const Req &q : qs) K += q.r.k;
+    float *V = reinterpret_cast<float *>(S->arena_base + qs[0].off), *O = V + (size_t)K * N;
+    int rc = HV_OK;
+    size_t at = 0;
+    for (const Req &q : qs) {
+        if (rc == HV_OK && cudaMemcpyAsync(V + at * N, q.r.v, (size_t)q.r.k * N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                           st) != cudaSuccess)
+            rc = hvi::fail(HV_ECUDA, "merged apply: gathering the vectors failed");
+        at += q.r.k;
+    }
+    if (rc == HV_OK) rc = hv_approx_apply(a, V, K, O, qs[0].r.approx_mode, (void *)st);
+    at = 0;
+    for (const Req &q : qs) {
+        if (rc == HV_OK && cudaMemcpyAsync(q.r.out, O + at * N, (size_t)q.r.k * N * sizeof(float),
+                                           cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            rc = hvi::fail(HV_ECUDA, "merged apply: scattering the outputs failed");
+        at += q.r.k;
+    }
+    cudaError_t e = cudaEventRecord(S->events[slot], st);
+    if (rc == HV_OK && e != cudaSuccess) rc = HV_ECUDA;
+    return rc;
+}
+
 // The queued requests that can run merged with the one at `head`: same problem
 // and model; H v and gradients with the same checkpoint budget; at most
 // merge_max Born vectors in all.
@@ -206,7 +248,19 @@ std::vector<unsigned long long> merge_group(hv_server *S, std::deque<unsigned lo
 {
     std::vector<unsigned long long> ids{*head};
     const hv_request &r0 = S->reqs[*head].r;
-    if (S->merge_max < 2 || !mergeable(r0)) return ids;
+    if (S->merge_max < 2) return ids;
+    if (r0.kind == HV_REQ_APPROX) {              // applies of one approximation in one mode
+        int vecs = r0.k;
+        for (auto it = std::next(head); it != S->queue.end(); ++it) {
+            const hv_request &r = S->reqs[*it].r;
+            if (r.kind != HV_REQ_APPROX || r.approx != r0.approx || r.approx_mode != r0.approx_mode) continue;
+            if (vecs + r.k > S->merge_max) continue;
+            vecs += r.k;
+            ids.push_back(*it);
+        }
+        return ids;
+    }
+    if (!mergeable(r0)) return ids;
     int ckpt = r0.kind == HV_REQ_MISFIT ? 0 : r0.ckpt;
     bool have_ckpt = r0.kind != HV_REQ_MISFIT;
     int vecs = r0.kind == HV_REQ_HV ? r0.k : (r0.kind == HV_REQ_GRAD ? 1 : 0);
@@ -228,6 +282,12 @@ std::vector<unsigned long long> merge_group(hv_server *S, std::deque<unsigned lo
 
 int merged_ws(hv_server *S, const std::vector<unsigned long long> &ids, size_t *bytes)
 {
+    if (S->reqs[ids[0]].r.kind == HV_REQ_APPROX) {   // staging for the vectors and the outputs
+        size_t K = 0;
+        for (auto id : ids) K += S->reqs[id].r.k;
+        *bytes = 2 * K * approx_points(S->reqs[ids[0]].r.approx) * sizeof(float);
+        return HV_OK;
+    }
     Merged M;
     for (auto id : ids) {
         const hv_request &r = S->reqs[id].r;
@@ -314,8 +374,9 @@ void worker_loop(hv_server *S)
             lk.unlock();                          // enqueueing thousands of launches takes a while
             std::vector<int> rcs;
             for (size_t i = 0; i < admitted.size(); ++i)
-                rcs.push_back(admitted[i].size() > 1 ? launch_merged(S, admitted[i], admitted_ws[i])
-                                                     : launch(S, admitted[i][0]));
+                rcs.push_back(admitted[i].size() == 1                  ? launch(S, admitted[i][0])
+                              : admitted[i][0].r.kind == HV_REQ_APPROX ? launch_merged_approx(S, admitted[i])
+                                                                       : launch_merged(S, admitted[i], admitted_ws[i]));
             lk.lock();
             for (size_t i = 0; i < admitted.size(); ++i) failed[admitted[i][0].slot] = rcs[i];
             progress = true;

@@ -231,3 +231,33 @@ def test_interleaved_queue_merges_every_request_once(problems):
         assert np.array_equal(out.cpu().numpy(), r)
     assert sum(S.info(rid)["batch"] > 1 for (rid, _), _ in subs) >= 6
     S.close()
+
+
+def test_queued_approximation_applies_merge_bitwise(problems):
+    """Applies of one approximation in one mode queued behind a running request run as one apply of all
+    their vectors; each result is bitwise that of its own direct apply (PSF, PDO through cuFFT, the square-root
+    PDO's three modes, and the low-rank approximation's H~ and sampling factor, whose prior inverse runs cuFFT)."""
+    from paper_2507_10804_gb300._lib import HV_APPROX_H, HV_APPROX_INVSQRT, HV_APPROX_SQRT, HV_APPROX_SQRT_T
+    (w0, P0), (w1, P1) = problems
+    m0 = t(w0.m)
+    A = P0.approx_build_psf(m0, 8, 4, ckpt=5)
+    D = P0.approx_build_pdo(m0, 0.15, 8, ckpt=5)
+    Q = D.sqrt()
+    omega = t(synth.normal(501, 8 * w0.nz * w0.nx).reshape(8, w0.nz, w0.nx))
+    L = P0.approx_build_lr(m0, 1.0, 2500.0, 6, omega, ckpt=5)
+    cases = [(A, HV_APPROX_H), (D, HV_APPROX_H), (Q, HV_APPROX_H), (Q, HV_APPROX_SQRT), (Q, HV_APPROX_SQRT_T),
+             (L, HV_APPROX_H), (L, HV_APPROX_INVSQRT)]
+    S = Server(hbm_budget=2 << 30, max_concurrent=1)
+    for obj, mode in cases:
+        vs = [t(synth.smoothed_normal_vectors(600 + i, 1 + i % 2, w0.nz, w0.nx, 1.5)) for i in range(5)]
+        direct = [obj.apply(v, mode).cpu().numpy() for v in vs]
+        blocker, _ = S.submit_hv(P1, t(w1.m), t(w1.v), ckpt=1)
+        subs = [S.submit_approx(obj, v, mode) for v in vs]
+        assert S.wait(blocker, timeout=300) == 0
+        for (rid, out), ref in zip(subs, direct):
+            assert S.wait(rid, timeout=300) == 0
+            assert np.array_equal(out.cpu().numpy(), ref), (obj.info["kind"], mode)
+        assert all(S.info(rid)["batch"] == 5 for rid, _ in subs), [S.info(rid)["batch"] for rid, _ in subs]
+    S.close()
+    for o in (A, D, Q, L):
+        o.close()
