@@ -962,7 +962,8 @@ def serve_chains(dev, concurrency, chains=64, fwi=4, steps=4, fwi_iters=2, beta=
     for kind, ids in rids.items():
         lat = np.array([(lambda i: i["t_done"] - i["t_submit"])(S.info(r)) for r in ids]) * 1e3
         if len(lat):
-            out[kind] = {"n": len(lat), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99))}
+            out[kind] = {"n": len(lat), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                         "mean_batch": float(np.mean([S.info(r)["batch"] for r in ids]))}
     S.close()
     for x in (LR, prior):
         x.close()

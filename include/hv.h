@@ -82,6 +82,7 @@ extern "C" {
 #define HV_OP_HV 4          /* hv_hessian_apply(_f64out)         */
 #define HV_OP_WAVEFIELD 5   /* hv_wavefield                      */
 #define HV_OP_MISFIT 6      /* hv_misfit                         */
+#define HV_OP_MISFITS 7     /* hv_misfit_models (k = models)     */
 
 /* Interior grid and sponge.  h in metres. */
 typedef struct hv_grid {
@@ -157,6 +158,19 @@ int hv_misfit_grad(hv_handle *h, const float *m, const float *d_obs, double *phi
  * negative log-likelihood of section 2 (one forward solve per shot; what a
  * gpCN proposal needs, paper section 2.3). */
 int hv_misfit(hv_handle *h, const float *m, const float *d_obs, double *phi, void *ws, size_t ws_bytes, void *stream);
+
+/* Misfits at k different models in one forward sweep: phi[i] = (1/(2 sigma^2))
+ * sum (f(m[i]) - d_obs[i])^2 for i < k, the negative log-likelihoods that k
+ * gpCN chains (section 2.3) need for their k proposals.  m, d_obs and phi are
+ * HOST arrays of k DEVICE pointers (m[i]: [nz][nx] velocity; d_obs[i]:
+ * [ns][nt][nr]; phi[i]: one double), read during the call; the models' k x ns
+ * forward fields advance together, one launch per time step.  Every phi[i]
+ * is bitwise what hv_misfit gives for m[i] and d_obs[i] alone.  Workspace:
+ * hv_workspace_size(h, HV_OP_MISFITS, k, 0, &bytes); 1 <= k <= 65535.
+ * Errors: HV_EINVAL for a null array or entry or k out of range, HV_ENOMEM
+ * for a short workspace (nothing is launched then). */
+int hv_misfit_models(hv_handle *h, int k, const float *const *m, const float *const *d_obs,
+                     double *const *phi, void *ws, size_t ws_bytes, void *stream);
 
 /* Gauss-Newton Hessian apply: Hv[j] = F^T F v[j] / sigma^2 for j < k; v and Hv
  * are [k][nz][nx].  Images accumulate in FP64 and are summed over shots in a

@@ -19,7 +19,7 @@ HEADER = os.path.join(_build.INCLUDE, "hv.h")
 
 HV_OK, HV_EINVAL, HV_ENOMEM, HV_ECUDA, HV_ETIMEOUT, HV_EBUSY, HV_ENOTSUP = range(7)
 HV_CKPT_ALL = -1
-HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD, HV_OP_MISFIT = range(7)
+HV_OP_FWD, HV_OP_BORN, HV_OP_MIGRATE, HV_OP_GRAD, HV_OP_HV, HV_OP_WAVEFIELD, HV_OP_MISFIT, HV_OP_MISFITS = range(8)
 HV_K_FWD, HV_K_ADVANCE, HV_K_ADJ, HV_K_OTHER = range(4)
 HV_K_COUNT = 4
 HV_LAUNCH_PLAIN, HV_LAUNCH_PDL, HV_LAUNCH_DATAFLOW = range(3)
@@ -87,6 +87,8 @@ _SIGS = {
     "hv_set_wait_limit": ([c_void_p, c_double], c_int),
     "hv_inject_wait_timeout": ([c_void_p], c_int),
     "hv_misfit": ([c_void_p, fp, fp, fp, fp, c_size_t, c_void_p], c_int),
+    "hv_misfit_models": ([c_void_p, c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                          fp, c_size_t, c_void_p], c_int),
     "hv_server_create": ([c_size_t, c_int, ctypes.POINTER(c_void_p)], c_int),
     "hv_server_destroy": ([c_void_p, c_double], c_int),
     "hv_submit": ([c_void_p, ctypes.POINTER(HvRequest), ctypes.POINTER(ctypes.c_ulonglong)], c_int),

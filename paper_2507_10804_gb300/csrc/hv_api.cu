@@ -111,11 +111,13 @@ constexpr int kWorkBatches = 4;
 
 int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
 {
-    if (op < HV_OP_FWD || op > HV_OP_MISFIT) return hvi::fail(HV_EINVAL, "unknown operation %d", op);
+    if (op < HV_OP_FWD || op > HV_OP_MISFITS) return hvi::fail(HV_EINVAL, "unknown operation %d", op);
     const bool adjoint = (op == HV_OP_MIGRATE || op == HV_OP_GRAD || op == HV_OP_HV);
     const bool born = (op == HV_OP_BORN || op == HV_OP_HV);
+    const bool models = op == HV_OP_MISFITS;
     if (born && (k < 1 || k > 65535)) return hvi::fail(HV_EINVAL, "k = %d vectors; need 1 <= k <= 65535", k);
-    if (!born) k = 1;
+    if (models && (k < 1 || k > 65535)) return hvi::fail(HV_EINVAL, "k = %d models; need 1 <= k <= 65535", k);
+    if (!born && !models) k = 1;
     if (adjoint) {
         if (ckpt != HV_CKPT_ALL && ckpt < 1)
             return hvi::fail(HV_EINVAL, "checkpoint budget %d; use HV_CKPT_ALL or a value >= 1", ckpt);
@@ -131,6 +133,15 @@ int make_layout(const hv_handle *h, int op, int k, int ckpt, Layout &L)
         return at;
     };
     const size_t fbytes = h->fsize * sizeof(float);
+    if (models) {             // k coefficient fields, a ring of three field batches per model, data, partial sums
+        L.C = take((size_t)k * fbytes);
+        L.work = take((size_t)3 * k * L.fb);
+        L.fields_end = o;
+        L.dd = take((size_t)k * h->ns * h->nt * h->nr * sizeof(float));
+        L.part = take((size_t)k * kResidualBlocks * sizeof(double));
+        L.total = o;
+        return HV_OK;
+    }
     L.C = take(fbytes);
     if (born) L.b = take((size_t)k * fbytes);
     L.zero = take(L.fb);
@@ -738,7 +749,8 @@ extern "C" int hv_workspace_size(const hv_handle *h, int op, int k, int ckpt, si
 {
     if (!h || !bytes) return hvi::fail(HV_EINVAL, "null handle or output");
     Layout L;
-    if (op == HV_OP_FWD || op == HV_OP_BORN || op == HV_OP_WAVEFIELD || op == HV_OP_MISFIT) ckpt = HV_CKPT_ALL;
+    if (op == HV_OP_FWD || op == HV_OP_BORN || op == HV_OP_WAVEFIELD || op == HV_OP_MISFIT || op == HV_OP_MISFITS)
+        ckpt = HV_CKPT_ALL;
     HV_RT(make_layout(h, op, k, ckpt, L));
     *bytes = L.total;
     return HV_OK;
@@ -776,6 +788,98 @@ extern "C" int hv_misfit(hv_handle *h, const float *m, const float *d_obs, doubl
     double *part = reinterpret_cast<double *>((char *)ws + L.part);
     HV_RT(hvk::launch_residual(h, dd, d_obs, dd, part, kResidualBlocks, st));
     HV_RT(hvk::launch_reduce_phi(part, kResidualBlocks, 0.5 / (h->sigma * h->sigma), phi, st));
+    return HV_OK;
+}
+
+namespace {
+
+// The forward sweep of hv_misfit_models: the k models' field batches side by
+// side in a ring of three (u^{n-1}, u^n, u^{n+1}), one launch per step for all
+// of them, receiver samples into the data region.  Touches only the workspace
+// and the handle.
+int misfit_models_sweep(hv_handle *h, int k, const Layout &L, char *w, cudaStream_t st)
+{
+    hvk::TmaMaps maps;
+    HV_RT(hvk::make_maps(h, w, (long long)(L.fields_end / (h->fsize * sizeof(float))), &maps));
+    const size_t rb = (size_t)k * L.fb;
+    float *ring[3];
+    for (int r = 0; r < 3; ++r) ring[r] = reinterpret_cast<float *>(w + L.work + r * rb);
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_CK(cudaMemsetAsync(w + L.work, 0, 3 * rb, st));   // u^{-1} = u^0 = 0 and every ghost band
+    }
+    const int cfg = h->cfg[1];
+    const hvi::RecTiles &rt = rectiles_for(h, hvk::tiling(h, cfg));
+    for (int n = 0; n < h->nt; ++n) {
+        ProfScope ps(h, st, HV_K_FWD);
+        hvk::FwdLaunch a{};
+        a.u_cur = ring[n % 3];
+        a.u_prev = ring[(n + 2) % 3];
+        a.u_next = ring[(n + 1) % 3];
+        a.C = reinterpret_cast<const float *>(w + L.C);
+        a.d_u = reinterpret_cast<float *>(w + L.dd);
+        a.n = n;
+        a.models = k;
+        HV_RT(hvk::launch_fwd(h, cfg, rt, maps, a, st));
+    }
+    return HV_OK;
+}
+
+}  // namespace
+
+extern "C" int hv_misfit_models(hv_handle *h, int k, const float *const *m, const float *const *d_obs,
+                                double *const *phi, void *ws, size_t ws_bytes, void *stream)
+{
+    if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "hv_misfit_models: k = %d models; need 1 <= k <= 65535", k);
+    if (!m || !d_obs || !phi) return hvi::fail(HV_EINVAL, "hv_misfit_models: null pointer array");
+    for (int i = 0; i < k; ++i)
+        if (!m[i] || !d_obs[i] || !phi[i])
+            return hvi::fail(HV_EINVAL, "hv_misfit_models: null model, data or phi pointer for model %d", i);
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_MISFITS, k, HV_CKPT_ALL, L));
+    cudaStream_t st = (cudaStream_t)stream;
+    char *w = (char *)ws;
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        float *C = reinterpret_cast<float *>(w + L.C);
+        for (int i = 0; i < k; ++i) HV_RT(hvk::launch_prep(h, m[i], nullptr, 0, C + (size_t)i * h->fsize, nullptr, st));
+    }
+    // The sweep touches only the workspace and the handle: captured once per
+    // workspace and replayed, as for H v (hv_set_graphs).
+    if (h->graphs_on && !h->prof_on && !h->inject_wait) {
+        const std::string key = "models/" + graph_key(ws, L.total, k, 0, h->cfg, h->launch_mode, false, false, h->wait_ns);
+        auto it = h->graphs.find(key);
+        if (it == h->graphs.end()) {
+            cudaStream_t cs = h->capture_stream;
+            HV_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+            int rc = misfit_models_sweep(h, k, L, w, cs);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(cs, &g);
+            if (rc != HV_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+            cudaGraphExec_t ex = nullptr;
+            e = cudaGraphInstantiate(&ex, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+            it = h->graphs.emplace(key, ex).first;
+        }
+        HV_CK(cudaGraphLaunch(it->second, st));
+    } else {
+        HV_RT(misfit_models_sweep(h, k, L, w, st));
+    }
+    ProfScope ps(h, st, HV_K_OTHER);
+    const size_t ndata = (size_t)h->ns * h->nt * h->nr;
+    float *dd = reinterpret_cast<float *>(w + L.dd);
+    double *part = reinterpret_cast<double *>(w + L.part);
+    for (int i = 0; i < k; ++i) {
+        float *di = dd + (size_t)i * ndata;
+        double *pi = part + (size_t)i * kResidualBlocks;
+        HV_RT(hvk::launch_residual(h, di, d_obs[i], di, pi, kResidualBlocks, st));
+        HV_RT(hvk::launch_reduce_phi(pi, kResidualBlocks, 0.5 / (h->sigma * h->sigma), phi[i], st));
+    }
     return HV_OK;
 }
 

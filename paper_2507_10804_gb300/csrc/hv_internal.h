@@ -156,6 +156,10 @@ struct FwdLaunch {
     float *d_u;                    // [ns][nt][nr] samples of u^{n+1} or nullptr
     float *d_du;                   // [k][ns][nt][nr] samples of du^{n+1} or nullptr
     int n, k;
+    // Without Born fields: models advanced in one launch (0 or 1: one).  Model
+    // i has coefficient field C + i fields, field batches starting `i ns`
+    // fields after u_cur, u_prev and u_next, and data d_u + i ns nt nr.
+    int models;
     StepDeps deps;
 };
 int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,

@@ -10,8 +10,10 @@
 // and model join it (up to the server's vector limit, if the merged
 // workspace fits) and run as one merged call (hv_apply_batch: one forward
 // sweep, the H v vectors and the gradients as one batch of Born vectors),
-// whose results are bitwise those of separate calls; queued applies of one
-// Hessian approximation in one mode join into one apply of all their vectors.  Completion is detected
+// whose results are bitwise those of separate calls; queued misfits on one
+// problem at different models (MCMC chains' proposals) run as one sweep of
+// all the models (hv_misfit_models); queued applies of one Hessian
+// approximation in one mode join into one apply of all their vectors.  Completion is detected
 // with events; the scheduler never blocks on the device (event queries plus
 // short sleeps), and every host wait is bounded.
 #include "hv_internal.h"
@@ -200,6 +202,37 @@ int launch_merged(hv_server *S, const std::vector<Req> &qs, size_t ws_bytes)
 
 bool mergeable(const hv_request &r) { return r.kind == HV_REQ_HV || r.kind == HV_REQ_GRAD || r.kind == HV_REQ_MISFIT; }
 
+// A merged group of misfits at more than one model runs as one sweep of all
+// the models (hv_misfit_models); other merged groups share one model.
+bool models_group(hv_server *S, const std::vector<unsigned long long> &ids)
+{
+    const hv_request &r0 = S->reqs[ids[0]].r;
+    bool other = false;
+    for (auto id : ids) {
+        const hv_request &r = S->reqs[id].r;
+        if (r.kind != HV_REQ_MISFIT) return false;
+        other |= r.m != r0.m;
+    }
+    return ids.size() > 1 && other;
+}
+
+int launch_merged_models(hv_server *S, const std::vector<Req> &qs, size_t ws_bytes)
+{
+    const int slot = qs[0].slot;
+    std::vector<const float *> m, d;
+    std::vector<double *> phi;
+    for (const Req &q : qs) {
+        m.push_back(q.r.m);
+        d.push_back(q.r.d_obs);
+        phi.push_back(q.r.phi);
+    }
+    int rc = hv_misfit_models(qs[0].r.problem, (int)qs.size(), m.data(), d.data(), phi.data(),
+                              S->arena_base + qs[0].off, ws_bytes, (void *)S->streams[slot]);
+    cudaError_t e = cudaEventRecord(S->events[slot], S->streams[slot]);
+    if (rc == HV_OK && e != cudaSuccess) rc = HV_ECUDA;
+    return rc;
+}
+
 // Points per field of an approximation (its grid).
 size_t approx_points(const hv_approx *a)
 {
@@ -261,6 +294,17 @@ std::vector<unsigned long long> merge_group(hv_server *S, std::deque<unsigned lo
         return ids;
     }
     if (!mergeable(r0)) return ids;
+    if (r0.kind == HV_REQ_MISFIT) {              // misfits on the problem at other models: one sweep of all models
+        std::vector<unsigned long long> mids{*head};
+        bool other = false;
+        for (auto it = std::next(head); it != S->queue.end() && (int)mids.size() < S->merge_max; ++it) {
+            const hv_request &r = S->reqs[*it].r;
+            if (r.kind != HV_REQ_MISFIT || r.problem != r0.problem) continue;
+            other |= r.m != r0.m;
+            mids.push_back(*it);
+        }
+        if (other) return mids;
+    }
     int ckpt = r0.kind == HV_REQ_MISFIT ? 0 : r0.ckpt;
     bool have_ckpt = r0.kind != HV_REQ_MISFIT;
     int vecs = r0.kind == HV_REQ_HV ? r0.k : (r0.kind == HV_REQ_GRAD ? 1 : 0);
@@ -288,6 +332,8 @@ int merged_ws(hv_server *S, const std::vector<unsigned long long> &ids, size_t *
         *bytes = 2 * K * approx_points(S->reqs[ids[0]].r.approx) * sizeof(float);
         return HV_OK;
     }
+    if (models_group(S, ids))
+        return hv_workspace_size(S->reqs[ids[0]].r.problem, HV_OP_MISFITS, (int)ids.size(), 0, bytes);
     Merged M;
     for (auto id : ids) {
         const hv_request &r = S->reqs[id].r;
@@ -324,6 +370,7 @@ void worker_loop(hv_server *S)
         // admissions, in arrival order; a request that does not fit yet is passed
         std::vector<std::vector<Req>> admitted;
         std::vector<size_t> admitted_ws;
+        std::vector<bool> admitted_models;
         for (auto it = S->queue.begin(); it != S->queue.end();) {
             int slot = -1;
             for (size_t sl = 0; sl < S->slot_reqs.size(); ++sl)
@@ -361,6 +408,7 @@ void worker_loop(hv_server *S)
             }
             S->slot_reqs[slot] = ids;
             S->slot_off[slot] = off;
+            admitted_models.push_back(models_group(S, ids));
             admitted.push_back(group);
             admitted_ws.push_back(ws);
             // Erasing from a deque invalidates its iterators: work by index.  The merged
@@ -373,10 +421,13 @@ void worker_loop(hv_server *S)
         if (!admitted.empty()) {
             lk.unlock();                          // enqueueing thousands of launches takes a while
             std::vector<int> rcs;
-            for (size_t i = 0; i < admitted.size(); ++i)
-                rcs.push_back(admitted[i].size() == 1                  ? launch(S, admitted[i][0])
-                              : admitted[i][0].r.kind == HV_REQ_APPROX ? launch_merged_approx(S, admitted[i])
-                                                                       : launch_merged(S, admitted[i], admitted_ws[i]));
+            for (size_t i = 0; i < admitted.size(); ++i) {
+                const std::vector<Req> &g = admitted[i];
+                rcs.push_back(g.size() == 1                  ? launch(S, g[0])
+                              : g[0].r.kind == HV_REQ_APPROX ? launch_merged_approx(S, g)
+                              : admitted_models[i]           ? launch_merged_models(S, g, admitted_ws[i])
+                                                             : launch_merged(S, g, admitted_ws[i]));
+            }
             lk.lock();
             for (size_t i = 0; i < admitted.size(); ++i) failed[admitted[i][0].slot] = rcs[i];
             progress = true;

@@ -486,8 +486,11 @@ __device__ __forceinline__ void drain_stages(uint64_t *bars, int from, int to, i
     for (int q = from; q < to; ++q) mbar_wait(&bars[q % ST], (q / ST) & 1, status, wait_ns);
 }
 
-// One forward time step.  grid = (ntiles, k or 1, shot groups).  Vector j = 0
-// writes u^{n+1}; every CTA recomputes Q^n = Lh u^n + s_n from its own tile.
+// One forward time step.  grid = (ntiles, k, shot groups).  With Born fields
+// y is the vector j (vector 0 writes u^{n+1}; every CTA recomputes
+// Q^n = Lh u^n + s_n from its own tile); without them y selects one of k
+// models, each with its own coefficient field, field batch [ns] and data
+// (several models in one sweep, hv_misfit_models).
 template <class C, bool BORN>
 __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdParams p)
 {
@@ -504,14 +507,15 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     const int s0 = grp * p.spg, s1 = min(p.ns, s0 + p.spg), nitems = s1 - s0;
     const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
     const int xb = x0 + 4 * tx, zrow0 = z0 + tz * C::RZ;
-    const bool write_u = p.f_unext >= 0 && j == 0;
+    const int mo = BORN ? 0 : j, uo = mo * p.ns;   // the model and the first field of its batch
+    const bool write_u = p.f_unext >= 0 && (!BORN || j == 0);
 
     auto issue = [&](int i) {
         const int st = i % C::ST, s = s0 + i;
         unsigned char *base = smem + st * S::STAGE;
         mbar_expect_tx(&bars[st], S::STAGE_TX);
-        tma_load(base, &p.map_halo, x0, z0, p.f_ucur + s, &bars[st]);
-        tma_load(base + C::HALOP, &p.map_pt, x0 + GH, z0 + GH, p.f_uprev + s, &bars[st]);
+        tma_load(base, &p.map_halo, x0, z0, p.f_ucur + uo + s, &bars[st]);
+        tma_load(base + C::HALOP, &p.map_pt, x0 + GH, z0 + GH, p.f_uprev + uo + s, &bars[st]);
         if constexpr (BORN) {
             const int fo = j * p.ns + s;
             tma_load(base + C::HALOP + C::PTP, &p.map_halo, x0, z0, p.f_du + fo, &bars[st]);
@@ -527,7 +531,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     if (!wait_for_inputs(p.flow, p.cnt, s0, s1, p.gsz, tile, p.g.ntx, p.g.ntiles, p.need, p.status, p.wait_ns)) return;
     if (threadIdx.x == 0) {
         mbar_expect_tx(&bars[C::ST], S::COEF_TX);
-        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C, &bars[C::ST]);
+        tma_load(sC, &p.map_pt, x0 + GH, z0 + GH, p.f_C + mo, &bars[C::ST]);
         if constexpr (BORN) tma_load(sB, &p.map_pt, x0 + GH, z0 + GH, p.f_b + j, &bars[C::ST]);
         for (int q = 0; q < C::ST && q < nitems; ++q) issue(q);
     }
@@ -568,7 +572,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
             add_source<C>(Q, zrow0, xb, tab.sz[i], tab.sx[i], wav);
             const int rb = tab.rb[i], re = tab.re[i];
             if (write_u) {
-                float *un = p.ws + (unsigned long long)(p.f_unext + s) * p.g.fsize;
+                float *un = p.ws + (unsigned long long)(p.f_unext + uo + s) * p.g.fsize;
 #pragma unroll
                 for (int r = 0; r < C::RZ; ++r) {
                     const int z = zrow0 + r;
@@ -583,7 +587,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                 if (p.d_u && rb < re) {
                     __syncthreads();
                     for (int q = rb + threadIdx.x; q < re; q += C::NT)
-                        p.d_u[((size_t)s * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + q]] = un[p.rt_pos[s * p.nr + q]];
+                        p.d_u[((size_t)(uo + s) * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + q]] = un[p.rt_pos[s * p.nr + q]];
                 }
             }
             if constexpr (BORN) {
@@ -1615,6 +1619,8 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         HV_RT_INTERNAL(field_index(maps.ws, a.u_next, fbytes, &p.f_unext));
         HV_RT_INTERNAL(field_index(maps.ws, a.C, fbytes, &p.f_C));
         const bool born = a.b != nullptr && a.k > 0;
+        if (!born && a.models > 1 && a.deps.cnt)
+            return hvi::fail(HV_EINVAL, "internal: step counters with %d models in one launch", a.models);
         HV_RT_INTERNAL(field_index(maps.ws, born ? a.b : nullptr, fbytes, &p.f_b));
         HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_cur : nullptr, fbytes, &p.f_du));
         HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_io : nullptr, fbytes, &p.f_dio));
@@ -1624,7 +1630,7 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
         p.status = h->status;
         p.wait_ns = h->wait_ns;
-        p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : 1;
+        p.n = a.n; p.nt = h->nt; p.nr = h->nr; p.ns = h->ns; p.k = born ? a.k : std::max(a.models, 1);
         p.gsz = (h->ns + adj_groups(h) - 1) / adj_groups(h);   // the adjoint's shot groups
         p.spg = p.gsz * C::GPC;                                  // shots per CTA: GPC whole groups
         p.cnt = a.deps.cnt;

@@ -230,6 +230,27 @@ class Problem:
         check(self.lib.hv_misfit(self._h, self._m(m), pd, phi.data_ptr(), ws, nb, self._stream()))
         return phi
 
+    def misfit_models(self, ms: torch.Tensor, d_obs: torch.Tensor) -> torch.Tensor:
+        """phi[i] = 1/(2 sigma^2) sum (f(ms[i]) - d_obs)^2 for the k models ms [k, nz, nx] in one forward sweep
+        (hv_misfit_models); d_obs is [ns, nt, nr] for every model or [k, ns, nt, nr].  Returns a float64 CUDA
+        tensor [k], each entry bitwise misfit(ms[i], d_obs[i])."""
+        if not isinstance(ms, torch.Tensor) or ms.dim() != 3:
+            raise ValueError("ms: expected a [k, nz, nx] tensor")
+        k = ms.shape[0]
+        pm = _dev(ms, torch.float32, (k, self.nz, self.nx), "ms", self.device)
+        shared = isinstance(d_obs, torch.Tensor) and d_obs.dim() == 3
+        pd = _dev(d_obs, torch.float32, (self.ns, self.nt, self.nr) if shared else (k, self.ns, self.nt, self.nr),
+                  "d_obs", self.device)
+        phi = torch.empty(k, dtype=torch.float64, device=self.device)
+        nd, npt = self.ns * self.nt * self.nr * 4, self.nz * self.nx * 4
+        arr = ctypes.c_void_p * max(k, 1)
+        m_p = arr(*[pm + i * npt for i in range(k)])
+        d_p = arr(*[pd + (0 if shared else i * nd) for i in range(k)])
+        f_p = arr(*[phi.data_ptr() + 8 * i for i in range(k)])
+        ws, nb = self._workspace(_lib.HV_OP_MISFITS, k, HV_CKPT_ALL)
+        check(self.lib.hv_misfit_models(self._h, int(k), m_p, d_p, f_p, ws, nb, self._stream()))
+        return phi
+
     def set_highpass(self, rho_c: float) -> None:
         """PSF and PDO builds on this problem approximate F_hp H_d F_hp (rho_c > 0 [rad/m]) or H_d (0)
         (hv_set_highpass)."""

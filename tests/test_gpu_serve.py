@@ -261,3 +261,22 @@ def test_queued_approximation_applies_merge_bitwise(problems):
     S.close()
     for o in (A, D, Q, L):
         o.close()
+
+
+def test_queued_misfits_at_different_models_run_as_one_sweep(problems):
+    """Misfit requests on one problem at different models (MCMC chains' proposals) queued behind a running
+    request run as one sweep of all their models (hv_misfit_models); each phi is bitwise the direct misfit."""
+    (w0, P0), (w1, P1) = problems
+    dobs = t(synth.normal(211, w0.ns * w0.nt * w0.nr).reshape(w0.ns, w0.nt, w0.nr) * 1e-3)
+    z = synth.smoothed_normal_vectors(213, 6, w0.nz, w0.nx, 4.0)
+    ms = [t(np.minimum(w0.m * (1.0 + 0.03 * z[i] / np.abs(z[i]).max()), w0.vmax)) for i in range(6)]
+    direct = [float(P0.misfit(m, dobs)) for m in ms]
+    S = Server(hbm_budget=2 << 30, max_concurrent=1)
+    blocker, _ = S.submit_hv(P1, t(w1.m), t(w1.v), ckpt=1)
+    subs = [S.submit_misfit(P0, m, dobs) for m in ms]
+    assert S.wait(blocker, timeout=300) == 0
+    for (rid, phi), ref in zip(subs, direct):
+        assert S.wait(rid, timeout=300) == 0
+        assert float(phi) == ref
+    assert [S.info(rid)["batch"] for rid, _ in subs] == [6] * 6
+    S.close()

@@ -187,3 +187,12 @@ def test_new_entry_points_validate_before_touching_a_gpu(lib):
     assert lib.hv_batch_workspace_size(None, ctypes.byref(b), -1, ctypes.byref(n)) == E
     assert "batch" in lib.hv_last_error().decode() or "handle" in lib.hv_last_error().decode()
     assert lib.hv_hessian_apply_partial(None, None, None, 1, None, -1, None, 0, None) == E
+    arr = (ctypes.c_void_p * 2)(1, 2)                    # non-null entries: nothing is dereferenced before the checks
+    assert lib.hv_misfit_models(None, 0, arr, arr, arr, None, 0, None) == E
+    assert "models" in lib.hv_last_error().decode()
+    assert lib.hv_misfit_models(None, 2, None, arr, arr, None, 0, None) == E
+    holes = (ctypes.c_void_p * 2)(1, None)
+    assert lib.hv_misfit_models(None, 2, arr, holes, arr, None, 0, None) == E
+    assert "model 1" in lib.hv_last_error().decode()
+    assert lib.hv_misfit_models(None, 2, arr, arr, arr, None, 0, None) == E
+    assert "handle" in lib.hv_last_error().decode()
