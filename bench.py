@@ -1012,7 +1012,7 @@ def main():
     ap.add_argument("--ckpt", type=int, default=None, help="snapshots per shot (profiling runs)")
     ap.add_argument("--requests", type=int, default=60, help="serving workload: requests per rate")
     ap.add_argument("--concurrency", type=int, default=16, help="serving workload: concurrent requests")
-    ap.add_argument("--rates", type=float, nargs="+", default=[0.5, 1.0, 2.0],
+    ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 0.8, 1.0, 2.0],
                     help="serving workload: arrival rates as fractions of the serial capacity")
     ap.add_argument("--workload", choices=["paper", "batched", "serve", "quadratic"], default="paper",
                     help="paper: 384x1152, 32 shots, 3000 steps, 1 vector (default); batched: the 64x64 model "

@@ -172,6 +172,29 @@ int hv_misfit(hv_handle *h, const float *m, const float *d_obs, double *phi, voi
 int hv_misfit_models(hv_handle *h, int k, const float *const *m, const float *const *d_obs,
                      double *const *phi, void *ws, size_t ws_bytes, void *stream);
 
+/* Misfit engine: misfit requests (as hv_misfit) that join a running forward
+ * sweep at its next time step instead of waiting for it to end.  The engine
+ * has `slots` slots; each holds one model with its own step counter.
+ * hv_engine_join enqueues the model's preparation and the zeroing of its
+ * fields on `stream` and takes a free slot (HV_EBUSY when none is free);
+ * every hv_engine_tick enqueues one launch that advances every occupied slot
+ * by one time step (slot i at step ticks-since-its-join); after a slot's
+ * nt-th step the same tick reduces its misfit into the slot's phi (bitwise
+ * what hv_misfit gives for that model and data), frees the slot and reports
+ * it in done[0 .. *n_done) (done: HOST array of `slots` ints).  A tick with
+ * no occupied slot launches nothing.  m, d_obs, phi: DEVICE pointers that
+ * must stay valid until the slot is reported done.  All calls of one engine
+ * go to one stream, from one thread.  Device memory: the caller's workspace
+ * of hv_engine_workspace_size bytes (256-byte aligned), owned by the engine
+ * until hv_engine_destroy (which neither synchronises nor frees it). */
+typedef struct hv_engine hv_engine;
+int hv_engine_workspace_size(const hv_handle *h, int slots, size_t *bytes);
+int hv_engine_create(hv_handle *h, int slots, void *ws, size_t ws_bytes, hv_engine **out);
+int hv_engine_join(hv_engine *e, const float *m, const float *d_obs, double *phi, void *stream, int *slot);
+int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done);
+int hv_engine_active(const hv_engine *e, int *active);
+int hv_engine_destroy(hv_engine *e);
+
 /* Gauss-Newton Hessian apply: Hv[j] = F^T F v[j] / sigma^2 for j < k; v and Hv
  * are [k][nz][nx].  Images accumulate in FP64 and are summed over shots in a
  * fixed order, so results do not depend on batching. */
@@ -654,7 +677,8 @@ typedef struct hv_request_info {
     int kind, status;
     double t_submit, t_start, t_done;   /* seconds since the server started        */
     size_t ws_bytes;                     /* arena bytes the request held (alone)     */
-    int batch;                           /* requests that ran merged with it (1: alone) */
+    int batch;                           /* requests that ran merged with it (1: alone); for a misfit
+                                            that joined a lane, the lane's occupied slots at its join */
 } hv_request_info;
 int hv_server_create(size_t hbm_budget, int max_concurrent, hv_server **out);
 /* Stops admitting, waits (bounded by timeout_s) for running requests, frees the arena. */
@@ -675,6 +699,19 @@ int hv_request_get_info(hv_server *s, unsigned long long id, hv_request_info *in
  * 2 x vectors x nz x nx floats).  max_vectors < 2 turns merging off (each
  * request runs alone).  Default 64.  Applies to later admissions. */
 int hv_server_set_batching(hv_server *s, int max_vectors);
+/* Misfit lanes (continuous batching by time step): with slots > 0 (default
+ * 64) a second scheduler thread gives each problem that receives misfit
+ * requests a misfit engine (hv_engine_*) of up to `slots` slots, sized to at
+ * most an eighth of the arena, on a stream of its own.  A queued misfit
+ * request on that problem joins the engine at its next tick, whatever step
+ * the other slots have reached, and is done after its own nt steps (its phi
+ * bitwise hv_misfit's); the thread keeps a few ticks in flight per lane, so
+ * lanes advance while the other thread enqueues long launch sequences, and
+ * releases a lane's arena block after it has been idle for 0.2 s.  When no lane fits in the
+ * arena, misfits run as calls (merged as hv_server_set_batching says; queued
+ * misfits at different models then run as one hv_misfit_models).  slots = 0
+ * turns lanes off.  Applies to lanes created later. */
+int hv_server_set_engine(hv_server *s, int slots);
 
 /* Tile configurations.  The stencil kernels come in a small menu of
  * configurations: a tile shape (TX x TZ points per CTA), a copy-pipeline depth

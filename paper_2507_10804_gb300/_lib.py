@@ -89,6 +89,13 @@ _SIGS = {
     "hv_misfit": ([c_void_p, fp, fp, fp, fp, c_size_t, c_void_p], c_int),
     "hv_misfit_models": ([c_void_p, c_int, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
                           fp, c_size_t, c_void_p], c_int),
+    "hv_engine_workspace_size": ([c_void_p, c_int, ctypes.POINTER(c_size_t)], c_int),
+    "hv_engine_create": ([c_void_p, c_int, fp, c_size_t, ctypes.POINTER(c_void_p)], c_int),
+    "hv_engine_join": ([c_void_p, fp, fp, fp, c_void_p, ip], c_int),
+    "hv_engine_tick": ([c_void_p, c_void_p, ip, ip], c_int),
+    "hv_engine_active": ([c_void_p, ip], c_int),
+    "hv_engine_destroy": ([c_void_p], c_int),
+    "hv_server_set_engine": ([c_void_p, c_int], c_int),
     "hv_server_create": ([c_size_t, c_int, ctypes.POINTER(c_void_p)], c_int),
     "hv_server_destroy": ([c_void_p, c_double], c_int),
     "hv_submit": ([c_void_p, ctypes.POINTER(HvRequest), ctypes.POINTER(ctypes.c_ulonglong)], c_int),

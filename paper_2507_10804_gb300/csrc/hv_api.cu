@@ -464,6 +464,25 @@ std::string graph_key(const void *ws, size_t bytes, int k, int ckpt, const int *
     return buf;
 }
 
+// Keeps an instantiated graph under `key`; the cache holds the kMaxGraphs most
+// recent (a server's arena offsets and batch sizes make many keys).  An
+// evicted graph still in flight is freed when it completes.
+constexpr size_t kMaxGraphs = 32;
+cudaGraphExec_t cache_graph(hv_handle *h, const std::string &key, cudaGraphExec_t ex)
+{
+    while (h->graphs.size() >= kMaxGraphs && !h->graph_order.empty()) {
+        auto old = h->graphs.find(h->graph_order.front());
+        if (old != h->graphs.end()) {
+            cudaGraphExecDestroy(old->second);
+            h->graphs.erase(old);
+        }
+        h->graph_order.pop_front();
+    }
+    h->graphs.emplace(key, ex);
+    h->graph_order.push_back(key);
+    return ex;
+}
+
 // The shared driver of migrate / misfit_grad / hessian_apply.
 //   kind 0: migrate   r = user data,                         scale h^2
 //   kind 1: gradient  r = f(m) - d_obs (computed),           scale h^2 / sigma^2
@@ -491,7 +510,8 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
             graph_key(ws, L.total, kk, ckpt, h->cfg, h->launch_mode + 16 * (int)h->img_f64, h->fuse_steps, L.resident,
                       h->wait_ns);
         auto it = h->graphs.find(key);
-        if (it == h->graphs.end()) {
+        cudaGraphExec_t ge = it == h->graphs.end() ? nullptr : it->second;
+        if (!ge) {
             cudaStream_t cs = h->capture_stream;
             HV_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             int rc = run_adjoint_body(h, kind, in, kk, phi, ckpt, ws, L, cs);
@@ -506,9 +526,9 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
             e = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-            it = h->graphs.emplace(key, ex).first;
+            ge = cache_graph(h, key, ex);
         }
-        HV_CK(cudaGraphLaunch(it->second, st));
+        HV_CK(cudaGraphLaunch(ge, st));
     } else {
         HV_RT(run_adjoint_body(h, kind, in, kk, phi, ckpt, ws, L, st));
     }
@@ -849,7 +869,8 @@ extern "C" int hv_misfit_models(hv_handle *h, int k, const float *const *m, cons
     if (h->graphs_on && !h->prof_on && !h->inject_wait) {
         const std::string key = "models/" + graph_key(ws, L.total, k, 0, h->cfg, h->launch_mode, false, false, h->wait_ns);
         auto it = h->graphs.find(key);
-        if (it == h->graphs.end()) {
+        cudaGraphExec_t ge = it == h->graphs.end() ? nullptr : it->second;
+        if (!ge) {
             cudaStream_t cs = h->capture_stream;
             HV_CK(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
             int rc = misfit_models_sweep(h, k, L, w, cs);
@@ -864,9 +885,9 @@ extern "C" int hv_misfit_models(hv_handle *h, int k, const float *const *m, cons
             e = cudaGraphInstantiate(&ex, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
-            it = h->graphs.emplace(key, ex).first;
+            ge = cache_graph(h, key, ex);
         }
-        HV_CK(cudaGraphLaunch(it->second, st));
+        HV_CK(cudaGraphLaunch(ge, st));
     } else {
         HV_RT(misfit_models_sweep(h, k, L, w, st));
     }
@@ -880,6 +901,162 @@ extern "C" int hv_misfit_models(hv_handle *h, int k, const float *const *m, cons
         HV_RT(hvk::launch_residual(h, di, d_obs[i], di, pi, kResidualBlocks, st));
         HV_RT(hvk::launch_reduce_phi(pi, kResidualBlocks, 0.5 / (h->sigma * h->sigma), phi[i], st));
     }
+    return HV_OK;
+}
+
+// ---------------------------------------------------------------- misfit engine
+// Misfit requests that join a running sweep at the next time step
+// (hv_engine_*): a fixed set of slots, each a model with its own coefficient
+// field, ring of three field batches, data and step counter; one launch per
+// tick advances every occupied slot by one step.
+struct hv_engine {
+    hv_handle *h = nullptr;
+    int slots = 0;
+    char *ws = nullptr;
+    Layout L;
+    int *join_dev = nullptr;           // [slots] tick of each slot's step 0 (kFreeSlot: free)
+    hvk::TmaMaps maps;
+    std::vector<int> join;
+    std::vector<const float *> dobs;
+    std::vector<double *> phi;
+    int tick = 0;                      // launches since the last rebase
+    int active = 0;
+    bool dirty = true;                 // join differs from join_dev
+};
+
+namespace {
+
+constexpr int kFreeSlot = 1 << 30;     // later than any tick: a free slot takes no step
+constexpr int kRebaseTick = 1 << 28;
+
+size_t engine_bytes(const Layout &L, int slots) { return L.total + align256((size_t)slots * sizeof(int)); }
+
+}  // namespace
+
+extern "C" int hv_engine_workspace_size(const hv_handle *h, int slots, size_t *bytes)
+{
+    if (!h || !bytes) return hvi::fail(HV_EINVAL, "hv_engine_workspace_size: null handle or output");
+    Layout L;
+    HV_RT(make_layout(h, HV_OP_MISFITS, slots, HV_CKPT_ALL, L));
+    *bytes = engine_bytes(L, slots);
+    return HV_OK;
+}
+
+extern "C" int hv_engine_create(hv_handle *h, int slots, void *ws, size_t ws_bytes, hv_engine **out)
+{
+    if (!out) return hvi::fail(HV_EINVAL, "hv_engine_create: null output pointer");
+    *out = nullptr;
+    if (slots < 1 || slots > 65535) return hvi::fail(HV_EINVAL, "hv_engine_create: %d slots; need 1..65535", slots);
+    Layout L;
+    HV_RT(check_common(h, ws, ws_bytes, HV_OP_MISFITS, slots, HV_CKPT_ALL, L));
+    if (ws_bytes < engine_bytes(L, slots))
+        return hvi::fail(HV_ENOMEM, "hv_engine_create: workspace of %zu bytes; %zu needed", ws_bytes, engine_bytes(L, slots));
+    hv_engine *e = new hv_engine();
+    e->h = h;
+    e->slots = slots;
+    e->ws = (char *)ws;
+    e->L = L;
+    e->join_dev = reinterpret_cast<int *>(e->ws + L.total);
+    e->join.assign(slots, kFreeSlot);
+    e->dobs.assign(slots, nullptr);
+    e->phi.assign(slots, nullptr);
+    int rc = hvk::make_maps(h, ws, (long long)(L.fields_end / (h->fsize * sizeof(float))), &e->maps);
+    if (rc != HV_OK) {
+        delete e;
+        return rc;
+    }
+    *out = e;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_destroy(hv_engine *e)
+{
+    delete e;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_join(hv_engine *e, const float *m, const float *d_obs, double *phi, void *stream, int *slot)
+{
+    if (!e || !m || !d_obs || !phi || !slot) return hvi::fail(HV_EINVAL, "hv_engine_join: null argument");
+    *slot = -1;
+    int j = 0;
+    while (j < e->slots && e->join[j] != kFreeSlot) ++j;
+    if (j == e->slots) return hvi::fail(HV_EBUSY, "hv_engine_join: all %d slots are taken", e->slots);
+    hv_handle *h = e->h;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t fbytes = h->fsize * sizeof(float);
+    if (e->active == 0) e->tick = 0;   // nothing in flight depends on the old count once every slot is free
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_prep(h, m, nullptr, 0, reinterpret_cast<float *>(e->ws + e->L.C) + (size_t)j * h->fsize,
+                               nullptr, st));
+        HV_CK(cudaMemsetAsync(e->ws + e->L.work + (size_t)3 * j * h->ns * fbytes, 0, (size_t)3 * h->ns * fbytes, st));
+    }
+    e->join[j] = e->tick;
+    e->dobs[j] = d_obs;
+    e->phi[j] = phi;
+    e->dirty = true;
+    ++e->active;
+    *slot = j;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done)
+{
+    if (!e || !done || !n_done) return hvi::fail(HV_EINVAL, "hv_engine_tick: null argument");
+    *n_done = 0;
+    if (e->active == 0) return HV_OK;
+    hv_handle *h = e->h;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (e->tick >= kRebaseTick) {      // keep the counters far below kFreeSlot
+        int base = kFreeSlot;
+        for (int v : e->join) base = std::min(base, v);
+        for (int &v : e->join)
+            if (v != kFreeSlot) v -= base;
+        e->tick -= base;
+        e->dirty = true;
+    }
+    if (e->dirty) {                    // pageable source: staged before the call returns
+        HV_CK(cudaMemcpyAsync(e->join_dev, e->join.data(), (size_t)e->slots * sizeof(int), cudaMemcpyHostToDevice, st));
+        e->dirty = false;
+    }
+    int ymax = 0;
+    for (int j = 0; j < e->slots; ++j)
+        if (e->join[j] != kFreeSlot) ymax = j + 1;
+    {
+        ProfScope ps(h, st, HV_K_FWD);
+        hvk::FwdLaunch a{};
+        a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
+        a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
+        a.C = reinterpret_cast<const float *>(e->ws + e->L.C);
+        a.d_u = reinterpret_cast<float *>(e->ws + e->L.dd);
+        a.n = e->tick;
+        a.models = ymax;
+        a.slot_join = e->join_dev;
+        const int cfg = h->cfg[1];
+        HV_RT(hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, st));
+    }
+    const size_t ndata = (size_t)h->ns * h->nt * h->nr;
+    for (int j = 0; j < e->slots; ++j) {
+        if (e->join[j] == kFreeSlot || e->tick - e->join[j] != h->nt - 1) continue;
+        ProfScope ps(h, st, HV_K_OTHER);
+        float *dj = reinterpret_cast<float *>(e->ws + e->L.dd) + (size_t)j * ndata;
+        double *pj = reinterpret_cast<double *>(e->ws + e->L.part) + (size_t)j * kResidualBlocks;
+        HV_RT(hvk::launch_residual(h, dj, e->dobs[j], dj, pj, kResidualBlocks, st));
+        HV_RT(hvk::launch_reduce_phi(pj, kResidualBlocks, 0.5 / (h->sigma * h->sigma), e->phi[j], st));
+        e->join[j] = kFreeSlot;
+        e->dirty = true;
+        --e->active;
+        done[(*n_done)++] = j;
+    }
+    ++e->tick;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_active(const hv_engine *e, int *active)
+{
+    if (!e || !active) return hvi::fail(HV_EINVAL, "hv_engine_active: null argument");
+    *active = e->active;
     return HV_OK;
 }
 

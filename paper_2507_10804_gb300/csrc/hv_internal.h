@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <functional>
+#include <deque>
 #include <map>
 #include <mutex>
 #include <string>
@@ -104,6 +105,7 @@ struct hv_handle {
     // a shot group added to double-float images; true = every shot's product added in FP64
     bool img_f64 = false;
     std::map<std::string, cudaGraphExec_t> graphs;
+    std::deque<std::string> graph_order;   // keys, oldest first (the cache holds at most kMaxGraphs)
     // profiling (hv_profile)
     bool prof_on = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -160,6 +162,10 @@ struct FwdLaunch {
     // i has coefficient field C + i fields, field batches starting `i ns`
     // fields after u_cur, u_prev and u_next, and data d_u + i ns nt nr.
     int models;
+    // Without Born fields: per-model step counters (device, [models]; see k_fwd),
+    // or nullptr.  With them, n counts launches and u_cur is the first field of
+    // the models' rings (model i: 3 ns fields from u_cur + 3 ns i fields).
+    const int *slot_join;
     StepDeps deps;
 };
 int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,

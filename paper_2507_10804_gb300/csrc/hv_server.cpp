@@ -10,10 +10,13 @@
 // and model join it (up to the server's vector limit, if the merged
 // workspace fits) and run as one merged call (hv_apply_batch: one forward
 // sweep, the H v vectors and the gradients as one batch of Born vectors),
-// whose results are bitwise those of separate calls; queued misfits on one
-// problem at different models (MCMC chains' proposals) run as one sweep of
-// all the models (hv_misfit_models); queued applies of one Hessian
-// approximation in one mode join into one apply of all their vectors.  Completion is detected
+// whose results are bitwise those of separate calls; queued applies of one
+// Hessian approximation in one mode join into one apply of all their vectors.
+// Misfit requests (MCMC chains' proposals) go to a misfit lane per problem,
+// driven by a second thread: a misfit engine (hv_engine_*) whose slots each
+// hold one model with its own step counter, so a misfit joins a running sweep
+// at its next time step; where no lane fits in the arena, queued misfits at
+// different models run as one sweep of all the models (hv_misfit_models).  Completion is detected
 // with events; the scheduler never blocks on the device (event queries plus
 // short sleeps), and every host wait is bounded.
 #include "hv_internal.h"
@@ -84,7 +87,26 @@ struct Req {
     size_t ws = 0, off = 0;
     int slot = -1;
     int batch = 1;            // requests that ran in the same launch sequence
+    bool no_lane = false;     // a misfit left to the scheduler (its lane did not fit)
     double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+// A misfit lane: the misfit engine of one problem (hv_engine_*) on its own
+// stream, in an arena block.  Queued misfits on the problem join it at its
+// next tick; the scheduler keeps up to kLookahead ticks in flight.
+constexpr int kLookahead = 8;
+struct Lane {
+    hv_engine *e = nullptr;
+    int slots = 0;
+    size_t off = 0;
+    cudaStream_t st = nullptr;
+    std::vector<unsigned long long> slot_req;   // request per engine slot (0: free)
+    int active = 0;                             // occupied engine slots
+    int busy = 0;                               // occupied + admitted, not yet joined
+    std::deque<cudaEvent_t> ticks;              // recorded after recent ticks, oldest first
+    std::vector<std::pair<cudaEvent_t, std::vector<unsigned long long>>> finishing;   // done when the event is
+    int failed = HV_OK;                         // a join or tick failed: the lane takes no more requests
+    double idle_since = -1;
 };
 
 }  // namespace
@@ -99,13 +121,17 @@ struct hv_server {
     std::vector<std::vector<unsigned long long>> slot_reqs;   // request ids per slot (empty = free)
     std::vector<size_t> slot_off;                              // arena offset held by the slot
     int merge_max = 64;                                        // vectors per merged call (< 2: no merging)
+    int engine_slots = 64;                                     // slots per misfit lane (0: misfits run as calls)
+    std::unordered_map<hv_handle *, Lane> lanes;               // lane thread only
+    int lane_reqs = 0;                                         // requests admitted to lanes and not done (under mu)
+    std::vector<cudaEvent_t> ev_pool;                          // lane thread only
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<unsigned long long> queue;
     std::unordered_map<unsigned long long, Req> reqs;
     unsigned long long next_id = 1;
     std::atomic<bool> stop{false};
-    std::thread worker;
+    std::thread worker, lane_worker;
     Clock::time_point t0;
 
     double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
@@ -343,6 +369,226 @@ int merged_ws(hv_server *S, const std::vector<unsigned long long> &ids, size_t *
     return hv_batch_workspace_size(S->reqs[ids[0]].r.problem, M.make(), M.ckpt, bytes);
 }
 
+// ---------------------------------------------------------------- misfit lanes
+// A queued misfit that its problem's lane takes (lanes on, and one fits).
+bool lane_bound(const hv_server *S, const Req &q)
+{
+    return q.r.kind == HV_REQ_MISFIT && S->engine_slots > 0 && !q.no_lane;
+}
+
+cudaEvent_t take_event(hv_server *S)
+{
+    cudaEvent_t e = nullptr;
+    if (!S->ev_pool.empty()) {
+        e = S->ev_pool.back();
+        S->ev_pool.pop_back();
+    } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+        e = nullptr;
+    }
+    return e;
+}
+
+// The lane of problem p, created on first use with as many slots (up to
+// engine_slots) as fit in an eighth of the budget; nullptr if none fits now.
+Lane *lane_for(hv_server *S, hv_handle *p)
+{
+    auto it = S->lanes.find(p);
+    if (it != S->lanes.end()) return it->second.failed == HV_OK ? &it->second : nullptr;
+    int slots = S->engine_slots;
+    size_t bytes = 0;
+    while (slots > 1 && (hv_engine_workspace_size(p, slots, &bytes) != HV_OK || bytes > S->budget / 8)) slots /= 2;
+    if (hv_engine_workspace_size(p, slots, &bytes) != HV_OK) return nullptr;
+    Lane L;
+    if (!S->arena->alloc(bytes, &L.off)) return nullptr;
+    if (cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) != cudaSuccess) {
+        S->arena->release(L.off);
+        return nullptr;
+    }
+    if (hv_engine_create(p, slots, S->arena_base + L.off, bytes, &L.e) != HV_OK) {
+        cudaStreamDestroy(L.st);
+        S->arena->release(L.off);
+        return nullptr;
+    }
+    L.slots = slots;
+    L.slot_req.assign(slots, 0);
+    return &(S->lanes[p] = std::move(L));
+}
+
+struct Join {
+    hv_handle *p;
+    unsigned long long id;
+    const float *m, *d_obs;
+    double *phi;
+};
+
+// Outside the lock: the admitted joins, then ticks until each lane has
+// kLookahead ticks in flight.  Returns whether anything was enqueued;
+// `failed` collects requests that could not join.
+bool lane_work(hv_server *S, const std::vector<Join> &joins, std::vector<std::pair<unsigned long long, int>> &failed)
+{
+    bool any = !joins.empty();
+    for (const Join &j : joins) {
+        Lane &L = S->lanes[j.p];
+        int slot = -1;
+        int rc = L.failed != HV_OK ? L.failed : hv_engine_join(L.e, j.m, j.d_obs, j.phi, (void *)L.st, &slot);
+        if (rc != HV_OK) {
+            if (L.failed == HV_OK) L.failed = rc;
+            --L.busy;
+            failed.push_back({j.id, rc});
+            continue;
+        }
+        L.slot_req[slot] = j.id;
+        ++L.active;
+    }
+    std::vector<int> done;
+    for (auto &kv : S->lanes) {
+        Lane &L = kv.second;
+        done.resize(L.slots);
+        while (L.active > 0 && L.failed == HV_OK) {
+            while (!L.ticks.empty() && cudaEventQuery(L.ticks.front()) != cudaErrorNotReady) {
+                S->ev_pool.push_back(L.ticks.front());
+                L.ticks.pop_front();
+            }
+            if ((int)L.ticks.size() >= kLookahead) break;
+            int nd = 0;
+            int rc = hv_engine_tick(L.e, (void *)L.st, done.data(), &nd);
+            cudaEvent_t ev = take_event(S);
+            if (rc == HV_OK && (!ev || cudaEventRecord(ev, L.st) != cudaSuccess)) rc = HV_ECUDA;
+            if (ev) L.ticks.push_back(ev);
+            any = true;
+            if (rc != HV_OK) {             // the occupied slots' requests fail; the lane takes no more
+                L.failed = rc;
+                for (int q = 0; q < L.slots; ++q)
+                    if (L.slot_req[q]) {
+                        failed.push_back({L.slot_req[q], rc});
+                        L.slot_req[q] = 0;
+                    }
+                L.busy -= L.active;
+                L.active = 0;
+                break;
+            }
+            if (nd > 0) {
+                std::vector<unsigned long long> ids;
+                for (int q = 0; q < nd; ++q) {
+                    ids.push_back(L.slot_req[done[q]]);
+                    L.slot_req[done[q]] = 0;
+                }
+                L.active -= nd;
+                L.busy -= nd;
+                cudaEvent_t f = take_event(S);
+                if (f && cudaEventRecord(f, L.st) == cudaSuccess) {
+                    L.finishing.push_back({f, ids});
+                } else {
+                    if (f) S->ev_pool.push_back(f);
+                    for (auto id : ids) failed.push_back({id, HV_ECUDA});
+                }
+            }
+        }
+    }
+    return any;
+}
+
+// Under the lock: requests whose last tick has completed, lanes idle for a
+// while released (their work has drained).  Returns whether a request finished.
+bool lane_completions(hv_server *S, std::vector<std::pair<unsigned long long, int>> &failed)
+{
+    bool any = false;
+    const double t = S->now();
+    for (auto &f : failed) {
+        Req &q = S->reqs[f.first];
+        q.status = f.second;
+        q.t_done = t;
+        --S->lane_reqs;
+        any = true;
+    }
+    failed.clear();
+    for (auto it = S->lanes.begin(); it != S->lanes.end();) {
+        Lane &L = it->second;
+        for (size_t i = 0; i < L.finishing.size();) {
+            cudaError_t e = cudaEventQuery(L.finishing[i].first);
+            if (e == cudaErrorNotReady) {
+                ++i;
+                continue;
+            }
+            for (auto id : L.finishing[i].second) {
+                Req &q = S->reqs[id];
+                q.status = e == cudaSuccess ? HV_OK : HV_ECUDA;
+                q.t_done = t;
+                --S->lane_reqs;
+            }
+            S->ev_pool.push_back(L.finishing[i].first);
+            L.finishing.erase(L.finishing.begin() + i);
+            any = true;
+        }
+        const bool idle = L.busy == 0 && L.finishing.empty();
+        if (!idle) {
+            L.idle_since = -1;
+            ++it;
+            continue;
+        }
+        if (L.idle_since < 0) L.idle_since = t;
+        if (t - L.idle_since < 0.2 || cudaStreamQuery(L.st) == cudaErrorNotReady) {
+            ++it;
+            continue;
+        }
+        for (cudaEvent_t e : L.ticks) S->ev_pool.push_back(e);
+        hv_engine_destroy(L.e);
+        cudaStreamDestroy(L.st);
+        S->arena->release(L.off);
+        it = S->lanes.erase(it);
+    }
+    return any;
+}
+
+// The lane thread: admits queued misfits into their problems' lanes (a
+// misfit whose lane does not fit in the arena is left to the scheduler), then
+// joins and ticks outside the lock, so that the lanes advance while the
+// scheduler thread enqueues long launch sequences.
+void lane_loop(hv_server *S)
+{
+    cudaSetDevice(S->device);
+    std::vector<std::pair<unsigned long long, int>> lane_failed;
+    std::unique_lock<std::mutex> lk(S->mu);
+    while (!S->stop.load()) {
+        bool progress = lane_completions(S, lane_failed);
+        if (progress) S->cv_done.notify_all();
+        std::vector<Join> joins;
+        for (auto it = S->queue.begin(); it != S->queue.end();) {
+            Req &q = S->reqs[*it];
+            if (!lane_bound(S, q)) {
+                ++it;
+                continue;
+            }
+            Lane *L = lane_for(S, q.r.problem);
+            if (!L) {                              // no room for a lane: the scheduler runs it as a call
+                q.no_lane = true;
+                S->cv_work.notify_all();
+                ++it;
+                continue;
+            }
+            if (L->busy >= L->slots) {
+                ++it;
+                continue;
+            }
+            ++L->busy;
+            ++S->lane_reqs;
+            q.status = HV_REQ_RUNNING;
+            q.t_start = S->now();
+            q.batch = L->busy;
+            joins.push_back({q.r.problem, q.id, q.r.m, q.r.d_obs, q.r.phi});
+            it = S->queue.erase(it);
+        }
+        bool active = !joins.empty();
+        for (auto &kv : S->lanes) active |= kv.second.active > 0;
+        if (active) {
+            lk.unlock();
+            progress |= lane_work(S, joins, lane_failed);
+            lk.lock();
+        }
+        if (!progress) S->cv_work.wait_for(lk, std::chrono::microseconds(active ? 10 : 50));
+    }
+}
+
 void worker_loop(hv_server *S)
 {
     cudaSetDevice(S->device);
@@ -372,13 +618,20 @@ void worker_loop(hv_server *S)
         std::vector<size_t> admitted_ws;
         std::vector<bool> admitted_models;
         for (auto it = S->queue.begin(); it != S->queue.end();) {
+            if (lane_bound(S, S->reqs[*it])) {   // the lane thread admits it
+                ++it;
+                continue;
+            }
             int slot = -1;
             for (size_t sl = 0; sl < S->slot_reqs.size(); ++sl)
                 if (S->slot_reqs[sl].empty()) {
                     slot = (int)sl;
                     break;
                 }
-            if (slot < 0) break;
+            if (slot < 0) {
+                ++it;
+                continue;
+            }
             std::vector<unsigned long long> ids = merge_group(S, it);
             size_t ws = S->reqs[*it].ws, off = 0;
             if (ids.size() > 1 && merged_ws(S, ids, &ws) != HV_OK) {
@@ -463,6 +716,7 @@ extern "C" int hv_server_create(size_t hbm_budget, int max_concurrent, hv_server
         cudaEventCreateWithFlags(&S->events[i], cudaEventDisableTiming);
     }
     S->worker = std::thread(worker_loop, S);
+    S->lane_worker = std::thread(lane_loop, S);
     *out = S;
     return HV_OK;
 }
@@ -479,7 +733,7 @@ extern "C" int hv_server_destroy(hv_server *S, double timeout_s)
         auto busy = [&] {
             for (auto &ids : S->slot_reqs)
                 if (!ids.empty()) return true;
-            return false;
+            return S->lane_reqs > 0;
         };
         while (busy()) {
             if (S->cv_done.wait_until(lk, deadline) == std::cv_status::timeout && busy()) {
@@ -491,7 +745,17 @@ extern "C" int hv_server_destroy(hv_server *S, double timeout_s)
     S->stop.store(true);
     S->cv_work.notify_all();
     S->worker.join();
+    S->lane_worker.join();
     if (rc == HV_OK) {
+        for (auto &kv : S->lanes) {
+            Lane &L = kv.second;
+            cudaStreamSynchronize(L.st);
+            for (cudaEvent_t e : L.ticks) cudaEventDestroy(e);
+            for (auto &f : L.finishing) cudaEventDestroy(f.first);
+            hv_engine_destroy(L.e);
+            cudaStreamDestroy(L.st);
+        }
+        for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
         for (auto st : S->streams) cudaStreamDestroy(st);
         for (auto ev : S->events) cudaEventDestroy(ev);
         cudaFree(S->arena_base);
@@ -576,6 +840,15 @@ extern "C" int hv_request_get_info(hv_server *S, unsigned long long id, hv_reque
     info->t_done = q.t_done;
     info->ws_bytes = q.ws;
     info->batch = q.batch;
+    return HV_OK;
+}
+
+extern "C" int hv_server_set_engine(hv_server *S, int slots)
+{
+    if (!S || slots < 0 || slots > 65535)
+        return hvi::fail(HV_EINVAL, "hv_server_set_engine: null server or slots outside 0..65535");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->engine_slots = slots;
     return HV_OK;
 }
 

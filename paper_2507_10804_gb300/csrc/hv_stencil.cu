@@ -403,6 +403,7 @@ struct FwdParams {
     CUtensorMap map_pt;         // box TX x TZ x 1
     float *ws;                  // workspace base (field 0)
     int f_ucur, f_uprev, f_unext;   // field-batch starts (f_unext < 0: do not write u)
+    const int *slot_join;       // per-model step counters (no Born fields), or nullptr (see k_fwd)
     int f_C, f_b, f_du, f_dio;      // coefficient fields and Born field batches
     float *d_u, *d_du;
     const float *az, *ax, *wavelet;
@@ -490,7 +491,11 @@ __device__ __forceinline__ void drain_stages(uint64_t *bars, int from, int to, i
 // y is the vector j (vector 0 writes u^{n+1}; every CTA recomputes
 // Q^n = Lh u^n + s_n from its own tile); without them y selects one of k
 // models, each with its own coefficient field, field batch [ns] and data
-// (several models in one sweep, hv_misfit_models).
+// (several models in one sweep, hv_misfit_models).  With slot_join (no Born
+// fields) every model has its own step counter: p.n counts the launches, model
+// j takes its step p.n - slot_join[j] (none if that is outside [0, nt), e.g. a
+// free slot, slot_join 1 << 30 > p.n) and its three time levels rotate through a
+// ring of three field batches of its own starting 3 ns j fields after f_ucur.
 template <class C, bool BORN>
 __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdParams p)
 {
@@ -507,15 +512,26 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
     const int s0 = grp * p.spg, s1 = min(p.ns, s0 + p.spg), nitems = s1 - s0;
     const int tx = threadIdx.x % C::BX, tz = threadIdx.x / C::BX;
     const int xb = x0 + 4 * tx, zrow0 = z0 + tz * C::RZ;
-    const int mo = BORN ? 0 : j, uo = mo * p.ns;   // the model and the first field of its batch
+    const int mo = BORN ? 0 : j;                    // the model
+    int n = p.n, fcur = p.f_ucur + mo * p.ns, fprev = p.f_uprev + mo * p.ns, fnext = p.f_unext + mo * p.ns;
+    if constexpr (!BORN) {
+        if (p.slot_join) {                          // read before the grid-dependency wait: written by an earlier copy
+            n = p.n - p.slot_join[j];
+            if (n < 0 || n >= p.nt) return;         // the slot takes no step in this launch
+            const int ring = p.f_ucur + 3 * p.ns * j;
+            fcur = ring + (n % 3) * p.ns;
+            fprev = ring + ((n + 2) % 3) * p.ns;
+            fnext = ring + ((n + 1) % 3) * p.ns;
+        }
+    }
     const bool write_u = p.f_unext >= 0 && (!BORN || j == 0);
 
     auto issue = [&](int i) {
         const int st = i % C::ST, s = s0 + i;
         unsigned char *base = smem + st * S::STAGE;
         mbar_expect_tx(&bars[st], S::STAGE_TX);
-        tma_load(base, &p.map_halo, x0, z0, p.f_ucur + uo + s, &bars[st]);
-        tma_load(base + C::HALOP, &p.map_pt, x0 + GH, z0 + GH, p.f_uprev + uo + s, &bars[st]);
+        tma_load(base, &p.map_halo, x0, z0, fcur + s, &bars[st]);
+        tma_load(base + C::HALOP, &p.map_pt, x0 + GH, z0 + GH, fprev + s, &bars[st]);
         if constexpr (BORN) {
             const int fo = j * p.ns + s;
             tma_load(base + C::HALOP + C::PTP, &p.map_halo, x0, z0, p.f_du + fo, &bars[st]);
@@ -545,7 +561,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                           x0 + C::TX <= p.g.nb + p.g.nx);
     SpongeRegs<C::RZ> spr{};
     if (sponge) sponge_regs<C::RZ>(spr, p.az, p.ax, zrow0, xb, p.g.NZ, p.g.NX);
-    const float wav = p.wavelet[p.n];
+    const float wav = p.wavelet[n];
 
     bool ok = mbar_wait(&bars[C::ST], 0, p.status, p.wait_ns);
     if (__syncthreads_or(!ok)) {
@@ -572,7 +588,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
             add_source<C>(Q, zrow0, xb, tab.sz[i], tab.sx[i], wav);
             const int rb = tab.rb[i], re = tab.re[i];
             if (write_u) {
-                float *un = p.ws + (unsigned long long)(p.f_unext + uo + s) * p.g.fsize;
+                float *un = p.ws + (unsigned long long)(fnext + s) * p.g.fsize;
 #pragma unroll
                 for (int r = 0; r < C::RZ; ++r) {
                     const int z = zrow0 + r;
@@ -587,7 +603,7 @@ __global__ void __launch_bounds__(C::NT, 2) k_fwd(const __grid_constant__ FwdPar
                 if (p.d_u && rb < re) {
                     __syncthreads();
                     for (int q = rb + threadIdx.x; q < re; q += C::NT)
-                        p.d_u[((size_t)(uo + s) * p.nt + p.n) * p.nr + p.rt_rec[s * p.nr + q]] = un[p.rt_pos[s * p.nr + q]];
+                        p.d_u[((size_t)(mo * p.ns + s) * p.nt + n) * p.nr + p.rt_rec[s * p.nr + q]] = un[p.rt_pos[s * p.nr + q]];
                 }
             }
             if constexpr (BORN) {
@@ -1626,6 +1642,7 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
         HV_RT_INTERNAL(field_index(maps.ws, born ? a.du_io : nullptr, fbytes, &p.f_dio));
         p.d_u = a.d_u;
         p.d_du = born ? a.d_du : nullptr;
+        p.slot_join = born ? nullptr : a.slot_join;
         p.az = h->az; p.ax = h->ax; p.wavelet = h->wavelet;
         p.src_zx = h->src_zx; p.rt_off = rt.off; p.rt_rec = rt.rec; p.rt_pos = rt.pos;
         p.status = h->status;

@@ -390,6 +390,61 @@ class Problem:
         return PdoApprox(self.lib, out, self.device)
 
 
+class MisfitEngine:
+    """Misfits that join a running forward sweep at its next time step (hv_engine_*): `slots` models, each with
+    its own step counter, advanced together one time step per tick.  All work runs on the problem's stream (the
+    current torch stream)."""
+
+    def __init__(self, problem: Problem, slots: int):
+        self.P, self.lib, self.slots = problem, problem.lib, int(slots)
+        n = ctypes.c_size_t()
+        check(self.lib.hv_engine_workspace_size(problem._h, self.slots, ctypes.byref(n)))
+        self._ws = torch.empty(max(n.value, 256), dtype=torch.uint8, device=problem.device)
+        e = ctypes.c_void_p()
+        check(self.lib.hv_engine_create(problem._h, self.slots, self._ws.data_ptr(), self._ws.numel(), ctypes.byref(e)))
+        self._e = e
+        self._done = (ctypes.c_int * self.slots)()
+        self._held = {}                 # slot -> the tensors its work reads and writes
+
+    def join(self, m: torch.Tensor, d_obs: torch.Tensor):
+        """(slot, phi): phi (0-d float64) receives the misfit once the slot is reported done by tick()."""
+        P = self.P
+        pm = P._m(m)
+        pd = _dev(d_obs, torch.float32, (P.ns, P.nt, P.nr), "d_obs", P.device)
+        phi = torch.empty((), dtype=torch.float64, device=P.device)
+        slot = ctypes.c_int()
+        check(self.lib.hv_engine_join(self._e, pm, pd, phi.data_ptr(), P._stream(), ctypes.byref(slot)))
+        self._held[slot.value] = (m, d_obs, phi)
+        return slot.value, phi
+
+    def tick(self) -> list:
+        """One time step of every occupied slot; returns the slots whose misfit this tick completed."""
+        n = ctypes.c_int()
+        check(self.lib.hv_engine_tick(self._e, self.P._stream(), self._done, ctypes.byref(n)))
+        done = [self._done[i] for i in range(n.value)]
+        for j in done:
+            self._held.pop(j, None)
+        return done
+
+    @property
+    def active(self) -> int:
+        n = ctypes.c_int()
+        check(self.lib.hv_engine_active(self._e, ctypes.byref(n)))
+        return n.value
+
+    def close(self) -> None:
+        if getattr(self, "_e", None):
+            torch.cuda.current_stream(self.P.device).synchronize()
+            self.lib.hv_engine_destroy(self._e)
+            self._e = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Approx:
     """A built Hessian approximation (owns its device memory; see hv_approx_*)."""
 

@@ -80,6 +80,11 @@ class Server:
         vectors (< 2: no merging; hv_server_set_batching)."""
         check(self.lib.hv_server_set_batching(self._s, int(max_vectors)))
 
+    def set_engine(self, slots: int) -> None:
+        """Misfit requests join a per-problem lane of up to `slots` models at its next time step (0: misfits run
+        as calls; hv_server_set_engine)."""
+        check(self.lib.hv_server_set_engine(self._s, int(slots)))
+
     def poll(self, rid: int) -> int:
         st = ctypes.c_int()
         check(self.lib.hv_poll(self._s, int(rid), ctypes.byref(st)))

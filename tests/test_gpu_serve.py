@@ -8,6 +8,7 @@ import torch
 from oracle import oracle as O
 from paper_2507_10804_gb300 import synth
 from paper_2507_10804_gb300.hv import Problem
+from paper_2507_10804_gb300._lib import HV_REQ_QUEUED
 from paper_2507_10804_gb300.serve import Server
 from tests._helpers import f32, oracle_problem, rel
 
@@ -193,6 +194,7 @@ def test_queued_requests_on_one_model_run_as_one_call(problems):
     ref_m = P.misfit(m, d).cpu().numpy()
     for batching in (64, 0):
         S = Server(hbm_budget=2 << 30, max_concurrent=1)
+        S.set_engine(0)                                   # the misfit runs as a call, not in a lane
         S.set_batching(batching)
         blocker, _ = S.submit_hv(P2, t(w2.m), t(w2.v), ckpt=1)        # about 80k recomputed steps
         (r1, o1), (r2, o2) = (S.submit_hv(P, m, v, ckpt=5) for v in vs)
@@ -272,6 +274,7 @@ def test_queued_misfits_at_different_models_run_as_one_sweep(problems):
     ms = [t(np.minimum(w0.m * (1.0 + 0.03 * z[i] / np.abs(z[i]).max()), w0.vmax)) for i in range(6)]
     direct = [float(P0.misfit(m, dobs)) for m in ms]
     S = Server(hbm_budget=2 << 30, max_concurrent=1)
+    S.set_engine(0)                                       # misfits run as calls, not in a lane
     blocker, _ = S.submit_hv(P1, t(w1.m), t(w1.v), ckpt=1)
     subs = [S.submit_misfit(P0, m, dobs) for m in ms]
     assert S.wait(blocker, timeout=300) == 0
@@ -279,4 +282,30 @@ def test_queued_misfits_at_different_models_run_as_one_sweep(problems):
         assert S.wait(rid, timeout=300) == 0
         assert float(phi) == ref
     assert [S.info(rid)["batch"] for rid, _ in subs] == [6] * 6
+    S.close()
+
+
+def test_misfits_join_a_running_lane_at_the_next_time_step():
+    """Misfit lanes: misfits submitted while another misfit on the same problem is running join the
+    problem's lane at its next time step instead of waiting for that sweep to end (their runs overlap);
+    each phi is bitwise the direct misfit, and the lane's occupancy at each join is reported."""
+    import time
+    w, P = make(48, 64, 4, 3000, 17)                      # a 3000-step sweep: tens of milliseconds
+    dobs = t(synth.normal(221, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3)
+    z = synth.smoothed_normal_vectors(223, 3, w.nz, w.nx, 4.0)
+    ms = [t(np.minimum(w.m * (1.0 + 0.03 * z[i] / np.abs(z[i]).max()), w.vmax)) for i in range(3)]
+    direct = [float(P.misfit(m, dobs)) for m in ms]
+    S = Server(hbm_budget=2 << 30, max_concurrent=2)
+    a, pa = S.submit_misfit(P, ms[0], dobs)
+    t0 = time.perf_counter()
+    while S.poll(a) == HV_REQ_QUEUED and time.perf_counter() - t0 < 60:
+        time.sleep(1e-4)
+    b, pb = S.submit_misfit(P, ms[1], dobs)
+    c, pc = S.submit_misfit(P, ms[2], dobs)
+    for rid in (a, b, c):
+        assert S.wait(rid, timeout=300) == 0
+    ia, ib, ic = S.info(a), S.info(b), S.info(c)
+    assert ib["t_start"] < ia["t_done"] and ic["t_start"] < ia["t_done"], (ia, ib, ic)   # joined mid-sweep
+    assert (ia["batch"], ib["batch"], ic["batch"]) == (1, 2, 3)
+    assert [float(pa), float(pb), float(pc)] == direct
     S.close()
