@@ -724,6 +724,85 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def misfits_measure(dev, models=64, steps=5, warm=3, nz=128, nx=128, ns=8, nt=1000):
+    """Misfits of `models` proposals on the gpCN chains' problem (128x128 at 10 m + 20-cell sponge, 8 shots,
+    1000 steps): one forward sweep of all models (hv_misfit_models, CUDA events around `steps` sweeps), the forward
+    kernel's time per step with its algorithmic bytes (12 per shot-point plus one coefficient field per model),
+    the same misfits one call at a time, and the misfit engine with a new model joining whenever a slot frees."""
+    import torch
+
+    from paper_2507_10804_gb300 import synth
+    from paper_2507_10804_gb300.hv import MisfitEngine, Problem
+
+    h = 10.0
+    m0 = synth.gradient_grf_model(31, nz, nx, h)
+    vmax = float(m0.max())
+    acq = synth.surface_acquisition(nx, ns, nx // 3)
+    w = synth.Workload(name="chains", nz=nz, nx=nx, nb=20, h=h, nt=nt, dt=synth.cfl_dt(h, vmax), f0=10.0, t0=0.15,
+                       vmax=vmax, acq=acq, m=m0, v=np.zeros((1, nz, nx)))
+    P = Problem.from_workload(w, device=dev)
+    z = synth.smoothed_normal_vectors(37, models, nz, nx, 4.0)
+    z /= np.abs(z).max(axis=(1, 2), keepdims=True)
+    ms = torch.tensor(np.minimum(m0[None] * (1.0 + 0.03 * z), vmax), dtype=torch.float32, device=dev)
+    dobs = P.fwd_model(torch.tensor(m0, dtype=torch.float32, device=dev) * 1.02)
+    st = torch.cuda.current_stream(dev)
+    for _ in range(warm):
+        P.misfit_models(ms, dobs)
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        P.misfit_models(ms, dobs)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    sweep_ms = e0.elapsed_time(e1) / steps
+    P.profile(True)
+    P.profile_read()
+    P.misfit_models(ms, dobs)
+    torch.cuda.synchronize(dev)
+    prof = P.profile_read()
+    P.profile(False)
+    n_fwd, t_fwd = prof["fwd"]
+    step_us = t_fwd / max(n_fwd, 1) * 1e3
+    pts = (nz + 2 * 20) * (nx + 2 * 20)
+    alg = models * pts * (12.0 * ns + 4.0)
+    pk, src = peaks()
+    for _ in range(2):
+        P.misfit(ms[0], dobs)
+    torch.cuda.synchronize(dev)
+    e0.record(st)
+    for i in range(8):
+        P.misfit(ms[i], dobs)
+    e1.record(st)
+    torch.cuda.synchronize(dev)
+    one_ms = e0.elapsed_time(e1) / 8
+    # the engine: every slot refilled with the next model as soon as it is done (host-driven ticks)
+    E = MisfitEngine(P, models)
+    done, joined, t0 = 0, 0, None
+    target = 4 * models
+    while done < target:
+        while joined < target and E.active < models:
+            E.join(ms[joined % models], dobs)
+            joined += 1
+        fin = E.tick()
+        if fin and t0 is None:
+            torch.cuda.synchronize(dev)
+            t0, base = time.perf_counter(), done + len(fin)
+        done += len(fin)
+    torch.cuda.synchronize(dev)
+    eng_s = time.perf_counter() - t0
+    E.close()
+    return {"problem": f"{nz}x{nx} + 20 sponge, {ns} shots, {nt} steps", "models": models, "tiles": list(P.tiles()),
+            "sweep_ms": sweep_ms, "misfits_per_s": models / sweep_ms * 1e3,
+            "step_kernel_us": step_us, "algorithmic_bytes_per_step": alg,
+            "achieved_GBps": alg / step_us * 1e-3, "frac": alg / step_us * 1e-3 / pk["hbm_gbs"],
+            "peak_GBps": pk["hbm_gbs"], "peak_source": src,
+            "one_at_a_time": {"ms": one_ms, "misfits_per_s": 1e3 / one_ms},
+            "engine": {"misfits_per_s": (done - base) / eng_s, "completed": done - base,
+                       "what": "host-driven ticks from Python; a new model joins whenever a slot frees"},
+            "what": "CUDA events around the sweeps; kernel time per step from per-launch events in a separate sweep"}
+
+
 def serve_requests(n, seed=20250719, shots=None):
     """The request stream of the serving workload: clients 0-63 are MCMC chains,
     64-67 FWI runs; each request draws its kind (H v 35%, gradient 35%, misfit
@@ -1014,10 +1093,11 @@ def main():
     ap.add_argument("--concurrency", type=int, default=16, help="serving workload: concurrent requests")
     ap.add_argument("--rates", type=float, nargs="+", default=[0.25, 0.5, 0.8, 1.0, 2.0],
                     help="serving workload: arrival rates as fractions of the serial capacity")
-    ap.add_argument("--workload", choices=["paper", "batched", "serve", "quadratic"], default="paper",
+    ap.add_argument("--workload", choices=["paper", "batched", "serve", "quadratic", "misfits"], default="paper",
                     help="paper: 384x1152, 32 shots, 3000 steps, 1 vector (default); batched: the 64x64 model "
                          "with 64 vectors x 32 shots x 600 steps, every level stored, CUDA graph; quadratic: "
-                         "the quadratic test model's approximation, posterior and gpCN measurements alone")
+                         "the quadratic test model's approximation, posterior and gpCN measurements alone; "
+                         "misfits: 64 gpCN proposals' misfits in one sweep and through the misfit engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true", help="paper workload: skip the serving sample")
     ap.add_argument("--no-resident", action="store_true", help="batched workload: the tiled per-step kernels")
@@ -1038,6 +1118,21 @@ def main():
                           "higher_is_better": True, "dtype": "f32", "data": "synthetic",
                           "config": {"workload": f"quadratic model {res['grid'][0]}x{res['grid'][1]}, "
                                                  f"{res['chains']} chains"}, "quadratic_model": res}))
+        return
+    if args.workload == "misfits":
+        import torch
+        dev = torch.device("cuda", 0)
+        torch.cuda.set_device(dev)
+        res = misfits_measure(dev, steps=args.steps, warm=args.warmup)
+        print(json.dumps({"metric": "misfits/s of 64 gpCN proposals (section 2.3)", "value": res["misfits_per_s"],
+                          "unit": "misfits/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                          "ms_per_step": res["sweep_ms"], "higher_is_better": True, "dtype": "f32",
+                          "data": "synthetic", "config": {"workload": f"misfits of {res['models']} models, "
+                                                                      f"{res['problem']}"},
+                          "roofline": {"bound": "hbm", "kernel": "fwd (all models)", "achieved": res["achieved_GBps"],
+                                       "peak": res["peak_GBps"], "unit": "GB/s", "frac": res["frac"],
+                                       "traffic": None, "peak_source": res["peak_source"]},
+                          "misfits": res}))
         return
     if args.workload == "batched":
         CKPT = args.ckpt if args.ckpt is not None else -1

@@ -4,6 +4,8 @@
 // plus the forward field; section 2.1, eq. (grad): misfit gradient).
 #include "hv_internal.h"
 
+#include <atomic>
+
 #include <functional>
 
 #include <algorithm>
@@ -689,7 +691,9 @@ extern "C" int hv_create(const hv_grid *g, const hv_acq *a, hv_handle **out)
     if (!out) return hvi::fail(HV_EINVAL, "null output handle pointer");
     *out = nullptr;
     HV_RT(validate_create(g, a));
+    static std::atomic<unsigned long long> next_serial{1};
     hv_handle *h = new hv_handle();
+    h->serial = next_serial++;
     h->nz = g->nz; h->nx = g->nx; h->nb = g->nb; h->h = g->h;
     h->NZ = g->nz + 2 * g->nb;
     h->NX = g->nx + 2 * g->nb;

@@ -69,6 +69,7 @@ struct RecTiles {
 }  // namespace hvi
 
 struct hv_handle {
+    unsigned long long serial = 0;   // unique per hv_create in the process (a later handle may reuse the address)
     int device = 0;
     int nz = 0, nx = 0, nb = 0, NZ = 0, NX = 0;
     int P = 0, rows = 0;

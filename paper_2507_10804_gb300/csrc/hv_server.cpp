@@ -97,6 +97,7 @@ struct Req {
 constexpr int kLookahead = 8;
 struct Lane {
     hv_engine *e = nullptr;
+    unsigned long long serial = 0;              // the problem's hv_create serial
     int slots = 0;
     size_t off = 0;
     cudaStream_t st = nullptr;
@@ -393,6 +394,20 @@ cudaEvent_t take_event(hv_server *S)
 Lane *lane_for(hv_server *S, hv_handle *p)
 {
     auto it = S->lanes.find(p);
+    if (it != S->lanes.end() && it->second.serial != p->serial) {
+        // The lane of a destroyed problem whose address a new problem reuses: it never
+        // runs for the new one; released here once idle (requests of a destroyed problem
+        // cannot be pending unless the caller broke the contract).
+        Lane &L = it->second;
+        if (L.busy != 0 || !L.finishing.empty()) return nullptr;
+        cudaStreamSynchronize(L.st);
+        for (cudaEvent_t e : L.ticks) S->ev_pool.push_back(e);
+        hv_engine_destroy(L.e);
+        cudaStreamDestroy(L.st);
+        S->arena->release(L.off);
+        S->lanes.erase(it);
+        it = S->lanes.end();
+    }
     if (it != S->lanes.end()) return it->second.failed == HV_OK ? &it->second : nullptr;
     int slots = S->engine_slots;
     size_t bytes = 0;
@@ -410,6 +425,7 @@ Lane *lane_for(hv_server *S, hv_handle *p)
         return nullptr;
     }
     L.slots = slots;
+    L.serial = p->serial;
     L.slot_req.assign(slots, 0);
     return &(S->lanes[p] = std::move(L));
 }
