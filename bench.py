@@ -1075,6 +1075,8 @@ def run_serve(args):
                    "requests": n, "concurrency": args.concurrency, "snapshots_per_shot": 30},
         "serve": res,
     }
+    # the first run in a process carries one-time costs (module loading, plans, graph capture) into its latencies
+    line["serve"]["gpcn_request_source_first_run"] = serve_chains(dev, args.concurrency)
     line["serve"]["gpcn_request_source"] = serve_chains(dev, args.concurrency)
     print(json.dumps(line))
 
