@@ -67,3 +67,16 @@ def test_full_engine_refuses_and_empty_tick_launches_nothing(ragged):
         done += E.tick()
     assert sorted(done) == [0, 1]
     E.close()
+
+
+def test_one_step_sweeps_and_a_single_slot():
+    """nt = 1: a slot joins and finishes in the same tick; one slot reused three times in a row."""
+    w, P = make(32, 40, 3, 1, 91)
+    dobs = t(synth.normal(93, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr))
+    ms = proposals(w, 3, 95)
+    E = MisfitEngine(P, 1)
+    for i in range(3):
+        slot, phi = E.join(t(ms[i]), dobs)
+        assert slot == 0 and E.tick() == [0] and E.active == 0
+        assert float(phi) == float(P.misfit(t(ms[i]), dobs)), i
+    E.close()
