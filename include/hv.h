@@ -195,6 +195,39 @@ int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done);
 int hv_engine_active(const hv_engine *e, int *active);
 int hv_engine_destroy(hv_engine *e);
 
+/* The engine's device-resident request loop: requests are posted into device
+ * memory and a loop running on the GPU admits them at its next time step,
+ * advances every occupied slot and reports each finished misfit to the host,
+ * with no host launch per step.  The loop is one CUDA graph launch: a
+ * conditional while node whose body is one iteration (admission, the forward
+ * step of every occupied slot, the misfits of the slots that took their last
+ * step, the loop condition).
+ *  - hv_engine_post takes a free slot (HV_EBUSY when none is), enqueues on
+ *    `stream` the model's preparation, the zeroing of the slot's fields and
+ *    the post itself (the request's data and phi pointers and a sequence
+ *    number written to device memory after the preparation), and returns the
+ *    slot.  Any stream may be used, also while the loop runs on another.
+ *  - hv_engine_serve launches the loop on `stream` unless it is running.  One
+ *    launch ends after 2000 iterations with no occupied slot and no waiting
+ *    request, after 2^20 iterations, or at the end of the iteration in which
+ *    hv_engine_stop's request is seen; occupied slots keep their state across
+ *    launches.  A post that lands as a launch ends waits for the next
+ *    hv_engine_serve: call it again when hv_engine_poll reports the loop not
+ *    running while posted requests are not done.
+ *  - hv_engine_poll reports, in done[0 .. *n_done) (HOST array of `slots`
+ *    ints), the slots whose misfit has been written to its phi (bitwise what
+ *    hv_misfit gives) since the last poll, frees them, and sets *running
+ *    (may be NULL) to whether the loop is running.
+ * The first post switches the engine to this mode: hv_engine_join and
+ * hv_engine_tick are refused from then on (and posting while joined slots
+ * run is refused).  hv_engine_destroy ends a running loop (a stop request and
+ * a wait for its current iteration) before it frees the engine.  Host memory:
+ * a small pinned, mapped mailbox per engine (allocated at the first post). */
+int hv_engine_post(hv_engine *e, const float *m, const float *d_obs, double *phi, void *stream, int *slot);
+int hv_engine_serve(hv_engine *e, void *stream);
+int hv_engine_poll(hv_engine *e, int *done, int *n_done, int *running);
+int hv_engine_stop(hv_engine *e);
+
 /* Gauss-Newton Hessian apply: Hv[j] = F^T F v[j] / sigma^2 for j < k; v and Hv
  * are [k][nz][nx].  Images accumulate in FP64 and are summed over shots in a
  * fixed order, so results do not depend on batching. */

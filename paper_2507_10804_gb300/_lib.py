@@ -95,6 +95,10 @@ _SIGS = {
     "hv_engine_tick": ([c_void_p, c_void_p, ip, ip], c_int),
     "hv_engine_active": ([c_void_p, ip], c_int),
     "hv_engine_destroy": ([c_void_p], c_int),
+    "hv_engine_post": ([c_void_p, fp, fp, fp, c_void_p, ip], c_int),
+    "hv_engine_serve": ([c_void_p, c_void_p], c_int),
+    "hv_engine_poll": ([c_void_p, ip, ip, ip], c_int),
+    "hv_engine_stop": ([c_void_p], c_int),
     "hv_server_set_engine": ([c_void_p, c_int], c_int),
     "hv_server_create": ([c_size_t, c_int, ctypes.POINTER(c_void_p)], c_int),
     "hv_server_destroy": ([c_void_p, c_double], c_int),

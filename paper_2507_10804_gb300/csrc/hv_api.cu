@@ -926,6 +926,22 @@ struct hv_engine {
     int tick = 0;                      // launches since the last rebase
     int active = 0;
     bool dirty = true;                 // join differs from join_dev
+    // The device-resident loop (hv_engine_post / serve / poll): its tables in
+    // the workspace after join_dev, host-mapped mailboxes, its graph.
+    bool loop = false;                 // a request was posted: join and tick are refused from then on
+    int *post = nullptr, *seen = nullptr, *step = nullptr, *fin = nullptr, *ctl = nullptr;
+    const float **dobs_tbl = nullptr;
+    double **phi_tbl = nullptr;
+    int *hmap = nullptr;               // pinned, mapped: ack[slots], done[slots], stop
+    int *hmap_dev = nullptr;
+    cudaEvent_t init_done = nullptr;   // the tables' initialisation (first post)
+    cudaEvent_t ran = nullptr;         // recorded after the last launch of the loop
+    bool launched = false;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int seq = 0;
+    std::vector<int> slot_seq;         // sequence number posted into each slot (0: free)
 };
 
 namespace {
@@ -933,7 +949,20 @@ namespace {
 constexpr int kFreeSlot = 1 << 30;     // later than any tick: a free slot takes no step
 constexpr int kRebaseTick = 1 << 28;
 
-size_t engine_bytes(const Layout &L, int slots) { return L.total + align256((size_t)slots * sizeof(int)); }
+constexpr int kLoopBlocks = 1024;       // residual blocks of one misfit: kResidualBlocks, as hv_misfit
+constexpr int kLoopMaxIter = 1 << 20;   // iterations of one launch of the loop, at most
+constexpr int kLoopIdle = 2000;         // iterations with nothing to do before the loop ends
+
+size_t loop_bytes(int slots)
+{
+    const size_t i = align256((size_t)slots * sizeof(int));
+    return 3 * i + align256((size_t)(slots + 1) * sizeof(int)) + 256 + 2 * align256((size_t)slots * sizeof(void *));
+}
+
+size_t engine_bytes(const Layout &L, int slots)
+{
+    return L.total + align256((size_t)slots * sizeof(int)) + loop_bytes(slots);
+}
 
 }  // namespace
 
@@ -961,6 +990,19 @@ extern "C" int hv_engine_create(hv_handle *h, int slots, void *ws, size_t ws_byt
     e->ws = (char *)ws;
     e->L = L;
     e->join_dev = reinterpret_cast<int *>(e->ws + L.total);
+    {
+        char *q = e->ws + L.total + align256((size_t)slots * sizeof(int));
+        const size_t i = align256((size_t)slots * sizeof(int));
+        e->post = reinterpret_cast<int *>(q);
+        e->seen = reinterpret_cast<int *>(q + i);
+        e->step = reinterpret_cast<int *>(q + 2 * i);
+        e->fin = reinterpret_cast<int *>(q + 3 * i);
+        e->ctl = reinterpret_cast<int *>(q + 3 * i + align256((size_t)(slots + 1) * sizeof(int)));
+        e->dobs_tbl = reinterpret_cast<const float **>(q + 3 * i + align256((size_t)(slots + 1) * sizeof(int)) + 256);
+        e->phi_tbl = reinterpret_cast<double **>(reinterpret_cast<char *>(e->dobs_tbl) +
+                                                 align256((size_t)slots * sizeof(void *)));
+    }
+    e->slot_seq.assign(slots, 0);
     e->join.assign(slots, kFreeSlot);
     e->dobs.assign(slots, nullptr);
     e->phi.assign(slots, nullptr);
@@ -975,6 +1017,17 @@ extern "C" int hv_engine_create(hv_handle *h, int slots, void *ws, size_t ws_byt
 
 extern "C" int hv_engine_destroy(hv_engine *e)
 {
+    if (!e) return HV_OK;
+    if (e->launched && cudaEventQuery(e->ran) == cudaErrorNotReady) {   // end the loop after its iteration
+        reinterpret_cast<volatile int *>(e->hmap)[2 * e->slots] = 1;
+        cudaEventSynchronize(e->ran);
+    }
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    if (e->cap) cudaStreamDestroy(e->cap);
+    if (e->ran) cudaEventDestroy(e->ran);
+    if (e->init_done) cudaEventDestroy(e->init_done);
+    if (e->hmap) cudaFreeHost(e->hmap);
     delete e;
     return HV_OK;
 }
@@ -983,6 +1036,7 @@ extern "C" int hv_engine_join(hv_engine *e, const float *m, const float *d_obs, 
 {
     if (!e || !m || !d_obs || !phi || !slot) return hvi::fail(HV_EINVAL, "hv_engine_join: null argument");
     *slot = -1;
+    if (e->loop) return hvi::fail(HV_EINVAL, "hv_engine_join: the engine serves posted requests (hv_engine_post)");
     int j = 0;
     while (j < e->slots && e->join[j] != kFreeSlot) ++j;
     if (j == e->slots) return hvi::fail(HV_EBUSY, "hv_engine_join: all %d slots are taken", e->slots);
@@ -1009,6 +1063,7 @@ extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done
 {
     if (!e || !done || !n_done) return hvi::fail(HV_EINVAL, "hv_engine_tick: null argument");
     *n_done = 0;
+    if (e->loop) return hvi::fail(HV_EINVAL, "hv_engine_tick: the engine serves posted requests (hv_engine_post)");
     if (e->active == 0) return HV_OK;
     hv_handle *h = e->h;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1054,6 +1109,153 @@ extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done
         done[(*n_done)++] = j;
     }
     ++e->tick;
+    return HV_OK;
+}
+
+namespace {
+
+// The loop's graph: a conditional while node whose body is one iteration
+// (admission, the step of every occupied slot, the finishing slots' misfits,
+// the loop condition), captured into the body graph.
+int build_loop_graph(hv_engine *e)
+{
+    hv_handle *h = e->h;
+    if (!e->cap) HV_CK(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
+    HV_CK(cudaGraphCreate(&e->graph, 0));
+    cudaGraphConditionalHandle hc;
+    HV_CK(cudaGraphConditionalHandleCreate(&hc, e->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    HV_CK(cudaGraphAddNode(&node, e->graph, nullptr, nullptr, 0, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    hvk::LoopParams lp{};
+    lp.slots = e->slots;
+    lp.nt = h->nt;
+    lp.nblk = kLoopBlocks;
+    lp.ndata = (size_t)h->ns * h->nt * h->nr;
+    lp.scale = 0.5 / (h->sigma * h->sigma);
+    lp.max_iter = kLoopMaxIter;
+    lp.idle_max = kLoopIdle;
+    lp.post = e->post;
+    lp.seen = e->seen;
+    lp.step = e->step;
+    lp.join = e->join_dev;
+    lp.fin = e->fin;
+    lp.ctl = e->ctl;
+    lp.dobs = e->dobs_tbl;
+    lp.phi = e->phi_tbl;
+    lp.data = reinterpret_cast<float *>(e->ws + e->L.dd);
+    lp.part = reinterpret_cast<double *>(e->ws + e->L.part);
+    lp.ack = e->hmap_dev;
+    lp.done = e->hmap_dev + e->slots;
+    lp.stop = e->hmap_dev + 2 * e->slots;
+    lp.cond = hc;
+    HV_CK(cudaStreamBeginCaptureToGraph(e->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    int rc = hvk::launch_loop_control(lp, e->cap);
+    if (rc == HV_OK) {
+        hvk::FwdLaunch a{};
+        a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
+        a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
+        a.C = reinterpret_cast<const float *>(e->ws + e->L.C);
+        a.d_u = lp.data;
+        a.n = 0;                       // k_fwd's step of slot j: 0 - join[j] = step[j]
+        a.models = e->slots;
+        a.slot_join = e->join_dev;
+        a.plain = true;                // the step reads the tables k_loop_control has just written
+        const int cfg = h->cfg[1];
+        rc = hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
+    }
+    if (rc == HV_OK) rc = hvk::launch_loop_finish(lp, e->cap);
+    if (rc == HV_OK) rc = hvk::launch_loop_cond(lp, e->cap);
+    cudaGraph_t out = nullptr;
+    cudaError_t ce = cudaStreamEndCapture(e->cap, &out);
+    if (rc != HV_OK) return rc;
+    if (ce != cudaSuccess) return hvi::fail(HV_ECUDA, "misfit loop capture: %s", cudaGetErrorString(ce));
+    HV_CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
+    return HV_OK;
+}
+
+}  // namespace
+
+extern "C" int hv_engine_post(hv_engine *e, const float *m, const float *d_obs, double *phi, void *stream, int *slot)
+{
+    if (!e || !m || !d_obs || !phi || !slot) return hvi::fail(HV_EINVAL, "hv_engine_post: null argument");
+    *slot = -1;
+    if (!e->loop && e->active > 0)
+        return hvi::fail(HV_EINVAL, "hv_engine_post: slots joined with hv_engine_join are still running");
+    hv_handle *h = e->h;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int S = e->slots;
+    if (!e->loop) {                                // first post: mailboxes, tables, events
+        HV_CK(cudaHostAlloc(reinterpret_cast<void **>(&e->hmap), (2 * (size_t)S + 1) * sizeof(int), cudaHostAllocMapped));
+        memset(e->hmap, 0, (2 * (size_t)S + 1) * sizeof(int));
+        HV_CK(cudaHostGetDevicePointer(reinterpret_cast<void **>(&e->hmap_dev), e->hmap, 0));
+        HV_CK(cudaEventCreateWithFlags(&e->init_done, cudaEventDisableTiming));
+        HV_CK(cudaEventCreateWithFlags(&e->ran, cudaEventDisableTiming));
+        HV_CK(cudaMemsetAsync(e->post, 0, (size_t)S * sizeof(int), st));
+        HV_CK(cudaMemsetAsync(e->seen, 0, (size_t)S * sizeof(int), st));
+        HV_CK(cudaMemsetAsync(e->step, 0xff, (size_t)S * sizeof(int), st));   // -1: free
+        HV_CK(cudaMemsetAsync(e->fin, 0, (size_t)(S + 1) * sizeof(int), st));
+        HV_CK(cudaMemsetAsync(e->ctl, 0, 4 * sizeof(int), st));
+        HV_CK(cudaEventRecord(e->init_done, st));
+        e->loop = true;
+    }
+    int j = 0;
+    while (j < S && e->slot_seq[j] != 0) ++j;
+    if (j == S) return hvi::fail(HV_EBUSY, "hv_engine_post: all %d slots are taken", S);
+    const size_t fbytes = h->fsize * sizeof(float);
+    if (++e->seq <= 0) e->seq = 1;
+    {
+        ProfScope ps(h, st, HV_K_OTHER);
+        HV_RT(hvk::launch_prep(h, m, nullptr, 0, reinterpret_cast<float *>(e->ws + e->L.C) + (size_t)j * h->fsize,
+                               nullptr, st));
+        HV_CK(cudaMemsetAsync(e->ws + e->L.work + (size_t)3 * j * h->ns * fbytes, 0, (size_t)3 * h->ns * fbytes, st));
+        HV_RT(hvk::launch_loop_post(e->post, e->dobs_tbl, e->phi_tbl, j, e->seq, d_obs, phi, st));
+    }
+    e->slot_seq[j] = e->seq;
+    *slot = j;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_serve(hv_engine *e, void *stream)
+{
+    if (!e) return hvi::fail(HV_EINVAL, "hv_engine_serve: null engine");
+    if (!e->loop) return hvi::fail(HV_EINVAL, "hv_engine_serve: nothing was posted to this engine");
+    if (e->launched && cudaEventQuery(e->ran) == cudaErrorNotReady) return HV_OK;   // running
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!e->exec) HV_RT(build_loop_graph(e));
+    reinterpret_cast<volatile int *>(e->hmap)[2 * e->slots] = 0;                   // no stop request
+    HV_CK(cudaStreamWaitEvent(st, e->init_done, 0));
+    HV_CK(cudaGraphLaunch(e->exec, st));
+    HV_CK(cudaEventRecord(e->ran, st));
+    e->launched = true;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_poll(hv_engine *e, int *done, int *n_done, int *running)
+{
+    if (!e || !done || !n_done) return hvi::fail(HV_EINVAL, "hv_engine_poll: null argument");
+    *n_done = 0;
+    if (e->loop) {
+        const volatile int *dn = e->hmap + e->slots;
+        for (int j = 0; j < e->slots; ++j)
+            if (e->slot_seq[j] != 0 && dn[j] == e->slot_seq[j]) {
+                done[(*n_done)++] = j;
+                e->slot_seq[j] = 0;
+            }
+    }
+    if (running) *running = e->launched && cudaEventQuery(e->ran) == cudaErrorNotReady;
+    return HV_OK;
+}
+
+extern "C" int hv_engine_stop(hv_engine *e)
+{
+    if (!e) return hvi::fail(HV_EINVAL, "hv_engine_stop: null engine");
+    if (e->hmap) reinterpret_cast<volatile int *>(e->hmap)[2 * e->slots] = 1;
     return HV_OK;
 }
 

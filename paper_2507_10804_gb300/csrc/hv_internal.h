@@ -167,6 +167,7 @@ struct FwdLaunch {
     // or nullptr.  With them, n counts launches and u_cur is the first field of
     // the models' rings (model i: 3 ns fields from u_cur + 3 ns i fields).
     const int *slot_join;
+    bool plain;                    // launch without programmatic dependent launch whatever the handle's mode
     StepDeps deps;
 };
 int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const FwdLaunch &a,
@@ -359,6 +360,39 @@ int launch_fold_ext(const hv_handle *h, const double *ext, int k, float *out32, 
 int launch_residual(const hv_handle *h, const float *d, const float *dobs, float *r, double *partials,
                     int nblocks, cudaStream_t st);
 int launch_reduce_phi(const double *partials, int nblocks, double scale, double *phi, cudaStream_t st);
+
+// The device-resident misfit loop (hv_engine_serve and the kernels of its
+// graph body, hv_kernels.cu).  One iteration: k_loop_control admits the
+// requests posted into free slots and advances every occupied slot's step,
+// the forward step kernel advances all occupied slots, k_loop_finish and
+// k_loop_reduce form the misfit of every slot that took its last step, and
+// k_loop_cond decides whether the loop goes on.
+constexpr int kLoopFreeSlot = 1 << 30;    // a slot_join entry that makes k_fwd skip the slot
+struct LoopParams {
+    int slots, nt, nblk;
+    size_t ndata;                  // data floats per slot (ns nt nr)
+    double scale;                  // 1 / (2 sigma^2)
+    int max_iter, idle_max;        // bounds of one launch of the loop
+    int *post;                     // [slots] sequence number of the last request posted into the slot
+    int *seen;                     // [slots] sequence number of the last request admitted
+    int *step;                     // [slots] step the slot takes in this iteration (-1: free)
+    int *join;                     // [slots] k_fwd's slot_join table: -step, or kLoopFreeSlot
+    int *fin;                      // [slots + 1] the slots taking their last step in this iteration, count last
+    int *ctl;                      // [4] iteration, idle iterations, occupied slots, exit reason
+    const float *const *dobs;      // [slots] observed data of each slot's request
+    double *const *phi;            // [slots] where each slot's misfit goes
+    float *data;                   // [slots][ndata]
+    double *part;                  // [slots][nblk]
+    volatile int *ack;             // [slots] host-mapped: sequence number admitted
+    volatile int *done;            // [slots] host-mapped: sequence number whose misfit is written
+    volatile int *stop;            // host-mapped: nonzero ends the loop at the end of the iteration
+    cudaGraphConditionalHandle cond;
+};
+int launch_loop_control(const LoopParams &p, cudaStream_t st);
+int launch_loop_finish(const LoopParams &p, cudaStream_t st);
+int launch_loop_cond(const LoopParams &p, cudaStream_t st);
+int launch_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq, const float *dobs,
+                     double *phi, cudaStream_t st);
 int launch_copy_wavefield(const hv_handle *h, const float *u, float *out, cudaStream_t st);
 int launch_zero_ghosts(const hv_handle *h, float *f, long long nfields, cudaStream_t st);
 int launch_setup(hv_handle *h, cudaStream_t st);

@@ -111,13 +111,16 @@ __global__ void k_fold_ext(const double *__restrict__ ext, int nz, int nx, int n
     if (out64) out64[o] = acc;
 }
 
-// r = d - dobs and per-block FP64 partial sums of r^2 (fixed assignment, fixed tree).
-__global__ void k_residual(const float *d, const float *__restrict__ dobs, float *r,
-                           size_t n, double *__restrict__ partials)
+// Block `blk` of `nblk` of the residual r = d - d_obs and its FP64 sum of
+// squares: a grid stride over n, then a fixed warp-shuffle tree (fixed
+// assignment, fixed tree: the value depends only on n, nblk and the block
+// size, never on which kernel runs the block).
+__device__ __forceinline__ void residual_block(const float *d, const float *__restrict__ dobs, float *r, size_t n,
+                                               double *__restrict__ partials, int blk, int nblk)
 {
     __shared__ double sw[32];
     double acc = 0.0;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    for (size_t i = (size_t)blk * blockDim.x + threadIdx.x; i < n; i += (size_t)nblk * blockDim.x) {
         double e = (double)d[i] - (double)dobs[i];
         r[i] = (float)e;
         acc += e * e;
@@ -130,11 +133,12 @@ __global__ void k_residual(const float *d, const float *__restrict__ dobs, float
         double v = (threadIdx.x < (blockDim.x >> 5)) ? sw[threadIdx.x] : 0.0;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (threadIdx.x == 0) partials[blockIdx.x] = v;
+        if (threadIdx.x == 0) partials[blk] = v;
     }
 }
 
-__global__ void k_reduce_phi(const double *__restrict__ partials, int nb, double scale, double *phi)
+// phi = scale * (the nb partials summed by one block in a fixed tree).
+__device__ __forceinline__ void reduce_partials(const double *__restrict__ partials, int nb, double scale, double *phi)
 {
     __shared__ double sw[32];
     double acc = 0.0;
@@ -149,6 +153,120 @@ __global__ void k_reduce_phi(const double *__restrict__ partials, int nb, double
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (threadIdx.x == 0) *phi = scale * v;
     }
+}
+
+// r = d - dobs and per-block FP64 partial sums of r^2.
+__global__ void k_residual(const float *d, const float *__restrict__ dobs, float *r, size_t n,
+                           double *__restrict__ partials)
+{
+    residual_block(d, dobs, r, n, partials, blockIdx.x, gridDim.x);
+}
+
+
+__global__ void k_reduce_phi(const double *__restrict__ partials, int nb, double scale, double *phi)
+{
+    reduce_partials(partials, nb, scale, phi);
+}
+
+// ---- the device-resident misfit loop (one iteration of its graph body per time step)
+
+// Admission and step bookkeeping of every slot (one block): a slot that took its
+// last step in the previous iteration is free again; a free slot whose mailbox
+// holds a new sequence number is admitted at step 0 (its model and fields were
+// prepared before the number was posted); the tables of this iteration's step
+// are written for the stencil kernel and the finishing stages.
+__global__ void k_loop_control(const LoopParams p)
+{
+    __shared__ int occ;
+    if (threadIdx.x == 0) occ = 0;
+    __syncthreads();
+    int local = 0;
+    for (int j = threadIdx.x; j < p.slots; j += blockDim.x) {
+        int st = p.step[j];
+        if (st >= 0 && ++st >= p.nt) st = -1;
+        const int posted = *reinterpret_cast<volatile const int *>(p.post + j);
+        if (st < 0 && posted != p.seen[j]) {
+            __threadfence();                   // the request's prepared fields, written before the post
+            st = 0;
+            p.seen[j] = posted;
+            p.ack[j] = posted;
+        }
+        p.step[j] = st;
+        p.join[j] = st >= 0 ? -st : kLoopFreeSlot;
+        local += st >= 0;
+    }
+    atomicAdd(&occ, local);
+    __syncthreads();
+    // the finishing slots in slot order (one thread: the list is short and its order fixed)
+    if (threadIdx.x == 0) {
+        int nf = 0;
+        for (int j = 0; j < p.slots; ++j)
+            if (p.step[j] == p.nt - 1) p.fin[nf++] = j;
+        p.fin[p.slots] = nf;
+        p.ctl[2] = occ;
+    }
+}
+
+// Residual blocks of the finishing slots: block b of every such slot, in the
+// assignment k_residual uses for a grid of nblk blocks.
+__global__ void k_loop_finish(const LoopParams p)
+{
+    const int nf = p.fin[p.slots];
+    for (int f = 0; f < nf; ++f) {
+        const int j = p.fin[f];
+        float *dj = p.data + (size_t)j * p.ndata;
+        residual_block(dj, p.dobs[j], dj, p.ndata, p.part + (size_t)j * p.nblk, blockIdx.x, p.nblk);
+        __syncthreads();                       // the block's shared scratch is reused by the next slot
+    }
+}
+
+// The finishing slots' misfits (one block of 1024 threads, the tree of
+// k_reduce_phi), each published to the host after its value.
+__global__ void k_loop_reduce(const LoopParams p)
+{
+    const int nf = p.fin[p.slots];
+    for (int f = 0; f < nf; ++f) {
+        const int j = p.fin[f];
+        reduce_partials(p.part + (size_t)j * p.nblk, p.nblk, p.scale, p.phi[j]);
+        if (threadIdx.x == 0) {
+            __threadfence_system();
+            p.done[j] = p.seen[j];
+        }
+        __syncthreads();
+    }
+}
+
+// Whether the loop runs another iteration: not after a stop request, after
+// max_iter iterations of this launch, or after idle_max iterations with no
+// occupied slot and no request waiting (one warp).
+__global__ void k_loop_cond(const LoopParams p)
+{
+    bool pending = false;
+    for (int j = threadIdx.x; j < p.slots; j += 32)
+        pending |= *reinterpret_cast<volatile const int *>(p.post + j) != p.seen[j];
+    pending = __any_sync(0xffffffffu, pending);
+    if (threadIdx.x == 0) {
+        const int it = p.ctl[0] + 1;
+        const int idle = (p.ctl[2] > 0 || pending) ? 0 : p.ctl[1] + 1;
+        const bool stop = *p.stop != 0;
+        const bool go = !stop && it < p.max_iter && idle < p.idle_max;
+        p.ctl[0] = go ? it : 0;
+        p.ctl[1] = go ? idle : 0;
+        p.ctl[3] = go ? 0 : (stop ? 1 : (it >= p.max_iter ? 2 : 3));
+        cudaGraphSetConditional(p.cond, go ? 1u : 0u);
+    }
+}
+
+// Posts request `seq` into slot `slot` with its data and misfit pointers; the
+// writes of the work before it on the stream (the slot's model preparation and
+// field zeroing) are complete, and the post is written last.
+__global__ void k_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq,
+                            const float *dobs, double *phi)
+{
+    dobs_tbl[slot] = dobs;
+    phi_tbl[slot] = phi;
+    __threadfence();
+    *reinterpret_cast<volatile int *>(post + slot) = seq;
 }
 
 // Zero the ghost band (the Dirichlet zeros every stencil read relies on) of
@@ -279,6 +397,33 @@ int launch_reduce_phi(const double *partials, int nblocks, double scale, double 
 {
     k_reduce_phi<<<1, 1024, 0, st>>>(partials, nblocks, scale, phi);
     return cuda_check("k_reduce_phi launch");
+}
+
+int launch_loop_control(const LoopParams &p, cudaStream_t st)
+{
+    k_loop_control<<<1, 256, 0, st>>>(p);
+    return cuda_check("k_loop_control launch");
+}
+
+int launch_loop_finish(const LoopParams &p, cudaStream_t st)
+{
+    k_loop_finish<<<p.nblk, 256, 0, st>>>(p);   // 256 threads and nblk blocks: the misfit's fixed tree
+    HV_RT_INTERNAL(cuda_check("k_loop_finish launch"));
+    k_loop_reduce<<<1, 1024, 0, st>>>(p);
+    return cuda_check("k_loop_reduce launch");
+}
+
+int launch_loop_cond(const LoopParams &p, cudaStream_t st)
+{
+    k_loop_cond<<<1, 32, 0, st>>>(p);
+    return cuda_check("k_loop_cond launch");
+}
+
+int launch_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq, const float *dobs,
+                     double *phi, cudaStream_t st)
+{
+    k_loop_post<<<1, 1, 0, st>>>(post, dobs_tbl, phi_tbl, slot, seq, dobs, phi);
+    return cuda_check("k_loop_post launch");
 }
 
 int launch_zero_ghosts(const hv_handle *h, float *f, long long nfields, cudaStream_t st)

@@ -1660,7 +1660,8 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
             return launch_step(k_fwd<C, true>, grid, C::NT, FwdSmem<C, true>::BYTES, st, pdl(h), p, "k_fwd launch");
         }
         HV_RT_INTERNAL(ensure_smem(1 * kTileMenu + cfg, h->device, k_fwd<C, false>, FwdSmem<C, false>::BYTES));
-        return launch_step(k_fwd<C, false>, grid, C::NT, FwdSmem<C, false>::BYTES, st, pdl(h), p, "k_fwd launch");
+        return launch_step(k_fwd<C, false>, grid, C::NT, FwdSmem<C, false>::BYTES, st, pdl(h) && !a.plain, p,
+                           "k_fwd launch");
     });
 }
 

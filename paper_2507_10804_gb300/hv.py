@@ -432,6 +432,39 @@ class MisfitEngine:
         check(self.lib.hv_engine_active(self._e, ctypes.byref(n)))
         return n.value
 
+    # ---- the device-resident loop (hv_engine_post / serve / poll / stop)
+    def post(self, m: torch.Tensor, d_obs: torch.Tensor, stream=None):
+        """(slot, phi): the request is prepared and posted on `stream` (default: the current stream); the
+        running loop admits it at its next time step.  phi is written once poll() reports the slot."""
+        P = self.P
+        pm = P._m(m)
+        pd = _dev(d_obs, torch.float32, (P.ns, P.nt, P.nr), "d_obs", P.device)
+        phi = torch.empty((), dtype=torch.float64, device=P.device)
+        s = stream if stream is not None else torch.cuda.current_stream(P.device)
+        slot = ctypes.c_int()
+        check(self.lib.hv_engine_post(self._e, pm, pd, phi.data_ptr(), ctypes.c_void_p(s.cuda_stream),
+                                      ctypes.byref(slot)))
+        self._held[slot.value] = (m, d_obs, phi)
+        return slot.value, phi
+
+    def serve(self, stream) -> None:
+        """Launch the loop on `stream` (a torch.cuda.Stream) unless it is running."""
+        check(self.lib.hv_engine_serve(self._e, ctypes.c_void_p(stream.cuda_stream)))
+
+    def poll(self):
+        """(done slots, running): the slots whose misfit is written since the last poll, and whether the loop
+        is running."""
+        n, run = ctypes.c_int(), ctypes.c_int()
+        check(self.lib.hv_engine_poll(self._e, self._done, ctypes.byref(n), ctypes.byref(run)))
+        done = [self._done[i] for i in range(n.value)]
+        for j in done:
+            self._held.pop(j, None)
+        return done, bool(run.value)
+
+    def stop(self) -> None:
+        """Ask the running loop to end after its current iteration."""
+        check(self.lib.hv_engine_stop(self._e))
+
     def close(self) -> None:
         if getattr(self, "_e", None):
             torch.cuda.current_stream(self.P.device).synchronize()

@@ -80,3 +80,87 @@ def test_one_step_sweeps_and_a_single_slot():
         assert slot == 0 and E.tick() == [0] and E.active == 0
         assert float(phi) == float(P.misfit(t(ms[i]), dobs)), i
     E.close()
+
+
+def _wait(cond, limit=120.0):
+    import time
+    t0 = time.perf_counter()
+    while not cond():
+        assert time.perf_counter() - t0 < limit, "timed out"
+        time.sleep(2e-4)
+
+
+def test_device_loop_admits_posts_while_it_runs(ragged):
+    """The device-resident loop: requests posted from another stream join at the loop's next time step
+    (here into slots freed while the loop runs); each misfit is bitwise hv_misfit's; the loop ends by itself
+    once idle and is relaunched for later posts."""
+    w, P, dobs = ragged
+    ms = [t(m) for m in proposals(w, 6, 101)]
+    D = t(dobs)
+    direct = [float(P.misfit(m, D)) for m in ms]
+    torch.cuda.synchronize()
+    E = MisfitEngine(P, 3)
+    loop_st, post_st = torch.cuda.Stream(), torch.cuda.Stream()
+    slot_of, phis, finished = {}, {}, []
+    pending = list(range(5))
+
+    def post_next():
+        i = pending.pop(0)
+        s, phi = E.post(ms[i], D, stream=post_st)
+        slot_of[s] = i
+        phis[i] = phi
+
+    post_next()
+    post_next()
+    E.serve(loop_st)
+
+    def step():
+        done, running = E.poll()
+        finished.extend(slot_of.pop(s) for s in done)
+        while pending and len(slot_of) < 3:
+            post_next()
+        if slot_of and not running:
+            E.serve(loop_st)
+        return len(finished) == 5
+
+    _wait(step)
+    assert sorted(finished) == list(range(5))
+    assert [float(phis[i]) for i in range(5)] == direct[:5]
+    _wait(lambda: not E.poll()[1])                      # idle: the launch ends by itself
+    s, phi = E.post(ms[5], D, stream=post_st)            # a later request relaunches the loop
+    E.serve(loop_st)
+    _wait(lambda: s in E.poll()[0])
+    assert float(phi) == direct[5]
+    E.close()
+
+
+def test_device_loop_stop_and_resume(ragged):
+    """A stop request ends the loop after its current iteration; the occupied slot keeps its step and the
+    next launch finishes it with the same misfit."""
+    import time
+    w, P, dobs = ragged
+    m = t(proposals(w, 1, 103)[0])
+    D = t(dobs)
+    ref = float(P.misfit(m, D))
+    torch.cuda.synchronize()
+    E = MisfitEngine(P, 2)
+    st = torch.cuda.Stream()
+    s, phi = E.post(m, D)
+    E.serve(st)
+    time.sleep(0.002)
+    E.stop()
+    seen = []
+
+    def stopped():
+        done, running = E.poll()
+        seen.extend(done)
+        return not running
+
+    _wait(stopped)
+    if s not in seen:
+        E.serve(st)
+        _wait(lambda: bool(seen.extend(E.poll()[0]) or s in seen))
+    assert float(phi) == ref
+    with pytest.raises(_lib.HvError):
+        E.join(m, D)                                     # the engine now serves posted requests only
+    E.close()
