@@ -735,16 +735,21 @@ int hv_server_set_batching(hv_server *s, int max_vectors);
 /* Misfit lanes (continuous batching by time step): with slots > 0 (default
  * 64) a second scheduler thread gives each problem that receives misfit
  * requests a misfit engine (hv_engine_*) of up to `slots` slots, sized to at
- * most an eighth of the arena, on a stream of its own.  A queued misfit
- * request on that problem joins the engine at its next tick, whatever step
- * the other slots have reached, and is done after its own nt steps (its phi
- * bitwise hv_misfit's); the thread keeps a few ticks in flight per lane, so
- * lanes advance while the other thread enqueues long launch sequences, and
- * releases a lane's arena block after it has been idle for 0.2 s.  When no lane fits in the
+ * most an eighth of the arena and to 16384 CTAs per step, on a stream of its
+ * own.  A queued misfit request on that problem joins the engine at its next
+ * time step, whatever step the other slots have reached, and is done after
+ * its own nt steps (its phi bitwise hv_misfit's).  By default the thread
+ * enqueues the engine's ticks (hv_engine_join / hv_engine_tick), keeping a few
+ * in flight; with hv_server_set_engine_loop(s, 1), lanes created afterwards
+ * are served by the engine's device-resident loop instead (requests posted
+ * with hv_engine_post on a second stream of the lane, completions polled with
+ * hv_engine_poll, the loop relaunched when it has ended while requests are
+ * out).  A lane's arena block is released after it has been idle for 0.2 s.  When no lane fits in the
  * arena, misfits run as calls (merged as hv_server_set_batching says; queued
  * misfits at different models then run as one hv_misfit_models).  slots = 0
  * turns lanes off.  Applies to lanes created later. */
 int hv_server_set_engine(hv_server *s, int slots);
+int hv_server_set_engine_loop(hv_server *s, int enable);
 
 /* Tile configurations.  The stencil kernels come in a small menu of
  * configurations: a tile shape (TX x TZ points per CTA), a copy-pipeline depth

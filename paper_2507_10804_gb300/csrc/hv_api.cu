@@ -951,7 +951,7 @@ constexpr int kRebaseTick = 1 << 28;
 
 constexpr int kLoopBlocks = 1024;       // residual blocks of one misfit: kResidualBlocks, as hv_misfit
 constexpr int kLoopMaxIter = 1 << 20;   // iterations of one launch of the loop, at most
-constexpr int kLoopIdle = 2000;         // iterations with nothing to do before the loop ends
+constexpr int kLoopIdle = 200;          // iterations with no occupied slot before the loop ends
 
 size_t loop_bytes(int slots)
 {
@@ -1114,25 +1114,46 @@ extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done
 
 namespace {
 
-// The loop's graph: a conditional while node whose body is one iteration
-// (admission, the step of every occupied slot, the finishing slots' misfits,
-// the loop condition), captured into the body graph.
+// The loop's graph: a conditional while node whose body is one iteration:
+// k_loop_control, then an if node holding the forward step of every slot,
+// then an if node holding the finishing slots' misfits.  Each node's body is
+// captured into the graph the node owns.
+int capture_into(cudaStream_t cs, cudaGraph_t g, const std::function<int()> &launch)
+{
+    HV_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    const int rc = launch();
+    cudaGraph_t out = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(cs, &out);
+    if (rc != HV_OK) return rc;
+    if (ce != cudaSuccess) return hvi::fail(HV_ECUDA, "misfit loop capture: %s", cudaGetErrorString(ce));
+    return HV_OK;
+}
+
+int add_conditional(cudaGraph_t g, cudaGraphConditionalHandle hc, cudaGraphConditionalNodeType type,
+                    const cudaGraphNode_t *dep, cudaGraphNode_t *node, cudaGraph_t *body)
+{
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    HV_CK(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
+    *body = np.conditional.phGraph_out[0];
+    return HV_OK;
+}
+
 int build_loop_graph(hv_engine *e)
 {
     hv_handle *h = e->h;
     if (!e->cap) HV_CK(cudaStreamCreateWithFlags(&e->cap, cudaStreamNonBlocking));
     HV_CK(cudaGraphCreate(&e->graph, 0));
-    cudaGraphConditionalHandle hc;
-    HV_CK(cudaGraphConditionalHandleCreate(&hc, e->graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNodeParams np = {};
-    np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = hc;
-    np.conditional.type = cudaGraphCondTypeWhile;
-    np.conditional.size = 1;
-    cudaGraphNode_t node;
-    HV_CK(cudaGraphAddNode(&node, e->graph, nullptr, nullptr, 0, &np));
-    cudaGraph_t body = np.conditional.phGraph_out[0];
     hvk::LoopParams lp{};
+    HV_CK(cudaGraphConditionalHandleCreate(&lp.cond, e->graph, 1, cudaGraphCondAssignDefault));
+    cudaGraphNode_t wnode, cnode, snode, fnode;
+    cudaGraph_t body, sbody, fbody;
+    HV_RT(add_conditional(e->graph, lp.cond, cudaGraphCondTypeWhile, nullptr, &wnode, &body));
+    HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_step, body, 0, 0));
+    HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_fin, body, 0, 0));
     lp.slots = e->slots;
     lp.nt = h->nt;
     lp.nblk = kLoopBlocks;
@@ -1153,10 +1174,12 @@ int build_loop_graph(hv_engine *e)
     lp.ack = e->hmap_dev;
     lp.done = e->hmap_dev + e->slots;
     lp.stop = e->hmap_dev + 2 * e->slots;
-    lp.cond = hc;
-    HV_CK(cudaStreamBeginCaptureToGraph(e->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
-    int rc = hvk::launch_loop_control(lp, e->cap);
-    if (rc == HV_OK) {
+    HV_RT(capture_into(e->cap, body, [&] { return hvk::launch_loop_control(lp, e->cap); }));
+    size_t n = 1;
+    HV_CK(cudaGraphGetNodes(body, &cnode, &n));
+    if (n != 1) return hvi::fail(HV_ECUDA, "misfit loop: %zu nodes captured for the control kernel", n);
+    HV_RT(add_conditional(body, lp.cond_step, cudaGraphCondTypeIf, &cnode, &snode, &sbody));
+    HV_RT(capture_into(e->cap, sbody, [&] {
         hvk::FwdLaunch a{};
         a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
         a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
@@ -1167,14 +1190,10 @@ int build_loop_graph(hv_engine *e)
         a.slot_join = e->join_dev;
         a.plain = true;                // the step reads the tables k_loop_control has just written
         const int cfg = h->cfg[1];
-        rc = hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
-    }
-    if (rc == HV_OK) rc = hvk::launch_loop_finish(lp, e->cap);
-    if (rc == HV_OK) rc = hvk::launch_loop_cond(lp, e->cap);
-    cudaGraph_t out = nullptr;
-    cudaError_t ce = cudaStreamEndCapture(e->cap, &out);
-    if (rc != HV_OK) return rc;
-    if (ce != cudaSuccess) return hvi::fail(HV_ECUDA, "misfit loop capture: %s", cudaGetErrorString(ce));
+        return hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
+    }));
+    HV_RT(add_conditional(body, lp.cond_fin, cudaGraphCondTypeIf, &snode, &fnode, &fbody));
+    HV_RT(capture_into(e->cap, fbody, [&] { return hvk::launch_loop_finish(lp, e->cap); }));
     HV_CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
     return HV_OK;
 }

@@ -199,6 +199,8 @@ struct AdjLaunch {
 int launch_adj(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const AdjLaunch &a,
                cudaStream_t st);
 int adj_groups(const hv_handle *h);
+// CTAs of one model in a forward step (no Born fields) with tile configuration cfg.
+int fwd_ctas_per_model(const hv_handle *h, int cfg);
 
 // Shared-memory-resident H v kernels (every forward level stored, grids whose
 // padded field fits twice in a CTA's shared memory): which = 0 the forward
@@ -363,10 +365,11 @@ int launch_reduce_phi(const double *partials, int nblocks, double scale, double 
 
 // The device-resident misfit loop (hv_engine_serve and the kernels of its
 // graph body, hv_kernels.cu).  One iteration: k_loop_control admits the
-// requests posted into free slots and advances every occupied slot's step,
-// the forward step kernel advances all occupied slots, k_loop_finish and
-// k_loop_reduce form the misfit of every slot that took its last step, and
-// k_loop_cond decides whether the loop goes on.
+// requests posted into free slots, advances every occupied slot's step and
+// sets the three conditions (another iteration; a step to take; misfits to
+// finish); then, if any slot is occupied, the forward step kernel advances
+// all of them, and, if any took its last step, k_loop_finish and
+// k_loop_reduce form those misfits.
 constexpr int kLoopFreeSlot = 1 << 30;    // a slot_join entry that makes k_fwd skip the slot
 struct LoopParams {
     int slots, nt, nblk;
@@ -386,11 +389,10 @@ struct LoopParams {
     volatile int *ack;             // [slots] host-mapped: sequence number admitted
     volatile int *done;            // [slots] host-mapped: sequence number whose misfit is written
     volatile int *stop;            // host-mapped: nonzero ends the loop at the end of the iteration
-    cudaGraphConditionalHandle cond;
+    cudaGraphConditionalHandle cond, cond_step, cond_fin;   // while; if a slot is occupied; if a misfit finishes
 };
 int launch_loop_control(const LoopParams &p, cudaStream_t st);
 int launch_loop_finish(const LoopParams &p, cudaStream_t st);
-int launch_loop_cond(const LoopParams &p, cudaStream_t st);
 int launch_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq, const float *dobs,
                      double *phi, cudaStream_t st);
 int launch_copy_wavefield(const hv_handle *h, const float *u, float *out, cudaStream_t st);

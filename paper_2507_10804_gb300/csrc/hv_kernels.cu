@@ -197,13 +197,27 @@ __global__ void k_loop_control(const LoopParams p)
     }
     atomicAdd(&occ, local);
     __syncthreads();
-    // the finishing slots in slot order (one thread: the list is short and its order fixed)
+    // The finishing slots in slot order (one thread: the list is short and its
+    // order fixed), then the conditions.  The loop goes on unless the host asked
+    // it to stop, max_iter iterations of this launch have run, or no slot has
+    // been occupied for idle_max iterations (a request posted after this scan is
+    // admitted by the next launch).
     if (threadIdx.x == 0) {
         int nf = 0;
         for (int j = 0; j < p.slots; ++j)
             if (p.step[j] == p.nt - 1) p.fin[nf++] = j;
         p.fin[p.slots] = nf;
         p.ctl[2] = occ;
+        const int it = p.ctl[0] + 1;
+        const int idle = occ > 0 ? 0 : p.ctl[1] + 1;
+        const bool stop = *p.stop != 0;
+        const bool go = !stop && it < p.max_iter && idle < p.idle_max;
+        p.ctl[0] = go ? it : 0;
+        p.ctl[1] = go ? idle : 0;
+        p.ctl[3] = go ? 0 : (stop ? 1 : (it >= p.max_iter ? 2 : 3));
+        cudaGraphSetConditional(p.cond, go ? 1u : 0u);
+        cudaGraphSetConditional(p.cond_step, occ > 0 ? 1u : 0u);
+        cudaGraphSetConditional(p.cond_fin, nf > 0 ? 1u : 0u);
     }
 }
 
@@ -233,27 +247,6 @@ __global__ void k_loop_reduce(const LoopParams p)
             p.done[j] = p.seen[j];
         }
         __syncthreads();
-    }
-}
-
-// Whether the loop runs another iteration: not after a stop request, after
-// max_iter iterations of this launch, or after idle_max iterations with no
-// occupied slot and no request waiting (one warp).
-__global__ void k_loop_cond(const LoopParams p)
-{
-    bool pending = false;
-    for (int j = threadIdx.x; j < p.slots; j += 32)
-        pending |= *reinterpret_cast<volatile const int *>(p.post + j) != p.seen[j];
-    pending = __any_sync(0xffffffffu, pending);
-    if (threadIdx.x == 0) {
-        const int it = p.ctl[0] + 1;
-        const int idle = (p.ctl[2] > 0 || pending) ? 0 : p.ctl[1] + 1;
-        const bool stop = *p.stop != 0;
-        const bool go = !stop && it < p.max_iter && idle < p.idle_max;
-        p.ctl[0] = go ? it : 0;
-        p.ctl[1] = go ? idle : 0;
-        p.ctl[3] = go ? 0 : (stop ? 1 : (it >= p.max_iter ? 2 : 3));
-        cudaGraphSetConditional(p.cond, go ? 1u : 0u);
     }
 }
 
@@ -411,12 +404,6 @@ int launch_loop_finish(const LoopParams &p, cudaStream_t st)
     HV_RT_INTERNAL(cuda_check("k_loop_finish launch"));
     k_loop_reduce<<<1, 1024, 0, st>>>(p);
     return cuda_check("k_loop_reduce launch");
-}
-
-int launch_loop_cond(const LoopParams &p, cudaStream_t st)
-{
-    k_loop_cond<<<1, 32, 0, st>>>(p);
-    return cuda_check("k_loop_cond launch");
 }
 
 int launch_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq, const float *dobs,

@@ -13,10 +13,12 @@
 // whose results are bitwise those of separate calls; queued applies of one
 // Hessian approximation in one mode join into one apply of all their vectors.
 // Misfit requests (MCMC chains' proposals) go to a misfit lane per problem,
-// driven by a second thread: a misfit engine (hv_engine_*) whose slots each
-// hold one model with its own step counter, so a misfit joins a running sweep
-// at its next time step; where no lane fits in the arena, queued misfits at
-// different models run as one sweep of all the models (hv_misfit_models).  Completion is detected
+// looked after by a second thread: a misfit engine (hv_engine_*) whose slots
+// each hold one model with its own step counter, ticked by that thread or
+// served by the engine's device-resident loop, so a misfit joins a running
+// sweep at its next time step; where no lane fits in the arena, queued
+// misfits at different models run as one sweep of all the models
+// (hv_misfit_models).  Completion is detected
 // with events; the scheduler never blocks on the device (event queries plus
 // short sleeps), and every host wait is bounded.
 #include "hv_internal.h"
@@ -91,22 +93,29 @@ struct Req {
     double t_submit = 0, t_start = 0, t_done = 0;
 };
 
-// A misfit lane: the misfit engine of one problem (hv_engine_*) on its own
-// stream, in an arena block.  Queued misfits on the problem join it at its
-// next tick; the scheduler keeps up to kLookahead ticks in flight.
+// A misfit lane: the misfit engine of one problem (hv_engine_*) in an arena
+// block.  Host-ticked (default): requests join on the lane's stream and the
+// lane thread enqueues the ticks, keeping up to kLookahead in flight.  Device
+// loop (hv_server_set_engine_loop): the engine's device-resident loop runs on
+// the lane's stream, requests are prepared and posted on a second stream and
+// join the loop at its next time step, and the lane thread polls the
+// engine's host-mapped completion words.
 constexpr int kLookahead = 8;
 struct Lane {
     hv_engine *e = nullptr;
     unsigned long long serial = 0;              // the problem's hv_create serial
+    bool device_loop = false;
     int slots = 0;
     size_t off = 0;
-    cudaStream_t st = nullptr;
+    cudaStream_t st = nullptr;                  // joins and ticks, or the loop
+    cudaStream_t post_st = nullptr;             // device loop: the requests' preparation and posts
     std::vector<unsigned long long> slot_req;   // request per engine slot (0: free)
-    int active = 0;                             // occupied engine slots
-    int busy = 0;                               // occupied + admitted, not yet joined
-    std::deque<cudaEvent_t> ticks;              // recorded after recent ticks, oldest first
+    int active = 0;                             // occupied slots (joined or posted, not done)
+    int busy = 0;                               // active + admitted, not yet joined or posted
+    std::deque<cudaEvent_t> ticks;              // host-ticked: recorded after recent ticks, oldest first
     std::vector<std::pair<cudaEvent_t, std::vector<unsigned long long>>> finishing;   // done when the event is
-    int failed = HV_OK;                         // a join or tick failed: the lane takes no more requests
+    bool running = false;                       // device loop: the loop, at the last poll
+    int failed = HV_OK;                         // a join, post, tick or launch failed: the lane takes no more
     double idle_since = -1;
 };
 
@@ -123,6 +132,7 @@ struct hv_server {
     std::vector<size_t> slot_off;                              // arena offset held by the slot
     int merge_max = 64;                                        // vectors per merged call (< 2: no merging)
     int engine_slots = 64;                                     // slots per misfit lane (0: misfits run as calls)
+    bool engine_loop = false;                                  // lanes created from now on run the device loop
     std::unordered_map<hv_handle *, Lane> lanes;               // lane thread only
     int lane_reqs = 0;                                         // requests admitted to lanes and not done (under mu)
     std::vector<cudaEvent_t> ev_pool;                          // lane thread only
@@ -389,8 +399,24 @@ cudaEvent_t take_event(hv_server *S)
     return e;
 }
 
+void lane_release(hv_server *S, Lane &L)
+{
+    hv_engine_destroy(L.e);                     // ends a running loop first
+    cudaStreamSynchronize(L.st);
+    if (L.post_st) cudaStreamSynchronize(L.post_st);
+    for (cudaEvent_t e : L.ticks) S->ev_pool.push_back(e);
+    for (auto &f : L.finishing) S->ev_pool.push_back(f.first);
+    cudaStreamDestroy(L.st);
+    if (L.post_st) cudaStreamDestroy(L.post_st);
+    S->arena->release(L.off);
+}
+
 // The lane of problem p, created on first use with as many slots (up to
-// engine_slots) as fit in an eighth of the budget; nullptr if none fits now.
+// engine_slots) as fit in an eighth of the budget and in kLaneCtas CTAs per
+// step (the loop's step kernel launches the CTAs of every slot; those of free
+// slots exit at once, but on a large grid they would still cost more than the
+// step); nullptr if none fits now.
+constexpr int kLaneCtas = 16384;
 Lane *lane_for(hv_server *S, hv_handle *p)
 {
     auto it = S->lanes.find(p);
@@ -399,17 +425,13 @@ Lane *lane_for(hv_server *S, hv_handle *p)
         // runs for the new one; released here once idle (requests of a destroyed problem
         // cannot be pending unless the caller broke the contract).
         Lane &L = it->second;
-        if (L.busy != 0 || !L.finishing.empty()) return nullptr;
-        cudaStreamSynchronize(L.st);
-        for (cudaEvent_t e : L.ticks) S->ev_pool.push_back(e);
-        hv_engine_destroy(L.e);
-        cudaStreamDestroy(L.st);
-        S->arena->release(L.off);
+        if (L.busy != 0) return nullptr;
+        lane_release(S, L);
         S->lanes.erase(it);
         it = S->lanes.end();
     }
     if (it != S->lanes.end()) return it->second.failed == HV_OK ? &it->second : nullptr;
-    int slots = S->engine_slots;
+    int slots = std::min(S->engine_slots, std::max(1, kLaneCtas / std::max(1, hvk::fwd_ctas_per_model(p, p->cfg[1]))));
     size_t bytes = 0;
     while (slots > 1 && (hv_engine_workspace_size(p, slots, &bytes) != HV_OK || bytes > S->budget / 8)) slots /= 2;
     if (hv_engine_workspace_size(p, slots, &bytes) != HV_OK) return nullptr;
@@ -419,8 +441,15 @@ Lane *lane_for(hv_server *S, hv_handle *p)
         S->arena->release(L.off);
         return nullptr;
     }
+    L.device_loop = S->engine_loop;
+    if (L.device_loop && cudaStreamCreateWithFlags(&L.post_st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamDestroy(L.st);
+        S->arena->release(L.off);
+        return nullptr;
+    }
     if (hv_engine_create(p, slots, S->arena_base + L.off, bytes, &L.e) != HV_OK) {
         cudaStreamDestroy(L.st);
+        if (L.post_st) cudaStreamDestroy(L.post_st);
         S->arena->release(L.off);
         return nullptr;
     }
@@ -437,91 +466,130 @@ struct Join {
     double *phi;
 };
 
-// Outside the lock: the admitted joins, then ticks until each lane has
-// kLookahead ticks in flight.  Returns whether anything was enqueued;
-// `failed` collects requests that could not join.
-bool lane_work(hv_server *S, const std::vector<Join> &joins, std::vector<std::pair<unsigned long long, int>> &failed)
+// A lane's occupied slots all fail with rc; the lane takes no more requests.
+void lane_fail(Lane &L, int rc, std::vector<std::pair<unsigned long long, int>> &finished)
 {
-    bool any = !joins.empty();
-    for (const Join &j : joins) {
-        Lane &L = S->lanes[j.p];
-        int slot = -1;
-        int rc = L.failed != HV_OK ? L.failed : hv_engine_join(L.e, j.m, j.d_obs, j.phi, (void *)L.st, &slot);
-        if (rc != HV_OK) {
-            if (L.failed == HV_OK) L.failed = rc;
-            --L.busy;
-            failed.push_back({j.id, rc});
-            continue;
+    L.failed = rc;
+    for (int q = 0; q < L.slots; ++q)
+        if (L.slot_req[q]) {
+            finished.push_back({L.slot_req[q], rc});
+            L.slot_req[q] = 0;
         }
-        L.slot_req[slot] = j.id;
-        ++L.active;
-    }
-    std::vector<int> done;
-    for (auto &kv : S->lanes) {
-        Lane &L = kv.second;
-        done.resize(L.slots);
-        while (L.active > 0 && L.failed == HV_OK) {
-            while (!L.ticks.empty() && cudaEventQuery(L.ticks.front()) != cudaErrorNotReady) {
-                S->ev_pool.push_back(L.ticks.front());
-                L.ticks.pop_front();
+    L.busy -= L.active;
+    L.active = 0;
+}
+
+// Host-ticked lane: ticks until kLookahead are in flight; the requests of a
+// tick that finishes slots are done once the event after it has completed.
+bool lane_ticks(hv_server *S, Lane &L, std::vector<std::pair<unsigned long long, int>> &finished)
+{
+    bool any = false;
+    std::vector<int> done(L.slots);
+    while (L.active > 0 && L.failed == HV_OK) {
+        while (!L.ticks.empty() && cudaEventQuery(L.ticks.front()) != cudaErrorNotReady) {
+            S->ev_pool.push_back(L.ticks.front());
+            L.ticks.pop_front();
+        }
+        if ((int)L.ticks.size() >= kLookahead) break;
+        int nd = 0;
+        int rc = hv_engine_tick(L.e, (void *)L.st, done.data(), &nd);
+        cudaEvent_t ev = take_event(S);
+        if (rc == HV_OK && (!ev || cudaEventRecord(ev, L.st) != cudaSuccess)) rc = HV_ECUDA;
+        if (ev) L.ticks.push_back(ev);
+        any = true;
+        if (rc != HV_OK) {
+            lane_fail(L, rc, finished);
+            break;
+        }
+        if (nd > 0) {
+            std::vector<unsigned long long> ids;
+            for (int q = 0; q < nd; ++q) {
+                ids.push_back(L.slot_req[done[q]]);
+                L.slot_req[done[q]] = 0;
             }
-            if ((int)L.ticks.size() >= kLookahead) break;
-            int nd = 0;
-            int rc = hv_engine_tick(L.e, (void *)L.st, done.data(), &nd);
-            cudaEvent_t ev = take_event(S);
-            if (rc == HV_OK && (!ev || cudaEventRecord(ev, L.st) != cudaSuccess)) rc = HV_ECUDA;
-            if (ev) L.ticks.push_back(ev);
-            any = true;
-            if (rc != HV_OK) {             // the occupied slots' requests fail; the lane takes no more
-                L.failed = rc;
-                for (int q = 0; q < L.slots; ++q)
-                    if (L.slot_req[q]) {
-                        failed.push_back({L.slot_req[q], rc});
-                        L.slot_req[q] = 0;
-                    }
-                L.busy -= L.active;
-                L.active = 0;
-                break;
-            }
-            if (nd > 0) {
-                std::vector<unsigned long long> ids;
-                for (int q = 0; q < nd; ++q) {
-                    ids.push_back(L.slot_req[done[q]]);
-                    L.slot_req[done[q]] = 0;
-                }
-                L.active -= nd;
-                L.busy -= nd;
-                cudaEvent_t f = take_event(S);
-                if (f && cudaEventRecord(f, L.st) == cudaSuccess) {
-                    L.finishing.push_back({f, ids});
-                } else {
-                    if (f) S->ev_pool.push_back(f);
-                    for (auto id : ids) failed.push_back({id, HV_ECUDA});
-                }
+            L.active -= nd;
+            L.busy -= nd;
+            cudaEvent_t f = take_event(S);
+            if (f && cudaEventRecord(f, L.st) == cudaSuccess) {
+                L.finishing.push_back({f, ids});
+            } else {
+                if (f) S->ev_pool.push_back(f);
+                for (auto id : ids) finished.push_back({id, HV_ECUDA});
             }
         }
     }
     return any;
 }
 
-// Under the lock: requests whose last tick has completed, lanes idle for a
-// while released (their work has drained).  Returns whether a request finished.
-bool lane_completions(hv_server *S, std::vector<std::pair<unsigned long long, int>> &failed)
+// Device-loop lane: the finished slots reported by the engine; the loop
+// relaunched if it has ended while requests are out.
+bool lane_poll(Lane &L, std::vector<std::pair<unsigned long long, int>> &finished)
+{
+    if (L.active == 0 && !L.running) return false;
+    std::vector<int> done(L.slots);
+    int nd = 0, run = 0;
+    if (hv_engine_poll(L.e, done.data(), &nd, &run) != HV_OK) run = 0;
+    for (int q = 0; q < nd; ++q) {
+        finished.push_back({L.slot_req[done[q]], HV_OK});
+        L.slot_req[done[q]] = 0;
+    }
+    L.active -= nd;
+    L.busy -= nd;
+    if (L.active > 0 && !run && L.failed == HV_OK) {
+        const int rc = hv_engine_serve(L.e, (void *)L.st);
+        if (rc == HV_OK) run = 1;
+        else lane_fail(L, rc, finished);
+    }
+    L.running = run != 0;
+    return nd > 0;
+}
+
+// Outside the lock: the admitted requests joined to (or posted to) their
+// lanes, then every lane ticked or polled.  Returns whether anything was
+// enqueued or finished; `finished` collects requests done (HV_OK) or failed.
+bool lane_work(hv_server *S, const std::vector<Join> &joins, std::vector<std::pair<unsigned long long, int>> &finished)
+{
+    bool any = !joins.empty();
+    for (const Join &j : joins) {
+        Lane &L = S->lanes[j.p];
+        int slot = -1;
+        int rc = L.failed;
+        if (rc == HV_OK)
+            rc = L.device_loop ? hv_engine_post(L.e, j.m, j.d_obs, j.phi, (void *)L.post_st, &slot)
+                               : hv_engine_join(L.e, j.m, j.d_obs, j.phi, (void *)L.st, &slot);
+        if (rc != HV_OK) {
+            if (L.failed == HV_OK) L.failed = rc;
+            --L.busy;
+            finished.push_back({j.id, rc});
+            continue;
+        }
+        L.slot_req[slot] = j.id;
+        ++L.active;
+    }
+    for (auto &kv : S->lanes) any |= kv.second.device_loop ? lane_poll(kv.second, finished)
+                                                          : lane_ticks(S, kv.second, finished);
+    return any;
+}
+
+// Under the lock: the statuses of finished (or failed) lane requests, the
+// host-ticked lanes' requests whose last tick has completed, and lanes idle
+// for a while released.  Returns whether a request finished.
+bool lane_completions(hv_server *S, std::vector<std::pair<unsigned long long, int>> &finished)
 {
     bool any = false;
     const double t = S->now();
-    for (auto &f : failed) {
+    for (auto &f : finished) {
         Req &q = S->reqs[f.first];
         q.status = f.second;
         q.t_done = t;
         --S->lane_reqs;
         any = true;
     }
-    failed.clear();
+    finished.clear();
     for (auto it = S->lanes.begin(); it != S->lanes.end();) {
         Lane &L = it->second;
         for (size_t i = 0; i < L.finishing.size();) {
-            cudaError_t e = cudaEventQuery(L.finishing[i].first);
+            const cudaError_t e = cudaEventQuery(L.finishing[i].first);
             if (e == cudaErrorNotReady) {
                 ++i;
                 continue;
@@ -536,8 +604,7 @@ bool lane_completions(hv_server *S, std::vector<std::pair<unsigned long long, in
             L.finishing.erase(L.finishing.begin() + i);
             any = true;
         }
-        const bool idle = L.busy == 0 && L.finishing.empty();
-        if (!idle) {
+        if (L.busy != 0 || !L.finishing.empty()) {
             L.idle_since = -1;
             ++it;
             continue;
@@ -547,10 +614,7 @@ bool lane_completions(hv_server *S, std::vector<std::pair<unsigned long long, in
             ++it;
             continue;
         }
-        for (cudaEvent_t e : L.ticks) S->ev_pool.push_back(e);
-        hv_engine_destroy(L.e);
-        cudaStreamDestroy(L.st);
-        S->arena->release(L.off);
+        lane_release(S, L);
         it = S->lanes.erase(it);
     }
     return any;
@@ -558,8 +622,8 @@ bool lane_completions(hv_server *S, std::vector<std::pair<unsigned long long, in
 
 // The lane thread: admits queued misfits into their problems' lanes (a
 // misfit whose lane does not fit in the arena is left to the scheduler), then
-// joins and ticks outside the lock, so that the lanes advance while the
-// scheduler thread enqueues long launch sequences.
+// joins or posts them and ticks or polls the lanes outside the lock, so that
+// the lanes advance whatever the scheduler thread is enqueueing.
 void lane_loop(hv_server *S)
 {
     cudaSetDevice(S->device);
@@ -595,7 +659,7 @@ void lane_loop(hv_server *S)
             it = S->queue.erase(it);
         }
         bool active = !joins.empty();
-        for (auto &kv : S->lanes) active |= kv.second.active > 0;
+        for (auto &kv : S->lanes) active |= kv.second.active > 0 || kv.second.running;
         if (active) {
             lk.unlock();
             progress |= lane_work(S, joins, lane_failed);
@@ -763,14 +827,7 @@ extern "C" int hv_server_destroy(hv_server *S, double timeout_s)
     S->worker.join();
     S->lane_worker.join();
     if (rc == HV_OK) {
-        for (auto &kv : S->lanes) {
-            Lane &L = kv.second;
-            cudaStreamSynchronize(L.st);
-            for (cudaEvent_t e : L.ticks) cudaEventDestroy(e);
-            for (auto &f : L.finishing) cudaEventDestroy(f.first);
-            hv_engine_destroy(L.e);
-            cudaStreamDestroy(L.st);
-        }
+        for (auto &kv : S->lanes) lane_release(S, kv.second);
         for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
         for (auto st : S->streams) cudaStreamDestroy(st);
         for (auto ev : S->events) cudaEventDestroy(ev);
@@ -865,6 +922,14 @@ extern "C" int hv_server_set_engine(hv_server *S, int slots)
         return hvi::fail(HV_EINVAL, "hv_server_set_engine: null server or slots outside 0..65535");
     std::lock_guard<std::mutex> g(S->mu);
     S->engine_slots = slots;
+    return HV_OK;
+}
+
+extern "C" int hv_server_set_engine_loop(hv_server *S, int enable)
+{
+    if (!S) return hvi::fail(HV_EINVAL, "hv_server_set_engine_loop: null server");
+    std::lock_guard<std::mutex> g(S->mu);
+    S->engine_loop = enable != 0;
     return HV_OK;
 }
 

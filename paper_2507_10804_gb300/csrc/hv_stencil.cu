@@ -1665,6 +1665,15 @@ int launch_fwd(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMa
     });
 }
 
+int fwd_ctas_per_model(const hv_handle *h, int cfg)
+{
+    return with_cfg(cfg, [&](auto c) -> int {
+        using C = decltype(c);
+        const int gsz = (h->ns + adj_groups(h) - 1) / adj_groups(h), spg = gsz * C::GPC;
+        return tiling(h, cfg).ntiles * ((h->ns + spg - 1) / spg);
+    });
+}
+
 int launch_fwd2(const hv_handle *h, int cfg, const hvi::RecTiles &rt, const TmaMaps &maps, const Fwd2Launch &a,
                 cudaStream_t st)
 {

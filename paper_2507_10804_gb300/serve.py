@@ -85,6 +85,11 @@ class Server:
         as calls; hv_server_set_engine)."""
         check(self.lib.hv_server_set_engine(self._s, int(slots)))
 
+    def set_engine_loop(self, enable: bool) -> None:
+        """Misfit lanes created from now on are served by the engine's device-resident loop instead of ticks
+        enqueued by the server's thread (hv_server_set_engine_loop)."""
+        check(self.lib.hv_server_set_engine_loop(self._s, int(bool(enable))))
+
     def poll(self, rid: int) -> int:
         st = ctypes.c_int()
         check(self.lib.hv_poll(self._s, int(rid), ctypes.byref(st)))

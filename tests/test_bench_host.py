@@ -13,7 +13,7 @@ def test_dram_counters_parse():
     table = bench.dram_traffic()
     assert table, "profiles/dram_traffic.txt holds no entries"
     for (workload, kind, tile), (h, nbytes) in table.items():
-        assert workload in ("paper", "batched", "batched-resident"), workload
+        assert workload in ("paper", "batched", "batched-resident", "misfits"), workload
         assert kind in ("fwd", "advance", "adj"), kind
         assert re.fullmatch(r"[0-9a-f]{16}", h), h
         assert nbytes > 0

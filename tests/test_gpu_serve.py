@@ -285,10 +285,12 @@ def test_queued_misfits_at_different_models_run_as_one_sweep(problems):
     S.close()
 
 
-def test_misfits_join_a_running_lane_at_the_next_time_step():
-    """Misfit lanes: misfits submitted while another misfit on the same problem is running join the
-    problem's lane at its next time step instead of waiting for that sweep to end (their runs overlap);
-    each phi is bitwise the direct misfit, and the lane's occupancy at each join is reported."""
+@pytest.mark.parametrize("device_loop", [False, True])
+def test_misfits_join_a_running_lane_at_the_next_time_step(device_loop):
+    """Misfit lanes, ticked by the server's thread or served by the engine's device-resident loop: misfits
+    submitted while another misfit on the same problem is running join the problem's lane at its next time
+    step instead of waiting for that sweep to end (their runs overlap); each phi is bitwise the direct misfit,
+    and the lane's occupancy at each join is reported."""
     import time
     w, P = make(48, 64, 4, 3000, 17)                      # a 3000-step sweep: tens of milliseconds
     dobs = t(synth.normal(221, w.ns * w.nt * w.nr).reshape(w.ns, w.nt, w.nr) * 1e-3)
@@ -296,6 +298,7 @@ def test_misfits_join_a_running_lane_at_the_next_time_step():
     ms = [t(np.minimum(w.m * (1.0 + 0.03 * z[i] / np.abs(z[i]).max()), w.vmax)) for i in range(3)]
     direct = [float(P.misfit(m, dobs)) for m in ms]
     S = Server(hbm_budget=2 << 30, max_concurrent=2)
+    S.set_engine_loop(device_loop)
     a, pa = S.submit_misfit(P, ms[0], dobs)
     t0 = time.perf_counter()
     while S.poll(a) == HV_REQ_QUEUED and time.perf_counter() - t0 < 60:
