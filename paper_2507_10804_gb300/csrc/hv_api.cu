@@ -9,6 +9,7 @@
 #include <functional>
 
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -1227,7 +1228,7 @@ extern "C" int hv_engine_post(hv_engine *e, const float *m, const float *d_obs, 
     while (j < S && e->slot_seq[j] != 0) ++j;
     if (j == S) return hvi::fail(HV_EBUSY, "hv_engine_post: all %d slots are taken", S);
     const size_t fbytes = h->fsize * sizeof(float);
-    if (++e->seq <= 0) e->seq = 1;
+    e->seq = e->seq == INT_MAX ? 1 : e->seq + 1;   // never 0, the value of a slot that was never posted
     {
         ProfScope ps(h, st, HV_K_OTHER);
         HV_RT(hvk::launch_prep(h, m, nullptr, 0, reinterpret_cast<float *>(e->ws + e->L.C) + (size_t)j * h->fsize,
