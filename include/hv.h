@@ -673,6 +673,13 @@ int hv_gpcn_propose(int n, int c, const float *m, const float *m_map, const floa
 int hv_gpcn_accept(int n, int c, const double *phi_new, const float *m_new, const float *d_new, const float *Hd_new,
                    const double *log_u, float *m, double *delta_cur, int *accepted, void *stream);
 
+/* Output checks: *count (DEVICE unsigned long long) = the number of NaN and
+ * +-Inf entries of the DEVICE array x[0, n) (a scan of any output, e.g. of an
+ * H v whose model violates the time step's stability bound).  The paper has no
+ * counterpart; it serves the checks of a run.  HV_EINVAL for a null count, or
+ * a null x with n > 0. */
+int hv_count_nonfinite(const float *x, size_t n, unsigned long long *count, void *stream);
+
 /* Serving.  A server owns one device arena of hbm_budget bytes (allocated at
  * creation) and max_concurrent CUDA streams on the current device.  Requests
  * (H v, gradient, misfit, and the apply of a built Hessian approximation) on

@@ -101,6 +101,7 @@ _SIGS = {
     "hv_engine_stop": ([c_void_p], c_int),
     "hv_server_set_engine": ([c_void_p, c_int], c_int),
     "hv_server_set_engine_loop": ([c_void_p, c_int], c_int),
+    "hv_count_nonfinite": ([fp, c_size_t, fp, c_void_p], c_int),
     "hv_server_create": ([c_size_t, c_int, ctypes.POINTER(c_void_p)], c_int),
     "hv_server_destroy": ([c_void_p, c_double], c_int),
     "hv_submit": ([c_void_p, ctypes.POINTER(HvRequest), ctypes.POINTER(ctypes.c_ulonglong)], c_int),

@@ -783,6 +783,7 @@ extern "C" int hv_workspace_size(const hv_handle *h, int op, int k, int ckpt, si
 
 extern "C" int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_fwd_model");
     Layout L;
     HV_RT(check_common(h, ws, ws_bytes, HV_OP_FWD, 1, HV_CKPT_ALL, L));
     if (!m || !d) return hvi::fail(HV_EINVAL, "null model or data pointer");
@@ -799,6 +800,7 @@ extern "C" int hv_fwd_model(hv_handle *h, const float *m, float *d, void *ws, si
 extern "C" int hv_misfit(hv_handle *h, const float *m, const float *d_obs, double *phi, void *ws, size_t ws_bytes,
                          void *stream)
 {
+    hvi::Range nvtx_range("hv_misfit");
     Layout L;
     HV_RT(check_common(h, ws, ws_bytes, HV_OP_MISFIT, 1, HV_CKPT_ALL, L));
     if (!m || !d_obs || !phi) return hvi::fail(HV_EINVAL, "null model, data or phi pointer");
@@ -855,6 +857,7 @@ int misfit_models_sweep(hv_handle *h, int k, const Layout &L, char *w, cudaStrea
 extern "C" int hv_misfit_models(hv_handle *h, int k, const float *const *m, const float *const *d_obs,
                                 double *const *phi, void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_misfit_models");
     if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "hv_misfit_models: k = %d models; need 1 <= k <= 65535", k);
     if (!m || !d_obs || !phi) return hvi::fail(HV_EINVAL, "hv_misfit_models: null pointer array");
     for (int i = 0; i < k; ++i)
@@ -1062,6 +1065,7 @@ extern "C" int hv_engine_join(hv_engine *e, const float *m, const float *d_obs, 
 
 extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done)
 {
+    hvi::Range nvtx_range("hv_engine_tick");
     if (!e || !done || !n_done) return hvi::fail(HV_EINVAL, "hv_engine_tick: null argument");
     *n_done = 0;
     if (e->loop) return hvi::fail(HV_EINVAL, "hv_engine_tick: the engine serves posted requests (hv_engine_post)");
@@ -1203,6 +1207,7 @@ int build_loop_graph(hv_engine *e)
 
 extern "C" int hv_engine_post(hv_engine *e, const float *m, const float *d_obs, double *phi, void *stream, int *slot)
 {
+    hvi::Range nvtx_range("hv_engine_post");
     if (!e || !m || !d_obs || !phi || !slot) return hvi::fail(HV_EINVAL, "hv_engine_post: null argument");
     *slot = -1;
     if (!e->loop && e->active > 0)
@@ -1243,6 +1248,7 @@ extern "C" int hv_engine_post(hv_engine *e, const float *m, const float *d_obs, 
 
 extern "C" int hv_engine_serve(hv_engine *e, void *stream)
 {
+    hvi::Range nvtx_range("hv_engine_serve");
     if (!e) return hvi::fail(HV_EINVAL, "hv_engine_serve: null engine");
     if (!e->loop) return hvi::fail(HV_EINVAL, "hv_engine_serve: nothing was posted to this engine");
     if (e->launched && cudaEventQuery(e->ran) == cudaErrorNotReady) return HV_OK;   // running
@@ -1289,6 +1295,7 @@ extern "C" int hv_engine_active(const hv_engine *e, int *active)
 extern "C" int hv_wavefield(hv_handle *h, const float *m, int n_out, const int *steps, float *out, void *ws,
                             size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_wavefield");
     Layout L;
     HV_RT(check_common(h, ws, ws_bytes, HV_OP_WAVEFIELD, 1, HV_CKPT_ALL, L));
     if (!m || !out || !steps || n_out < 1) return hvi::fail(HV_EINVAL, "null pointer or n_out < 1");
@@ -1315,6 +1322,7 @@ extern "C" int hv_wavefield(hv_handle *h, const float *m, int n_out, const int *
 extern "C" int hv_born(hv_handle *h, const float *m, const float *dm, int k, float *dd, void *ws, size_t ws_bytes,
                        void *stream)
 {
+    hvi::Range nvtx_range("hv_born");
     Layout L;
     HV_RT(check_common(h, ws, ws_bytes, HV_OP_BORN, k, HV_CKPT_ALL, L));
     if (!m || !dm || !dd) return hvi::fail(HV_EINVAL, "null model, perturbation or output");
@@ -1332,6 +1340,7 @@ extern "C" int hv_born(hv_handle *h, const float *m, const float *dm, int k, flo
 extern "C" int hv_migrate(hv_handle *h, const float *m, const float *r, float *g, int ckpt, void *ws, size_t ws_bytes,
                           void *stream)
 {
+    hvi::Range nvtx_range("hv_migrate");
     if (!m || !r || !g) return hvi::fail(HV_EINVAL, "null model, data or output");
     return run_adjoint(h, 0, m, r, 1, g, nullptr, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
 }
@@ -1339,6 +1348,7 @@ extern "C" int hv_migrate(hv_handle *h, const float *m, const float *r, float *g
 extern "C" int hv_misfit_grad(hv_handle *h, const float *m, const float *d_obs, double *phi, float *grad, int ckpt,
                               void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_misfit_grad");
     if (!m || !d_obs || !phi || !grad) return hvi::fail(HV_EINVAL, "null model, data, phi or gradient");
     return run_adjoint(h, 1, m, d_obs, 1, grad, nullptr, phi, ckpt, ws, ws_bytes, (cudaStream_t)stream);
 }
@@ -1346,6 +1356,7 @@ extern "C" int hv_misfit_grad(hv_handle *h, const float *m, const float *d_obs, 
 extern "C" int hv_hessian_apply(hv_handle *h, const float *m, const float *v, int k, float *Hv, int ckpt, void *ws,
                                 size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_hessian_apply");
     if (!m || !v || !Hv) return hvi::fail(HV_EINVAL, "null model, vector or output");
     return run_adjoint(h, 2, m, v, k, Hv, nullptr, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
 }
@@ -1353,6 +1364,7 @@ extern "C" int hv_hessian_apply(hv_handle *h, const float *m, const float *v, in
 extern "C" int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float *v, int k, double *Hv, int ckpt,
                                        void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_hessian_apply_f64out");
     if (!m || !v || !Hv) return hvi::fail(HV_EINVAL, "null model, vector or output");
     return run_adjoint(h, 2, m, v, k, nullptr, Hv, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream);
 }
@@ -1360,12 +1372,14 @@ extern "C" int hv_hessian_apply_f64out(hv_handle *h, const float *m, const float
 extern "C" int hv_hessian_apply_partial(hv_handle *h, const float *m, const float *v, int k, double *ext, int ckpt,
                                         void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_hessian_apply_partial");
     if (!m || !v || !ext) return hvi::fail(HV_EINVAL, "null model, vector or output");
     return run_adjoint(h, 2, m, v, k, nullptr, nullptr, nullptr, ckpt, ws, ws_bytes, (cudaStream_t)stream, ext);
 }
 
 extern "C" int hv_image_fold(hv_handle *h, const double *ext, int k, float *out, double *out64, void *stream)
 {
+    hvi::Range nvtx_range("hv_image_fold");
     if (!h || !ext || (!out && !out64)) return hvi::fail(HV_EINVAL, "null handle, image or output");
     if (k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "k = %d; need 1 <= k <= 65535", k);
     int dev = -1;
@@ -1443,6 +1457,7 @@ extern "C" int hv_batch_workspace_size(const hv_handle *h, const hv_batch *b, in
 extern "C" int hv_apply_batch(hv_handle *h, const float *m, const hv_batch *b, int ckpt, void *ws, size_t ws_bytes,
                               void *stream)
 {
+    hvi::Range nvtx_range("hv_apply_batch");
     if (!m) return hvi::fail(HV_EINVAL, "null model");
     BatchLayout B;
     HV_RT(batch_layout(h, b, ckpt, B));
@@ -1517,6 +1532,12 @@ extern "C" int hv_apply_batch(hv_handle *h, const float *m, const hv_batch *b, i
     for (int g = 0; g < b->n_grad; ++g)
         HV_CK(cudaMemcpyAsync(b->grad[g], O + (g0 + g) * N, N * sizeof(float), cudaMemcpyDeviceToDevice, st));
     return HV_OK;
+}
+
+extern "C" int hv_count_nonfinite(const float *x, size_t n, unsigned long long *count, void *stream)
+{
+    if (!count || (n > 0 && !x)) return hvi::fail(HV_EINVAL, "hv_count_nonfinite: null pointer");
+    return hvk::launch_count_nonfinite(x, n, count, (cudaStream_t)stream);
 }
 
 extern "C" int hv_profile(hv_handle *h, int enable)
@@ -1832,6 +1853,7 @@ extern "C" int hv_set_launch_mode(hv_handle *h, int mode)
 // data-dependent work) and keeps the fastest per kernel kind.
 extern "C" int hv_autotune(hv_handle *h, int k, void *ws, size_t ws_bytes, void *stream, int *chosen, float *ms)
 {
+    hvi::Range nvtx_range("hv_autotune");
     Layout L;
     HV_RT(check_common(h, ws, ws_bytes, HV_OP_HV, k, 1, L));
     cudaStream_t st = (cudaStream_t)stream;
@@ -2058,6 +2080,7 @@ extern "C" int hv_set_highpass(hv_handle *h, double rho_c)
 extern "C" int hv_highpass_apply(int nz, int nx, double h, double rho_c, const float *v, int k, float *out,
                                  void *stream)
 {
+    hvi::Range nvtx_range("hv_highpass_apply");
     if (!v || !out || k < 1) return hvi::fail(HV_EINVAL, "null field or k < 1");
     cudaStream_t st = (cudaStream_t)stream;
     hvk::Highpass F;
@@ -2149,6 +2172,7 @@ extern "C" int hv_filtered_destroy(hv_filtered *f)
 extern "C" int hv_approx_build_psf(hv_handle *h, const float *m, int spacing_cells, int n_batches, int ckpt,
                                    hv_approx **out, void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_psf");
     if (out) *out = nullptr;
     if (!h || !out || !m) return hvi::fail(HV_EINVAL, "null handle, model or output");
     hvk::PsfGeo g;
@@ -2233,6 +2257,7 @@ extern "C" int hv_approx_pdo_workspace_size(hv_handle *h, int ckpt, size_t *byte
 extern "C" int hv_approx_build_pdo(hv_handle *h, const float *m, double rho0, int r, int ckpt, hv_approx **out,
                                    void *ws, size_t ws_bytes, void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_pdo");
     if (out) *out = nullptr;
     if (!h || !out || !m) return hvi::fail(HV_EINVAL, "null handle, model or output");
     hvk::LrGeo g;
@@ -2292,6 +2317,7 @@ extern "C" int hv_approx_build_lr(hv_handle *h, const float *m, double delta, do
                                   const float *omega, int k, int ckpt, hv_approx **out, void *ws, size_t ws_bytes,
                                   void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_lr");
     if (out) *out = nullptr;
     if (!h || !m || !omega || !out) return hvi::fail(HV_EINVAL, "null handle, model, test vectors or output");
     if (rank < 1 || k < rank || k > 256) return hvi::fail(HV_EINVAL, "rank %d with %d test vectors; need 1 <= rank <= k <= 256", rank, k);
@@ -2372,6 +2398,7 @@ HessFn op_fn(const hv_operator *op, cudaStream_t st)
 extern "C" int hv_approx_build_psf_op(const hv_operator *op, int spacing_cells, int n_batches, hv_approx **out,
                                       void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_psf_op");
     if (out) *out = nullptr;
     if (!out) return hvi::fail(HV_EINVAL, "null output");
     HV_RT(check_operator(op));
@@ -2391,6 +2418,7 @@ extern "C" int hv_approx_build_psf_op(const hv_operator *op, int spacing_cells, 
 
 extern "C" int hv_approx_build_pdo_op(const hv_operator *op, double rho0, int r, hv_approx **out, void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_pdo_op");
     if (out) *out = nullptr;
     if (!out) return hvi::fail(HV_EINVAL, "null output");
     HV_RT(check_operator(op));
@@ -2410,6 +2438,7 @@ extern "C" int hv_approx_build_pdo_op(const hv_operator *op, double rho0, int r,
 extern "C" int hv_approx_build_lr_op(const hv_operator *op, double delta, double gamma, int rank, const float *omega,
                                      int k, hv_approx **out, void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_lr_op");
     if (out) *out = nullptr;
     if (!out || !omega) return hvi::fail(HV_EINVAL, "null test vectors or output");
     HV_RT(check_operator(op));
@@ -2438,6 +2467,7 @@ extern "C" int hv_approx_lr_eigs(const hv_approx *a, double *lambda, float *V, v
 extern "C" int hv_prior_apply(int nz, int nx, double h, double delta, double gamma, const float *v, int k, float *out,
                               int op, void *stream)
 {
+    hvi::Range nvtx_range("hv_prior_apply");
     if (!v || !out || k < 1 || k > 65535) return hvi::fail(HV_EINVAL, "null field or k outside [1, 65535]");
     if (op < 0 || op > 3) return hvi::fail(HV_EINVAL, "prior operation %d", op);
     hvk::Prior P;
@@ -2484,17 +2514,20 @@ static int build_psfplus_common(const hv_approx *psf, const hv_approx *pdo, doub
 extern "C" int hv_approx_build_psfplus(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
                                        void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_psfplus");
     return build_psfplus_common(psf, pdo, tol, false, out, stream);
 }
 
 extern "C" int hv_approx_build_psfplus_sqrt(const hv_approx *psf, const hv_approx *pdo, double tol, hv_approx **out,
                                             void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_build_psfplus_sqrt");
     return build_psfplus_common(psf, pdo, tol, true, out, stream);
 }
 
 extern "C" int hv_approx_sqrt_pdo(const hv_approx *pdo, hv_approx **out, void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_sqrt_pdo");
     if (out) *out = nullptr;
     if (!pdo || !out) return hvi::fail(HV_EINVAL, "null approximation or output");
     if (pdo->kind != 1 || pdo->lr.spd) return hvi::fail(HV_EINVAL, "the square root is taken of a PDO approximation of H_d");
@@ -2528,6 +2561,7 @@ extern "C" int hv_approx_pdo_symbol(const hv_approx *a, float *cols, float *weig
 
 extern "C" int hv_approx_apply(const hv_approx *a, const float *v, int k, float *out, int mode, void *stream)
 {
+    hvi::Range nvtx_range("hv_approx_apply");
     if (!a) return hvi::fail(HV_EINVAL, "null approximation");
     if (mode < HV_APPROX_H || mode > HV_APPROX_SQRT_T) return hvi::fail(HV_EINVAL, "unknown apply mode %d", mode);
     const bool spd = (a->kind == 1 || a->kind == 2) && a->lr.spd;

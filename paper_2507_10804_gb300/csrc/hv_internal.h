@@ -24,7 +24,20 @@
         if (r_ != HV_OK) return r_;                                                                   \
     } while (0)
 
+#include <nvtx3/nvToolsExt.h>
+
 namespace hvi {
+
+// An NVTX range over one library call: profilers that record NVTX show the
+// call's name over its launches; without one attached it costs a few
+// nanoseconds (header-only NVTX, no link-time dependency).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+
 
 // ---------------------------------------------------------------- status
 int fail(int code, const char *fmt, ...);
@@ -392,6 +405,7 @@ struct LoopParams {
     cudaGraphConditionalHandle cond, cond_step, cond_fin;   // while; if a slot is occupied; if a misfit finishes
 };
 int launch_loop_control(const LoopParams &p, cudaStream_t st);
+int launch_count_nonfinite(const float *x, size_t n, unsigned long long *count, cudaStream_t st);
 int launch_loop_finish(const LoopParams &p, cudaStream_t st);
 int launch_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq, const float *dobs,
                      double *phi, cudaStream_t st);

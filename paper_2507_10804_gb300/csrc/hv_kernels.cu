@@ -10,6 +10,7 @@
 // FP64 misfit reduction, the ghost-band clearing and the wavefield export.
 #include "hv_internal.h"
 
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 
@@ -166,6 +167,16 @@ __global__ void k_residual(const float *d, const float *__restrict__ dobs, float
 __global__ void k_reduce_phi(const double *__restrict__ partials, int nb, double scale, double *phi)
 {
     reduce_partials(partials, nb, scale, phi);
+}
+
+// Adds the number of non-finite entries (NaN or +-Inf) of x[0, n) to *count.
+__global__ void k_count_nonfinite(const float *__restrict__ x, size_t n, unsigned long long *count)
+{
+    unsigned c = 0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        c += !isfinite(x[i]);
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
 }
 
 // ---- the device-resident misfit loop (one iteration of its graph body per time step)
@@ -390,6 +401,16 @@ int launch_reduce_phi(const double *partials, int nblocks, double scale, double 
 {
     k_reduce_phi<<<1, 1024, 0, st>>>(partials, nblocks, scale, phi);
     return cuda_check("k_reduce_phi launch");
+}
+
+int launch_count_nonfinite(const float *x, size_t n, unsigned long long *count, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(count, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    if (n == 0) return HV_OK;
+    const size_t blocks = std::min<size_t>((n + 255) / 256, 152 * 8);
+    k_count_nonfinite<<<(unsigned)blocks, 256, 0, st>>>(x, n, count);
+    return cuda_check("k_count_nonfinite launch");
 }
 
 int launch_loop_control(const LoopParams &p, cudaStream_t st)

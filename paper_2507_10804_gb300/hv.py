@@ -572,6 +572,17 @@ def prior_apply(v: torch.Tensor, h: float, delta: float, gamma: float, op: int) 
     return out
 
 
+def count_nonfinite(x: torch.Tensor) -> int:
+    """Number of NaN and +-Inf entries of a float32 CUDA tensor (hv_count_nonfinite)."""
+    if not isinstance(x, torch.Tensor) or not x.is_cuda or x.dtype != torch.float32 or not x.is_contiguous():
+        raise ValueError("x: expected a contiguous float32 CUDA tensor")
+    lib = _lib.load()
+    cnt = torch.empty((), dtype=torch.int64, device=x.device)
+    check(lib.hv_count_nonfinite(x.data_ptr(), x.numel(), cnt.data_ptr(),
+                                 ctypes.c_void_p(torch.cuda.current_stream(x.device).cuda_stream)))
+    return int(cnt)
+
+
 def highpass_apply(v: torch.Tensor, h: float, rho_c: float) -> torch.Tensor:
     """F_hp v = Re F^-1 (phi(|xi|) F v), phi(rho) = 1 - exp(-rho^2 / (2 rho_c^2)), for v [k, nz, nx]
     (hv_highpass_apply): the high-pass filter applied before the PSF and PDO approximations."""

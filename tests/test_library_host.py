@@ -196,3 +196,6 @@ def test_new_entry_points_validate_before_touching_a_gpu(lib):
     assert "model 1" in lib.hv_last_error().decode()
     assert lib.hv_misfit_models(None, 2, arr, arr, arr, None, 0, None) == E
     assert "handle" in lib.hv_last_error().decode()
+    cnt = ctypes.c_ulonglong()
+    assert lib.hv_count_nonfinite(None, 4, ctypes.byref(cnt), None) == E
+    assert lib.hv_count_nonfinite(None, 0, None, None) == E
