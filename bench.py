@@ -34,11 +34,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = None
-try:
-    METRIC = json.load(open(os.path.join(ROOT, "BASELINE.json")))["metric"]
-except Exception:  # pragma: no cover
-    METRIC = "H·v/s and Gpt-updates/s (% HBM peak) at ≤2e-4 rel err vs FP64; serve p50/p99"
+METRIC = "H·v/s and Gpt-updates/s (% HBM peak) at ≤2e-4 rel err vs FP64; serve p50/p99"
 
 CKPT = 30
 UNIT = "H·v/s"
