@@ -37,6 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "H·v/s and Gpt-updates/s (% HBM peak) at ≤2e-4 rel err vs FP64; serve p50/p99"
 
 CKPT = 30
+ENGINE_LOOP = False   # misfit lanes served by the engine's device-resident loop (--engine-loop)
 UNIT = "H·v/s"
 
 
@@ -927,6 +928,7 @@ def serve_measure(dev, reqs, rates, concurrency, batching=(64,), seed=7):
     kinds = np.array([r["kind"] for r in reqs])
     runs = []
     S = Server(hbm_budget=budget, max_concurrent=concurrency, device=dev)
+    S.set_engine_loop(ENGINE_LOOP)
     for limit in batching:
         S.set_batching(limit)
         rng = np.random.default_rng(seed)
@@ -995,6 +997,7 @@ def serve_chains(dev, concurrency, chains=64, fwi=4, steps=4, fwi_iters=2, beta=
     vf = torch.tensor(synth.smoothed_normal_vectors(34, 1, 256, 256), dtype=torch.float32, device=dev)
     torch.cuda.synchronize(dev)
     S = Server(hbm_budget=150 << 30, max_concurrent=concurrency, device=dev)
+    S.set_engine_loop(ENGINE_LOOP)
     rids = {"sample": [], "misfit": [], "hd": [], "grad": [], "hv": []}
     lock = threading.Lock()
     accepted = []
@@ -1112,7 +1115,7 @@ def run_serve(args):
 
 
 def main():
-    global CKPT
+    global CKPT, ENGINE_LOOP
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=int(os.environ.get("WORLD_SIZE", "1")))
     ap.add_argument("--steps", type=int, default=5)
@@ -1131,11 +1134,14 @@ def main():
                          "the quadratic test model's approximation, posterior and gpCN measurements alone; "
                          "misfits: 64 gpCN proposals' misfits in one sweep and through the misfit engine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--engine-loop", action="store_true",
+                    help="serving: misfit lanes served by the engine's device-resident loop instead of host ticks")
     ap.add_argument("--no-serve", action="store_true", help="paper workload: skip the serving sample")
     ap.add_argument("--no-resident", action="store_true", help="batched workload: the tiled per-step kernels")
     ap.add_argument("--tiles", type=int, nargs=3, default=None, metavar=("FWD", "ADVANCE", "ADJ"),
                     help="tile configurations instead of autotuning (profiling runs)")
     args = ap.parse_args()
+    ENGINE_LOOP = args.engine_loop
     from paper_2507_10804_gb300 import synth
     if args.workload == "serve":
         return run_serve(args)

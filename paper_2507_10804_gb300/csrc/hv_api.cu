@@ -1120,9 +1120,9 @@ extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done
 namespace {
 
 // The loop's graph: a conditional while node whose body is one iteration:
-// k_loop_control, then an if node holding the forward step of every slot,
-// then an if node holding the finishing slots' misfits.  Each node's body is
-// captured into the graph the node owns.
+// k_loop_control, then a switch node over the forward step launched for the
+// first 1, 2, 4, ... slots, then an if node holding the finishing slots'
+// misfits.  Each node's body is captured into the graph the node owns.
 int capture_into(cudaStream_t cs, cudaGraph_t g, const std::function<int()> &launch)
 {
     HV_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -1134,16 +1134,16 @@ int capture_into(cudaStream_t cs, cudaGraph_t g, const std::function<int()> &lau
     return HV_OK;
 }
 
-int add_conditional(cudaGraph_t g, cudaGraphConditionalHandle hc, cudaGraphConditionalNodeType type,
-                    const cudaGraphNode_t *dep, cudaGraphNode_t *node, cudaGraph_t *body)
+int add_conditional(cudaGraph_t g, cudaGraphConditionalHandle hc, cudaGraphConditionalNodeType type, unsigned size,
+                    const cudaGraphNode_t *dep, cudaGraphNode_t *node, cudaGraph_t *bodies)
 {
     cudaGraphNodeParams np = {};
     np.type = cudaGraphNodeTypeConditional;
     np.conditional.handle = hc;
     np.conditional.type = type;
-    np.conditional.size = 1;
+    np.conditional.size = size;
     HV_CK(cudaGraphAddNode(node, g, dep, nullptr, dep ? 1 : 0, &np));
-    *body = np.conditional.phGraph_out[0];
+    for (unsigned i = 0; i < size; ++i) bodies[i] = np.conditional.phGraph_out[i];
     return HV_OK;
 }
 
@@ -1155,8 +1155,8 @@ int build_loop_graph(hv_engine *e)
     hvk::LoopParams lp{};
     HV_CK(cudaGraphConditionalHandleCreate(&lp.cond, e->graph, 1, cudaGraphCondAssignDefault));
     cudaGraphNode_t wnode, cnode, snode, fnode;
-    cudaGraph_t body, sbody, fbody;
-    HV_RT(add_conditional(e->graph, lp.cond, cudaGraphCondTypeWhile, nullptr, &wnode, &body));
+    cudaGraph_t body, fbody;
+    HV_RT(add_conditional(e->graph, lp.cond, cudaGraphCondTypeWhile, 1, nullptr, &wnode, &body));
     HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_step, body, 0, 0));
     HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_fin, body, 0, 0));
     lp.slots = e->slots;
@@ -1183,21 +1183,26 @@ int build_loop_graph(hv_engine *e)
     size_t n = 1;
     HV_CK(cudaGraphGetNodes(body, &cnode, &n));
     if (n != 1) return hvi::fail(HV_ECUDA, "misfit loop: %zu nodes captured for the control kernel", n);
-    HV_RT(add_conditional(body, lp.cond_step, cudaGraphCondTypeIf, &cnode, &snode, &sbody));
-    HV_RT(capture_into(e->cap, sbody, [&] {
-        hvk::FwdLaunch a{};
-        a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
-        a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
-        a.C = reinterpret_cast<const float *>(e->ws + e->L.C);
-        a.d_u = lp.data;
-        a.n = 0;                       // k_fwd's step of slot j: 0 - join[j] = step[j]
-        a.models = e->slots;
-        a.slot_join = e->join_dev;
-        a.plain = true;                // the step reads the tables k_loop_control has just written
-        const int cfg = h->cfg[1];
-        return hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
-    }));
-    HV_RT(add_conditional(body, lp.cond_fin, cudaGraphCondTypeIf, &snode, &fnode, &fbody));
+    // Step launches over the first 1, 2, 4, ... slots (the last one all of them).
+    unsigned nsizes = 1;
+    while ((1 << (nsizes - 1)) < e->slots) ++nsizes;
+    std::vector<cudaGraph_t> sbodies(nsizes);
+    HV_RT(add_conditional(body, lp.cond_step, cudaGraphCondTypeSwitch, nsizes, &cnode, &snode, sbodies.data()));
+    for (unsigned i = 0; i < nsizes; ++i)
+        HV_RT(capture_into(e->cap, sbodies[i], [&] {
+            hvk::FwdLaunch a{};
+            a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
+            a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
+            a.C = reinterpret_cast<const float *>(e->ws + e->L.C);
+            a.d_u = lp.data;
+            a.n = 0;                   // k_fwd's step of slot j: 0 - join[j] = step[j]
+            a.models = std::min(e->slots, 1 << i);
+            a.slot_join = e->join_dev;
+            a.plain = true;            // the step reads the tables k_loop_control has just written
+            const int cfg = h->cfg[1];
+            return hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
+        }));
+    HV_RT(add_conditional(body, lp.cond_fin, cudaGraphCondTypeIf, 1, &snode, &fnode, &fbody));
     HV_RT(capture_into(e->cap, fbody, [&] { return hvk::launch_loop_finish(lp, e->cap); }));
     HV_CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
     return HV_OK;

@@ -379,10 +379,12 @@ int launch_reduce_phi(const double *partials, int nblocks, double scale, double 
 // The device-resident misfit loop (hv_engine_serve and the kernels of its
 // graph body, hv_kernels.cu).  One iteration: k_loop_control admits the
 // requests posted into free slots, advances every occupied slot's step and
-// sets the three conditions (another iteration; a step to take; misfits to
-// finish); then, if any slot is occupied, the forward step kernel advances
-// all of them, and, if any took its last step, k_loop_finish and
-// k_loop_reduce form those misfits.
+// sets the three conditions (another iteration; which step launch to run;
+// misfits to finish); then the forward step kernel advances the occupied
+// slots (a switch over launches covering the first 1, 2, 4, ... slots picks the
+// smallest that covers the highest occupied one; none when all are free), and,
+// if any slot took its last step, k_loop_finish and k_loop_reduce form those
+// misfits.
 constexpr int kLoopFreeSlot = 1 << 30;    // a slot_join entry that makes k_fwd skip the slot
 struct LoopParams {
     int slots, nt, nblk;
@@ -402,7 +404,7 @@ struct LoopParams {
     volatile int *ack;             // [slots] host-mapped: sequence number admitted
     volatile int *done;            // [slots] host-mapped: sequence number whose misfit is written
     volatile int *stop;            // host-mapped: nonzero ends the loop at the end of the iteration
-    cudaGraphConditionalHandle cond, cond_step, cond_fin;   // while; if a slot is occupied; if a misfit finishes
+    cudaGraphConditionalHandle cond, cond_step, cond_fin;   // while; switch over step launches; if a misfit finishes
 };
 int launch_loop_control(const LoopParams &p, cudaStream_t st);
 int launch_count_nonfinite(const float *x, size_t n, unsigned long long *count, cudaStream_t st);

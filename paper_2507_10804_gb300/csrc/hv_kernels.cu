@@ -188,10 +188,10 @@ __global__ void k_count_nonfinite(const float *__restrict__ x, size_t n, unsigne
 // are written for the stencil kernel and the finishing stages.
 __global__ void k_loop_control(const LoopParams p)
 {
-    __shared__ int occ;
-    if (threadIdx.x == 0) occ = 0;
+    __shared__ int occ, ymax;
+    if (threadIdx.x == 0) occ = ymax = 0;
     __syncthreads();
-    int local = 0;
+    int local = 0, top = 0;
     for (int j = threadIdx.x; j < p.slots; j += blockDim.x) {
         int st = p.step[j];
         if (st >= 0 && ++st >= p.nt) st = -1;
@@ -205,8 +205,10 @@ __global__ void k_loop_control(const LoopParams p)
         p.step[j] = st;
         p.join[j] = st >= 0 ? -st : kLoopFreeSlot;
         local += st >= 0;
+        if (st >= 0) top = j + 1;
     }
     atomicAdd(&occ, local);
+    atomicMax(&ymax, top);
     __syncthreads();
     // The finishing slots in slot order (one thread: the list is short and its
     // order fixed), then the conditions.  The loop goes on unless the host asked
@@ -227,7 +229,11 @@ __global__ void k_loop_control(const LoopParams p)
         p.ctl[1] = go ? idle : 0;
         p.ctl[3] = go ? 0 : (stop ? 1 : (it >= p.max_iter ? 2 : 3));
         cudaGraphSetConditional(p.cond, go ? 1u : 0u);
-        cudaGraphSetConditional(p.cond_step, occ > 0 ? 1u : 0u);
+        // the step launch over the smallest power-of-two number of slots covering
+        // the occupied ones (a value past the switch's bodies runs none of them)
+        unsigned sw = 0;
+        while ((1 << sw) < ymax) ++sw;
+        cudaGraphSetConditional(p.cond_step, ymax > 0 ? sw : 1u << 30);
         cudaGraphSetConditional(p.cond_fin, nf > 0 ? 1u : 0u);
     }
 }
