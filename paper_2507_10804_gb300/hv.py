@@ -467,8 +467,8 @@ class MisfitEngine:
 
     def close(self) -> None:
         if getattr(self, "_e", None):
-            torch.cuda.current_stream(self.P.device).synchronize()
-            self.lib.hv_engine_destroy(self._e)
+            self.lib.hv_engine_destroy(self._e)          # ends a running loop
+            torch.cuda.synchronize(self.P.device)        # posts and ticks on any stream, before the workspace goes
             self._e = None
 
     def __del__(self):
