@@ -1258,7 +1258,14 @@ extern "C" int hv_engine_serve(hv_engine *e, void *stream)
     if (!e->loop) return hvi::fail(HV_EINVAL, "hv_engine_serve: nothing was posted to this engine");
     if (e->launched && cudaEventQuery(e->ran) == cudaErrorNotReady) return HV_OK;   // running
     cudaStream_t st = (cudaStream_t)stream;
-    if (!e->exec) HV_RT(build_loop_graph(e));
+    if (!e->exec) {
+        const int rc = build_loop_graph(e);
+        if (rc != HV_OK) {                         // a later call builds it again from scratch
+            if (e->graph) cudaGraphDestroy(e->graph);
+            e->graph = nullptr;
+            return rc;
+        }
+    }
     reinterpret_cast<volatile int *>(e->hmap)[2 * e->slots] = 0;                   // no stop request
     HV_CK(cudaStreamWaitEvent(st, e->init_done, 0));
     HV_CK(cudaGraphLaunch(e->exec, st));
