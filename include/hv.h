@@ -199,9 +199,9 @@ int hv_engine_destroy(hv_engine *e);
  * memory and a loop running on the GPU admits them at its next time step,
  * advances every occupied slot and reports each finished misfit to the host,
  * with no host launch per step.  The loop is one CUDA graph launch: a
- * conditional while node whose body is one iteration (admission, the forward
- * step of every occupied slot, the misfits of the slots that took their last
- * step, the loop condition).
+ * conditional while node whose body is one iteration (the forward step of the
+ * occupied slots, admission and the loop's conditions, the misfits of the
+ * slots that took their last step).
  *  - hv_engine_post takes a free slot (HV_EBUSY when none is), enqueues on
  *    `stream` the model's preparation, the zeroing of the slot's fields and
  *    the post itself (the request's data and phi pointers and a sequence

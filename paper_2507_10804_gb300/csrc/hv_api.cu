@@ -1119,10 +1119,11 @@ extern "C" int hv_engine_tick(hv_engine *e, void *stream, int *done, int *n_done
 
 namespace {
 
-// The loop's graph: a conditional while node whose body is one iteration:
-// k_loop_control, then a switch node over the forward step launched for the
-// first 1, 2, 4, ... slots, then an if node holding the finishing slots'
-// misfits.  Each node's body is captured into the graph the node owns.
+// The loop's graph: a conditional while node whose body is a switch over
+// the iterations: the forward step launched over the first 1, 2, 4, ...
+// slots, followed by k_loop_control and an if node holding the finishing
+// slots' misfits; or k_loop_control alone.  Each node's body is captured into
+// the graph the node owns.
 int capture_into(cudaStream_t cs, cudaGraph_t g, const std::function<int()> &launch)
 {
     HV_CK(cudaStreamBeginCaptureToGraph(cs, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
@@ -1154,11 +1155,14 @@ int build_loop_graph(hv_engine *e)
     HV_CK(cudaGraphCreate(&e->graph, 0));
     hvk::LoopParams lp{};
     HV_CK(cudaGraphConditionalHandleCreate(&lp.cond, e->graph, 1, cudaGraphCondAssignDefault));
-    cudaGraphNode_t wnode, cnode, snode, fnode;
-    cudaGraph_t body, fbody;
+    cudaGraphNode_t wnode, snode;
+    cudaGraph_t body;
     HV_RT(add_conditional(e->graph, lp.cond, cudaGraphCondTypeWhile, 1, nullptr, &wnode, &body));
-    HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_step, body, 0, 0));
-    HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_fin, body, 0, 0));
+    int nsizes = 1;                    // step launches over the first 1, 2, 4, ... slots, the last all of them
+    while ((1 << (nsizes - 1)) < e->slots) ++nsizes;
+    // Every launch starts with the body without a step (the default is applied per launch), so
+    // a relaunch never advances a slot twice.
+    HV_CK(cudaGraphConditionalHandleCreate(&lp.cond_step, body, (unsigned)nsizes, cudaGraphCondAssignDefault));
     lp.slots = e->slots;
     lp.nt = h->nt;
     lp.nblk = kLoopBlocks;
@@ -1179,31 +1183,48 @@ int build_loop_graph(hv_engine *e)
     lp.ack = e->hmap_dev;
     lp.done = e->hmap_dev + e->slots;
     lp.stop = e->hmap_dev + 2 * e->slots;
-    HV_RT(capture_into(e->cap, body, [&] { return hvk::launch_loop_control(lp, e->cap); }));
-    size_t n = 1;
-    HV_CK(cudaGraphGetNodes(body, &cnode, &n));
-    if (n != 1) return hvi::fail(HV_ECUDA, "misfit loop: %zu nodes captured for the control kernel", n);
-    // Step launches over the first 1, 2, 4, ... slots (the last one all of them).
-    unsigned nsizes = 1;
-    while ((1 << (nsizes - 1)) < e->slots) ++nsizes;
-    std::vector<cudaGraph_t> sbodies(nsizes);
-    HV_RT(add_conditional(body, lp.cond_step, cudaGraphCondTypeSwitch, nsizes, &cnode, &snode, sbodies.data()));
-    for (unsigned i = 0; i < nsizes; ++i)
-        HV_RT(capture_into(e->cap, sbodies[i], [&] {
-            hvk::FwdLaunch a{};
-            a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
-            a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
-            a.C = reinterpret_cast<const float *>(e->ws + e->L.C);
-            a.d_u = lp.data;
-            a.n = 0;                   // k_fwd's step of slot j: 0 - join[j] = step[j]
-            a.models = std::min(e->slots, 1 << i);
-            a.slot_join = e->join_dev;
-            a.plain = true;            // the step reads the tables k_loop_control has just written
-            const int cfg = h->cfg[1];
-            return hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
+    lp.nsizes = nsizes;
+    std::vector<cudaGraph_t> sb(nsizes + 1);
+    HV_RT(add_conditional(body, lp.cond_step, cudaGraphCondTypeSwitch, (unsigned)nsizes + 1, nullptr, &snode,
+                          sb.data()));
+    for (int i = 0; i <= nsizes; ++i) {
+        const bool step = i < nsizes;
+        hvk::LoopParams li = lp;
+        li.after_tick = step ? 1 : 0;
+        if (step) HV_CK(cudaGraphConditionalHandleCreate(&li.cond_fin, sb[i], 0, 0));
+        HV_RT(capture_into(e->cap, sb[i], [&] {
+            int rc = HV_OK;
+            if (step) {
+                hvk::FwdLaunch a{};
+                a.u_cur = a.u_prev = reinterpret_cast<const float *>(e->ws + e->L.work);
+                a.u_next = reinterpret_cast<float *>(e->ws + e->L.work);
+                a.C = reinterpret_cast<const float *>(e->ws + e->L.C);
+                a.d_u = lp.data;
+                a.n = 0;               // k_fwd's step of slot j: 0 - join[j] = step[j]
+                a.models = std::min(e->slots, 1 << i);
+                a.slot_join = e->join_dev;
+                a.plain = true;        // first in its body
+                const int cfg = h->cfg[1];
+                rc = hvk::launch_fwd(h, cfg, rectiles_for(h, hvk::tiling(h, cfg)), e->maps, a, e->cap);
+            }
+            // behind the step by programmatic dependent launch: resident while the step drains
+            if (rc == HV_OK) rc = hvk::launch_loop_control(li, e->cap, step);
+            return rc;
         }));
-    HV_RT(add_conditional(body, lp.cond_fin, cudaGraphCondTypeIf, 1, &snode, &fnode, &fbody));
-    HV_RT(capture_into(e->cap, fbody, [&] { return hvk::launch_loop_finish(lp, e->cap); }));
+        if (!step) continue;
+        cudaGraphNode_t root[2];
+        size_t nroot = 2, nall = 0;
+        HV_CK(cudaGraphGetRootNodes(sb[i], root, &nroot));
+        HV_CK(cudaGraphGetNodes(sb[i], nullptr, &nall));
+        std::vector<cudaGraphNode_t> all(nall);
+        HV_CK(cudaGraphGetNodes(sb[i], all.data(), &nall));
+        if (nroot != 1 || nall != 2) return hvi::fail(HV_ECUDA, "misfit loop: step body of %zu nodes", nall);
+        const cudaGraphNode_t ctrl = all[0] == root[0] ? all[1] : all[0];
+        cudaGraphNode_t fnode;
+        cudaGraph_t fb;
+        HV_RT(add_conditional(sb[i], li.cond_fin, cudaGraphCondTypeIf, 1, &ctrl, &fnode, &fb));
+        HV_RT(capture_into(e->cap, fb, [&] { return hvk::launch_loop_finish(li, e->cap); }));
+    }
     HV_CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
     return HV_OK;
 }

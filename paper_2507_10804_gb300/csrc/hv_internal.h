@@ -377,14 +377,12 @@ int launch_residual(const hv_handle *h, const float *d, const float *dobs, float
 int launch_reduce_phi(const double *partials, int nblocks, double scale, double *phi, cudaStream_t st);
 
 // The device-resident misfit loop (hv_engine_serve and the kernels of its
-// graph body, hv_kernels.cu).  One iteration: k_loop_control admits the
-// requests posted into free slots, advances every occupied slot's step and
-// sets the three conditions (another iteration; which step launch to run;
-// misfits to finish); then the forward step kernel advances the occupied
-// slots (a switch over launches covering the first 1, 2, 4, ... slots picks the
-// smallest that covers the highest occupied one; none when all are free), and,
-// if any slot took its last step, k_loop_finish and k_loop_reduce form those
-// misfits.
+// graph body, hv_kernels.cu).  One iteration is one body of a switch: the
+// forward step of the occupied slots launched over the first 1, 2, 4, ...
+// slots (the smallest prefix covering the highest occupied one), then
+// k_loop_control (admission, steps, conditions), then, if any slot took its
+// last step, k_loop_finish and k_loop_reduce form those misfits; or, with no
+// slot occupied (and first in every launch), k_loop_control alone.
 constexpr int kLoopFreeSlot = 1 << 30;    // a slot_join entry that makes k_fwd skip the slot
 struct LoopParams {
     int slots, nt, nblk;
@@ -405,8 +403,10 @@ struct LoopParams {
     volatile int *done;            // [slots] host-mapped: sequence number whose misfit is written
     volatile int *stop;            // host-mapped: nonzero ends the loop at the end of the iteration
     cudaGraphConditionalHandle cond, cond_step, cond_fin;   // while; switch over step launches; if a misfit finishes
+    int nsizes;                    // step launches of the switch; body nsizes has no step
+    int after_tick;                // k_loop_control runs behind a step (advance the slots, list the finishing ones)
 };
-int launch_loop_control(const LoopParams &p, cudaStream_t st);
+int launch_loop_control(const LoopParams &p, cudaStream_t st, bool pdl);
 int launch_count_nonfinite(const float *x, size_t n, unsigned long long *count, cudaStream_t st);
 int launch_loop_finish(const LoopParams &p, cudaStream_t st);
 int launch_loop_post(int *post, const float **dobs_tbl, double **phi_tbl, int slot, int seq, const float *dobs,

@@ -181,20 +181,34 @@ __global__ void k_count_nonfinite(const float *__restrict__ x, size_t n, unsigne
 
 // ---- the device-resident misfit loop (one iteration of its graph body per time step)
 
-// Admission and step bookkeeping of every slot (one block): a slot that took its
-// last step in the previous iteration is free again; a free slot whose mailbox
-// holds a new sequence number is admitted at step 0 (its model and fields were
-// prepared before the number was posted); the tables of this iteration's step
-// are written for the stencil kernel and the finishing stages.
+// Admission and step bookkeeping of every slot (one block).  After a step
+// (after_tick): the slots that took their last step are listed for the misfit
+// kernels and freed, and every other occupied slot advances; then (in both
+// modes) a free slot whose mailbox holds a new sequence number is admitted at
+// step 0 (its model and fields were prepared before the number was posted),
+// the step table of the next step is written for k_fwd, and the conditions
+// are set: another iteration or not, which step launch comes next (the
+// smallest power-of-two prefix of slots covering the highest occupied one, or
+// the body without a step), and whether this iteration's misfit kernels run.
+// Launched behind the step by programmatic dependent launch: it is resident
+// while the step drains and waits for it before touching the tables.
 __global__ void k_loop_control(const LoopParams p)
 {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     __shared__ int occ, ymax;
-    if (threadIdx.x == 0) occ = ymax = 0;
+    if (threadIdx.x == 0) {
+        occ = ymax = 0;
+        int nf = 0;                            // in slot order (one thread: the list is short, its order fixed)
+        if (p.after_tick)
+            for (int j = 0; j < p.slots; ++j)
+                if (p.step[j] == p.nt - 1) p.fin[nf++] = j;
+        p.fin[p.slots] = nf;
+    }
     __syncthreads();
     int local = 0, top = 0;
     for (int j = threadIdx.x; j < p.slots; j += blockDim.x) {
         int st = p.step[j];
-        if (st >= 0 && ++st >= p.nt) st = -1;
+        if (p.after_tick && st >= 0 && ++st >= p.nt) st = -1;
         const int posted = *reinterpret_cast<volatile const int *>(p.post + j);
         if (st < 0 && posted != p.seen[j]) {
             __threadfence();                   // the request's prepared fields, written before the post
@@ -210,16 +224,10 @@ __global__ void k_loop_control(const LoopParams p)
     atomicAdd(&occ, local);
     atomicMax(&ymax, top);
     __syncthreads();
-    // The finishing slots in slot order (one thread: the list is short and its
-    // order fixed), then the conditions.  The loop goes on unless the host asked
-    // it to stop, max_iter iterations of this launch have run, or no slot has
-    // been occupied for idle_max iterations (a request posted after this scan is
-    // admitted by the next launch).
+    // The loop goes on unless the host asked it to stop, max_iter iterations of
+    // this launch have run, or no slot has been occupied for idle_max
+    // iterations (a request posted after this scan is admitted by the next launch).
     if (threadIdx.x == 0) {
-        int nf = 0;
-        for (int j = 0; j < p.slots; ++j)
-            if (p.step[j] == p.nt - 1) p.fin[nf++] = j;
-        p.fin[p.slots] = nf;
         p.ctl[2] = occ;
         const int it = p.ctl[0] + 1;
         const int idle = occ > 0 ? 0 : p.ctl[1] + 1;
@@ -229,12 +237,10 @@ __global__ void k_loop_control(const LoopParams p)
         p.ctl[1] = go ? idle : 0;
         p.ctl[3] = go ? 0 : (stop ? 1 : (it >= p.max_iter ? 2 : 3));
         cudaGraphSetConditional(p.cond, go ? 1u : 0u);
-        // the step launch over the smallest power-of-two number of slots covering
-        // the occupied ones (a value past the switch's bodies runs none of them)
         unsigned sw = 0;
         while ((1 << sw) < ymax) ++sw;
-        cudaGraphSetConditional(p.cond_step, ymax > 0 ? sw : 1u << 30);
-        cudaGraphSetConditional(p.cond_fin, nf > 0 ? 1u : 0u);
+        cudaGraphSetConditional(p.cond_step, ymax > 0 ? sw : (unsigned)p.nsizes);
+        if (p.after_tick) cudaGraphSetConditional(p.cond_fin, p.fin[p.slots] > 0 ? 1u : 0u);
     }
 }
 
@@ -419,9 +425,19 @@ int launch_count_nonfinite(const float *x, size_t n, unsigned long long *count, 
     return cuda_check("k_count_nonfinite launch");
 }
 
-int launch_loop_control(const LoopParams &p, cudaStream_t st)
+int launch_loop_control(const LoopParams &p, cudaStream_t st, bool pdl)
 {
-    k_loop_control<<<1, 256, 0, st>>>(p);
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3(1);
+    lc.blockDim = dim3(256);
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = pdl ? 1 : 0;
+    cudaError_t e = cudaLaunchKernelEx(&lc, k_loop_control, p);
+    if (e != cudaSuccess) return hvi::fail(HV_ECUDA, "k_loop_control launch: %s", cudaGetErrorString(e));
     return cuda_check("k_loop_control launch");
 }
 
