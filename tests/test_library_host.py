@@ -199,3 +199,17 @@ def test_new_entry_points_validate_before_touching_a_gpu(lib):
     cnt = ctypes.c_ulonglong()
     assert lib.hv_count_nonfinite(None, 4, ctypes.byref(cnt), None) == E
     assert lib.hv_count_nonfinite(None, 0, None, None) == E
+    # the misfit engine and its device-resident loop, and the server's lane switches
+    i1, i2, i3 = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    assert lib.hv_engine_create(None, 4, None, 0, ctypes.byref(ctypes.c_void_p())) == E
+    assert lib.hv_engine_create(None, 0, None, 0, ctypes.byref(ctypes.c_void_p())) == E
+    assert lib.hv_engine_join(None, None, None, None, None, ctypes.byref(i1)) == E
+    assert lib.hv_engine_tick(None, None, ctypes.byref(i1), ctypes.byref(i2)) == E
+    assert lib.hv_engine_post(None, None, None, None, None, ctypes.byref(i1)) == E
+    assert lib.hv_engine_serve(None, None) == E
+    assert lib.hv_engine_poll(None, ctypes.byref(i1), ctypes.byref(i2), ctypes.byref(i3)) == E
+    assert lib.hv_engine_stop(None) == E
+    assert lib.hv_engine_active(None, ctypes.byref(i1)) == E
+    assert lib.hv_engine_destroy(None) == 0
+    assert lib.hv_server_set_engine(None, 8) == E
+    assert lib.hv_server_set_engine_loop(None, 1) == E
