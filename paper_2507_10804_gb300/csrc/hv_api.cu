@@ -542,7 +542,7 @@ int run_adjoint(hv_handle *h, int kind, const float *m, const float *in, int k, 
             return hvk::launch_partial_image(h, m, reinterpret_cast<double *>((char *)ws + L.img), fmt,
                                              L.resident ? h->ns : L.G, kk, ext, st);
         HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>((char *)ws + L.img), fmt, L.resident ? h->ns : L.G, kk,
-                                   out32, out64, st));
+                                   out32, out64, reinterpret_cast<double *>((char *)ws + L.D), st));
     }
     return HV_OK;
 }
@@ -1555,7 +1555,7 @@ extern "C" int hv_apply_batch(hv_handle *h, const float *m, const hv_batch *b, i
     {
         ProfScope ps(h, st, HV_K_OTHER);
         HV_RT(hvk::launch_finalize(h, m, reinterpret_cast<double *>(w + L.img), h->img_f64 ? hvk::kImgF64 : hvk::kImgPairs,
-                                   L.G, B.K, O, nullptr, st));
+                                   L.G, B.K, O, nullptr, reinterpret_cast<double *>(w + L.D), st));
     }
     at = 0;
     for (int i = 0; i < b->n_hv; ++i) {

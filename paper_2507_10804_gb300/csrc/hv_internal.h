@@ -364,11 +364,13 @@ int launch_psf_impulses(const PsfGeo &g, float *v, cudaStream_t st);   // v zero
 int launch_psf_extract(const PsfGeo &g, const float *Hv, float *psf, cudaStream_t st);
 int launch_psf_apply(const PsfGeo &g, const float *psf, const float *v, int k, float *out, cudaStream_t st);
 int psf_apply_smem_bytes(int S, int R, int nvec);   // dynamic shared memory of the apply kernel
-// Image formats (see k_finalize): 0 double-float pairs per shot group, 1 FP64
+// Image formats (img_at): 0 double-float pairs per shot group, 1 FP64
 // per shot group (both in the field layout), 2 one dense FP64 [k][NZ][NX] image.
 constexpr int kImgPairs = 0, kImgF64 = 1, kImgDense = 2;
+// The fold of the group images onto the interior; scratch: k NZ nx doubles,
+// apart from img (the call's Born / adjoint field region, free by then).
 int launch_finalize(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, float *out32,
-                    double *out64, cudaStream_t st);
+                    double *out64, double *scratch, cudaStream_t st);
 int launch_partial_image(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, double *out,
                          cudaStream_t st);
 int launch_fold_ext(const hv_handle *h, const double *ext, int k, float *out32, double *out64, cudaStream_t st);
