@@ -367,9 +367,10 @@ int psf_apply_smem_bytes(int S, int R, int nvec);   // dynamic shared memory of 
 // Image formats (img_at): 0 double-float pairs per shot group, 1 FP64
 // per shot group (both in the field layout), 2 one dense FP64 [k][NZ][NX] image.
 constexpr int kImgPairs = 0, kImgF64 = 1, kImgDense = 2;
-// The fold of the group images onto the interior; scratch: k NZ nx doubles,
-// apart from img (the call's Born / adjoint field region, free by then).
-int launch_finalize(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, float *out32,
+// The fold of the group images onto the interior; the group sums overwrite
+// group 0's image; scratch: k NZ nx doubles apart from img (the call's Born /
+// adjoint field region, free by then).
+int launch_finalize(const hv_handle *h, const float *m, double *img, int fmt, int G, int k, float *out32,
                     double *out64, double *scratch, cudaStream_t st);
 int launch_partial_image(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, double *out,
                          cudaStream_t st);

@@ -38,8 +38,6 @@ __global__ void k_prep(const float *__restrict__ m, const float *__restrict__ v,
             b[(size_t)j * fsize + off] = (float)(2.0 * (double)v[((size_t)j * nz + iz) * nx + ix] / mm);
 }
 
-// Hv[j][iz][ix] = (2 / (m h^2)) sum over the E-preimage of (iz, ix) of sum_g img[g][j],
-// the partial images held as double-float pairs (hi, lo), summed in FP64.
 // The image of group g, vector j at padded node offset `off` in format fmt:
 // 0: double-float (hi, lo) FP32 pairs per group in the field layout, 1: FP64
 // per group in the field layout, 2: one dense FP64 image [k][NZ][NX] (g = 0).
@@ -54,14 +52,27 @@ __device__ __forceinline__ double img_at(const double *img, int fmt, int g, int 
     return img[((size_t)j * NZ + z) * NX + x];
 }
 
-// The fold Hv[j][iz][ix] = 2 / (m h^2) * (E^T sum_g img_g)[iz][ix] in two
-// passes, so that no thread walks a whole sponge corner (41 x 41 nodes per
-// group on the benchmark's grid): k_fold_x sums, for every padded row, the
-// x-preimage of each interior column over the groups (group order innermost,
-// FP64) into t[j][z][ix]; k_fold_z sums the z-preimage of each interior row
-// of t and scales.
-__global__ void k_fold_x(const double *__restrict__ img, int fmt, int G, int k, int nx, int nb, int NZ, int NX, int P,
-                         size_t fsize, double *__restrict__ t)
+// The fold Hv[j][iz][ix] = 2 / (m h^2) * (E^T sum_g img_g)[iz][ix] in three
+// passes, so that no thread walks more than one group list or one sponge
+// width (a 41 x 41 corner of 4 groups on the benchmark's grid, of 32 per-pair
+// images on the resident path, took one thread 1-2 ms): k_fold_g sums the
+// groups of every padded node in group order in FP64 and writes the sum over
+// group 0's word of that node (each thread reads and writes its own node
+// only); k_fold_x sums the x-preimage of each interior column of every padded
+// row into t[j][z][ix]; k_fold_z sums the z-preimage of each interior row of t
+// and scales.
+__global__ void k_fold_g(double *img, int fmt, int G, int k, int NZ, int NX, int P, size_t fsize)
+{
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y, j = blockIdx.z;
+    if (x >= NX) return;
+    const size_t off = (size_t)(z + GH) * P + (x + GH);
+    double acc = 0.0;
+    for (int g = 0; g < G; ++g) acc += img_at(img, fmt, g, k, j, fsize, off, z, x, NZ, NX);
+    img[(size_t)j * fsize + off] = acc;
+}
+
+__global__ void k_fold_x(const double *__restrict__ gsum, int nx, int nb, int NZ, int NX, int P, size_t fsize,
+                         double *__restrict__ t)
 {
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int z = blockIdx.y;
@@ -69,11 +80,7 @@ __global__ void k_fold_x(const double *__restrict__ img, int fmt, int G, int k, 
     if (ix >= nx) return;
     const int xlo = (ix == 0) ? 0 : ix + nb, xhi = (ix == nx - 1) ? NX - 1 : ix + nb;
     double acc = 0.0;
-    for (int x = xlo; x <= xhi; ++x) {
-        const size_t off = (size_t)(z + GH) * P + (x + GH);
-#pragma unroll 8
-        for (int g = 0; g < G; ++g) acc += img_at(img, fmt, g, k, j, fsize, off, z, x, NZ, NX);   // loads ahead, adds in order
-    }
+    for (int x = xlo; x <= xhi; ++x) acc += gsum[(size_t)j * fsize + (size_t)(z + GH) * P + (x + GH)];
     t[((size_t)j * NZ + z) * nx + ix] = acc;
 }
 
@@ -86,7 +93,6 @@ __global__ void k_fold_z(const float *__restrict__ m, const double *__restrict__
     if (ix >= nx) return;
     const int zlo = (iz == 0) ? 0 : iz + nb, zhi = (iz == nz - 1) ? NZ - 1 : iz + nb;
     double acc = 0.0;
-#pragma unroll 8
     for (int z = zlo; z <= zhi; ++z) acc += t[((size_t)j * NZ + z) * nx + ix];
     const double mm = (double)m[(size_t)iz * nx + ix];
     const double val = 2.0 / (mm * h * h) * acc;
@@ -393,11 +399,13 @@ int launch_prep(const hv_handle *h, const float *m, const float *v, int k, float
     return cuda_check("k_prep launch");
 }
 
-int launch_finalize(const hv_handle *h, const float *m, const double *img, int fmt, int G, int k, float *out32,
+int launch_finalize(const hv_handle *h, const float *m, double *img, int fmt, int G, int k, float *out32,
                     double *out64, double *scratch, cudaStream_t st)
 {
-    dim3 gx((h->nx + 127) / 128, h->NZ, k), gz((h->nx + 127) / 128, h->nz, k);
-    k_fold_x<<<gx, 128, 0, st>>>(img, fmt, G, k, h->nx, h->nb, h->NZ, h->NX, h->P, h->fsize, scratch);
+    dim3 gg((h->NX + 127) / 128, h->NZ, k), gx((h->nx + 127) / 128, h->NZ, k), gz((h->nx + 127) / 128, h->nz, k);
+    k_fold_g<<<gg, 128, 0, st>>>(img, fmt, G, k, h->NZ, h->NX, h->P, h->fsize);
+    HV_RT_INTERNAL(cuda_check("k_fold_g launch"));
+    k_fold_x<<<gx, 128, 0, st>>>(img, h->nx, h->nb, h->NZ, h->NX, h->P, h->fsize, scratch);
     HV_RT_INTERNAL(cuda_check("k_fold_x launch"));
     k_fold_z<<<gz, 128, 0, st>>>(m, scratch, h->nz, h->nx, h->nb, h->NZ, h->h, out32, out64);
     return cuda_check("k_fold_z launch");

@@ -894,7 +894,7 @@ __global__ void __launch_bounds__(C::NT, C::NT <= 64 ? 8 : C::NT <= 128 ? 4 : 2)
     // Adds the FP32 partial of a finished group of shots to that group's image.
     // The image is held as double-float pairs (hi, lo) and added to by TwoSum on
     // the FP32 pipe -- about 2^-44 relative accuracy, where FP64 arithmetic (and
-    // its conversions) would run on this part's slow FP64 pipe; k_fold_x sums
+    // its conversions) would run on this part's slow FP64 pipe; k_fold_g sums
     // the pairs in FP64.
     auto add_df = [](float2 &v, float a) {
         const float s = __fadd_rn(v.x, a), bv = __fsub_rn(s, v.x);
