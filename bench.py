@@ -302,12 +302,18 @@ def peaks():
 def csrc_hash(resident: bool = False) -> str:
     """Hash of the device code the DRAM counters under profiles/ were taken on: the tiled stencil kernels
     (csrc/hv_stencil.cu up to the resident kernels) or, for the resident kernels, the file's device code
-    up to the host side.  Counters apply only while that code is unchanged."""
+    up to the host side, with comments and blank space removed.  Counters apply only while that code is
+    unchanged."""
+    import re
     text = open(os.path.join(ROOT, "paper_2507_10804_gb300", "csrc", "hv_stencil.cu"), "rb").read()
     mark = b"// ------------------------------------------------------------------ "
     cut = text.find(mark + (b"host side" if resident else b"resident kernels"))
+    code = text[:cut] if cut >= 0 else text
+    code = re.sub(rb"/\*.*?\*/", b"", code, flags=re.S)
+    code = re.sub(rb"//[^\n]*", b"", code)
+    code = re.sub(rb"\s+", b" ", code)
     h = hashlib.sha256()
-    h.update(text[:cut] if cut >= 0 else text)
+    h.update(code)
     return h.hexdigest()[:16]
 
 
